@@ -1,0 +1,636 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a value the
+paper prints, an identity the paper states (consistency, Tadmor's EC condition,
+the rotation identity, dU/dV = R R^T), a closed form, an independent symbolic
+derivation, or an invariant of the scheme (discrete SCL / free-stream, zero
+entropy production of the EC scheme, design order).  No GPU is needed.
+"""
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle
+from paper_2202_07989_gb300 import workloads as W
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")))
+
+CASES = [(2, 1), (2, 2), (3, 1), (3, 2)]
+
+
+def _random_state(pb, rng, pinf_scale=1.0):
+    rl = rng.uniform(0.3, 2.0, size=pb.N)
+    v = rng.uniform(-1.0, 1.0, size=pb.d)
+    p = rng.uniform(0.3, 2.0)
+    return W.cons_state(pb, rl, v, p)[: pb.nc]
+
+
+def _pb(d, N, pinf=0.0, **kw):
+    pb = W.random_problem(d, N, (12,) * d, pinf=pinf, **kw)
+    if N == 2 and pinf:
+        pb = pb.with_(pinf=(pinf, 0.5 * pinf))
+    return pb
+
+
+# ---------------------------------------------------------------------------
+# coefficients
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("w", [1, 2, 3])
+def test_alpha_matches_paper_conditions(w):
+    """alpha_{w,m} of Sec. 3.1 equal the exact rational solutions."""
+    o = Oracle(_pb(2, 1))
+    want = [float(Fraction(a, b)) for a, b in GOLD["alpha"]["w%d" % w]]
+    np.testing.assert_allclose(o.alpha(w), want, rtol=0, atol=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# pointwise physics
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("d,N", CASES)
+@pytest.mark.parametrize("pinf", [0.0, 2.5])
+def test_entropy_variables_are_gradient_of_eta(d, N, pinf):
+    """V = eta'(U)^T (Definition of the entropy pair, Sec. 1) by central differences of eta."""
+    pb = _pb(d, N, pinf)
+    o = Oracle(pb)
+    rng = np.random.default_rng(11)
+    for _ in range(5):
+        U = _random_state(pb, rng)
+        V = o.entropy_vars(U)
+        g = np.zeros(pb.nc)
+        for q in range(pb.nc):
+            h = 1e-6 * max(1.0, abs(U[q]))
+            up, um = U.copy(), U.copy()
+            up[q] += h
+            um[q] -= h
+            g[q] = (o.eta(up) - o.eta(um)) / (2 * h)
+        np.testing.assert_allclose(V, g, rtol=2e-7, atol=2e-7)
+
+
+@pytest.mark.parametrize("d,N", CASES)
+@pytest.mark.parametrize("pinf", [0.0, 2.5])
+def test_potentials(d, N, pinf):
+    """phi = V^T U - eta and psi_k = V^T F_k - q_k = phi v_k with q_k = eta v_k (Sec. 1, Sec. 3.3)."""
+    pb = _pb(d, N, pinf)
+    o = Oracle(pb)
+    rng = np.random.default_rng(12)
+    for _ in range(5):
+        U = _random_state(pb, rng)
+        V, eta, phi = o.entropy_vars(U), o.eta(U), o.phi(U)
+        _, v, _, _ = o.primitives(U)
+        assert abs(V @ U - eta - phi) <= 1e-13 * (abs(V) @ abs(U) + abs(eta))
+        for k in range(d):
+            F = o.phys_flux(k, U)
+            lhs = V @ F - eta * v[k]
+            assert abs(lhs - phi * v[k]) <= 1e-13 * (abs(V) @ abs(F) + abs(eta * v[k]))
+
+
+def test_logmean_against_high_precision():
+    """{a}^ln = [[a]]/[[ln a]] (Sec. 3.3.1) to 1e-15 across both branches (mpmath reference)."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 50
+    o = Oracle(_pb(2, 1))
+    rng = np.random.default_rng(13)
+    for rel in [0.0, 1e-14, 1e-9, 1e-5, 1e-3, 0.019, 0.021, 0.1, 1.0, 10.0]:
+        for _ in range(20):
+            a = rng.uniform(0.1, 10.0)
+            b = a * (1.0 + rel * rng.uniform(-1, 1)) if rel < 1 else a * rng.uniform(1.0, 1.0 + rel)
+            got = o.logmean(a, b)
+            A, B = mpmath.mpf(a), mpmath.mpf(b)
+            want = A if A == B else (B - A) / (mpmath.log(B) - mpmath.log(A))
+            f = (b - a) / (b + a)
+            # series branch: a few ulps; [[a]]/[[ln a]] branch: cancellation in [[ln a]]
+            # costs about 5e-16 / |[[ln a]]|, at most ~3e-14 above the branch threshold
+            tol = 2e-15 if f * f < 1e-4 else 1e-13
+            assert abs(got - float(want)) <= tol * float(want), (a, b, got, float(want))
+            assert got == o.logmean(b, a)
+
+
+# ---------------------------------------------------------------------------
+# two-point EC flux (Sec. 3.3)
+# ---------------------------------------------------------------------------
+
+def _random_metrics(d, rng):
+    return rng.uniform(-1.0, 1.0, size=d + 1) + np.r_[0.0, np.ones(d)]
+
+
+def _pair(pb, rng, kind):
+    Ul = _random_state(pb, rng)
+    if kind == "near":
+        rl, v, T, p = Oracle(pb).primitives(Ul)
+        rl2 = rl * (1 + 1e-4 * rng.uniform(-1, 1, size=pb.N))
+        v2 = v + 1e-4 * rng.uniform(-1, 1, size=pb.d)
+        p2 = p * (1 + 1e-4 * rng.uniform(-1, 1))
+        Ur = W.cons_state(pb, rl2, v2, p2)[: pb.nc]
+    else:
+        Ur = _random_state(pb, rng)
+    return Ul, Ur
+
+
+@pytest.mark.parametrize("d,N", CASES)
+@pytest.mark.parametrize("pinf", [0.0, 2.5])
+def test_ec_pair_consistency(d, N, pinf):
+    """F(U, U, M, M) = J xi_t U + sum_j J xi_x_j F_j(U) (Proposition 3.1)."""
+    pb = _pb(d, N, pinf)
+    o = Oracle(pb)
+    rng = np.random.default_rng(14)
+    for _ in range(10):
+        U = _random_state(pb, rng)
+        M = _random_metrics(d, rng)
+        got = o.ec_pair(U, U, M, M)
+        want = M[0] * U + sum(M[1 + j] * o.phys_flux(j, U) for j in range(d))
+        scale = abs(M[0]) * abs(U) + sum(abs(M[1 + j]) * abs(o.phys_flux(j, U)) for j in range(d))
+        assert np.all(np.abs(got - want) <= 1e-13 * scale)
+
+
+@pytest.mark.parametrize("d,N", CASES)
+@pytest.mark.parametrize("pinf", [0.0, 2.5])
+@pytest.mark.parametrize("kind", ["far", "near"])
+def test_ec_condition_and_symmetry(d, N, pinf, kind):
+    """Tadmor's condition Eq. (ECCondition_curv) to 1e-13 relative; symmetry F(l,r) = F(r,l)."""
+    pb = _pb(d, N, pinf)
+    o = Oracle(pb)
+    rng = np.random.default_rng(15)
+    for _ in range(20):
+        Ul, Ur = _pair(pb, rng, kind)
+        Ml, Mr = _random_metrics(d, rng), _random_metrics(d, rng)
+        F = o.ec_pair(Ul, Ur, Ml, Mr)
+        assert np.array_equal(F, o.ec_pair(Ur, Ul, Mr, Ml))
+        dV = o.entropy_vars(Ur) - o.entropy_vars(Ul)
+        _, vl, _, _ = o.primitives(Ul)
+        _, vr, _, _ = o.primitives(Ur)
+        pl, pr = o.phi(Ul), o.phi(Ur)
+        rhs = 0.5 * (Ml[0] + Mr[0]) * (pr - pl)
+        scale = abs(0.5 * (Ml[0] + Mr[0])) * (abs(pr) + abs(pl))
+        for j in range(d):
+            mj = 0.5 * (Ml[1 + j] + Mr[1 + j])
+            rhs += mj * (pr * vr[j] - pl * vl[j])
+            scale += abs(mj) * (abs(pr * vr[j]) + abs(pl * vl[j]))
+        lhs = dV @ F
+        scale += np.abs(o.entropy_vars(Ur)) @ np.abs(F) + np.abs(o.entropy_vars(Ul)) @ np.abs(F)
+        assert abs(lhs - rhs) <= 1e-13 * scale, (lhs, rhs, scale)
+
+
+@pytest.mark.parametrize("N", [1, 2])
+def test_rotation_identity(N):
+    """F~_{phi,theta} = T^{-1} F~_1(T U_l, T U_r) (Eq. (rotation)) gives F~_2, F~_3 at the two
+    stated angle pairs and the normal combination sum_j n_j F~_j for any angles."""
+    pb = _pb(3, N, 1.5)
+    o = Oracle(pb)
+    rng = np.random.default_rng(16)
+
+    def Tmat(ph, th):
+        T = np.eye(pb.nc)
+        cp, sp, ct, st = math.cos(ph), math.sin(ph), math.cos(th), math.sin(th)
+        T[N:N + 3, N:N + 3] = [[cp * ct, cp * st, sp], [-st, ct, 0], [-sp * ct, -sp * st, cp]]
+        return T
+
+    for _ in range(10):
+        Ul, Ur = _pair(pb, rng, "far")
+        for (ph, th), j in [((0.0, math.pi / 2), 1), ((math.pi / 2, 0.0), 2)]:
+            T = Tmat(ph, th)
+            got = np.linalg.solve(T, o.Ftilde(0, T @ Ul, T @ Ur))
+            np.testing.assert_allclose(got, o.Ftilde(j, Ul, Ur), rtol=1e-13, atol=1e-13)
+        ph, th = rng.uniform(0, 2 * math.pi), rng.uniform(0, math.pi)
+        T = Tmat(ph, th)
+        n = T[N, N:N + 3]
+        got = np.linalg.solve(T, o.Ftilde(0, T @ Ul, T @ Ur))
+        want = sum(n[j] * o.Ftilde(j, Ul, Ur) for j in range(3))
+        np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# scaled eigenvectors (Sec. 3.4, Eq. (eigen))
+# ---------------------------------------------------------------------------
+
+def _jac(f, U, n):
+    Jm = np.zeros((n, len(U)))
+    for q in range(len(U)):
+        h = 1e-6 * max(1.0, abs(U[q]))
+        up, um = U.copy(), U.copy()
+        up[q] += h
+        um[q] -= h
+        Jm[:, q] = (f(up) - f(um)) / (2 * h)
+    return Jm
+
+
+@pytest.mark.parametrize("d,N", CASES)
+@pytest.mark.parametrize("pinf", [0.0, 2.5])
+def test_scaled_eigenvectors(d, N, pinf):
+    """dU/dV = R R^T and dF_1/dU R = R Lambda with Lambda = diag(v1-c, v1, .., v1, v1+c)."""
+    pb = _pb(d, N, pinf)
+    o = Oracle(pb)
+    rng = np.random.default_rng(17)
+    for _ in range(4):
+        U = _random_state(pb, rng)
+        R = o.eigvec_point(U)
+        dVdU = _jac(o.entropy_vars, U, pb.nc)
+        np.testing.assert_allclose(R @ R.T @ dVdU, np.eye(pb.nc), atol=2e-6)
+        rl, v, T, p = o.primitives(U)
+        rho = rl.sum()
+        Rm = sum((pb.gamma[l] - 1) * pb.cv[l] * rl[l] for l in range(N)) / rho
+        Gm = sum(pb.gamma[l] * pb.cv[l] * rl[l] for l in range(N)) / sum(pb.cv[l] * rl[l] for l in range(N))
+        c = math.sqrt(Rm * Gm * T)
+        lam = np.array([v[0] - c] + [v[0]] * (pb.nc - 2) + [v[0] + c])
+        A = _jac(lambda u: o.phys_flux(0, u), U, pb.nc)
+        np.testing.assert_allclose(A @ R, R * lam[None, :], atol=2e-6 * max(1.0, np.abs(A @ R).max()))
+
+
+@pytest.mark.parametrize("d,N", CASES)
+def test_interface_eigenvectors_reduce_to_point(d, N):
+    """With U_l = U_r the averaged R of Sec. 3.4 equals the point-state R."""
+    pb = _pb(d, N, 1.0)
+    o = Oracle(pb)
+    rng = np.random.default_rng(18)
+    U = _random_state(pb, rng)
+    R, _ = o.eigvec_avg(U, U)
+    np.testing.assert_allclose(R, o.eigvec_point(U), rtol=1e-12, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# WENO-MR (Appendix A)
+# ---------------------------------------------------------------------------
+
+def test_weno_linear_limit_is_five_point_stencil():
+    """With linear weights (eps -> infinity) the value is h_3(x_{j+1/2}) = (2,-13,47,27,-3)/60."""
+    o = Oracle(_pb(2, 1))
+    rng = np.random.default_rng(19)
+    st = np.array(GOLD["weno_mr"]["linear_stencil_60ths"]) / 60.0
+    for _ in range(20):
+        w5 = rng.uniform(-2, 2, size=5)
+        got = o.weno_mr(w5, eps=1e30)
+        assert abs(got - st @ w5) <= 1e-14 * (np.abs(st) @ np.abs(w5))
+
+
+def test_weno_weights_from_symbolic_indicators():
+    """beta_1..beta_3, tau and the nonlinear weights rebuilt from the definitions of
+    Appendix A with sympy (beta_2, beta_3 integrated over the central cell), then
+    compared with the oracle's WENO-MR value."""
+    sp = pytest.importorskip("sympy")
+    x = sp.symbols("x")
+    Ws = sp.symbols("w0:5")
+    L = [sp.Integer(1), x, x ** 2 - sp.Rational(1, 12), x ** 3 - sp.Rational(3, 20) * x,
+         x ** 4 - sp.Rational(3, 14) * x ** 2 + sp.Rational(3, 560)]
+
+    def recon(deg, cells):
+        cs = sp.symbols("c0:%d" % (deg + 1))
+        h = sum(ci * Li for ci, Li in zip(cs, L))
+        eqs = [sp.integrate(h, (x, l - sp.Rational(1, 2), l + sp.Rational(1, 2))) - Ws[l + 2] for l in cells]
+        return sp.expand(h.subs(sp.solve(eqs, cs)))
+
+    h2 = recon(2, [-1, 0, 1])
+    h3 = recon(4, [-2, -1, 0, 1, 2])
+    half = sp.Rational(1, 2)
+
+    def beta(h, deg):
+        return sum(sp.integrate(sp.diff(h, x, a) ** 2, (x, -half, half)) for a in range(1, deg + 1))
+
+    b2f = sp.lambdify(Ws, beta(h2, 2))
+    b3f = sp.lambdify(Ws, beta(h3, 4))
+    h2f = sp.lambdify(Ws, h2.subs(x, half))
+    h3f = sp.lambdify(Ws, h3.subs(x, half))
+    o = Oracle(_pb(2, 1))
+    chi = np.array([float(Fraction(a, b)) for a, b in GOLD["weno_mr"]["chi"]])
+    eps = GOLD["weno_mr"]["eps"]
+    rng = np.random.default_rng(20)
+    samples = [rng.uniform(-1, 1, size=5) for _ in range(30)]
+    samples += [np.array([0, 0, 0, 0, 1.0]), np.array([0, 0, 1.0, 1, 1]), np.array([1.0, 1, 1, 0, 0])]
+    for w in samples:
+        b1 = min((w[2] - w[1]) ** 2, (w[3] - w[2]) ** 2)
+        b2, b3 = b2f(*w), b3f(*w)
+        tau = (0.5 * (abs(b3 - b1) + abs(b3 - b2))) ** 2
+        wb = chi * (1 + tau / (eps + np.array([b1, b2, b3])))
+        om = wb / wb.sum()
+        hv = np.array([w[2], h2f(*w), h3f(*w)])
+        want = om[0] * hv[0] + om[1] * hv[1] + om[2] * (hv[2] / chi[2] - chi[0] / chi[2] * hv[0] - chi[1] / chi[2] * hv[1])
+        got = o.weno_mr(w)
+        assert abs(got - want) <= 1e-12 * max(1.0, np.abs(w).max()), (w, got, want)
+
+
+def test_weno_jump_is_fifth_order():
+    """[[W]]^WENOMR = W^+ - W^- at x_{j+1/2} vanishes at fifth order on smooth data."""
+    o = Oracle(_pb(2, 1))
+    errs = []
+    for n in [20, 40, 80]:
+        h = 2 * math.pi / n
+        xs = 0.3 + h * np.arange(-2, 4)
+        f = np.sin(xs)
+        wm = o.weno_mr(f[0:5])
+        wp = o.weno_mr(f[5:0:-1])
+        errs.append(abs(wp - wm))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(orders) > 4.5, (errs, orders)
+
+
+# ---------------------------------------------------------------------------
+# metrics (Sec. 3.2)
+# ---------------------------------------------------------------------------
+
+def _interior(pb, M, depth):
+    sl = [slice(None)]
+    for k in (2, 1, 0):
+        if k < pb.d:
+            sl.append(slice(3 + depth, 3 + pb.n[k] - depth))
+        else:
+            sl.append(slice(None))
+    return M[tuple(sl)]
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_metrics_exact_for_polynomial_maps(d):
+    """J xi_k/x_j of Eq. (SCLCoeff) (and the 2D degenerate case) equal the cofactors of
+    dx/dxi for polynomial maps the 2w-order central differences integrate exactly."""
+    n = 20 if d == 2 else 16
+    pb = W.random_problem(d, 1, (n,) * d, bc="reflect")
+    o = Oracle(pb)
+    rng = np.random.default_rng(21)
+    xi = W.xi_nodes(pb)
+    deg = 6 if d == 2 else 2
+    coef = rng.uniform(-0.05, 0.05, size=(d, d, deg + 1))
+
+    def comp(j, xs):
+        out = xs[j].copy()
+        for k in range(d):
+            for e in range(1, deg + 1):
+                out = out + coef[j, k, e] * xs[k] ** e
+        return out
+
+    def dcomp(j, k, xs):
+        return (1.0 if j == k else 0.0) + sum(e * coef[j, k, e] * xs[k] ** (e - 1) for e in range(1, deg + 1))
+
+    x = np.stack([comp(j, xi) for j in range(d)])
+    M = o.metrics(x)
+    depth = 3 if d == 2 else 6
+    A = np.zeros((d, d) + pb.shape)
+    for j in range(d):
+        for k in range(d):
+            A[j, k] = dcomp(j, k, xi)
+    # cofactor C[k][j] = det(A) (A^{-1})[k][j]
+    Am = np.moveaxis(A, (0, 1), (-2, -1))
+    cof = np.linalg.det(Am)[..., None, None] * np.linalg.inv(Am)
+    for k in range(d):
+        for j in range(d):
+            got = _interior(pb, M[k * (d + 1) + 1 + j][None], depth)[0]
+            sl = tuple(slice(depth, pb.shape[a] - depth) if (2 - a) < d else slice(None) for a in range(3))
+            np.testing.assert_allclose(got, cof[..., k, j][sl], rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+@pytest.mark.parametrize("bc", ["periodic", "mixed"])
+def test_discrete_scl(d, bc):
+    """Discrete SCL Eq. (SCL_dis): sum_k delta_k[J xi_k/x_j]/dxi_k = 0 at every node
+    (the GCL-flux difference telescopes to delta_k), random smooth moving meshes."""
+    n = 12 if d == 2 else 10
+    pb = W.random_problem(d, 1, (n,) * d, bc=bc)
+    o = Oracle(pb)
+    rng = np.random.default_rng(22)
+    x = W.smooth_mesh(pb, rng)
+    M = o.metrics(x)
+    al = o.alpha()
+    for j in range(d):
+        tot = 0.0
+        for k in range(d):
+            f = M[k * (d + 1) + 1 + j]
+            ax = 2 - k
+            dk = sum(0.5 * al[m - 1] * (np.roll(f, -m, axis=ax) - np.roll(f, m, axis=ax)) for m in (1, 2, 3))
+            tot = tot + dk / pb.dxi[k]
+        inner = _interior(pb, np.asarray(tot)[None], 0)[0]
+        assert np.abs(inner).max() <= 1e-11 * np.abs(M).max()
+
+
+# ---------------------------------------------------------------------------
+# whole residual
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("d,N", CASES)
+@pytest.mark.parametrize("es", [False, True])
+def test_free_stream_preservation(d, N, es):
+    """A constant state on a randomly perturbed moving mesh stays constant: d(JU)/dt = U dJ/dt
+    for the residual and U is unchanged to round-off after SSP-RK3 steps (remark in Sec. 3.2)."""
+    n = 12 if d == 2 else 10
+    pb = W.random_problem(d, N, (n,) * d, pinf=1.0 if N == 1 else 0.0, es=es)
+    o = Oracle(pb)
+    rng = np.random.default_rng(23)
+    x = W.smooth_mesh(pb, rng)
+    xdot = 0.3 * W.smooth_mesh(pb, rng) - 0.3 * np.stack(W.xi_nodes(pb))
+    U0 = _random_state(pb, rng)
+    J = o.init_J(x)
+    U = np.broadcast_to(U0.reshape((-1,) + (1,) * 3), (pb.nc,) + pb.shape).copy()
+    JU = U * J
+    dJU, dJ = o.rhs(JU, J, x, xdot)
+    scale = np.abs(U).max() * max(np.abs(dJ).max(), 1.0) / min(pb.dxi[: d])
+    assert np.abs(dJU - U * dJ).max() <= 1e-12 * scale
+    dt = 0.2 * min(pb.dxi[:d])
+    for _ in range(2):
+        JU, J, x = o.rk_step(JU, J, x, xdot, dt)
+    np.testing.assert_allclose(JU / J, U, rtol=1e-12, atol=1e-12 * np.abs(U).max())
+
+
+@pytest.mark.parametrize("d,N", CASES)
+def test_ec_entropy_production_zero(d, N):
+    """The EC scheme on periodic data satisfies the semi-discrete entropy identity
+    Eq. (NumEntropyID): P = sum (V^T dJU - phi dJ) dxi^d = 0 (telescoping)."""
+    n = 12 if d == 2 else 8
+    pb = W.random_problem(d, N, (n,) * d, es=False, pinf=0.5 if N == 1 else 0.0)
+    o = Oracle(pb)
+    rng = np.random.default_rng(24)
+    x = W.smooth_mesh(pb, rng)
+    xdot = 0.3 * (W.smooth_mesh(pb, rng) - np.stack(W.xi_nodes(pb)))
+    U = W.smooth_state(pb, x, rng, amp=0.3)
+    J = o.init_J(x)
+    JU = U * J
+    dJU, dJ = o.rhs(JU, J, x, xdot)
+    P, _ = o.entropy(JU, J, dJU, dJ)
+    V = np.stack([o.entropy_vars(U[(slice(None),) + idx]) for idx in np.ndindex(pb.shape)], axis=1)
+    scale = (np.abs(V) * np.abs(dJU.reshape(pb.nc, -1))).sum() * np.prod(pb.dxi[:d])
+    assert abs(P) <= 1e-12 * scale, (P, scale)
+
+
+@pytest.mark.parametrize("d,N", CASES)
+def test_es_entropy_production_nonpositive(d, N):
+    """The ES scheme dissipates entropy: P <= 0 (Sec. 3.4, the sign property of Y), on smooth
+    and on discontinuous periodic data."""
+    n = 12 if d == 2 else 8
+    pb = W.random_problem(d, N, (n,) * d, es=True)
+    o = Oracle(pb)
+    rng = np.random.default_rng(25)
+    x = W.smooth_mesh(pb, rng)
+    xdot = 0.3 * (W.smooth_mesh(pb, rng) - np.stack(W.xi_nodes(pb)))
+    J = o.init_J(x)
+    for kind in ["smooth", "jump"]:
+        U = W.smooth_state(pb, x, rng, amp=0.3)
+        if kind == "jump":
+            mask = (x[0] > 0.5)
+            U = np.where(mask[None], U * 2.0, U)
+        JU = U * J
+        dJU, dJ = o.rhs(JU, J, x, xdot)
+        pb_ec = pb.with_(es=False)
+        dJU0, dJ0 = Oracle(pb_ec).rhs(JU, J, x, xdot)
+        P, _ = o.entropy(JU, J, dJU, dJ)
+        P0, _ = o.entropy(JU, J, dJU0, dJ0)
+        scale = np.abs(dJU0).sum() * np.prod(pb.dxi[:d])
+        assert abs(P0) <= 1e-11 * scale
+        assert P <= 1e-12 * scale, (kind, P)
+
+
+def test_3d_residual_on_extruded_data_equals_2d():
+    """A xi_3-independent state with v_3 = 0 on the extruded mesh x_3 = xi_3 gives the 2D
+    residual in the (rho, m_1, m_2, E) rows and zero in the m_3 row (Sec. 3: 2D is the
+    degenerate case of the 3D scheme)."""
+    rng = np.random.default_rng(26)
+    pb2 = W.random_problem(2, 1, (12, 12), es=True)
+    pb3 = W.random_problem(3, 1, (12, 12, 8), es=True)
+    o2, o3 = Oracle(pb2), Oracle(pb3)
+    x2 = W.smooth_mesh(pb2, rng)
+    xd2 = 0.2 * (W.smooth_mesh(pb2, rng) - np.stack(W.xi_nodes(pb2)))
+    U2 = W.smooth_state(pb2, x2, rng)
+    n3 = pb3.n[2]
+    x3 = np.stack([np.repeat(x2[0], n3, axis=0), np.repeat(x2[1], n3, axis=0), np.stack(W.xi_nodes(pb3))[2]])
+    xd3 = np.stack([np.repeat(xd2[0], n3, axis=0), np.repeat(xd2[1], n3, axis=0), np.zeros(pb3.shape)])
+    U3 = np.zeros((5,) + pb3.shape)
+    U3[[0, 1, 2, 4]] = np.repeat(U2, n3, axis=1)
+    J2, J3 = o2.init_J(x2), o3.init_J(x3)
+    np.testing.assert_allclose(J3, np.repeat(J2, n3, axis=0), rtol=1e-13)
+    r2 = o2.rhs(U2 * J2, J2, x2, xd2)
+    r3 = o3.rhs(U3 * J3, J3, x3, xd3)
+    want = np.repeat(r2[0], n3, axis=1)
+    got = r3[0][[0, 1, 2, 4]]
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-11 * np.abs(want).max())
+    assert np.abs(r3[0][3]).max() <= 1e-11 * np.abs(want).max()
+    np.testing.assert_allclose(r3[1], np.repeat(r2[1], n3, axis=0), atol=1e-12)
+
+
+def test_two_species_reduce_to_one():
+    """N = 2 with identical species and a uniform mass fraction gives the N = 1 EC residual
+    (summed species): the log mean is homogeneous, so sum_l {Y rho}^ln = {rho}^ln."""
+    rng = np.random.default_rng(27)
+    pb1 = W.random_problem(2, 1, (12, 12), es=False)
+    pb2 = W.random_problem(2, 2, (12, 12), es=False).with_(gamma=(1.4, 1.4), cv=(1.0, 1.0))
+    x = W.smooth_mesh(pb1, rng)
+    xd = 0.2 * (W.smooth_mesh(pb1, rng) - np.stack(W.xi_nodes(pb1)))
+    U1 = W.smooth_state(pb1, x, rng)
+    Y = 0.3
+    U2 = np.concatenate([Y * U1[:1], (1 - Y) * U1[:1], U1[1:]])
+    o1, o2 = Oracle(pb1), Oracle(pb2)
+    J = o1.init_J(x)
+    a = o1.rhs(U1 * J, J, x, xd)[0]
+    b = o2.rhs(U2 * J, J, x, xd)[0]
+    np.testing.assert_allclose(b[0] + b[1], a[0], atol=1e-12 * np.abs(a).max())
+    np.testing.assert_allclose(b[2:], a[1:], atol=1e-12 * np.abs(a).max())
+
+
+@pytest.mark.slow
+def test_design_order_density_wave():
+    """Fifth-order accuracy (Sec. 5, Example 5.1) on a smooth density wave advected through
+    the periodic unit box on the moving sinusoidal mesh, Delta t = C (min dxi)^{5/3}."""
+    errs = []
+    ns = [20, 40]
+    for n in ns:
+        pb = W.random_problem(2, 1, (n, n), es=True)
+        o = Oracle(pb)
+        xi = W.xi_nodes(pb)
+        bump = 0.02 * np.sin(2 * math.pi * xi[0]) * np.sin(2 * math.pi * xi[1])
+        x = np.stack([xi[0] + bump, xi[1] + bump])
+        xdot = np.stack([bump, bump])
+
+        def exact(xx, t):
+            rho = 1.0 + 0.2 * np.sin(2 * math.pi * (xx[0] + xx[1] - 2 * t))
+            return W.prim_to_cons(pb, [rho], [np.ones_like(rho), np.ones_like(rho)], np.ones_like(rho))
+
+        J = o.init_J(x)
+        JU = exact(x, 0.0) * J
+        tend = 0.05
+        dt0 = 0.4 * (1.0 / n) ** (5.0 / 3.0)
+        nsteps = int(math.ceil(tend / dt0))
+        dt = tend / nsteps
+        for _ in range(nsteps):
+            JU, J, x = o.rk_step(JU, J, x, xdot, dt)
+        err = np.abs(JU[0] / J - exact(x, tend)[0]).mean()
+        errs.append(err)
+    order = math.log2(errs[0] / errs[1])
+    assert order > 4.5, (errs, order)
+
+
+# ---------------------------------------------------------------------------
+# time step and mesh (Sec. 4, Eq. (cfl))
+# ---------------------------------------------------------------------------
+
+def test_cfl_uniform_mesh_closed_form():
+    """On the uniform mesh with a constant state, Eq. (cfl) reads
+    Delta t = C / sum_k (|v_k| + c)/dxi_k."""
+    pb = W.random_problem(2, 1, (16, 8), es=True).with_(length=(1.0, 0.5, 1.0))
+    o = Oracle(pb)
+    x = np.stack(W.xi_nodes(pb))
+    U0 = W.cons_state(pb, [1.3], [0.4, -0.7], 0.9)[: pb.nc]
+    U = np.broadcast_to(U0.reshape(-1, 1, 1, 1), (pb.nc,) + pb.shape).copy()
+    J = o.init_J(x)
+    np.testing.assert_allclose(J, 1.0, rtol=1e-14)
+    c = math.sqrt(1.4 * 0.9 / 1.3)
+    want = pb.cfl / ((0.4 + c) / pb.dxi[0] + (0.7 + c) / pb.dxi[1])
+    assert abs(o.cfl_dt(U * J, J, x) - want) <= 1e-14 * want
+
+
+def test_filter_preserves_constants_and_weights():
+    """The low-pass filter of Sec. 4 keeps constants and spreads a unit spike with the
+    weights (1/2)^(|j|+d)."""
+    pb = W.random_problem(3, 1, (8, 8, 8))
+    o = Oracle(pb)
+    th = np.full(pb.shape, 2.5)
+    np.testing.assert_allclose(o.filter(th), 2.5, rtol=1e-15)
+    sp = np.zeros(pb.shape)
+    sp[4, 4, 4] = 1.0
+    f = o.filter(sp)
+    g = GOLD["filter_weights"]
+    assert f[4, 4, 4] == float(Fraction(*g["centre_3d"]))
+    assert f[4, 4, 5] == float(Fraction(*g["face_3d"]))
+    assert f[4, 5, 5] == float(Fraction(*g["edge_3d"]))
+    assert f[5, 5, 5] == float(Fraction(*g["corner_3d"]))
+
+
+@pytest.mark.parametrize("bc", ["periodic", "mixed"])
+def test_uniform_mesh_is_fixed_point(bc):
+    """Theta = const: the uniform mesh solves the discrete mesh equation, so the Jacobi
+    sweeps leave it in place and the limiter gives Delta_tau = 1 with zero motion."""
+    pb = W.random_problem(2, 1, (16, 12), bc=bc).with_(mu=10)
+    o = Oracle(pb)
+    x = np.stack(W.xi_nodes(pb))
+    xmu = o.jacobi(x, np.full(pb.shape, 1.7))
+    np.testing.assert_allclose(xmu, x, rtol=0, atol=1e-14)
+    assert o.limiter(x, xmu) == 1.0
+
+
+def test_monitor_closed_form():
+    """Eq. (monitor) with central xi-gradients for sigma = rho = 1 + 0.3 sin(2 pi xi_1)."""
+    pb = W.random_problem(2, 1, (16, 8)).with_(alpha=(50.0,), nf=0)
+    o = Oracle(pb)
+    xi = W.xi_nodes(pb)
+    rho = 1.0 + 0.3 * np.sin(2 * math.pi * xi[0])
+    U = W.prim_to_cons(pb, [rho], [np.zeros_like(rho)] * 2, np.ones_like(rho))
+    J = np.ones(pb.shape)
+    h = pb.dxi[0]
+    g = np.abs(0.3 * (np.sin(2 * math.pi * (xi[0] + h)) - np.sin(2 * math.pi * (xi[0] - h))) / (2 * h))
+    want = np.sqrt(1 + 50.0 * (g / g.max()) ** 2)
+    np.testing.assert_allclose(o.monitor(U, J), want, rtol=1e-14)
+
+
+def test_limiter_keeps_node_order_and_mesh_velocity():
+    """x^{n+1} = x^n + Delta_tau delta_tau x keeps every grid line monotone (the bounds of
+    Sec. 4 allow at most half the neighbour spacing) and xdot = Delta_tau delta_tau x / Delta t."""
+    pb, U, x = W.shock_bubble_2d(48, 24)
+    o = Oracle(pb.with_(mu=10))
+    J = o.init_J(x)
+    JU = U * J
+    xdot, dt, dtau = o.mesh_redistribute(JU, J, x)
+    assert 0 < dtau <= 1 and dt > 0
+    xn = x + dt * xdot
+    assert np.all(np.diff(xn[0], axis=2) > 0)
+    assert np.all(np.diff(xn[1], axis=1) > 0)
+    th = o.monitor(JU, J)
+    xmu = o.jacobi(x, th)
+    np.testing.assert_allclose(xdot, dtau * (xmu - x) / dt, rtol=1e-13, atol=1e-15)
+    assert abs(o.limiter(x, xmu) - dtau) == 0.0
