@@ -1,0 +1,494 @@
+#!/usr/bin/env python
+"""Benchmark of the ES adaptive moving-mesh hot path on one GB300 (or N, one process each).
+
+A step is one full time step of the method: mesh redistribution (CFL time step,
+monitor + filter, Jacobi sweeps, limiter, mesh velocity) followed by one SSP-RK3
+step (three residual evaluations with metrics, sixth-order EC flux, WENO-MR
+dissipation, divergence and the fused stage update).  The metric is cell-stage
+updates per second: cells x 3 stages x steps / time, summed over all ranks.
+
+Default workload: the 2D two-component stiffened-gas shock-bubble instance,
+400 x 200 cells on [0, 2] x [0, 1], adaptive moving mesh with 5 Jacobi sweeps
+and 3 filter passes per step, in the mixed FP32/FP64 form; the FP64 form and the
+batched form (64 uneven instances, one launch per kernel per stage) are timed
+beside it.  Inputs are synthetic and seeded; they are resident in HBM before
+the timed region starts.  L2 is flushed (a 256 MiB buffer is rewritten) before
+every timed step, outside the events.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank advances its own copy of the workload (independent
+instances, no collective on the data path) and rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-stage updates/s on 1 GB300 (mixed/batched vs FP64 form) at stated L1 error"
+UNIT = "cell-stage updates/s"
+WORKLOAD = ("2D two-component stiffened-gas shock-bubble, 400x200 cells on [0,2]x[0,1], Ms 1.22, bubble r 0.2 "
+            "(Gamma2 1.648, density ratio 0.138), adaptive moving mesh (monitor sqrt(1+alpha|grad rho|^2/max), "
+            "alpha 100, 3 filter passes, 5 Jacobi sweeps per step), sixth-order EC + WENO-MR ES flux, SSP-RK3, CFL 0.4")
+
+# peaks: FP32 from the SM count and maximum clock (152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz);
+# FP64 as stated for GB300 (1.25 TFLOP/s)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_PEAK_TFLOPS = 1.25
+
+
+def flux_flops_per_interface(D, NS, es=True):
+    """Algorithmic flops of one interface of the flux kernel (each +, -, x, /, sqrt counted once;
+    the per-term counts are those of the contracted two-point flux, the GCL stencil, the
+    interface averages and the WENO-MR evaluations)."""
+    NC = NS + D + 1
+    pair = 26 + 18 * D + 21 * NS
+    ec = 6 * pair
+    gcl = 8 + 8 * D + 3 * D + 2
+    if not es:
+        return ec + gcl + NC
+    setup = (2 if D == 2 else 15) + 3 * D + 2 * D * D + (12 if NS == 1 else 45) + 4
+    weno = 96
+    column = 8 + NC + 2 * D * D + 12 * NC + 2 * weno + 2 * NC
+    return ec + gcl + setup + NC * column + NC
+
+
+def launches_per_step(pb):
+    m = 1 if pb.d == 2 else 2
+    mesh = 6 + m + pb.nf + pb.mu
+    return mesh + 3 * (m + pb.d)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons, pw = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+                pw.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "power_w_max": max(pw) if pw else None, "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def _dev(a, torch):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+class Single:
+    """One instance: device state, one full step, a CUDA graph of it."""
+
+    def __init__(self, pb, U, x, precision, torch):
+        from paper_2202_07989_gb300 import es
+        self.torch = torch
+        self.pb = pb
+        self.ctx = es.Context(pb, precision)
+        self.x = _dev(x, torch)
+        self.J = self.ctx.es_init_mesh(self.x)
+        self.JU = (_dev(U, torch) * self.J).contiguous()
+        self.xdot = torch.zeros_like(self.x)
+        self.dd = torch.zeros(2, dtype=torch.float64, device="cuda")
+        self.state0 = (self.JU.clone(), self.J.clone(), self.x.clone())
+        self.graph = None
+
+    def reset(self):
+        self.JU.copy_(self.state0[0])
+        self.J.copy_(self.state0[1])
+        self.x.copy_(self.state0[2])
+
+    def step(self):
+        self.ctx.mesh_redistribute(self.JU, self.J, self.x, 0.0, self.xdot, self.dd)
+        self.ctx.es_rk_step(self.JU, self.J, self.x, self.xdot, self.dd)
+
+    def capture(self):
+        torch = self.torch
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.step()
+        torch.cuda.current_stream().wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.step()
+        self.graph = g
+
+    def run(self):
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self.step()
+
+    @property
+    def cells(self):
+        return self.pb.ncell
+
+
+class Batch:
+    """Independent instances advanced by one launch per kernel per stage."""
+
+    def __init__(self, insts, precision, torch):
+        from paper_2202_07989_gb300 import es
+        self.torch = torch
+        self.probs = [p for p, _, _ in insts]
+        self.ctx = es.Context(self.probs, precision)
+        self.JU, self.J, self.x, self.xd, self.dd = [], [], [], [], []
+        for p, U, x in insts:
+            c1 = es.Context(p, precision)
+            xx = _dev(x, torch)
+            J = c1.es_init_mesh(xx)
+            self.x.append(xx)
+            self.J.append(J)
+            self.JU.append((_dev(U, torch) * J).contiguous())
+            self.xd.append(torch.zeros_like(xx))
+            self.dd.append(torch.zeros(2, dtype=torch.float64, device="cuda"))
+            del c1
+        self.ctx.es_bind_batch(self.JU, self.J, self.x, self.xd, self.dd)
+        self.graph = None
+
+    def step(self):
+        self.ctx.es_step_batch()
+
+    def capture(self):
+        torch = self.torch
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.step()
+        torch.cuda.current_stream().wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.step()
+        self.graph = g
+
+    def run(self):
+        self.graph.replay() if self.graph is not None else self.step()
+
+    @property
+    def cells(self):
+        return sum(p.ncell for p in self.probs)
+
+
+def time_steps(runner, steps, warmup, torch, flush):
+    for _ in range(warmup):
+        runner.run()
+    torch.cuda.synchronize()
+    total = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        runner.run()
+        b.record()
+        b.synchronize()
+        total += a.elapsed_time(b)
+    torch.cuda.synchronize()
+    return total / 1000.0
+
+
+def kernel_profile(runner, steps, torch):
+    """Per-class kernel time from CUDA events the library records on its launch stream."""
+    ctx = runner.ctx
+    ctx.es_profile(True)
+    ctx.es_profile_read()
+    g = runner.graph
+    runner.graph = None
+    for _ in range(steps):
+        runner.run()
+    torch.cuda.synchronize()
+    prof = ctx.es_profile_read()
+    ctx.es_profile(False)
+    runner.graph = g
+    return prof
+
+
+def errors_vs(ref_JU, ref_J, pb, JU, J):
+    """L1 (cell mean) and Linf errors of rho, p and the total entropy of (JU, J) against the reference."""
+    def prims(JU_, J_):
+        U = JU_ / J_
+        rho = U[: pb.N].sum(0)
+        v2 = sum((U[pb.N + m] / rho) ** 2 for m in range(pb.d))
+        cvr = sum(pb.cv[l] * U[l] for l in range(pb.N))
+        rr = sum(pb.R(l) * U[l] for l in range(pb.N))
+        pinf = sum(pb.pinf[: pb.N])
+        T = (U[pb.N + pb.d] - 0.5 * rho * v2 - pinf) / cvr
+        p = rr * T - pinf
+        eta = -sum(U[l] * (pb.cv[l] * np.log(T) - pb.R(l) * np.log(U[l])) for l in range(pb.N))
+        return rho, p, (J_ * eta).sum() * np.prod(pb.dxi[: pb.d])
+    r0, p0, s0 = prims(ref_JU, ref_J)
+    r1, p1, s1 = prims(JU, J)
+    return {"rho_l1": float(np.abs(r1 - r0).mean()), "rho_linf": float(np.abs(r1 - r0).max()),
+            "p_l1": float(np.abs(p1 - p0).mean()), "p_linf": float(np.abs(p1 - p0).max()),
+            "total_entropy_abs": float(abs(s1 - s0)), "total_entropy_rel": float(abs(s1 - s0) / abs(s0))}
+
+
+def cpu_baseline_leg(pb, U, x, gpu_after_one, budget_s=20.0):
+    """The oracle as it stands, single-threaded on the host: full steps of the same workload
+    until about budget_s of CPU time; returns its throughput and its one-step state."""
+    from oracle.oracle import Oracle
+    o = Oracle(pb)
+    J = o.init_J(x)
+    JU = U * J
+    t0 = time.perf_counter()
+    steps = 0
+    first = None
+    while True:
+        xd, dt, dtau = o.mesh_redistribute(JU, J, x)
+        JU, J, x = o.rk_step(JU, J, x, xd, dt)
+        steps += 1
+        if first is None:
+            first = (JU.copy(), J.copy(), x.copy())
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    el = time.perf_counter() - t0
+    val = pb.ncell * 3 * steps / el
+    return {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d full steps (mesh redistribution + SSP-RK3) of the 400x200 workload from t = 0, %.1f s" % (steps, el)}, first
+
+
+def main_ours(args):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2202_07989_gb300 import build as B
+    B.build()
+    from paper_2202_07989_gb300 import es, workloads as W
+
+    pb, U, x = W.shock_bubble_2d(400, 200)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    forms = {}
+    runners = {}
+    for name, prec in (("mixed", es.MIXED), ("fp64", es.FP64)):
+        r = Single(pb, U, x, prec, torch)
+        r.step()                      # first call on the context, outside capture
+        r.reset()
+        r.capture()
+        r.reset()
+        runners[name] = r
+
+    # headline: mixed form, CUDA graph per step
+    main = runners["mixed"]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_main = time_steps(main, args.steps, args.warmup, torch, flush)
+    clk = clocks.stop()
+    if world > 1:
+        tt = torch.tensor([t_main], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+        t_main = float(tt.item())
+    value = pb.ncell * 3 * args.steps * world / t_main
+    forms["mixed"] = {"value": pb.ncell * 3 * args.steps / t_main, "ms_per_step": 1e3 * t_main / args.steps}
+
+    # FP64 form
+    r64 = runners["fp64"]
+    k64 = max(3, min(args.steps, 10))
+    t64 = time_steps(r64, k64, 2, torch, flush)
+    forms["fp64"] = {"value": pb.ncell * 3 * k64 / t64, "ms_per_step": 1e3 * t64 / k64}
+
+    # kernel profile (dominant kernel = flux) of both forms
+    prof_m = kernel_profile(main, args.steps, torch)
+    prof_d = kernel_profile(r64, k64, torch)
+
+    # batched form: 64 uneven instances, mixed
+    batched = None
+    if not args.no_batched:
+        insts = W.batched_2d(64)
+        bt = Batch(insts, es.MIXED, torch)
+        bt.step()
+        torch.cuda.synchronize()
+        bt.capture()
+        kb = max(3, min(args.steps, 10))
+        tb = time_steps(bt, kb, 2, torch, flush)
+        batched = {"value": bt.cells * 3 * kb / tb, "ms_per_step": 1e3 * tb / kb, "instances": len(insts),
+                   "cells": bt.cells}
+        forms["batched_mixed"] = batched
+
+    # end to end: C-ABI call on pinned host buffers, copies inside the timed region
+    e2e = None
+    if rank == 0:
+        c = es.Context(pb, es.MIXED)
+        J0 = runners["mixed"].state0[1].cpu()
+        JU0 = runners["mixed"].state0[0].cpu()
+        x0 = runners["mixed"].state0[2].cpu()
+        hJU, hJ, hx = JU0.pin_memory(), J0.pin_memory(), x0.pin_memory()
+        c.es_run_host(hJU, hJ, hx, 1)
+        torch.cuda.synchronize()
+        ke = max(3, min(args.steps, 10))
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            c.es_run_host(hJU, hJ, hx, 1)
+        te = time.perf_counter() - t0
+        nb = (pb.nc + 1 + pb.d) * pb.ncell * 8
+        e2e = {"value": pb.ncell * 3 * ke / te, "unit": UNIT, "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb + 8,
+               "steps": ke, "call": "es_run_host (host buffers, 1 step per call)"}
+
+    # roofline of the dominant kernel (flux + divergence + RK stage) in the headline form
+    flux_ms = sum(prof_m[k][0] for k in ("flux_k1", "flux_k2", "flux_k3"))
+    flux_n = sum(prof_m[k][1] for k in ("flux_k1", "flux_k2", "flux_k3"))
+    per_iface = flux_flops_per_interface(pb.d, pb.N, pb.es)
+    # interfaces per launch: (n_k + 1) per grid line, averaged over the directions
+    ifaces = sum((pb.n[k] + 1) * pb.ncell // pb.n[k] for k in range(pb.d)) / pb.d
+    flops_launch = per_iface * ifaces
+    avg_s = flux_ms / flux_n / 1e3 if flux_n else float("nan")
+    ach = flops_launch / avg_s / 1e12
+    roofline = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
+                "traffic": None, "kernel": "flux_kernel (mixed form)", "flops_per_launch": flops_launch,
+                "avg_launch_ms": avg_s * 1e3, "peak_source": "FP32: 152 SMs x 128 lanes x 2 x 2.07 GHz"}
+    flux64_ms = sum(prof_d[k][0] for k in ("flux_k1", "flux_k2", "flux_k3"))
+    flux64_n = sum(prof_d[k][1] for k in ("flux_k1", "flux_k2", "flux_k3"))
+    avg64 = flux64_ms / flux64_n / 1e3 if flux64_n else float("nan")
+    ach64 = flops_launch / avg64 / 1e12
+    roofline_fp64 = {"bound": "alu", "achieved": ach64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": ach64 / FP64_PEAK_TFLOPS, "avg_launch_ms": avg64 * 1e3, "kernel": "flux_kernel (FP64 form)"}
+
+    # CPU baseline (rank 0 only): the oracle on a bounded sample, and the errors after one step
+    cpu = None
+    errs = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu, ref1 = cpu_baseline_leg(pb, U, x, None, budget_s=args.cpu_seconds)
+        errs = {}
+        for name in ("fp64", "mixed"):
+            r = runners[name]
+            r.reset()
+            r.step()
+            torch.cuda.synchronize()
+            errs[name] = errors_vs(ref1[0], ref1[1], pb, r.JU.cpu().numpy(), r.J.cpu().numpy())
+            errs[name]["vs"] = "FP64 oracle after one full step from t = 0"
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_main / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": pb.ncell, "stages_per_step": 3, "form": "mixed FP32/FP64",
+                   "graph": "one CUDA graph per full step", "l2": "256 MiB buffer rewritten before every timed step",
+                   "instances_per_rank": 1},
+        "forms": forms, "errors": errs, "roofline": roofline, "roofline_fp64": roofline_fp64,
+        "kernel_ms": {"mixed": {k: v[0] / args.steps for k, v in prof_m.items()},
+                      "fp64": {k: v[0] / k64 for k, v in prof_d.items()}},
+        "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+        "gpu_launches": launches_per_step(pb) * args.steps,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle, as it stands, on the host cores
+# ---------------------------------------------------------------------------
+
+def main_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return
+    from oracle.oracle import Oracle
+    from paper_2202_07989_gb300 import workloads as W
+    pb, U, x = W.shock_bubble_2d(400, 200)
+    o = Oracle(pb)
+    J = o.init_J(x)
+    JU = U * J
+    for _ in range(args.warmup):
+        xd, dt, dtau = o.mesh_redistribute(JU, J, x)
+        JU, J, x = o.rk_step(JU, J, x, xd, dt)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        xd, dt, dtau = o.mesh_redistribute(JU, J, x)
+        JU, J, x = o.rk_step(JU, J, x, xd, dt)
+    el = time.perf_counter() - t0
+    val = pb.ncell * 3 * args.steps / el
+    sample = "%d full steps of the 400x200 workload after %d warm-up steps, single-threaded oracle" % (args.steps, args.warmup)
+    line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "cells": pb.ncell, "stages_per_step": 3, "form": "FP64 CPU oracle"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        main_reference(args)
+    else:
+        main_ours(args)
+
+
+if __name__ == "__main__":
+    main()

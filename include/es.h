@@ -1,0 +1,183 @@
+/*
+ * es.h -- C ABI of the GB300 library for the entropy-stable adaptive
+ * moving-mesh finite-difference method of arXiv 2202.07989 (Duan & Tang,
+ * "High-order accurate entropy stable adaptive moving mesh finite difference
+ * schemes for (multi-component) compressible Euler equations with the
+ * stiffened equation of state").
+ *
+ * Problem (Sec. 1, Eq. (1.1)): U = (rho_1..rho_N, rho v_1..rho v_d, E),
+ * N in {1, 2} species, d in {2, 3}, stiffened mixture EOS (Eq. (1.2)).
+ * The state advanced in time is (JU, J, x) on a fixed computational grid
+ * (Sec. 2, Eq. (2.2)): the Jacobian-weighted conserved variables, the
+ * Jacobian and the physical node positions.
+ *
+ * Data layout (all calls): every array is a contiguous structure of arrays,
+ * field-major, a[f][i3][i2][i1] with i1 fastest, interior nodes only, FP64.
+ * n_c = N + d + 1 conserved fields; x and xdot have d fields; J has 1.  In 2D
+ * n[2] = 1.  Nodes sit at the cell centres xi_{k,i} = xi_lo[k] + (i + 1/2) dxi[k].
+ *
+ * Ownership: the caller owns every state, input and output buffer; pointers
+ * are DEVICE pointers unless a call says HOST.  A context owns only scratch it
+ * allocates in es_create / es_create_batch and frees in es_destroy; no call
+ * after creation allocates device memory, except the first es_run_host and
+ * es_profile(ctx, 1) on a context.
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ * stream).  Calls are asynchronous on that stream unless they say otherwise;
+ * scalar results are written to device memory so whole steps can be captured
+ * in a CUDA graph (es_rk_step, mesh_redistribute, entropy_production).
+ *
+ * Errors: every call returns an es_status.  Argument errors are detected on
+ * the host before any launch (ES_ERR_ARG, ES_ERR_UNSUPPORTED).  Launch errors
+ * return ES_ERR_CUDA.  Non-physical states met by a kernel (rho_l <= 0,
+ * T <= 0, NaN) set a sticky device status word and the kernel carries on with
+ * placeholder values; es_poll_status reads it (synchronising the stream) and
+ * reports ES_ERR_NONPHYSICAL.  No kernel traps or asserts.  es_last_error
+ * returns a message for the last failing call on a context.
+ */
+#ifndef ES_H
+#define ES_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum es_status {
+    ES_OK = 0,
+    ES_ERR_ARG = 1,          /* bad argument (null pointer, size, parameter range) */
+    ES_ERR_UNSUPPORTED = 2,  /* configuration outside what this build implements */
+    ES_ERR_CUDA = 3,         /* a CUDA runtime call or launch failed */
+    ES_ERR_NONPHYSICAL = 4,  /* a kernel met rho_l <= 0, T <= 0 or NaN */
+    ES_ERR_TIMEOUT = 5       /* reserved for bounded device waits */
+} es_status;
+
+enum { ES_BC_PERIODIC = 0, ES_BC_REFLECT = 1, ES_BC_INFLOW = 2, ES_BC_OUTFLOW = 3 };
+enum { ES_FP64 = 0, ES_MIXED = 1 };
+enum { ES_SIG_RHO = 0, ES_SIG_RHO1 = 1, ES_SIG_RHO2 = 2, ES_SIG_P = 3, ES_SIG_Y2 = 4, ES_SIG_V1 = 5 };
+
+/* One instance.  Physics: Gamma_l, c_{v,l}, p_{inf,l} (Sec. 1, Eq. (1.2)).
+ * Scheme: sixth-order EC flux (w = 3, Sec. 3.1), WENO-MR dissipation with
+ * linear weights chi and epsilon (Appendix A) when es = 1, SSP-RK3, CFL number
+ * cfl (Eq. (cfl)).  Mesh: monitor Eq. (monitor) on the variables sigma[] with
+ * weights alpha[], nf filter passes and mu Jacobi sweeps (Sec. 4).
+ * precision: ES_FP64 runs everything in FP64; ES_MIXED runs the EC pairs, the
+ * WENO-MR dissipation and the monitor/filter in FP32 and keeps metrics, the
+ * GCL flux of J, the small-jump logarithmic-mean branch, divergence and RK
+ * accumulation and the entropy diagnostics in FP64. */
+typedef struct es_config {
+    int d;                   /* 2 or 3 */
+    int N;                   /* 1 or 2 species */
+    int n[3];                /* nodes per direction; n[2] = 1 when d = 2; n[k] >= 10 */
+    double xi_lo[3];         /* lower corner of the computational box */
+    double dxi[3];           /* node spacing (box length / n) */
+    int bc[3][2];            /* ES_BC_* per direction and side (periodic on both or neither) */
+    double inflow[3][2][8];  /* conserved state on ES_BC_INFLOW sides */
+    double gamma[2], cv[2], pinf[2];
+    int es;                  /* 1: entropy stable (EC + dissipation); 0: entropy conservative */
+    int precision;           /* ES_FP64 or ES_MIXED */
+    double chi[3];           /* WENO-MR linear weights, positive, summing to 1 */
+    double weno_eps;         /* WENO-MR epsilon (1e-10 in the paper) */
+    double cfl;              /* CFL number (0.4 in 2D, 0.3 in 3D in the paper) */
+    int n_sigma;             /* 0..4 monitor variables */
+    int sigma[4];            /* ES_SIG_* */
+    double alpha[4];         /* monitor weights alpha_k >= 0 */
+    int mu;                  /* Jacobi sweeps per step (>= 0) */
+    int nf;                  /* filter passes per step (>= 0) */
+} es_config;
+
+typedef struct es_ctx es_ctx;
+
+/* Create a context for one instance (es_create) or for n_inst independent
+ * instances advanced together (es_create_batch; cfgs is a HOST array).  All
+ * instances of a batch share d, N and precision.  Allocates the scratch of
+ * every later call on the current CUDA device.  On failure *out is NULL. */
+es_status es_create(const es_config* cfg, es_ctx** out);
+es_status es_create_batch(const es_config* cfgs, int n_inst, es_ctx** out);
+void es_destroy(es_ctx* ctx);
+const char* es_last_error(const es_ctx* ctx);
+int es_num_instances(const es_ctx* ctx);
+
+/* Bytes of device scratch the context holds. */
+unsigned long long es_scratch_bytes(const es_ctx* ctx);
+
+/* J^0 = det(delta_k[x_j] / dxi_k) at the nodes from caller-filled positions x
+ * (the initial Jacobian; Sec. 3.2 operators).  x: d fields (read), J: 1 field
+ * (written).  Instance 0 of the context. */
+es_status es_init_mesh(es_ctx* ctx, const double* x, double* J, void* stream);
+
+/* Metrics of Sec. 3.2: J xi_k/x_j by Eq. (SCLCoeff) (3D; the 2D degenerate
+ * case otherwise) and J xi_k/t = -sum_j xdot_j J xi_k/x_j (Eq. (VCLCoeff)).
+ * x, xdot: d fields each (xdot may be NULL = 0).  metrics (written):
+ * d*(d+1) fields on the padded grid with 3 ghost layers per direction,
+ * metrics[(k*(d+1) + c)][i3+3][i2+3][i1+3], c = 0 for J xi_k/t and 1 + j for
+ * J xi_k/x_j; padded extents n[k] + 6 (1 for the absent third direction in 2D). */
+es_status es_metrics(es_ctx* ctx, const double* x, const double* xdot, double* metrics, void* stream);
+
+/* Semi-discrete residual, Eqs. (semi_U) and (semi_J): dJU = d(JU)/dt (n_c
+ * fields) and dJ = dJ/dt (1 field) from the state (JU, J, x) and the mesh
+ * velocity xdot (NULL = 0).  EC flux Eq. (ECFlux_curv_2p) with the two-point
+ * flux Eq. (ECfluxMM); ES flux Eq. (HOstable) when cfg.es = 1.  Instance 0. */
+es_status es_rhs(es_ctx* ctx, const double* JU, const double* J, const double* x, const double* xdot,
+                 double* dJU, double* dJ, void* stream);
+
+/* One SSP-RK3 step (Shu-Osher form, Sec. 5) of (JU, J, x) IN PLACE with the
+ * mesh velocity xdot held constant over the step (xdot may be NULL = 0).
+ * dt: DEVICE pointer to the time step (e.g. the first output of
+ * mesh_redistribute).  Three residual evaluations; no host synchronisation. */
+es_status es_rk_step(es_ctx* ctx, double* JU, double* J, double* x, const double* xdot, const double* dt,
+                     void* stream);
+
+/* Mesh redistribution of Sec. 4 for the next step: Delta t by Eq. (cfl) on
+ * x (or dt_fixed when dt_fixed > 0, HOST value), the monitor Eq. (monitor)
+ * smoothed nf times, mu Jacobi sweeps of the discrete mesh equations, the
+ * limiter Delta_tau and xdot = Delta_tau (x^[mu] - x) / Delta t.
+ * xdot (written): d fields.  dt_dtau (written, DEVICE): {Delta t, Delta_tau}. */
+es_status mesh_redistribute(es_ctx* ctx, const double* JU, const double* J, const double* x, double dt_fixed,
+                            double* xdot, double* dt_dtau, void* stream);
+
+/* Entropy diagnostics (Sec. 1 definitions, Sec. 5 total entropy):
+ * out2[0] = P = sum_i dxi^d (V_i . dJU_i - phi_i dJ_i)  (= d/dt of the total
+ * entropy; 0 for the EC scheme on periodic data, <= 0 for the ES scheme) and
+ * out2[1] = sum_i J_i eta(U_i) dxi^d.  dJU, dJ may be NULL (then P = 0).
+ * out2: DEVICE, 2 doubles.  Deterministic (fixed reduction order). */
+es_status entropy_production(es_ctx* ctx, const double* JU, const double* J, const double* dJU, const double* dJ,
+                             double* out2, void* stream);
+
+/* Batched forms: arrays of n_inst DEVICE pointers passed as HOST arrays; one
+ * launch per kernel covers every instance.  es_bind_batch uploads the
+ * pointer tables (synchronous; call it again when buffers change) and
+ * es_step_batch then runs, for every instance, mesh_redistribute followed by
+ * es_rk_step with the instance's own Delta t, Delta_tau and xdot, writing
+ * {Delta t, Delta_tau} to dt_dtau[i].  es_step_batch does not synchronise and
+ * can be captured in a CUDA graph. */
+es_status es_bind_batch(es_ctx* ctx, double* const* JU, double* const* J, double* const* x, double* const* xdot,
+                        double* const* dt_dtau);
+es_status es_step_batch(es_ctx* ctx, void* stream);
+
+/* Full steps on HOST buffers (instance 0): copies (JU, J, x) to the device,
+ * runs `steps` times mesh_redistribute (CFL Delta t, or dt_fixed > 0) + an
+ * SSP-RK3 step, copies (JU, J, x) back and adds the elapsed time to *t.
+ * Synchronous.  Uses device buffers owned by the context, allocated by the
+ * first call. */
+es_status es_run_host(es_ctx* ctx, double* JU, double* J, double* x, int steps, double dt_fixed, double* t,
+                      void* stream);
+
+/* Kernel timing.  es_profile(ctx, 1) preallocates CUDA events; while enabled,
+ * calls that are not being captured into a CUDA graph record an event pair
+ * around every kernel launch on the call's stream.  es_profile_read
+ * synchronises, returns per class the summed milliseconds and the launch
+ * count since the last read, then resets them.  Classes (n_classes <= 8):
+ * 0..2 flux + divergence (+ RK stage) for directions 1..3, 3 metrics,
+ * 4 mesh redistribution (CFL, monitor, filter, Jacobi, limiter, xdot),
+ * 5 entropy diagnostics.  es_profile(ctx, 0) frees the events. */
+es_status es_profile(es_ctx* ctx, int enable);
+es_status es_profile_read(es_ctx* ctx, double* ms, long long* launches, int n_classes);
+
+/* Reads and clears the sticky device status (synchronises the stream):
+ * *flags = bit 0 non-physical state, bit 1 timeout. */
+es_status es_poll_status(es_ctx* ctx, int* flags, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

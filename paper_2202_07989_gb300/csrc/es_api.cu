@@ -1,0 +1,706 @@
+// C ABI of the library (include/es.h): contexts, argument checks, work lists and
+// the launch sequences of every entry point.  Single-instance calls pass their
+// pointers to the kernels by value; batched calls use per-instance tables
+// uploaded by es_bind_batch.  Nothing here allocates after creation.
+#include "../../include/es.h"
+#include "es_mesh.cuh"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace es;
+
+struct es_ctx {
+    int n_inst = 0, d = 2, N = 1, nc = 4;
+    bool mixed = false;
+    std::vector<Inst> hI;
+    Inst* dI = nullptr;
+    std::vector<Scratch> hS;
+    Scratch* dS = nullptr;
+    std::vector<void*> allocs;
+    unsigned long long bytes = 0;
+    // work lists (inst, tile)
+    int2* w_pad = nullptr;  int n_pad = 0;
+    int2* w_ext = nullptr;  int n_ext = 0;
+    int2* w_cell = nullptr; int n_cell = 0;
+    int2* w_flux[3] = { nullptr, nullptr, nullptr };
+    int n_flux[3] = { 0, 0, 0 };
+    int* d_first_cell = nullptr;
+    double* partial = nullptr;
+    int* status = nullptr;
+    // stage buffers (per instance): (JU | J | x) for the two intermediate stages
+    std::vector<double*> stA, stB;
+    // batched tables
+    StagePtrs* tab_mesh = nullptr;
+    StagePtrs* tab_stage[3] = { nullptr, nullptr, nullptr };
+    bool bound = false;
+    // device buffers of es_run_host
+    double *hJU = nullptr, *hJ = nullptr, *hx = nullptr, *hxd = nullptr, *hdt = nullptr, *htacc = nullptr;
+    int sms = 152;
+    int flux_grid[3] = { 0, 0, 0 };
+    std::string err;
+    // kernel timing (es_profile)
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> ev_class;
+    size_t ev_used = 0;
+    double prof_ms[8] = { 0 };
+    long long prof_n[8] = { 0 };
+};
+
+namespace {
+
+es_status fail(es_ctx* c, es_status s, const std::string& m)
+{
+    if (c) c->err = m;
+    return s;
+}
+
+bool dalloc(es_ctx* c, void** p, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    if (cudaMalloc(p, bytes) != cudaSuccess) return false;
+    c->allocs.push_back(*p);
+    c->bytes += bytes;
+    return true;
+}
+
+es_status cuda_check(es_ctx* c, const char* where)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(c, ES_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+    return ES_OK;
+}
+
+std::string check_cfg(const es_config& g)
+{
+    if (g.d != 2 && g.d != 3) return "d must be 2 or 3";
+    if (g.N != 1 && g.N != 2) return "N must be 1 or 2";
+    if (g.precision != ES_FP64 && g.precision != ES_MIXED) return "precision must be ES_FP64 or ES_MIXED";
+    for (int k = 0; k < 3; ++k) {
+        if (k < g.d) {
+            if (g.n[k] < 10) return "n[k] must be >= 10";
+            if (!(g.dxi[k] > 0.0)) return "dxi[k] must be > 0";
+            for (int s = 0; s < 2; ++s)
+                if (g.bc[k][s] < 0 || g.bc[k][s] > 3) return "bad boundary code";
+            if ((g.bc[k][0] == ES_BC_PERIODIC) != (g.bc[k][1] == ES_BC_PERIODIC))
+                return "a periodic direction must be periodic on both sides";
+        } else if (g.n[k] != 1) {
+            return "n[2] must be 1 when d = 2";
+        }
+    }
+    if ((double)g.n[0] * g.n[1] * g.n[2] > 2.0e9) return "grid too large (over 2^31 nodes)";
+    for (int l = 0; l < g.N; ++l) {
+        if (!(g.gamma[l] > 1.0)) return "gamma must be > 1";
+        if (!(g.cv[l] > 0.0)) return "cv must be > 0";
+        if (!(g.pinf[l] >= 0.0)) return "pinf must be >= 0";
+    }
+    if (!(g.chi[0] > 0 && g.chi[1] > 0 && g.chi[2] > 0)) return "chi must be positive";
+    if (!(g.weno_eps > 0)) return "weno_eps must be > 0";
+    if (!(g.cfl > 0)) return "cfl must be > 0";
+    if (g.n_sigma < 0 || g.n_sigma > 4) return "n_sigma must be in 0..4";
+    for (int s = 0; s < g.n_sigma; ++s) {
+        if (g.sigma[s] < 0 || g.sigma[s] > 5) return "bad monitor variable";
+        if (!(g.alpha[s] >= 0)) return "alpha must be >= 0";
+    }
+    if (g.mu < 0 || g.nf < 0) return "mu and nf must be >= 0";
+    return "";
+}
+
+Inst make_inst(const es_config& g)
+{
+    Inst I;
+    memset(&I, 0, sizeof(I));
+    I.d = g.d;
+    I.N = g.N;
+    I.nc = g.N + g.d + 1;
+    for (int k = 0; k < 3; ++k) {
+        I.n[k] = k < g.d ? g.n[k] : 1;
+        I.P[k] = k < g.d ? g.n[k] + 6 : 1;
+        I.dxi[k] = k < g.d ? g.dxi[k] : 1.0;
+        I.inv_dxi[k] = 1.0 / I.dxi[k];
+        I.xi_lo[k] = g.xi_lo[k];
+        I.L[k] = I.n[k] * I.dxi[k];
+        for (int s = 0; s < 2; ++s) {
+            I.bc[k][s] = g.bc[k][s];
+            for (int q = 0; q < 8; ++q) I.inflow[k][s][q] = g.inflow[k][s][q];
+        }
+    }
+    I.ncell = (long long)I.n[0] * I.n[1] * I.n[2];
+    I.npad = (long long)I.P[0] * I.P[1] * I.P[2];
+    I.pinf_tot = 0.0;
+    for (int l = 0; l < 2; ++l) {
+        I.gamma[l] = g.gamma[l];
+        I.cv[l] = g.cv[l];
+        I.pinf[l] = l < g.N ? g.pinf[l] : 0.0;
+        I.Rs[l] = g.cv[l] * (g.gamma[l] - 1.0);
+        I.cvG[l] = g.cv[l] * g.gamma[l];
+        if (l < g.N) I.pinf_tot += g.pinf[l];
+    }
+    I.es = g.es;
+    for (int q = 0; q < 3; ++q) I.chi[q] = g.chi[q];
+    I.weno_eps = g.weno_eps;
+    I.cfl = g.cfl;
+    I.n_sigma = g.n_sigma;
+    for (int s = 0; s < 4; ++s) { I.sigma[s] = g.sigma[s]; I.alpha[s] = g.alpha[s]; }
+    I.mu = g.mu;
+    I.nf = g.nf;
+    for (int k = 0; k < g.d; ++k) {
+        int S = k == 0 ? S_K0 : S_KN, WT = k == 0 ? WT_K0 : WT_KN;
+        int adim = k == 0 ? 1 : 0, bdim = k == 2 ? 1 : 2;
+        int nb = bdim < g.d ? I.n[bdim] : 1;
+        I.tiles[k] = ((I.n[k] + S - 1) / S) * ((I.n[adim] + WT - 1) / WT) * nb;
+    }
+    I.ntile_nodes = (int)((I.ncell + NODE_TPB - 1) / NODE_TPB);
+    return I;
+}
+
+template <typename F>
+int2* build_work(es_ctx* c, F count, int& n)
+{
+    std::vector<int2> w;
+    for (int i = 0; i < c->n_inst; ++i) {
+        long long t = count(c->hI[i]);
+        for (long long j = 0; j < t; ++j) w.push_back(make_int2(i, (int)j));
+    }
+    n = (int)w.size();
+    int2* d = nullptr;
+    if (!dalloc(c, (void**)&d, sizeof(int2) * (w.empty() ? 1 : w.size()))) return nullptr;
+    if (!w.empty()) cudaMemcpy(d, w.data(), sizeof(int2) * w.size(), cudaMemcpyHostToDevice);
+    return d;
+}
+
+template <int D, int NS>
+void prepare_all()
+{
+    prepare_flux<D, NS, double>();
+    prepare_flux<D, NS, float>();
+}
+
+void flux_dispatch(es_ctx* c, const FluxLaunch& L, cudaStream_t st)
+{
+    int grid = L.nwork < c->flux_grid[L.k] ? L.nwork : c->flux_grid[L.k];
+    if (grid <= 0) return;
+#define FD(d, n) do { if (c->mixed) launch_flux<d, n, float>(L, grid, st); else launch_flux<d, n, double>(L, grid, st); } while (0)
+    if (c->d == 2 && c->N == 1) FD(2, 1);
+    else if (c->d == 2 && c->N == 2) FD(2, 2);
+    else if (c->d == 3 && c->N == 1) FD(3, 1);
+    else FD(3, 2);
+#undef FD
+}
+
+int flux_occ(es_ctx* c, int k)
+{
+#define FO(d, n) return c->mixed ? flux_blocks_per_sm<d, n, float>(k) : flux_blocks_per_sm<d, n, double>(k)
+    if (c->d == 2 && c->N == 1) FO(2, 1);
+    if (c->d == 2 && c->N == 2) FO(2, 2);
+    if (c->d == 3 && c->N == 1) FO(3, 1);
+    FO(3, 2);
+#undef FO
+}
+
+int node_grid(es_ctx* c, int nwork)
+{
+    int cap = c->sms * 8;
+    return nwork < cap ? nwork : cap;
+}
+
+constexpr int PC_FLUX = 0, PC_METRICS = 3, PC_MESH = 4, PC_ENTROPY = 5;
+
+bool capturing(cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+// event pair around one launch: prof_begin returns the pair index or -1
+int prof_begin(es_ctx* c, int cls, cudaStream_t st)
+{
+    if (!c->prof || c->ev_used + 2 > c->ev.size() || capturing(st)) return -1;
+    int i = (int)c->ev_used;
+    c->ev_used += 2;
+    c->ev_class[i / 2] = cls;
+    cudaEventRecord(c->ev[i], st);
+    return i;
+}
+
+void prof_end(es_ctx* c, int i, cudaStream_t st)
+{
+    if (i >= 0) cudaEventRecord(c->ev[i + 1], st);
+}
+
+struct ProfScope {
+    es_ctx* c;
+    int i;
+    cudaStream_t st;
+    ProfScope(es_ctx* c_, int cls, cudaStream_t s) : c(c_), i(prof_begin(c_, cls, s)), st(s) {}
+    ~ProfScope() { prof_end(c, i, st); }
+};
+
+// metrics of the stage mesh P.x / P.xdot into P.M
+void launch_metrics(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStream_t st)
+{
+    ProfScope ps(c, PC_METRICS, st);
+    if (c->d == 2) {
+        metrics2d_kernel<<<node_grid(c, c->n_pad), NODE_TPB, 0, st>>>(c->dI, P, tab, c->w_pad, c->n_pad);
+    } else {
+        dx3d_kernel<<<node_grid(c, c->n_ext), NODE_TPB, 0, st>>>(c->dI, P, tab, c->w_ext, c->n_ext, c->dS);
+        metrics3d_kernel<<<node_grid(c, c->n_pad), NODE_TPB, 0, st>>>(c->dI, P, tab, c->w_pad, c->n_pad, c->dS);
+    }
+}
+
+// residual of one stage: metrics, then one flux launch per direction.  With
+// rk = true the last direction applies the Shu-Osher stage (a, b).
+void launch_residual(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, bool rk, double a, double b, cudaStream_t st)
+{
+    launch_metrics(c, P, tab, st);
+    for (int k = 0; k < c->d; ++k) {
+        FluxLaunch L;
+        L.insts = c->dI;
+        L.single = P;
+        L.ptrs = tab;
+        L.work = c->w_flux[k];
+        L.nwork = c->n_flux[k];
+        L.k = k;
+        L.mode = k == 0 ? MODE_WRITE : MODE_ACC;
+        if (rk && k == c->d - 1) L.mode = MODE_RK;
+        L.a = a;
+        L.b = b;
+        L.status = c->status;
+        ProfScope ps(c, PC_FLUX + k, st);
+        flux_dispatch(c, L, st);
+    }
+}
+
+// the stage pointer sets of one SSP-RK3 step on (JU, J, x)
+void stage_ptrs(es_ctx* c, int i, double* JU, double* J, double* x, const double* xdot, const double* dt, StagePtrs out[3])
+{
+    const Inst& I = c->hI[i];
+    const Scratch& S = c->hS[i];
+    long long n = I.ncell;
+    double* A = c->stA[i];
+    double* B = c->stB[i];
+    double* Au = A;
+    double* Aj = A + I.nc * n;
+    double* Ax = Aj + n;
+    double* Bu = B;
+    double* Bj = B + I.nc * n;
+    double* Bx = Bj + n;
+    const double* in_u[3] = { JU, Au, Bu };
+    const double* in_j[3] = { J, Aj, Bj };
+    const double* in_x[3] = { x, Ax, Bx };
+    double* out_u[3] = { Au, Bu, JU };
+    double* out_j[3] = { Aj, Bj, J };
+    double* out_x[3] = { Ax, Bx, x };
+    for (int s = 0; s < 3; ++s) {
+        StagePtrs P;
+        memset(&P, 0, sizeof(P));
+        P.JU = in_u[s];
+        P.J = in_j[s];
+        P.x = in_x[s];
+        P.xdot = xdot ? xdot : S.zeros;
+        P.M = S.M;
+        P.accU = S.accU;
+        P.accJ = S.accJ;
+        P.JU0 = JU;
+        P.J0 = J;
+        P.x0 = x;
+        P.JUo = out_u[s];
+        P.Jo = out_j[s];
+        P.xo = out_x[s];
+        P.dt = dt;
+        out[s] = P;
+    }
+}
+
+const double RK_A[3] = { 0.0, 0.75, 1.0 / 3.0 };
+const double RK_B[3] = { 1.0, 0.25, 2.0 / 3.0 };
+
+void launch_mesh(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStream_t st)
+{
+    {
+    ProfScope ps(c, PC_MESH, st);
+    red_init_kernel<<<(c->n_inst + 127) / 128, 128, 0, st>>>(c->dS, c->n_inst);
+    // node metrics of x^n (no mesh velocity) for Eq. (cfl)
+    StagePtrs Q = P;
+    Q.xdot = nullptr;
+    Q.M = c->hS[0].M;
+    if (tab) {
+        // batched: metrics target is each instance's scratch; the mesh table already points there
+        launch_metrics(c, Q, tab, st);
+    } else {
+        launch_metrics(c, Q, nullptr, st);
+    }
+    }
+    int gc = node_grid(c, c->n_cell);
+    ProfScope ps(c, PC_MESH, st);
+    cfl_kernel<<<gc, NODE_TPB, 0, st>>>(c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
+    monitor_grad_kernel<<<gc, NODE_TPB, 0, st>>>(c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
+    int nf = c->hI[0].nf, mu = c->hI[0].mu;
+    launch_monitor_theta(c->mixed, gc, st, c->dI, c->w_cell, c->n_cell, c->dS);
+    for (int f = 0; f < nf; ++f) launch_filter(c->mixed, gc, st, c->dI, c->w_cell, c->n_cell, c->dS, f % 2);
+    int th_sel = nf % 2;
+    for (int s = 0; s < mu; ++s) launch_jacobi(c->mixed, gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS, s, th_sel);
+    limiter_kernel<<<gc, NODE_TPB, 0, st>>>(c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
+    xdot_kernel<<<gc, NODE_TPB, 0, st>>>(c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
+}
+
+__global__ void time_acc_kernel(double* t, const double* dt_dtau) { *t += dt_dtau[0]; }
+
+}  // namespace
+
+extern "C" {
+
+es_status es_create_batch(const es_config* cfgs, int n_inst, es_ctx** out)
+{
+    if (!out) return ES_ERR_ARG;
+    *out = nullptr;
+    if (!cfgs || n_inst <= 0) return ES_ERR_ARG;
+    for (int i = 0; i < n_inst; ++i) {
+        std::string m = check_cfg(cfgs[i]);
+        if (!m.empty()) {
+            fprintf(stderr, "es_create: instance %d: %s\n", i, m.c_str());
+            return ES_ERR_ARG;
+        }
+        if (cfgs[i].d != cfgs[0].d || cfgs[i].N != cfgs[0].N || cfgs[i].precision != cfgs[0].precision ||
+            cfgs[i].mu != cfgs[0].mu || cfgs[i].nf != cfgs[0].nf) {
+            fprintf(stderr, "es_create: instances of a batch must share d, N, precision, mu and nf\n");
+            return ES_ERR_UNSUPPORTED;
+        }
+    }
+    es_ctx* c = new es_ctx();
+    c->n_inst = n_inst;
+    c->d = cfgs[0].d;
+    c->N = cfgs[0].N;
+    c->nc = c->N + c->d + 1;
+    c->mixed = cfgs[0].precision == ES_MIXED;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
+    for (int i = 0; i < n_inst; ++i) c->hI.push_back(make_inst(cfgs[i]));
+    bool ok = true;
+    ok = ok && dalloc(c, (void**)&c->dI, sizeof(Inst) * n_inst);
+    size_t rsz = c->mixed ? sizeof(float) : sizeof(double);
+    for (int i = 0; i < n_inst && ok; ++i) {
+        const Inst& I = c->hI[i];
+        Scratch S;
+        memset(&S, 0, sizeof(S));
+        long long n = I.ncell;
+        ok = ok && dalloc(c, (void**)&S.M, sizeof(double) * I.d * (I.d + 1) * I.npad);
+        if (I.d == 3) {
+            long long ne = (long long)(I.n[0] + 12) * (I.n[1] + 12) * (I.n[2] + 12);
+            ok = ok && dalloc(c, (void**)&S.D3, sizeof(double) * 9 * ne);
+        }
+        ok = ok && dalloc(c, (void**)&S.accU, sizeof(double) * I.nc * n);
+        ok = ok && dalloc(c, (void**)&S.accJ, sizeof(double) * n);
+        ok = ok && dalloc(c, (void**)&S.red, sizeof(double) * 8);
+        ok = ok && dalloc(c, (void**)&S.g, sizeof(double) * (I.n_sigma > 0 ? I.n_sigma : 1) * n);
+        ok = ok && dalloc(c, &S.th0, rsz * n);
+        ok = ok && dalloc(c, &S.th1, rsz * n);
+        ok = ok && dalloc(c, (void**)&S.xa, sizeof(double) * I.d * n);
+        ok = ok && dalloc(c, (void**)&S.xb, sizeof(double) * I.d * n);
+        ok = ok && dalloc(c, (void**)&S.zeros, sizeof(double) * I.d * n);
+        if (ok) cudaMemset(S.zeros, 0, sizeof(double) * I.d * n);
+        double *A = nullptr, *B = nullptr;
+        ok = ok && dalloc(c, (void**)&A, sizeof(double) * (I.nc + 1 + I.d) * n);
+        ok = ok && dalloc(c, (void**)&B, sizeof(double) * (I.nc + 1 + I.d) * n);
+        c->stA.push_back(A);
+        c->stB.push_back(B);
+        c->hS.push_back(S);
+    }
+    ok = ok && dalloc(c, (void**)&c->dS, sizeof(Scratch) * n_inst);
+    ok = ok && dalloc(c, (void**)&c->status, sizeof(int));
+    if (!ok) {
+        es_destroy(c);
+        fprintf(stderr, "es_create: device allocation failed\n");
+        return ES_ERR_CUDA;
+    }
+    cudaMemcpy(c->dI, c->hI.data(), sizeof(Inst) * n_inst, cudaMemcpyHostToDevice);
+    cudaMemcpy(c->dS, c->hS.data(), sizeof(Scratch) * n_inst, cudaMemcpyHostToDevice);
+    cudaMemset(c->status, 0, sizeof(int));
+    c->w_pad = build_work(c, [](const Inst& I) { return (I.npad + NODE_TPB - 1) / NODE_TPB; }, c->n_pad);
+    c->w_cell = build_work(c, [](const Inst& I) { return (I.ncell + NODE_TPB - 1) / NODE_TPB; }, c->n_cell);
+    if (c->d == 3)
+        c->w_ext = build_work(c, [](const Inst& I) {
+            long long ne = (long long)(I.n[0] + 12) * (I.n[1] + 12) * (I.n[2] + 12);
+            return (ne + NODE_TPB - 1) / NODE_TPB;
+        }, c->n_ext);
+    for (int k = 0; k < c->d; ++k) c->w_flux[k] = build_work(c, [k](const Inst& I) { return (long long)I.tiles[k]; }, c->n_flux[k]);
+    // per-instance ranges of the cell work list (entropy reduction)
+    std::vector<int> first(n_inst + 1, 0);
+    for (int i = 0; i < n_inst; ++i) first[i + 1] = first[i] + c->hI[i].ntile_nodes;
+    ok = dalloc(c, (void**)&c->d_first_cell, sizeof(int) * (n_inst + 1)) &&
+         dalloc(c, (void**)&c->partial, sizeof(double) * 2 * (first[n_inst] > 0 ? first[n_inst] : 1));
+    if (ok) cudaMemcpy(c->d_first_cell, first.data(), sizeof(int) * (n_inst + 1), cudaMemcpyHostToDevice);
+    if (c->d == 2 && c->N == 1) prepare_all<2, 1>();
+    else if (c->d == 2 && c->N == 2) prepare_all<2, 2>();
+    else if (c->d == 3 && c->N == 1) prepare_all<3, 1>();
+    else prepare_all<3, 2>();
+    for (int k = 0; k < c->d; ++k) c->flux_grid[k] = c->sms * flux_occ(c, k);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (!ok || e != cudaSuccess || !c->w_pad || !c->w_cell || (c->d == 3 && !c->w_ext)) {
+        fprintf(stderr, "es_create: setup failed: %s\n", cudaGetErrorString(e));
+        es_destroy(c);
+        return ES_ERR_CUDA;
+    }
+    *out = c;
+    return ES_OK;
+}
+
+es_status es_create(const es_config* cfg, es_ctx** out) { return es_create_batch(cfg, 1, out); }
+
+void es_destroy(es_ctx* c)
+{
+    if (!c) return;
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    for (void* p : c->allocs) cudaFree(p);
+    delete c;
+}
+
+const char* es_last_error(const es_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int es_num_instances(const es_ctx* c) { return c ? c->n_inst : 0; }
+
+unsigned long long es_scratch_bytes(const es_ctx* c) { return c ? c->bytes : 0ull; }
+
+es_status es_init_mesh(es_ctx* c, const double* x, double* J, void* stream)
+{
+    if (!c) return ES_ERR_ARG;
+    if (!x || !J) return fail(c, ES_ERR_ARG, "es_init_mesh: null pointer");
+    StagePtrs P;
+    memset(&P, 0, sizeof(P));
+    P.x = x;
+    P.Jo = J;
+    int n = c->hI[0].ntile_nodes;
+    // instance 0 only: its cell tiles are the first n entries of the cell work list
+    init_J_kernel<<<node_grid(c, n), NODE_TPB, 0, (cudaStream_t)stream>>>(c->dI, P, nullptr, c->w_cell, n);
+    return cuda_check(c, "es_init_mesh");
+}
+
+es_status es_metrics(es_ctx* c, const double* x, const double* xdot, double* metrics, void* stream)
+{
+    if (!c) return ES_ERR_ARG;
+    if (!x || !metrics) return fail(c, ES_ERR_ARG, "es_metrics: null pointer");
+    if (c->n_inst != 1) return fail(c, ES_ERR_UNSUPPORTED, "es_metrics: single-instance context required");
+    StagePtrs P;
+    memset(&P, 0, sizeof(P));
+    P.x = x;
+    P.xdot = xdot;
+    P.M = metrics;
+    launch_metrics(c, P, nullptr, (cudaStream_t)stream);
+    return cuda_check(c, "es_metrics");
+}
+
+es_status es_rhs(es_ctx* c, const double* JU, const double* J, const double* x, const double* xdot, double* dJU,
+                 double* dJ, void* stream)
+{
+    if (!c) return ES_ERR_ARG;
+    if (!JU || !J || !x || !dJU || !dJ) return fail(c, ES_ERR_ARG, "es_rhs: null pointer");
+    if (c->n_inst != 1) return fail(c, ES_ERR_UNSUPPORTED, "es_rhs: single-instance context required");
+    StagePtrs P;
+    memset(&P, 0, sizeof(P));
+    P.JU = JU;
+    P.J = J;
+    P.x = x;
+    P.xdot = xdot ? xdot : c->hS[0].zeros;
+    P.M = c->hS[0].M;
+    P.accU = dJU;
+    P.accJ = dJ;
+    launch_residual(c, P, nullptr, false, 0.0, 1.0, (cudaStream_t)stream);
+    return cuda_check(c, "es_rhs");
+}
+
+es_status es_rk_step(es_ctx* c, double* JU, double* J, double* x, const double* xdot, const double* dt, void* stream)
+{
+    if (!c) return ES_ERR_ARG;
+    if (!JU || !J || !x || !dt) return fail(c, ES_ERR_ARG, "es_rk_step: null pointer");
+    if (c->n_inst != 1) return fail(c, ES_ERR_UNSUPPORTED, "es_rk_step: single-instance context required");
+    StagePtrs P[3];
+    stage_ptrs(c, 0, JU, J, x, xdot, dt, P);
+    for (int s = 0; s < 3; ++s) launch_residual(c, P[s], nullptr, true, RK_A[s], RK_B[s], (cudaStream_t)stream);
+    return cuda_check(c, "es_rk_step");
+}
+
+es_status mesh_redistribute(es_ctx* c, const double* JU, const double* J, const double* x, double dt_fixed,
+                            double* xdot, double* dt_dtau, void* stream)
+{
+    if (!c) return ES_ERR_ARG;
+    if (!JU || !J || !x || !xdot || !dt_dtau) return fail(c, ES_ERR_ARG, "mesh_redistribute: null pointer");
+    if (c->n_inst != 1) return fail(c, ES_ERR_UNSUPPORTED, "mesh_redistribute: single-instance context required");
+    if (!(dt_fixed >= 0.0)) return fail(c, ES_ERR_ARG, "mesh_redistribute: dt_fixed must be >= 0");
+    StagePtrs P;
+    memset(&P, 0, sizeof(P));
+    P.JU = JU;
+    P.J = J;
+    P.x = x;
+    P.xdot_out = xdot;
+    P.out = dt_dtau;
+    P.dt_fixed = dt_fixed;
+    launch_mesh(c, P, nullptr, (cudaStream_t)stream);
+    return cuda_check(c, "mesh_redistribute");
+}
+
+es_status entropy_production(es_ctx* c, const double* JU, const double* J, const double* dJU, const double* dJ,
+                             double* out2, void* stream)
+{
+    if (!c) return ES_ERR_ARG;
+    if (!JU || !J || !out2) return fail(c, ES_ERR_ARG, "entropy_production: null pointer");
+    if (c->n_inst != 1) return fail(c, ES_ERR_UNSUPPORTED, "entropy_production: single-instance context required");
+    StagePtrs P;
+    memset(&P, 0, sizeof(P));
+    P.JU = JU;
+    P.J = J;
+    P.accU = const_cast<double*>(dJU);
+    P.accJ = const_cast<double*>(dJ);
+    P.out = out2;
+    cudaStream_t st = (cudaStream_t)stream;
+    ProfScope ps(c, PC_ENTROPY, st);
+    entropy_partial_kernel<<<node_grid(c, c->n_cell), NODE_TPB, 0, st>>>(c->dI, P, nullptr, c->w_cell, c->n_cell, c->partial);
+    entropy_final_kernel<<<1, 256, 0, st>>>(c->dI, P, nullptr, c->d_first_cell, c->partial);
+    return cuda_check(c, "entropy_production");
+}
+
+es_status es_bind_batch(es_ctx* c, double* const* JU, double* const* J, double* const* x, double* const* xdot,
+                        double* const* dt_dtau)
+{
+    if (!c) return ES_ERR_ARG;
+    if (!JU || !J || !x || !xdot || !dt_dtau) return fail(c, ES_ERR_ARG, "es_bind_batch: null table");
+    for (int i = 0; i < c->n_inst; ++i)
+        if (!JU[i] || !J[i] || !x[i] || !xdot[i] || !dt_dtau[i]) return fail(c, ES_ERR_ARG, "es_bind_batch: null pointer");
+    std::vector<StagePtrs> mesh(c->n_inst), st[3];
+    for (int s = 0; s < 3; ++s) st[s].resize(c->n_inst);
+    for (int i = 0; i < c->n_inst; ++i) {
+        StagePtrs P;
+        memset(&P, 0, sizeof(P));
+        P.JU = JU[i];
+        P.J = J[i];
+        P.x = x[i];
+        P.M = c->hS[i].M;
+        P.xdot_out = xdot[i];
+        P.out = dt_dtau[i];
+        mesh[i] = P;
+        StagePtrs S3[3];
+        stage_ptrs(c, i, JU[i], J[i], x[i], xdot[i], dt_dtau[i], S3);
+        for (int s = 0; s < 3; ++s) st[s][i] = S3[s];
+    }
+    if (!c->tab_mesh) {
+        bool ok = dalloc(c, (void**)&c->tab_mesh, sizeof(StagePtrs) * c->n_inst);
+        for (int s = 0; s < 3; ++s) ok = ok && dalloc(c, (void**)&c->tab_stage[s], sizeof(StagePtrs) * c->n_inst);
+        if (!ok) return fail(c, ES_ERR_CUDA, "es_bind_batch: table allocation failed");
+    }
+    cudaMemcpy(c->tab_mesh, mesh.data(), sizeof(StagePtrs) * c->n_inst, cudaMemcpyHostToDevice);
+    for (int s = 0; s < 3; ++s) cudaMemcpy(c->tab_stage[s], st[s].data(), sizeof(StagePtrs) * c->n_inst, cudaMemcpyHostToDevice);
+    c->bound = true;
+    return cuda_check(c, "es_bind_batch");
+}
+
+es_status es_step_batch(es_ctx* c, void* stream)
+{
+    if (!c) return ES_ERR_ARG;
+    if (!c->bound) return fail(c, ES_ERR_ARG, "es_step_batch: call es_bind_batch first");
+    cudaStream_t st = (cudaStream_t)stream;
+    StagePtrs none;
+    memset(&none, 0, sizeof(none));
+    launch_mesh(c, none, c->tab_mesh, st);
+    for (int s = 0; s < 3; ++s) launch_residual(c, none, c->tab_stage[s], true, RK_A[s], RK_B[s], st);
+    return cuda_check(c, "es_step_batch");
+}
+
+es_status es_run_host(es_ctx* c, double* JU, double* J, double* x, int steps, double dt_fixed, double* t, void* stream)
+{
+    if (!c) return ES_ERR_ARG;
+    if (!JU || !J || !x || steps < 0) return fail(c, ES_ERR_ARG, "es_run_host: bad argument");
+    if (c->n_inst != 1) return fail(c, ES_ERR_UNSUPPORTED, "es_run_host: single-instance context required");
+    const Inst& I = c->hI[0];
+    long long n = I.ncell;
+    if (!c->hJU) {
+        bool ok = dalloc(c, (void**)&c->hJU, sizeof(double) * I.nc * n) && dalloc(c, (void**)&c->hJ, sizeof(double) * n) &&
+                  dalloc(c, (void**)&c->hx, sizeof(double) * I.d * n) && dalloc(c, (void**)&c->hxd, sizeof(double) * I.d * n) &&
+                  dalloc(c, (void**)&c->hdt, sizeof(double) * 2) && dalloc(c, (void**)&c->htacc, sizeof(double));
+        if (!ok) return fail(c, ES_ERR_CUDA, "es_run_host: allocation failed");
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaMemcpyAsync(c->hJU, JU, sizeof(double) * I.nc * n, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(c->hJ, J, sizeof(double) * n, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(c->hx, x, sizeof(double) * I.d * n, cudaMemcpyHostToDevice, st);
+    cudaMemsetAsync(c->htacc, 0, sizeof(double), st);
+    for (int s = 0; s < steps; ++s) {
+        es_status r = mesh_redistribute(c, c->hJU, c->hJ, c->hx, dt_fixed, c->hxd, c->hdt, stream);
+        if (r != ES_OK) return r;
+        r = es_rk_step(c, c->hJU, c->hJ, c->hx, c->hxd, c->hdt, stream);
+        if (r != ES_OK) return r;
+        time_acc_kernel<<<1, 1, 0, st>>>(c->htacc, c->hdt);
+    }
+    double tacc = 0.0;
+    cudaMemcpyAsync(JU, c->hJU, sizeof(double) * I.nc * n, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(J, c->hJ, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(x, c->hx, sizeof(double) * I.d * n, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&tacc, c->htacc, sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(c, ES_ERR_CUDA, std::string("es_run_host: ") + cudaGetErrorString(e));
+    if (t) *t += tacc;
+    return cuda_check(c, "es_run_host");
+}
+
+es_status es_profile(es_ctx* c, int enable)
+{
+    if (!c) return ES_ERR_ARG;
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    c->ev.clear();
+    c->ev_class.clear();
+    c->ev_used = 0;
+    for (int q = 0; q < 8; ++q) { c->prof_ms[q] = 0.0; c->prof_n[q] = 0; }
+    c->prof = enable != 0;
+    if (c->prof) {
+        const int pairs = 8192;
+        c->ev.resize(2 * pairs);
+        c->ev_class.resize(pairs);
+        for (auto& e : c->ev)
+            if (cudaEventCreate(&e) != cudaSuccess) { c->prof = false; return fail(c, ES_ERR_CUDA, "es_profile: event creation failed"); }
+    }
+    return ES_OK;
+}
+
+es_status es_profile_read(es_ctx* c, double* ms, long long* launches, int n_classes)
+{
+    if (!c || n_classes < 0 || n_classes > 8) return ES_ERR_ARG;
+    if (c->ev_used > 0) {
+        cudaError_t e = cudaEventSynchronize(c->ev[c->ev_used - 1]);
+        if (e != cudaSuccess) return fail(c, ES_ERR_CUDA, std::string("es_profile_read: ") + cudaGetErrorString(e));
+    }
+    for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, c->ev[i], c->ev[i + 1]);
+        int cls = c->ev_class[i / 2];
+        c->prof_ms[cls] += t;
+        c->prof_n[cls] += 1;
+    }
+    c->ev_used = 0;
+    for (int q = 0; q < n_classes; ++q) {
+        if (ms) ms[q] = c->prof_ms[q];
+        if (launches) launches[q] = c->prof_n[q];
+        c->prof_ms[q] = 0.0;
+        c->prof_n[q] = 0;
+    }
+    return ES_OK;
+}
+
+es_status es_poll_status(es_ctx* c, int* flags, void* stream)
+{
+    if (!c || !flags) return ES_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int h = 0;
+    cudaMemcpyAsync(&h, c->status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaMemsetAsync(c->status, 0, sizeof(int), st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(c, ES_ERR_CUDA, std::string("es_poll_status: ") + cudaGetErrorString(e));
+    *flags = h;
+    if (h & ST_NONPHYSICAL) return fail(c, ES_ERR_NONPHYSICAL, "non-physical state (rho_l <= 0, T <= 0 or NaN)");
+    return ES_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,204 @@
+// Shared device definitions of the ES moving-mesh library (arXiv 2202.07989).
+//
+// Data layout in HBM: every field is structure of arrays, field-major,
+// a[f][i3][i2][i1], interior nodes only (no ghost storage).  Ghost nodes are
+// reached through index maps on load (periodic wrap, wall mirror, outflow copy,
+// inflow state).  Metrics live in a padded buffer with 3 ghost layers per
+// direction, M[(k*(d+1)+c)][i3+3][i2+3][i1+3].
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace es {
+
+constexpr int MAXC = 6;    // N + d + 1 <= 6
+constexpr int HALO = 3;    // stencil half width of the flux (w = 3) and WENO-MR
+
+enum { BC_PERIODIC = 0, BC_REFLECT = 1, BC_INFLOW = 2, BC_OUTFLOW = 3 };
+enum { SIG_RHO = 0, SIG_RHO1 = 1, SIG_RHO2 = 2, SIG_P = 3, SIG_Y2 = 4, SIG_V1 = 5 };
+enum { ST_NONPHYSICAL = 1, ST_TIMEOUT = 2 };
+
+// alpha_{3,m} of the sixth-order EC flux (Sec. 3.1) and the matching delta weights
+__host__ __device__ constexpr double alpha3(int m) { return m == 1 ? 1.5 : (m == 2 ? -0.3 : 1.0 / 30.0); }
+
+// one instance of the problem: grid, boundary, physics and scheme parameters
+struct Inst {
+    int d, N, nc;
+    int n[3];                 // nodes per direction (n[2] = 1 in 2D)
+    int P[3];                 // padded extents of the metric buffer
+    long long ncell, npad;
+    double dxi[3], inv_dxi[3], xi_lo[3], L[3];
+    int bc[3][2];
+    double inflow[3][2][8];
+    double gamma[2], cv[2], pinf[2], Rs[2], cvG[2], pinf_tot;
+    int es;
+    double chi[3], weno_eps, cfl;
+    int n_sigma, sigma[4];
+    double alpha[4];
+    int mu, nf;
+    int tiles[3];             // flux tiles per direction
+    int ntile_nodes;          // 1D node tiles for node-wise kernels
+};
+
+// per-call device pointers of one instance: the stage input, the metric target,
+// the residual accumulators, the RK base and output, and the step scalars.
+// Single-instance calls pass it by value; batched calls use a device table.
+struct StagePtrs {
+    const double* JU;         // stage input (JU, J, x) and the mesh velocity
+    const double* J;
+    const double* x;
+    const double* xdot;
+    double* M;                // padded metrics target
+    double* accU;             // residual accumulators: n_c fields and J
+    double* accJ;
+    const double* JU0;        // RK base state q^n
+    const double* J0;
+    const double* x0;
+    double* JUo;              // RK stage output
+    double* Jo;
+    double* xo;
+    const double* dt;         // device scalar: the time step
+    double* xdot_out;         // mesh_redistribute outputs
+    double* out;              // {Delta t, Delta_tau}, or {P, S} of the entropy diagnostics
+    double dt_fixed;          // > 0: use this time step instead of Eq. (cfl)
+};
+
+// context-owned scratch of one instance (fixed for the context's lifetime)
+struct Scratch {
+    double* M;                // padded metrics
+    double* D3;               // 3D: delta_b[x_p] on the grid with 6 ghost layers
+    double* accU;
+    double* accJ;
+    double* red;              // reductions: [0] CFL max, [1..4] monitor maxima, [5] Delta_tau
+    double* g;                // monitor gradients, n_sigma fields
+    void* th0;                // monitor function ping-pong (compute type)
+    void* th1;
+    double* xa;               // Jacobi ping-pong
+    double* xb;
+    double* zeros;            // d zero fields (absent mesh velocity)
+};
+
+#define ES_PTRS(P) const StagePtrs P = (table ? table[it.x] : single)
+
+__host__ __device__ inline long long lin(const Inst& I, int i0, int i1, int i2)
+{
+    return ((long long)i2 * I.n[1] + i1) * I.n[0] + i0;
+}
+
+__host__ __device__ inline long long plin(const Inst& I, int i0, int i1, int i2)
+{
+    return ((long long)(I.d == 3 ? i2 + 3 : 0) * I.P[1] + (i1 + 3)) * I.P[0] + (i0 + 3);
+}
+
+__device__ inline int floordiv_(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// mesh position at any node index: periodic sides wrap and shift x_k by the box
+// length, all other sides mirror about the wall (velocity: mirror negates x_k)
+template <bool VEL>
+__device__ inline void x_at(const Inst& I, const double* __restrict__ x, int i0, int i1, int i2, double* out)
+{
+    int i[3] = { i0, i1, i2 };
+    double shift[3] = { 0, 0, 0 }, wall[3] = { 0, 0, 0 };
+    bool flip[3] = { false, false, false };
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (k >= I.d) break;
+        int n = I.n[k];
+        if (i[k] >= 0 && i[k] < n) continue;
+        int side = i[k] < 0 ? 0 : 1;
+        if (I.bc[k][side] == BC_PERIODIC) {
+            int s = floordiv_(i[k], n);
+            i[k] -= s * n;
+            shift[k] = s * I.L[k];
+        } else {
+            i[k] = side == 0 ? -1 - i[k] : 2 * n - 1 - i[k];
+            flip[k] = true;
+            wall[k] = side == 0 ? I.xi_lo[k] : I.xi_lo[k] + I.L[k];
+        }
+    }
+    long long id = lin(I, i[0], i[1], I.d == 3 ? i[2] : 0);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        if (j >= I.d) break;
+        double v = x[j * I.ncell + id];
+        if (VEL) {
+            if (flip[j]) v = -v;
+        } else {
+            if (flip[j]) v = 2.0 * wall[j] - v;
+            v += shift[j];
+        }
+        out[j] = v;
+    }
+}
+
+// node index along direction k (g may be a ghost) -> interior index and the
+// boundary treatment: 0 none, 1 negate the k-momentum (reflect), 2 inflow state
+__device__ inline int map_line(const Inst& I, int k, int g, int& gi, int& side)
+{
+    int n = I.n[k];
+    side = g < 0 ? 0 : 1;
+    if (g >= 0 && g < n) { gi = g; return 0; }
+    switch (I.bc[k][side]) {
+    case BC_PERIODIC: gi = g - floordiv_(g, n) * n; return 0;
+    case BC_REFLECT: gi = side == 0 ? -1 - g : 2 * n - 1 - g; if (gi < 0) gi = 0; if (gi >= n) gi = n - 1; return 1;
+    case BC_OUTFLOW: gi = side == 0 ? 0 : n - 1; return 0;
+    default: gi = side == 0 ? 0 : n - 1; return 2;
+    }
+}
+
+// scalar node field with periodic wrap, else copy of the boundary node
+__device__ inline long long s_map(const Inst& I, int i0, int i1, int i2)
+{
+    int i[3] = { i0, i1, i2 };
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (k >= I.d) break;
+        int n = I.n[k];
+        if (i[k] >= 0 && i[k] < n) continue;
+        int side = i[k] < 0 ? 0 : 1;
+        if (I.bc[k][side] == BC_PERIODIC) i[k] -= floordiv_(i[k], n) * n;
+        else i[k] = side == 0 ? 0 : n - 1;
+    }
+    return lin(I, i[0], i[1], I.d == 3 ? i[2] : 0);
+}
+
+// conserved point state at a node reached along one grid line (ghost maps of the
+// boundary conditions); returns false for a non-physical state
+__device__ inline void load_U(const Inst& I, const double* __restrict__ JU, const double* __restrict__ J,
+                              int i0, int i1, int i2, double* U)
+{
+    int i[3] = { i0, i1, i2 };
+    int neg = -1;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (k >= I.d) break;
+        if (i[k] >= 0 && i[k] < I.n[k]) continue;
+        int gi, side;
+        int t = map_line(I, k, i[k], gi, side);
+        if (t == 2) {
+            for (int q = 0; q < I.nc; ++q) U[q] = I.inflow[k][side][q];
+            return;
+        }
+        if (t == 1) neg = k;
+        i[k] = gi;
+    }
+    long long id = lin(I, i[0], i[1], I.d == 3 ? i[2] : 0);
+    double inv = 1.0 / J[id];
+    for (int q = 0; q < I.nc; ++q) U[q] = JU[q * I.ncell + id] * inv;
+    if (neg >= 0) U[I.N + neg] = -U[I.N + neg];
+}
+
+// bounded reductions of non-negative doubles: the IEEE order of non-negative
+// doubles is the order of their bit patterns
+__device__ inline void atomic_max_pos(double* a, double v)
+{
+    atomicMax(reinterpret_cast<unsigned long long*>(a), (unsigned long long)__double_as_longlong(v));
+}
+
+__device__ inline void atomic_min_pos(double* a, double v)
+{
+    atomicMin(reinterpret_cast<unsigned long long*>(a), (unsigned long long)__double_as_longlong(v));
+}
+
+}  // namespace es

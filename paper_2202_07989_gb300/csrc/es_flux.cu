@@ -1,0 +1,582 @@
+// Flux + divergence kernel of the semi-discrete scheme, one launch per direction k
+// (Eqs. (semi_U), (semi_J)), with the SSP-RK3 stage update fused into the last
+// direction.  Per interface i+1/2 along k it forms
+//   * the sixth-order EC flux: sum_m alpha_m sum_s F(U_{i-s}, U_{i-s+m}, M_{i-s}, M_{i-s+m})
+//     with the two-point flux of Eq. (ECfluxMM) (Sec. 3.3, written in the
+//     contracted form below),
+//   * the GCL flux of J xi_k/t (Eq. (GCL_flux)),
+//   * the ES dissipation -1/2 T^T R |Lambda| Y [[W]]^WENOMR of Eq. (HOstable)
+//     with the scaled eigenvectors of Sec. 3.4 and the WENO-MR of Appendix A,
+// and the divergence -(F_{i+1/2} - F_{i-1/2}) / dxi_k is accumulated per node.
+//
+// Tile: (S + 6) x WT nodes staged in shared memory (3 halo nodes per side along
+// k), one thread per interface ((S + 1) x WT = 256), one thread per node in the
+// load and store phases (coalesced along the contiguous dimension).
+//
+// Contracted two-point flux.  With means over the pair, u~ = Mt + sum_j Mx_j {v_j},
+// rho~ = sum_l {rho_l}^ln, P' = sum_l R_l {rho_l} / {beta} (= P~ + p_inf) and
+// E' = sum_l {rho_l}^ln c_{v,l} / {beta}^ln - rho~ sum_m {v_m^2}/2 + rho~ sum_m {v_m}^2
+// (= U~_E - p_inf), the flux of Eq. (ECfluxMM) is
+//   F_l = u~ {rho_l}^ln,  F_m = u~ rho~ {v_m} + Mx_m (P' - p_inf),
+//   F_E = u~ E' + (u~ - Mt) P' + p_inf Mt.
+// Summed over the pairs, the p_inf Mx_m terms give p_inf times the GCL flux of
+// J xi_k/x_m, whose divergence vanishes by the discrete SCL (Eq. (SCL_dis)), and
+// the p_inf Mt terms give p_inf times the GCL flux of J xi_k/t.  The kernel drops
+// the first and adds the second in FP64, which keeps the large p_inf of stiffened
+// gases out of the low-precision pair arithmetic.
+#include "es_kernels.cuh"
+
+#include <type_traits>
+
+namespace es {
+
+template <typename R>
+struct Ar;
+
+template <>
+struct Ar<double> {
+    static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+    static __device__ __forceinline__ double dv(double a, double b) { return a / b; }
+    static __device__ __forceinline__ double lg(double x) { return log(x); }
+    static __device__ __forceinline__ double sq(double x) { return sqrt(x); }
+    static __device__ __forceinline__ double ab(double x) { return fabs(x); }
+    // {a}^ln: [[a]]/[[ln a]], Ismail-Roe series when ((b-a)/(b+a))^2 < 1e-4
+    static __device__ __forceinline__ double lmean(double a, double b, double la, double lb)
+    {
+        double s = a + b, dd = b - a;
+        if (fabs(dd) < 0.01 * s) {
+            double f = dd / s, u = f * f;
+            return 0.5 * s * (1.0 - u * (1.0 / 3.0 + u * (4.0 / 45.0 + u * (44.0 / 945.0))));
+        }
+        return dd / (lb - la);
+    }
+    // 1/{a}^ln given is = 1/(a + b)
+    static __device__ __forceinline__ double inv_lmean(double a, double b, double la, double lb, double is)
+    {
+        double dd = b - a;
+        if (fabs(dd) < 0.01 * (a + b)) {
+            double f = dd * is, u = f * f;
+            return 2.0 * is * (1.0 + u * (1.0 / 3.0 + u * (1.0 / 5.0 + u * (1.0 / 7.0))));
+        }
+        return (lb - la) / dd;
+    }
+};
+
+template <>
+struct Ar<float> {
+    static __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+    static __device__ __forceinline__ float dv(float a, float b) { return __fdividef(a, b); }
+    static __device__ __forceinline__ float lg(float x) { return logf(x); }
+    static __device__ __forceinline__ float sq(float x) { return sqrtf(x); }
+    static __device__ __forceinline__ float ab(float x) { return fabsf(x); }
+    // small jumps ((b-a)/(b+a))^2 < 1e-2: {a}^ln = {a} (1 - delta(u)), the mean {a}
+    // and the correction formed in FP64; delta is the series of 1 - f/artanh(f)
+    static __device__ __forceinline__ double small_branch(float a, float b, float u)
+    {
+        float del = u * (1.f / 3.f + u * (4.f / 45.f + u * (44.f / 945.f + u * (428.f / 14175.f))));
+        double hs = 0.5 * ((double)a + (double)b);
+        return fma(-hs, (double)del, hs);
+    }
+    static __device__ __forceinline__ float lmean(float a, float b, float la, float lb)
+    {
+        float s = a + b, dd = b - a;
+        if (fabsf(dd) < 0.1f * s) {
+            float f = __fdividef(dd, s);
+            return (float)small_branch(a, b, f * f);
+        }
+        return __fdividef(dd, lb - la);
+    }
+    static __device__ __forceinline__ float inv_lmean(float a, float b, float la, float lb, float is)
+    {
+        float dd = b - a;
+        if (fabsf(dd) < 0.1f * (a + b)) {
+            float f = dd * is;
+            return __frcp_rn((float)small_branch(a, b, f * f));
+        }
+        return __fdividef(lb - la, dd);
+    }
+};
+
+// fifth-order multi-resolution WENO value at x_{j+1/2} from W_{j-2..j+2} (Appendix A);
+// beta_2, beta_3 are the closed forms printed there.
+template <typename R>
+__device__ __forceinline__ R weno_mr(R w0, R w1, R w2, R w3, R w4, R c1, R c2, R c3, R eps)
+{
+    R a2 = R(0.5) * (w3 - w1);
+    R a3 = R(0.5) * (w1 + w3) - w2;
+    R b2 = (R(11) * (w0 - w4) + R(82) * (w3 - w1)) * R(1.0 / 120.0);
+    R b3 = (R(-3) * (w0 + w4) + R(40) * (w1 + w3) - R(74) * w2) * R(1.0 / 56.0);
+    R b4 = (w4 - w0 + R(2) * (w1 - w3)) * R(1.0 / 12.0);
+    R b5 = (w0 + w4 - R(4) * (w1 + w3) + R(6) * w2) * R(1.0 / 24.0);
+    R d0 = (w2 - w1) * (w2 - w1), d1 = (w3 - w2) * (w3 - w2);
+    R be1 = d0 < d1 ? d0 : d1;
+    R be2 = a2 * a2 + R(13.0 / 3.0) * a3 * a3;
+    R t1 = b2 + R(0.1) * b4, t2 = b3 + R(123.0 / 455.0) * b5;
+    R be3 = t1 * t1 + R(13.0 / 3.0) * t2 * t2 + R(781.0 / 20.0) * b4 * b4 + R(1421461.0 / 2275.0) * b5 * b5;
+    R tau = R(0.5) * (Ar<R>::ab(be3 - be1) + Ar<R>::ab(be3 - be2));
+    tau = tau * tau;
+    R h1 = w2;
+    R h2 = w2 + R(0.5) * a2 + R(1.0 / 6.0) * a3;
+    R h3 = w2 + R(0.5) * b2 + R(1.0 / 6.0) * b3 + R(0.05) * b4 + R(1.0 / 70.0) * b5;
+    R h3c = (h3 - c1 * h1 - c2 * h2) * Ar<R>::rcp(c3);
+    R e1 = eps + be1, e2 = eps + be2, e3 = eps + be3;
+    if constexpr (std::is_same<R, double>::value) {
+        // common denominator e1 e2 e3: one division
+        R o1 = c1 * (e1 + tau) * e2 * e3, o2 = c2 * (e2 + tau) * e1 * e3, o3 = c3 * (e3 + tau) * e1 * e2;
+        return (o1 * h1 + o2 * h2 + o3 * h3c) / (o1 + o2 + o3);
+    } else {
+        R o1 = c1 * (R(1) + Ar<R>::dv(tau, e1)), o2 = c2 * (R(1) + Ar<R>::dv(tau, e2)), o3 = c3 * (R(1) + Ar<R>::dv(tau, e3));
+        return Ar<R>::dv(o1 * h1 + o2 * h2 + o3 * h3c, o1 + o2 + o3);
+    }
+}
+
+template <int D, int NS>
+struct Lay {
+    static constexpr int NC = NS + D + 1;
+    static constexpr int RHO = 0, LRHO = NS, V = 2 * NS, B = 2 * NS + D, LB = B + 1, X = LB + 1;
+    static constexpr int NX = NS == 2 ? 5 : 0;   // p, rho, ln rho, R_mix, Gamma_mix
+    static constexpr int VV = X + NX;            // entropy variables
+    static constexpr int MR = VV + NC;           // metrics J xi_k/t, J xi_k/x_j (compute type)
+    static constexpr int NF = MR + 1 + D;
+};
+
+template <int S, int WT>
+struct Tile {
+    static constexpr int NN = (S + 6) * WT;
+    static constexpr int NI = (S + 1) * WT;
+};
+
+template <int D, int NS, typename R, int S, int WT>
+__global__ void __launch_bounds__(FLUX_TPB) flux_kernel(FluxLaunch L)
+{
+    using Y = Lay<D, NS>;
+    constexpr int NC = Y::NC, NN = Tile<S, WT>::NN, NI = Tile<S, WT>::NI, NF = Y::NF;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* fl = reinterpret_cast<double*>(smem_raw);        // [NC + 1][NI]
+    double* mt64 = fl + (NC + 1) * NI;                          // [NN]
+    R* nr = reinterpret_cast<R*>(mt64 + NN);                    // [NF][NN]
+    const int k = L.k;
+    const int adim = k == 0 ? 1 : 0, bdim = k == 2 ? 1 : 2;
+
+    for (int wi = blockIdx.x; wi < L.nwork; wi += gridDim.x) {
+        const int2 it = L.work[wi];
+        const Inst& I = L.insts[it.x];
+        const StagePtrs P = L.ptrs ? L.ptrs[it.x] : L.single;
+        const int nk = I.n[k], na = I.n[adim], nb = (bdim < D) ? I.n[bdim] : 1;
+        const int ns = (nk + S - 1) / S, nat = (na + WT - 1) / WT;
+        const int ts = it.y % ns, ta = (it.y / ns) % nat, tb = it.y / (ns * nat);
+        const int s0 = ts * S, a0 = ta * WT;
+        const long long ncell = I.ncell;
+        const double inv_dx = I.inv_dxi[k];
+
+        // ---------------- phase 1: node states, entropy variables, metrics ----------------
+        for (int t = threadIdx.x; t < NN; t += blockDim.x) {
+            int s, w;
+            if (k == 0) { s = t % (S + 6); w = t / (S + 6); }
+            else { w = t % WT; s = t / WT; }
+            const int node = w * (S + 6) + s;
+            const int g = s0 - 3 + s, a = a0 + w;
+            if (a >= na || g > nk + 2) {
+                // outside the grid: benign values, never read by a valid interface
+                for (int f = 0; f < NF; ++f) nr[f * NN + node] = R(1);
+                mt64[node] = 0.0;
+                continue;
+            }
+            int idx[3] = { 0, 0, 0 };
+            idx[k] = g;
+            idx[adim] = a;
+            if (bdim < D) idx[bdim] = tb;
+            double Ud[MAXC];
+            load_U(I, P.JU, P.J, idx[0], idx[1], idx[2], Ud);
+            // primitives: T = (E - rho|v|^2/2 - p_inf) / sum cv_l rho_l, p = sum rho_l R_l T - p_inf
+            R U[MAXC];
+#pragma unroll
+            for (int q = 0; q < NC; ++q) U[q] = (R)Ud[q];
+            R rho = U[0] + (NS == 2 ? U[1] : R(0));
+            R irho = Ar<R>::rcp(rho);
+            R v[D], v2 = R(0);
+#pragma unroll
+            for (int m = 0; m < D; ++m) { v[m] = U[NS + m] * irho; v2 += v[m] * v[m]; }
+            R cvr = R(I.cv[0]) * U[0] + (NS == 2 ? R(I.cv[1]) * U[1] : R(0));
+            R rhoe_p = U[NS + D] - R(0.5) * rho * v2 - R(I.pinf_tot);
+            R beta = cvr * Ar<R>::rcp(rhoe_p);
+            bool bad = !(rhoe_p > R(0)) || !(U[0] > R(0)) || (NS == 2 && !(U[1] > R(0)));
+            if (bad) {
+                atomicOr(L.status, ST_NONPHYSICAL);
+                beta = R(1);
+            }
+            R lb = Ar<R>::lg(beta);
+            R lr0 = Ar<R>::lg(bad ? R(1) : U[0]);
+            R lr1 = NS == 2 ? Ar<R>::lg(bad ? R(1) : U[1]) : R(0);
+            nr[Y::RHO * NN + node] = U[0];
+            nr[Y::LRHO * NN + node] = lr0;
+            if (NS == 2) { nr[(Y::RHO + 1) * NN + node] = U[1]; nr[(Y::LRHO + 1) * NN + node] = lr1; }
+#pragma unroll
+            for (int m = 0; m < D; ++m) nr[(Y::V + m) * NN + node] = v[m];
+            nr[Y::B * NN + node] = beta;
+            nr[Y::LB * NN + node] = lb;
+            if (NS == 2) {
+                R T = Ar<R>::rcp(beta);
+                R rr = R(I.Rs[0]) * U[0] + R(I.Rs[1]) * U[1];
+                nr[(Y::X + 0) * NN + node] = rr * T - R(I.pinf_tot);                 // p
+                nr[(Y::X + 1) * NN + node] = rho;                                    // rho
+                nr[(Y::X + 2) * NN + node] = Ar<R>::lg(bad ? R(1) : rho);           // ln rho
+                nr[(Y::X + 3) * NN + node] = rr * irho;                              // R_mix
+                nr[(Y::X + 4) * NN + node] = (R(I.cvG[0]) * U[0] + R(I.cvG[1]) * U[1]) * Ar<R>::rcp(cvr);  // Gamma_mix
+            }
+            // entropy variables V_l = c_{v,l} ln beta + R_l ln rho_l - |v|^2 beta/2 + c_{v,l} Gamma_l
+            R hv = R(0.5) * v2 * beta;
+            nr[(Y::VV + 0) * NN + node] = R(I.cv[0]) * lb + R(I.Rs[0]) * lr0 - hv + R(I.cvG[0]);
+            if (NS == 2) nr[(Y::VV + 1) * NN + node] = R(I.cv[1]) * lb + R(I.Rs[1]) * lr1 - hv + R(I.cvG[1]);
+#pragma unroll
+            for (int m = 0; m < D; ++m) nr[(Y::VV + NS + m) * NN + node] = v[m] * beta;
+            nr[(Y::VV + NS + D) * NN + node] = -beta;
+            // metrics of direction k at this node (padded buffer covers g in [-3, n + 3))
+            long long pid = plin(I, idx[0], idx[1], idx[2]);
+            double m0 = P.M[(long long)(k * (D + 1)) * I.npad + pid];
+            mt64[node] = m0;
+            nr[Y::MR * NN + node] = (R)m0;
+#pragma unroll
+            for (int j = 0; j < D; ++j) nr[(Y::MR + 1 + j) * NN + node] = (R)P.M[(long long)(k * (D + 1) + 1 + j) * I.npad + pid];
+        }
+        __syncthreads();
+
+        // ---------------- phase 2: interface fluxes ----------------
+        for (int f = threadIdx.x; f < NI; f += blockDim.x) {
+            const int s = f % (S + 1), w = f / (S + 1);
+            const int gi = s0 - 1 + s;     // interface gi + 1/2
+            if (a0 + w >= na || gi > nk - 1) continue;
+            const int base = w * (S + 6) + s;   // node gi - 2
+#define NR(fld, j) nr[(fld) * NN + base + (j)]
+            R Fe[NC];
+#pragma unroll
+            for (int q = 0; q < NC; ++q) Fe[q] = R(0);
+            // means of the centre pair (i, i+1), reused by the dissipation
+            R lr_c[NS], ilb_c = R(0);
+#pragma unroll
+            for (int m = 1; m <= 3; ++m) {
+#pragma unroll
+                for (int ss = 0; ss < m; ++ss) {
+                    const int l = 2 - ss, r = 2 - ss + m;
+                    const R am = R(alpha3(m));
+                    R mt = R(0.5) * (NR(Y::MR, l) + NR(Y::MR, r));
+                    R mx[D], vb[D];
+                    R ut = mt, v2b = R(0), vbsq = R(0);
+#pragma unroll
+                    for (int j = 0; j < D; ++j) {
+                        mx[j] = R(0.5) * (NR(Y::MR + 1 + j, l) + NR(Y::MR + 1 + j, r));
+                        R vl = NR(Y::V + j, l), vr = NR(Y::V + j, r);
+                        vb[j] = R(0.5) * (vl + vr);
+                        v2b += R(0.5) * (vl * vl + vr * vr);
+                        vbsq += vb[j] * vb[j];
+                        ut += mx[j] * vb[j];
+                    }
+                    R lr[NS], rt = R(0), rra = R(0);
+#pragma unroll
+                    for (int q = 0; q < NS; ++q) {
+                        R al = NR(Y::RHO + q, l), ar = NR(Y::RHO + q, r);
+                        lr[q] = Ar<R>::lmean(al, ar, NR(Y::LRHO + q, l), NR(Y::LRHO + q, r));
+                        rt += lr[q];
+                        rra += R(I.Rs[q]) * (al + ar);
+                    }
+                    R bl = NR(Y::B, l), br = NR(Y::B, r);
+                    R is = Ar<R>::rcp(bl + br);
+                    R ilb = Ar<R>::inv_lmean(bl, br, NR(Y::LB, l), NR(Y::LB, r), is);
+                    R Pp = rra * is;                                   // sum R_l {rho_l} / {beta}
+                    R Ep = -R(0.5) * rt * v2b + rt * vbsq;
+#pragma unroll
+                    for (int q = 0; q < NS; ++q) Ep += lr[q] * R(I.cv[q]) * ilb;
+                    R aut = am * ut;
+#pragma unroll
+                    for (int q = 0; q < NS; ++q) Fe[q] += aut * lr[q];
+#pragma unroll
+                    for (int j = 0; j < D; ++j) Fe[NS + j] += aut * rt * vb[j] + am * mx[j] * Pp;
+                    Fe[NS + D] += aut * Ep + am * (ut - mt) * Pp;
+                    if (m == 1) {
+#pragma unroll
+                        for (int q = 0; q < NS; ++q) lr_c[q] = lr[q];
+                        ilb_c = ilb;
+                    }
+                }
+            }
+            // GCL flux of (J xi_k/t, J xi_k/x_j): stencil (1, -8, 37, 37, -8, 1)/60
+            const double c0 = 0.5 * (alpha3(1) + alpha3(2) + alpha3(3)), c1 = 0.5 * (alpha3(2) + alpha3(3)), c2 = 0.5 * alpha3(3);
+            const double* m64 = mt64 + base;
+            double Gt = c0 * (m64[2] + m64[3]) + c1 * (m64[1] + m64[4]) + c2 * (m64[0] + m64[5]);
+            double Fd_out[NC];
+#pragma unroll
+            for (int q = 0; q < NC; ++q) Fd_out[q] = 0.0;
+            if (I.es) {
+                R Gx[D], L2 = R(0);
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    const int fj = Y::MR + 1 + j;
+                    Gx[j] = R(c0) * (NR(fj, 2) + NR(fj, 3)) + R(c1) * (NR(fj, 1) + NR(fj, 4)) + R(c2) * (NR(fj, 0) + NR(fj, 5));
+                    L2 += Gx[j] * Gx[j];
+                }
+                R Ln = Ar<R>::sq(L2), iL = Ar<R>::rcp(Ln);
+                R n[D];
+#pragma unroll
+                for (int j = 0; j < D; ++j) n[j] = Gx[j] * iL;
+                // rotation rows t0 = n, t1, t2 (Eq. (rotamatrix) built from the unit normal)
+                R T[D][D];
+                if constexpr (D == 2) {
+                    T[0][0] = n[0]; T[0][1] = n[1];
+                    T[1][0] = -n[1]; T[1][1] = n[0];
+                } else {
+                    R rr2 = n[0] * n[0] + n[1] * n[1];
+                    R rq = Ar<R>::sq(rr2);
+                    R ct = R(1), st = R(0);
+                    if (rq > R(0)) { R irq = Ar<R>::rcp(rq); ct = n[0] * irq; st = n[1] * irq; }
+                    R cp = rq, sp = n[D - 1];
+                    T[0][0] = n[0]; T[0][1] = n[1]; T[0][D - 1] = n[D - 1];
+                    T[1][0] = -st; T[1][1] = ct; T[1][D - 1] = R(0);
+                    T[D - 1][0] = -sp * ct; T[D - 1][1] = -sp * st; T[D - 1][D - 1] = cp;
+                }
+                // interface averages (Sec. 3.4)
+                R vb[D], vh[D], vv = R(0);
+#pragma unroll
+                for (int j = 0; j < D; ++j) { vb[j] = R(0.5) * (NR(Y::V + j, 2) + NR(Y::V + j, 3)); vv += vb[j] * vb[j]; }
+#pragma unroll
+                for (int m = 0; m < D; ++m) {
+                    R s_ = R(0);
+#pragma unroll
+                    for (int j = 0; j < D; ++j) s_ += T[m][j] * vb[j];
+                    vh[m] = s_;
+                }
+                const R Tb = ilb_c;       // T-bar = 1 / {beta}^ln
+                R cb, H, sa, se = R(0), ssh, Y1 = R(1), Y2 = R(0), pre = R(0), D11 = R(0), D12 = R(0), D21 = R(0), D22 = R(0), e1 = R(0), e2 = R(0);
+                if constexpr (NS == 1) {
+                    const R G = R(I.gamma[0]), Rg = R(I.Rs[0]), cv = R(I.cv[0]);
+                    const R rb = lr_c[0];
+                    cb = Ar<R>::sq(Rg * G * Tb);
+                    H = G * cv * Tb + R(0.5) * vv;
+                    sa = Ar<R>::sq(rb * Ar<R>::rcp(R(2) * G * Rg));
+                    se = Ar<R>::sq(rb * Ar<R>::rcp(cv * G));
+                    ssh = Ar<R>::sq(rb * Tb);
+                } else {
+                    const R rb = Ar<R>::lmean(NR(Y::X + 1, 2), NR(Y::X + 1, 3), NR(Y::X + 2, 2), NR(Y::X + 2, 3));
+                    const R Rb = R(0.5) * (NR(Y::X + 3, 2) + NR(Y::X + 3, 3));
+                    const R Gb = R(0.5) * (NR(Y::X + 4, 2) + NR(Y::X + 4, 3));
+                    const R pb = R(0.5) * (NR(Y::X + 0, 2) + NR(Y::X + 0, 3));
+                    R rh = pb + R(I.pinf_tot) + (R(I.cv[0]) * lr_c[0] + R(I.cv[1]) * lr_c[1]) * Tb;
+                    R irb = Ar<R>::rcp(rb);
+                    Y1 = lr_c[0] * irb;
+                    Y2 = lr_c[1] * irb;
+                    H = rh * irb + R(0.5) * vv;
+                    cb = Ar<R>::sq(Rb * Gb * Tb);
+                    pre = Ar<R>::sq(rb * Ar<R>::rcp(Gb * Rb));
+                    sa = pre * R(0.70710678118654752440);
+                    ssh = Ar<R>::sq(rb * Tb);
+                    const R R1 = R(I.Rs[0]), R2 = R(I.Rs[1]);
+                    R sy = Ar<R>::sq(Y1 * Y2), sg = Ar<R>::sq(Gb - R(1));
+                    D11 = -pre * sy * Ar<R>::sq(Gb * R2 * Ar<R>::rcp(R1));
+                    D21 = pre * sy * Ar<R>::sq(Gb * R1 * Ar<R>::rcp(R2));
+                    D12 = pre * Y1 * sg;
+                    D22 = pre * Y2 * sg;
+                    R igm = Ar<R>::rcp(Gb - R(1));
+                    e1 = R(0.5) * vv - (R(I.cv[0]) + R1 - Gb * R(I.cv[0])) * Tb * igm;
+                    e2 = R(0.5) * vv - (R(I.cv[1]) + R2 - Gb * R(I.cv[1])) * Tb * igm;
+                }
+                const R lam = Ar<R>::ab(R(Gt) + Ln * vh[0]) + Ln * cb;
+                const R ch1 = R(I.chi[0]), ch2 = R(I.chi[1]), ch3 = R(I.chi[2]), eps = R(I.weno_eps);
+                R Fd[NC];
+#pragma unroll
+                for (int q = 0; q < NC; ++q) Fd[q] = R(0);
+#pragma unroll
+                for (int col = 0; col < NC; ++col) {
+                    // column col of R in the rotated frame
+                    R rc[NC];
+#pragma unroll
+                    for (int q = 0; q < NC; ++q) rc[q] = R(0);
+                    if (col == 0 || col == NC - 1) {
+                        const R sg = col == 0 ? R(-1) : R(1);
+                        if (NS == 1) rc[0] = R(1);
+                        else { rc[0] = Y1; rc[1] = Y2; }
+#pragma unroll
+                        for (int j = 0; j < D; ++j) rc[NS + j] = vh[j];
+                        rc[NS] += sg * cb;
+                        rc[NS + D] = H + sg * cb * vh[0];
+#pragma unroll
+                        for (int q = 0; q < NC; ++q) rc[q] *= sa;
+                    } else if (col <= NS) {
+                        if constexpr (NS == 1) {
+#pragma unroll
+                            for (int j = 0; j < D; ++j) rc[1 + j] = se * vh[j];
+                            rc[0] = se;
+                            rc[1 + D] = se * R(0.5) * vv;
+                        } else {
+                            const R da = col == 1 ? D11 : D12, db = col == 1 ? D21 : D22;
+                            rc[0] = da;
+                            rc[1] = db;
+#pragma unroll
+                            for (int j = 0; j < D; ++j) rc[2 + j] = (da + db) * vh[j];
+                            rc[2 + D] = da * e1 + db * e2;
+                        }
+                    } else {
+                        const int mm = col - NS;      // shear: rotated velocity component mm (1..D-1)
+                        rc[NS + mm] = ssh;
+                        rc[NS + D] = ssh * vh[mm];
+                    }
+                    // back to the unrotated frame: T^T on the velocity block
+                    R ru[D];
+#pragma unroll
+                    for (int j = 0; j < D; ++j) {
+                        R s_ = R(0);
+#pragma unroll
+                        for (int m = 0; m < D; ++m) s_ += T[m][j] * rc[NS + m];
+                        ru[j] = s_;
+                    }
+#pragma unroll
+                    for (int j = 0; j < D; ++j) rc[NS + j] = ru[j];
+                    // scaled entropy variables W_j = r_col . V_j at the six nodes
+                    R wv[6];
+#pragma unroll
+                    for (int j = 0; j < 6; ++j) {
+                        R s_ = R(0);
+#pragma unroll
+                        for (int q = 0; q < NC; ++q) s_ += rc[q] * NR(Y::VV + q, j);
+                        wv[j] = s_;
+                    }
+                    R Wm = weno_mr<R>(wv[0], wv[1], wv[2], wv[3], wv[4], ch1, ch2, ch3, eps);
+                    R Wp = weno_mr<R>(wv[5], wv[4], wv[3], wv[2], wv[1], ch1, ch2, ch3, eps);
+                    R jw = Wp - Wm, jp = wv[3] - wv[2];
+                    if ((jw > R(0) && jp > R(0)) || (jw < R(0) && jp < R(0))) {
+                        R cf = lam * jw;
+#pragma unroll
+                        for (int q = 0; q < NC; ++q) Fd[q] += rc[q] * cf;
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < NC; ++q) Fd_out[q] = -0.5 * (double)Fd[q];
+            }
+#undef NR
+#pragma unroll
+            for (int q = 0; q < NC; ++q) fl[q * NI + f] = (double)Fe[q] + Fd_out[q];
+            fl[(NC - 1) * NI + f] += I.pinf_tot * Gt;
+            fl[NC * NI + f] = Gt;
+        }
+        __syncthreads();
+
+        // ---------------- phase 3: divergence and output ----------------
+        const double dt = L.mode == MODE_RK ? *P.dt : 0.0;
+        for (int t = threadIdx.x; t < S * WT; t += blockDim.x) {
+            int s, w;
+            if (k == 0) { s = t % S; w = t / S; }
+            else { w = t % WT; s = t / WT; }
+            const int g = s0 + s, a = a0 + w;
+            if (g >= nk || a >= na) continue;
+            int idx[3] = { 0, 0, 0 };
+            idx[k] = g;
+            idx[adim] = a;
+            if (bdim < D) idx[bdim] = tb;
+            const long long id = lin(I, idx[0], idx[1], idx[2]);
+            const int fr = w * (S + 1) + s + 1, fL = fr - 1;
+            double r[NC + 1];
+#pragma unroll
+            for (int q = 0; q <= NC; ++q) r[q] = -(fl[q * NI + fr] - fl[q * NI + fL]) * inv_dx;
+            if (L.mode == MODE_WRITE) {
+#pragma unroll
+                for (int q = 0; q < NC; ++q) P.accU[q * ncell + id] = r[q];
+                P.accJ[id] = r[NC];
+            } else if (L.mode == MODE_ACC) {
+#pragma unroll
+                for (int q = 0; q < NC; ++q) P.accU[q * ncell + id] += r[q];
+                P.accJ[id] += r[NC];
+            } else {
+                const double A = L.a, B = L.b;
+#pragma unroll
+                for (int q = 0; q < NC; ++q) {
+                    double rq = P.accU[q * ncell + id] + r[q];
+                    double base = A != 0.0 ? A * P.JU0[q * ncell + id] : 0.0;
+                    P.JUo[q * ncell + id] = base + B * (P.JU[q * ncell + id] + dt * rq);
+                }
+                double rj = P.accJ[id] + r[NC];
+                double bj = A != 0.0 ? A * P.J0[id] : 0.0;
+                P.Jo[id] = bj + B * (P.J[id] + dt * rj);
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    double bx = A != 0.0 ? A * P.x0[j * ncell + id] : 0.0;
+                    P.xo[j * ncell + id] = bx + B * (P.x[j * ncell + id] + dt * P.xdot[j * ncell + id]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int D, int NS, typename R, int S, int WT>
+static size_t smem_of()
+{
+    using Y = Lay<D, NS>;
+    constexpr int NN = Tile<S, WT>::NN, NI = Tile<S, WT>::NI;
+    return sizeof(double) * ((Y::NC + 1) * NI + NN) + sizeof(R) * Y::NF * NN;
+}
+
+size_t flux_smem_bytes(int D, int NS, bool mixed, int k)
+{
+#define SM(d, n, r) (k == 0 ? smem_of<d, n, r, S_K0, WT_K0>() : smem_of<d, n, r, S_KN, WT_KN>())
+    if (D == 2 && NS == 1) return mixed ? SM(2, 1, float) : SM(2, 1, double);
+    if (D == 2 && NS == 2) return mixed ? SM(2, 2, float) : SM(2, 2, double);
+    if (D == 3 && NS == 1) return mixed ? SM(3, 1, float) : SM(3, 1, double);
+    return mixed ? SM(3, 2, float) : SM(3, 2, double);
+#undef SM
+}
+
+template <int D, int NS, typename R>
+void prepare_flux()
+{
+    cudaFuncSetAttribute(flux_kernel<D, NS, R, S_K0, WT_K0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem_of<D, NS, R, S_K0, WT_K0>());
+    cudaFuncSetAttribute(flux_kernel<D, NS, R, S_KN, WT_KN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem_of<D, NS, R, S_KN, WT_KN>());
+}
+
+template <int D, int NS, typename R>
+int flux_blocks_per_sm(int k)
+{
+    int nb = 0;
+    if (k == 0)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, flux_kernel<D, NS, R, S_K0, WT_K0>, FLUX_TPB,
+                                                      smem_of<D, NS, R, S_K0, WT_K0>());
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, flux_kernel<D, NS, R, S_KN, WT_KN>, FLUX_TPB,
+                                                      smem_of<D, NS, R, S_KN, WT_KN>());
+    return nb > 0 ? nb : 1;
+}
+
+template <int D, int NS, typename R>
+void launch_flux(const FluxLaunch& L, int grid, cudaStream_t st)
+{
+    if (L.k == 0)
+        flux_kernel<D, NS, R, S_K0, WT_K0><<<grid, FLUX_TPB, smem_of<D, NS, R, S_K0, WT_K0>(), st>>>(L);
+    else
+        flux_kernel<D, NS, R, S_KN, WT_KN><<<grid, FLUX_TPB, smem_of<D, NS, R, S_KN, WT_KN>(), st>>>(L);
+}
+
+template void prepare_flux<2, 1, double>();
+template int flux_blocks_per_sm<2, 1, double>(int);
+template void prepare_flux<2, 1, float>();
+template int flux_blocks_per_sm<2, 1, float>(int);
+template void prepare_flux<2, 2, double>();
+template int flux_blocks_per_sm<2, 2, double>(int);
+template void prepare_flux<2, 2, float>();
+template int flux_blocks_per_sm<2, 2, float>(int);
+template void prepare_flux<3, 1, double>();
+template int flux_blocks_per_sm<3, 1, double>(int);
+template void prepare_flux<3, 1, float>();
+template int flux_blocks_per_sm<3, 1, float>(int);
+template void prepare_flux<3, 2, double>();
+template int flux_blocks_per_sm<3, 2, double>(int);
+template void prepare_flux<3, 2, float>();
+template int flux_blocks_per_sm<3, 2, float>(int);
+template void launch_flux<2, 1, double>(const FluxLaunch&, int, cudaStream_t);
+template void launch_flux<2, 2, double>(const FluxLaunch&, int, cudaStream_t);
+template void launch_flux<3, 1, double>(const FluxLaunch&, int, cudaStream_t);
+template void launch_flux<3, 2, double>(const FluxLaunch&, int, cudaStream_t);
+template void launch_flux<2, 1, float>(const FluxLaunch&, int, cudaStream_t);
+template void launch_flux<2, 2, float>(const FluxLaunch&, int, cudaStream_t);
+template void launch_flux<3, 1, float>(const FluxLaunch&, int, cudaStream_t);
+template void launch_flux<3, 2, float>(const FluxLaunch&, int, cudaStream_t);
+
+}  // namespace es

@@ -1,0 +1,187 @@
+// Geometry kernels: SCL-consistent metrics (Sec. 3.2, Eq. (SCLCoeff) and its
+// cyclic permutations; the 2D degenerate case), the VCL metric
+// J xi_k/t = -sum_j xdot_j J xi_k/x_j (Eq. (VCLCoeff)) and the initial
+// Jacobian J^0 = det(delta_k[x_j] / dxi_k).  All FP64.
+#include "es_kernels.cuh"
+
+namespace es {
+
+// delta_k[a] = (1/2) sum_m alpha_m (a_{+m} - a_{-m}) of the mesh coordinate p
+__device__ inline double delta_x(const Inst& I, const double* __restrict__ x, int i0, int i1, int i2, int k, int p)
+{
+    double acc = 0.0;
+#pragma unroll
+    for (int m = 1; m <= 3; ++m) {
+        double a[3], b[3];
+        int ip[3] = { i0, i1, i2 }, im[3] = { i0, i1, i2 };
+        ip[k] += m;
+        im[k] -= m;
+        x_at<false>(I, x, ip[0], ip[1], ip[2], a);
+        x_at<false>(I, x, im[0], im[1], im[2], b);
+        acc += alpha3(m) * (a[p] - b[p]);
+    }
+    return 0.5 * acc;
+}
+
+// 2D: J xi_1/x = (delta_2[x_2], -delta_2[x_1]) / dxi_2, J xi_2/x = (-delta_1[x_2], delta_1[x_1]) / dxi_1
+__global__ void metrics2d_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
+                                 const int2* __restrict__ work, int nwork)
+{
+    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+        int2 it = work[wi];
+        const Inst& I = insts[it.x];
+        ES_PTRS(S);
+        long long p = (long long)it.y * blockDim.x + threadIdx.x;
+        if (p >= I.npad) continue;
+        int i0 = (int)(p % I.P[0]) - 3, i1 = (int)(p / I.P[0]) - 3;
+        double a[2], b[2], c[2], e[2];
+        // delta_1 and delta_2 of both coordinates, sharing the neighbour loads
+        double d1[2] = { 0, 0 }, d2[2] = { 0, 0 };
+#pragma unroll
+        for (int m = 1; m <= 3; ++m) {
+            x_at<false>(I, S.x, i0 + m, i1, 0, a);
+            x_at<false>(I, S.x, i0 - m, i1, 0, b);
+            x_at<false>(I, S.x, i0, i1 + m, 0, c);
+            x_at<false>(I, S.x, i0, i1 - m, 0, e);
+            d1[0] += alpha3(m) * (a[0] - b[0]);
+            d1[1] += alpha3(m) * (a[1] - b[1]);
+            d2[0] += alpha3(m) * (c[0] - e[0]);
+            d2[1] += alpha3(m) * (c[1] - e[1]);
+        }
+        double m11 = 0.5 * d2[1] * I.inv_dxi[1], m12 = -0.5 * d2[0] * I.inv_dxi[1];
+        double m21 = -0.5 * d1[1] * I.inv_dxi[0], m22 = 0.5 * d1[0] * I.inv_dxi[0];
+        double xd[2] = { 0, 0 };
+        if (S.xdot) x_at<true>(I, S.xdot, i0, i1, 0, xd);
+        double* M = S.M;
+        long long np = I.npad;
+        M[0 * np + p] = -(xd[0] * m11 + xd[1] * m12);
+        M[1 * np + p] = m11;
+        M[2 * np + p] = m12;
+        M[3 * np + p] = -(xd[0] * m21 + xd[1] * m22);
+        M[4 * np + p] = m21;
+        M[5 * np + p] = m22;
+    }
+}
+
+// 3D pass 1: D[b][p] = delta_b[x_p] at nodes with 6 ghost layers (extent n + 12)
+__global__ void dx3d_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
+                            const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr)
+{
+    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+        int2 it = work[wi];
+        const Inst& I = insts[it.x];
+        ES_PTRS(S);
+        long long E0 = I.n[0] + 12, E1 = I.n[1] + 12, E2 = I.n[2] + 12, ne = E0 * E1 * E2;
+        long long p = (long long)it.y * blockDim.x + threadIdx.x;
+        if (p >= ne) continue;
+        int i0 = (int)(p % E0) - 6, i1 = (int)((p / E0) % E1) - 6, i2 = (int)(p / (E0 * E1)) - 6;
+        double* D = scr[it.x].D3;
+        double acc[3][3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) acc[b][q] = 0.0;
+#pragma unroll
+        for (int m = 1; m <= 3; ++m) {
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                double u[3], v[3];
+                int ip[3] = { i0, i1, i2 }, im[3] = { i0, i1, i2 };
+                ip[b] += m;
+                im[b] -= m;
+                x_at<false>(I, S.x, ip[0], ip[1], ip[2], u);
+                x_at<false>(I, S.x, im[0], im[1], im[2], v);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) acc[b][q] += alpha3(m) * (u[q] - v[q]);
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) D[(b * 3 + q) * ne + p] = 0.5 * acc[b][q];
+    }
+}
+
+// 3D pass 2: J xi_k/x_j = (delta_a[D_b[x_p] x_q] - delta_b[D_a[x_p] x_q]) / (dxi_a dxi_b)
+// with (a, b) = (3,2), (1,3), (2,1) for k = 1, 2, 3 and (p, q) = (2,3), (3,1), (1,2)
+// for j = 1, 2, 3 (cyclic permutation of Eq. (SCLCoeff)).
+__global__ void metrics3d_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
+                                 const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr)
+{
+    const int AB[3][2] = { { 2, 1 }, { 0, 2 }, { 1, 0 } };
+    const int PQ[3][2] = { { 1, 2 }, { 2, 0 }, { 0, 1 } };
+    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+        int2 it = work[wi];
+        const Inst& I = insts[it.x];
+        ES_PTRS(S);
+        long long p = (long long)it.y * blockDim.x + threadIdx.x;
+        if (p >= I.npad) continue;
+        int i0 = (int)(p % I.P[0]) - 3, i1 = (int)((p / I.P[0]) % I.P[1]) - 3, i2 = (int)(p / ((long long)I.P[0] * I.P[1])) - 3;
+        const double* D = scr[it.x].D3;
+        long long E0 = I.n[0] + 12, E1 = I.n[1] + 12, ne = E0 * E1 * (I.n[2] + 12);
+        auto eidx = [&](int a0, int a1, int a2) { return ((long long)(a2 + 6) * E1 + (a1 + 6)) * E0 + (a0 + 6); };
+        double m[3][3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            int a = AB[k][0], b = AB[k][1];
+            double t[3] = { 0, 0, 0 };
+#pragma unroll
+            for (int mm = 1; mm <= 3; ++mm) {
+                // neighbours along a and along b
+                int pa[3] = { i0, i1, i2 }, ma[3] = { i0, i1, i2 }, pb_[3] = { i0, i1, i2 }, mb[3] = { i0, i1, i2 };
+                pa[a] += mm; ma[a] -= mm; pb_[b] += mm; mb[b] -= mm;
+                double xpa[3], xma[3], xpb[3], xmb[3];
+                x_at<false>(I, S.x, pa[0], pa[1], pa[2], xpa);
+                x_at<false>(I, S.x, ma[0], ma[1], ma[2], xma);
+                x_at<false>(I, S.x, pb_[0], pb_[1], pb_[2], xpb);
+                x_at<false>(I, S.x, mb[0], mb[1], mb[2], xmb);
+                long long ipa = eidx(pa[0], pa[1], pa[2]), ima = eidx(ma[0], ma[1], ma[2]);
+                long long ipb = eidx(pb_[0], pb_[1], pb_[2]), imb = eidx(mb[0], mb[1], mb[2]);
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    int pp = PQ[j][0], q = PQ[j][1];
+                    double ta = D[(b * 3 + pp) * ne + ipa] * xpa[q] - D[(b * 3 + pp) * ne + ima] * xma[q];
+                    double tb = D[(a * 3 + pp) * ne + ipb] * xpb[q] - D[(a * 3 + pp) * ne + imb] * xmb[q];
+                    t[j] += alpha3(mm) * (ta - tb);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 3; ++j) m[k][j] = 0.5 * t[j] * I.inv_dxi[a] * I.inv_dxi[b];
+        }
+        double xd[3] = { 0, 0, 0 };
+        if (S.xdot) x_at<true>(I, S.xdot, i0, i1, i2, xd);
+        double* M = S.M;
+        long long np = I.npad;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            M[(k * 4 + 0) * np + p] = -(xd[0] * m[k][0] + xd[1] * m[k][1] + xd[2] * m[k][2]);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) M[(k * 4 + 1 + j) * np + p] = m[k][j];
+        }
+    }
+}
+
+// J^0 = det(delta_k[x_j] / dxi_k) at the interior nodes
+__global__ void init_J_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
+                              const int2* __restrict__ work, int nwork)
+{
+    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+        int2 it = work[wi];
+        const Inst& I = insts[it.x];
+        ES_PTRS(S);
+        long long p = (long long)it.y * blockDim.x + threadIdx.x;
+        if (p >= I.ncell) continue;
+        int i0 = (int)(p % I.n[0]), i1 = (int)((p / I.n[0]) % I.n[1]), i2 = (int)(p / ((long long)I.n[0] * I.n[1]));
+        double A[3][3];
+        for (int j = 0; j < I.d; ++j)
+            for (int k = 0; k < I.d; ++k) A[j][k] = delta_x(I, S.x, i0, i1, i2, k, j) * I.inv_dxi[k];
+        double det;
+        if (I.d == 2) det = A[0][0] * A[1][1] - A[0][1] * A[1][0];
+        else
+            det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0])
+                + A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+        S.Jo[p] = det;
+    }
+}
+
+}  // namespace es

@@ -1,0 +1,410 @@
+// Per-step kernels: CFL time step (Eq. (cfl)), monitor function (Eq. (monitor)),
+// low-pass filter (remark in Sec. 4), Jacobi sweeps of the discrete mesh
+// equation, the movement limiter Delta_tau and the mesh velocity (Sec. 4), and
+// the entropy diagnostics.  FP64 positions and reductions; the monitor and the
+// filter run in the compute type of the context (FP32 in the mixed form).
+#include "es_mesh.cuh"
+
+namespace es {
+
+// reduction slots per instance
+//   red[0] max_i sum_k rho_{i,k}/dxi_k,  red[1..4] max |grad sigma_s|,  red[5] Delta_tau
+
+__global__ void red_init_kernel(const Scratch* __restrict__ scr, int ninst)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ninst) return;
+    double* r = scr[i].red;
+    for (int q = 0; q < 5; ++q) r[q] = 0.0;
+    r[5] = 1.0;
+}
+
+template <typename T>
+__device__ inline T block_max(T v, T* sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? sh[lane] : T(0);
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    }
+    return v;
+}
+
+__device__ inline double block_min_pos(double v, double* sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? sh[lane] : 1.0;
+        for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    }
+    return v;
+}
+
+__device__ inline void node_coords(const Inst& I, long long p, int& i0, int& i1, int& i2)
+{
+    i0 = (int)(p % I.n[0]);
+    i1 = (int)((p / I.n[0]) % I.n[1]);
+    i2 = (int)(p / ((long long)I.n[0] * I.n[1]));
+}
+
+__device__ inline void prim(const Inst& I, const double* U, double* rl, double* v, double& T, double& p, double& rho)
+{
+    rho = 0.0;
+    double cvr = 0.0, rr = 0.0;
+    for (int l = 0; l < I.N; ++l) { rl[l] = U[l]; rho += U[l]; cvr += I.cv[l] * U[l]; rr += I.Rs[l] * U[l]; }
+    double v2 = 0.0;
+    for (int m = 0; m < I.d; ++m) { v[m] = U[I.N + m] / rho; v2 += v[m] * v[m]; }
+    T = (U[I.N + I.d] - 0.5 * rho * v2 - I.pinf_tot) / cvr;
+    p = rr * T - I.pinf_tot;
+}
+
+// CFL: s_i = sum_k (|J xi_k/x . v| + c |J xi_k/x|) / (J dxi_k) from node metrics at x^n
+__global__ void cfl_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
+                           const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr)
+{
+    __shared__ double sh[32];
+    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+        int2 it = work[wi];
+        const Inst& I = insts[it.x];
+        ES_PTRS(P);
+        long long p = (long long)it.y * blockDim.x + threadIdx.x;
+        double s = 0.0;
+        if (p < I.ncell) {
+            int i0, i1, i2;
+            node_coords(I, p, i0, i1, i2);
+            double U[MAXC], rl[2], v[3], T, pr, rho;
+            load_U(I, P.JU, P.J, i0, i1, i2, U);
+            prim(I, U, rl, v, T, pr, rho);
+            double a = 0.0, g = 0.0, cvr = 0.0;
+            for (int l = 0; l < I.N; ++l) { a += (I.gamma[l] - 1.0) * I.cv[l] * rl[l]; g += I.gamma[l] * I.cv[l] * rl[l]; cvr += I.cv[l] * rl[l]; }
+            double c = sqrt((a / rho) * (g / cvr) * T);
+            long long pid = plin(I, i0, i1, i2);
+            for (int k = 0; k < I.d; ++k) {
+                double L2 = 0.0, vn = 0.0;
+                for (int j = 0; j < I.d; ++j) {
+                    double m = scr[it.x].M[(long long)(k * (I.d + 1) + 1 + j) * I.npad + pid];
+                    L2 += m * m;
+                    vn += m * v[j];
+                }
+                s += (fabs(vn) + c * sqrt(L2)) / P.J[p] * I.inv_dxi[k];
+            }
+            if (!(s >= 0.0)) s = 0.0;
+        }
+        double m = block_max<double>(s, sh);
+        if (threadIdx.x == 0) atomic_max_pos(&scr[it.x].red[0], m);
+    }
+}
+
+__device__ inline double sigma_of(const Inst& I, int kind, const double* U)
+{
+    double rl[2], v[3], T, p, rho;
+    prim(I, U, rl, v, T, p, rho);
+    switch (kind) {
+    case SIG_RHO1: return rl[0];
+    case SIG_RHO2: return I.N == 2 ? rl[1] : 0.0;
+    case SIG_P: return p;
+    case SIG_Y2: return I.N == 2 ? rl[1] / rho : 0.0;
+    case SIG_V1: return v[0];
+    default: return rho;
+    }
+}
+
+// |grad_xi sigma_s| by second-order central differences; per-instance maxima
+__global__ void monitor_grad_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
+                                    const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr)
+{
+    __shared__ double sh[32];
+    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+        int2 it = work[wi];
+        const Inst& I = insts[it.x];
+        ES_PTRS(P);
+        long long p = (long long)it.y * blockDim.x + threadIdx.x;
+        double g[4] = { 0, 0, 0, 0 };
+        if (p < I.ncell) {
+            int i[3];
+            node_coords(I, p, i[0], i[1], i[2]);
+            for (int k = 0; k < I.d; ++k) {
+                int ip[3] = { i[0], i[1], i[2] }, im[3] = { i[0], i[1], i[2] };
+                ip[k] += 1;
+                im[k] -= 1;
+                double Up[MAXC], Um[MAXC];
+                load_U(I, P.JU, P.J, ip[0], ip[1], ip[2], Up);
+                load_U(I, P.JU, P.J, im[0], im[1], im[2], Um);
+                for (int s = 0; s < I.n_sigma; ++s) {
+                    double gk = (sigma_of(I, I.sigma[s], Up) - sigma_of(I, I.sigma[s], Um)) * (0.5 * I.inv_dxi[k]);
+                    g[s] += gk * gk;
+                }
+            }
+            for (int s = 0; s < I.n_sigma; ++s) {
+                g[s] = sqrt(g[s]);
+                if (!(g[s] >= 0.0)) g[s] = 0.0;
+                scr[it.x].g[(long long)s * I.ncell + p] = g[s];
+            }
+        }
+        for (int s = 0; s < 4; ++s) {
+            if (s >= I.n_sigma) break;
+            double m = block_max<double>(g[s], sh);
+            if (threadIdx.x == 0) atomic_max_pos(&scr[it.x].red[1 + s], m);
+        }
+    }
+}
+
+template <typename R>
+__global__ void monitor_theta_kernel(const Inst* __restrict__ insts, const int2* __restrict__ work, int nwork,
+                                     const Scratch* __restrict__ scr)
+{
+    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+        int2 it = work[wi];
+        const Inst& I = insts[it.x];
+        const Scratch& P = scr[it.x];
+        long long p = (long long)it.y * blockDim.x + threadIdx.x;
+        if (p >= I.ncell) continue;
+        R t = R(1);
+        for (int s = 0; s < I.n_sigma; ++s) {
+            double mx = P.red[1 + s];
+            if (mx > 0.0) {
+                R r = R(P.g[(long long)s * I.ncell + p] / mx);
+                t += R(I.alpha[s]) * r * r;
+            }
+        }
+        reinterpret_cast<R*>(P.th0)[p] = sqrt(t);
+    }
+}
+
+// one pass of the low-pass filter, weights (1/2)^(|j|_1 + d) over the 3^d stencil
+template <typename R>
+__global__ void filter_kernel(const Inst* __restrict__ insts, const int2* __restrict__ work, int nwork,
+                              const Scratch* __restrict__ scr, int parity)
+{
+    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+        int2 it = work[wi];
+        const Inst& I = insts[it.x];
+        long long p = (long long)it.y * blockDim.x + threadIdx.x;
+        if (p >= I.ncell) continue;
+        int i0, i1, i2;
+        node_coords(I, p, i0, i1, i2);
+        const R* a = reinterpret_cast<const R*>(parity ? scr[it.x].th1 : scr[it.x].th0);
+        R* dst = reinterpret_cast<R*>(parity ? scr[it.x].th0 : scr[it.x].th1);
+        R acc = R(0);
+        int lo3 = I.d == 3 ? -1 : 0, hi3 = I.d == 3 ? 1 : 0;
+        for (int j3 = lo3; j3 <= hi3; ++j3)
+            for (int j2 = -1; j2 <= 1; ++j2) {
+                R row = R(0);
+                for (int j1 = -1; j1 <= 1; ++j1) row += (j1 == 0 ? R(0.5) : R(0.25)) * a[s_map(I, i0 + j1, i1 + j2, i2 + j3)];
+                acc += (j2 == 0 ? R(0.5) : R(0.25)) * (j3 == 0 ? (I.d == 3 ? R(0.5) : R(1)) : R(0.25)) * row;
+            }
+        dst[p] = acc;
+    }
+}
+
+// one Jacobi sweep: x_i = sum_k (T_{k+} x_{i+e_k} + T_{k-} x_{i-e_k}) / dxi_k^2 / sum_k (T_{k+} + T_{k-}) / dxi_k^2
+template <typename R>
+__global__ void jacobi_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
+                              const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr, int sweep,
+                              int theta_sel)
+{
+    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+        int2 it = work[wi];
+        const Inst& I = insts[it.x];
+        long long p = (long long)it.y * blockDim.x + threadIdx.x;
+        if (p >= I.ncell) continue;
+        int i[3];
+        node_coords(I, p, i[0], i[1], i[2]);
+        ES_PTRS(P);
+        const Scratch& Sc = scr[it.x];
+        const R* th = reinterpret_cast<const R*>(theta_sel ? Sc.th1 : Sc.th0);
+        const double* xs = sweep == 0 ? P.x : (sweep % 2 == 1 ? Sc.xa : Sc.xb);
+        double* xd_ = sweep % 2 == 0 ? Sc.xa : Sc.xb;
+        double tc = (double)th[p];
+        double num[3] = { 0, 0, 0 }, den = 0.0;
+        for (int k = 0; k < I.d; ++k) {
+            int ip[3] = { i[0], i[1], i[2] }, im[3] = { i[0], i[1], i[2] };
+            ip[k] += 1;
+            im[k] -= 1;
+            double tp = 0.5 * (tc + (double)th[s_map(I, ip[0], ip[1], ip[2])]);
+            double tm = 0.5 * (tc + (double)th[s_map(I, im[0], im[1], im[2])]);
+            double xp[3], xm[3];
+            x_at<false>(I, xs, ip[0], ip[1], ip[2], xp);
+            x_at<false>(I, xs, im[0], im[1], im[2], xm);
+            double h2 = I.inv_dxi[k] * I.inv_dxi[k];
+            for (int j = 0; j < I.d; ++j) num[j] += (tp * xp[j] + tm * xm[j]) * h2;
+            den += (tp + tm) * h2;
+        }
+        double id = 1.0 / den;
+        for (int j = 0; j < I.d; ++j) xd_[(long long)j * I.ncell + p] = num[j] * id;
+    }
+}
+
+// Delta_tau = min(1, bounds of Sec. 4) per instance
+__device__ inline const double* xmu_of(const StagePtrs& P, const Scratch& S, int mu)
+{
+    return mu == 0 ? P.x : (mu % 2 == 1 ? S.xa : S.xb);
+}
+
+__global__ void limiter_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
+                               const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr)
+{
+    __shared__ double sh[32];
+    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+        int2 it = work[wi];
+        const Inst& I = insts[it.x];
+        ES_PTRS(P);
+        const double* xmu = xmu_of(P, scr[it.x], I.mu);
+        long long p = (long long)it.y * blockDim.x + threadIdx.x;
+        double b = 1.0;
+        if (p < I.ncell) {
+            int i[3];
+            node_coords(I, p, i[0], i[1], i[2]);
+            for (int k = 0; k < I.d; ++k) {
+                double xc = P.x[(long long)k * I.ncell + p];
+                double dx = xmu[(long long)k * I.ncell + p] - xc;
+                int nb[3] = { i[0], i[1], i[2] };
+                double xn[3];
+                if (dx < 0.0) {
+                    nb[k] -= 1;
+                    x_at<false>(I, P.x, nb[0], nb[1], nb[2], xn);
+                    b = fmin(b, -(xc - xn[k]) / (2.0 * dx));
+                } else if (dx > 0.0) {
+                    nb[k] += 1;
+                    x_at<false>(I, P.x, nb[0], nb[1], nb[2], xn);
+                    b = fmin(b, (xn[k] - xc) / (2.0 * dx));
+                }
+            }
+            if (!(b >= 0.0)) b = 0.0;
+        }
+        double m = block_min_pos(b, sh);
+        if (threadIdx.x == 0) atomic_min_pos(&scr[it.x].red[5], m);
+    }
+}
+
+// Delta t = C / max (or the given step), xdot = Delta_tau (x^[mu] - x^n) / Delta t;
+// out = (Delta t, Delta_tau)
+__global__ void xdot_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
+                            const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr)
+{
+    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+        int2 it = work[wi];
+        const Inst& I = insts[it.x];
+        ES_PTRS(P);
+        const double* red = scr[it.x].red;
+        const double* xmu = xmu_of(P, scr[it.x], I.mu);
+        double dt = P.dt_fixed > 0.0 ? P.dt_fixed : I.cfl / red[0];
+        double dtau = red[5];
+        long long p = (long long)it.y * blockDim.x + threadIdx.x;
+        if (it.y == 0 && threadIdx.x == 0) {
+            P.out[0] = dt;
+            P.out[1] = dtau;
+        }
+        if (p >= I.ncell) continue;
+        for (int j = 0; j < I.d; ++j) {
+            long long q = (long long)j * I.ncell + p;
+            P.xdot_out[q] = dtau * (xmu[q] - P.x[q]) / dt;
+        }
+    }
+}
+
+// entropy diagnostics: per-block partial sums of V.dJU - phi dJ and J eta
+__global__ void entropy_partial_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
+                                       const int2* __restrict__ work, int nwork, double* __restrict__ partial)
+{
+    __shared__ double sh[2][32];
+    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+        int2 it = work[wi];
+        const Inst& I = insts[it.x];
+        ES_PTRS(P);
+        long long p = (long long)it.y * blockDim.x + threadIdx.x;
+        double a = 0.0, b = 0.0;
+        if (p < I.ncell) {
+            const double* JU = P.JU;
+            double J = P.J[p], U[MAXC];
+            for (int q = 0; q < I.nc; ++q) U[q] = JU[(long long)q * I.ncell + p] / J;
+            double rl[2], v[3], T, pr, rho;
+            prim(I, U, rl, v, T, pr, rho);
+            double v2 = 0.0, eta = 0.0, phi = 0.0;
+            for (int m = 0; m < I.d; ++m) v2 += v[m] * v[m];
+            double lT = log(T);
+            double V[MAXC];
+            for (int l = 0; l < I.N; ++l) {
+                double S = I.cv[l] * lT - I.Rs[l] * log(rl[l]);
+                V[l] = -S - v2 / (2.0 * T) + I.cvG[l];
+                eta -= rl[l] * S;
+                phi += I.Rs[l] * rl[l] - I.pinf[l] / T;
+            }
+            for (int m = 0; m < I.d; ++m) V[I.N + m] = v[m] / T;
+            V[I.N + I.d] = -1.0 / T;
+            if (P.accU && P.accJ) {
+                for (int q = 0; q < I.nc; ++q) a += V[q] * P.accU[(long long)q * I.ncell + p];
+                a -= phi * P.accJ[p];
+            }
+            b = J * eta;
+        }
+        // deterministic block sums (fixed shuffle tree)
+        for (int o = 16; o > 0; o >>= 1) { a += __shfl_xor_sync(0xffffffffu, a, o); b += __shfl_xor_sync(0xffffffffu, b, o); }
+        int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        __syncthreads();
+        if (lane == 0) { sh[0][wid] = a; sh[1][wid] = b; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double sa = 0.0, sb = 0.0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { sa += sh[0][q]; sb += sh[1][q]; }
+            partial[2 * (long long)wi] = sa;
+            partial[2 * (long long)wi + 1] = sb;
+        }
+    }
+}
+
+// one block per instance sums its partials in a fixed order
+__global__ void entropy_final_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
+                                     const int* __restrict__ first_work, const double* __restrict__ partial)
+{
+    __shared__ double sh[2][32];
+    int inst = blockIdx.x;
+    const Inst& I = insts[inst];
+    const StagePtrs P = table ? table[inst] : single;
+    int w0 = first_work[inst], w1 = first_work[inst + 1];
+    double a = 0.0, b = 0.0;
+    for (int w = w0 + threadIdx.x; w < w1; w += blockDim.x) { a += partial[2 * (long long)w]; b += partial[2 * (long long)w + 1]; }
+    for (int o = 16; o > 0; o >>= 1) { a += __shfl_xor_sync(0xffffffffu, a, o); b += __shfl_xor_sync(0xffffffffu, b, o); }
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { sh[0][wid] = a; sh[1][wid] = b; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sa = 0.0, sb = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { sa += sh[0][q]; sb += sh[1][q]; }
+        double vol = 1.0;
+        for (int k = 0; k < I.d; ++k) vol *= I.dxi[k];
+        P.out[0] = vol * sa;
+        P.out[1] = vol * sb;
+    }
+}
+
+void launch_monitor_theta(bool mixed, int grid, cudaStream_t st, const Inst* insts, const int2* work, int nwork,
+                          const Scratch* scr)
+{
+    if (mixed) monitor_theta_kernel<float><<<grid, NODE_TPB, 0, st>>>(insts, work, nwork, scr);
+    else monitor_theta_kernel<double><<<grid, NODE_TPB, 0, st>>>(insts, work, nwork, scr);
+}
+
+void launch_filter(bool mixed, int grid, cudaStream_t st, const Inst* insts, const int2* work, int nwork,
+                   const Scratch* scr, int parity)
+{
+    if (mixed) filter_kernel<float><<<grid, NODE_TPB, 0, st>>>(insts, work, nwork, scr, parity);
+    else filter_kernel<double><<<grid, NODE_TPB, 0, st>>>(insts, work, nwork, scr, parity);
+}
+
+void launch_jacobi(bool mixed, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
+                   const StagePtrs* table, const int2* work, int nwork, const Scratch* scr, int sweep, int theta_sel)
+{
+    if (mixed) jacobi_kernel<float><<<grid, NODE_TPB, 0, st>>>(insts, single, table, work, nwork, scr, sweep, theta_sel);
+    else jacobi_kernel<double><<<grid, NODE_TPB, 0, st>>>(insts, single, table, work, nwork, scr, sweep, theta_sel);
+}
+
+}  // namespace es

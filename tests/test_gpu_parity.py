@@ -1,0 +1,229 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Sizes span several flux tiles with ragged tails (tiles are 63 x 4 nodes along
+direction 1 and 31 x 8 along directions 2 and 3).  FP64 path: relative max-norm
+error per field <= 1e-12.  Mixed path: FP32-level bounds, with the measured
+errors printed.
+"""
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle
+from paper_2202_07989_gb300 import workloads as W
+
+from .helpers import TOL_FP64, case, fieldwise, need_gpu, rel_max_err, to_dev
+
+pytestmark = pytest.mark.gpu
+
+GRIDS = {2: (70, 37), 3: (22, 12, 11)}
+CASES = [(2, 1), (2, 2), (3, 1), (3, 2)]
+
+
+def _ctx(pb, precision=0):
+    from paper_2202_07989_gb300 import es
+    return es.Context(pb, precision)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+@pytest.mark.parametrize("bc", ["periodic", "mixed"])
+def test_init_mesh_and_metrics(d, bc):
+    torch = need_gpu()
+    pb, JU, J, x, xdot = case(d, 1, GRIDS[d], bc)
+    o = Oracle(pb)
+    ctx = _ctx(pb)
+    Jg = ctx.es_init_mesh(to_dev(x, torch)).cpu().numpy()
+    assert rel_max_err(Jg, o.init_J(x)) <= TOL_FP64
+    Mg = ctx.es_metrics(to_dev(x, torch), to_dev(xdot, torch)).cpu().numpy()
+    Mo = o.metrics(x, xdot)
+    errs = fieldwise(Mg, Mo, floor=1e-3)
+    assert max(errs) <= TOL_FP64, errs
+
+
+@pytest.mark.parametrize("d,N", CASES)
+@pytest.mark.parametrize("bc", ["periodic", "mixed"])
+@pytest.mark.parametrize("es_", [False, True])
+def test_rhs_fp64(d, N, bc, es_):
+    torch = need_gpu()
+    pb, JU, J, x, xdot = case(d, N, GRIDS[d], bc, es=es_, seed=d * 10 + N, pinf=0.7 if N == 1 else 0.0)
+    dJU_o, dJ_o = Oracle(pb).rhs(JU, J, x, xdot)
+    ctx = _ctx(pb)
+    dJU, dJ = ctx.es_rhs(to_dev(JU, torch), to_dev(J, torch), to_dev(x, torch), to_dev(xdot, torch))
+    e = fieldwise(dJU.cpu().numpy(), dJU_o) + [rel_max_err(dJ.cpu().numpy(), dJ_o)]
+    assert max(e) <= TOL_FP64, e
+    assert ctx.es_poll_status() == 0
+
+
+@pytest.mark.parametrize("d,N", [(2, 1), (2, 2), (3, 2)])
+def test_rhs_fp64_discontinuous(d, N):
+    """Discontinuous data: the sign matrix Y and beta_1 = min(..) decide; both sides agree."""
+    torch = need_gpu()
+    pb, JU, J, x, xdot = case(d, N, GRIDS[d], "mixed", es=True, seed=7, jump=True)
+    dJU_o, dJ_o = Oracle(pb).rhs(JU, J, x, xdot)
+    ctx = _ctx(pb)
+    dJU, dJ = ctx.es_rhs(to_dev(JU, torch), to_dev(J, torch), to_dev(x, torch), to_dev(xdot, torch))
+    e = fieldwise(dJU.cpu().numpy(), dJU_o) + [rel_max_err(dJ.cpu().numpy(), dJ_o)]
+    assert max(e) <= TOL_FP64, e
+
+
+def test_rk_steps_vortex_config():
+    """The 64 x 64 moving-mesh isentropic vortex (sixth-order EC + WENO-MR, SSP-RK3,
+    CFL 0.4): 10 steps on the GPU vs 10 oracle steps, FP64."""
+    torch = need_gpu()
+    pb, U, x, xdot = W.vortex_2d(64)
+    o = Oracle(pb)
+    J = o.init_J(x)
+    JU = U * J
+    dt = o.cfl_dt(JU, J, x)
+    ctx = _ctx(pb)
+    JUg, Jg, xg = to_dev(JU, torch), to_dev(J, torch), to_dev(x, torch)
+    xdg = to_dev(xdot, torch)
+    dtg = torch.tensor([dt], dtype=torch.float64, device="cuda")
+    JUo, Jo, xo = JU, J, x
+    for _ in range(10):
+        ctx.es_rk_step(JUg, Jg, xg, xdg, dtg)
+        JUo, Jo, xo = o.rk_step(JUo, Jo, xo, xdot, dt)
+    e = fieldwise(JUg.cpu().numpy(), JUo) + [rel_max_err(Jg.cpu().numpy(), Jo), rel_max_err(xg.cpu().numpy(), xo)]
+    assert max(e) <= TOL_FP64, e
+
+
+@pytest.mark.parametrize("d,N", CASES)
+def test_rk_step_small(d, N):
+    torch = need_gpu()
+    pb, JU, J, x, xdot = case(d, N, GRIDS[d], "mixed", es=True, seed=3)
+    o = Oracle(pb)
+    dt = 0.3 * o.cfl_dt(JU, J, x)
+    ctx = _ctx(pb)
+    JUg, Jg, xg = to_dev(JU, torch), to_dev(J, torch), to_dev(x, torch)
+    ctx.es_rk_step(JUg, Jg, xg, to_dev(xdot, torch), torch.tensor([dt], dtype=torch.float64, device="cuda"))
+    JUo, Jo, xo = o.rk_step(JU, J, x, xdot, dt)
+    e = fieldwise(JUg.cpu().numpy(), JUo) + [rel_max_err(Jg.cpu().numpy(), Jo), rel_max_err(xg.cpu().numpy(), xo)]
+    assert max(e) <= TOL_FP64, e
+
+
+@pytest.mark.parametrize("d,N", [(2, 1), (2, 2), (3, 1)])
+@pytest.mark.parametrize("bc", ["periodic", "mixed"])
+def test_mesh_redistribute(d, N, bc):
+    torch = need_gpu()
+    pb, JU, J, x, xdot = case(d, N, GRIDS[d], bc, seed=5, jump=True)
+    pb = pb.with_(mu=5, nf=3, sigma=(W.SIG_RHO, W.SIG_P), alpha=(100.0, 30.0))
+    o = Oracle(pb)
+    xd_o, dt_o, dtau_o = o.mesh_redistribute(JU, J, x)
+    ctx = _ctx(pb)
+    xd, dd = ctx.mesh_redistribute(to_dev(JU, torch), to_dev(J, torch), to_dev(x, torch))
+    dd = dd.cpu().numpy()
+    assert abs(dd[0] - dt_o) <= TOL_FP64 * dt_o
+    assert abs(dd[1] - dtau_o) <= TOL_FP64 * dtau_o
+    e = fieldwise(xd.cpu().numpy(), xd_o, floor=1e-12)
+    assert max(e) <= 1e-11, e
+
+
+@pytest.mark.parametrize("d,N", CASES)
+def test_entropy_production(d, N):
+    torch = need_gpu()
+    pb, JU, J, x, xdot = case(d, N, GRIDS[d], "periodic", es=False, seed=9)
+    o = Oracle(pb)
+    dJU, dJ = o.rhs(JU, J, x, xdot)
+    P_o, S_o = o.entropy(JU, J, dJU, dJ)
+    ctx = _ctx(pb)
+    out = ctx.entropy_production(to_dev(JU, torch), to_dev(J, torch), to_dev(dJU, torch), to_dev(dJ, torch)).cpu().numpy()
+    scale = np.abs(dJU).sum() * np.prod(pb.dxi[:d])
+    assert abs(out[0] - P_o) <= 1e-12 * scale
+    assert abs(out[1] - S_o) <= 1e-12 * abs(S_o)
+    # the GPU residual itself conserves entropy (EC on periodic data)
+    dJUg, dJg = ctx.es_rhs(to_dev(JU, torch), to_dev(J, torch), to_dev(x, torch), to_dev(xdot, torch))
+    Pg = ctx.entropy_production(to_dev(JU, torch), to_dev(J, torch), dJUg, dJg).cpu().numpy()[0]
+    assert abs(Pg) <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("d,N", CASES)
+def test_mixed_precision_error(d, N):
+    """Mixed path (FP32 pairs / WENO-MR / monitor, FP64 metrics, GCL, divergence and RK):
+    residual error vs the FP64 oracle at FP32 level."""
+    torch = need_gpu()
+    pb, JU, J, x, xdot = case(d, N, GRIDS[d], "mixed", es=True, seed=11)
+    dJU_o, dJ_o = Oracle(pb).rhs(JU, J, x, xdot)
+    ctx = _ctx(pb, precision=1)
+    dJU, dJ = ctx.es_rhs(to_dev(JU, torch), to_dev(J, torch), to_dev(x, torch), to_dev(xdot, torch))
+    e = fieldwise(dJU.cpu().numpy(), dJU_o)
+    eJ = rel_max_err(dJ.cpu().numpy(), dJ_o)
+    print("mixed residual rel max errors", d, N, e, eJ)
+    assert eJ <= TOL_FP64
+    assert max(e) <= 2e-4, e
+
+
+def test_free_stream_fp64_and_mixed():
+    """Constant state on a perturbed moving mesh: FP64 keeps U to round-off after RK steps;
+    the mixed path keeps it to FP32 round-off."""
+    torch = need_gpu()
+    for prec, tol in [(0, 1e-12), (1, 1e-5)]:
+        pb, JU, J, x, xdot = case(2, 2, GRIDS[2], "periodic", es=True, seed=13)
+        U0 = W.cons_state(pb, [0.7, 0.4], [0.3, -0.2], 1.1)[: pb.nc]
+        U = np.broadcast_to(U0.reshape(-1, 1, 1, 1), JU.shape).copy()
+        ctx = _ctx(pb, prec)
+        JUg, Jg, xg = to_dev(U * J, torch), to_dev(J, torch), to_dev(x, torch)
+        dt = torch.tensor([0.2 * min(pb.dxi[:2])], dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            ctx.es_rk_step(JUg, Jg, xg, to_dev(xdot, torch), dt)
+        Ug = (JUg / Jg).cpu().numpy()
+        assert rel_max_err(Ug, U) <= tol
+
+
+def test_batched_equals_single():
+    """es_step_batch over uneven instances equals per-instance single calls, bit for bit."""
+    torch = need_gpu()
+    from paper_2202_07989_gb300 import es
+    insts = W.batched_2d(count=3, nmin=40, nmax=90, mu=3)
+    probs = [p for p, _, _ in insts]
+    o = [Oracle(p) for p in probs]
+    st = []
+    for (p, U, x), oo in zip(insts, o):
+        J = oo.init_J(x)
+        st.append((U * J, J, x))
+    for prec in (0, 1):
+        b = es.Context(probs, prec)
+        JU = [to_dev(s[0], torch) for s in st]
+        J = [to_dev(s[1], torch) for s in st]
+        X = [to_dev(s[2], torch) for s in st]
+        XD = [torch.zeros_like(t) for t in X]
+        DD = [torch.zeros(2, dtype=torch.float64, device="cuda") for _ in st]
+        b.es_bind_batch(JU, J, X, XD, DD)
+        for _ in range(2):
+            b.es_step_batch()
+        for i, p in enumerate(probs):
+            c = es.Context(p, prec)
+            ju, jj, xx = to_dev(st[i][0], torch), to_dev(st[i][1], torch), to_dev(st[i][2], torch)
+            for _ in range(2):
+                xd, dd = c.mesh_redistribute(ju, jj, xx)
+                c.es_rk_step(ju, jj, xx, xd, dd)
+            assert torch.equal(ju, JU[i]) and torch.equal(jj, J[i]) and torch.equal(xx, X[i])
+
+
+def test_full_step_shock_bubble_config():
+    """The 400 x 200 two-component shock-bubble instance (adaptive mesh, 5 sweeps): one full
+    step (mesh redistribution + SSP-RK3) on the GPU vs the oracle, FP64."""
+    torch = need_gpu()
+    pb, U, x = W.shock_bubble_2d(400, 200)
+    o = Oracle(pb)
+    J = o.init_J(x)
+    JU = U * J
+    xd_o, dt_o, dtau_o = o.mesh_redistribute(JU, J, x)
+    JUo, Jo, xo = o.rk_step(JU, J, x, xd_o, dt_o)
+    ctx = _ctx(pb)
+    JUg, Jg, xg = to_dev(JU, torch), to_dev(J, torch), to_dev(x, torch)
+    xd, dd = ctx.mesh_redistribute(JUg, Jg, xg)
+    ctx.es_rk_step(JUg, Jg, xg, xd, dd)
+    e = fieldwise(JUg.cpu().numpy(), JUo) + [rel_max_err(Jg.cpu().numpy(), Jo), rel_max_err(xg.cpu().numpy(), xo)]
+    assert max(e) <= 1e-11, e
+
+
+def test_nonphysical_state_is_reported():
+    """A negative density planted on the host is reported through the status word; the
+    kernels finish and the context stays usable."""
+    torch = need_gpu()
+    pb, JU, J, x, xdot = case(2, 1, GRIDS[2], "periodic", seed=17)
+    JU = JU.copy()
+    JU[0, 0, 5, 5] = -1.0
+    ctx = _ctx(pb)
+    ctx.es_rhs(to_dev(JU, torch), to_dev(J, torch), to_dev(x, torch), to_dev(xdot, torch))
+    assert ctx.es_poll_status() & 1
+    assert ctx.es_poll_status() == 0
