@@ -21,6 +21,8 @@
  *  - mesh velocity is constant over a time step; the stage meshes come from
  *    the same SSP-RK3 combination as (JU, J);
  *  - CFL spectral radius (|n.v| + c) L / J at x^n, mesh velocity excluded;
+ *  - sign matrix Y: a jump [[W_m]] within 1e-12 of its round-off scale
+ *    ||r_m|| (||V_i|| + ||V_i+1||) has no sign (Y = 0), as an exactly zero jump;
  *  - initial Jacobian: determinant of the delta-derivative matrix.
  */
 #include "es_oracle.h"
@@ -30,6 +32,7 @@
 #include <string.h>
 
 #define MAXC 8   /* max conserved components (N + d + 1 <= 6) */
+#define OR_Y_ROUNDOFF 1.0e-12   /* sign band of [[W_m]] in the sign matrix Y (FP64) */
 
 /* ------------------------------------------------------------------------ */
 /* sizes and indexing                                                        */
@@ -672,7 +675,7 @@ static void rotate(const or_config* c, double Tv[3][3], const double* a, double*
 
 /* dissipation term of Eq. (HOstable) at the interface between u6[2] and u6[3];
  * G = (J xi_t, J xi_x1..xd) from the GCL flux at that interface. */
-static void dissipation(const or_config* c, double u6[6][MAXC], const double* G, double* D)
+static void dissipation(const or_config* c, double u6[6][MAXC], const double* G, double* D, double* margin)
 {
     int d = c->d, N = c->N, nc = or_nc(c);
     double L = 0.0, n[3];
@@ -699,6 +702,15 @@ static void dissipation(const or_config* c, double u6[6][MAXC], const double* G,
             W[j][m] = s;
         }
     }
+    /* round-off scale of [[W_m]]: ||r_m|| (||V_i|| + ||V_i+1||) (rotation invariant) */
+    double nv = 0.0;
+    {
+        double Vi[MAXC], Vr[MAXC], a = 0.0, b = 0.0;
+        or_entropy_vars(c, u6[2], Vi);
+        or_entropy_vars(c, u6[3], Vr);
+        for (int q = 0; q < nc; ++q) { a += Vi[q] * Vi[q]; b += Vr[q] * Vr[q]; }
+        nv = sqrt(a) + sqrt(b);
+    }
     double coef[MAXC];
     for (int m = 0; m < nc; ++m) {
         double wl[5] = { W[0][m], W[1][m], W[2][m], W[3][m], W[4][m] };
@@ -707,8 +719,20 @@ static void dissipation(const or_config* c, double u6[6][MAXC], const double* G,
         double Wplus = or_weno_mr(wr, c->chi, c->weno_eps);
         double jw = Wplus - Wminus, jump = W[3][m] - W[2][m];
         int sjw = (jw > 0) - (jw < 0), sj = (jump > 0) - (jump < 0);
-        double Y = (sjw * sj > 0) ? 1.0 : 0.0;
+        /* Y of Sec. 3.4: 1 when sign([[W_m]]^WENOMR) sign([[W_m]]) > 0.  A jump no larger
+         * than OR_Y_ROUNDOFF times its round-off scale has no reliable sign and counts as 0
+         * (zero jumps give Y = 0). */
+        double rn = 0.0;
+        for (int q = 0; q < nc; ++q) rn += R[q * nc + m] * R[q * nc + m];
+        double scale = sqrt(rn) * nv;
+        int sig = fabs(jump) > OR_Y_ROUNDOFF * scale;
+        double Y = (sig && sjw * sj > 0) ? 1.0 : 0.0;
         coef[m] = lam * Y * jw;
+        if (margin && scale > 0.0) {
+            /* distance of the decision from the round-off band, in decades */
+            double mg = fabs(log10(fabs(jump) / (OR_Y_ROUNDOFF * scale) + 1e-300));
+            if (mg < *margin) *margin = mg;
+        }
     }
     double Dh[MAXC];
     for (int q = 0; q < nc; ++q) {
@@ -721,8 +745,26 @@ static void dissipation(const or_config* c, double u6[6][MAXC], const double* G,
     for (int q = 0; q < nc; ++q) D[q] = -0.5 * Dr[q];
 }
 
+static void rhs_impl(const or_config* c, const double* JU, const double* J, const double* x,
+                     const double* xdot, double* dJU, double* dJ, double* node_margin);
+
 void or_rhs(const or_config* c, const double* JU, const double* J, const double* x,
             const double* xdot, double* dJU, double* dJ)
+{
+    rhs_impl(c, JU, J, x, xdot, dJU, dJ, NULL);
+}
+
+/* the residual plus, per node, the smallest relative magnitude |[[W_m]]| / (|W_m,i| + |W_m,i+1|)
+ * over the interfaces around the node: where it is at round-off level the sign matrix Y
+ * of Sec. 3.4 is decided by rounding (test diagnostics) */
+void or_rhs_margins(const or_config* c, const double* JU, const double* J, const double* x,
+                    const double* xdot, double* dJU, double* dJ, double* node_margin)
+{
+    rhs_impl(c, JU, J, x, xdot, dJU, dJ, node_margin);
+}
+
+static void rhs_impl(const or_config* c, const double* JU, const double* J, const double* x,
+                     const double* xdot, double* dJU, double* dJ, double* node_margin)
 {
     int d = c->d, nc = or_nc(c), w = c->w;
     long nn = or_ncell(c), np = or_npad(c);
@@ -737,6 +779,9 @@ void or_rhs(const or_config* c, const double* JU, const double* J, const double*
     if (n2 > nmax) nmax = n2;
     double* F = (double*)malloc(sizeof(double) * (size_t)(nmax + 1) * nc);
     double* G = (double*)malloc(sizeof(double) * (size_t)(nmax + 1));
+    double* Mg = (double*)malloc(sizeof(double) * (size_t)(nmax + 1));
+    if (node_margin)
+        for (long q = 0; q < nn; ++q) node_margin[q] = 1.0e300;
     for (int k = 0; k < d; ++k) {
         int nk = c->n[k];
         int lim[3] = { c->n[0], c->n[1], n2 };
@@ -765,9 +810,10 @@ void or_rhs(const or_config* c, const double* JU, const double* J, const double*
                                 for (int q = 0; q < nc; ++q) f[q] += alpha[m - 1] * pair[q];
                                 for (int q = 0; q <= d; ++q) g[q] += alpha[m - 1] * 0.5 * (m6[l][q] + m6[r][q]);
                             }
+                        Mg[i + 1] = 1.0e300;
                         if (c->es) {
                             double D[MAXC];
-                            dissipation(c, u6, g, D);
+                            dissipation(c, u6, g, D, node_margin ? &Mg[i + 1] : NULL);
                             for (int q = 0; q < nc; ++q) f[q] += D[q];
                         }
                         for (int q = 0; q < nc; ++q) F[(i + 1) * nc + q] = f[q];
@@ -780,11 +826,16 @@ void or_rhs(const or_config* c, const double* JU, const double* J, const double*
                         for (int q = 0; q < nc; ++q)
                             dJU[q * nn + li] -= (F[(i + 1) * nc + q] - F[i * nc + q]) / c->dxi[k];
                         dJ[li] -= (G[i + 1] - G[i]) / c->dxi[k];
+                        if (node_margin) {
+                            double mm = Mg[i + 1] < Mg[i] ? Mg[i + 1] : Mg[i];
+                            if (mm < node_margin[li]) node_margin[li] = mm;
+                        }
                     }
                 }
     }
     free(F);
     free(G);
+    free(Mg);
     free(M);
 }
 

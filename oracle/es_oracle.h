@@ -81,6 +81,11 @@ void   or_init_J(const or_config* c, const double* x, double* J);
 /* semi-discrete residual, Eqs. (semi_U), (semi_J) */
 void   or_rhs(const or_config* c, const double* JU, const double* J, const double* x,
               const double* xdot, double* dJU, double* dJ);
+/* the residual and, per node, the smallest distance (in decades) of a Y decision from the
+ * round-off band |[[W_m]]| = 1e-12 ||r_m|| (||V_i|| + ||V_i+1||) over its interfaces; near 0
+ * means that rounding can decide Y */
+void   or_rhs_margins(const or_config* c, const double* JU, const double* J, const double* x,
+                      const double* xdot, double* dJU, double* dJ, double* node_margin);
 /* one SSP-RK3 step on (JU, J, x) with a constant mesh velocity */
 void   or_rk_step(const or_config* c, double* JU, double* J, double* x, const double* xdot, double dt);
 

@@ -54,6 +54,7 @@ def lib():
             "or_init_J": (None, [cp, dp, dp]),
             "or_rhs": (None, [cp, dp, dp, dp, dp, dp, dp]),
             "or_rk_step": (None, [cp, dp, dp, dp, dp, C.c_double]),
+            "or_rhs_margins": (None, [cp, dp, dp, dp, dp, dp, dp, dp]),
             "or_cfl_dt": (C.c_double, [cp, dp, dp, dp]),
             "or_monitor": (None, [cp, dp, dp, dp]),
             "or_filter": (None, [cp, dp]),
@@ -202,6 +203,16 @@ class Oracle:
         self.L.or_rhs(C.byref(self.cfg), _p(self._grid(JU, pb.nc)), _p(self._grid(J, 1)),
                       _p(self._grid(x, pb.d)), _p(self._grid(xdot, pb.d)), _p(dJU), _p(dJ))
         return dJU, dJ
+
+    def rhs_margins(self, JU, J, x, xdot):
+        """Residual plus the per-node Y-decision margin in decades (see es_oracle.h)."""
+        pb = self.pb
+        dJU = np.zeros((pb.nc,) + pb.shape)
+        dJ = np.zeros(pb.shape)
+        mg = np.zeros(pb.shape)
+        self.L.or_rhs_margins(C.byref(self.cfg), _p(self._grid(JU, pb.nc)), _p(self._grid(J, 1)),
+                              _p(self._grid(x, pb.d)), _p(self._grid(xdot, pb.d)), _p(dJU), _p(dJ), _p(mg))
+        return dJU, dJ, mg
 
     def rk_step(self, JU, J, x, xdot, dt):
         pb = self.pb

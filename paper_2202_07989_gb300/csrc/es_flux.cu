@@ -97,6 +97,16 @@ struct Ar<float> {
     }
 };
 
+// Sign band of the sign matrix Y (Sec. 3.4): a jump [[W_m]] no larger than delta times
+// its round-off scale ||r_m|| (||V_i|| + ||V_i+1||) has no reliable sign and counts as
+// zero, like an exactly zero jump (Y = 0 keeps the ES sign property).
+template <typename R>
+struct YBand;
+template <>
+struct YBand<double> { static constexpr double value = 1.0e-12; };
+template <>
+struct YBand<float> { static constexpr double value = 1.0e-5; };
+
 // fifth-order multi-resolution WENO value at x_{j+1/2} from W_{j-2..j+2} (Appendix A);
 // beta_2, beta_3 are the closed forms printed there.
 template <typename R>
@@ -136,7 +146,8 @@ struct Lay {
     static constexpr int RHO = 0, LRHO = NS, V = 2 * NS, B = 2 * NS + D, LB = B + 1, X = LB + 1;
     static constexpr int NX = NS == 2 ? 5 : 0;   // p, rho, ln rho, R_mix, Gamma_mix
     static constexpr int VV = X + NX;            // entropy variables
-    static constexpr int MR = VV + NC;           // metrics J xi_k/t, J xi_k/x_j (compute type)
+    static constexpr int VN = VV + NC;           // ||V||_2
+    static constexpr int MR = VN + 1;            // metrics J xi_k/t, J xi_k/x_j (compute type)
     static constexpr int NF = MR + 1 + D;
 };
 
@@ -231,6 +242,12 @@ __global__ void __launch_bounds__(FLUX_TPB) flux_kernel(FluxLaunch L)
 #pragma unroll
             for (int m = 0; m < D; ++m) nr[(Y::VV + NS + m) * NN + node] = v[m] * beta;
             nr[(Y::VV + NS + D) * NN + node] = -beta;
+            {
+                R vn = R(0);
+#pragma unroll
+                for (int q = 0; q < NC; ++q) { R t = nr[(Y::VV + q) * NN + node]; vn += t * t; }
+                nr[Y::VN * NN + node] = Ar<R>::sq(vn);
+            }
             // metrics of direction k at this node (padded buffer covers g in [-3, n + 3))
             long long pid = plin(I, idx[0], idx[1], idx[2]);
             double m0 = P.M[(long long)(k * (D + 1)) * I.npad + pid];
@@ -379,6 +396,9 @@ __global__ void __launch_bounds__(FLUX_TPB) flux_kernel(FluxLaunch L)
                     e2 = R(0.5) * vv - (R(I.cv[1]) + R2 - Gb * R(I.cv[1])) * Tb * igm;
                 }
                 const R lam = Ar<R>::ab(R(Gt) + Ln * vh[0]) + Ln * cb;
+                // round-off band of [[W_m]]: delta ||r_m|| (||V_i|| + ||V_i+1||)
+                const R nvb = NR(Y::VN, 2) + NR(Y::VN, 3);
+                const R band2 = R(YBand<R>::value * YBand<R>::value) * nvb * nvb;
                 const R ch1 = R(I.chi[0]), ch2 = R(I.chi[1]), ch3 = R(I.chi[2]), eps = R(I.weno_eps);
                 R Fd[NC];
 #pragma unroll
@@ -441,7 +461,11 @@ __global__ void __launch_bounds__(FLUX_TPB) flux_kernel(FluxLaunch L)
                     R Wm = weno_mr<R>(wv[0], wv[1], wv[2], wv[3], wv[4], ch1, ch2, ch3, eps);
                     R Wp = weno_mr<R>(wv[5], wv[4], wv[3], wv[2], wv[1], ch1, ch2, ch3, eps);
                     R jw = Wp - Wm, jp = wv[3] - wv[2];
-                    if ((jw > R(0) && jp > R(0)) || (jw < R(0) && jp < R(0))) {
+                    R rn = R(0);
+#pragma unroll
+                    for (int q = 0; q < NC; ++q) rn += rc[q] * rc[q];
+                    const bool sig = jp * jp > band2 * rn;
+                    if (sig && ((jw > R(0) && jp > R(0)) || (jw < R(0) && jp < R(0)))) {
                         R cf = lam * jw;
 #pragma unroll
                         for (int q = 0; q < NC; ++q) Fd[q] += rc[q] * cf;
