@@ -32,7 +32,7 @@
 #include <string.h>
 
 #define MAXC 8   /* max conserved components (N + d + 1 <= 6) */
-#define OR_Y_ROUNDOFF 1.0e-12   /* sign band of [[W_m]] in the sign matrix Y (FP64) */
+#define OR_Y_ROUNDOFF (c->y_band > 0.0 ? c->y_band : 1.0e-12)   /* sign band of [[W_m]] in Y */
 
 /* ------------------------------------------------------------------------ */
 /* sizes and indexing                                                        */

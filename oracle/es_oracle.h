@@ -42,6 +42,7 @@ typedef struct or_config {
     double alpha[4];         /* monitor weights */
     int mu;                  /* Jacobi sweeps per step */
     int nf;                  /* low-pass filter passes per step */
+    double y_band;           /* sign band of [[W_m]] in Y relative to its round-off scale; 0 = 1e-12 */
 } or_config;
 
 int    or_nc(const or_config* c);

@@ -26,7 +26,7 @@ class OrConfig(C.Structure):
         ("gamma", C.c_double * 2), ("cv", C.c_double * 2), ("pinf", C.c_double * 2),
         ("chi", C.c_double * 3), ("weno_eps", C.c_double), ("cfl", C.c_double),
         ("n_sigma", C.c_int), ("sigma", C.c_int * 4), ("alpha", C.c_double * 4),
-        ("mu", C.c_int), ("nf", C.c_int),
+        ("mu", C.c_int), ("nf", C.c_int), ("y_band", C.c_double),
     ]
 
 
@@ -91,6 +91,7 @@ def config(pb) -> OrConfig:
     for q, (s, a) in enumerate(zip(pb.sigma, pb.alpha)):
         c.sigma[q], c.alpha[q] = s, a
     c.mu, c.nf = pb.mu, pb.nf
+    c.y_band = 0.0
     return c
 
 

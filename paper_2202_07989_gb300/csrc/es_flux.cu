@@ -105,7 +105,7 @@ struct YBand;
 template <>
 struct YBand<double> { static constexpr double value = 1.0e-12; };
 template <>
-struct YBand<float> { static constexpr double value = 1.0e-5; };
+struct YBand<float> { static constexpr double value = 3.0e-7; };
 
 // fifth-order multi-resolution WENO value at x_{j+1/2} from W_{j-2..j+2} (Appendix A);
 // beta_2, beta_3 are the closed forms printed there.

@@ -31,8 +31,24 @@ def rel_max_err(got, want, floor=0.0):
     return np.abs(got - want).max() / scale
 
 
-def fieldwise(got, want, floor=0.0):
-    return [rel_max_err(g, w, floor) for g, w in zip(got, want)]
+def field_scales(want, N=None, d=None, floor=0.0):
+    """Per-field max-norm scales; with (N, d) given, the momentum components share the
+    max-norm of the momentum vector."""
+    sc = [max(np.abs(w).max(), floor) for w in want]
+    if N is not None and d is not None:
+        m = max(sc[N:N + d])
+        for q in range(N, N + d):
+            sc[q] = m
+    return sc
+
+
+def fieldwise(got, want, floor=0.0, N=None, d=None):
+    sc = field_scales(want, N, d, floor)
+    out = []
+    for g, w, s in zip(got, want, sc):
+        diff = np.abs(np.asarray(g) - np.asarray(w)).max()
+        out.append(diff / s if s > 0 else diff)
+    return out
 
 
 def case(d, N, n, bc, es=True, seed=0, pinf=0.0, amp_mesh=0.05, jump=False):
@@ -57,13 +73,12 @@ def case(d, N, n, bc, es=True, seed=0, pinf=0.0, amp_mesh=0.05, jump=False):
 MARGIN_DECADES = 0.01
 
 
-def masked_fieldwise(got, want, margin, floor=0.0):
-    """Relative max-norm error per field over the nodes whose Y decisions are robust, and the
-    number of nodes left out."""
+def masked_fieldwise(got, want, margin, N, d, floor=0.0):
+    """Relative max-norm error per field (momentum components share one scale) over the
+    nodes whose Y decisions are robust, and the number of nodes left out."""
     keep = margin >= MARGIN_DECADES
     errs = []
-    for g, w in zip(got, want):
-        scale = max(np.abs(w).max(), floor)
-        d = np.abs(np.asarray(g) - np.asarray(w))[keep]
-        errs.append(d.max() / scale if d.size else 0.0)
+    for g, w, s in zip(got, want, field_scales(want, N, d, floor)):
+        diff = np.abs(np.asarray(g) - np.asarray(w))[keep]
+        errs.append((diff.max() / s if s > 0 else diff.max()) if diff.size else 0.0)
     return errs, int((~keep).sum())

@@ -48,7 +48,7 @@ def test_rhs_fp64(d, N, bc, es_):
     dJU_o, dJ_o, mg = Oracle(pb).rhs_margins(JU, J, x, xdot)
     ctx = _ctx(pb)
     dJU, dJ = ctx.es_rhs(to_dev(JU, torch), to_dev(J, torch), to_dev(x, torch), to_dev(xdot, torch))
-    e, skipped = masked_fieldwise(dJU.cpu().numpy(), dJU_o, mg)
+    e, skipped = masked_fieldwise(dJU.cpu().numpy(), dJU_o, mg, pb.N, pb.d)
     e.append(rel_max_err(dJ.cpu().numpy(), dJ_o))
     assert max(e) <= TOL_FP64, e
     assert skipped <= 0.01 * pb.ncell, skipped
@@ -63,7 +63,7 @@ def test_rhs_fp64_discontinuous(d, N):
     dJU_o, dJ_o, mg = Oracle(pb).rhs_margins(JU, J, x, xdot)
     ctx = _ctx(pb)
     dJU, dJ = ctx.es_rhs(to_dev(JU, torch), to_dev(J, torch), to_dev(x, torch), to_dev(xdot, torch))
-    e, skipped = masked_fieldwise(dJU.cpu().numpy(), dJU_o, mg)
+    e, skipped = masked_fieldwise(dJU.cpu().numpy(), dJU_o, mg, pb.N, pb.d)
     e.append(rel_max_err(dJ.cpu().numpy(), dJ_o))
     print("discontinuous", d, N, "errors", e, "nodes near the Y band", skipped)
     assert max(e) <= TOL_FP64, e
@@ -83,7 +83,7 @@ def test_rhs_shock_bubble_initial_state(n):
     dJU_o, dJ_o, mg = o.rhs_margins(JU, J, x, xd)
     ctx = _ctx(pb)
     dJU, dJ = ctx.es_rhs(to_dev(JU, torch), to_dev(J, torch), to_dev(x, torch), to_dev(xd, torch))
-    e, skipped = masked_fieldwise(dJU.cpu().numpy(), dJU_o, mg)
+    e, skipped = masked_fieldwise(dJU.cpu().numpy(), dJU_o, mg, pb.N, pb.d)
     e.append(rel_max_err(dJ.cpu().numpy(), dJ_o))
     assert max(e) <= TOL_FP64, e
     assert skipped == 0
@@ -91,7 +91,10 @@ def test_rhs_shock_bubble_initial_state(n):
 
 def test_rk_steps_vortex_config():
     """The 64 x 64 moving-mesh isentropic vortex (sixth-order EC + WENO-MR, SSP-RK3,
-    CFL 0.4): 10 steps on the GPU vs 10 oracle steps, FP64."""
+    CFL 0.4), FP64: every GPU step taken from the oracle's state matches the oracle's step
+    to 1e-12; over 10 free-running steps the GPU stays within 10x the distance the oracle
+    itself drifts from a run whose initial state is perturbed by 1e-15 (the scheme's
+    discrete WENO-MR / Y decisions amplify round-off by about 3x per step)."""
     torch = need_gpu()
     pb, U, x, xdot = W.vortex_2d(64)
     o = Oracle(pb)
@@ -99,15 +102,25 @@ def test_rk_steps_vortex_config():
     JU = U * J
     dt = o.cfl_dt(JU, J, x)
     ctx = _ctx(pb)
-    JUg, Jg, xg = to_dev(JU, torch), to_dev(J, torch), to_dev(x, torch)
     xdg = to_dev(xdot, torch)
     dtg = torch.tensor([dt], dtype=torch.float64, device="cuda")
-    JUo, Jo, xo = JU, J, x
+    S = (JU, J, x)
+    G = [to_dev(t, torch) for t in S]
+    rng = np.random.default_rng(1)
+    P = (JU * (1.0 + 1e-15 * rng.standard_normal(JU.shape)), J, x)
     for _ in range(10):
-        ctx.es_rk_step(JUg, Jg, xg, xdg, dtg)
-        JUo, Jo, xo = o.rk_step(JUo, Jo, xo, xdot, dt)
-    e = fieldwise(JUg.cpu().numpy(), JUo) + [rel_max_err(Jg.cpu().numpy(), Jo), rel_max_err(xg.cpu().numpy(), xo)]
-    assert max(e) <= TOL_FP64, e
+        H = [to_dev(t, torch) for t in S]
+        ctx.es_rk_step(H[0], H[1], H[2], xdg, dtg)
+        ctx.es_rk_step(G[0], G[1], G[2], xdg, dtg)
+        S_new = o.rk_step(*S, xdot, dt)
+        e = fieldwise(H[0].cpu().numpy(), S_new[0], N=1, d=2) + [rel_max_err(H[1].cpu().numpy(), S_new[1])]
+        assert max(e) <= TOL_FP64, e
+        S = S_new
+        P = o.rk_step(*P, xdot, dt)
+    drift = max(fieldwise(P[0], S[0], N=1, d=2))
+    free = max(fieldwise(G[0].cpu().numpy(), S[0], N=1, d=2))
+    print("vortex 10 steps: GPU vs oracle %.3e, oracle vs perturbed oracle %.3e" % (free, drift))
+    assert free <= 10 * drift + 1e-13
 
 
 @pytest.mark.parametrize("d,N", CASES)
@@ -120,7 +133,7 @@ def test_rk_step_small(d, N):
     JUg, Jg, xg = to_dev(JU, torch), to_dev(J, torch), to_dev(x, torch)
     ctx.es_rk_step(JUg, Jg, xg, to_dev(xdot, torch), torch.tensor([dt], dtype=torch.float64, device="cuda"))
     JUo, Jo, xo = o.rk_step(JU, J, x, xdot, dt)
-    e = fieldwise(JUg.cpu().numpy(), JUo) + [rel_max_err(Jg.cpu().numpy(), Jo), rel_max_err(xg.cpu().numpy(), xo)]
+    e = fieldwise(JUg.cpu().numpy(), JUo, N=N, d=d) + [rel_max_err(Jg.cpu().numpy(), Jo), rel_max_err(xg.cpu().numpy(), xo)]
     assert max(e) <= TOL_FP64, e
 
 
@@ -168,11 +181,14 @@ def test_mixed_precision_error(d, N):
     dJU_o, dJ_o = Oracle(pb).rhs(JU, J, x, xdot)
     ctx = _ctx(pb, precision=1)
     dJU, dJ = ctx.es_rhs(to_dev(JU, torch), to_dev(J, torch), to_dev(x, torch), to_dev(xdot, torch))
-    e = fieldwise(dJU.cpu().numpy(), dJU_o)
+    e = fieldwise(dJU.cpu().numpy(), dJU_o, N=N, d=d)
     eJ = rel_max_err(dJ.cpu().numpy(), dJ_o)
     print("mixed residual rel max errors", d, N, e, eJ)
+    # the GCL flux of J stays FP64; the FP32 pairs and WENO-MR, and the FP32 sign band
+    # (3e-7 of the round-off scale, which drops dissipation of jumps below it) give
+    # differences of a few 1e-6 of the residual's max-norm
     assert eJ <= TOL_FP64
-    assert max(e) <= 2e-4, e
+    assert max(e) <= 5e-5, e
 
 
 def test_free_stream_fp64_and_mixed():
@@ -236,8 +252,9 @@ def test_full_step_shock_bubble_config():
     JUg, Jg, xg = to_dev(JU, torch), to_dev(J, torch), to_dev(x, torch)
     xd, dd = ctx.mesh_redistribute(JUg, Jg, xg)
     ctx.es_rk_step(JUg, Jg, xg, xd, dd)
-    e = fieldwise(JUg.cpu().numpy(), JUo) + [rel_max_err(Jg.cpu().numpy(), Jo), rel_max_err(xg.cpu().numpy(), xo)]
+    e = fieldwise(JUg.cpu().numpy(), JUo, N=pb.N, d=pb.d) + [rel_max_err(Jg.cpu().numpy(), Jo), rel_max_err(xg.cpu().numpy(), xo)]
     assert max(e) <= 1e-11, e
+    assert np.isfinite(JUo).all()
 
 
 def test_nonphysical_state_is_reported():
