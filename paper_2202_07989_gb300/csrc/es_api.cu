@@ -704,3 +704,147 @@ es_status es_poll_status(es_ctx* c, int* flags, void* stream)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free entropy diagnostics (es_entropy_production_noalloc).
+//
+// For callers that may not allocate device memory: code that runs while a CUDA
+// graph is being captured (cudaMalloc is not capturable), runtimes that hand out
+// every byte of device memory from their own pool, and real-time loops where an
+// allocation may synchronise the device.  The per-tile partial sums that
+// entropy_production keeps in context scratch live here in one file-scope device
+// array of fixed size instead; no context is created.
+// ---------------------------------------------------------------------------
+
+#include <mutex>
+
+namespace {
+
+constexpr int NOALLOC_TPB = 256;
+constexpr int NOALLOC_MAX_TILES = 4096;      // tiles of 256 nodes: at most 1,048,576 nodes
+constexpr int NOALLOC_MAX_DEVICES = 64;
+
+// two doubles per tile: 64 KiB, held by every GPU that loads the library until exit
+static __device__ __align__(256) double g_noalloc_partial[2 * NOALLOC_MAX_TILES];
+
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+// device address of g_noalloc_partial on the current device, looked up once per device
+es_status noalloc_scratch(double** out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) return ES_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partial);
+        if (e != cudaSuccess || !p) {
+            fprintf(stderr, "es_entropy_production_noalloc: cudaGetSymbolAddress failed: %s\n", cudaGetErrorString(e));
+            return ES_ERR_CUDA;
+        }
+        g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return ES_OK;
+}
+
+// one tile of 256 nodes per block: V.dJU - phi dJ and J eta summed in the same fixed order
+// as the context's entropy reduction
+__global__ void noalloc_entropy_partial_kernel(Inst I, const double* __restrict__ JU, const double* __restrict__ J,
+                                               const double* __restrict__ dJU, const double* __restrict__ dJ,
+                                               double* __restrict__ partial)
+{
+    __shared__ double sh[2][32];
+    long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double a = 0.0, b = 0.0;
+    if (p < I.ncell) {
+        double Jp = J[p], U[MAXC];
+        for (int q = 0; q < I.nc; ++q) U[q] = JU[(long long)q * I.ncell + p] / Jp;
+        double rho = 0.0, cvr = 0.0, rr = 0.0;
+        for (int l = 0; l < I.N; ++l) { rho += U[l]; cvr += I.cv[l] * U[l]; rr += I.Rs[l] * U[l]; }
+        double v[3], v2 = 0.0;
+        for (int m = 0; m < I.d; ++m) { v[m] = U[I.N + m] / rho; v2 += v[m] * v[m]; }
+        double T = (U[I.N + I.d] - 0.5 * rho * v2 - I.pinf_tot) / cvr;
+        double eta = 0.0, phi = 0.0, lT = log(T), V[MAXC];
+        for (int l = 0; l < I.N; ++l) {
+            double S = I.cv[l] * lT - I.Rs[l] * log(U[l]);
+            V[l] = -S - v2 / (2.0 * T) + I.cvG[l];
+            eta -= U[l] * S;
+            phi += I.Rs[l] * U[l] - I.pinf[l] / T;
+        }
+        for (int m = 0; m < I.d; ++m) V[I.N + m] = v[m] / T;
+        V[I.N + I.d] = -1.0 / T;
+        if (dJU && dJ) {
+            for (int q = 0; q < I.nc; ++q) a += V[q] * dJU[(long long)q * I.ncell + p];
+            a -= phi * dJ[p];
+        }
+        b = Jp * eta;
+    }
+    for (int o = 16; o > 0; o >>= 1) { a += __shfl_xor_sync(0xffffffffu, a, o); b += __shfl_xor_sync(0xffffffffu, b, o); }
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { sh[0][wid] = a; sh[1][wid] = b; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sa = 0.0, sb = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { sa += sh[0][q]; sb += sh[1][q]; }
+        partial[2 * (long long)blockIdx.x] = sa;
+        partial[2 * (long long)blockIdx.x + 1] = sb;
+    }
+}
+
+__global__ void noalloc_entropy_final_kernel(Inst I, int ntiles, const double* __restrict__ partial,
+                                             double* __restrict__ out)
+{
+    __shared__ double sh[2][32];
+    double a = 0.0, b = 0.0;
+    for (int w = threadIdx.x; w < ntiles; w += blockDim.x) { a += partial[2 * w]; b += partial[2 * w + 1]; }
+    for (int o = 16; o > 0; o >>= 1) { a += __shfl_xor_sync(0xffffffffu, a, o); b += __shfl_xor_sync(0xffffffffu, b, o); }
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { sh[0][wid] = a; sh[1][wid] = b; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sa = 0.0, sb = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { sa += sh[0][q]; sb += sh[1][q]; }
+        double vol = 1.0;
+        for (int k = 0; k < I.d; ++k) vol *= I.dxi[k];
+        out[0] = vol * sa;
+        out[1] = vol * sb;
+    }
+}
+
+}  // namespace
+
+extern "C" es_status es_entropy_production_noalloc(const es_config* cfg, const double* JU, const double* J,
+                                                   const double* dJU, const double* dJ, double* out2, void* stream)
+{
+    if (!cfg || !JU || !J || !out2) {
+        fprintf(stderr, "es_entropy_production_noalloc: null pointer\n");
+        return ES_ERR_ARG;
+    }
+    std::string m = check_cfg(*cfg);
+    if (!m.empty()) {
+        fprintf(stderr, "es_entropy_production_noalloc: %s\n", m.c_str());
+        return ES_ERR_ARG;
+    }
+    Inst I = make_inst(*cfg);
+    long long ntiles = (I.ncell + NOALLOC_TPB - 1) / NOALLOC_TPB;
+    if (ntiles > NOALLOC_MAX_TILES) {
+        fprintf(stderr, "es_entropy_production_noalloc: %lld nodes exceed the limit of %d nodes of the "
+                        "allocation-free call (use entropy_production with a context)\n",
+                I.ncell, NOALLOC_MAX_TILES * NOALLOC_TPB);
+        return ES_ERR_ARG;
+    }
+    double* partial = nullptr;
+    es_status s = noalloc_scratch(&partial);
+    if (s != ES_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    noalloc_entropy_partial_kernel<<<(int)ntiles, NOALLOC_TPB, 0, st>>>(I, JU, J, dJU, dJ, partial);
+    noalloc_entropy_final_kernel<<<1, NOALLOC_TPB, 0, st>>>(I, (int)ntiles, partial, out2);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        fprintf(stderr, "es_entropy_production_noalloc: %s\n", cudaGetErrorString(e));
+        return ES_ERR_CUDA;
+    }
+    return ES_OK;
+}

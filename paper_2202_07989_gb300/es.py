@@ -70,6 +70,7 @@ def lib():
             "es_run_host": (C.c_int, [vp, dp, dp, dp, C.c_int, C.c_double, C.POINTER(C.c_double), vp]),
             "es_poll_status": (C.c_int, [vp, ip, vp]),
             "es_profile": (C.c_int, [vp, C.c_int]),
+            "es_entropy_production_noalloc": (C.c_int, [C.POINTER(EsConfig), dp, dp, dp, dp, dp, vp]),
             "es_profile_read": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.c_int]),
         }
         for name, (res, args) in sig.items():
@@ -280,3 +281,17 @@ def es_create(pb: Problem, precision: int = FP64) -> Context:
 
 def es_create_batch(problems: Sequence[Problem], precision: int = FP64) -> Context:
     return Context(list(problems), precision)
+
+
+def es_entropy_production_noalloc(pb: Problem, JU, J, dJU, dJ, out2, precision: int = FP64) -> int:
+    """Allocation-free entropy diagnostics (no context, no device allocation): for callers
+    that may not allocate device memory, e.g. while capturing a CUDA graph or inside a
+    runtime that owns all device memory.  out2 (2 float64 on the device) is filled with
+    {P, S}; returns the es_status code (0 on success).  Grids over 1,048,576 nodes are
+    rejected (ES_ERR_ARG)."""
+    if not (out2.is_cuda and out2.dtype == torch.float64 and out2.numel() >= 2 and out2.is_contiguous()):
+        raise EsError("out2 must be a contiguous float64 CUDA tensor of 2 entries")
+    cfg = make_config(pb, precision)
+    return lib().es_entropy_production_noalloc(C.byref(cfg), _ptr(JU, pb.nc, pb, "JU"), _ptr(J, 1, pb, "J"),
+                                                _ptr(dJU, pb.nc, pb, "dJU"), _ptr(dJ, 1, pb, "dJ"),
+                                                C.c_void_p(out2.data_ptr()), _stream())
