@@ -472,6 +472,22 @@ def main_reference(args):
     print(json.dumps(line))
 
 
+def main_kernel_case(args):
+    """A few eager full steps of the shock-bubble instance at the given size (for ncu captures)."""
+    import torch
+    from paper_2202_07989_gb300 import build as B
+    B.build()
+    from paper_2202_07989_gb300 import es, workloads as W
+    nx, ny = [int(v) for v in args.kernel_case.split("x")]
+    pb, U, x = W.shock_bubble_2d(nx, ny, length=(2.0, 1.0))
+    r = Single(pb, U, x, es.MIXED if args.kernel_form == "mixed" else es.FP64, torch)
+    for _ in range(args.kernel_steps):
+        r.step()
+    torch.cuda.synchronize()
+    assert r.ctx.es_poll_status() == 0
+    print("kernel case %s %s: %d steps done" % (args.kernel_case, args.kernel_form, args.kernel_steps))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -481,7 +497,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--kernel-case", default=None, help="NXxNY: only run a few steps of that grid (profiling)")
+    ap.add_argument("--kernel-form", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--kernel-steps", type=int, default=2)
     args = ap.parse_args()
+    if args.kernel_case:
+        return main_kernel_case(args)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
