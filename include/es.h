@@ -192,6 +192,13 @@ es_status es_run_host(es_ctx* ctx, double* JU, double* J, double* x, int steps, 
 es_status es_profile(es_ctx* ctx, int enable);
 es_status es_profile_read(es_ctx* ctx, double* ms, long long* launches, int n_classes);
 
+/* Self-check of the IEEE 754 binary64 <-> binary32 conversions the mixed form
+ * does with integer instructions (GB300 issues the hardware conversions on its
+ * FP64 pipe): out32[i] = round-to-nearest-even binary32 of in[i] (values below
+ * 2^-126 in magnitude become a signed zero) and out64[i] = out32[i] widened
+ * exactly.  in, out32, out64: DEVICE arrays of n elements. */
+es_status es_check_conversions(const double* in, int n, float* out32, double* out64, void* stream);
+
 /* Reads and clears the sticky device status (synchronises the stream):
  * *flags = bit 0 non-physical state, bit 1 timeout. */
 es_status es_poll_status(es_ctx* ctx, int* flags, void* stream);

@@ -646,6 +646,14 @@ es_status es_run_host(es_ctx* c, double* JU, double* J, double* x, int steps, do
     return cuda_check(c, "es_run_host");
 }
 
+es_status es_check_conversions(const double* in, int n, float* out32, double* out64, void* stream)
+{
+    if (!in || !out32 || !out64 || n < 0) return ES_ERR_ARG;
+    if (n == 0) return ES_OK;
+    conversion_check_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(in, n, out32, out64);
+    return cudaGetLastError() == cudaSuccess ? ES_OK : ES_ERR_CUDA;
+}
+
 es_status es_profile(es_ctx* c, int enable)
 {
     if (!c) return ES_ERR_ARG;

@@ -189,6 +189,49 @@ __device__ inline void load_U(const Inst& I, const double* __restrict__ JU, cons
     if (neg >= 0) U[I.N + neg] = -U[I.N + neg];
 }
 
+// IEEE 754 binary64 -> binary32 with round-to-nearest-even, done with integer
+// instructions (the hardware conversion issues on the FP64 pipe, which GB300 runs at
+// 1/64 of the FP32 rate).  Values below 2^-126 in magnitude become a signed zero;
+// values of 2^128 and above, infinities and NaN take the hardware conversion.
+__device__ __forceinline__ float f64_to_f32(double x)
+{
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    unsigned int hi = (unsigned int)(b >> 32);
+    int e = (int)((hi >> 20) & 0x7ffu);
+    unsigned int sign = hi & 0x80000000u;
+    if (e < 1023 - 126) return __int_as_float((int)sign);
+    if (e > 1023 + 127) return __double2float_rn(x);
+    unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
+    unsigned int m = (unsigned int)(mant >> 29);
+    unsigned int rem = (unsigned int)(mant & 0x1FFFFFFFull);
+    unsigned int f = sign | ((unsigned int)(e - 1023 + 127) << 23) | m;
+    f += (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;
+    return __int_as_float((int)f);
+}
+
+// IEEE 754 binary32 -> binary64 (exact), with integer instructions; zero keeps its sign,
+// subnormals, infinities and NaN take the hardware conversion
+__device__ __forceinline__ double f32_to_f64(float f)
+{
+    unsigned int b = (unsigned int)__float_as_int(f);
+    unsigned int e = (b >> 23) & 0xffu;
+    unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+    if ((b & 0x7fffffffu) == 0u) return __longlong_as_double((long long)sign);
+    if (e == 0u || e == 0xffu) return (double)f;
+    unsigned long long d = sign | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(b & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)d);
+}
+
+template <typename R>
+__device__ __forceinline__ R to_r(double x);
+template <>
+__device__ __forceinline__ double to_r<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float to_r<float>(double x) { return f64_to_f32(x); }
+
+__device__ __forceinline__ double to_d(double x) { return x; }
+__device__ __forceinline__ double to_d(float x) { return f32_to_f64(x); }
+
 // bounded reductions of non-negative doubles: the IEEE order of non-negative
 // doubles is the order of their bit patterns
 __device__ inline void atomic_max_pos(double* a, double v)

@@ -74,15 +74,15 @@ struct Ar<float> {
     static __device__ __forceinline__ double small_branch(float a, float b, float u)
     {
         float del = u * (1.f / 3.f + u * (4.f / 45.f + u * (44.f / 945.f + u * (428.f / 14175.f))));
-        double hs = 0.5 * ((double)a + (double)b);
-        return fma(-hs, (double)del, hs);
+        double hs = f32_to_f64(0.5f * a) + f32_to_f64(0.5f * b);   // {a}, exact
+        return fma(-hs, f32_to_f64(del), hs);
     }
     static __device__ __forceinline__ float lmean(float a, float b, float la, float lb)
     {
         float s = a + b, dd = b - a;
         if (fabsf(dd) < 0.1f * s) {
             float f = __fdividef(dd, s);
-            return (float)small_branch(a, b, f * f);
+            return f64_to_f32(small_branch(a, b, f * f));
         }
         return __fdividef(dd, lb - la);
     }
@@ -91,7 +91,7 @@ struct Ar<float> {
         float dd = b - a;
         if (fabsf(dd) < 0.1f * (a + b)) {
             float f = dd * is;
-            return __frcp_rn((float)small_branch(a, b, f * f));
+            return __frcp_rn(f64_to_f32(small_branch(a, b, f * f)));
         }
         return __fdividef(lb - la, dd);
     }
@@ -153,19 +153,48 @@ struct Lay {
 
 template <int S, int WT>
 struct Tile {
-    static constexpr int NN = (S + 6) * WT;
-    static constexpr int NI = (S + 1) * WT;
+    static constexpr int NN = (S + 6) * WT;   // staged nodes (3 halo nodes per side)
+    static constexpr int NI = (S + 1) * WT;   // interfaces
+    static constexpr int NPL = 3 * S + 6;     // distinct node pairs (j, j+m), m = 1..3, per line
+    static constexpr int NP = NPL * WT;
 };
 
+// conserved point state at a node reached along line direction k, in the compute type
+template <typename R>
+__device__ __forceinline__ void load_U_r(const Inst& I, const double* __restrict__ JU, const double* __restrict__ J,
+                                         int k, const int* idx_in, R* U)
+{
+    int idx[3] = { idx_in[0], idx_in[1], idx_in[2] };
+    int gi, side;
+    int t = map_line(I, k, idx[k], gi, side);
+    if (t == 2) {
+        for (int q = 0; q < I.nc; ++q) U[q] = to_r<R>(I.inflow[k][side][q]);
+        return;
+    }
+    idx[k] = gi;
+    long long id = lin(I, idx[0], idx[1], I.d == 3 ? idx[2] : 0);
+    R inv = Ar<R>::rcp(to_r<R>(J[id]));
+    for (int q = 0; q < I.nc; ++q) U[q] = to_r<R>(JU[q * I.ncell + id]) * inv;
+    if (t == 1) U[I.N + k] = -U[I.N + k];
+}
+
+// Phases of one tile: (1) node states, entropy variables and metrics into shared memory;
+// (2) every distinct two-point flux F(U_j, U_{j+m}) (m = 1, 2, 3) of the tile, once; (3)
+// per interface the 2w-order EC flux as sum_m alpha_m sum_s of the stored pairs, the GCL
+// flux of J xi_k/t and the ES dissipation; (4) divergence and output / RK stage.
 template <int D, int NS, typename R, int S, int WT>
 __global__ void __launch_bounds__(FLUX_TPB) flux_kernel(FluxLaunch L)
 {
     using Y = Lay<D, NS>;
-    constexpr int NC = Y::NC, NN = Tile<S, WT>::NN, NI = Tile<S, WT>::NI, NF = Y::NF;
+    using TL = Tile<S, WT>;
+    constexpr int NC = Y::NC, NN = TL::NN, NI = TL::NI, NF = Y::NF, NPL = TL::NPL, NP = TL::NP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double* fl = reinterpret_cast<double*>(smem_raw);        // [NC + 1][NI]
-    double* mt64 = fl + (NC + 1) * NI;                          // [NN]
-    R* nr = reinterpret_cast<R*>(mt64 + NN);                    // [NF][NN]
+    double* gt = reinterpret_cast<double*>(smem_raw);           // [NI] GCL flux of J xi_k/t
+    double* mt64 = gt + NI;                                      // [NN] J xi_k/t at the nodes
+    R* nr = reinterpret_cast<R*>(mt64 + NN);                     // [NF][NN] node data
+    R* pf = nr + NF * NN;                                        // [NC][NP] pair fluxes
+    R* cm = pf + NC * NP;                                        // [NS + 1][NI] centre-pair means
+    R* fl = cm + (NS + 1) * NI;                                  // [NC][NI] interface fluxes
     const int k = L.k;
     const int adim = k == 0 ? 1 : 0, bdim = k == 2 ? 1 : 2;
 
@@ -173,7 +202,7 @@ __global__ void __launch_bounds__(FLUX_TPB) flux_kernel(FluxLaunch L)
         const int2 it = L.work[wi];
         const Inst& I = L.insts[it.x];
         const StagePtrs P = L.ptrs ? L.ptrs[it.x] : L.single;
-        const int nk = I.n[k], na = I.n[adim], nb = (bdim < D) ? I.n[bdim] : 1;
+        const int nk = I.n[k], na = I.n[adim];
         const int ns = (nk + S - 1) / S, nat = (na + WT - 1) / WT;
         const int ts = it.y % ns, ta = (it.y / ns) % nat, tb = it.y / (ns * nat);
         const int s0 = ts * S, a0 = ta * WT;
@@ -188,7 +217,6 @@ __global__ void __launch_bounds__(FLUX_TPB) flux_kernel(FluxLaunch L)
             const int node = w * (S + 6) + s;
             const int g = s0 - 3 + s, a = a0 + w;
             if (a >= na || g > nk + 2) {
-                // outside the grid: benign values, never read by a valid interface
                 for (int f = 0; f < NF; ++f) nr[f * NN + node] = R(1);
                 mt64[node] = 0.0;
                 continue;
@@ -197,12 +225,8 @@ __global__ void __launch_bounds__(FLUX_TPB) flux_kernel(FluxLaunch L)
             idx[k] = g;
             idx[adim] = a;
             if (bdim < D) idx[bdim] = tb;
-            double Ud[MAXC];
-            load_U(I, P.JU, P.J, idx[0], idx[1], idx[2], Ud);
-            // primitives: T = (E - rho|v|^2/2 - p_inf) / sum cv_l rho_l, p = sum rho_l R_l T - p_inf
             R U[MAXC];
-#pragma unroll
-            for (int q = 0; q < NC; ++q) U[q] = (R)Ud[q];
+            load_U_r<R>(I, P.JU, P.J, k, idx, U);
             R rho = U[0] + (NS == 2 ? U[1] : R(0));
             R irho = Ar<R>::rcp(rho);
             R v[D], v2 = R(0);
@@ -237,92 +261,95 @@ __global__ void __launch_bounds__(FLUX_TPB) flux_kernel(FluxLaunch L)
             }
             // entropy variables V_l = c_{v,l} ln beta + R_l ln rho_l - |v|^2 beta/2 + c_{v,l} Gamma_l
             R hv = R(0.5) * v2 * beta;
-            nr[(Y::VV + 0) * NN + node] = R(I.cv[0]) * lb + R(I.Rs[0]) * lr0 - hv + R(I.cvG[0]);
-            if (NS == 2) nr[(Y::VV + 1) * NN + node] = R(I.cv[1]) * lb + R(I.Rs[1]) * lr1 - hv + R(I.cvG[1]);
+            R Vn[NC];
+            Vn[0] = R(I.cv[0]) * lb + R(I.Rs[0]) * lr0 - hv + R(I.cvG[0]);
+            if (NS == 2) Vn[1] = R(I.cv[1]) * lb + R(I.Rs[1]) * lr1 - hv + R(I.cvG[1]);
 #pragma unroll
-            for (int m = 0; m < D; ++m) nr[(Y::VV + NS + m) * NN + node] = v[m] * beta;
-            nr[(Y::VV + NS + D) * NN + node] = -beta;
-            {
-                R vn = R(0);
+            for (int m = 0; m < D; ++m) Vn[NS + m] = v[m] * beta;
+            Vn[NS + D] = -beta;
+            R vn = R(0);
 #pragma unroll
-                for (int q = 0; q < NC; ++q) { R t = nr[(Y::VV + q) * NN + node]; vn += t * t; }
-                nr[Y::VN * NN + node] = Ar<R>::sq(vn);
-            }
-            // metrics of direction k at this node (padded buffer covers g in [-3, n + 3))
+            for (int q = 0; q < NC; ++q) { nr[(Y::VV + q) * NN + node] = Vn[q]; vn += Vn[q] * Vn[q]; }
+            nr[Y::VN * NN + node] = Ar<R>::sq(vn);
+            // metrics of direction k at this node (the padded buffer covers g in [-3, n + 3))
             long long pid = plin(I, idx[0], idx[1], idx[2]);
             double m0 = P.M[(long long)(k * (D + 1)) * I.npad + pid];
             mt64[node] = m0;
-            nr[Y::MR * NN + node] = (R)m0;
+            nr[Y::MR * NN + node] = to_r<R>(m0);
 #pragma unroll
-            for (int j = 0; j < D; ++j) nr[(Y::MR + 1 + j) * NN + node] = (R)P.M[(long long)(k * (D + 1) + 1 + j) * I.npad + pid];
+            for (int j = 0; j < D; ++j) nr[(Y::MR + 1 + j) * NN + node] = to_r<R>(P.M[(long long)(k * (D + 1) + 1 + j) * I.npad + pid]);
         }
         __syncthreads();
 
-        // ---------------- phase 2: interface fluxes ----------------
+        // ---------------- phase 2: distinct two-point EC fluxes ----------------
+        for (int t = threadIdx.x; t < NP; t += blockDim.x) {
+            const int w = t / NPL, r_ = t % NPL;
+            int m, Ln;
+            if (r_ < S + 1) { m = 1; Ln = r_ + 2; }
+            else if (r_ < 2 * S + 3) { m = 2; Ln = r_ - (S + 1) + 1; }
+            else { m = 3; Ln = r_ - (2 * S + 3); }
+            if (a0 + w >= na || s0 - 3 + Ln + m > nk + 2) continue;
+            const int l = w * (S + 6) + Ln, rr = l + m;
+            R mt = R(0.5) * (nr[Y::MR * NN + l] + nr[Y::MR * NN + rr]);
+            R mx[D], vb[D];
+            R ut = mt, v2b = R(0), vbsq = R(0);
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                mx[j] = R(0.5) * (nr[(Y::MR + 1 + j) * NN + l] + nr[(Y::MR + 1 + j) * NN + rr]);
+                R vl = nr[(Y::V + j) * NN + l], vr = nr[(Y::V + j) * NN + rr];
+                vb[j] = R(0.5) * (vl + vr);
+                v2b += R(0.5) * (vl * vl + vr * vr);
+                vbsq += vb[j] * vb[j];
+                ut += mx[j] * vb[j];
+            }
+            R lr[NS], rt = R(0), rra = R(0);
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                R al = nr[(Y::RHO + q) * NN + l], ar = nr[(Y::RHO + q) * NN + rr];
+                lr[q] = Ar<R>::lmean(al, ar, nr[(Y::LRHO + q) * NN + l], nr[(Y::LRHO + q) * NN + rr]);
+                rt += lr[q];
+                rra += R(I.Rs[q]) * (al + ar);
+            }
+            R bl = nr[Y::B * NN + l], br = nr[Y::B * NN + rr];
+            R is = Ar<R>::rcp(bl + br);
+            R ilb = Ar<R>::inv_lmean(bl, br, nr[Y::LB * NN + l], nr[Y::LB * NN + rr], is);
+            R Pp = rra * is;                                   // sum R_l {rho_l} / {beta}
+            R Ep = -R(0.5) * rt * v2b + rt * vbsq;
+#pragma unroll
+            for (int q = 0; q < NS; ++q) Ep += lr[q] * R(I.cv[q]) * ilb;
+#pragma unroll
+            for (int q = 0; q < NS; ++q) pf[q * NP + t] = ut * lr[q];
+#pragma unroll
+            for (int j = 0; j < D; ++j) pf[(NS + j) * NP + t] = ut * rt * vb[j] + mx[j] * Pp;
+            pf[(NS + D) * NP + t] = ut * Ep + (ut - mt) * Pp;
+            if (m == 1) {
+                const int ci = w * (S + 1) + (Ln - 2);
+#pragma unroll
+                for (int q = 0; q < NS; ++q) cm[q * NI + ci] = lr[q];
+                cm[NS * NI + ci] = ilb;
+            }
+        }
+        __syncthreads();
+
+        // ---------------- phase 3: interface fluxes ----------------
         for (int f = threadIdx.x; f < NI; f += blockDim.x) {
             const int s = f % (S + 1), w = f / (S + 1);
             const int gi = s0 - 1 + s;     // interface gi + 1/2
             if (a0 + w >= na || gi > nk - 1) continue;
             const int base = w * (S + 6) + s;   // node gi - 2
 #define NR(fld, j) nr[(fld) * NN + base + (j)]
+            const int p1 = w * NPL + s, p2 = w * NPL + (S + 1) + s, p3 = w * NPL + (2 * S + 3) + s;
+            const R a1 = R(alpha3(1)), a2 = R(alpha3(2)), a3 = R(alpha3(3));
             R Fe[NC];
 #pragma unroll
-            for (int q = 0; q < NC; ++q) Fe[q] = R(0);
-            // means of the centre pair (i, i+1), reused by the dissipation
-            R lr_c[NS], ilb_c = R(0);
-#pragma unroll
-            for (int m = 1; m <= 3; ++m) {
-#pragma unroll
-                for (int ss = 0; ss < m; ++ss) {
-                    const int l = 2 - ss, r = 2 - ss + m;
-                    const R am = R(alpha3(m));
-                    R mt = R(0.5) * (NR(Y::MR, l) + NR(Y::MR, r));
-                    R mx[D], vb[D];
-                    R ut = mt, v2b = R(0), vbsq = R(0);
-#pragma unroll
-                    for (int j = 0; j < D; ++j) {
-                        mx[j] = R(0.5) * (NR(Y::MR + 1 + j, l) + NR(Y::MR + 1 + j, r));
-                        R vl = NR(Y::V + j, l), vr = NR(Y::V + j, r);
-                        vb[j] = R(0.5) * (vl + vr);
-                        v2b += R(0.5) * (vl * vl + vr * vr);
-                        vbsq += vb[j] * vb[j];
-                        ut += mx[j] * vb[j];
-                    }
-                    R lr[NS], rt = R(0), rra = R(0);
-#pragma unroll
-                    for (int q = 0; q < NS; ++q) {
-                        R al = NR(Y::RHO + q, l), ar = NR(Y::RHO + q, r);
-                        lr[q] = Ar<R>::lmean(al, ar, NR(Y::LRHO + q, l), NR(Y::LRHO + q, r));
-                        rt += lr[q];
-                        rra += R(I.Rs[q]) * (al + ar);
-                    }
-                    R bl = NR(Y::B, l), br = NR(Y::B, r);
-                    R is = Ar<R>::rcp(bl + br);
-                    R ilb = Ar<R>::inv_lmean(bl, br, NR(Y::LB, l), NR(Y::LB, r), is);
-                    R Pp = rra * is;                                   // sum R_l {rho_l} / {beta}
-                    R Ep = -R(0.5) * rt * v2b + rt * vbsq;
-#pragma unroll
-                    for (int q = 0; q < NS; ++q) Ep += lr[q] * R(I.cv[q]) * ilb;
-                    R aut = am * ut;
-#pragma unroll
-                    for (int q = 0; q < NS; ++q) Fe[q] += aut * lr[q];
-#pragma unroll
-                    for (int j = 0; j < D; ++j) Fe[NS + j] += aut * rt * vb[j] + am * mx[j] * Pp;
-                    Fe[NS + D] += aut * Ep + am * (ut - mt) * Pp;
-                    if (m == 1) {
-#pragma unroll
-                        for (int q = 0; q < NS; ++q) lr_c[q] = lr[q];
-                        ilb_c = ilb;
-                    }
-                }
+            for (int q = 0; q < NC; ++q) {
+                const R* pq = pf + q * NP;
+                Fe[q] = a1 * pq[p1] + a2 * (pq[p2] + pq[p2 + 1]) + a3 * (pq[p3] + pq[p3 + 1] + pq[p3 + 2]);
             }
             // GCL flux of (J xi_k/t, J xi_k/x_j): stencil (1, -8, 37, 37, -8, 1)/60
             const double c0 = 0.5 * (alpha3(1) + alpha3(2) + alpha3(3)), c1 = 0.5 * (alpha3(2) + alpha3(3)), c2 = 0.5 * alpha3(3);
             const double* m64 = mt64 + base;
-            double Gt = c0 * (m64[2] + m64[3]) + c1 * (m64[1] + m64[4]) + c2 * (m64[0] + m64[5]);
-            double Fd_out[NC];
-#pragma unroll
-            for (int q = 0; q < NC; ++q) Fd_out[q] = 0.0;
+            const double Gt = c0 * (m64[2] + m64[3]) + c1 * (m64[1] + m64[4]) + c2 * (m64[0] + m64[5]);
             if (I.es) {
                 R Gx[D], L2 = R(0);
 #pragma unroll
@@ -350,7 +377,11 @@ __global__ void __launch_bounds__(FLUX_TPB) flux_kernel(FluxLaunch L)
                     T[1][0] = -st; T[1][1] = ct; T[1][D - 1] = R(0);
                     T[D - 1][0] = -sp * ct; T[D - 1][1] = -sp * st; T[D - 1][D - 1] = cp;
                 }
-                // interface averages (Sec. 3.4)
+                // interface averages (Sec. 3.4); the log means of the centre pair come from phase 2
+                R lr_c[NS];
+#pragma unroll
+                for (int q = 0; q < NS; ++q) lr_c[q] = cm[q * NI + f];
+                const R Tb = cm[NS * NI + f];       // T-bar = 1 / {beta}^ln
                 R vb[D], vh[D], vv = R(0);
 #pragma unroll
                 for (int j = 0; j < D; ++j) { vb[j] = R(0.5) * (NR(Y::V + j, 2) + NR(Y::V + j, 3)); vv += vb[j] * vb[j]; }
@@ -361,8 +392,7 @@ __global__ void __launch_bounds__(FLUX_TPB) flux_kernel(FluxLaunch L)
                     for (int j = 0; j < D; ++j) s_ += T[m][j] * vb[j];
                     vh[m] = s_;
                 }
-                const R Tb = ilb_c;       // T-bar = 1 / {beta}^ln
-                R cb, H, sa, se = R(0), ssh, Y1 = R(1), Y2 = R(0), pre = R(0), D11 = R(0), D12 = R(0), D21 = R(0), D22 = R(0), e1 = R(0), e2 = R(0);
+                R cb, H, sa, se = R(0), ssh, Y1 = R(1), Y2 = R(0), D11 = R(0), D12 = R(0), D21 = R(0), D22 = R(0), e1 = R(0), e2 = R(0);
                 if constexpr (NS == 1) {
                     const R G = R(I.gamma[0]), Rg = R(I.Rs[0]), cv = R(I.cv[0]);
                     const R rb = lr_c[0];
@@ -382,7 +412,7 @@ __global__ void __launch_bounds__(FLUX_TPB) flux_kernel(FluxLaunch L)
                     Y2 = lr_c[1] * irb;
                     H = rh * irb + R(0.5) * vv;
                     cb = Ar<R>::sq(Rb * Gb * Tb);
-                    pre = Ar<R>::sq(rb * Ar<R>::rcp(Gb * Rb));
+                    const R pre = Ar<R>::sq(rb * Ar<R>::rcp(Gb * Rb));
                     sa = pre * R(0.70710678118654752440);
                     ssh = Ar<R>::sq(rb * Tb);
                     const R R1 = R(I.Rs[0]), R2 = R(I.Rs[1]);
@@ -395,7 +425,7 @@ __global__ void __launch_bounds__(FLUX_TPB) flux_kernel(FluxLaunch L)
                     e1 = R(0.5) * vv - (R(I.cv[0]) + R1 - Gb * R(I.cv[0])) * Tb * igm;
                     e2 = R(0.5) * vv - (R(I.cv[1]) + R2 - Gb * R(I.cv[1])) * Tb * igm;
                 }
-                const R lam = Ar<R>::ab(R(Gt) + Ln * vh[0]) + Ln * cb;
+                const R lam = Ar<R>::ab(to_r<R>(Gt) + Ln * vh[0]) + Ln * cb;
                 // round-off band of [[W_m]]: delta ||r_m|| (||V_i|| + ||V_i+1||)
                 const R nvb = NR(Y::VN, 2) + NR(Y::VN, 3);
                 const R band2 = R(YBand<R>::value * YBand<R>::value) * nvb * nvb;
@@ -472,18 +502,18 @@ __global__ void __launch_bounds__(FLUX_TPB) flux_kernel(FluxLaunch L)
                     }
                 }
 #pragma unroll
-                for (int q = 0; q < NC; ++q) Fd_out[q] = -0.5 * (double)Fd[q];
+                for (int q = 0; q < NC; ++q) Fe[q] -= R(0.5) * Fd[q];
             }
 #undef NR
 #pragma unroll
-            for (int q = 0; q < NC; ++q) fl[q * NI + f] = (double)Fe[q] + Fd_out[q];
-            fl[(NC - 1) * NI + f] += I.pinf_tot * Gt;
-            fl[NC * NI + f] = Gt;
+            for (int q = 0; q < NC; ++q) fl[q * NI + f] = Fe[q];
+            gt[f] = Gt;
         }
         __syncthreads();
 
-        // ---------------- phase 3: divergence and output ----------------
+        // ---------------- phase 4: divergence and output ----------------
         const double dt = L.mode == MODE_RK ? *P.dt : 0.0;
+        const R rdx = to_r<R>(inv_dx);
         for (int t = threadIdx.x; t < S * WT; t += blockDim.x) {
             int s, w;
             if (k == 0) { s = t % S; w = t / S; }
@@ -497,8 +527,10 @@ __global__ void __launch_bounds__(FLUX_TPB) flux_kernel(FluxLaunch L)
             const long long id = lin(I, idx[0], idx[1], idx[2]);
             const int fr = w * (S + 1) + s + 1, fL = fr - 1;
             double r[NC + 1];
+            r[NC] = -(gt[fr] - gt[fL]) * inv_dx;       // J: the GCL flux, FP64
 #pragma unroll
-            for (int q = 0; q <= NC; ++q) r[q] = -(fl[q * NI + fr] - fl[q * NI + fL]) * inv_dx;
+            for (int q = 0; q < NC; ++q) r[q] = to_d(-(fl[q * NI + fr] - fl[q * NI + fL]) * rdx);
+            r[NC - 1] += I.pinf_tot * r[NC];           // the p_inf J xi_k/t part of the energy flux
             if (L.mode == MODE_WRITE) {
 #pragma unroll
                 for (int q = 0; q < NC; ++q) P.accU[q * ncell + id] = r[q];
@@ -533,8 +565,9 @@ template <int D, int NS, typename R, int S, int WT>
 static size_t smem_of()
 {
     using Y = Lay<D, NS>;
-    constexpr int NN = Tile<S, WT>::NN, NI = Tile<S, WT>::NI;
-    return sizeof(double) * ((Y::NC + 1) * NI + NN) + sizeof(R) * Y::NF * NN;
+    using TL = Tile<S, WT>;
+    return sizeof(double) * (TL::NI + TL::NN) +
+           sizeof(R) * (Y::NF * TL::NN + Y::NC * TL::NP + (NS + 1) * TL::NI + Y::NC * TL::NI);
 }
 
 size_t flux_smem_bytes(int D, int NS, bool mixed, int k)

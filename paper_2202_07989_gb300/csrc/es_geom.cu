@@ -184,4 +184,14 @@ __global__ void init_J_kernel(const Inst* __restrict__ insts, StagePtrs single, 
     }
 }
 
+__global__ void conversion_check_kernel(const double* __restrict__ in, int n, float* __restrict__ o32,
+                                        double* __restrict__ o64)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float f = f64_to_f32(in[i]);
+    o32[i] = f;
+    o64[i] = f32_to_f64(f);
+}
+
 }  // namespace es

@@ -5,10 +5,11 @@
 
 namespace es {
 
-// flux tiles: (S + 1) * WT interfaces = 256 threads per tile
+// flux tiles of S nodes along the line x WT lines: (3S + 6) WT = 768 distinct node pairs
+// (three per thread) and (S + 1) WT <= 256 interfaces
 constexpr int FLUX_TPB = 256;
-constexpr int S_K0 = 63, WT_K0 = 4;    // direction 1: 63 nodes along the line x 4 lines
-constexpr int S_KN = 31, WT_KN = 8;    // directions 2, 3: 31 nodes x 8 neighbouring lines (coalesced)
+constexpr int S_K0 = 62, WT_K0 = 4;    // direction 1: 62 nodes along the line x 4 lines
+constexpr int S_KN = 30, WT_KN = 8;    // directions 2, 3: 30 nodes x 8 neighbouring lines (coalesced)
 constexpr int NODE_TPB = 256;
 
 enum { MODE_WRITE = 0, MODE_ACC = 1, MODE_RK = 2 };
@@ -30,6 +31,7 @@ __global__ void dx3d_kernel(const Inst* insts, StagePtrs single, const StagePtrs
                             const Scratch* scr);
 __global__ void metrics3d_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work, int nwork,
                                  const Scratch* scr);
+__global__ void conversion_check_kernel(const double* in, int n, float* o32, double* o64);
 __global__ void init_J_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work, int nwork);
 
 // flux + divergence (+ RK stage) for one direction; D dims, NS species, R compute type

@@ -70,6 +70,7 @@ def lib():
             "es_run_host": (C.c_int, [vp, dp, dp, dp, C.c_int, C.c_double, C.POINTER(C.c_double), vp]),
             "es_poll_status": (C.c_int, [vp, ip, vp]),
             "es_profile": (C.c_int, [vp, C.c_int]),
+            "es_check_conversions": (C.c_int, [dp, C.c_int, dp, dp, vp]),
             "es_entropy_production_noalloc": (C.c_int, [C.POINTER(EsConfig), dp, dp, dp, dp, dp, vp]),
             "es_profile_read": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.c_int]),
         }
@@ -272,6 +273,20 @@ class Context:
         if st not in (0, 4):
             self._chk(st, "es_poll_status")
         return f.value
+
+
+def es_check_conversions(x: torch.Tensor):
+    """(binary32, widened binary64) of a float64 CUDA tensor through the library's integer-pipe
+    conversions."""
+    if not (x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()):
+        raise EsError("x must be a contiguous float64 CUDA tensor")
+    o32 = torch.empty(x.shape, dtype=torch.float32, device=x.device)
+    o64 = torch.empty(x.shape, dtype=torch.float64, device=x.device)
+    st = lib().es_check_conversions(C.c_void_p(x.data_ptr()), x.numel(), C.c_void_p(o32.data_ptr()),
+                                    C.c_void_p(o64.data_ptr()), _stream())
+    if st != 0:
+        raise EsError("es_check_conversions: %s" % ES_STATUS.get(st, st))
+    return o32, o64
 
 
 # module-level aliases with the C names

@@ -268,3 +268,23 @@ def test_nonphysical_state_is_reported():
     ctx.es_rhs(to_dev(JU, torch), to_dev(J, torch), to_dev(x, torch), to_dev(xdot, torch))
     assert ctx.es_poll_status() & 1
     assert ctx.es_poll_status() == 0
+
+
+def test_integer_pipe_conversions_match_hardware():
+    """The mixed form's integer-instruction binary64 -> binary32 rounding equals the hardware
+    conversion bit for bit (outside the flushed range below 2^-126), and widening is exact."""
+    torch = need_gpu()
+    from paper_2202_07989_gb300 import es
+    rng = np.random.default_rng(41)
+    mant = rng.uniform(-1, 1, size=200000)
+    expo = rng.integers(-120, 120, size=200000)
+    vals = np.concatenate([mant * np.exp2(expo), [0.0, -0.0, 1.0, -1.0, 3.4e38, -3.4e38, 1.5, 2.5 * 2.0 ** -29],
+                           # exact halfway cases between two binary32 values
+                           (1.0 + (2 * np.arange(1, 64) + 1) * 2.0 ** -24), -(1.0 + (2 * np.arange(1, 64)) * 2.0 ** -24)])
+    x = torch.from_numpy(vals).cuda()
+    o32, o64 = es.es_check_conversions(x)
+    ref = x.float()
+    keep = x.abs() >= 2.0 ** -126
+    assert torch.equal(o32[keep].view(torch.int32), ref[keep].view(torch.int32))
+    assert torch.equal(o64, o32.double())
+    assert bool((o32[~keep] == 0).all())
