@@ -154,7 +154,7 @@ Inst make_inst(const es_config& g)
         int nb = bdim < g.d ? I.n[bdim] : 1;
         I.tiles[k] = ((I.n[k] + S - 1) / S) * ((I.n[adim] + WT - 1) / WT) * nb;
     }
-    I.ntile_nodes = (int)((I.ncell + NODE_TPB - 1) / NODE_TPB);
+    I.ntile_nodes = node_tiles(I, 0);
     return I;
 }
 
@@ -422,13 +422,9 @@ es_status es_create_batch(const es_config* cfgs, int n_inst, es_ctx** out)
     cudaMemcpy(c->dI, c->hI.data(), sizeof(Inst) * n_inst, cudaMemcpyHostToDevice);
     cudaMemcpy(c->dS, c->hS.data(), sizeof(Scratch) * n_inst, cudaMemcpyHostToDevice);
     cudaMemset(c->status, 0, sizeof(int));
-    c->w_pad = build_work(c, [](const Inst& I) { return (I.npad + NODE_TPB - 1) / NODE_TPB; }, c->n_pad);
-    c->w_cell = build_work(c, [](const Inst& I) { return (I.ncell + NODE_TPB - 1) / NODE_TPB; }, c->n_cell);
-    if (c->d == 3)
-        c->w_ext = build_work(c, [](const Inst& I) {
-            long long ne = (long long)(I.n[0] + 12) * (I.n[1] + 12) * (I.n[2] + 12);
-            return (ne + NODE_TPB - 1) / NODE_TPB;
-        }, c->n_ext);
+    c->w_pad = build_work(c, [](const Inst& I) { return (long long)node_tiles(I, 3); }, c->n_pad);
+    c->w_cell = build_work(c, [](const Inst& I) { return (long long)node_tiles(I, 0); }, c->n_cell);
+    if (c->d == 3) c->w_ext = build_work(c, [](const Inst& I) { return (long long)node_tiles(I, 6); }, c->n_ext);
     for (int k = 0; k < c->d; ++k) c->w_flux[k] = build_work(c, [k](const Inst& I) { return (long long)I.tiles[k]; }, c->n_flux[k]);
     // per-instance ranges of the cell work list (entropy reduction)
     std::vector<int> first(n_inst + 1, 0);

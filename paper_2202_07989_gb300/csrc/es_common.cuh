@@ -81,6 +81,31 @@ struct Scratch {
 
 #define ES_PTRS(P) const StagePtrs P = (table ? table[it.x] : single)
 
+// node-wise kernels run over tiles of NT_X x NT_Y nodes of one (i1, i0) plane
+constexpr int NT_X = 32, NT_Y = 8;
+
+// number of node tiles of a grid extended by `pad` ghost layers in every direction of the instance
+__host__ __device__ inline int node_tiles(const Inst& I, int pad)
+{
+    int e0 = I.n[0] + 2 * pad, e1 = I.n[1] + 2 * pad, e2 = I.d == 3 ? I.n[2] + 2 * pad : 1;
+    return ((e0 + NT_X - 1) / NT_X) * ((e1 + NT_Y - 1) / NT_Y) * e2;
+}
+
+// the node of this thread in node tile `tile` (ghost layers included); false outside the grid
+__device__ inline bool tile_node(const Inst& I, int tile, int pad, int& i0, int& i1, int& i2)
+{
+    int e0 = I.n[0] + 2 * pad, e1 = I.n[1] + 2 * pad;
+    int ntx = (e0 + NT_X - 1) / NT_X, nty = (e1 + NT_Y - 1) / NT_Y;
+    int tx = tile % ntx, r = tile / ntx;
+    int ty = r % nty, tz = r / nty;
+    int lx = (int)threadIdx.x % NT_X, ly = (int)threadIdx.x / NT_X;
+    int a = tx * NT_X + lx, b = ty * NT_Y + ly;
+    i0 = a - pad;
+    i1 = b - pad;
+    i2 = I.d == 3 ? tz - pad : 0;
+    return a < e0 && b < e1;
+}
+
 __host__ __device__ inline long long lin(const Inst& I, int i0, int i1, int i2)
 {
     return ((long long)i2 * I.n[1] + i1) * I.n[0] + i0;

@@ -31,22 +31,37 @@ __global__ void metrics2d_kernel(const Inst* __restrict__ insts, StagePtrs singl
         int2 it = work[wi];
         const Inst& I = insts[it.x];
         ES_PTRS(S);
-        long long p = (long long)it.y * blockDim.x + threadIdx.x;
-        if (p >= I.npad) continue;
-        int i0 = (int)(p % I.P[0]) - 3, i1 = (int)(p / I.P[0]) - 3;
-        double a[2], b[2], c[2], e[2];
-        // delta_1 and delta_2 of both coordinates, sharing the neighbour loads
+        int i0, i1, i2;
+        if (!tile_node(I, it.y, 3, i0, i1, i2)) continue;
+        const long long p = plin(I, i0, i1, 0);
+        // delta_1 and delta_2 of both coordinates
         double d1[2] = { 0, 0 }, d2[2] = { 0, 0 };
+        const int n0 = I.n[0], n1 = I.n[1];
+        if (i0 >= 3 && i0 < n0 - 3 && i1 >= 3 && i1 < n1 - 3) {
+            // interior: no ghost node in the stencil
+            const double* X0 = S.x;
+            const double* X1 = S.x + I.ncell;
+            const int c = i1 * n0 + i0;
 #pragma unroll
-        for (int m = 1; m <= 3; ++m) {
-            x_at<false>(I, S.x, i0 + m, i1, 0, a);
-            x_at<false>(I, S.x, i0 - m, i1, 0, b);
-            x_at<false>(I, S.x, i0, i1 + m, 0, c);
-            x_at<false>(I, S.x, i0, i1 - m, 0, e);
-            d1[0] += alpha3(m) * (a[0] - b[0]);
-            d1[1] += alpha3(m) * (a[1] - b[1]);
-            d2[0] += alpha3(m) * (c[0] - e[0]);
-            d2[1] += alpha3(m) * (c[1] - e[1]);
+            for (int m = 1; m <= 3; ++m) {
+                d1[0] += alpha3(m) * (X0[c + m] - X0[c - m]);
+                d1[1] += alpha3(m) * (X1[c + m] - X1[c - m]);
+                d2[0] += alpha3(m) * (X0[c + m * n0] - X0[c - m * n0]);
+                d2[1] += alpha3(m) * (X1[c + m * n0] - X1[c - m * n0]);
+            }
+        } else {
+            double a[2], b[2], cc[2], e[2];
+#pragma unroll
+            for (int m = 1; m <= 3; ++m) {
+                x_at<false>(I, S.x, i0 + m, i1, 0, a);
+                x_at<false>(I, S.x, i0 - m, i1, 0, b);
+                x_at<false>(I, S.x, i0, i1 + m, 0, cc);
+                x_at<false>(I, S.x, i0, i1 - m, 0, e);
+                d1[0] += alpha3(m) * (a[0] - b[0]);
+                d1[1] += alpha3(m) * (a[1] - b[1]);
+                d2[0] += alpha3(m) * (cc[0] - e[0]);
+                d2[1] += alpha3(m) * (cc[1] - e[1]);
+            }
         }
         double m11 = 0.5 * d2[1] * I.inv_dxi[1], m12 = -0.5 * d2[0] * I.inv_dxi[1];
         double m21 = -0.5 * d1[1] * I.inv_dxi[0], m22 = 0.5 * d1[0] * I.inv_dxi[0];
@@ -72,9 +87,9 @@ __global__ void dx3d_kernel(const Inst* __restrict__ insts, StagePtrs single, co
         const Inst& I = insts[it.x];
         ES_PTRS(S);
         long long E0 = I.n[0] + 12, E1 = I.n[1] + 12, E2 = I.n[2] + 12, ne = E0 * E1 * E2;
-        long long p = (long long)it.y * blockDim.x + threadIdx.x;
-        if (p >= ne) continue;
-        int i0 = (int)(p % E0) - 6, i1 = (int)((p / E0) % E1) - 6, i2 = (int)(p / (E0 * E1)) - 6;
+        int i0, i1, i2;
+        if (!tile_node(I, it.y, 6, i0, i1, i2)) continue;
+        const long long p = ((long long)(i2 + 6) * E1 + (i1 + 6)) * E0 + (i0 + 6);
         double* D = scr[it.x].D3;
         double acc[3][3];
 #pragma unroll
@@ -114,9 +129,9 @@ __global__ void metrics3d_kernel(const Inst* __restrict__ insts, StagePtrs singl
         int2 it = work[wi];
         const Inst& I = insts[it.x];
         ES_PTRS(S);
-        long long p = (long long)it.y * blockDim.x + threadIdx.x;
-        if (p >= I.npad) continue;
-        int i0 = (int)(p % I.P[0]) - 3, i1 = (int)((p / I.P[0]) % I.P[1]) - 3, i2 = (int)(p / ((long long)I.P[0] * I.P[1])) - 3;
+        int i0, i1, i2;
+        if (!tile_node(I, it.y, 3, i0, i1, i2)) continue;
+        const long long p = plin(I, i0, i1, i2);
         const double* D = scr[it.x].D3;
         long long E0 = I.n[0] + 12, E1 = I.n[1] + 12, ne = E0 * E1 * (I.n[2] + 12);
         auto eidx = [&](int a0, int a1, int a2) { return ((long long)(a2 + 6) * E1 + (a1 + 6)) * E0 + (a0 + 6); };
@@ -169,9 +184,9 @@ __global__ void init_J_kernel(const Inst* __restrict__ insts, StagePtrs single, 
         int2 it = work[wi];
         const Inst& I = insts[it.x];
         ES_PTRS(S);
-        long long p = (long long)it.y * blockDim.x + threadIdx.x;
-        if (p >= I.ncell) continue;
-        int i0 = (int)(p % I.n[0]), i1 = (int)((p / I.n[0]) % I.n[1]), i2 = (int)(p / ((long long)I.n[0] * I.n[1]));
+        int i0, i1, i2;
+        if (!tile_node(I, it.y, 0, i0, i1, i2)) continue;
+        const long long p = lin(I, i0, i1, i2);
         double A[3][3];
         for (int j = 0; j < I.d; ++j)
             for (int k = 0; k < I.d; ++k) A[j][k] = delta_x(I, S.x, i0, i1, i2, k, j) * I.inv_dxi[k];

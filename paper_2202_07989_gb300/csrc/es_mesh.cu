@@ -75,11 +75,11 @@ __global__ void cfl_kernel(const Inst* __restrict__ insts, StagePtrs single, con
         int2 it = work[wi];
         const Inst& I = insts[it.x];
         ES_PTRS(P);
-        long long p = (long long)it.y * blockDim.x + threadIdx.x;
+        int i0, i1, i2;
+        const bool valid = tile_node(I, it.y, 0, i0, i1, i2);
+        const long long p = valid ? lin(I, i0, i1, i2) : 0;
         double s = 0.0;
-        if (p < I.ncell) {
-            int i0, i1, i2;
-            node_coords(I, p, i0, i1, i2);
+        if (valid) {
             double U[MAXC], rl[2], v[3], T, pr, rho;
             load_U(I, P.JU, P.J, i0, i1, i2, U);
             prim(I, U, rl, v, T, pr, rho);
@@ -105,14 +105,17 @@ __global__ void cfl_kernel(const Inst* __restrict__ insts, StagePtrs single, con
 
 __device__ inline double sigma_of(const Inst& I, int kind, const double* U)
 {
-    double rl[2], v[3], T, p, rho;
-    prim(I, U, rl, v, T, p, rho);
+    const double rho = I.N == 2 ? U[0] + U[1] : U[0];
     switch (kind) {
-    case SIG_RHO1: return rl[0];
-    case SIG_RHO2: return I.N == 2 ? rl[1] : 0.0;
-    case SIG_P: return p;
-    case SIG_Y2: return I.N == 2 ? rl[1] / rho : 0.0;
-    case SIG_V1: return v[0];
+    case SIG_RHO1: return U[0];
+    case SIG_RHO2: return I.N == 2 ? U[1] : 0.0;
+    case SIG_Y2: return I.N == 2 ? U[1] / rho : 0.0;
+    case SIG_V1: return U[I.N] / rho;
+    case SIG_P: {
+        double rl[2], v[3], T, p, r;
+        prim(I, U, rl, v, T, p, r);
+        return p;
+    }
     default: return rho;
     }
 }
@@ -126,11 +129,11 @@ __global__ void monitor_grad_kernel(const Inst* __restrict__ insts, StagePtrs si
         int2 it = work[wi];
         const Inst& I = insts[it.x];
         ES_PTRS(P);
-        long long p = (long long)it.y * blockDim.x + threadIdx.x;
+        int i[3];
+        const bool valid = tile_node(I, it.y, 0, i[0], i[1], i[2]);
+        const long long p = valid ? lin(I, i[0], i[1], i[2]) : 0;
         double g[4] = { 0, 0, 0, 0 };
-        if (p < I.ncell) {
-            int i[3];
-            node_coords(I, p, i[0], i[1], i[2]);
+        if (valid) {
             for (int k = 0; k < I.d; ++k) {
                 int ip[3] = { i[0], i[1], i[2] }, im[3] = { i[0], i[1], i[2] };
                 ip[k] += 1;
@@ -165,8 +168,9 @@ __global__ void monitor_theta_kernel(const Inst* __restrict__ insts, const int2*
         int2 it = work[wi];
         const Inst& I = insts[it.x];
         const Scratch& P = scr[it.x];
-        long long p = (long long)it.y * blockDim.x + threadIdx.x;
-        if (p >= I.ncell) continue;
+        int i0, i1, i2;
+        if (!tile_node(I, it.y, 0, i0, i1, i2)) continue;
+        const long long p = lin(I, i0, i1, i2);
         R t = R(1);
         for (int s = 0; s < I.n_sigma; ++s) {
             double mx = P.red[1 + s];
@@ -187,18 +191,24 @@ __global__ void filter_kernel(const Inst* __restrict__ insts, const int2* __rest
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
         int2 it = work[wi];
         const Inst& I = insts[it.x];
-        long long p = (long long)it.y * blockDim.x + threadIdx.x;
-        if (p >= I.ncell) continue;
         int i0, i1, i2;
-        node_coords(I, p, i0, i1, i2);
+        if (!tile_node(I, it.y, 0, i0, i1, i2)) continue;
+        const long long p = lin(I, i0, i1, i2);
         const R* a = reinterpret_cast<const R*>(parity ? scr[it.x].th1 : scr[it.x].th0);
         R* dst = reinterpret_cast<R*>(parity ? scr[it.x].th0 : scr[it.x].th1);
         R acc = R(0);
         int lo3 = I.d == 3 ? -1 : 0, hi3 = I.d == 3 ? 1 : 0;
+        const int n0 = I.n[0], n1 = I.n[1];
+        const bool inner = i0 >= 1 && i0 < n0 - 1 && i1 >= 1 && i1 < n1 - 1 && (I.d == 2 || (i2 >= 1 && i2 < I.n[2] - 1));
         for (int j3 = lo3; j3 <= hi3; ++j3)
             for (int j2 = -1; j2 <= 1; ++j2) {
                 R row = R(0);
-                for (int j1 = -1; j1 <= 1; ++j1) row += (j1 == 0 ? R(0.5) : R(0.25)) * a[s_map(I, i0 + j1, i1 + j2, i2 + j3)];
+                if (inner) {
+                    const R* q = a + p + (long long)j3 * n0 * n1 + j2 * n0;
+                    row = R(0.25) * (q[-1] + q[1]) + R(0.5) * q[0];
+                } else {
+                    for (int j1 = -1; j1 <= 1; ++j1) row += (j1 == 0 ? R(0.5) : R(0.25)) * a[s_map(I, i0 + j1, i1 + j2, i2 + j3)];
+                }
                 acc += (j2 == 0 ? R(0.5) : R(0.25)) * (j3 == 0 ? (I.d == 3 ? R(0.5) : R(1)) : R(0.25)) * row;
             }
         dst[p] = acc;
@@ -214,26 +224,38 @@ __global__ void jacobi_kernel(const Inst* __restrict__ insts, StagePtrs single, 
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
         int2 it = work[wi];
         const Inst& I = insts[it.x];
-        long long p = (long long)it.y * blockDim.x + threadIdx.x;
-        if (p >= I.ncell) continue;
         int i[3];
-        node_coords(I, p, i[0], i[1], i[2]);
+        if (!tile_node(I, it.y, 0, i[0], i[1], i[2])) continue;
+        const long long p = lin(I, i[0], i[1], i[2]);
         ES_PTRS(P);
         const Scratch& Sc = scr[it.x];
         const R* th = reinterpret_cast<const R*>(theta_sel ? Sc.th1 : Sc.th0);
         const double* xs = sweep == 0 ? P.x : (sweep % 2 == 1 ? Sc.xa : Sc.xb);
         double* xd_ = sweep % 2 == 0 ? Sc.xa : Sc.xb;
-        double tc = (double)th[p];
+        double tc = to_d(th[p]);
         double num[3] = { 0, 0, 0 }, den = 0.0;
+        bool inner = true;
+        for (int k = 0; k < I.d; ++k) inner = inner && i[k] >= 1 && i[k] < I.n[k] - 1;
+        long long stride = 1;
         for (int k = 0; k < I.d; ++k) {
-            int ip[3] = { i[0], i[1], i[2] }, im[3] = { i[0], i[1], i[2] };
-            ip[k] += 1;
-            im[k] -= 1;
-            double tp = 0.5 * (tc + (double)th[s_map(I, ip[0], ip[1], ip[2])]);
-            double tm = 0.5 * (tc + (double)th[s_map(I, im[0], im[1], im[2])]);
-            double xp[3], xm[3];
-            x_at<false>(I, xs, ip[0], ip[1], ip[2], xp);
-            x_at<false>(I, xs, im[0], im[1], im[2], xm);
+            double tp, tm, xp[3], xm[3];
+            if (inner) {
+                tp = 0.5 * (tc + to_d(th[p + stride]));
+                tm = 0.5 * (tc + to_d(th[p - stride]));
+                for (int j = 0; j < I.d; ++j) {
+                    xp[j] = xs[(long long)j * I.ncell + p + stride];
+                    xm[j] = xs[(long long)j * I.ncell + p - stride];
+                }
+            } else {
+                int ip[3] = { i[0], i[1], i[2] }, im[3] = { i[0], i[1], i[2] };
+                ip[k] += 1;
+                im[k] -= 1;
+                tp = 0.5 * (tc + to_d(th[s_map(I, ip[0], ip[1], ip[2])]));
+                tm = 0.5 * (tc + to_d(th[s_map(I, im[0], im[1], im[2])]));
+                x_at<false>(I, xs, ip[0], ip[1], ip[2], xp);
+                x_at<false>(I, xs, im[0], im[1], im[2], xm);
+            }
+            stride *= I.n[k];
             double h2 = I.inv_dxi[k] * I.inv_dxi[k];
             for (int j = 0; j < I.d; ++j) num[j] += (tp * xp[j] + tm * xm[j]) * h2;
             den += (tp + tm) * h2;
@@ -258,11 +280,11 @@ __global__ void limiter_kernel(const Inst* __restrict__ insts, StagePtrs single,
         const Inst& I = insts[it.x];
         ES_PTRS(P);
         const double* xmu = xmu_of(P, scr[it.x], I.mu);
-        long long p = (long long)it.y * blockDim.x + threadIdx.x;
+        int i[3];
+        const bool valid = tile_node(I, it.y, 0, i[0], i[1], i[2]);
+        const long long p = valid ? lin(I, i[0], i[1], i[2]) : 0;
         double b = 1.0;
-        if (p < I.ncell) {
-            int i[3];
-            node_coords(I, p, i[0], i[1], i[2]);
+        if (valid) {
             for (int k = 0; k < I.d; ++k) {
                 double xc = P.x[(long long)k * I.ncell + p];
                 double dx = xmu[(long long)k * I.ncell + p] - xc;
@@ -298,12 +320,13 @@ __global__ void xdot_kernel(const Inst* __restrict__ insts, StagePtrs single, co
         const double* xmu = xmu_of(P, scr[it.x], I.mu);
         double dt = P.dt_fixed > 0.0 ? P.dt_fixed : I.cfl / red[0];
         double dtau = red[5];
-        long long p = (long long)it.y * blockDim.x + threadIdx.x;
         if (it.y == 0 && threadIdx.x == 0) {
             P.out[0] = dt;
             P.out[1] = dtau;
         }
-        if (p >= I.ncell) continue;
+        int i0, i1, i2;
+        if (!tile_node(I, it.y, 0, i0, i1, i2)) continue;
+        const long long p = lin(I, i0, i1, i2);
         for (int j = 0; j < I.d; ++j) {
             long long q = (long long)j * I.ncell + p;
             P.xdot_out[q] = dtau * (xmu[q] - P.x[q]) / dt;
@@ -320,9 +343,11 @@ __global__ void entropy_partial_kernel(const Inst* __restrict__ insts, StagePtrs
         int2 it = work[wi];
         const Inst& I = insts[it.x];
         ES_PTRS(P);
-        long long p = (long long)it.y * blockDim.x + threadIdx.x;
+        int i0, i1, i2;
+        const bool valid = tile_node(I, it.y, 0, i0, i1, i2);
+        const long long p = valid ? lin(I, i0, i1, i2) : 0;
         double a = 0.0, b = 0.0;
-        if (p < I.ncell) {
+        if (valid) {
             const double* JU = P.JU;
             double J = P.J[p], U[MAXC];
             for (int q = 0; q < I.nc; ++q) U[q] = JU[(long long)q * I.ncell + p] / J;
