@@ -355,6 +355,8 @@ def main_ours(args):
 
     # batched form: 64 uneven instances, mixed
     batched = None
+    prof_b = None
+    kb = 1
     if not args.no_batched:
         insts = W.batched_2d(64)
         bt = Batch(insts, es.MIXED, torch)
@@ -366,6 +368,7 @@ def main_ours(args):
         batched = {"value": bt.cells * 3 * kb / tb, "ms_per_step": 1e3 * tb / kb, "instances": len(insts),
                    "cells": bt.cells}
         forms["batched_mixed"] = batched
+        prof_b = kernel_profile(bt, kb, torch)
 
     # end to end: C-ABI call on pinned host buffers, copies inside the timed region
     e2e = None
@@ -428,7 +431,8 @@ def main_ours(args):
                    "instances_per_rank": 1},
         "forms": forms, "errors": errs, "roofline": roofline, "roofline_fp64": roofline_fp64,
         "kernel_ms": {"mixed": {k: v[0] / args.steps for k, v in prof_m.items()},
-                      "fp64": {k: v[0] / k64 for k, v in prof_d.items()}},
+                      "fp64": {k: v[0] / k64 for k, v in prof_d.items()},
+                      "batched_mixed": ({k: v[0] / kb for k, v in prof_b.items()} if batched else None)},
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
         "gpu_launches": launches_per_step(pb) * args.steps,
     }

@@ -322,30 +322,24 @@ const double RK_B[3] = { 1.0, 0.25, 2.0 / 3.0 };
 
 void launch_mesh(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStream_t st)
 {
-    {
     ProfScope ps(c, PC_MESH, st);
     red_init_kernel<<<(c->n_inst + 127) / 128, 128, 0, st>>>(c->dS, c->n_inst);
-    // node metrics of x^n (no mesh velocity) for Eq. (cfl)
-    StagePtrs Q = P;
-    Q.xdot = nullptr;
-    Q.M = c->hS[0].M;
-    if (tab) {
-        // batched: metrics target is each instance's scratch; the mesh table already points there
+    if (c->d == 3) {
+        // node metrics of x^n (no mesh velocity) for Eq. (cfl); 2D forms them inline
+        StagePtrs Q = P;
+        Q.xdot = nullptr;
+        Q.M = c->hS[0].M;
         launch_metrics(c, Q, tab, st);
-    } else {
-        launch_metrics(c, Q, nullptr, st);
-    }
     }
     int gc = node_grid(c, c->n_cell);
-    ProfScope ps(c, PC_MESH, st);
-    cfl_kernel<<<gc, NODE_TPB, 0, st>>>(c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
-    monitor_grad_kernel<<<gc, NODE_TPB, 0, st>>>(c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
+    cfl_grad_kernel<<<gc, NODE_TPB, 0, st>>>(c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
     int nf = c->hI[0].nf, mu = c->hI[0].mu;
-    launch_monitor_theta(c->mixed, gc, st, c->dI, c->w_cell, c->n_cell, c->dS);
-    for (int f = 0; f < nf; ++f) launch_filter(c->mixed, gc, st, c->dI, c->w_cell, c->n_cell, c->dS, f % 2);
+    if (nf == 0) launch_monitor_theta(c->mixed, gc, st, c->dI, c->w_cell, c->n_cell, c->dS);
+    for (int f = 0; f < nf; ++f) launch_filter(c->mixed, f == 0, gc, st, c->dI, c->w_cell, c->n_cell, c->dS, f % 2);
     int th_sel = nf % 2;
-    for (int s = 0; s < mu; ++s) launch_jacobi(c->mixed, gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS, s, th_sel);
-    limiter_kernel<<<gc, NODE_TPB, 0, st>>>(c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
+    for (int s = 0; s < mu; ++s)
+        launch_jacobi(c->mixed, s == mu - 1, gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS, s, th_sel);
+    if (mu == 0) limiter_kernel<<<gc, NODE_TPB, 0, st>>>(c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
     xdot_kernel<<<gc, NODE_TPB, 0, st>>>(c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
 }
 

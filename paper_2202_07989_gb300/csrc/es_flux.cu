@@ -271,13 +271,16 @@ __global__ void __launch_bounds__(FLUX_TPB) flux_kernel(FluxLaunch L)
 #pragma unroll
             for (int q = 0; q < NC; ++q) { nr[(Y::VV + q) * NN + node] = Vn[q]; vn += Vn[q] * Vn[q]; }
             nr[Y::VN * NN + node] = Ar<R>::sq(vn);
-            // metrics of direction k at this node (the padded buffer covers g in [-3, n + 3))
-            long long pid = plin(I, idx[0], idx[1], idx[2]);
-            double m0 = P.M[(long long)(k * (D + 1)) * I.npad + pid];
-            mt64[node] = m0;
-            nr[Y::MR * NN + node] = to_r<R>(m0);
+            // metrics of direction k at this node from the metrics kernel (padded buffer covering
+            // g in [-3, n + 3))
+            {
+                long long pid = plin(I, idx[0], idx[1], idx[2]);
+                double m0 = P.M[(long long)(k * (D + 1)) * I.npad + pid];
+                mt64[node] = m0;
+                nr[Y::MR * NN + node] = to_r<R>(m0);
 #pragma unroll
-            for (int j = 0; j < D; ++j) nr[(Y::MR + 1 + j) * NN + node] = to_r<R>(P.M[(long long)(k * (D + 1) + 1 + j) * I.npad + pid]);
+                for (int j = 0; j < D; ++j) nr[(Y::MR + 1 + j) * NN + node] = to_r<R>(P.M[(long long)(k * (D + 1) + 1 + j) * I.npad + pid]);
+            }
         }
         __syncthreads();
 

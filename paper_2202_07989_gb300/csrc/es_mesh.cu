@@ -66,43 +66,6 @@ __device__ inline void prim(const Inst& I, const double* U, double* rl, double* 
     p = rr * T - I.pinf_tot;
 }
 
-// CFL: s_i = sum_k (|J xi_k/x . v| + c |J xi_k/x|) / (J dxi_k) from node metrics at x^n
-__global__ void cfl_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
-                           const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr)
-{
-    __shared__ double sh[32];
-    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
-        int2 it = work[wi];
-        const Inst& I = insts[it.x];
-        ES_PTRS(P);
-        int i0, i1, i2;
-        const bool valid = tile_node(I, it.y, 0, i0, i1, i2);
-        const long long p = valid ? lin(I, i0, i1, i2) : 0;
-        double s = 0.0;
-        if (valid) {
-            double U[MAXC], rl[2], v[3], T, pr, rho;
-            load_U(I, P.JU, P.J, i0, i1, i2, U);
-            prim(I, U, rl, v, T, pr, rho);
-            double a = 0.0, g = 0.0, cvr = 0.0;
-            for (int l = 0; l < I.N; ++l) { a += (I.gamma[l] - 1.0) * I.cv[l] * rl[l]; g += I.gamma[l] * I.cv[l] * rl[l]; cvr += I.cv[l] * rl[l]; }
-            double c = sqrt((a / rho) * (g / cvr) * T);
-            long long pid = plin(I, i0, i1, i2);
-            for (int k = 0; k < I.d; ++k) {
-                double L2 = 0.0, vn = 0.0;
-                for (int j = 0; j < I.d; ++j) {
-                    double m = scr[it.x].M[(long long)(k * (I.d + 1) + 1 + j) * I.npad + pid];
-                    L2 += m * m;
-                    vn += m * v[j];
-                }
-                s += (fabs(vn) + c * sqrt(L2)) / P.J[p] * I.inv_dxi[k];
-            }
-            if (!(s >= 0.0)) s = 0.0;
-        }
-        double m = block_max<double>(s, sh);
-        if (threadIdx.x == 0) atomic_max_pos(&scr[it.x].red[0], m);
-    }
-}
-
 __device__ inline double sigma_of(const Inst& I, int kind, const double* U)
 {
     const double rho = I.N == 2 ? U[0] + U[1] : U[0];
@@ -120,9 +83,47 @@ __device__ inline double sigma_of(const Inst& I, int kind, const double* U)
     }
 }
 
-// |grad_xi sigma_s| by second-order central differences; per-instance maxima
-__global__ void monitor_grad_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
-                                    const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr)
+// 2D node metrics J xi_k/x_j at interior node (i0, i1) (Sec. 3.2, degenerate case)
+__device__ inline void node_metrics2d(const Inst& I, const double* __restrict__ x, int i0, int i1, double m[3][3])
+{
+    double d1[2] = { 0, 0 }, d2[2] = { 0, 0 };
+    const int n0 = I.n[0], n1 = I.n[1];
+    if (i0 >= 3 && i0 < n0 - 3 && i1 >= 3 && i1 < n1 - 3) {
+        const double* X0 = x;
+        const double* X1 = x + I.ncell;
+        const int c = i1 * n0 + i0;
+#pragma unroll
+        for (int q = 1; q <= 3; ++q) {
+            d1[0] += alpha3(q) * (X0[c + q] - X0[c - q]);
+            d1[1] += alpha3(q) * (X1[c + q] - X1[c - q]);
+            d2[0] += alpha3(q) * (X0[c + q * n0] - X0[c - q * n0]);
+            d2[1] += alpha3(q) * (X1[c + q * n0] - X1[c - q * n0]);
+        }
+    } else {
+        double a[2], b[2], cc[2], e[2];
+#pragma unroll
+        for (int q = 1; q <= 3; ++q) {
+            x_at<false>(I, x, i0 + q, i1, 0, a);
+            x_at<false>(I, x, i0 - q, i1, 0, b);
+            x_at<false>(I, x, i0, i1 + q, 0, cc);
+            x_at<false>(I, x, i0, i1 - q, 0, e);
+            d1[0] += alpha3(q) * (a[0] - b[0]);
+            d1[1] += alpha3(q) * (a[1] - b[1]);
+            d2[0] += alpha3(q) * (cc[0] - e[0]);
+            d2[1] += alpha3(q) * (cc[1] - e[1]);
+        }
+    }
+    m[0][0] = 0.5 * d2[1] * I.inv_dxi[1];
+    m[0][1] = -0.5 * d2[0] * I.inv_dxi[1];
+    m[1][0] = -0.5 * d1[1] * I.inv_dxi[0];
+    m[1][1] = 0.5 * d1[0] * I.inv_dxi[0];
+}
+
+// one pass over the nodes: the CFL spectral-radius sum of Eq. (cfl) at x^n and the
+// monitor gradients |grad_xi sigma_s| (second-order central differences); per-instance
+// maxima by atomics on the non-negative bit patterns
+__global__ void cfl_grad_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
+                                const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr)
 {
     __shared__ double sh[32];
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
@@ -132,8 +133,28 @@ __global__ void monitor_grad_kernel(const Inst* __restrict__ insts, StagePtrs si
         int i[3];
         const bool valid = tile_node(I, it.y, 0, i[0], i[1], i[2]);
         const long long p = valid ? lin(I, i[0], i[1], i[2]) : 0;
-        double g[4] = { 0, 0, 0, 0 };
+        double s = 0.0, g[4] = { 0, 0, 0, 0 };
         if (valid) {
+            double U[MAXC], rl[2], v[3], T, pr, rho;
+            load_U(I, P.JU, P.J, i[0], i[1], i[2], U);
+            prim(I, U, rl, v, T, pr, rho);
+            double a = 0.0, gm = 0.0, cvr = 0.0;
+            for (int l = 0; l < I.N; ++l) { a += (I.gamma[l] - 1.0) * I.cv[l] * rl[l]; gm += I.gamma[l] * I.cv[l] * rl[l]; cvr += I.cv[l] * rl[l]; }
+            double c = sqrt((a / rho) * (gm / cvr) * T);
+            double m[3][3];
+            if (I.d == 2) {
+                node_metrics2d(I, P.x, i[0], i[1], m);
+            } else {
+                long long pid = plin(I, i[0], i[1], i[2]);
+                for (int k = 0; k < 3; ++k)
+                    for (int j = 0; j < 3; ++j) m[k][j] = scr[it.x].M[(long long)(k * 4 + 1 + j) * I.npad + pid];
+            }
+            for (int k = 0; k < I.d; ++k) {
+                double L2 = 0.0, vn = 0.0;
+                for (int j = 0; j < I.d; ++j) { L2 += m[k][j] * m[k][j]; vn += m[k][j] * v[j]; }
+                s += (fabs(vn) + c * sqrt(L2)) / P.J[p] * I.inv_dxi[k];
+            }
+            if (!(s >= 0.0)) s = 0.0;
             for (int k = 0; k < I.d; ++k) {
                 int ip[3] = { i[0], i[1], i[2] }, im[3] = { i[0], i[1], i[2] };
                 ip[k] += 1;
@@ -141,23 +162,39 @@ __global__ void monitor_grad_kernel(const Inst* __restrict__ insts, StagePtrs si
                 double Up[MAXC], Um[MAXC];
                 load_U(I, P.JU, P.J, ip[0], ip[1], ip[2], Up);
                 load_U(I, P.JU, P.J, im[0], im[1], im[2], Um);
-                for (int s = 0; s < I.n_sigma; ++s) {
-                    double gk = (sigma_of(I, I.sigma[s], Up) - sigma_of(I, I.sigma[s], Um)) * (0.5 * I.inv_dxi[k]);
-                    g[s] += gk * gk;
+                for (int q = 0; q < I.n_sigma; ++q) {
+                    double gk = (sigma_of(I, I.sigma[q], Up) - sigma_of(I, I.sigma[q], Um)) * (0.5 * I.inv_dxi[k]);
+                    g[q] += gk * gk;
                 }
             }
-            for (int s = 0; s < I.n_sigma; ++s) {
-                g[s] = sqrt(g[s]);
-                if (!(g[s] >= 0.0)) g[s] = 0.0;
-                scr[it.x].g[(long long)s * I.ncell + p] = g[s];
+            for (int q = 0; q < I.n_sigma; ++q) {
+                g[q] = sqrt(g[q]);
+                if (!(g[q] >= 0.0)) g[q] = 0.0;
+                scr[it.x].g[(long long)q * I.ncell + p] = g[q];
             }
         }
-        for (int s = 0; s < 4; ++s) {
-            if (s >= I.n_sigma) break;
-            double m = block_max<double>(g[s], sh);
-            if (threadIdx.x == 0) atomic_max_pos(&scr[it.x].red[1 + s], m);
+        double mx = block_max<double>(s, sh);
+        if (threadIdx.x == 0) atomic_max_pos(&scr[it.x].red[0], mx);
+        for (int q = 0; q < 4; ++q) {
+            if (q >= I.n_sigma) break;
+            double mq = block_max<double>(g[q], sh);
+            if (threadIdx.x == 0) atomic_max_pos(&scr[it.x].red[1 + q], mq);
         }
     }
+}
+
+// Eq. (monitor) at node p from the gradients and the reciprocal instance maxima (0 for a zero maximum)
+template <typename R>
+__device__ __forceinline__ R theta_at(const Inst& I, const Scratch& S, const double* inv, long long p)
+{
+    R t = R(1);
+    for (int q = 0; q < I.n_sigma; ++q) {
+        if (inv[q] > 0.0) {
+            R r = to_r<R>(S.g[(long long)q * I.ncell + p] * inv[q]);
+            t += R(I.alpha[q]) * r * r;
+        }
+    }
+    return sqrt(t);
 }
 
 template <typename R>
@@ -171,31 +208,31 @@ __global__ void monitor_theta_kernel(const Inst* __restrict__ insts, const int2*
         int i0, i1, i2;
         if (!tile_node(I, it.y, 0, i0, i1, i2)) continue;
         const long long p = lin(I, i0, i1, i2);
-        R t = R(1);
-        for (int s = 0; s < I.n_sigma; ++s) {
-            double mx = P.red[1 + s];
-            if (mx > 0.0) {
-                R r = R(P.g[(long long)s * I.ncell + p] / mx);
-                t += R(I.alpha[s]) * r * r;
-            }
-        }
-        reinterpret_cast<R*>(P.th0)[p] = sqrt(t);
+        double inv[4] = { 0, 0, 0, 0 };
+        for (int q = 0; q < I.n_sigma; ++q) inv[q] = P.red[1 + q] > 0.0 ? 1.0 / P.red[1 + q] : 0.0;
+        reinterpret_cast<R*>(P.th0)[p] = theta_at<R>(I, P, inv, p);
     }
 }
 
-// one pass of the low-pass filter, weights (1/2)^(|j|_1 + d) over the 3^d stencil
-template <typename R>
+// one pass of the low-pass filter, weights (1/2)^(|j|_1 + d) over the 3^d stencil; the first
+// pass (FROM_G) forms the monitor function of each stencil node from the gradients directly
+template <typename R, bool FROM_G>
 __global__ void filter_kernel(const Inst* __restrict__ insts, const int2* __restrict__ work, int nwork,
                               const Scratch* __restrict__ scr, int parity)
 {
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
         int2 it = work[wi];
         const Inst& I = insts[it.x];
+        const Scratch& Sc = scr[it.x];
         int i0, i1, i2;
         if (!tile_node(I, it.y, 0, i0, i1, i2)) continue;
         const long long p = lin(I, i0, i1, i2);
-        const R* a = reinterpret_cast<const R*>(parity ? scr[it.x].th1 : scr[it.x].th0);
-        R* dst = reinterpret_cast<R*>(parity ? scr[it.x].th0 : scr[it.x].th1);
+        const R* a = reinterpret_cast<const R*>(parity ? Sc.th1 : Sc.th0);
+        R* dst = reinterpret_cast<R*>(parity ? Sc.th0 : Sc.th1);
+        double inv[4] = { 0, 0, 0, 0 };
+        if (FROM_G)
+            for (int q = 0; q < I.n_sigma; ++q) inv[q] = Sc.red[1 + q] > 0.0 ? 1.0 / Sc.red[1 + q] : 0.0;
+        auto val = [&](long long q) -> R { return FROM_G ? theta_at<R>(I, Sc, inv, q) : a[q]; };
         R acc = R(0);
         int lo3 = I.d == 3 ? -1 : 0, hi3 = I.d == 3 ? 1 : 0;
         const int n0 = I.n[0], n1 = I.n[1];
@@ -204,10 +241,10 @@ __global__ void filter_kernel(const Inst* __restrict__ insts, const int2* __rest
             for (int j2 = -1; j2 <= 1; ++j2) {
                 R row = R(0);
                 if (inner) {
-                    const R* q = a + p + (long long)j3 * n0 * n1 + j2 * n0;
-                    row = R(0.25) * (q[-1] + q[1]) + R(0.5) * q[0];
+                    const long long q = p + (long long)j3 * n0 * n1 + j2 * n0;
+                    row = R(0.25) * (val(q - 1) + val(q + 1)) + R(0.5) * val(q);
                 } else {
-                    for (int j1 = -1; j1 <= 1; ++j1) row += (j1 == 0 ? R(0.5) : R(0.25)) * a[s_map(I, i0 + j1, i1 + j2, i2 + j3)];
+                    for (int j1 = -1; j1 <= 1; ++j1) row += (j1 == 0 ? R(0.5) : R(0.25)) * val(s_map(I, i0 + j1, i1 + j2, i2 + j3));
                 }
                 acc += (j2 == 0 ? R(0.5) : R(0.25)) * (j3 == 0 ? (I.d == 3 ? R(0.5) : R(1)) : R(0.25)) * row;
             }
@@ -215,53 +252,84 @@ __global__ void filter_kernel(const Inst* __restrict__ insts, const int2* __rest
     }
 }
 
-// one Jacobi sweep: x_i = sum_k (T_{k+} x_{i+e_k} + T_{k-} x_{i-e_k}) / dxi_k^2 / sum_k (T_{k+} + T_{k-}) / dxi_k^2
-template <typename R>
+// one Jacobi sweep: x_i = sum_k (T_{k+} x_{i+e_k} + T_{k-} x_{i-e_k}) / dxi_k^2 / sum_k (T_{k+} + T_{k-}) / dxi_k^2;
+// the last sweep also forms the limiter bounds of Sec. 4 from x^[mu] - x^n (per-instance minimum)
+template <typename R, bool LAST>
 __global__ void jacobi_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
                               const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr, int sweep,
                               int theta_sel)
 {
+    __shared__ double sh[32];
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
         int2 it = work[wi];
         const Inst& I = insts[it.x];
         int i[3];
-        if (!tile_node(I, it.y, 0, i[0], i[1], i[2])) continue;
-        const long long p = lin(I, i[0], i[1], i[2]);
+        const bool valid = tile_node(I, it.y, 0, i[0], i[1], i[2]);
         ES_PTRS(P);
-        const Scratch& Sc = scr[it.x];
-        const R* th = reinterpret_cast<const R*>(theta_sel ? Sc.th1 : Sc.th0);
-        const double* xs = sweep == 0 ? P.x : (sweep % 2 == 1 ? Sc.xa : Sc.xb);
-        double* xd_ = sweep % 2 == 0 ? Sc.xa : Sc.xb;
-        double tc = to_d(th[p]);
-        double num[3] = { 0, 0, 0 }, den = 0.0;
-        bool inner = true;
-        for (int k = 0; k < I.d; ++k) inner = inner && i[k] >= 1 && i[k] < I.n[k] - 1;
-        long long stride = 1;
-        for (int k = 0; k < I.d; ++k) {
-            double tp, tm, xp[3], xm[3];
-            if (inner) {
-                tp = 0.5 * (tc + to_d(th[p + stride]));
-                tm = 0.5 * (tc + to_d(th[p - stride]));
-                for (int j = 0; j < I.d; ++j) {
-                    xp[j] = xs[(long long)j * I.ncell + p + stride];
-                    xm[j] = xs[(long long)j * I.ncell + p - stride];
+        double bnd = 1.0;
+        if (valid) {
+            const long long p = lin(I, i[0], i[1], i[2]);
+            const Scratch& Sc = scr[it.x];
+            const R* th = reinterpret_cast<const R*>(theta_sel ? Sc.th1 : Sc.th0);
+            const double* xs = sweep == 0 ? P.x : (sweep % 2 == 1 ? Sc.xa : Sc.xb);
+            double* xd_ = sweep % 2 == 0 ? Sc.xa : Sc.xb;
+            double tc = to_d(th[p]);
+            double num[3] = { 0, 0, 0 }, den = 0.0;
+            bool inner = true;
+            for (int k = 0; k < I.d; ++k) inner = inner && i[k] >= 1 && i[k] < I.n[k] - 1;
+            long long stride = 1;
+            for (int k = 0; k < I.d; ++k) {
+                double tp, tm, xp[3], xm[3];
+                if (inner) {
+                    tp = 0.5 * (tc + to_d(th[p + stride]));
+                    tm = 0.5 * (tc + to_d(th[p - stride]));
+                    for (int j = 0; j < I.d; ++j) {
+                        xp[j] = xs[(long long)j * I.ncell + p + stride];
+                        xm[j] = xs[(long long)j * I.ncell + p - stride];
+                    }
+                } else {
+                    int ip[3] = { i[0], i[1], i[2] }, im[3] = { i[0], i[1], i[2] };
+                    ip[k] += 1;
+                    im[k] -= 1;
+                    tp = 0.5 * (tc + to_d(th[s_map(I, ip[0], ip[1], ip[2])]));
+                    tm = 0.5 * (tc + to_d(th[s_map(I, im[0], im[1], im[2])]));
+                    x_at<false>(I, xs, ip[0], ip[1], ip[2], xp);
+                    x_at<false>(I, xs, im[0], im[1], im[2], xm);
                 }
-            } else {
-                int ip[3] = { i[0], i[1], i[2] }, im[3] = { i[0], i[1], i[2] };
-                ip[k] += 1;
-                im[k] -= 1;
-                tp = 0.5 * (tc + to_d(th[s_map(I, ip[0], ip[1], ip[2])]));
-                tm = 0.5 * (tc + to_d(th[s_map(I, im[0], im[1], im[2])]));
-                x_at<false>(I, xs, ip[0], ip[1], ip[2], xp);
-                x_at<false>(I, xs, im[0], im[1], im[2], xm);
+                stride *= I.n[k];
+                double h2 = I.inv_dxi[k] * I.inv_dxi[k];
+                for (int j = 0; j < I.d; ++j) num[j] += (tp * xp[j] + tm * xm[j]) * h2;
+                den += (tp + tm) * h2;
             }
-            stride *= I.n[k];
-            double h2 = I.inv_dxi[k] * I.inv_dxi[k];
-            for (int j = 0; j < I.d; ++j) num[j] += (tp * xp[j] + tm * xm[j]) * h2;
-            den += (tp + tm) * h2;
+            double id = 1.0 / den;
+            double xnew[3];
+            for (int j = 0; j < I.d; ++j) {
+                xnew[j] = num[j] * id;
+                xd_[(long long)j * I.ncell + p] = xnew[j];
+            }
+            if (LAST) {
+                for (int k = 0; k < I.d; ++k) {
+                    double xc = P.x[(long long)k * I.ncell + p];
+                    double dx = xnew[k] - xc;
+                    int nb[3] = { i[0], i[1], i[2] };
+                    double xn[3];
+                    if (dx < 0.0) {
+                        nb[k] -= 1;
+                        x_at<false>(I, P.x, nb[0], nb[1], nb[2], xn);
+                        bnd = fmin(bnd, -(xc - xn[k]) / (2.0 * dx));
+                    } else if (dx > 0.0) {
+                        nb[k] += 1;
+                        x_at<false>(I, P.x, nb[0], nb[1], nb[2], xn);
+                        bnd = fmin(bnd, (xn[k] - xc) / (2.0 * dx));
+                    }
+                }
+                if (!(bnd >= 0.0)) bnd = 0.0;
+            }
         }
-        double id = 1.0 / den;
-        for (int j = 0; j < I.d; ++j) xd_[(long long)j * I.ncell + p] = num[j] * id;
+        if (LAST) {
+            double m = block_min_pos(bnd, sh);
+            if (threadIdx.x == 0) atomic_min_pos(&scr[it.x].red[5], m);
+        }
     }
 }
 
@@ -418,18 +486,25 @@ void launch_monitor_theta(bool mixed, int grid, cudaStream_t st, const Inst* ins
     else monitor_theta_kernel<double><<<grid, NODE_TPB, 0, st>>>(insts, work, nwork, scr);
 }
 
-void launch_filter(bool mixed, int grid, cudaStream_t st, const Inst* insts, const int2* work, int nwork,
+void launch_filter(bool mixed, bool from_g, int grid, cudaStream_t st, const Inst* insts, const int2* work, int nwork,
                    const Scratch* scr, int parity)
 {
-    if (mixed) filter_kernel<float><<<grid, NODE_TPB, 0, st>>>(insts, work, nwork, scr, parity);
-    else filter_kernel<double><<<grid, NODE_TPB, 0, st>>>(insts, work, nwork, scr, parity);
+    if (mixed) {
+        if (from_g) filter_kernel<float, true><<<grid, NODE_TPB, 0, st>>>(insts, work, nwork, scr, parity);
+        else filter_kernel<float, false><<<grid, NODE_TPB, 0, st>>>(insts, work, nwork, scr, parity);
+    } else {
+        if (from_g) filter_kernel<double, true><<<grid, NODE_TPB, 0, st>>>(insts, work, nwork, scr, parity);
+        else filter_kernel<double, false><<<grid, NODE_TPB, 0, st>>>(insts, work, nwork, scr, parity);
+    }
 }
 
-void launch_jacobi(bool mixed, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
+void launch_jacobi(bool mixed, bool last, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
                    const StagePtrs* table, const int2* work, int nwork, const Scratch* scr, int sweep, int theta_sel)
 {
-    if (mixed) jacobi_kernel<float><<<grid, NODE_TPB, 0, st>>>(insts, single, table, work, nwork, scr, sweep, theta_sel);
-    else jacobi_kernel<double><<<grid, NODE_TPB, 0, st>>>(insts, single, table, work, nwork, scr, sweep, theta_sel);
+#define JL(R, LS) jacobi_kernel<R, LS><<<grid, NODE_TPB, 0, st>>>(insts, single, table, work, nwork, scr, sweep, theta_sel)
+    if (mixed) { if (last) JL(float, true); else JL(float, false); }
+    else { if (last) JL(double, true); else JL(double, false); }
+#undef JL
 }
 
 }  // namespace es

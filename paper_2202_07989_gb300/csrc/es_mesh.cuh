@@ -6,15 +6,13 @@
 namespace es {
 
 __global__ void red_init_kernel(const Scratch* scr, int ninst);
-__global__ void cfl_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work, int nwork,
-                           const Scratch* scr);
-__global__ void monitor_grad_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work,
-                                    int nwork, const Scratch* scr);
+__global__ void cfl_grad_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work,
+                                int nwork, const Scratch* scr);
 void launch_monitor_theta(bool mixed, int grid, cudaStream_t st, const Inst* insts, const int2* work, int nwork,
                           const Scratch* scr);
-void launch_filter(bool mixed, int grid, cudaStream_t st, const Inst* insts, const int2* work, int nwork,
+void launch_filter(bool mixed, bool from_g, int grid, cudaStream_t st, const Inst* insts, const int2* work, int nwork,
                    const Scratch* scr, int parity);
-void launch_jacobi(bool mixed, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
+void launch_jacobi(bool mixed, bool last, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
                    const StagePtrs* table, const int2* work, int nwork, const Scratch* scr, int sweep, int theta_sel);
 __global__ void limiter_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work, int nwork,
                                const Scratch* scr);

@@ -139,10 +139,11 @@ def test_rk_step_small(d, N):
 
 @pytest.mark.parametrize("d,N", [(2, 1), (2, 2), (3, 1)])
 @pytest.mark.parametrize("bc", ["periodic", "mixed"])
-def test_mesh_redistribute(d, N, bc):
+@pytest.mark.parametrize("mu,nf", [(5, 3), (0, 0), (1, 1)])
+def test_mesh_redistribute(d, N, bc, mu, nf):
     torch = need_gpu()
     pb, JU, J, x, xdot = case(d, N, GRIDS[d], bc, seed=5, jump=True)
-    pb = pb.with_(mu=5, nf=3, sigma=(W.SIG_RHO, W.SIG_P), alpha=(100.0, 30.0))
+    pb = pb.with_(mu=mu, nf=nf, sigma=(W.SIG_RHO, W.SIG_P), alpha=(100.0, 30.0))
     o = Oracle(pb)
     xd_o, dt_o, dtau_o = o.mesh_redistribute(JU, J, x)
     ctx = _ctx(pb)
