@@ -370,6 +370,20 @@ def main_ours(args):
         forms["batched_mixed"] = batched
         prof_b = kernel_profile(bt, kb, torch)
 
+    # 3D forms (mixed): octant Riemann problem 128^3 (N = 1) and shock-bubble 128 x 64 x 64 (N = 2)
+    if not args.no_3d:
+        for name, (p3, U3, x3) in (("mixed_3d_riemann_128^3", W.riemann_3d(128)),
+                                   ("mixed_3d_shock_bubble_128x64x64", W.shock_bubble_3d(64))):
+            r3 = Single(p3, U3, x3, es.MIXED, torch)
+            r3.step()
+            r3.reset()
+            r3.capture()
+            r3.reset()
+            k3 = max(3, min(args.steps, 8))
+            t3 = time_steps(r3, k3, 2, torch, flush)
+            forms[name] = {"value": p3.ncell * 3 * k3 / t3, "ms_per_step": 1e3 * t3 / k3, "cells": p3.ncell}
+            del r3
+
     # end to end: C-ABI call on pinned host buffers, copies inside the timed region
     e2e = None
     if rank == 0:
@@ -482,14 +496,25 @@ def main_kernel_case(args):
     from paper_2202_07989_gb300 import build as B
     B.build()
     from paper_2202_07989_gb300 import es, workloads as W
-    nx, ny = [int(v) for v in args.kernel_case.split("x")]
-    pb, U, x = W.shock_bubble_2d(nx, ny, length=(2.0, 1.0))
+    if args.kernel_case.startswith("3d:"):
+        # 3D octant Riemann problem (single component) or water/air (two components)
+        kind, n = args.kernel_case[3:].split(":")
+        pb, U, x = W.riemann_3d(int(n)) if kind == "riemann" else W.water_air_3d(int(n))
+    else:
+        nx, ny = [int(v) for v in args.kernel_case.split("x")]
+        pb, U, x = W.shock_bubble_2d(nx, ny, length=(2.0, 1.0))
     r = Single(pb, U, x, es.MIXED if args.kernel_form == "mixed" else es.FP64, torch)
     for _ in range(args.kernel_steps):
         r.step()
     torch.cuda.synchronize()
     assert r.ctx.es_poll_status() == 0
-    print("kernel case %s %s: %d steps done" % (args.kernel_case, args.kernel_form, args.kernel_steps))
+    out = {"case": args.kernel_case, "form": args.kernel_form, "steps": args.kernel_steps}
+    if args.kernel_time:
+        r.reset()
+        prof = kernel_profile(r, args.kernel_time, torch)
+        out["kernel_ms_per_step"] = {k: v[0] / args.kernel_time for k, v in prof.items() if v[1]}
+        out["launches_per_step"] = {k: v[1] / args.kernel_time for k, v in prof.items() if v[1]}
+    print(json.dumps(out))
 
 
 def main():
@@ -500,10 +525,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-3d", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--kernel-case", default=None, help="NXxNY: only run a few steps of that grid (profiling)")
     ap.add_argument("--kernel-form", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--kernel-steps", type=int, default=2)
+    ap.add_argument("--kernel-time", type=int, default=0, help="also time this many eager steps per kernel class")
     args = ap.parse_args()
     if args.kernel_case:
         return main_kernel_case(args)

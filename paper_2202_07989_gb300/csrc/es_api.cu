@@ -155,6 +155,15 @@ Inst make_inst(const es_config& g)
         I.tiles[k] = ((I.n[k] + S - 1) / S) * ((I.n[adim] + WT - 1) / WT) * nb;
     }
     I.ntile_nodes = node_tiles(I, 0);
+    for (int l = 0; l < 2; ++l) {
+        I.f_gamma[l] = (float)I.gamma[l];
+        I.f_cv[l] = (float)I.cv[l];
+        I.f_Rs[l] = (float)I.Rs[l];
+        I.f_cvG[l] = (float)I.cvG[l];
+    }
+    I.f_pinf_tot = (float)I.pinf_tot;
+    for (int q = 0; q < 3; ++q) I.f_chi[q] = (float)I.chi[q];
+    I.f_eps = (float)I.weno_eps;
     return I;
 }
 
@@ -332,7 +341,7 @@ void launch_mesh(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStream
         launch_metrics(c, Q, tab, st);
     }
     int gc = node_grid(c, c->n_cell);
-    cfl_grad_kernel<<<gc, NODE_TPB, 0, st>>>(c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
+    launch_cfl_grad(c->mixed, gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
     int nf = c->hI[0].nf, mu = c->hI[0].mu;
     if (nf == 0) launch_monitor_theta(c->mixed, gc, st, c->dI, c->w_cell, c->n_cell, c->dS);
     for (int f = 0; f < nf; ++f) launch_filter(c->mixed, f == 0, gc, st, c->dI, c->w_cell, c->n_cell, c->dS, f % 2);
@@ -340,7 +349,7 @@ void launch_mesh(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStream
     for (int s = 0; s < mu; ++s)
         launch_jacobi(c->mixed, s == mu - 1, gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS, s, th_sel);
     if (mu == 0) limiter_kernel<<<gc, NODE_TPB, 0, st>>>(c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
-    xdot_kernel<<<gc, NODE_TPB, 0, st>>>(c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
+    launch_xdot(c->mixed, gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
 }
 
 __global__ void time_acc_kernel(double* t, const double* dt_dtau) { *t += dt_dtau[0]; }

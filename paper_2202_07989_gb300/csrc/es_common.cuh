@@ -39,6 +39,33 @@ struct Inst {
     int mu, nf;
     int tiles[3];             // flux tiles per direction
     int ntile_nodes;          // 1D node tiles for node-wise kernels
+    // binary32 copies of the physical and scheme constants for the FP32 arithmetic of the
+    // mixed form (converting the binary64 ones in the kernels would use the FP64 pipe)
+    float f_gamma[2], f_cv[2], f_Rs[2], f_cvG[2], f_pinf_tot, f_chi[3], f_eps;
+};
+
+// the constants of an instance in the compute type R
+template <typename R>
+struct Cst;
+template <>
+struct Cst<double> {
+    static __device__ __forceinline__ double gamma(const Inst& I, int l) { return I.gamma[l]; }
+    static __device__ __forceinline__ double cv(const Inst& I, int l) { return I.cv[l]; }
+    static __device__ __forceinline__ double Rs(const Inst& I, int l) { return I.Rs[l]; }
+    static __device__ __forceinline__ double cvG(const Inst& I, int l) { return I.cvG[l]; }
+    static __device__ __forceinline__ double pinf(const Inst& I) { return I.pinf_tot; }
+    static __device__ __forceinline__ double chi(const Inst& I, int q) { return I.chi[q]; }
+    static __device__ __forceinline__ double eps(const Inst& I) { return I.weno_eps; }
+};
+template <>
+struct Cst<float> {
+    static __device__ __forceinline__ float gamma(const Inst& I, int l) { return I.f_gamma[l]; }
+    static __device__ __forceinline__ float cv(const Inst& I, int l) { return I.f_cv[l]; }
+    static __device__ __forceinline__ float Rs(const Inst& I, int l) { return I.f_Rs[l]; }
+    static __device__ __forceinline__ float cvG(const Inst& I, int l) { return I.f_cvG[l]; }
+    static __device__ __forceinline__ float pinf(const Inst& I) { return I.f_pinf_tot; }
+    static __device__ __forceinline__ float chi(const Inst& I, int q) { return I.f_chi[q]; }
+    static __device__ __forceinline__ float eps(const Inst& I) { return I.f_eps; }
 };
 
 // per-call device pointers of one instance: the stage input, the metric target,

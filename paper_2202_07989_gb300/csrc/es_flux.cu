@@ -182,8 +182,9 @@ __device__ __forceinline__ void load_U_r(const Inst& I, const double* __restrict
 // (2) every distinct two-point flux F(U_j, U_{j+m}) (m = 1, 2, 3) of the tile, once; (3)
 // per interface the 2w-order EC flux as sum_m alpha_m sum_s of the stored pairs, the GCL
 // flux of J xi_k/t and the ES dissipation; (4) divergence and output / RK stage.
+// FP32 tiles: 3 CTAs per SM in 2D (<= 85 registers), 2 in 3D; FP64 tiles: 1 (FP64-pipe bound)
 template <int D, int NS, typename R, int S, int WT>
-__global__ void __launch_bounds__(FLUX_TPB) flux_kernel(FluxLaunch L)
+__global__ void __launch_bounds__(FLUX_TPB, (sizeof(R) == 4 ? (D == 2 ? 3 : 2) : 1)) flux_kernel(FluxLaunch L)
 {
     using Y = Lay<D, NS>;
     using TL = Tile<S, WT>;
@@ -232,8 +233,8 @@ __global__ void __launch_bounds__(FLUX_TPB) flux_kernel(FluxLaunch L)
             R v[D], v2 = R(0);
 #pragma unroll
             for (int m = 0; m < D; ++m) { v[m] = U[NS + m] * irho; v2 += v[m] * v[m]; }
-            R cvr = R(I.cv[0]) * U[0] + (NS == 2 ? R(I.cv[1]) * U[1] : R(0));
-            R rhoe_p = U[NS + D] - R(0.5) * rho * v2 - R(I.pinf_tot);
+            R cvr = Cst<R>::cv(I, 0) * U[0] + (NS == 2 ? Cst<R>::cv(I, 1) * U[1] : R(0));
+            R rhoe_p = U[NS + D] - R(0.5) * rho * v2 - Cst<R>::pinf(I);
             R beta = cvr * Ar<R>::rcp(rhoe_p);
             bool bad = !(rhoe_p > R(0)) || !(U[0] > R(0)) || (NS == 2 && !(U[1] > R(0)));
             if (bad) {
@@ -252,18 +253,18 @@ __global__ void __launch_bounds__(FLUX_TPB) flux_kernel(FluxLaunch L)
             nr[Y::LB * NN + node] = lb;
             if (NS == 2) {
                 R T = Ar<R>::rcp(beta);
-                R rr = R(I.Rs[0]) * U[0] + R(I.Rs[1]) * U[1];
-                nr[(Y::X + 0) * NN + node] = rr * T - R(I.pinf_tot);                 // p
+                R rr = Cst<R>::Rs(I, 0) * U[0] + Cst<R>::Rs(I, 1) * U[1];
+                nr[(Y::X + 0) * NN + node] = rr * T - Cst<R>::pinf(I);                 // p
                 nr[(Y::X + 1) * NN + node] = rho;                                    // rho
                 nr[(Y::X + 2) * NN + node] = Ar<R>::lg(bad ? R(1) : rho);           // ln rho
                 nr[(Y::X + 3) * NN + node] = rr * irho;                              // R_mix
-                nr[(Y::X + 4) * NN + node] = (R(I.cvG[0]) * U[0] + R(I.cvG[1]) * U[1]) * Ar<R>::rcp(cvr);  // Gamma_mix
+                nr[(Y::X + 4) * NN + node] = (Cst<R>::cvG(I, 0) * U[0] + Cst<R>::cvG(I, 1) * U[1]) * Ar<R>::rcp(cvr);  // Gamma_mix
             }
             // entropy variables V_l = c_{v,l} ln beta + R_l ln rho_l - |v|^2 beta/2 + c_{v,l} Gamma_l
             R hv = R(0.5) * v2 * beta;
             R Vn[NC];
-            Vn[0] = R(I.cv[0]) * lb + R(I.Rs[0]) * lr0 - hv + R(I.cvG[0]);
-            if (NS == 2) Vn[1] = R(I.cv[1]) * lb + R(I.Rs[1]) * lr1 - hv + R(I.cvG[1]);
+            Vn[0] = Cst<R>::cv(I, 0) * lb + Cst<R>::Rs(I, 0) * lr0 - hv + Cst<R>::cvG(I, 0);
+            if (NS == 2) Vn[1] = Cst<R>::cv(I, 1) * lb + Cst<R>::Rs(I, 1) * lr1 - hv + Cst<R>::cvG(I, 1);
 #pragma unroll
             for (int m = 0; m < D; ++m) Vn[NS + m] = v[m] * beta;
             Vn[NS + D] = -beta;
@@ -311,7 +312,7 @@ __global__ void __launch_bounds__(FLUX_TPB) flux_kernel(FluxLaunch L)
                 R al = nr[(Y::RHO + q) * NN + l], ar = nr[(Y::RHO + q) * NN + rr];
                 lr[q] = Ar<R>::lmean(al, ar, nr[(Y::LRHO + q) * NN + l], nr[(Y::LRHO + q) * NN + rr]);
                 rt += lr[q];
-                rra += R(I.Rs[q]) * (al + ar);
+                rra += Cst<R>::Rs(I, q) * (al + ar);
             }
             R bl = nr[Y::B * NN + l], br = nr[Y::B * NN + rr];
             R is = Ar<R>::rcp(bl + br);
@@ -319,7 +320,7 @@ __global__ void __launch_bounds__(FLUX_TPB) flux_kernel(FluxLaunch L)
             R Pp = rra * is;                                   // sum R_l {rho_l} / {beta}
             R Ep = -R(0.5) * rt * v2b + rt * vbsq;
 #pragma unroll
-            for (int q = 0; q < NS; ++q) Ep += lr[q] * R(I.cv[q]) * ilb;
+            for (int q = 0; q < NS; ++q) Ep += lr[q] * Cst<R>::cv(I, q) * ilb;
 #pragma unroll
             for (int q = 0; q < NS; ++q) pf[q * NP + t] = ut * lr[q];
 #pragma unroll
@@ -397,7 +398,7 @@ __global__ void __launch_bounds__(FLUX_TPB) flux_kernel(FluxLaunch L)
                 }
                 R cb, H, sa, se = R(0), ssh, Y1 = R(1), Y2 = R(0), D11 = R(0), D12 = R(0), D21 = R(0), D22 = R(0), e1 = R(0), e2 = R(0);
                 if constexpr (NS == 1) {
-                    const R G = R(I.gamma[0]), Rg = R(I.Rs[0]), cv = R(I.cv[0]);
+                    const R G = Cst<R>::gamma(I, 0), Rg = Cst<R>::Rs(I, 0), cv = Cst<R>::cv(I, 0);
                     const R rb = lr_c[0];
                     cb = Ar<R>::sq(Rg * G * Tb);
                     H = G * cv * Tb + R(0.5) * vv;
@@ -409,7 +410,7 @@ __global__ void __launch_bounds__(FLUX_TPB) flux_kernel(FluxLaunch L)
                     const R Rb = R(0.5) * (NR(Y::X + 3, 2) + NR(Y::X + 3, 3));
                     const R Gb = R(0.5) * (NR(Y::X + 4, 2) + NR(Y::X + 4, 3));
                     const R pb = R(0.5) * (NR(Y::X + 0, 2) + NR(Y::X + 0, 3));
-                    R rh = pb + R(I.pinf_tot) + (R(I.cv[0]) * lr_c[0] + R(I.cv[1]) * lr_c[1]) * Tb;
+                    R rh = pb + Cst<R>::pinf(I) + (Cst<R>::cv(I, 0) * lr_c[0] + Cst<R>::cv(I, 1) * lr_c[1]) * Tb;
                     R irb = Ar<R>::rcp(rb);
                     Y1 = lr_c[0] * irb;
                     Y2 = lr_c[1] * irb;
@@ -418,21 +419,21 @@ __global__ void __launch_bounds__(FLUX_TPB) flux_kernel(FluxLaunch L)
                     const R pre = Ar<R>::sq(rb * Ar<R>::rcp(Gb * Rb));
                     sa = pre * R(0.70710678118654752440);
                     ssh = Ar<R>::sq(rb * Tb);
-                    const R R1 = R(I.Rs[0]), R2 = R(I.Rs[1]);
+                    const R R1 = Cst<R>::Rs(I, 0), R2 = Cst<R>::Rs(I, 1);
                     R sy = Ar<R>::sq(Y1 * Y2), sg = Ar<R>::sq(Gb - R(1));
                     D11 = -pre * sy * Ar<R>::sq(Gb * R2 * Ar<R>::rcp(R1));
                     D21 = pre * sy * Ar<R>::sq(Gb * R1 * Ar<R>::rcp(R2));
                     D12 = pre * Y1 * sg;
                     D22 = pre * Y2 * sg;
                     R igm = Ar<R>::rcp(Gb - R(1));
-                    e1 = R(0.5) * vv - (R(I.cv[0]) + R1 - Gb * R(I.cv[0])) * Tb * igm;
-                    e2 = R(0.5) * vv - (R(I.cv[1]) + R2 - Gb * R(I.cv[1])) * Tb * igm;
+                    e1 = R(0.5) * vv - (Cst<R>::cv(I, 0) + R1 - Gb * Cst<R>::cv(I, 0)) * Tb * igm;
+                    e2 = R(0.5) * vv - (Cst<R>::cv(I, 1) + R2 - Gb * Cst<R>::cv(I, 1)) * Tb * igm;
                 }
                 const R lam = Ar<R>::ab(to_r<R>(Gt) + Ln * vh[0]) + Ln * cb;
                 // round-off band of [[W_m]]: delta ||r_m|| (||V_i|| + ||V_i+1||)
                 const R nvb = NR(Y::VN, 2) + NR(Y::VN, 3);
                 const R band2 = R(YBand<R>::value * YBand<R>::value) * nvb * nvb;
-                const R ch1 = R(I.chi[0]), ch2 = R(I.chi[1]), ch3 = R(I.chi[2]), eps = R(I.weno_eps);
+                const R ch1 = Cst<R>::chi(I, 0), ch2 = Cst<R>::chi(I, 1), ch3 = Cst<R>::chi(I, 2), eps = Cst<R>::eps(I);
                 R Fd[NC];
 #pragma unroll
                 for (int q = 0; q < NC; ++q) Fd[q] = R(0);

@@ -5,6 +5,8 @@
 // filter run in the compute type of the context (FP32 in the mixed form).
 #include "es_mesh.cuh"
 
+#include <type_traits>
+
 namespace es {
 
 // reduction slots per instance
@@ -119,9 +121,60 @@ __device__ inline void node_metrics2d(const Inst& I, const double* __restrict__ 
     m[1][1] = 0.5 * d1[0] * I.inv_dxi[0];
 }
 
+// conserved point state at a node in the compute type (ghost maps of load_U)
+template <typename R>
+__device__ __forceinline__ void load_U_t(const Inst& I, const double* __restrict__ JU, const double* __restrict__ J,
+                                         int i0, int i1, int i2, R* U)
+{
+    if constexpr (std::is_same<R, double>::value) {
+        load_U(I, JU, J, i0, i1, i2, U);
+    } else {
+        int i[3] = { i0, i1, i2 };
+        int neg = -1;
+        for (int k = 0; k < I.d; ++k) {
+            if (i[k] >= 0 && i[k] < I.n[k]) continue;
+            int gi, side;
+            int t = map_line(I, k, i[k], gi, side);
+            if (t == 2) {
+                for (int q = 0; q < I.nc; ++q) U[q] = to_r<R>(I.inflow[k][side][q]);
+                return;
+            }
+            if (t == 1) neg = k;
+            i[k] = gi;
+        }
+        long long id = lin(I, i[0], i[1], I.d == 3 ? i[2] : 0);
+        R inv = R(1) / to_r<R>(J[id]);
+        for (int q = 0; q < I.nc; ++q) U[q] = to_r<R>(JU[q * I.ncell + id]) * inv;
+        if (neg >= 0) U[I.N + neg] = -U[I.N + neg];
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ R sigma_t(const Inst& I, int kind, const R* U)
+{
+    const R rho = I.N == 2 ? U[0] + U[1] : U[0];
+    switch (kind) {
+    case SIG_RHO1: return U[0];
+    case SIG_RHO2: return I.N == 2 ? U[1] : R(0);
+    case SIG_Y2: return I.N == 2 ? U[1] / rho : R(0);
+    case SIG_V1: return U[I.N] / rho;
+    case SIG_P: {
+        R cvr = R(0), rr = R(0), v2 = R(0);
+        for (int l = 0; l < I.N; ++l) { cvr += to_r<R>(I.cv[l]) * U[l]; rr += to_r<R>(I.Rs[l]) * U[l]; }
+        for (int m = 0; m < I.d; ++m) { R v = U[I.N + m] / rho; v2 += v * v; }
+        R T = (U[I.N + I.d] - R(0.5) * rho * v2 - to_r<R>(I.pinf_tot)) / cvr;
+        return rr * T - to_r<R>(I.pinf_tot);
+    }
+    default: return rho;
+    }
+}
+
 // one pass over the nodes: the CFL spectral-radius sum of Eq. (cfl) at x^n and the
 // monitor gradients |grad_xi sigma_s| (second-order central differences); per-instance
-// maxima by atomics on the non-negative bit patterns
+// maxima by atomics on the non-negative bit patterns.  R = float in the mixed form (the
+// time step is a bound and the monitor is an FP32 quantity there); the metrics are
+// formed in FP64.
+template <typename R>
 __global__ void cfl_grad_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
                                 const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr)
 {
@@ -135,12 +188,18 @@ __global__ void cfl_grad_kernel(const Inst* __restrict__ insts, StagePtrs single
         const long long p = valid ? lin(I, i[0], i[1], i[2]) : 0;
         double s = 0.0, g[4] = { 0, 0, 0, 0 };
         if (valid) {
-            double U[MAXC], rl[2], v[3], T, pr, rho;
-            load_U(I, P.JU, P.J, i[0], i[1], i[2], U);
-            prim(I, U, rl, v, T, pr, rho);
-            double a = 0.0, gm = 0.0, cvr = 0.0;
-            for (int l = 0; l < I.N; ++l) { a += (I.gamma[l] - 1.0) * I.cv[l] * rl[l]; gm += I.gamma[l] * I.cv[l] * rl[l]; cvr += I.cv[l] * rl[l]; }
-            double c = sqrt((a / rho) * (gm / cvr) * T);
+            R U[MAXC];
+            load_U_t<R>(I, P.JU, P.J, i[0], i[1], i[2], U);
+            R rho = U[0] + (I.N == 2 ? U[1] : R(0));
+            R v[3], v2 = R(0), cvr = R(0), a = R(0), gm = R(0);
+            for (int m = 0; m < I.d; ++m) { v[m] = U[I.N + m] / rho; v2 += v[m] * v[m]; }
+            for (int l = 0; l < I.N; ++l) {
+                a += to_r<R>((I.gamma[l] - 1.0) * I.cv[l]) * U[l];
+                gm += to_r<R>(I.gamma[l] * I.cv[l]) * U[l];
+                cvr += to_r<R>(I.cv[l]) * U[l];
+            }
+            R T = (U[I.N + I.d] - R(0.5) * rho * v2 - to_r<R>(I.pinf_tot)) / cvr;
+            R c = sqrt((a / rho) * (gm / cvr) * T);
             double m[3][3];
             if (I.d == 2) {
                 node_metrics2d(I, P.x, i[0], i[1], m);
@@ -149,26 +208,30 @@ __global__ void cfl_grad_kernel(const Inst* __restrict__ insts, StagePtrs single
                 for (int k = 0; k < 3; ++k)
                     for (int j = 0; j < 3; ++j) m[k][j] = scr[it.x].M[(long long)(k * 4 + 1 + j) * I.npad + pid];
             }
+            const R Jp = to_r<R>(P.J[p]);
+            R sr = R(0);
             for (int k = 0; k < I.d; ++k) {
-                double L2 = 0.0, vn = 0.0;
-                for (int j = 0; j < I.d; ++j) { L2 += m[k][j] * m[k][j]; vn += m[k][j] * v[j]; }
-                s += (fabs(vn) + c * sqrt(L2)) / P.J[p] * I.inv_dxi[k];
+                R L2 = R(0), vn = R(0);
+                for (int j = 0; j < I.d; ++j) { R mk = to_r<R>(m[k][j]); L2 += mk * mk; vn += mk * v[j]; }
+                sr += (fabs(vn) + c * sqrt(L2)) / Jp * to_r<R>(I.inv_dxi[k]);
             }
+            s = to_d(sr);
             if (!(s >= 0.0)) s = 0.0;
+            R gr[4] = { R(0), R(0), R(0), R(0) };
             for (int k = 0; k < I.d; ++k) {
                 int ip[3] = { i[0], i[1], i[2] }, im[3] = { i[0], i[1], i[2] };
                 ip[k] += 1;
                 im[k] -= 1;
-                double Up[MAXC], Um[MAXC];
-                load_U(I, P.JU, P.J, ip[0], ip[1], ip[2], Up);
-                load_U(I, P.JU, P.J, im[0], im[1], im[2], Um);
+                R Up[MAXC], Um[MAXC];
+                load_U_t<R>(I, P.JU, P.J, ip[0], ip[1], ip[2], Up);
+                load_U_t<R>(I, P.JU, P.J, im[0], im[1], im[2], Um);
                 for (int q = 0; q < I.n_sigma; ++q) {
-                    double gk = (sigma_of(I, I.sigma[q], Up) - sigma_of(I, I.sigma[q], Um)) * (0.5 * I.inv_dxi[k]);
-                    g[q] += gk * gk;
+                    R gk = (sigma_t<R>(I, I.sigma[q], Up) - sigma_t<R>(I, I.sigma[q], Um)) * to_r<R>(0.5 * I.inv_dxi[k]);
+                    gr[q] += gk * gk;
                 }
             }
             for (int q = 0; q < I.n_sigma; ++q) {
-                g[q] = sqrt(g[q]);
+                g[q] = to_d(R(sqrt(gr[q])));
                 if (!(g[q] >= 0.0)) g[q] = 0.0;
                 scr[it.x].g[(long long)q * I.ncell + p] = g[q];
             }
@@ -190,8 +253,10 @@ __device__ __forceinline__ R theta_at(const Inst& I, const Scratch& S, const dou
     R t = R(1);
     for (int q = 0; q < I.n_sigma; ++q) {
         if (inv[q] > 0.0) {
-            R r = to_r<R>(S.g[(long long)q * I.ncell + p] * inv[q]);
-            t += R(I.alpha[q]) * r * r;
+            R r;
+            if constexpr (std::is_same<R, double>::value) r = S.g[(long long)q * I.ncell + p] * inv[q];
+            else r = to_r<R>(S.g[(long long)q * I.ncell + p]) * to_r<R>(inv[q]);
+            t += to_r<R>(I.alpha[q]) * r * r;
         }
     }
     return sqrt(t);
@@ -301,7 +366,14 @@ __global__ void jacobi_kernel(const Inst* __restrict__ insts, StagePtrs single, 
                 for (int j = 0; j < I.d; ++j) num[j] += (tp * xp[j] + tm * xm[j]) * h2;
                 den += (tp + tm) * h2;
             }
-            double id = 1.0 / den;
+            double id;
+            if constexpr (std::is_same<R, double>::value) {
+                id = 1.0 / den;
+            } else {
+                // FP32 reciprocal refined by one Newton-Raphson step in FP64 (relative error ~1e-14)
+                double r0 = f32_to_f64(__frcp_rn(f64_to_f32(den)));
+                id = r0 * fma(-den, r0, 2.0);
+            }
             double xnew[3];
             for (int j = 0; j < I.d; ++j) {
                 xnew[j] = num[j] * id;
@@ -377,6 +449,7 @@ __global__ void limiter_kernel(const Inst* __restrict__ insts, StagePtrs single,
 
 // Delta t = C / max (or the given step), xdot = Delta_tau (x^[mu] - x^n) / Delta t;
 // out = (Delta t, Delta_tau)
+template <bool FAST>
 __global__ void xdot_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
                             const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr)
 {
@@ -395,9 +468,10 @@ __global__ void xdot_kernel(const Inst* __restrict__ insts, StagePtrs single, co
         int i0, i1, i2;
         if (!tile_node(I, it.y, 0, i0, i1, i2)) continue;
         const long long p = lin(I, i0, i1, i2);
+        const double sc = FAST ? dtau / dt : 0.0;
         for (int j = 0; j < I.d; ++j) {
             long long q = (long long)j * I.ncell + p;
-            P.xdot_out[q] = dtau * (xmu[q] - P.x[q]) / dt;
+            P.xdot_out[q] = FAST ? sc * (xmu[q] - P.x[q]) : dtau * (xmu[q] - P.x[q]) / dt;
         }
     }
 }
@@ -496,6 +570,20 @@ void launch_filter(bool mixed, bool from_g, int grid, cudaStream_t st, const Ins
         if (from_g) filter_kernel<double, true><<<grid, NODE_TPB, 0, st>>>(insts, work, nwork, scr, parity);
         else filter_kernel<double, false><<<grid, NODE_TPB, 0, st>>>(insts, work, nwork, scr, parity);
     }
+}
+
+void launch_cfl_grad(bool mixed, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
+                     const StagePtrs* table, const int2* work, int nwork, const Scratch* scr)
+{
+    if (mixed) cfl_grad_kernel<float><<<grid, NODE_TPB, 0, st>>>(insts, single, table, work, nwork, scr);
+    else cfl_grad_kernel<double><<<grid, NODE_TPB, 0, st>>>(insts, single, table, work, nwork, scr);
+}
+
+void launch_xdot(bool mixed, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
+                 const StagePtrs* table, const int2* work, int nwork, const Scratch* scr)
+{
+    if (mixed) xdot_kernel<true><<<grid, NODE_TPB, 0, st>>>(insts, single, table, work, nwork, scr);
+    else xdot_kernel<false><<<grid, NODE_TPB, 0, st>>>(insts, single, table, work, nwork, scr);
 }
 
 void launch_jacobi(bool mixed, bool last, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,

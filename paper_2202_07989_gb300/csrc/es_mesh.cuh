@@ -6,8 +6,10 @@
 namespace es {
 
 __global__ void red_init_kernel(const Scratch* scr, int ninst);
-__global__ void cfl_grad_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work,
-                                int nwork, const Scratch* scr);
+void launch_cfl_grad(bool mixed, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
+                     const StagePtrs* table, const int2* work, int nwork, const Scratch* scr);
+void launch_xdot(bool mixed, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
+                 const StagePtrs* table, const int2* work, int nwork, const Scratch* scr);
 void launch_monitor_theta(bool mixed, int grid, cudaStream_t st, const Inst* insts, const int2* work, int nwork,
                           const Scratch* scr);
 void launch_filter(bool mixed, bool from_g, int grid, cudaStream_t st, const Inst* insts, const int2* work, int nwork,
@@ -16,8 +18,6 @@ void launch_jacobi(bool mixed, bool last, int grid, cudaStream_t st, const Inst*
                    const StagePtrs* table, const int2* work, int nwork, const Scratch* scr, int sweep, int theta_sel);
 __global__ void limiter_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work, int nwork,
                                const Scratch* scr);
-__global__ void xdot_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work, int nwork,
-                            const Scratch* scr);
 __global__ void entropy_partial_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work,
                                        int nwork, double* partial);
 __global__ void entropy_final_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int* first_work,

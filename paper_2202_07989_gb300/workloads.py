@@ -284,6 +284,37 @@ def riemann_3d(n: int = 128, seed: int = SEED, mu: int = 10) -> Tuple[Problem, n
     return pb, U, x
 
 
+def shock_bubble_3d(n: int = 128, Ms: float = 1.22, radius: float = 0.2, gamma2: float = 1.648,
+                    rho_ratio: float = 0.138, eps: float = 0.03, mu: int = 10) -> Tuple[Problem, np.ndarray, np.ndarray]:
+    """3D two-component shock-bubble shaped like Example 5.10: (2n, n, n) cells on [0, 2] x [0, 1]^2,
+    gas 1 (Gamma 1.4) at rest with rho = p = 1, a Mach Ms shock at x_1 = 1.4 moving left, a
+    spherical bubble of radius 0.2 at (1, 0.5, 0.5) of gas 2 (density ratio rho_ratio at equal p, T),
+    trace eps of the absent species; reflecting side walls, inflow right, outflow left."""
+    cv1 = 1.0
+    R1 = cv1 * 0.4
+    R2 = R1 / rho_ratio
+    cv2 = R2 / (gamma2 - 1.0)
+    pb = Problem(d=3, N=2, n=(2 * n, n, n), xi_lo=(0.0, 0.0, 0.0), length=(2.0, 1.0, 1.0),
+                 bc=((OUTFLOW, INFLOW), (REFLECT, REFLECT), (REFLECT, REFLECT)),
+                 gamma=(1.4, gamma2), cv=(cv1, cv2), pinf=(0.0, 0.0), es=True, cfl=0.3,
+                 sigma=(SIG_RHO,), alpha=(100.0,), mu=mu, nf=3)
+    rho_s, u_s, p_s = _post_shock(pb, Ms, 1.0, 1.0)
+    x = np.stack(xi_nodes(pb))
+    r2 = (x[0] - 1.0) ** 2 + (x[1] - 0.5) ** 2 + (x[2] - 0.5) ** 2
+    inside = r2 < radius * radius
+    post = x[0] > 1.4
+    rb = rho_ratio
+    r1 = np.where(post, rho_s - eps, np.where(inside, eps, 1.0 - eps))
+    r2_ = np.where(post, eps, np.where(inside, rb - eps, eps))
+    v1 = np.where(post, -u_s, 0.0)
+    z = np.zeros_like(v1)
+    p = np.where(post, p_s, 1.0)
+    U = prim_to_cons(pb, [r1, r2_], [v1, z, z], p)
+    inflow = np.zeros((3, 2, 8))
+    inflow[0, 1] = cons_state(pb, [rho_s - eps, eps], [-u_s, 0.0, 0.0], p_s)
+    return pb.with_(inflow=inflow), U, x
+
+
 def water_air_3d(n: int = 256, mu: int = 10, eps: float = 1e-5) -> Tuple[Problem, np.ndarray, np.ndarray]:
     """3D water/air shock-bubble shaped like Example 5.11: water (Gamma 4.4, p_inf 6000,
     rho 1) with an air bubble of radius 0.25 at the centre (Gamma 1.4, p_inf 0,

@@ -258,6 +258,27 @@ def test_full_step_shock_bubble_config():
     assert np.isfinite(JUo).all()
 
 
+@pytest.mark.parametrize("form", [0, 1])
+def test_full_step_3d_shock_bubble(form):
+    """3D two-component shock-bubble (32 x 16 x 16, reflecting walls, inflow/outflow, adaptive
+    mesh with 10 Jacobi sweeps): one full step; FP64 at 1e-11, mixed at FP32 level."""
+    torch = need_gpu()
+    pb, U, x = W.shock_bubble_3d(16)
+    o = Oracle(pb)
+    J = o.init_J(x)
+    JU = U * J
+    xd_o, dt_o, dtau_o = o.mesh_redistribute(JU, J, x)
+    JUo, Jo, xo = o.rk_step(JU, J, x, xd_o, dt_o)
+    ctx = _ctx(pb, form)
+    JUg, Jg, xg = to_dev(JU, torch), to_dev(J, torch), to_dev(x, torch)
+    xd, dd = ctx.mesh_redistribute(JUg, Jg, xg)
+    ctx.es_rk_step(JUg, Jg, xg, xd, dd)
+    e = fieldwise(JUg.cpu().numpy(), JUo, N=2, d=3) + [rel_max_err(Jg.cpu().numpy(), Jo), rel_max_err(xg.cpu().numpy(), xo)]
+    print("3D shock-bubble full step, form", form, "errors", e)
+    assert max(e) <= (1e-11 if form == 0 else 2e-4), e
+    assert ctx.es_poll_status() == 0
+
+
 def test_nonphysical_state_is_reported():
     """A negative density planted on the host is reported through the status word; the
     kernels finish and the context stays usable."""
