@@ -96,16 +96,27 @@ __global__ void dx3d_kernel(const Inst* __restrict__ insts, StagePtrs single, co
         for (int b = 0; b < 3; ++b)
 #pragma unroll
             for (int q = 0; q < 3; ++q) acc[b][q] = 0.0;
+        const bool inner = i0 >= 3 && i0 < I.n[0] - 3 && i1 >= 3 && i1 < I.n[1] - 3 && i2 >= 3 && i2 < I.n[2] - 3;
+        const long long ci = inner ? lin(I, i0, i1, i2) : 0;
+        const long long st[3] = { 1, I.n[0], (long long)I.n[0] * I.n[1] };
 #pragma unroll
         for (int m = 1; m <= 3; ++m) {
 #pragma unroll
             for (int b = 0; b < 3; ++b) {
                 double u[3], v[3];
-                int ip[3] = { i0, i1, i2 }, im[3] = { i0, i1, i2 };
-                ip[b] += m;
-                im[b] -= m;
-                x_at<false>(I, S.x, ip[0], ip[1], ip[2], u);
-                x_at<false>(I, S.x, im[0], im[1], im[2], v);
+                if (inner) {
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        u[q] = S.x[q * I.ncell + ci + m * st[b]];
+                        v[q] = S.x[q * I.ncell + ci - m * st[b]];
+                    }
+                } else {
+                    int ip[3] = { i0, i1, i2 }, im[3] = { i0, i1, i2 };
+                    ip[b] += m;
+                    im[b] -= m;
+                    x_at<false>(I, S.x, ip[0], ip[1], ip[2], u);
+                    x_at<false>(I, S.x, im[0], im[1], im[2], v);
+                }
 #pragma unroll
                 for (int q = 0; q < 3; ++q) acc[b][q] += alpha3(m) * (u[q] - v[q]);
             }
@@ -119,10 +130,15 @@ __global__ void dx3d_kernel(const Inst* __restrict__ insts, StagePtrs single, co
 
 // 3D pass 2: J xi_k/x_j = (delta_a[D_b[x_p] x_q] - delta_b[D_a[x_p] x_q]) / (dxi_a dxi_b)
 // with (a, b) = (3,2), (1,3), (2,1) for k = 1, 2, 3 and (p, q) = (2,3), (3,1), (1,2)
-// for j = 1, 2, 3 (cyclic permutation of Eq. (SCLCoeff)).
+// for j = 1, 2, 3 (cyclic permutation of Eq. (SCLCoeff)).  Every ordered pair (a, b), a != b,
+// belongs to exactly one k, with sign +1 when (a, b) is k's pair and -1 when reversed; the
+// kernel walks the outer direction a and offset m once and adds each product term to its k.
 __global__ void metrics3d_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
                                  const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr)
 {
+    // KOF[a][b]: metric row k of the ordered pair (a, b); SGN[a][b]: its sign
+    const int KOF[3][3] = { { -1, 2, 1 }, { 2, -1, 0 }, { 1, 0, -1 } };
+    const double SGN[3][3] = { { 0.0, -1.0, 1.0 }, { 1.0, 0.0, -1.0 }, { -1.0, 1.0, 0.0 } };
     const int AB[3][2] = { { 2, 1 }, { 0, 2 }, { 1, 0 } };
     const int PQ[3][2] = { { 1, 2 }, { 2, 0 }, { 0, 1 } };
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
@@ -133,36 +149,55 @@ __global__ void metrics3d_kernel(const Inst* __restrict__ insts, StagePtrs singl
         if (!tile_node(I, it.y, 3, i0, i1, i2)) continue;
         const long long p = plin(I, i0, i1, i2);
         const double* D = scr[it.x].D3;
-        long long E0 = I.n[0] + 12, E1 = I.n[1] + 12, ne = E0 * E1 * (I.n[2] + 12);
-        auto eidx = [&](int a0, int a1, int a2) { return ((long long)(a2 + 6) * E1 + (a1 + 6)) * E0 + (a0 + 6); };
-        double m[3][3];
+        const long long E0 = I.n[0] + 12, E1 = I.n[1] + 12, ne = E0 * E1 * (I.n[2] + 12);
+        const long long e_c = ((long long)(i2 + 6) * E1 + (i1 + 6)) * E0 + (i0 + 6);
+        const long long est[3] = { 1, E0, E0 * E1 };
+        const bool inner = i0 >= 3 && i0 < I.n[0] - 3 && i1 >= 3 && i1 < I.n[1] - 3 && i2 >= 3 && i2 < I.n[2] - 3;
+        const long long ci = inner ? lin(I, i0, i1, i2) : 0;
+        const long long st[3] = { 1, I.n[0], (long long)I.n[0] * I.n[1] };
+        double t[3][3];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            int a = AB[k][0], b = AB[k][1];
-            double t[3] = { 0, 0, 0 };
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) t[k][j] = 0.0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
 #pragma unroll
             for (int mm = 1; mm <= 3; ++mm) {
-                // neighbours along a and along b
-                int pa[3] = { i0, i1, i2 }, ma[3] = { i0, i1, i2 }, pb_[3] = { i0, i1, i2 }, mb[3] = { i0, i1, i2 };
-                pa[a] += mm; ma[a] -= mm; pb_[b] += mm; mb[b] -= mm;
-                double xpa[3], xma[3], xpb[3], xmb[3];
-                x_at<false>(I, S.x, pa[0], pa[1], pa[2], xpa);
-                x_at<false>(I, S.x, ma[0], ma[1], ma[2], xma);
-                x_at<false>(I, S.x, pb_[0], pb_[1], pb_[2], xpb);
-                x_at<false>(I, S.x, mb[0], mb[1], mb[2], xmb);
-                long long ipa = eidx(pa[0], pa[1], pa[2]), ima = eidx(ma[0], ma[1], ma[2]);
-                long long ipb = eidx(pb_[0], pb_[1], pb_[2]), imb = eidx(mb[0], mb[1], mb[2]);
+                double xp[3], xm[3];
+                if (inner) {
 #pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    int pp = PQ[j][0], q = PQ[j][1];
-                    double ta = D[(b * 3 + pp) * ne + ipa] * xpa[q] - D[(b * 3 + pp) * ne + ima] * xma[q];
-                    double tb = D[(a * 3 + pp) * ne + ipb] * xpb[q] - D[(a * 3 + pp) * ne + imb] * xmb[q];
-                    t[j] += alpha3(mm) * (ta - tb);
+                    for (int q = 0; q < 3; ++q) {
+                        xp[q] = S.x[q * I.ncell + ci + mm * st[a]];
+                        xm[q] = S.x[q * I.ncell + ci - mm * st[a]];
+                    }
+                } else {
+                    int ip[3] = { i0, i1, i2 }, im[3] = { i0, i1, i2 };
+                    ip[a] += mm;
+                    im[a] -= mm;
+                    x_at<false>(I, S.x, ip[0], ip[1], ip[2], xp);
+                    x_at<false>(I, S.x, im[0], im[1], im[2], xm);
+                }
+                const long long ep = e_c + mm * est[a], em = e_c - mm * est[a];
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    if (b == a) continue;
+                    const int k = KOF[a][b];
+                    const double sg = SGN[a][b] * alpha3(mm);
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        const int pp = PQ[j][0], q = PQ[j][1];
+                        const double* Dbp = D + (long long)(b * 3 + pp) * ne;
+                        t[k][j] += sg * (Dbp[ep] * xp[q] - Dbp[em] * xm[q]);
+                    }
                 }
             }
-#pragma unroll
-            for (int j = 0; j < 3; ++j) m[k][j] = 0.5 * t[j] * I.inv_dxi[a] * I.inv_dxi[b];
         }
+        double m[3][3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) m[k][j] = 0.5 * t[k][j] * I.inv_dxi[AB[k][0]] * I.inv_dxi[AB[k][1]];
         double xd[3] = { 0, 0, 0 };
         if (S.xdot) x_at<true>(I, S.xdot, i0, i1, i2, xd);
         double* M = S.M;
