@@ -164,6 +164,10 @@ Inst make_inst(const es_config& g)
     I.f_pinf_tot = (float)I.pinf_tot;
     for (int q = 0; q < 3; ++q) I.f_chi[q] = (float)I.chi[q];
     I.f_eps = (float)I.weno_eps;
+    for (int k = 0; k < 3; ++k) {
+        I.f_h2[k] = (float)(I.inv_dxi[k] * I.inv_dxi[k]);
+        for (int m = 1; m <= 3; ++m) I.mc[k][m - 1] = 0.5 * alpha3(m) * I.inv_dxi[k];
+    }
     return I;
 }
 
@@ -347,7 +351,7 @@ void launch_mesh(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStream
     for (int f = 0; f < nf; ++f) launch_filter(c->mixed, f == 0, gc, st, c->dI, c->w_cell, c->n_cell, c->dS, f % 2);
     int th_sel = nf % 2;
     for (int s = 0; s < mu; ++s)
-        launch_jacobi(c->mixed, s == mu - 1, gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS, s, th_sel);
+        launch_jacobi(c->mixed, c->d, s == mu - 1, gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS, s, th_sel);
     if (mu == 0) limiter_kernel<<<gc, NODE_TPB, 0, st>>>(c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
     launch_xdot(c->mixed, gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
 }
@@ -406,6 +410,7 @@ es_status es_create_batch(const es_config* cfgs, int n_inst, es_ctx** out)
         ok = ok && dalloc(c, &S.th1, rsz * n);
         ok = ok && dalloc(c, (void**)&S.xa, sizeof(double) * I.d * n);
         ok = ok && dalloc(c, (void**)&S.xb, sizeof(double) * I.d * n);
+        if (c->mixed) ok = ok && dalloc(c, (void**)&S.dl, sizeof(float) * 2 * I.d * I.d * n);
         ok = ok && dalloc(c, (void**)&S.zeros, sizeof(double) * I.d * n);
         if (ok) cudaMemset(S.zeros, 0, sizeof(double) * I.d * n);
         double *A = nullptr, *B = nullptr;

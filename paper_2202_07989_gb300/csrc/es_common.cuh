@@ -42,6 +42,8 @@ struct Inst {
     // binary32 copies of the physical and scheme constants for the FP32 arithmetic of the
     // mixed form (converting the binary64 ones in the kernels would use the FP64 pipe)
     float f_gamma[2], f_cv[2], f_Rs[2], f_cvG[2], f_pinf_tot, f_chi[3], f_eps;
+    float f_h2[3];            // 1 / dxi_k^2 (Jacobi weights of the mixed form)
+    double mc[3][3];          // (1/2) alpha_m / dxi_k: delta_k of a coordinate divided by dxi_k
 };
 
 // the constants of an instance in the compute type R
@@ -101,8 +103,9 @@ struct Scratch {
     double* g;                // monitor gradients, n_sigma fields
     void* th0;                // monitor function ping-pong (compute type)
     void* th1;
-    double* xa;               // Jacobi ping-pong
+    double* xa;               // Jacobi ping-pong (mixed form: binary32 displacements x - x^n)
     double* xb;
+    float* dl;                // mixed form: mesh spacings x^n_{i+-e_k} - x^n_i, [k][+-][j][node]
     double* zeros;            // d zero fields (absent mesh velocity)
 };
 

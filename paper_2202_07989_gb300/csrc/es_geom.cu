@@ -24,55 +24,71 @@ __device__ inline double delta_x(const Inst& I, const double* __restrict__ x, in
 }
 
 // 2D: J xi_1/x = (delta_2[x_2], -delta_2[x_1]) / dxi_2, J xi_2/x = (-delta_1[x_2], delta_1[x_1]) / dxi_1
-__global__ void metrics2d_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
-                                 const int2* __restrict__ work, int nwork)
+// over the padded node range (3 ghost layers).  Each block stages x on its tile and on a
+// halo of 3 nodes in shared memory (ghost nodes through the boundary maps, once per node),
+// then forms both derivatives from shared memory; the coefficients mc = alpha_m / (2 dxi_k)
+// fold the scaling into the stencil.
+__global__ void __launch_bounds__(NODE_TPB) metrics2d_kernel(const Inst* __restrict__ insts, StagePtrs single,
+                                                              const StagePtrs* __restrict__ table,
+                                                              const int2* __restrict__ work, int nwork)
 {
+    constexpr int HX = NT_X + 6, HY = NT_Y + 6;
+    __shared__ double sx[2][HY][HX];
+    const int lx = (int)threadIdx.x % NT_X, ly = (int)threadIdx.x / NT_X;
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
-        int2 it = work[wi];
+        const int2 it = work[wi];
         const Inst& I = insts[it.x];
         ES_PTRS(S);
-        int i0, i1, i2;
-        if (!tile_node(I, it.y, 3, i0, i1, i2)) continue;
-        const long long p = plin(I, i0, i1, 0);
-        // delta_1 and delta_2 of both coordinates
-        double d1[2] = { 0, 0 }, d2[2] = { 0, 0 };
         const int n0 = I.n[0], n1 = I.n[1];
-        if (i0 >= 3 && i0 < n0 - 3 && i1 >= 3 && i1 < n1 - 3) {
-            // interior: no ghost node in the stencil
-            const double* X0 = S.x;
-            const double* X1 = S.x + I.ncell;
-            const int c = i1 * n0 + i0;
-#pragma unroll
-            for (int m = 1; m <= 3; ++m) {
-                d1[0] += alpha3(m) * (X0[c + m] - X0[c - m]);
-                d1[1] += alpha3(m) * (X1[c + m] - X1[c - m]);
-                d2[0] += alpha3(m) * (X0[c + m * n0] - X0[c - m * n0]);
-                d2[1] += alpha3(m) * (X1[c + m * n0] - X1[c - m * n0]);
+        const int ntx = (n0 + 6 + NT_X - 1) / NT_X;
+        // node of the halo box's first entry: tile origin (pad 3) minus the halo of 3
+        const int b0 = (it.y % ntx) * NT_X - 6, b1 = (it.y / ntx) * NT_Y - 6;
+        const bool inner = b0 >= 0 && b0 + HX <= n0 && b1 >= 0 && b1 + HY <= n1;
+        __syncthreads();
+        for (int q = threadIdx.x; q < HX * HY; q += NODE_TPB) {
+            const int a = q % HX, b = q / HX;
+            const int g0 = b0 + a, g1 = b1 + b;
+            double v[2] = { 0.0, 0.0 };
+            if (inner) {
+                const int c = g1 * n0 + g0;
+                v[0] = S.x[c];
+                v[1] = S.x[I.ncell + c];
+            } else if (g0 >= -6 && g0 < n0 + 6 && g1 >= -6 && g1 < n1 + 6) {
+                // entries beyond 6 ghost layers feed only nodes outside the padded range
+                x_at<false>(I, S.x, g0, g1, 0, v);
             }
-        } else {
-            double a[2], b[2], cc[2], e[2];
-#pragma unroll
-            for (int m = 1; m <= 3; ++m) {
-                x_at<false>(I, S.x, i0 + m, i1, 0, a);
-                x_at<false>(I, S.x, i0 - m, i1, 0, b);
-                x_at<false>(I, S.x, i0, i1 + m, 0, cc);
-                x_at<false>(I, S.x, i0, i1 - m, 0, e);
-                d1[0] += alpha3(m) * (a[0] - b[0]);
-                d1[1] += alpha3(m) * (a[1] - b[1]);
-                d2[0] += alpha3(m) * (cc[0] - e[0]);
-                d2[1] += alpha3(m) * (cc[1] - e[1]);
-            }
+            sx[0][b][a] = v[0];
+            sx[1][b][a] = v[1];
         }
-        double m11 = 0.5 * d2[1] * I.inv_dxi[1], m12 = -0.5 * d2[0] * I.inv_dxi[1];
-        double m21 = -0.5 * d1[1] * I.inv_dxi[0], m22 = 0.5 * d1[0] * I.inv_dxi[0];
-        double xd[2] = { 0, 0 };
-        if (S.xdot) x_at<true>(I, S.xdot, i0, i1, 0, xd);
+        __syncthreads();
+        const int i0 = b0 + 3 + lx, i1 = b1 + 3 + ly;
+        if (i0 >= n0 + 3 || i1 >= n1 + 3) continue;
+        const int cx = lx + 3, cy = ly + 3;
+        // m11 = delta_2[x_2] / dxi_2, m12 = -delta_2[x_1] / dxi_2, m21 = -delta_1[x_2] / dxi_1, m22 = delta_1[x_1] / dxi_1
+        double m11 = 0.0, m12 = 0.0, m21 = 0.0, m22 = 0.0;
+#pragma unroll
+        for (int m = 1; m <= 3; ++m) {
+            const double c1 = I.mc[0][m - 1], c2 = I.mc[1][m - 1];
+            m11 = fma(c2, sx[1][cy + m][cx] - sx[1][cy - m][cx], m11);
+            m12 = fma(c2, sx[0][cy - m][cx] - sx[0][cy + m][cx], m12);
+            m21 = fma(c1, sx[1][cy][cx - m] - sx[1][cy][cx + m], m21);
+            m22 = fma(c1, sx[0][cy][cx + m] - sx[0][cy][cx - m], m22);
+        }
+        double xd[2] = { 0.0, 0.0 };
+        if (!S.xdot) {
+        } else if (i0 >= 0 && i0 < n0 && i1 >= 0 && i1 < n1) {
+            const int c = i1 * n0 + i0;
+            xd[0] = S.xdot[c];
+            xd[1] = S.xdot[I.ncell + c];
+        } else {
+            x_at<true>(I, S.xdot, i0, i1, 0, xd);
+        }
         double* M = S.M;
-        long long np = I.npad;
-        M[0 * np + p] = -(xd[0] * m11 + xd[1] * m12);
+        const long long np = I.npad, p = plin(I, i0, i1, 0);
+        M[0 * np + p] = -fma(xd[1], m12, xd[0] * m11);
         M[1 * np + p] = m11;
         M[2 * np + p] = m12;
-        M[3 * np + p] = -(xd[0] * m21 + xd[1] * m22);
+        M[3 * np + p] = -fma(xd[1], m22, xd[0] * m21);
         M[4 * np + p] = m21;
         M[5 * np + p] = m22;
     }

@@ -405,6 +405,133 @@ __global__ void jacobi_kernel(const Inst* __restrict__ insts, StagePtrs single, 
     }
 }
 
+// binary32 displacement y = x - x^n at a node reached along grid lines: periodic wrap
+// (the shift cancels), wall mirror negates the mirrored component
+__device__ inline void y_at(const Inst& I, const float* __restrict__ y, int i0, int i1, int i2, float* out)
+{
+    int i[3] = { i0, i1, i2 };
+    bool flip[3] = { false, false, false };
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (k >= I.d) break;
+        const int n = I.n[k];
+        if (i[k] >= 0 && i[k] < n) continue;
+        const int side = i[k] < 0 ? 0 : 1;
+        if (I.bc[k][side] == BC_PERIODIC) {
+            i[k] -= floordiv_(i[k], n) * n;
+        } else {
+            i[k] = side == 0 ? -1 - i[k] : 2 * n - 1 - i[k];
+            flip[k] = true;
+        }
+    }
+    const long long id = lin(I, i[0], i[1], I.d == 3 ? i[2] : 0);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        if (j >= I.d) break;
+        const float v = y[j * I.ncell + id];
+        out[j] = flip[j] ? -v : v;
+    }
+}
+
+// Mixed form: one Jacobi sweep of the mesh equation on the displacement y = x - x^n in
+// binary32.  With the spacings dl_{k+-} = x^n_{i+-e_k} - x^n_i (formed in FP64 by the first
+// sweep, stored rounded to binary32) the sweep x_i <- sum T_{k+-} x_{i+-e_k} / dxi_k^2 /
+// sum T_{k+-} / dxi_k^2 reads y_i <- sum w_{k+-} (dl_{k+-} + y_{i+-e_k}) / sum w_{k+-}.
+// The positions stay FP64 (x^n + y); only the sweep arithmetic is FP32.  The last sweep
+// also forms the limiter bounds of Sec. 4, dl_{k,s}[k] / (2 y_k) with s the sign of y_k.
+template <int D, bool FIRST, bool LAST>
+__global__ void __launch_bounds__(NODE_TPB) jacobi_y_kernel(const Inst* __restrict__ insts, StagePtrs single,
+                                                             const StagePtrs* __restrict__ table,
+                                                             const int2* __restrict__ work, int nwork,
+                                                             const Scratch* __restrict__ scr, int sweep, int theta_sel)
+{
+    __shared__ double sh[32];
+    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+        const int2 it = work[wi];
+        const Inst& I = insts[it.x];
+        int i[3];
+        const bool valid = tile_node(I, it.y, 0, i[0], i[1], i[2]);
+        ES_PTRS(P);
+        float bnd = 1.0f;
+        if (valid) {
+            const Scratch& Sc = scr[it.x];
+            const long long n = I.ncell;
+            const long long p = lin(I, i[0], i[1], i[2]);
+            const float* th = reinterpret_cast<const float*>(theta_sel ? Sc.th1 : Sc.th0);
+            const float* ys = reinterpret_cast<const float*>(sweep % 2 == 1 ? Sc.xa : Sc.xb);
+            float* yd = reinterpret_cast<float*>(sweep % 2 == 0 ? Sc.xa : Sc.xb);
+            float* dl = Sc.dl;
+            const float tc = th[p];
+            bool inner = true;
+#pragma unroll
+            for (int k = 0; k < D; ++k) inner = inner && i[k] >= 1 && i[k] < I.n[k] - 1;
+            float num[D], den = 0.0f, dk[D][2];
+#pragma unroll
+            for (int j = 0; j < D; ++j) num[j] = 0.0f;
+            long long stride = 1;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+#pragma unroll
+                for (int s = 0; s < 2; ++s) {
+                    int nb[3] = { i[0], i[1], i[2] };
+                    nb[k] += s ? 1 : -1;
+                    const long long q = p + (s ? stride : -stride);
+                    const float w = 0.5f * (tc + th[inner ? q : s_map(I, nb[0], nb[1], nb[2])]) * I.f_h2[k];
+                    float dv[D], yv[D];
+                    if (FIRST) {
+                        double xn[3];
+                        if (inner) {
+#pragma unroll
+                            for (int j = 0; j < D; ++j) xn[j] = P.x[j * n + q];
+                        } else {
+                            x_at<false>(I, P.x, nb[0], nb[1], nb[2], xn);
+                        }
+#pragma unroll
+                        for (int j = 0; j < D; ++j) {
+                            dv[j] = f64_to_f32(xn[j] - P.x[j * n + p]);
+                            dl[((k * 2 + s) * D + j) * n + p] = dv[j];
+                            yv[j] = 0.0f;
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < D; ++j) dv[j] = dl[((k * 2 + s) * D + j) * n + p];
+                        if (inner) {
+#pragma unroll
+                            for (int j = 0; j < D; ++j) yv[j] = ys[j * n + q];
+                        } else {
+                            y_at(I, ys, nb[0], nb[1], nb[2], yv);
+                        }
+                    }
+                    dk[k][s] = dv[k];
+#pragma unroll
+                    for (int j = 0; j < D; ++j) num[j] = fmaf(w, dv[j] + yv[j], num[j]);
+                    den += w;
+                }
+                stride *= I.n[k];
+            }
+            float ynew[D];
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                ynew[j] = num[j] / den;
+                yd[j * n + p] = ynew[j];
+            }
+            if (LAST) {
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    const float dx = ynew[k];
+                    if (dx < 0.0f) bnd = fminf(bnd, dk[k][0] / (2.0f * dx));
+                    else if (dx > 0.0f) bnd = fminf(bnd, dk[k][1] / (2.0f * dx));
+                }
+                if (!(bnd >= 0.0f)) bnd = 0.0f;
+            }
+        }
+        if (LAST) {
+            const double m = block_min_pos(f32_to_f64(bnd), sh);
+            if (threadIdx.x == 0) atomic_min_pos(&scr[it.x].red[5], m);
+        }
+    }
+}
+
 // Delta_tau = min(1, bounds of Sec. 4) per instance
 __device__ inline const double* xmu_of(const StagePtrs& P, const Scratch& S, int mu)
 {
@@ -468,10 +595,19 @@ __global__ void xdot_kernel(const Inst* __restrict__ insts, StagePtrs single, co
         int i0, i1, i2;
         if (!tile_node(I, it.y, 0, i0, i1, i2)) continue;
         const long long p = lin(I, i0, i1, i2);
-        const double sc = FAST ? dtau / dt : 0.0;
-        for (int j = 0; j < I.d; ++j) {
-            long long q = (long long)j * I.ncell + p;
-            P.xdot_out[q] = FAST ? sc * (xmu[q] - P.x[q]) : dtau * (xmu[q] - P.x[q]) / dt;
+        if (FAST) {
+            // mixed form: x^[mu] - x^n is the binary32 displacement of the sweeps
+            const double sc = dtau / dt;
+            const float* y = reinterpret_cast<const float*>(xmu);
+            for (int j = 0; j < I.d; ++j) {
+                const long long q = (long long)j * I.ncell + p;
+                P.xdot_out[q] = I.mu > 0 ? sc * f32_to_f64(y[q]) : 0.0;
+            }
+        } else {
+            for (int j = 0; j < I.d; ++j) {
+                const long long q = (long long)j * I.ncell + p;
+                P.xdot_out[q] = dtau * (xmu[q] - P.x[q]) / dt;
+            }
         }
     }
 }
@@ -586,12 +722,25 @@ void launch_xdot(bool mixed, int grid, cudaStream_t st, const Inst* insts, const
     else xdot_kernel<false><<<grid, NODE_TPB, 0, st>>>(insts, single, table, work, nwork, scr);
 }
 
-void launch_jacobi(bool mixed, bool last, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
+void launch_jacobi(bool mixed, int d, bool last, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
                    const StagePtrs* table, const int2* work, int nwork, const Scratch* scr, int sweep, int theta_sel)
 {
 #define JL(R, LS) jacobi_kernel<R, LS><<<grid, NODE_TPB, 0, st>>>(insts, single, table, work, nwork, scr, sweep, theta_sel)
-    if (mixed) { if (last) JL(float, true); else JL(float, false); }
-    else { if (last) JL(double, true); else JL(double, false); }
+#define JY(D, F, LS) jacobi_y_kernel<D, F, LS><<<grid, NODE_TPB, 0, st>>>(insts, single, table, work, nwork, scr, sweep, theta_sel)
+    if (mixed) {
+        const bool first = sweep == 0;
+        if (d == 2) {
+            if (first) { if (last) JY(2, true, true); else JY(2, true, false); }
+            else { if (last) JY(2, false, true); else JY(2, false, false); }
+        } else {
+            if (first) { if (last) JY(3, true, true); else JY(3, true, false); }
+            else { if (last) JY(3, false, true); else JY(3, false, false); }
+        }
+    } else {
+        if (last) JL(double, true);
+        else JL(double, false);
+    }
+#undef JY
 #undef JL
 }
 

@@ -14,7 +14,7 @@ void launch_monitor_theta(bool mixed, int grid, cudaStream_t st, const Inst* ins
                           const Scratch* scr);
 void launch_filter(bool mixed, bool from_g, int grid, cudaStream_t st, const Inst* insts, const int2* work, int nwork,
                    const Scratch* scr, int parity);
-void launch_jacobi(bool mixed, bool last, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
+void launch_jacobi(bool mixed, int d, bool last, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
                    const StagePtrs* table, const int2* work, int nwork, const Scratch* scr, int sweep, int theta_sel);
 __global__ void limiter_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work, int nwork,
                                const Scratch* scr);

@@ -155,6 +155,30 @@ def test_mesh_redistribute(d, N, bc, mu, nf):
     assert max(e) <= 1e-11, e
 
 
+@pytest.mark.parametrize("d,N", [(2, 2), (3, 1)])
+@pytest.mark.parametrize("bc", ["periodic", "mixed"])
+@pytest.mark.parametrize("mu,nf", [(5, 3), (0, 0), (1, 1)])
+def test_mesh_redistribute_mixed(d, N, bc, mu, nf):
+    """Mixed form (binary32 monitor, filter and Jacobi sweeps on the displacement x - x^n,
+    FP64 positions): Delta t, Delta_tau and the mesh velocity vs the FP64 oracle at FP32
+    level (relative to the largest mesh velocity)."""
+    torch = need_gpu()
+    pb, JU, J, x, xdot = case(d, N, GRIDS[d], bc, seed=5, jump=True)
+    pb = pb.with_(mu=mu, nf=nf, sigma=(W.SIG_RHO, W.SIG_P), alpha=(100.0, 30.0))
+    o = Oracle(pb)
+    xd_o, dt_o, dtau_o = o.mesh_redistribute(JU, J, x)
+    ctx = _ctx(pb, precision=1)
+    xd, dd = ctx.mesh_redistribute(to_dev(JU, torch), to_dev(J, torch), to_dev(x, torch))
+    dd = dd.cpu().numpy()
+    xd = xd.cpu().numpy()
+    e_dt, e_tau = abs(dd[0] - dt_o) / dt_o, abs(dd[1] - dtau_o) / dtau_o
+    scale = max(np.abs(xd_o).max(), 1e-300)
+    e_x = np.abs(xd - xd_o).max() / scale if mu > 0 else np.abs(xd).max()
+    print("mixed mesh errors dt %.2e dtau %.2e xdot %.2e" % (e_dt, e_tau, e_x))
+    assert e_dt <= 1e-6 and e_tau <= 1e-5
+    assert e_x <= (1e-5 if mu > 0 else 0.0)
+
+
 @pytest.mark.parametrize("d,N", CASES)
 def test_entropy_production(d, N):
     torch = need_gpu()
@@ -239,9 +263,11 @@ def test_batched_equals_single():
             assert torch.equal(ju, JU[i]) and torch.equal(jj, J[i]) and torch.equal(xx, X[i])
 
 
-def test_full_step_shock_bubble_config():
+@pytest.mark.parametrize("form", [0, 1])
+def test_full_step_shock_bubble_config(form):
     """The 400 x 200 two-component shock-bubble instance (adaptive mesh, 5 sweeps): one full
-    step (mesh redistribution + SSP-RK3) on the GPU vs the oracle, FP64."""
+    step (mesh redistribution + SSP-RK3) on the GPU vs the oracle; FP64 at 1e-11, mixed at
+    FP32 level."""
     torch = need_gpu()
     pb, U, x = W.shock_bubble_2d(400, 200)
     o = Oracle(pb)
@@ -249,12 +275,13 @@ def test_full_step_shock_bubble_config():
     JU = U * J
     xd_o, dt_o, dtau_o = o.mesh_redistribute(JU, J, x)
     JUo, Jo, xo = o.rk_step(JU, J, x, xd_o, dt_o)
-    ctx = _ctx(pb)
+    ctx = _ctx(pb, form)
     JUg, Jg, xg = to_dev(JU, torch), to_dev(J, torch), to_dev(x, torch)
     xd, dd = ctx.mesh_redistribute(JUg, Jg, xg)
     ctx.es_rk_step(JUg, Jg, xg, xd, dd)
     e = fieldwise(JUg.cpu().numpy(), JUo, N=pb.N, d=pb.d) + [rel_max_err(Jg.cpu().numpy(), Jo), rel_max_err(xg.cpu().numpy(), xo)]
-    assert max(e) <= 1e-11, e
+    print("2D shock-bubble full step, form", form, "errors", e)
+    assert max(e) <= (1e-11 if form == 0 else 2e-4), e
     assert np.isfinite(JUo).all()
 
 
