@@ -25,7 +25,7 @@
  * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
  * stream).  Calls are asynchronous on that stream unless they say otherwise;
  * scalar results are written to device memory so whole steps can be captured
- * in a CUDA graph (es_rk_step, mesh_redistribute, entropy_production).
+ * in a CUDA graph (es_rk_step, mesh_redistribute, es_step, entropy_production).
  *
  * Errors: every call returns an es_status.  Argument errors are detected on
  * the host before any launch (ES_ERR_ARG, ES_ERR_UNSUPPORTED).  Launch errors
@@ -134,6 +134,17 @@ es_status es_rk_step(es_ctx* ctx, double* JU, double* J, double* x, const double
  * xdot (written): d fields.  dt_dtau (written, DEVICE): {Delta t, Delta_tau}. */
 es_status mesh_redistribute(es_ctx* ctx, const double* JU, const double* J, const double* x, double dt_fixed,
                             double* xdot, double* dt_dtau, void* stream);
+
+/* One full time step on one instance: mesh_redistribute on (JU, J, x), then
+ * es_rk_step with the mesh velocity and time step just formed -- the same
+ * results, bit for bit, as those two calls in sequence.  The first RK stage
+ * reuses the spatial metrics of x that the mesh step forms, so the step forms
+ * metrics three times instead of four.  JU, J, x: updated IN PLACE.
+ * dt_fixed: HOST value as in mesh_redistribute.  xdot (written): d fields.
+ * dt_dtau (written, DEVICE): {Delta t, Delta_tau}.  ES_ERR_UNSUPPORTED on a
+ * batch context (use es_step_batch); no host synchronisation. */
+es_status es_step(es_ctx* ctx, double* JU, double* J, double* x, double dt_fixed, double* xdot, double* dt_dtau,
+                  void* stream);
 
 /* Entropy diagnostics (Sec. 1 definitions, Sec. 5 total entropy):
  * out2[0] = P = sum_i dxi^d (V_i . dJU_i - phi_i dJ_i)  (= d/dt of the total

@@ -267,10 +267,12 @@ void launch_metrics(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStr
 }
 
 // residual of one stage: metrics, then one flux launch per direction.  With
-// rk = true the last direction applies the Shu-Osher stage (a, b).
-void launch_residual(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, bool rk, double a, double b, cudaStream_t st)
+// rk = true the last direction applies the Shu-Osher stage (a, b); metrics = false
+// when M already holds the metrics of the stage (the first stage of a full step).
+void launch_residual(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, bool rk, double a, double b, cudaStream_t st,
+                     bool metrics = true)
 {
-    launch_metrics(c, P, tab, st);
+    if (metrics) launch_metrics(c, P, tab, st);
     for (int k = 0; k < c->d; ++k) {
         FluxLaunch L;
         L.insts = c->dI;
@@ -333,17 +335,18 @@ void stage_ptrs(es_ctx* c, int i, double* JU, double* J, double* x, const double
 const double RK_A[3] = { 0.0, 0.75, 1.0 / 3.0 };
 const double RK_B[3] = { 1.0, 0.25, 2.0 / 3.0 };
 
-void launch_mesh(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStream_t st)
+// mesh redistribution (Sec. 4): the metrics of x^n (Eq. (cfl) and the monitor need them),
+// Delta t and the monitor gradients, the filter passes, the Jacobi sweeps with the limiter,
+// and the mesh velocity.  With step = true (a full time step follows) the velocity pass
+// also stores the VCL metrics of the first RK stage in M.
+void launch_mesh(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStream_t st, bool step = false)
 {
+    StagePtrs Q = P;
+    Q.xdot = nullptr;
+    Q.M = c->hS[0].M;
+    launch_metrics(c, Q, tab, st);
     ProfScope ps(c, PC_MESH, st);
     red_init_kernel<<<(c->n_inst + 127) / 128, 128, 0, st>>>(c->dS, c->n_inst);
-    if (c->d == 3) {
-        // node metrics of x^n (no mesh velocity) for Eq. (cfl); 2D forms them inline
-        StagePtrs Q = P;
-        Q.xdot = nullptr;
-        Q.M = c->hS[0].M;
-        launch_metrics(c, Q, tab, st);
-    }
     int gc = node_grid(c, c->n_cell);
     launch_cfl_grad(c->mixed, gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
     int nf = c->hI[0].nf, mu = c->hI[0].mu;
@@ -353,7 +356,18 @@ void launch_mesh(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStream
     for (int s = 0; s < mu; ++s)
         launch_jacobi(c->mixed, c->d, s == mu - 1, gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS, s, th_sel);
     if (mu == 0) limiter_kernel<<<gc, NODE_TPB, 0, st>>>(c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
-    launch_xdot(c->mixed, gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
+    if (step) launch_xdot_vcl(c->mixed, c->d, node_grid(c, c->n_pad), st, c->dI, P, tab, c->w_pad, c->n_pad, c->dS);
+    else launch_xdot(c->mixed, gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
+}
+
+// one full time step: mesh redistribution, then the three SSP-RK3 stages; the first
+// stage reuses the metrics the mesh step formed
+void launch_step(es_ctx* c, const StagePtrs& mesh, const StagePtrs* tab_mesh, const StagePtrs stage[3],
+                 StagePtrs* const tab_stage[3], cudaStream_t st)
+{
+    launch_mesh(c, mesh, tab_mesh, st, true);
+    for (int s = 0; s < 3; ++s)
+        launch_residual(c, stage[s], tab_stage[s], true, RK_A[s], RK_B[s], st, s > 0);
 }
 
 __global__ void time_acc_kernel(double* t, const double* dt_dtau) { *t += dt_dtau[0]; }
@@ -548,6 +562,28 @@ es_status mesh_redistribute(es_ctx* c, const double* JU, const double* J, const 
     return cuda_check(c, "mesh_redistribute");
 }
 
+es_status es_step(es_ctx* c, double* JU, double* J, double* x, double dt_fixed, double* xdot, double* dt_dtau,
+                  void* stream)
+{
+    if (!c) return ES_ERR_ARG;
+    if (!JU || !J || !x || !xdot || !dt_dtau) return fail(c, ES_ERR_ARG, "es_step: null pointer");
+    if (c->n_inst != 1) return fail(c, ES_ERR_UNSUPPORTED, "es_step: single-instance context required");
+    if (!(dt_fixed >= 0.0)) return fail(c, ES_ERR_ARG, "es_step: dt_fixed must be >= 0");
+    StagePtrs M;
+    memset(&M, 0, sizeof(M));
+    M.JU = JU;
+    M.J = J;
+    M.x = x;
+    M.xdot_out = xdot;
+    M.out = dt_dtau;
+    M.dt_fixed = dt_fixed;
+    StagePtrs P[3];
+    stage_ptrs(c, 0, JU, J, x, xdot, dt_dtau, P);
+    StagePtrs* const none[3] = { nullptr, nullptr, nullptr };
+    launch_step(c, M, nullptr, P, none, (cudaStream_t)stream);
+    return cuda_check(c, "es_step");
+}
+
 es_status entropy_production(es_ctx* c, const double* JU, const double* J, const double* dJU, const double* dJ,
                              double* out2, void* stream)
 {
@@ -609,8 +645,8 @@ es_status es_step_batch(es_ctx* c, void* stream)
     cudaStream_t st = (cudaStream_t)stream;
     StagePtrs none;
     memset(&none, 0, sizeof(none));
-    launch_mesh(c, none, c->tab_mesh, st);
-    for (int s = 0; s < 3; ++s) launch_residual(c, none, c->tab_stage[s], true, RK_A[s], RK_B[s], st);
+    const StagePtrs stage[3] = { none, none, none };
+    launch_step(c, none, c->tab_mesh, stage, c->tab_stage, st);
     return cuda_check(c, "es_step_batch");
 }
 
@@ -633,9 +669,7 @@ es_status es_run_host(es_ctx* c, double* JU, double* J, double* x, int steps, do
     cudaMemcpyAsync(c->hx, x, sizeof(double) * I.d * n, cudaMemcpyHostToDevice, st);
     cudaMemsetAsync(c->htacc, 0, sizeof(double), st);
     for (int s = 0; s < steps; ++s) {
-        es_status r = mesh_redistribute(c, c->hJU, c->hJ, c->hx, dt_fixed, c->hxd, c->hdt, stream);
-        if (r != ES_OK) return r;
-        r = es_rk_step(c, c->hJU, c->hJ, c->hx, c->hxd, c->hdt, stream);
+        es_status r = es_step(c, c->hJU, c->hJ, c->hx, dt_fixed, c->hxd, c->hdt, stream);
         if (r != ES_OK) return r;
         time_acc_kernel<<<1, 1, 0, st>>>(c->htacc, c->hdt);
     }

@@ -202,6 +202,17 @@ __device__ inline int map_line(const Inst& I, int k, int g, int& gi, int& side)
     }
 }
 
+// VCL metric J xi_k/t = -sum_j xdot_j J xi_k/x_j (Eq. (VCLCoeff)) from one row of the spatial
+// metrics, in one fixed evaluation order for every kernel that forms it
+template <int D>
+__device__ __forceinline__ double vcl_metric(const double* xd, const double* m)
+{
+    double s = xd[0] * m[0];
+#pragma unroll
+    for (int j = 1; j < D; ++j) s = fma(xd[j], m[j], s);
+    return -s;
+}
+
 // scalar node field with periodic wrap, else copy of the boundary node
 __device__ inline long long s_map(const Inst& I, int i0, int i1, int i2)
 {

@@ -85,10 +85,11 @@ __global__ void __launch_bounds__(NODE_TPB) metrics2d_kernel(const Inst* __restr
         }
         double* M = S.M;
         const long long np = I.npad, p = plin(I, i0, i1, 0);
-        M[0 * np + p] = -fma(xd[1], m12, xd[0] * m11);
+        const double r1[2] = { m11, m12 }, r2[2] = { m21, m22 };
+        M[0 * np + p] = vcl_metric<2>(xd, r1);
         M[1 * np + p] = m11;
         M[2 * np + p] = m12;
-        M[3 * np + p] = -fma(xd[1], m22, xd[0] * m21);
+        M[3 * np + p] = vcl_metric<2>(xd, r2);
         M[4 * np + p] = m21;
         M[5 * np + p] = m22;
     }
@@ -220,7 +221,7 @@ __global__ void metrics3d_kernel(const Inst* __restrict__ insts, StagePtrs singl
         long long np = I.npad;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            M[(k * 4 + 0) * np + p] = -(xd[0] * m[k][0] + xd[1] * m[k][1] + xd[2] * m[k][2]);
+            M[(k * 4 + 0) * np + p] = vcl_metric<3>(xd, m[k]);
 #pragma unroll
             for (int j = 0; j < 3; ++j) M[(k * 4 + 1 + j) * np + p] = m[k][j];
         }

@@ -172,8 +172,8 @@ __device__ __forceinline__ R sigma_t(const Inst& I, int kind, const R* U)
 // one pass over the nodes: the CFL spectral-radius sum of Eq. (cfl) at x^n and the
 // monitor gradients |grad_xi sigma_s| (second-order central differences); per-instance
 // maxima by atomics on the non-negative bit patterns.  R = float in the mixed form (the
-// time step is a bound and the monitor is an FP32 quantity there); the metrics are
-// formed in FP64.
+// time step is a bound and the monitor is an FP32 quantity there); the metrics are read
+// from M.
 template <typename R>
 __global__ void cfl_grad_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
                                 const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr)
@@ -200,14 +200,11 @@ __global__ void cfl_grad_kernel(const Inst* __restrict__ insts, StagePtrs single
             }
             R T = (U[I.N + I.d] - R(0.5) * rho * v2 - to_r<R>(I.pinf_tot)) / cvr;
             R c = sqrt((a / rho) * (gm / cvr) * T);
+            // spatial metrics of x^n, formed by the metrics pass that opens the mesh step
             double m[3][3];
-            if (I.d == 2) {
-                node_metrics2d(I, P.x, i[0], i[1], m);
-            } else {
-                long long pid = plin(I, i[0], i[1], i[2]);
-                for (int k = 0; k < 3; ++k)
-                    for (int j = 0; j < 3; ++j) m[k][j] = scr[it.x].M[(long long)(k * 4 + 1 + j) * I.npad + pid];
-            }
+            const long long pid = plin(I, i[0], i[1], i[2]);
+            for (int k = 0; k < I.d; ++k)
+                for (int j = 0; j < I.d; ++j) m[k][j] = scr[it.x].M[(long long)(k * (I.d + 1) + 1 + j) * I.npad + pid];
             const R Jp = to_r<R>(P.J[p]);
             R sr = R(0);
             for (int k = 0; k < I.d; ++k) {
@@ -612,6 +609,81 @@ __global__ void xdot_kernel(const Inst* __restrict__ insts, StagePtrs single, co
     }
 }
 
+// xdot_kernel over the padded node range of a full time step: interior nodes store the
+// mesh velocity, and every node of the padded range stores the VCL metrics of the first
+// RK stage from that velocity (ghost nodes through the velocity map) and the spatial
+// metrics of x^n that the mesh step left in M, so the first stage forms no metrics.
+// The velocity and the VCL metric are evaluated exactly as xdot_kernel and the metrics
+// kernels do.
+template <int D, bool MIXED>
+__global__ void xdot_vcl_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
+                                const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr)
+{
+    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+        const int2 it = work[wi];
+        const Inst& I = insts[it.x];
+        ES_PTRS(P);
+        const double* red = scr[it.x].red;
+        const double* xmu = xmu_of(P, scr[it.x], I.mu);
+        const double dt = P.dt_fixed > 0.0 ? P.dt_fixed : I.cfl / red[0];
+        const double dtau = red[5];
+        if (it.y == 0 && threadIdx.x == 0) {
+            P.out[0] = dt;
+            P.out[1] = dtau;
+        }
+        int i[3];
+        if (!tile_node(I, it.y, 3, i[0], i[1], i[2])) continue;
+        bool interior = true;
+#pragma unroll
+        for (int k = 0; k < D; ++k) interior = interior && i[k] >= 0 && i[k] < I.n[k];
+        const long long n = I.ncell;
+        const long long c = interior ? lin(I, i[0], i[1], i[2]) : 0;
+        double xd[3] = { 0.0, 0.0, 0.0 };
+        if (MIXED) {
+            if (I.mu > 0) {
+                const double sc = dtau / dt;
+                const float* y = reinterpret_cast<const float*>(xmu);
+                float yv[3];
+                if (interior) {
+#pragma unroll
+                    for (int j = 0; j < D; ++j) yv[j] = y[j * n + c];
+                } else {
+                    y_at(I, y, i[0], i[1], i[2], yv);
+                }
+#pragma unroll
+                for (int j = 0; j < D; ++j) xd[j] = sc * f32_to_f64(yv[j]);
+            }
+        } else {
+            double a[3], b[3];
+            if (interior) {
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    a[j] = xmu[j * n + c];
+                    b[j] = P.x[j * n + c];
+                }
+            } else {
+                x_at<true>(I, xmu, i[0], i[1], i[2], a);
+                x_at<true>(I, P.x, i[0], i[1], i[2], b);
+            }
+#pragma unroll
+            for (int j = 0; j < D; ++j) xd[j] = dtau * (a[j] - b[j]) / dt;
+        }
+        if (interior) {
+#pragma unroll
+            for (int j = 0; j < D; ++j) P.xdot_out[j * n + c] = xd[j];
+        }
+        double* M = scr[it.x].M;
+        const long long np = I.npad, p = plin(I, i[0], i[1], i[2]);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            double m[3];
+#pragma unroll
+            for (int j = 0; j < D; ++j) m[j] = M[(k * (D + 1) + 1 + j) * np + p];
+            M[(k * (D + 1)) * np + p] = vcl_metric<D>(xd, m);
+        }
+    }
+}
+
 // entropy diagnostics: per-block partial sums of V.dJU - phi dJ and J eta
 __global__ void entropy_partial_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
                                        const int2* __restrict__ work, int nwork, double* __restrict__ partial)
@@ -713,6 +785,15 @@ void launch_cfl_grad(bool mixed, int grid, cudaStream_t st, const Inst* insts, c
 {
     if (mixed) cfl_grad_kernel<float><<<grid, NODE_TPB, 0, st>>>(insts, single, table, work, nwork, scr);
     else cfl_grad_kernel<double><<<grid, NODE_TPB, 0, st>>>(insts, single, table, work, nwork, scr);
+}
+
+void launch_xdot_vcl(bool mixed, int d, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
+                     const StagePtrs* table, const int2* work, int nwork, const Scratch* scr)
+{
+#define XV(D, MX) xdot_vcl_kernel<D, MX><<<grid, NODE_TPB, 0, st>>>(insts, single, table, work, nwork, scr)
+    if (d == 2) { if (mixed) XV(2, true); else XV(2, false); }
+    else { if (mixed) XV(3, true); else XV(3, false); }
+#undef XV
 }
 
 void launch_xdot(bool mixed, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,

@@ -64,6 +64,7 @@ def lib():
             "es_rhs": (C.c_int, [vp, dp, dp, dp, dp, dp, dp, vp]),
             "es_rk_step": (C.c_int, [vp, dp, dp, dp, dp, dp, vp]),
             "mesh_redistribute": (C.c_int, [vp, dp, dp, dp, C.c_double, dp, dp, vp]),
+            "es_step": (C.c_int, [vp, dp, dp, dp, C.c_double, dp, dp, vp]),
             "entropy_production": (C.c_int, [vp, dp, dp, dp, dp, dp, vp]),
             "es_bind_batch": (C.c_int, [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp)]),
             "es_step_batch": (C.c_int, [vp, vp]),
@@ -209,6 +210,18 @@ class Context:
         self._chk(self.L.mesh_redistribute(self.h, _ptr(JU, pb.nc, pb, "JU"), _ptr(J, 1, pb, "J"),
                                            _ptr(x, pb.d, pb, "x"), float(dt_fixed), _ptr(xdot, pb.d, pb, "xdot"),
                                            C.c_void_p(dt_dtau.data_ptr()), _stream()), "mesh_redistribute")
+        return xdot, dt_dtau
+
+    def es_step(self, JU, J, x, dt_fixed: float = 0.0, xdot=None, dt_dtau=None):
+        """One full time step (mesh redistribution, then SSP-RK3) of (JU, J, x) in place."""
+        pb = self.pb
+        if xdot is None:
+            xdot = torch.empty((pb.d,) + pb.shape, dtype=torch.float64, device=JU.device)
+        if dt_dtau is None:
+            dt_dtau = torch.empty(2, dtype=torch.float64, device=JU.device)
+        self._chk(self.L.es_step(self.h, _ptr(JU, pb.nc, pb, "JU"), _ptr(J, 1, pb, "J"), _ptr(x, pb.d, pb, "x"),
+                                 float(dt_fixed), _ptr(xdot, pb.d, pb, "xdot"), C.c_void_p(dt_dtau.data_ptr()),
+                                 _stream()), "es_step")
         return xdot, dt_dtau
 
     def entropy_production(self, JU, J, dJU=None, dJ=None, out=None):

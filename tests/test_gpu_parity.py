@@ -179,6 +179,29 @@ def test_mesh_redistribute_mixed(d, N, bc, mu, nf):
     assert e_x <= (1e-5 if mu > 0 else 0.0)
 
 
+@pytest.mark.parametrize("d,N", [(2, 2), (3, 1)])
+@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("mu,nf", [(3, 2), (0, 0)])
+def test_step_equals_mesh_then_rk(d, N, form, mu, nf):
+    """es_step (its first RK stage reuses the metrics of x^n formed by the mesh step, with
+    the VCL metrics stored by the velocity pass) equals mesh_redistribute followed by
+    es_rk_step bit for bit, with reflecting, inflow, outflow and periodic sides."""
+    torch = need_gpu()
+    pb, JU, J, x, xdot = case(d, N, GRIDS[d], "mixed", seed=21, jump=True)
+    pb = pb.with_(mu=mu, nf=nf, sigma=(W.SIG_RHO, W.SIG_P), alpha=(100.0, 30.0))
+    a, b = _ctx(pb, form), _ctx(pb, form)
+    A = [to_dev(t, torch) for t in (JU, J, x)]
+    B = [to_dev(t, torch) for t in (JU, J, x)]
+    for _ in range(2):
+        xd, dd = a.mesh_redistribute(*A)
+        a.es_rk_step(*A, xd, dd)
+        xe, de = b.es_step(*B)
+        assert torch.equal(xd, xe) and torch.equal(dd, de)
+    for s, t in zip(A, B):
+        assert torch.equal(s, t)
+    assert a.es_poll_status() == 0 and b.es_poll_status() == 0
+
+
 @pytest.mark.parametrize("d,N", CASES)
 def test_entropy_production(d, N):
     torch = need_gpu()
