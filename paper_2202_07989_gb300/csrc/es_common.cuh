@@ -256,35 +256,49 @@ __device__ inline void load_U(const Inst& I, const double* __restrict__ JU, cons
 }
 
 // IEEE 754 binary64 -> binary32 with round-to-nearest-even, done with integer
-// instructions (the hardware conversion issues on the FP64 pipe, which GB300 runs at
-// 1/64 of the FP32 rate).  Values below 2^-126 in magnitude become a signed zero;
-// values of 2^128 and above, infinities and NaN take the hardware conversion.
+// instructions only (the hardware conversion issues on the FP64 pipe, which GB300 runs
+// at 1/64 of the FP32 rate).  Values below 2^-126 in magnitude become a signed zero;
+// |x| >= 2^128 (after rounding) and infinities become infinities; NaN becomes the
+// canonical binary32 NaN.
 __device__ __forceinline__ float f64_to_f32(double x)
 {
-    unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    unsigned int hi = (unsigned int)(b >> 32);
-    int e = (int)((hi >> 20) & 0x7ffu);
-    unsigned int sign = hi & 0x80000000u;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned int hi = (unsigned int)(b >> 32);
+    const int e = (int)((hi >> 20) & 0x7ffu);
+    const unsigned int sign = hi & 0x80000000u;
+    const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
     if (e < 1023 - 126) return __int_as_float((int)sign);
-    if (e > 1023 + 127) return __double2float_rn(x);
-    unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
-    unsigned int m = (unsigned int)(mant >> 29);
-    unsigned int rem = (unsigned int)(mant & 0x1FFFFFFFull);
+    if (e > 1023 + 127) return __int_as_float((int)(e == 0x7ff && mant != 0ull ? 0x7fffffffu : (sign | 0x7f800000u)));
+    const unsigned int m = (unsigned int)(mant >> 29);
+    const unsigned int rem = (unsigned int)(mant & 0x1FFFFFFFull);
     unsigned int f = sign | ((unsigned int)(e - 1023 + 127) << 23) | m;
+    // a carry out of the significand steps the exponent (up to infinity), as rounding must
     f += (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;
     return __int_as_float((int)f);
 }
 
-// IEEE 754 binary32 -> binary64 (exact), with integer instructions; zero keeps its sign,
-// subnormals, infinities and NaN take the hardware conversion
+// IEEE 754 binary32 -> binary64 (exact), with integer instructions only; subnormals are
+// normalised, infinities kept, NaN keeps its payload with the quiet bit set
 __device__ __forceinline__ double f32_to_f64(float f)
 {
-    unsigned int b = (unsigned int)__float_as_int(f);
-    unsigned int e = (b >> 23) & 0xffu;
-    unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
-    if ((b & 0x7fffffffu) == 0u) return __longlong_as_double((long long)sign);
-    if (e == 0u || e == 0xffu) return (double)f;
-    unsigned long long d = sign | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(b & 0x7fffffu) << 29);
+    const unsigned int b = (unsigned int)__float_as_int(f);
+    const unsigned int e = (b >> 23) & 0xffu;
+    const unsigned int mant = b & 0x7fffffu;
+    const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+    unsigned long long d;
+    if (e == 0xffu) {
+        d = sign | 0x7ff0000000000000ull | ((unsigned long long)mant << 29) | (mant ? 0x0008000000000000ull : 0ull);
+    } else if (e == 0u) {
+        if (mant == 0u) {
+            d = sign;
+        } else {
+            // mant * 2^-149 with its leading one at bit 23 - sh
+            const int sh = __clz((int)mant) - 8;
+            d = sign | ((unsigned long long)(897 - sh) << 52) | ((unsigned long long)((mant << sh) & 0x7fffffu) << 29);
+        }
+    } else {
+        d = sign | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)mant << 29);
+    }
     return __longlong_as_double((long long)d);
 }
 

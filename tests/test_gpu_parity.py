@@ -353,10 +353,15 @@ def test_integer_pipe_conversions_match_hardware():
     vals = np.concatenate([mant * np.exp2(expo), [0.0, -0.0, 1.0, -1.0, 3.4e38, -3.4e38, 1.5, 2.5 * 2.0 ** -29],
                            # exact halfway cases between two binary32 values
                            (1.0 + (2 * np.arange(1, 64) + 1) * 2.0 ** -24), -(1.0 + (2 * np.arange(1, 64)) * 2.0 ** -24)])
+    # overflow (2^128 and the halfway point below it round to infinity), infinities, NaN
+    big = np.array([2.0 ** 128, -1e39, 1e300, 3.4028235677973366e38, 3.4028235677973362e38, np.inf, -np.inf, np.nan])
+    vals = np.concatenate([vals, big])
     x = torch.from_numpy(vals).cuda()
     o32, o64 = es.es_check_conversions(x)
     ref = x.float()
-    keep = x.abs() >= 2.0 ** -126
+    nan = torch.isnan(x)
+    keep = (x.abs() >= 2.0 ** -126) & ~nan
     assert torch.equal(o32[keep].view(torch.int32), ref[keep].view(torch.int32))
-    assert torch.equal(o64, o32.double())
-    assert bool((o32[~keep] == 0).all())
+    assert bool(torch.isnan(o32[nan]).all()) and bool(torch.isnan(o64[nan]).all())
+    assert torch.equal(o64[~nan], o32[~nan].double())
+    assert bool((o32[~keep & ~nan] == 0).all())
