@@ -239,6 +239,16 @@ class Batch:
         return sum(p.ncell for p in self.probs)
 
 
+def tune(runner, batched=False):
+    """Run the library's flux autotuner on the runner's state; returns the choice per
+    direction as "S x WT tile, grid CTAs"."""
+    if batched:
+        t = runner.ctx.es_autotune()
+    else:
+        t = runner.ctx.es_autotune(runner.JU, runner.J, runner.x, runner.xdot)
+    return ["%dx%d tile, %d CTAs, %.3f ms" % (S, WT, grid, ms) for _, S, WT, grid, ms in t]
+
+
 def time_steps(runner, steps, warmup, torch, flush):
     for _ in range(warmup):
         runner.run()
@@ -335,10 +345,12 @@ def main_ours(args):
 
     forms = {}
     runners = {}
+    tiles = {}
     for name, prec in (("mixed", es.MIXED), ("fp64", es.FP64)):
         r = Single(pb, U, x, prec, torch)
         r.step()                      # first call on the context, outside capture
         r.reset()
+        tiles[name] = tune(r)
         r.capture()
         r.reset()
         runners[name] = r
@@ -370,6 +382,7 @@ def main_ours(args):
     rk = RkOnly(pb, U, x, es.MIXED, torch)
     rk.step()
     rk.reset()
+    tune(rk)
     rk.capture()
     rk.reset()
     krk = max(3, min(args.steps, 200))
@@ -391,6 +404,7 @@ def main_ours(args):
         bt = Batch(insts, es.MIXED, torch)
         bt.step()
         torch.cuda.synchronize()
+        tiles["batched_mixed"] = tune(bt, batched=True)
         bt.capture()
         kb = max(3, min(args.steps, 10))
         tb = time_steps(bt, kb, 2, torch, flush)
@@ -406,6 +420,7 @@ def main_ours(args):
             r3 = Single(p3, U3, x3, es.MIXED, torch)
             r3.step()
             r3.reset()
+            tiles[name] = tune(r3)
             r3.capture()
             r3.reset()
             k3 = max(3, min(args.steps, 8))
@@ -471,7 +486,8 @@ def main_ours(args):
         "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "cells": pb.ncell, "stages_per_step": 3, "form": "mixed FP32/FP64",
                    "graph": "one CUDA graph per full step", "l2": "256 MiB buffer rewritten before every timed step",
-                   "instances_per_rank": 1},
+                   "instances_per_rank": 1, "flux_tiles": tiles.get("mixed")},
+        "flux_tiles": tiles,
         "forms": forms, "errors": errs, "roofline": roofline, "roofline_fp64": roofline_fp64,
         "kernel_ms": {"mixed": {k: v[0] / args.steps for k, v in prof_m.items()},
                       "fp64": {k: v[0] / k64 for k, v in prof_d.items()},
@@ -526,18 +542,19 @@ def main_kernel_case(args):
     B.build()
     from paper_2202_07989_gb300 import es, workloads as W
     if args.kernel_case.startswith("3d:"):
-        # 3D octant Riemann problem (single component) or water/air (two components)
+        # 3D octant Riemann problem (single component) or shock-bubble (two components, 2n x n x n)
         kind, n = args.kernel_case[3:].split(":")
-        pb, U, x = W.riemann_3d(int(n)) if kind == "riemann" else W.water_air_3d(int(n))
+        pb, U, x = W.riemann_3d(int(n)) if kind == "riemann" else W.shock_bubble_3d(int(n))
     else:
         nx, ny = [int(v) for v in args.kernel_case.split("x")]
         pb, U, x = W.shock_bubble_2d(nx, ny, length=(2.0, 1.0))
     r = Single(pb, U, x, es.MIXED if args.kernel_form == "mixed" else es.FP64, torch)
+    tiles = tune(r) if args.kernel_tune else None
     for _ in range(args.kernel_steps):
         r.step()
     torch.cuda.synchronize()
     assert r.ctx.es_poll_status() == 0
-    out = {"case": args.kernel_case, "form": args.kernel_form, "steps": args.kernel_steps}
+    out = {"case": args.kernel_case, "form": args.kernel_form, "steps": args.kernel_steps, "flux_tiles": tiles}
     if args.kernel_time:
         r.reset()
         prof = kernel_profile(r, args.kernel_time, torch)
@@ -556,10 +573,11 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-3d", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
-    ap.add_argument("--kernel-case", default=None, help="NXxNY: only run a few steps of that grid (profiling)")
+    ap.add_argument("--kernel-case", default=None, help="NXxNY | 3d:riemann:N | 3d:sb:N: only run a few steps of that grid (profiling)")
     ap.add_argument("--kernel-form", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--kernel-steps", type=int, default=2)
     ap.add_argument("--kernel-time", type=int, default=0, help="also time this many eager steps per kernel class")
+    ap.add_argument("--kernel-tune", action="store_true", help="run the flux autotuner before the steps")
     args = ap.parse_args()
     if args.kernel_case:
         return main_kernel_case(args)

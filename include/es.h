@@ -146,6 +146,30 @@ es_status mesh_redistribute(es_ctx* ctx, const double* JU, const double* J, cons
 es_status es_step(es_ctx* ctx, double* JU, double* J, double* x, double dt_fixed, double* xdot, double* dt_dtau,
                   void* stream);
 
+/* Autotuner of the flux launches (tile shapes and schedules; the paper has no
+ * counterpart -- it is part of the batched form).  For every direction it times
+ * each flux tile shape (S nodes along the line x WT lines; es_get_tuning lists
+ * the one chosen) at one and at full persistent occupancy on the given state,
+ * and keeps the fastest for all later calls on the context.  Tile shape and grid
+ * change no result: every interface flux and node divergence is formed by the
+ * same arithmetic in any tile.  Single-instance context: JU, J, x (and xdot, may
+ * be NULL) give the state, read only.  Batch context: pass NULLs after
+ * es_bind_batch; the bound state is read only.  The timed launches write only
+ * context scratch.  reps <= 0 means 5 timed launches per candidate.  Host
+ * synchronisation; ES_ERR_ARG during stream capture. */
+es_status es_autotune(es_ctx* ctx, const double* JU, const double* J, const double* x, const double* xdot, int reps,
+                      void* stream);
+
+/* The flux launch configuration per direction k = 0..2 (zeros for directions
+ * the problem lacks): shape index, S, WT, persistent grid size (CTAs) and the
+ * time per launch the last es_autotune measured (0 if none).  Each argument
+ * points to 3 values (HOST). */
+es_status es_get_tuning(const es_ctx* ctx, int* shape, int* S, int* WT, int* grid, float* ms);
+
+/* Fix the flux launch of direction k to tile shape `shape` (0..5) and `grid`
+ * CTAs (0 = SM count x occupancy of that shape).  ES_ERR_ARG when out of range. */
+es_status es_set_tuning(es_ctx* ctx, int k, int shape, int grid);
+
 /* Entropy diagnostics (Sec. 1 definitions, Sec. 5 total entropy):
  * out2[0] = P = sum_i dxi^d (V_i . dJU_i - phi_i dJ_i)  (= d/dt of the total
  * entropy; 0 for the EC scheme on periodic data, <= 0 for the ES scheme) and

@@ -8,8 +8,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libes.so")
-SOURCES = ["es_flux.cu", "es_geom.cu", "es_mesh.cu", "es_api.cu"]
-HEADERS = ["es_common.cuh", "es_kernels.cuh", "es_mesh.cuh"]
+SOURCES = ["es_flux_2d1.cu", "es_flux_2d2.cu", "es_flux_3d1.cu", "es_flux_3d2.cu", "es_geom.cu", "es_mesh.cu", "es_api.cu"]
+HEADERS = ["es_common.cuh", "es_kernels.cuh", "es_mesh.cuh", "es_flux_impl.cuh"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-gencode", "arch=compute_103a,code=sm_103a",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-diag-suppress", "177"]

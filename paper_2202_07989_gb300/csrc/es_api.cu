@@ -26,8 +26,8 @@ struct es_ctx {
     int2* w_pad = nullptr;  int n_pad = 0;
     int2* w_ext = nullptr;  int n_ext = 0;
     int2* w_cell = nullptr; int n_cell = 0;
-    int2* w_flux[3] = { nullptr, nullptr, nullptr };
-    int n_flux[3] = { 0, 0, 0 };
+    int2* w_flux[3][NSHAPE] = {};          // flux work list per direction and tile shape
+    int n_flux[3][NSHAPE] = {};
     int* d_first_cell = nullptr;
     double* partial = nullptr;
     int* status = nullptr;
@@ -40,7 +40,10 @@ struct es_ctx {
     // device buffers of es_run_host
     double *hJU = nullptr, *hJ = nullptr, *hx = nullptr, *hxd = nullptr, *hdt = nullptr, *htacc = nullptr;
     int sms = 152;
+    // flux launch configuration per direction (defaults, or the autotuner's choice)
+    int flux_shape[3] = { SHAPE_DEFAULT_K0, SHAPE_DEFAULT_KN, SHAPE_DEFAULT_KN };
     int flux_grid[3] = { 0, 0, 0 };
+    float flux_ms[3] = { 0.f, 0.f, 0.f };
     std::string err;
     // kernel timing (es_profile)
     bool prof = false;
@@ -148,12 +151,6 @@ Inst make_inst(const es_config& g)
     for (int s = 0; s < 4; ++s) { I.sigma[s] = g.sigma[s]; I.alpha[s] = g.alpha[s]; }
     I.mu = g.mu;
     I.nf = g.nf;
-    for (int k = 0; k < g.d; ++k) {
-        int S = k == 0 ? S_K0 : S_KN, WT = k == 0 ? WT_K0 : WT_KN;
-        int adim = k == 0 ? 1 : 0, bdim = k == 2 ? 1 : 2;
-        int nb = bdim < g.d ? I.n[bdim] : 1;
-        I.tiles[k] = ((I.n[k] + S - 1) / S) * ((I.n[adim] + WT - 1) / WT) * nb;
-    }
     I.ntile_nodes = node_tiles(I, 0);
     for (int l = 0; l < 2; ++l) {
         I.f_gamma[l] = (float)I.gamma[l];
@@ -193,11 +190,12 @@ void prepare_all()
     prepare_flux<D, NS, float>();
 }
 
-void flux_dispatch(es_ctx* c, const FluxLaunch& L, cudaStream_t st)
+// one flux launch in the given tile shape and grid
+void flux_launch(es_ctx* c, const FluxLaunch& L, int shape, int grid, cudaStream_t st)
 {
-    int grid = L.nwork < c->flux_grid[L.k] ? L.nwork : c->flux_grid[L.k];
+    if (grid > L.nwork) grid = L.nwork;
     if (grid <= 0) return;
-#define FD(d, n) do { if (c->mixed) launch_flux<d, n, float>(L, grid, st); else launch_flux<d, n, double>(L, grid, st); } while (0)
+#define FD(d, n) do { if (c->mixed) launch_flux<d, n, float>(L, shape, grid, st); else launch_flux<d, n, double>(L, shape, grid, st); } while (0)
     if (c->d == 2 && c->N == 1) FD(2, 1);
     else if (c->d == 2 && c->N == 2) FD(2, 2);
     else if (c->d == 3 && c->N == 1) FD(3, 1);
@@ -205,9 +203,18 @@ void flux_dispatch(es_ctx* c, const FluxLaunch& L, cudaStream_t st)
 #undef FD
 }
 
-int flux_occ(es_ctx* c, int k)
+// flux tiles of instance I along direction k in tile shape `shape`
+long long flux_tiles(const Inst& I, int k, int shape)
 {
-#define FO(d, n) return c->mixed ? flux_blocks_per_sm<d, n, float>(k) : flux_blocks_per_sm<d, n, double>(k)
+    const int S = SHAPE_S[shape], WT = SHAPE_WT[shape];
+    const int adim = k == 0 ? 1 : 0, bdim = k == 2 ? 1 : 2;
+    const long long nb = bdim < I.d ? I.n[bdim] : 1;
+    return (long long)((I.n[k] + S - 1) / S) * ((I.n[adim] + WT - 1) / WT) * nb;
+}
+
+int flux_occ(es_ctx* c, int shape)
+{
+#define FO(d, n) return c->mixed ? flux_blocks_per_sm<d, n, float>(shape) : flux_blocks_per_sm<d, n, double>(shape)
     if (c->d == 2 && c->N == 1) FO(2, 1);
     if (c->d == 2 && c->N == 2) FO(2, 2);
     if (c->d == 3 && c->N == 1) FO(3, 1);
@@ -278,8 +285,9 @@ void launch_residual(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, bool r
         L.insts = c->dI;
         L.single = P;
         L.ptrs = tab;
-        L.work = c->w_flux[k];
-        L.nwork = c->n_flux[k];
+        const int sh = c->flux_shape[k];
+        L.work = c->w_flux[k][sh];
+        L.nwork = c->n_flux[k][sh];
         L.k = k;
         L.mode = k == 0 ? MODE_WRITE : MODE_ACC;
         if (rk && k == c->d - 1) L.mode = MODE_RK;
@@ -287,7 +295,7 @@ void launch_residual(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, bool r
         L.b = b;
         L.status = c->status;
         ProfScope ps(c, PC_FLUX + k, st);
-        flux_dispatch(c, L, st);
+        flux_launch(c, L, sh, c->flux_grid[k], st);
     }
 }
 
@@ -447,18 +455,22 @@ es_status es_create_batch(const es_config* cfgs, int n_inst, es_ctx** out)
     c->w_pad = build_work(c, [](const Inst& I) { return (long long)node_tiles(I, 3); }, c->n_pad);
     c->w_cell = build_work(c, [](const Inst& I) { return (long long)node_tiles(I, 0); }, c->n_cell);
     if (c->d == 3) c->w_ext = build_work(c, [](const Inst& I) { return (long long)node_tiles(I, 6); }, c->n_ext);
-    for (int k = 0; k < c->d; ++k) c->w_flux[k] = build_work(c, [k](const Inst& I) { return (long long)I.tiles[k]; }, c->n_flux[k]);
+    for (int k = 0; k < c->d; ++k)
+        for (int sh = 0; sh < NSHAPE; ++sh) {
+            c->w_flux[k][sh] = build_work(c, [k, sh](const Inst& I) { return flux_tiles(I, k, sh); }, c->n_flux[k][sh]);
+            ok = ok && c->w_flux[k][sh];
+        }
     // per-instance ranges of the cell work list (entropy reduction)
     std::vector<int> first(n_inst + 1, 0);
     for (int i = 0; i < n_inst; ++i) first[i + 1] = first[i] + c->hI[i].ntile_nodes;
-    ok = dalloc(c, (void**)&c->d_first_cell, sizeof(int) * (n_inst + 1)) &&
+    ok = ok && dalloc(c, (void**)&c->d_first_cell, sizeof(int) * (n_inst + 1)) &&
          dalloc(c, (void**)&c->partial, sizeof(double) * 2 * (first[n_inst] > 0 ? first[n_inst] : 1));
     if (ok) cudaMemcpy(c->d_first_cell, first.data(), sizeof(int) * (n_inst + 1), cudaMemcpyHostToDevice);
     if (c->d == 2 && c->N == 1) prepare_all<2, 1>();
     else if (c->d == 2 && c->N == 2) prepare_all<2, 2>();
     else if (c->d == 3 && c->N == 1) prepare_all<3, 1>();
     else prepare_all<3, 2>();
-    for (int k = 0; k < c->d; ++k) c->flux_grid[k] = c->sms * flux_occ(c, k);
+    for (int k = 0; k < c->d; ++k) c->flux_grid[k] = c->sms * flux_occ(c, c->flux_shape[k]);
     cudaError_t e = cudaDeviceSynchronize();
     if (!ok || e != cudaSuccess || !c->w_pad || !c->w_cell || (c->d == 3 && !c->w_ext)) {
         fprintf(stderr, "es_create: setup failed: %s\n", cudaGetErrorString(e));
@@ -682,6 +694,96 @@ es_status es_run_host(es_ctx* c, double* JU, double* J, double* x, int steps, do
     if (e != cudaSuccess) return fail(c, ES_ERR_CUDA, std::string("es_run_host: ") + cudaGetErrorString(e));
     if (t) *t += tacc;
     return cuda_check(c, "es_run_host");
+}
+
+es_status es_autotune(es_ctx* c, const double* JU, const double* J, const double* x, const double* xdot, int reps,
+                      void* stream)
+{
+    if (!c) return ES_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (capturing(st)) return fail(c, ES_ERR_ARG, "es_autotune: not allowed during stream capture");
+    StagePtrs P;
+    memset(&P, 0, sizeof(P));
+    const StagePtrs* tab = nullptr;
+    if (c->n_inst == 1 && JU) {
+        if (!J || !x) return fail(c, ES_ERR_ARG, "es_autotune: null pointer");
+        StagePtrs S3[3];
+        stage_ptrs(c, 0, const_cast<double*>(JU), const_cast<double*>(J), const_cast<double*>(x), xdot, nullptr, S3);
+        P = S3[0];
+    } else if (c->bound) {
+        tab = c->tab_stage[0];
+    } else {
+        return fail(c, ES_ERR_ARG, "es_autotune: pass the state of a single-instance context or bind a batch first");
+    }
+    if (reps <= 0) reps = 5;
+    // the metrics of the state into the context's scratch; the timed flux launches write
+    // only the scratch accumulators (MODE_WRITE), so no caller buffer changes
+    launch_metrics(c, P, tab, st);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int k = 0; k < c->d; ++k) {
+        float best = 3.0e38f;
+        for (int sh = 0; sh < NSHAPE; ++sh) {
+            const int occ = flux_occ(c, sh);
+            for (int o = occ; o >= 1 && o >= occ - 1; --o) {
+                FluxLaunch L;
+                L.insts = c->dI;
+                L.single = P;
+                L.ptrs = tab;
+                L.work = c->w_flux[k][sh];
+                L.nwork = c->n_flux[k][sh];
+                L.k = k;
+                L.mode = MODE_WRITE;
+                L.a = 0.0;
+                L.b = 1.0;
+                L.status = c->status;
+                const int grid = c->sms * o;
+                flux_launch(c, L, sh, grid, st);
+                cudaEventRecord(e0, st);
+                for (int r = 0; r < reps; ++r) flux_launch(c, L, sh, grid, st);
+                cudaEventRecord(e1, st);
+                if (cudaEventSynchronize(e1) != cudaSuccess) break;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms /= (float)reps;
+                if (ms < best) {
+                    best = ms;
+                    c->flux_shape[k] = sh;
+                    c->flux_grid[k] = grid;
+                }
+            }
+        }
+        c->flux_ms[k] = best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return cuda_check(c, "es_autotune");
+}
+
+es_status es_get_tuning(const es_ctx* c, int* shape, int* S, int* WT, int* grid, float* ms)
+{
+    if (!c || !shape || !S || !WT || !grid || !ms) return ES_ERR_ARG;
+    for (int k = 0; k < 3; ++k) {
+        const bool on = k < c->d;
+        shape[k] = on ? c->flux_shape[k] : 0;
+        S[k] = on ? SHAPE_S[c->flux_shape[k]] : 0;
+        WT[k] = on ? SHAPE_WT[c->flux_shape[k]] : 0;
+        grid[k] = on ? c->flux_grid[k] : 0;
+        ms[k] = on ? c->flux_ms[k] : 0.f;
+    }
+    return ES_OK;
+}
+
+es_status es_set_tuning(es_ctx* c, int k, int shape, int grid)
+{
+    if (!c) return ES_ERR_ARG;
+    if (k < 0 || k >= c->d || shape < 0 || shape >= NSHAPE || grid < 0)
+        return fail(c, ES_ERR_ARG, "es_set_tuning: direction, shape or grid out of range");
+    c->flux_shape[k] = shape;
+    c->flux_grid[k] = grid > 0 ? grid : c->sms * flux_occ(c, shape);
+    c->flux_ms[k] = 0.f;
+    return ES_OK;
 }
 
 es_status es_check_conversions(const double* in, int n, float* out32, double* out64, void* stream)

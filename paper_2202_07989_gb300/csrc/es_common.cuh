@@ -37,7 +37,6 @@ struct Inst {
     int n_sigma, sigma[4];
     double alpha[4];
     int mu, nf;
-    int tiles[3];             // flux tiles per direction
     int ntile_nodes;          // 1D node tiles for node-wise kernels
     // binary32 copies of the physical and scheme constants for the FP32 arithmetic of the
     // mixed form (converting the binary64 ones in the kernels would use the FP64 pipe)

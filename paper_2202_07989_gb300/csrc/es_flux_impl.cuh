@@ -24,6 +24,8 @@
 // the p_inf Mt terms give p_inf times the GCL flux of J xi_k/t.  The kernel drops
 // the first and adds the second in FP64, which keeps the large p_inf of stiffened
 // gases out of the low-precision pair arithmetic.
+#pragma once
+
 #include "es_kernels.cuh"
 
 #include <type_traits>
@@ -574,70 +576,51 @@ static size_t smem_of()
            sizeof(R) * (Y::NF * TL::NN + Y::NC * TL::NP + (NS + 1) * TL::NI + Y::NC * TL::NI);
 }
 
-size_t flux_smem_bytes(int D, int NS, bool mixed, int k)
-{
-#define SM(d, n, r) (k == 0 ? smem_of<d, n, r, S_K0, WT_K0>() : smem_of<d, n, r, S_KN, WT_KN>())
-    if (D == 2 && NS == 1) return mixed ? SM(2, 1, float) : SM(2, 1, double);
-    if (D == 2 && NS == 2) return mixed ? SM(2, 2, float) : SM(2, 2, double);
-    if (D == 3 && NS == 1) return mixed ? SM(3, 1, float) : SM(3, 1, double);
-    return mixed ? SM(3, 2, float) : SM(3, 2, double);
-#undef SM
-}
+// one case per tile shape of the table in es_kernels.cuh
+#define ES_FLUX_SHAPES(X) X(0) X(1) X(2) X(3) X(4) X(5)
+static_assert(NSHAPE == 6, "ES_FLUX_SHAPES lists every tile shape");
 
 template <int D, int NS, typename R>
 void prepare_flux()
 {
-    cudaFuncSetAttribute(flux_kernel<D, NS, R, S_K0, WT_K0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem_of<D, NS, R, S_K0, WT_K0>());
-    cudaFuncSetAttribute(flux_kernel<D, NS, R, S_KN, WT_KN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem_of<D, NS, R, S_KN, WT_KN>());
+#define ES_PREP(SH)                                                                                                  \
+    cudaFuncSetAttribute(flux_kernel<D, NS, R, SHAPE_S[SH], SHAPE_WT[SH]>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                         (int)smem_of<D, NS, R, SHAPE_S[SH], SHAPE_WT[SH]>());
+    ES_FLUX_SHAPES(ES_PREP)
+#undef ES_PREP
 }
 
 template <int D, int NS, typename R>
-int flux_blocks_per_sm(int k)
+int flux_blocks_per_sm(int shape)
 {
     int nb = 0;
-    if (k == 0)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, flux_kernel<D, NS, R, S_K0, WT_K0>, FLUX_TPB,
-                                                      smem_of<D, NS, R, S_K0, WT_K0>());
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, flux_kernel<D, NS, R, S_KN, WT_KN>, FLUX_TPB,
-                                                      smem_of<D, NS, R, S_KN, WT_KN>());
+#define ES_OCC(SH)                                                                                                  \
+    if (shape == SH)                                                                                                \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, flux_kernel<D, NS, R, SHAPE_S[SH], SHAPE_WT[SH]>, FLUX_TPB, \
+                                                      smem_of<D, NS, R, SHAPE_S[SH], SHAPE_WT[SH]>());
+    ES_FLUX_SHAPES(ES_OCC)
+#undef ES_OCC
     return nb > 0 ? nb : 1;
 }
 
 template <int D, int NS, typename R>
-void launch_flux(const FluxLaunch& L, int grid, cudaStream_t st)
+void launch_flux(const FluxLaunch& L, int shape, int grid, cudaStream_t st)
 {
-    if (L.k == 0)
-        flux_kernel<D, NS, R, S_K0, WT_K0><<<grid, FLUX_TPB, smem_of<D, NS, R, S_K0, WT_K0>(), st>>>(L);
-    else
-        flux_kernel<D, NS, R, S_KN, WT_KN><<<grid, FLUX_TPB, smem_of<D, NS, R, S_KN, WT_KN>(), st>>>(L);
+#define ES_LAUNCH(SH)                                                                                              \
+    if (shape == SH)                                                                                               \
+        flux_kernel<D, NS, R, SHAPE_S[SH], SHAPE_WT[SH]>                                                           \
+            <<<grid, FLUX_TPB, smem_of<D, NS, R, SHAPE_S[SH], SHAPE_WT[SH]>(), st>>>(L);
+    ES_FLUX_SHAPES(ES_LAUNCH)
+#undef ES_LAUNCH
 }
 
-template void prepare_flux<2, 1, double>();
-template int flux_blocks_per_sm<2, 1, double>(int);
-template void prepare_flux<2, 1, float>();
-template int flux_blocks_per_sm<2, 1, float>(int);
-template void prepare_flux<2, 2, double>();
-template int flux_blocks_per_sm<2, 2, double>(int);
-template void prepare_flux<2, 2, float>();
-template int flux_blocks_per_sm<2, 2, float>(int);
-template void prepare_flux<3, 1, double>();
-template int flux_blocks_per_sm<3, 1, double>(int);
-template void prepare_flux<3, 1, float>();
-template int flux_blocks_per_sm<3, 1, float>(int);
-template void prepare_flux<3, 2, double>();
-template int flux_blocks_per_sm<3, 2, double>(int);
-template void prepare_flux<3, 2, float>();
-template int flux_blocks_per_sm<3, 2, float>(int);
-template void launch_flux<2, 1, double>(const FluxLaunch&, int, cudaStream_t);
-template void launch_flux<2, 2, double>(const FluxLaunch&, int, cudaStream_t);
-template void launch_flux<3, 1, double>(const FluxLaunch&, int, cudaStream_t);
-template void launch_flux<3, 2, double>(const FluxLaunch&, int, cudaStream_t);
-template void launch_flux<2, 1, float>(const FluxLaunch&, int, cudaStream_t);
-template void launch_flux<2, 2, float>(const FluxLaunch&, int, cudaStream_t);
-template void launch_flux<3, 1, float>(const FluxLaunch&, int, cudaStream_t);
-template void launch_flux<3, 2, float>(const FluxLaunch&, int, cudaStream_t);
+// explicit instantiation of one (dimension, species) case in both compute types
+#define ES_FLUX_INSTANTIATE(D, NS)                                                \
+    template void prepare_flux<D, NS, double>();                                  \
+    template void prepare_flux<D, NS, float>();                                   \
+    template int flux_blocks_per_sm<D, NS, double>(int);                          \
+    template int flux_blocks_per_sm<D, NS, float>(int);                           \
+    template void launch_flux<D, NS, double>(const FluxLaunch&, int, int, cudaStream_t); \
+    template void launch_flux<D, NS, float>(const FluxLaunch&, int, int, cudaStream_t);
 
 }  // namespace es

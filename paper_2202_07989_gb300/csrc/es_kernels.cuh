@@ -5,11 +5,15 @@
 
 namespace es {
 
-// flux tiles of S nodes along the line x WT lines: (3S + 6) WT = 768 distinct node pairs
-// (three per thread) and (S + 1) WT <= 256 interfaces
+// flux tile shapes: S nodes along the line x WT neighbouring lines, (S + 1) WT <= 256
+// interfaces (one thread each), (S + 6) WT staged nodes and (3S + 6) WT distinct node pairs.
+// The autotuner picks one shape (and a persistent grid size) per direction.
 constexpr int FLUX_TPB = 256;
-constexpr int S_K0 = 62, WT_K0 = 4;    // direction 1: 62 nodes along the line x 4 lines
-constexpr int S_KN = 30, WT_KN = 8;    // directions 2, 3: 30 nodes x 8 neighbouring lines (coalesced)
+constexpr int NSHAPE = 6;
+constexpr int SHAPE_S[NSHAPE] = { 62, 58, 122, 30, 26, 14 };
+constexpr int SHAPE_WT[NSHAPE] = { 4, 4, 2, 8, 8, 16 };
+constexpr int SHAPE_DEFAULT_K0 = 0;    // direction 1: 62 nodes along the line x 4 lines
+constexpr int SHAPE_DEFAULT_KN = 3;    // directions 2, 3: 30 nodes x 8 neighbouring lines (coalesced)
 constexpr int NODE_TPB = 256;
 
 enum { MODE_WRITE = 0, MODE_ACC = 1, MODE_RK = 2 };
@@ -34,14 +38,13 @@ __global__ void metrics3d_kernel(const Inst* insts, StagePtrs single, const Stag
 __global__ void conversion_check_kernel(const double* in, int n, float* o32, double* o64);
 __global__ void init_J_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work, int nwork);
 
-// flux + divergence (+ RK stage) for one direction; D dims, NS species, R compute type
+// flux + divergence (+ RK stage) for one direction; D dims, NS species, R compute type,
+// tile shape index `shape`
 template <int D, int NS, typename R>
-void launch_flux(const FluxLaunch& L, int grid, cudaStream_t st);
+void launch_flux(const FluxLaunch& L, int shape, int grid, cudaStream_t st);
 template <int D, int NS, typename R>
 void prepare_flux();
 template <int D, int NS, typename R>
-int flux_blocks_per_sm(int k);
-
-size_t flux_smem_bytes(int D, int NS, bool mixed, int k);
+int flux_blocks_per_sm(int shape);
 
 }  // namespace es

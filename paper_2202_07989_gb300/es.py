@@ -65,6 +65,9 @@ def lib():
             "es_rk_step": (C.c_int, [vp, dp, dp, dp, dp, dp, vp]),
             "mesh_redistribute": (C.c_int, [vp, dp, dp, dp, C.c_double, dp, dp, vp]),
             "es_step": (C.c_int, [vp, dp, dp, dp, C.c_double, dp, dp, vp]),
+            "es_autotune": (C.c_int, [vp, dp, dp, dp, dp, C.c_int, vp]),
+            "es_get_tuning": (C.c_int, [vp, ip, ip, ip, ip, C.POINTER(C.c_float)]),
+            "es_set_tuning": (C.c_int, [vp, C.c_int, C.c_int, C.c_int]),
             "entropy_production": (C.c_int, [vp, dp, dp, dp, dp, dp, vp]),
             "es_bind_batch": (C.c_int, [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp)]),
             "es_step_batch": (C.c_int, [vp, vp]),
@@ -223,6 +226,27 @@ class Context:
                                  float(dt_fixed), _ptr(xdot, pb.d, pb, "xdot"), C.c_void_p(dt_dtau.data_ptr()),
                                  _stream()), "es_step")
         return xdot, dt_dtau
+
+    def es_autotune(self, JU=None, J=None, x=None, xdot=None, reps: int = 5):
+        """Pick the flux tile shape and grid per direction by timing them on the given state
+        (single instance) or on the bound batch (no arguments); returns es_get_tuning()."""
+        pb = self.pb
+        if JU is None:
+            args = (None, None, None, None)
+        else:
+            args = (_ptr(JU, pb.nc, pb, "JU"), _ptr(J, 1, pb, "J"), _ptr(x, pb.d, pb, "x"), _ptr(xdot, pb.d, pb, "xdot"))
+        self._chk(self.L.es_autotune(self.h, *args, int(reps), _stream()), "es_autotune")
+        return self.es_get_tuning()
+
+    def es_get_tuning(self):
+        """[(shape, S, WT, grid, ms per launch)] for the directions of the problem."""
+        a = [(C.c_int * 3)() for _ in range(4)]
+        ms = (C.c_float * 3)()
+        self._chk(self.L.es_get_tuning(self.h, a[0], a[1], a[2], a[3], ms), "es_get_tuning")
+        return [(a[0][k], a[1][k], a[2][k], a[3][k], ms[k]) for k in range(self.pb.d)]
+
+    def es_set_tuning(self, k: int, shape: int, grid: int = 0):
+        self._chk(self.L.es_set_tuning(self.h, int(k), int(shape), int(grid)), "es_set_tuning")
 
     def entropy_production(self, JU, J, dJU=None, dJ=None, out=None):
         pb = self.pb

@@ -202,6 +202,39 @@ def test_step_equals_mesh_then_rk(d, N, form, mu, nf):
     assert a.es_poll_status() == 0 and b.es_poll_status() == 0
 
 
+@pytest.mark.parametrize("d,N", [(2, 2), (3, 1)])
+@pytest.mark.parametrize("form", [0, 1])
+def test_flux_tile_shapes_and_autotune_bitwise(d, N, form):
+    """Every flux tile shape, at one CTA per SM and at full occupancy, and the autotuner's
+    choice give the same residual and RK step bit for bit (tile shape and grid change no
+    arithmetic); the tuning reported is a valid shape per direction."""
+    torch = need_gpu()
+    pb, JU, J, x, xdot = case(d, N, GRIDS[d], "mixed", es=True, seed=23, jump=True)
+    ctx = _ctx(pb, form)
+    G = [to_dev(t, torch) for t in (JU, J, x, xdot)]
+    ref = ctx.es_rhs(*G)
+    for shape in range(6):
+        for grid in (0, 152):
+            for k in range(d):
+                ctx.es_set_tuning(k, shape, grid)
+            got = ctx.es_rhs(*G)
+            assert torch.equal(got[0], ref[0]) and torch.equal(got[1], ref[1]), (shape, grid)
+    tun = ctx.es_autotune(*G, reps=2)
+    assert len(tun) == d
+    for sh, S, WT, grid, ms in tun:
+        assert 0 <= sh < 6 and (S + 1) * WT <= 256 and grid > 0 and ms > 0
+    got = ctx.es_rhs(*G)
+    assert torch.equal(got[0], ref[0]) and torch.equal(got[1], ref[1])
+    # RK step after tuning equals a fresh context's step
+    dt = torch.tensor([0.2 * min(pb.dxi[:d])], dtype=torch.float64, device="cuda")
+    A = [t.clone() for t in G[:3]]
+    B = [t.clone() for t in G[:3]]
+    ctx.es_rk_step(*A, G[3], dt)
+    _ctx(pb, form).es_rk_step(*B, G[3], dt)
+    for a, b in zip(A, B):
+        assert torch.equal(a, b)
+
+
 @pytest.mark.parametrize("d,N", CASES)
 def test_entropy_production(d, N):
     torch = need_gpu()
