@@ -49,7 +49,10 @@ FP64_PEAK_TFLOPS = 1.25
 def flux_flops_per_interface(D, NS, es=True):
     """Algorithmic flops of one interface of the flux kernel (each +, -, x, /, sqrt counted once;
     the per-term counts are those of the contracted two-point flux, the GCL stencil, the
-    interface averages and the WENO-MR evaluations)."""
+    interface averages and the WENO-MR evaluations: EC pair 26 + 18D + 21N (six pairs), GCL
+    10 + 11D, dissipation set-up 3D + 2D^2 + 4 + (2 in 2D, 15 in 3D) + (12 for N = 1, 45 for
+    N = 2), per column of R 8 + 15 n_c + 2D^2 + 192 (the projection and two WENO-MR
+    evaluations of 96), and n_c for the flux difference)."""
     NC = NS + D + 1
     pair = 26 + 18 * D + 21 * NS
     ec = 6 * pair

@@ -4,7 +4,7 @@
  * check and the benchmark's CPU-baseline leg use it.  It shares no code with
  * the CUDA library.  See es_oracle.h for the data layout.
  *
- * Readings of points the paper leaves open (each also listed in the design doc):
+ * Readings of points the paper leaves open:
  *  - nodes sit at cell centres, dxi = box length / n (Sec. 3 puts nodes on both
  *    ends; the workloads count cells);
  *  - ghost nodes: periodic sides wrap (x shifted by the box length), all other
