@@ -394,6 +394,21 @@ def main_ours(args):
                               "what": "residual + SSP-RK3 stage updates only, no mesh redistribution"}
     del rk
 
+    # uniform-mesh mode (the paper's UM-WENOMR runs): the same instance on its uniform mesh,
+    # fixed (no redistribution, metrics once per step); the paper compares MM and UM costs
+    um = Single(pb.with_(fixed_mesh=True), U, x, es.MIXED, torch)
+    um.step()
+    um.reset()
+    tiles["uniform_mesh_mixed"] = tune(um)
+    um.capture()
+    um.reset()
+    kum = max(3, min(args.steps, 200))
+    tum = time_steps(um, kum, 3, torch, flush)
+    forms["uniform_mesh_mixed"] = {"value": pb.ncell * 3 * kum / tum, "ms_per_step": 1e3 * tum / kum,
+                                   "mm_over_um_cost": (t_main / args.steps) / (tum / kum),
+                                   "what": "fixed uniform mesh: CFL step + SSP-RK3, metrics once per step"}
+    del um
+
     # kernel profile (dominant kernel = flux) of both forms
     prof_m = kernel_profile(main, args.steps, torch)
     prof_d = kernel_profile(r64, k64, torch)

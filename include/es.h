@@ -53,6 +53,7 @@ typedef enum es_status {
 
 enum { ES_BC_PERIODIC = 0, ES_BC_REFLECT = 1, ES_BC_INFLOW = 2, ES_BC_OUTFLOW = 3 };
 enum { ES_FP64 = 0, ES_MIXED = 1 };
+enum { ES_WENO_MR = 0, ES_WENO_JS = 1 };
 enum { ES_SIG_RHO = 0, ES_SIG_RHO1 = 1, ES_SIG_RHO2 = 2, ES_SIG_P = 3, ES_SIG_Y2 = 4, ES_SIG_V1 = 5 };
 
 /* One instance.  Physics: Gamma_l, c_{v,l}, p_{inf,l} (Sec. 1, Eq. (1.2)).
@@ -83,6 +84,10 @@ typedef struct es_config {
     double alpha[4];         /* monitor weights alpha_k >= 0 */
     int mu;                  /* Jacobi sweeps per step (>= 0) */
     int nf;                  /* filter passes per step (>= 0) */
+    int weno;                /* ES_WENO_MR (Appendix A; the paper's scheme) or ES_WENO_JS */
+    int fixed_mesh;          /* 1: the mesh never moves (the paper's uniform-mesh runs): xdot = 0,
+                                no monitor or sweeps, metrics formed once per step and x never
+                                rewritten; sigma, alpha, mu and nf are ignored */
 } es_config;
 
 typedef struct es_ctx es_ctx;

@@ -110,6 +110,8 @@ std::string check_cfg(const es_config& g)
         if (!(g.alpha[s] >= 0)) return "alpha must be >= 0";
     }
     if (g.mu < 0 || g.nf < 0) return "mu and nf must be >= 0";
+    if (g.weno != ES_WENO_MR && g.weno != ES_WENO_JS) return "weno must be ES_WENO_MR or ES_WENO_JS";
+    if (g.fixed_mesh != 0 && g.fixed_mesh != 1) return "fixed_mesh must be 0 or 1";
     return "";
 }
 
@@ -151,6 +153,14 @@ Inst make_inst(const es_config& g)
     for (int s = 0; s < 4; ++s) { I.sigma[s] = g.sigma[s]; I.alpha[s] = g.alpha[s]; }
     I.mu = g.mu;
     I.nf = g.nf;
+    I.weno = g.weno;
+    I.fixed = g.fixed_mesh;
+    if (I.fixed) {
+        // no monitor, no sweeps: the mesh step reduces to the CFL time step
+        I.n_sigma = 0;
+        I.mu = 0;
+        I.nf = 0;
+    }
     I.ntile_nodes = node_tiles(I, 0);
     for (int l = 0; l < 2; ++l) {
         I.f_gamma[l] = (float)I.gamma[l];
@@ -315,17 +325,19 @@ void stage_ptrs(es_ctx* c, int i, double* JU, double* J, double* x, const double
     double* Bx = Bj + n;
     const double* in_u[3] = { JU, Au, Bu };
     const double* in_j[3] = { J, Aj, Bj };
-    const double* in_x[3] = { x, Ax, Bx };
+    const bool fixed = I.fixed != 0;
+    const double* in_x[3] = { x, fixed ? x : Ax, fixed ? x : Bx };
     double* out_u[3] = { Au, Bu, JU };
     double* out_j[3] = { Aj, Bj, J };
-    double* out_x[3] = { Ax, Bx, x };
+    // a fixed mesh is never rewritten (no x update in the RK stages)
+    double* out_x[3] = { fixed ? nullptr : Ax, fixed ? nullptr : Bx, fixed ? nullptr : x };
     for (int s = 0; s < 3; ++s) {
         StagePtrs P;
         memset(&P, 0, sizeof(P));
         P.JU = in_u[s];
         P.J = in_j[s];
         P.x = in_x[s];
-        P.xdot = xdot ? xdot : S.zeros;
+        P.xdot = (xdot && !fixed) ? xdot : S.zeros;
         P.M = S.M;
         P.accU = S.accU;
         P.accJ = S.accJ;
@@ -357,6 +369,11 @@ void launch_mesh(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStream
     red_init_kernel<<<(c->n_inst + 127) / 128, 128, 0, st>>>(c->dS, c->n_inst);
     int gc = node_grid(c, c->n_cell);
     launch_cfl_grad(c->mixed, gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
+    if (c->hI[0].fixed) {
+        // fixed mesh: Delta t only; xdot = 0 (the metrics above carry no VCL part)
+        launch_xdot(c->mixed, gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
+        return;
+    }
     int nf = c->hI[0].nf, mu = c->hI[0].mu;
     if (nf == 0) launch_monitor_theta(c->mixed, gc, st, c->dI, c->w_cell, c->n_cell, c->dS);
     for (int f = 0; f < nf; ++f) launch_filter(c->mixed, f == 0, gc, st, c->dI, c->w_cell, c->n_cell, c->dS, f % 2);
@@ -374,8 +391,10 @@ void launch_step(es_ctx* c, const StagePtrs& mesh, const StagePtrs* tab_mesh, co
                  StagePtrs* const tab_stage[3], cudaStream_t st)
 {
     launch_mesh(c, mesh, tab_mesh, st, true);
+    // the first stage reuses the metrics of x^n; on a fixed mesh every stage does
+    const bool fixed = c->hI[0].fixed != 0;
     for (int s = 0; s < 3; ++s)
-        launch_residual(c, stage[s], tab_stage[s], true, RK_A[s], RK_B[s], st, s > 0);
+        launch_residual(c, stage[s], tab_stage[s], true, RK_A[s], RK_B[s], st, s > 0 && !fixed);
 }
 
 __global__ void time_acc_kernel(double* t, const double* dt_dtau) { *t += dt_dtau[0]; }
@@ -396,8 +415,8 @@ es_status es_create_batch(const es_config* cfgs, int n_inst, es_ctx** out)
             return ES_ERR_ARG;
         }
         if (cfgs[i].d != cfgs[0].d || cfgs[i].N != cfgs[0].N || cfgs[i].precision != cfgs[0].precision ||
-            cfgs[i].mu != cfgs[0].mu || cfgs[i].nf != cfgs[0].nf) {
-            fprintf(stderr, "es_create: instances of a batch must share d, N, precision, mu and nf\n");
+            cfgs[i].mu != cfgs[0].mu || cfgs[i].nf != cfgs[0].nf || cfgs[i].fixed_mesh != cfgs[0].fixed_mesh) {
+            fprintf(stderr, "es_create: instances of a batch must share d, N, precision, mu, nf and fixed_mesh\n");
             return ES_ERR_UNSUPPORTED;
         }
     }
@@ -551,7 +570,10 @@ es_status es_rk_step(es_ctx* c, double* JU, double* J, double* x, const double* 
     if (c->n_inst != 1) return fail(c, ES_ERR_UNSUPPORTED, "es_rk_step: single-instance context required");
     StagePtrs P[3];
     stage_ptrs(c, 0, JU, J, x, xdot, dt, P);
-    for (int s = 0; s < 3; ++s) launch_residual(c, P[s], nullptr, true, RK_A[s], RK_B[s], (cudaStream_t)stream);
+    // on a fixed mesh the stage meshes equal x, so the metrics of the first stage serve all three
+    const bool fixed = c->hI[0].fixed != 0;
+    for (int s = 0; s < 3; ++s)
+        launch_residual(c, P[s], nullptr, true, RK_A[s], RK_B[s], (cudaStream_t)stream, s == 0 || !fixed);
     return cuda_check(c, "es_rk_step");
 }
 

@@ -37,6 +37,8 @@ struct Inst {
     int n_sigma, sigma[4];
     double alpha[4];
     int mu, nf;
+    int weno;                 // ES_WENO_MR (0) or ES_WENO_JS (1)
+    int fixed;                // 1: the mesh never moves
     int ntile_nodes;          // 1D node tiles for node-wise kernels
     // binary32 copies of the physical and scheme constants for the FP32 arithmetic of the
     // mixed form (converting the binary64 ones in the kernels would use the FP64 pipe)

@@ -556,10 +556,12 @@ __global__ void __launch_bounds__(FLUX_TPB, (sizeof(R) == 4 ? (D == 2 ? 3 : 2) :
                 double rj = P.accJ[id] + r[NC];
                 double bj = A != 0.0 ? A * P.J0[id] : 0.0;
                 P.Jo[id] = bj + B * (P.J[id] + dt * rj);
+                if (P.xo) {    // null on a fixed mesh
 #pragma unroll
-                for (int j = 0; j < D; ++j) {
-                    double bx = A != 0.0 ? A * P.x0[j * ncell + id] : 0.0;
-                    P.xo[j * ncell + id] = bx + B * (P.x[j * ncell + id] + dt * P.xdot[j * ncell + id]);
+                    for (int j = 0; j < D; ++j) {
+                        double bx = A != 0.0 ? A * P.x0[j * ncell + id] : 0.0;
+                        P.xo[j * ncell + id] = bx + B * (P.x[j * ncell + id] + dt * P.xdot[j * ncell + id]);
+                    }
                 }
             }
         }

@@ -40,7 +40,7 @@ class EsConfig(C.Structure):
         ("es", C.c_int), ("precision", C.c_int),
         ("chi", C.c_double * 3), ("weno_eps", C.c_double), ("cfl", C.c_double),
         ("n_sigma", C.c_int), ("sigma", C.c_int * 4), ("alpha", C.c_double * 4),
-        ("mu", C.c_int), ("nf", C.c_int),
+        ("mu", C.c_int), ("nf", C.c_int), ("weno", C.c_int), ("fixed_mesh", C.c_int),
     ]
 
 
@@ -109,6 +109,7 @@ def make_config(pb: Problem, precision: int = FP64) -> EsConfig:
     for q, (s, a) in enumerate(zip(pb.sigma, pb.alpha)):
         c.sigma[q], c.alpha[q] = s, a
     c.mu, c.nf = pb.mu, pb.nf
+    c.weno, c.fixed_mesh = int(pb.weno), int(pb.fixed_mesh)
     return c
 
 

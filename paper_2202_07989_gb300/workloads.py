@@ -49,6 +49,8 @@ class Problem:
     alpha: Tuple[float, ...] = (100.0,)
     mu: int = 10
     nf: int = 3
+    weno: int = 0                             # 0: WENO-MR (Appendix A), 1: WENO-JS
+    fixed_mesh: bool = False                  # the mesh never moves (uniform-mesh runs)
 
     @property
     def nc(self) -> int:

@@ -153,6 +153,10 @@ def test_mesh_redistribute(d, N, bc, mu, nf):
     assert abs(dd[1] - dtau_o) <= TOL_FP64 * dtau_o
     e = fieldwise(xd.cpu().numpy(), xd_o, floor=1e-12)
     assert max(e) <= 1e-11, e
+    # redistributed node positions x^n + Delta t xdot = x^n + Delta_tau (x^[mu] - x^n)
+    xn_g = x + dd[0] * xd.cpu().numpy()
+    xn_o = x + dt_o * xd_o
+    assert rel_max_err(xn_g, xn_o) <= 1e-12
 
 
 @pytest.mark.parametrize("d,N", [(2, 2), (3, 1)])
@@ -233,6 +237,33 @@ def test_flux_tile_shapes_and_autotune_bitwise(d, N, form):
     _ctx(pb, form).es_rk_step(*B, G[3], dt)
     for a, b in zip(A, B):
         assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("d,N", [(2, 2), (3, 1)])
+@pytest.mark.parametrize("form", [0, 1])
+def test_fixed_mesh_step(d, N, form):
+    """Fixed-mesh mode (the paper's uniform-mesh runs, here on a curvilinear mesh): es_step
+    takes Delta t from Eq. (cfl), leaves x untouched bit for bit, sets xdot = 0 and advances
+    (JU, J) by SSP-RK3 with the metrics formed once; vs the oracle's CFL step and RK step with
+    xdot = 0, FP64 at 1e-12 (J at 1e-12 relative), mixed at FP32 level."""
+    torch = need_gpu()
+    pb, JU, J, x, xdot = case(d, N, GRIDS[d], "mixed", es=True, seed=29)
+    pb = pb.with_(fixed_mesh=True)
+    o = Oracle(pb)
+    dt = o.cfl_dt(JU, J, x)
+    JUo, Jo, _ = o.rk_step(JU, J, x, np.zeros_like(x), dt)
+    ctx = _ctx(pb, form)
+    JUg, Jg, xg = to_dev(JU, torch), to_dev(J, torch), to_dev(x, torch)
+    x0 = xg.clone()
+    xd, dd = ctx.es_step(JUg, Jg, xg)
+    assert torch.equal(xg, x0)
+    assert float(xd.abs().max()) == 0.0
+    assert abs(float(dd[0]) - dt) <= (1e-12 if form == 0 else 1e-6) * dt
+    e = fieldwise(JUg.cpu().numpy(), JUo, N=N, d=d)
+    eJ = rel_max_err(Jg.cpu().numpy(), Jo)
+    print("fixed-mesh step errors", d, N, form, e, eJ)
+    assert eJ <= 1e-12
+    assert max(e) <= (TOL_FP64 if form == 0 else 5e-5), e
 
 
 @pytest.mark.parametrize("d,N", CASES)
