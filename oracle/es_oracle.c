@@ -418,6 +418,35 @@ void or_eigvec_avg(const or_config* c, const double* Ul, const double* Ur, doubl
 /* fifth-order multi-resolution WENO, Appendix A                              */
 /* ------------------------------------------------------------------------ */
 
+/* Classical fifth-order WENO at x_{j+1/2}.  Three quadratic reconstructions on the
+ * cells {j-2,j-1,j}, {j-1,j,j+1}, {j,j+1,j+2} give the candidate values q_k; the
+ * smoothness indicator of each is the sum over the first two derivatives of the
+ * squared derivative integrated over cell j (scaled by the cell width); the linear
+ * weights 1/10, 6/10, 3/10 make the combination the five-cell value; the nonlinear
+ * weights are d_k / (eps + beta_k)^2, normalised. */
+double or_weno_js(const double* w5, double eps)
+{
+    double Wm2 = w5[0], Wm1 = w5[1], W0 = w5[2], Wp1 = w5[3], Wp2 = w5[4];
+    double q[3], beta[3], a[3];
+    const double d[3] = { 0.1, 0.6, 0.3 };
+    q[0] = (2.0 * Wm2 - 7.0 * Wm1 + 11.0 * W0) / 6.0;
+    q[1] = (-Wm1 + 5.0 * W0 + 2.0 * Wp1) / 6.0;
+    q[2] = (2.0 * W0 + 5.0 * Wp1 - Wp2) / 6.0;
+    beta[0] = 13.0 / 12.0 * (Wm2 - 2.0 * Wm1 + W0) * (Wm2 - 2.0 * Wm1 + W0)
+            + 0.25 * (Wm2 - 4.0 * Wm1 + 3.0 * W0) * (Wm2 - 4.0 * Wm1 + 3.0 * W0);
+    beta[1] = 13.0 / 12.0 * (Wm1 - 2.0 * W0 + Wp1) * (Wm1 - 2.0 * W0 + Wp1)
+            + 0.25 * (Wm1 - Wp1) * (Wm1 - Wp1);
+    beta[2] = 13.0 / 12.0 * (W0 - 2.0 * Wp1 + Wp2) * (W0 - 2.0 * Wp1 + Wp2)
+            + 0.25 * (3.0 * W0 - 4.0 * Wp1 + Wp2) * (3.0 * W0 - 4.0 * Wp1 + Wp2);
+    double as = 0.0, num = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        a[k] = d[k] / ((eps + beta[k]) * (eps + beta[k]));
+        as += a[k];
+        num += a[k] * q[k];
+    }
+    return num / as;
+}
+
 double or_weno_mr(const double* w5, const double* chi, double eps)
 {
     double Wm2 = w5[0], Wm1 = w5[1], W0 = w5[2], Wp1 = w5[3], Wp2 = w5[4];
@@ -715,8 +744,8 @@ static void dissipation(const or_config* c, double u6[6][MAXC], const double* G,
     for (int m = 0; m < nc; ++m) {
         double wl[5] = { W[0][m], W[1][m], W[2][m], W[3][m], W[4][m] };
         double wr[5] = { W[5][m], W[4][m], W[3][m], W[2][m], W[1][m] };
-        double Wminus = or_weno_mr(wl, c->chi, c->weno_eps);
-        double Wplus = or_weno_mr(wr, c->chi, c->weno_eps);
+        double Wminus = c->weno ? or_weno_js(wl, c->weno_eps) : or_weno_mr(wl, c->chi, c->weno_eps);
+        double Wplus = c->weno ? or_weno_js(wr, c->weno_eps) : or_weno_mr(wr, c->chi, c->weno_eps);
         double jw = Wplus - Wminus, jump = W[3][m] - W[2][m];
         int sjw = (jw > 0) - (jw < 0), sj = (jump > 0) - (jump < 0);
         /* Y of Sec. 3.4: 1 when sign([[W_m]]^WENOMR) sign([[W_m]]) > 0.  A jump no larger

@@ -43,6 +43,7 @@ typedef struct or_config {
     int mu;                  /* Jacobi sweeps per step */
     int nf;                  /* low-pass filter passes per step */
     double y_band;           /* sign band of [[W_m]] in Y relative to its round-off scale; 0 = 1e-12 */
+    int weno;                /* 0: WENO-MR (Appendix A), 1: classical fifth-order WENO-JS */
 } or_config;
 
 int    or_nc(const or_config* c);
@@ -74,6 +75,9 @@ void   or_eigvec_avg(const or_config* c, const double* Ul, const double* Ur, dou
 
 /* fifth-order multi-resolution WENO value at x_{j+1/2} from W_{j-2..j+2} (Appendix A) */
 double or_weno_mr(const double* w5, const double* chi, double eps);
+/* classical fifth-order WENO (Jiang and Shu, cited in Sec. 3.4 and Sec. 5 for the
+   MM-WENOJS comparison) at x_{j+1/2} from W_{j-2..j+2}, with the same epsilon */
+double or_weno_js(const double* w5, double eps);
 
 /* geometry (Sec. 3.2) */
 void   or_metrics(const or_config* c, const double* x, const double* xdot, double* M);

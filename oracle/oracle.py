@@ -26,7 +26,7 @@ class OrConfig(C.Structure):
         ("gamma", C.c_double * 2), ("cv", C.c_double * 2), ("pinf", C.c_double * 2),
         ("chi", C.c_double * 3), ("weno_eps", C.c_double), ("cfl", C.c_double),
         ("n_sigma", C.c_int), ("sigma", C.c_int * 4), ("alpha", C.c_double * 4),
-        ("mu", C.c_int), ("nf", C.c_int), ("y_band", C.c_double),
+        ("mu", C.c_int), ("nf", C.c_int), ("y_band", C.c_double), ("weno", C.c_int),
     ]
 
 
@@ -50,6 +50,7 @@ def lib():
             "or_eigvec_point": (None, [cp, dp, dp]),
             "or_eigvec_avg": (None, [cp, dp, dp, dp, dp]),
             "or_weno_mr": (C.c_double, [dp, dp, C.c_double]),
+            "or_weno_js": (C.c_double, [dp, C.c_double]),
             "or_metrics": (None, [cp, dp, dp, dp]),
             "or_init_J": (None, [cp, dp, dp]),
             "or_rhs": (None, [cp, dp, dp, dp, dp, dp, dp]),
@@ -92,6 +93,7 @@ def config(pb) -> OrConfig:
         c.sigma[q], c.alpha[q] = s, a
     c.mu, c.nf = pb.mu, pb.nf
     c.y_band = 0.0
+    c.weno = int(getattr(pb, "weno", 0))
     return c
 
 
@@ -173,6 +175,9 @@ class Oracle:
     def weno_mr(self, w5, chi=None, eps=None):
         chi = _f64(chi if chi is not None else self.pb.chi)
         return self.L.or_weno_mr(_p(_f64(w5)), _p(chi), float(self.pb.weno_eps if eps is None else eps))
+
+    def weno_js(self, w5, eps=None):
+        return self.L.or_weno_js(_p(_f64(w5)), float(self.pb.weno_eps if eps is None else eps))
 
     # ---- grid operators ----------------------------------------------------
     def _grid(self, a, fields):

@@ -328,6 +328,77 @@ def test_weno_jump_is_fifth_order():
 
 
 # ---------------------------------------------------------------------------
+# classical WENO-JS (the MM-WENOJS comparison of Sec. 5)
+# ---------------------------------------------------------------------------
+
+def test_weno_js_linear_limit_is_five_point_stencil():
+    """With linear weights (eps -> infinity) WENO-JS also gives (2,-13,47,27,-3)/60."""
+    o = Oracle(_pb(2, 1))
+    rng = np.random.default_rng(31)
+    st = np.array(GOLD["weno_mr"]["linear_stencil_60ths"]) / 60.0
+    for _ in range(20):
+        w5 = rng.uniform(-2, 2, size=5)
+        got = o.weno_js(w5, eps=1e30)
+        assert abs(got - st @ w5) <= 1e-14 * (np.abs(st) @ np.abs(w5))
+
+
+def test_weno_js_from_symbolic_definitions():
+    """Candidate values, smoothness indicators and linear weights rebuilt with sympy from
+    their definitions (quadratic reconstructions of three cell averages; beta_k = sum over
+    the first two derivatives of the squared derivative integrated over the central cell;
+    linear weights that reproduce the five-cell reconstruction), then compared with the
+    oracle's WENO-JS value."""
+    sp = pytest.importorskip("sympy")
+    x = sp.symbols("x")
+    Ws = sp.symbols("w0:5")
+    half = sp.Rational(1, 2)
+
+    def recon(deg, cells):
+        cs = sp.symbols("c0:%d" % (deg + 1))
+        h = sum(ci * x ** i for i, ci in enumerate(cs))
+        eqs = [sp.integrate(h, (x, l - half, l + half)) - Ws[l + 2] for l in cells]
+        return sp.expand(h.subs(sp.solve(eqs, cs)))
+
+    p = [recon(2, [-2, -1, 0]), recon(2, [-1, 0, 1]), recon(2, [0, 1, 2])]
+    p5 = recon(4, [-2, -1, 0, 1, 2])
+    dk = sp.symbols("d0:3")
+    lin = sp.expand(sum(dk[k] * p[k].subs(x, half) for k in range(3)) - p5.subs(x, half))
+    dsol = sp.solve([lin.coeff(w) for w in Ws], dk)
+    d = np.array([float(dsol[dk[k]]) for k in range(3)])
+    assert np.allclose(d, [0.1, 0.6, 0.3], rtol=0, atol=1e-15)
+    beta = [sp.lambdify(Ws, sum(sp.integrate(sp.diff(pk, x, a) ** 2, (x, -half, half)) for a in (1, 2))) for pk in p]
+    qv = [sp.lambdify(Ws, pk.subs(x, half)) for pk in p]
+    o = Oracle(_pb(2, 1))
+    eps = GOLD["weno_mr"]["eps"]
+    rng = np.random.default_rng(32)
+    samples = [rng.uniform(-1, 1, size=5) for _ in range(30)]
+    samples += [np.array([0, 0, 0, 0, 1.0]), np.array([0, 0, 1.0, 1, 1]), np.array([1.0, 1, 1, 0, 0])]
+    for w in samples:
+        b = np.array([f(*w) for f in beta])
+        q = np.array([f(*w) for f in qv])
+        a = d / (eps + b) ** 2
+        want = (a @ q) / a.sum()
+        got = o.weno_js(w)
+        assert abs(got - want) <= 1e-13 * max(1.0, np.abs(w).max()), (w, got, want)
+
+
+def test_weno_js_jump_is_fifth_order_and_eno_at_a_step():
+    """[[W]]^WENOJS vanishes at fifth order on smooth data away from extrema, and at a step
+    the reconstruction comes from the smooth side."""
+    o = Oracle(_pb(2, 1))
+    errs = []
+    for n in [20, 40, 80]:
+        h = 2 * math.pi / n
+        xs = 0.3 + h * np.arange(-2, 4)
+        f = np.sin(xs)
+        errs.append(abs(o.weno_js(f[5:0:-1]) - o.weno_js(f[0:5])))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(orders) > 4.5, (errs, orders)
+    assert abs(o.weno_js(np.array([0.0, 0.0, 0.0, 1.0, 1.0]))) < 1e-6
+    assert abs(o.weno_js(np.array([0.0, 0.0, 1.0, 1.0, 1.0])) - 1.0) < 1e-6
+
+
+# ---------------------------------------------------------------------------
 # metrics (Sec. 3.2)
 # ---------------------------------------------------------------------------
 
@@ -452,11 +523,13 @@ def test_ec_entropy_production_zero(d, N):
 
 
 @pytest.mark.parametrize("d,N", CASES)
-def test_es_entropy_production_nonpositive(d, N):
-    """The ES scheme dissipates entropy: P <= 0 (Sec. 3.4, the sign property of Y), on smooth
-    and on discontinuous periodic data."""
+@pytest.mark.parametrize("weno", [0, 1])
+def test_es_entropy_production_nonpositive(d, N, weno):
+    """The ES scheme dissipates entropy: P <= 0 (Sec. 3.4, the sign property of Y, which holds
+    for any reconstruction of [[W]], so for WENO-MR and WENO-JS), on smooth and on
+    discontinuous periodic data."""
     n = 12 if d == 2 else 8
-    pb = W.random_problem(d, N, (n,) * d, es=True)
+    pb = W.random_problem(d, N, (n,) * d, es=True).with_(weno=weno)
     o = Oracle(pb)
     rng = np.random.default_rng(25)
     x = W.smooth_mesh(pb, rng)
