@@ -409,6 +409,21 @@ def main_ours(args):
                                    "what": "fixed uniform mesh: CFL step + SSP-RK3, metrics once per step"}
     del um
 
+    # the MM-WENOJS comparison: the same moving-mesh step with the classical WENO-JS
+    # dissipation (the paper reports WENO-MR 7.6..12% dearer on CPUs)
+    js = Single(pb.with_(weno=1), U, x, es.MIXED, torch)
+    js.step()
+    js.reset()
+    tiles["mm_wenojs_mixed"] = tune(js)
+    js.capture()
+    js.reset()
+    kjs = max(3, min(args.steps, 200))
+    tjs = time_steps(js, kjs, 3, torch, flush)
+    forms["mm_wenojs_mixed"] = {"value": pb.ncell * 3 * kjs / tjs, "ms_per_step": 1e3 * tjs / kjs,
+                                "wenomr_over_wenojs_cost": (t_main / args.steps) / (tjs / kjs),
+                                "what": "moving-mesh step with the WENO-JS dissipation"}
+    del js
+
     # kernel profile (dominant kernel = flux) of both forms
     prof_m = kernel_profile(main, args.steps, torch)
     prof_d = kernel_profile(r64, k64, torch)

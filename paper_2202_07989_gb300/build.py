@@ -8,7 +8,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libes.so")
-SOURCES = ["es_flux_2d1.cu", "es_flux_2d2.cu", "es_flux_3d1.cu", "es_flux_3d2.cu", "es_geom.cu", "es_mesh.cu", "es_api.cu"]
+SOURCES = ["es_flux_%s_%s.cu" % (case, kind) for case in ("2d1", "2d2", "3d1", "3d2") for kind in ("mr", "js")] + \
+    ["es_geom.cu", "es_mesh.cu", "es_api.cu"]
 HEADERS = ["es_common.cuh", "es_kernels.cuh", "es_mesh.cuh", "es_flux_impl.cuh"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-gencode", "arch=compute_103a,code=sm_103a",
@@ -40,7 +41,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             raise RuntimeError("nvcc failed: %s\n%s%s" % (" ".join(cmd), r.stdout, r.stderr))
         return r.stdout + r.stderr
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES), max(2, os.cpu_count() or 2))) as ex:
         for out in ex.map(run, jobs):
             if verbose and out.strip():
                 print(out)

@@ -16,6 +16,7 @@ using namespace es;
 struct es_ctx {
     int n_inst = 0, d = 2, N = 1, nc = 4;
     bool mixed = false;
+    int weno = 0;             // reconstruction of the dissipation: 0 WENO-MR, 1 WENO-JS
     std::vector<Inst> hI;
     Inst* dI = nullptr;
     std::vector<Scratch> hS;
@@ -194,10 +195,15 @@ int2* build_work(es_ctx* c, F count, int& n)
 }
 
 template <int D, int NS>
-void prepare_all()
+void prepare_all(int weno)
 {
-    prepare_flux<D, NS, double>();
-    prepare_flux<D, NS, float>();
+    if (weno) {
+        prepare_flux<D, NS, double, 1>();
+        prepare_flux<D, NS, float, 1>();
+    } else {
+        prepare_flux<D, NS, double, 0>();
+        prepare_flux<D, NS, float, 0>();
+    }
 }
 
 // one flux launch in the given tile shape and grid
@@ -205,7 +211,11 @@ void flux_launch(es_ctx* c, const FluxLaunch& L, int shape, int grid, cudaStream
 {
     if (grid > L.nwork) grid = L.nwork;
     if (grid <= 0) return;
-#define FD(d, n) do { if (c->mixed) launch_flux<d, n, float>(L, shape, grid, st); else launch_flux<d, n, double>(L, shape, grid, st); } while (0)
+#define FD(d, n)                                                                                      \
+    do {                                                                                              \
+        if (c->weno) { if (c->mixed) launch_flux<d, n, float, 1>(L, shape, grid, st); else launch_flux<d, n, double, 1>(L, shape, grid, st); } \
+        else { if (c->mixed) launch_flux<d, n, float, 0>(L, shape, grid, st); else launch_flux<d, n, double, 0>(L, shape, grid, st); }        \
+    } while (0)
     if (c->d == 2 && c->N == 1) FD(2, 1);
     else if (c->d == 2 && c->N == 2) FD(2, 2);
     else if (c->d == 3 && c->N == 1) FD(3, 1);
@@ -224,7 +234,11 @@ long long flux_tiles(const Inst& I, int k, int shape)
 
 int flux_occ(es_ctx* c, int shape)
 {
-#define FO(d, n) return c->mixed ? flux_blocks_per_sm<d, n, float>(shape) : flux_blocks_per_sm<d, n, double>(shape)
+#define FO(d, n)                                                                                             \
+    do {                                                                                                     \
+        if (c->weno) return c->mixed ? flux_blocks_per_sm<d, n, float, 1>(shape) : flux_blocks_per_sm<d, n, double, 1>(shape); \
+        return c->mixed ? flux_blocks_per_sm<d, n, float, 0>(shape) : flux_blocks_per_sm<d, n, double, 0>(shape);            \
+    } while (0)
     if (c->d == 2 && c->N == 1) FO(2, 1);
     if (c->d == 2 && c->N == 2) FO(2, 2);
     if (c->d == 3 && c->N == 1) FO(3, 1);
@@ -415,8 +429,9 @@ es_status es_create_batch(const es_config* cfgs, int n_inst, es_ctx** out)
             return ES_ERR_ARG;
         }
         if (cfgs[i].d != cfgs[0].d || cfgs[i].N != cfgs[0].N || cfgs[i].precision != cfgs[0].precision ||
-            cfgs[i].mu != cfgs[0].mu || cfgs[i].nf != cfgs[0].nf || cfgs[i].fixed_mesh != cfgs[0].fixed_mesh) {
-            fprintf(stderr, "es_create: instances of a batch must share d, N, precision, mu, nf and fixed_mesh\n");
+            cfgs[i].mu != cfgs[0].mu || cfgs[i].nf != cfgs[0].nf || cfgs[i].fixed_mesh != cfgs[0].fixed_mesh ||
+            cfgs[i].weno != cfgs[0].weno) {
+            fprintf(stderr, "es_create: instances of a batch must share d, N, precision, mu, nf, fixed_mesh and weno\n");
             return ES_ERR_UNSUPPORTED;
         }
     }
@@ -426,6 +441,7 @@ es_status es_create_batch(const es_config* cfgs, int n_inst, es_ctx** out)
     c->N = cfgs[0].N;
     c->nc = c->N + c->d + 1;
     c->mixed = cfgs[0].precision == ES_MIXED;
+    c->weno = cfgs[0].weno;
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
@@ -485,10 +501,10 @@ es_status es_create_batch(const es_config* cfgs, int n_inst, es_ctx** out)
     ok = ok && dalloc(c, (void**)&c->d_first_cell, sizeof(int) * (n_inst + 1)) &&
          dalloc(c, (void**)&c->partial, sizeof(double) * 2 * (first[n_inst] > 0 ? first[n_inst] : 1));
     if (ok) cudaMemcpy(c->d_first_cell, first.data(), sizeof(int) * (n_inst + 1), cudaMemcpyHostToDevice);
-    if (c->d == 2 && c->N == 1) prepare_all<2, 1>();
-    else if (c->d == 2 && c->N == 2) prepare_all<2, 2>();
-    else if (c->d == 3 && c->N == 1) prepare_all<3, 1>();
-    else prepare_all<3, 2>();
+    if (c->d == 2 && c->N == 1) prepare_all<2, 1>(c->weno);
+    else if (c->d == 2 && c->N == 2) prepare_all<2, 2>(c->weno);
+    else if (c->d == 3 && c->N == 1) prepare_all<3, 1>(c->weno);
+    else prepare_all<3, 2>(c->weno);
     for (int k = 0; k < c->d; ++k) c->flux_grid[k] = c->sms * flux_occ(c, c->flux_shape[k]);
     cudaError_t e = cudaDeviceSynchronize();
     if (!ok || e != cudaSuccess || !c->w_pad || !c->w_cell || (c->d == 3 && !c->w_ext)) {

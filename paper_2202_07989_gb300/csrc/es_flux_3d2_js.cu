@@ -1,0 +1,7 @@
+// Flux kernels of the 3D, 2-species case with the WENO-JS dissipation, in both compute
+// types and every tile shape (one translation unit per case keeps the build parallel).
+#include "es_flux_impl.cuh"
+
+namespace es {
+ES_FLUX_INSTANTIATE(3, 2, 1)
+}  // namespace es

@@ -142,6 +142,41 @@ __device__ __forceinline__ R weno_mr(R w0, R w1, R w2, R w3, R w4, R c1, R c2, R
     }
 }
 
+// classical fifth-order WENO (Jiang and Shu; the MM-WENOJS comparison of Sec. 5) at
+// x_{j+1/2} from W_{j-2..j+2}: candidate values of the three quadratic reconstructions,
+// their smoothness indicators, linear weights 1/10, 6/10, 3/10 and weights d_k/(eps+beta_k)^2
+template <typename R>
+__device__ __forceinline__ R weno_js(R w0, R w1, R w2, R w3, R w4, R eps)
+{
+    const R s0 = w0 - R(2) * w1 + w2, t0 = w0 - R(4) * w1 + R(3) * w2;
+    const R s1 = w1 - R(2) * w2 + w3, t1 = w1 - w3;
+    const R s2 = w2 - R(2) * w3 + w4, t2 = R(3) * w2 - R(4) * w3 + w4;
+    const R e0 = eps + (R(13.0 / 12.0) * s0 * s0 + R(0.25) * t0 * t0);
+    const R e1 = eps + (R(13.0 / 12.0) * s1 * s1 + R(0.25) * t1 * t1);
+    const R e2 = eps + (R(13.0 / 12.0) * s2 * s2 + R(0.25) * t2 * t2);
+    const R q0 = (R(2) * w0 - R(7) * w1 + R(11) * w2) * R(1.0 / 6.0);
+    const R q1 = (-w1 + R(5) * w2 + R(2) * w3) * R(1.0 / 6.0);
+    const R q2 = (R(2) * w2 + R(5) * w3 - w4) * R(1.0 / 6.0);
+    if constexpr (std::is_same<R, double>::value) {
+        // common denominator (e0 e1 e2)^2: one division
+        const R f0 = e0 * e0, f1 = e1 * e1, f2 = e2 * e2;
+        const R a0 = R(0.1) * f1 * f2, a1 = R(0.6) * f0 * f2, a2 = R(0.3) * f0 * f1;
+        return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+    } else {
+        // products of the squared terms could leave the binary32 range: one division each
+        const R a0 = Ar<R>::dv(R(0.1), e0 * e0), a1 = Ar<R>::dv(R(0.6), e1 * e1), a2 = Ar<R>::dv(R(0.3), e2 * e2);
+        return Ar<R>::dv(a0 * q0 + a1 * q1 + a2 * q2, a0 + a1 + a2);
+    }
+}
+
+// the reconstruction of the dissipation: WK = 0 WENO-MR (Appendix A), 1 WENO-JS
+template <typename R, int WK>
+__device__ __forceinline__ R weno_val(R w0, R w1, R w2, R w3, R w4, R c1, R c2, R c3, R eps)
+{
+    if constexpr (WK == 0) return weno_mr<R>(w0, w1, w2, w3, w4, c1, c2, c3, eps);
+    else return weno_js<R>(w0, w1, w2, w3, w4, eps);
+}
+
 template <int D, int NS>
 struct Lay {
     static constexpr int NC = NS + D + 1;
@@ -185,7 +220,7 @@ __device__ __forceinline__ void load_U_r(const Inst& I, const double* __restrict
 // per interface the 2w-order EC flux as sum_m alpha_m sum_s of the stored pairs, the GCL
 // flux of J xi_k/t and the ES dissipation; (4) divergence and output / RK stage.
 // FP32 tiles: 3 CTAs per SM in 2D (<= 85 registers), 2 in 3D; FP64 tiles: 1 (FP64-pipe bound)
-template <int D, int NS, typename R, int S, int WT>
+template <int D, int NS, typename R, int S, int WT, int WK>
 __global__ void __launch_bounds__(FLUX_TPB, (sizeof(R) == 4 ? (D == 2 ? 3 : 2) : 1)) flux_kernel(FluxLaunch L)
 {
     using Y = Lay<D, NS>;
@@ -494,8 +529,8 @@ __global__ void __launch_bounds__(FLUX_TPB, (sizeof(R) == 4 ? (D == 2 ? 3 : 2) :
                         for (int q = 0; q < NC; ++q) s_ += rc[q] * NR(Y::VV + q, j);
                         wv[j] = s_;
                     }
-                    R Wm = weno_mr<R>(wv[0], wv[1], wv[2], wv[3], wv[4], ch1, ch2, ch3, eps);
-                    R Wp = weno_mr<R>(wv[5], wv[4], wv[3], wv[2], wv[1], ch1, ch2, ch3, eps);
+                    R Wm = weno_val<R, WK>(wv[0], wv[1], wv[2], wv[3], wv[4], ch1, ch2, ch3, eps);
+                    R Wp = weno_val<R, WK>(wv[5], wv[4], wv[3], wv[2], wv[1], ch1, ch2, ch3, eps);
                     R jw = Wp - Wm, jp = wv[3] - wv[2];
                     R rn = R(0);
 #pragma unroll
@@ -582,47 +617,47 @@ static size_t smem_of()
 #define ES_FLUX_SHAPES(X) X(0) X(1) X(2) X(3) X(4) X(5)
 static_assert(NSHAPE == 6, "ES_FLUX_SHAPES lists every tile shape");
 
-template <int D, int NS, typename R>
+template <int D, int NS, typename R, int WK>
 void prepare_flux()
 {
-#define ES_PREP(SH)                                                                                                  \
-    cudaFuncSetAttribute(flux_kernel<D, NS, R, SHAPE_S[SH], SHAPE_WT[SH]>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                         (int)smem_of<D, NS, R, SHAPE_S[SH], SHAPE_WT[SH]>());
+#define ES_PREP(SH)                                                                                       \
+    cudaFuncSetAttribute(flux_kernel<D, NS, R, SHAPE_S[SH], SHAPE_WT[SH], WK>,                             \
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_of<D, NS, R, SHAPE_S[SH], SHAPE_WT[SH]>());
     ES_FLUX_SHAPES(ES_PREP)
 #undef ES_PREP
 }
 
-template <int D, int NS, typename R>
+template <int D, int NS, typename R, int WK>
 int flux_blocks_per_sm(int shape)
 {
     int nb = 0;
-#define ES_OCC(SH)                                                                                                  \
-    if (shape == SH)                                                                                                \
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, flux_kernel<D, NS, R, SHAPE_S[SH], SHAPE_WT[SH]>, FLUX_TPB, \
-                                                      smem_of<D, NS, R, SHAPE_S[SH], SHAPE_WT[SH]>());
+#define ES_OCC(SH)                                                                                           \
+    if (shape == SH)                                                                                         \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, flux_kernel<D, NS, R, SHAPE_S[SH], SHAPE_WT[SH], WK>, \
+                                                      FLUX_TPB, smem_of<D, NS, R, SHAPE_S[SH], SHAPE_WT[SH]>());
     ES_FLUX_SHAPES(ES_OCC)
 #undef ES_OCC
     return nb > 0 ? nb : 1;
 }
 
-template <int D, int NS, typename R>
+template <int D, int NS, typename R, int WK>
 void launch_flux(const FluxLaunch& L, int shape, int grid, cudaStream_t st)
 {
-#define ES_LAUNCH(SH)                                                                                              \
-    if (shape == SH)                                                                                               \
-        flux_kernel<D, NS, R, SHAPE_S[SH], SHAPE_WT[SH]>                                                           \
+#define ES_LAUNCH(SH)                                                                                        \
+    if (shape == SH)                                                                                         \
+        flux_kernel<D, NS, R, SHAPE_S[SH], SHAPE_WT[SH], WK>                                                 \
             <<<grid, FLUX_TPB, smem_of<D, NS, R, SHAPE_S[SH], SHAPE_WT[SH]>(), st>>>(L);
     ES_FLUX_SHAPES(ES_LAUNCH)
 #undef ES_LAUNCH
 }
 
-// explicit instantiation of one (dimension, species) case in both compute types
-#define ES_FLUX_INSTANTIATE(D, NS)                                                \
-    template void prepare_flux<D, NS, double>();                                  \
-    template void prepare_flux<D, NS, float>();                                   \
-    template int flux_blocks_per_sm<D, NS, double>(int);                          \
-    template int flux_blocks_per_sm<D, NS, float>(int);                           \
-    template void launch_flux<D, NS, double>(const FluxLaunch&, int, int, cudaStream_t); \
-    template void launch_flux<D, NS, float>(const FluxLaunch&, int, int, cudaStream_t);
+// explicit instantiation of one (dimension, species, reconstruction) case in both compute types
+#define ES_FLUX_INSTANTIATE(D, NS, WK)                                                        \
+    template void prepare_flux<D, NS, double, WK>();                                          \
+    template void prepare_flux<D, NS, float, WK>();                                           \
+    template int flux_blocks_per_sm<D, NS, double, WK>(int);                                  \
+    template int flux_blocks_per_sm<D, NS, float, WK>(int);                                   \
+    template void launch_flux<D, NS, double, WK>(const FluxLaunch&, int, int, cudaStream_t);  \
+    template void launch_flux<D, NS, float, WK>(const FluxLaunch&, int, int, cudaStream_t);
 
 }  // namespace es

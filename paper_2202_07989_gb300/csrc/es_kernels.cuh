@@ -39,12 +39,12 @@ __global__ void conversion_check_kernel(const double* in, int n, float* o32, dou
 __global__ void init_J_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work, int nwork);
 
 // flux + divergence (+ RK stage) for one direction; D dims, NS species, R compute type,
-// tile shape index `shape`
-template <int D, int NS, typename R>
+// WK the reconstruction of the dissipation (0 WENO-MR, 1 WENO-JS), tile shape index `shape`
+template <int D, int NS, typename R, int WK>
 void launch_flux(const FluxLaunch& L, int shape, int grid, cudaStream_t st);
-template <int D, int NS, typename R>
+template <int D, int NS, typename R, int WK>
 void prepare_flux();
-template <int D, int NS, typename R>
+template <int D, int NS, typename R, int WK>
 int flux_blocks_per_sm(int shape);
 
 }  // namespace es
