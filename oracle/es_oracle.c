@@ -966,8 +966,11 @@ void or_monitor(const or_config* c, const double* JU, const double* J, double* t
         for (i[1] = 0; i[1] < c->n[1]; ++i[1])
             for (i[0] = 0; i[0] < c->n[0]; ++i[0]) {
                 long id = idx_of(c, i);
+                double Uc[MAXC];
+                U_at(c, JU, J, i, Uc);
                 for (int s = 0; s < c->n_sigma; ++s) {
-                    double acc = 0.0;
+                    /* |grad_xi sigma| by central differences, or the Laplacian's magnitude */
+                    double acc = 0.0, lap = 0.0;
                     for (int k = 0; k < d; ++k) {
                         int ip[3] = { i[0], i[1], i[2] }, im[3] = { i[0], i[1], i[2] };
                         ip[k] += 1;
@@ -975,21 +978,75 @@ void or_monitor(const or_config* c, const double* JU, const double* J, double* t
                         double Up[MAXC], Um[MAXC];
                         U_at(c, JU, J, ip, Up);
                         U_at(c, JU, J, im, Um);
-                        double gk = (sigma_of(c, c->sigma[s], Up) - sigma_of(c, c->sigma[s], Um)) / (2.0 * c->dxi[k]);
+                        double sp = sigma_of(c, c->sigma[s], Up), sm = sigma_of(c, c->sigma[s], Um);
+                        double gk = (sp - sm) / (2.0 * c->dxi[k]);
                         acc += gk * gk;
+                        lap += (sp - 2.0 * sigma_of(c, c->sigma[s], Uc) + sm) / (c->dxi[k] * c->dxi[k]);
                     }
-                    g[s * nn + id] = sqrt(acc);
+                    g[s * nn + id] = c->sigma_op[s] == OR_MON_LAP ? fabs(lap) : sqrt(acc);
                     if (g[s * nn + id] > gmax[s]) gmax[s] = g[s * nn + id];
                 }
             }
     for (long id = 0; id < nn; ++id) {
         double t = 1.0;
         for (int s = 0; s < c->n_sigma; ++s)
-            if (gmax[s] > 0.0) { double r = g[s * nn + id] / gmax[s]; t += c->alpha[s] * r * r; }
+            if (gmax[s] > 0.0) {
+                double r = g[s * nn + id] / gmax[s];
+                t += c->sigma_op[s] == OR_MON_GRAD2 ? c->alpha[s] * r * r : c->alpha[s] * r;
+            }
         theta[id] = sqrt(t);
     }
     free(g);
     for (int f = 0; f < c->nf; ++f) or_filter(c, theta);
+}
+
+void or_schlieren(const or_config* c, const double* JU, const double* J, const double* x, double psi1, double psi2,
+                  double* phi)
+{
+    int d = c->d;
+    long nn = or_ncell(c), np = or_npad(c);
+    int n2 = d == 3 ? c->n[2] : 1;
+    double* M = (double*)malloc(sizeof(double) * (size_t)np * d * (d + 1));
+    double* g = (double*)malloc(sizeof(double) * (size_t)nn);
+    or_metrics(c, x, NULL, M);
+    double gmax = 0.0;
+    int i[3] = { 0, 0, 0 };
+    for (i[2] = 0; i[2] < n2; ++i[2])
+        for (i[1] = 0; i[1] < c->n[1]; ++i[1])
+            for (i[0] = 0; i[0] < c->n[0]; ++i[0]) {
+                long id = idx_of(c, i);
+                double drho[3] = { 0, 0, 0 };
+                for (int k = 0; k < d; ++k) {
+                    int ip[3] = { i[0], i[1], i[2] }, im[3] = { i[0], i[1], i[2] };
+                    ip[k] += 1;
+                    im[k] -= 1;
+                    double Up[MAXC], Um[MAXC];
+                    U_at(c, JU, J, ip, Up);
+                    U_at(c, JU, J, im, Um);
+                    drho[k] = (sigma_of(c, OR_SIG_RHO, Up) - sigma_of(c, OR_SIG_RHO, Um)) / (2.0 * c->dxi[k]);
+                }
+                double acc = 0.0;
+                for (int j = 0; j < d; ++j) {
+                    double gj = 0.0;
+                    for (int k = 0; k < d; ++k) gj += M[(long)(k * (d + 1) + 1 + j) * np + pidx_of(c, i)] * drho[k];
+                    gj /= J[id];
+                    acc += gj * gj;
+                }
+                g[id] = sqrt(acc);
+                if (g[id] > gmax) gmax = g[id];
+            }
+    for (i[2] = 0; i[2] < n2; ++i[2])
+        for (i[1] = 0; i[1] < c->n[1]; ++i[1])
+            for (i[0] = 0; i[0] < c->n[0]; ++i[0]) {
+                long id = idx_of(c, i);
+                double U[MAXC];
+                U_at(c, JU, J, i, U);
+                double rho = sigma_of(c, OR_SIG_RHO, U);
+                double psi = (psi1 * U[0] + (c->N == 2 ? psi2 * U[1] : 0.0)) / rho;
+                phi[id] = gmax > 0.0 ? exp(-psi * g[id] / gmax) : 1.0;
+            }
+    free(M);
+    free(g);
 }
 
 /* one pass of the low-pass filter: weights (1/2)^(|j1|+..+|jd| + d) */

@@ -44,9 +44,20 @@ typedef struct or_config {
     int nf;                  /* low-pass filter passes per step */
     double y_band;           /* sign band of [[W_m]] in Y relative to its round-off scale; 0 = 1e-12 */
     int weno;                /* 0: WENO-MR (Appendix A), 1: classical fifth-order WENO-JS */
+    int sigma_op[4];         /* per monitor term: OR_MON_GRAD2 (Eq. (monitor)), OR_MON_GRAD, OR_MON_LAP */
 } or_config;
 
+/* monitor terms: alpha (|grad_xi sigma| / max)^2 as in Eq. (monitor); alpha |grad_xi sigma| / max
+   and alpha |Laplacian_xi sigma| / max as in the vortex monitor of Example 5.1 */
+enum { OR_MON_GRAD2 = 0, OR_MON_GRAD = 1, OR_MON_LAP = 2 };
+
 int    or_nc(const or_config* c);
+
+/* schlieren function of Example 5.8, Eq. (schlieren): Phi = exp(-Psi |grad rho| / max |grad rho|),
+   Psi = (psi1 rho_1 + psi2 rho_2) / rho, grad the physical gradient (1/J) sum_k J xi_k/x
+   d rho/d xi_k with second-order central differences in xi; Phi = 1 where max |grad rho| = 0 */
+void   or_schlieren(const or_config* c, const double* JU, const double* J, const double* x, double psi1, double psi2,
+                    double* phi);
 long   or_ncell(const or_config* c);
 long   or_npad(const or_config* c);
 

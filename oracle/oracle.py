@@ -27,6 +27,7 @@ class OrConfig(C.Structure):
         ("chi", C.c_double * 3), ("weno_eps", C.c_double), ("cfl", C.c_double),
         ("n_sigma", C.c_int), ("sigma", C.c_int * 4), ("alpha", C.c_double * 4),
         ("mu", C.c_int), ("nf", C.c_int), ("y_band", C.c_double), ("weno", C.c_int),
+        ("sigma_op", C.c_int * 4),
     ]
 
 
@@ -58,6 +59,7 @@ def lib():
             "or_rhs_margins": (None, [cp, dp, dp, dp, dp, dp, dp, dp]),
             "or_cfl_dt": (C.c_double, [cp, dp, dp, dp]),
             "or_monitor": (None, [cp, dp, dp, dp]),
+            "or_schlieren": (None, [cp, dp, dp, dp, C.c_double, C.c_double, dp]),
             "or_filter": (None, [cp, dp]),
             "or_jacobi": (None, [cp, dp, dp, dp]),
             "or_limiter": (C.c_double, [cp, dp, dp]),
@@ -94,6 +96,8 @@ def config(pb) -> OrConfig:
     c.mu, c.nf = pb.mu, pb.nf
     c.y_band = 0.0
     c.weno = int(getattr(pb, "weno", 0))
+    for q, op in enumerate(getattr(pb, "sigma_op", ())):
+        c.sigma_op[q] = int(op)
     return c
 
 
@@ -238,6 +242,13 @@ class Oracle:
         th = np.zeros(pb.shape)
         self.L.or_monitor(C.byref(self.cfg), _p(self._grid(JU, pb.nc)), _p(self._grid(J, 1)), _p(th))
         return th
+
+    def schlieren(self, JU, J, x, psi1=30.0, psi2=150.0):
+        pb = self.pb
+        phi = np.zeros(pb.shape)
+        self.L.or_schlieren(C.byref(self.cfg), _p(self._grid(JU, pb.nc)), _p(self._grid(J, 1)), _p(self._grid(x, pb.d)),
+                            float(psi1), float(psi2), _p(phi))
+        return phi
 
     def filter(self, theta):
         th = self._grid(theta, 1).copy()

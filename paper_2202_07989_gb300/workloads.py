@@ -22,6 +22,9 @@ import numpy as np
 
 PERIODIC, REFLECT, INFLOW, OUTFLOW = 0, 1, 2, 3
 SIG_RHO, SIG_RHO1, SIG_RHO2, SIG_P, SIG_Y2, SIG_V1 = 0, 1, 2, 3, 4, 5
+# monitor terms: alpha (|grad sigma|/max)^2 of Eq. (monitor); the linear gradient and Laplacian
+# terms of Example 5.1's vortex monitor
+MON_GRAD2, MON_GRAD, MON_LAP = 0, 1, 2
 
 SEED = 2202
 
@@ -50,6 +53,7 @@ class Problem:
     mu: int = 10
     nf: int = 3
     weno: int = 0                             # 0: WENO-MR (Appendix A), 1: WENO-JS
+    sigma_op: Tuple[int, ...] = ()            # per monitor term: MON_GRAD2 (default), MON_GRAD, MON_LAP
     fixed_mesh: bool = False                  # the mesh never moves (uniform-mesh runs)
 
     @property

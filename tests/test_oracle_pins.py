@@ -691,6 +691,77 @@ def test_monitor_closed_form():
     np.testing.assert_allclose(o.monitor(U, J), want, rtol=1e-14)
 
 
+def test_vortex_monitor_closed_form():
+    """Example 5.1's monitor Theta = (1 + 20 |grad_xi rho| / max + 10 |Laplacian_xi rho| / max)^(1/2)
+    (linear terms) for rho = 1 + a sin(2 pi xi_1) + b cos(2 pi xi_2) on a periodic grid.  The
+    central first and second differences of the trigonometric terms are written with the
+    identities sin(t+h) - sin(t-h) = 2 cos t sin h and sin(t+h) - 2 sin t + sin(t-h) =
+    -2 sin t (1 - cos h)."""
+    pb = W.random_problem(2, 1, (16, 12)).with_(sigma=(W.SIG_RHO, W.SIG_RHO), alpha=(20.0, 10.0),
+                                                sigma_op=(W.MON_GRAD, W.MON_LAP), nf=0)
+    o = Oracle(pb)
+    xi = W.xi_nodes(pb)
+    a, b = 0.3, 0.2
+    rho = 1.0 + a * np.sin(2 * math.pi * xi[0]) + b * np.cos(2 * math.pi * xi[1])
+    U = W.prim_to_cons(pb, [rho], [np.zeros_like(rho)] * 2, np.ones_like(rho))
+    J = np.ones(pb.shape)
+    h1, h2 = pb.dxi[0], pb.dxi[1]
+    t1, t2 = 2 * math.pi * xi[0], 2 * math.pi * xi[1]
+    g1 = a * np.cos(t1) * math.sin(2 * math.pi * h1) / h1
+    g2 = -b * np.sin(t2) * math.sin(2 * math.pi * h2) / h2
+    lap = -2 * a * np.sin(t1) * (1 - math.cos(2 * math.pi * h1)) / h1 ** 2 \
+          - 2 * b * np.cos(t2) * (1 - math.cos(2 * math.pi * h2)) / h2 ** 2
+    g = np.sqrt(g1 ** 2 + g2 ** 2)
+    want = np.sqrt(1 + 20.0 * g / g.max() + 10.0 * np.abs(lap) / np.abs(lap).max())
+    np.testing.assert_allclose(o.monitor(U, J), want, rtol=1e-12)
+
+
+@pytest.mark.parametrize("N", [1, 2])
+def test_schlieren_exact_on_a_linear_density(N):
+    """Eq. (schlieren) on the identity mesh with rho = 1 + 0.5 xi_1 between reflecting walls:
+    |grad rho| = 0.5 at interior nodes (central differences are exact) and 0.25 at the wall
+    nodes (the mirrored ghost equals the node), so Phi = exp(-Psi) inside and exp(-Psi/2) on
+    the walls; Psi = (30 rho_1 + 150 rho_2) / rho (constant here).  Uniform rho gives Phi = 1."""
+    pb = W.random_problem(2, N, (12, 10), bc="reflect")
+    o = Oracle(pb)
+    xi = W.xi_nodes(pb)
+    x = np.stack(xi)
+    rho = 1.0 + 0.5 * xi[0]
+    frac = [1.0] if N == 1 else [0.6, 0.4]
+    U = W.prim_to_cons(pb, [f * rho for f in frac], [np.zeros_like(rho)] * 2, np.ones_like(rho))
+    J = np.ones(pb.shape)
+    psi = 30.0 if N == 1 else 30.0 * 0.6 + 150.0 * 0.4
+    want = np.full(pb.shape, math.exp(-psi))
+    want[..., 0] = want[..., -1] = math.exp(-psi / 2)
+    np.testing.assert_allclose(o.schlieren(U, J, x), want, rtol=1e-12)
+    U1 = W.prim_to_cons(pb, [f * np.ones_like(rho) for f in frac], [np.zeros_like(rho)] * 2, np.ones_like(rho))
+    assert np.all(o.schlieren(U1, J, x) == 1.0)
+
+
+def test_schlieren_gradient_converges_on_curvilinear_mesh():
+    """The physical gradient (1/J) sum_k J xi_k/x (d rho/d xi_k) of the schlieren function
+    converges at second order to the exact |grad_x rho| on a perturbed periodic mesh
+    (a transposed metric contraction would leave an O(1) error)."""
+    errs = []
+    for n in (16, 32, 64):
+        pb = W.random_problem(2, 1, (n, n))
+        o = Oracle(pb)
+        rng = np.random.default_rng(33)
+        x = W.smooth_mesh(pb, rng, amp=0.05)
+        J = o.init_J(x)
+        k = 2 * math.pi
+        rho = 1.0 + 0.2 * np.sin(k * x[0]) * np.cos(k * x[1])
+        gx = 0.2 * k * np.cos(k * x[0]) * np.cos(k * x[1])
+        gy = -0.2 * k * np.sin(k * x[0]) * np.sin(k * x[1])
+        g = np.sqrt(gx ** 2 + gy ** 2)
+        U = W.prim_to_cons(pb, [rho], [np.zeros_like(rho)] * 2, np.ones_like(rho))
+        phi = o.schlieren(U * J, J, x)
+        got = -np.log(phi) / 30.0          # |grad rho| / max |grad rho|
+        errs.append(np.abs(got - g / g.max()).max())
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(orders) > 1.7, (errs, orders)
+
+
 def test_limiter_keeps_node_order_and_mesh_velocity():
     """x^{n+1} = x^n + Delta_tau delta_tau x keeps every grid line monotone (the bounds of
     Sec. 4 allow at most half the neighbour spacing) and xdot = Delta_tau delta_tau x / Delta t."""
