@@ -54,6 +54,7 @@ typedef enum es_status {
 enum { ES_BC_PERIODIC = 0, ES_BC_REFLECT = 1, ES_BC_INFLOW = 2, ES_BC_OUTFLOW = 3 };
 enum { ES_FP64 = 0, ES_MIXED = 1 };
 enum { ES_WENO_MR = 0, ES_WENO_JS = 1 };
+enum { ES_MON_GRAD2 = 0, ES_MON_GRAD = 1, ES_MON_LAP = 2 };
 enum { ES_SIG_RHO = 0, ES_SIG_RHO1 = 1, ES_SIG_RHO2 = 2, ES_SIG_P = 3, ES_SIG_Y2 = 4, ES_SIG_V1 = 5 };
 
 /* One instance.  Physics: Gamma_l, c_{v,l}, p_{inf,l} (Sec. 1, Eq. (1.2)).
@@ -88,6 +89,10 @@ typedef struct es_config {
     int fixed_mesh;          /* 1: the mesh never moves (the paper's uniform-mesh runs): xdot = 0,
                                 no monitor or sweeps, metrics formed once per step and x never
                                 rewritten; sigma, alpha, mu and nf are ignored */
+    int sigma_op[4];         /* per monitor term: ES_MON_GRAD2 (alpha (|grad_xi sigma|/max)^2, Eq.
+                                (monitor); 0 = default), ES_MON_GRAD (alpha |grad_xi sigma|/max) or
+                                ES_MON_LAP (alpha |Laplacian_xi sigma|/max), the linear terms of
+                                Example 5.1's vortex monitor; second-order central differences */
 } es_config;
 
 typedef struct es_ctx es_ctx;
@@ -174,6 +179,17 @@ es_status es_get_tuning(const es_ctx* ctx, int* shape, int* S, int* WT, int* gri
 /* Fix the flux launch of direction k to tile shape `shape` (0..5) and `grid`
  * CTAs (0 = SM count x occupancy of that shape).  ES_ERR_ARG when out of range. */
 es_status es_set_tuning(es_ctx* ctx, int k, int shape, int grid);
+
+/* Schlieren function of Example 5.8, Eq. (schlieren), on one instance:
+ * phi = exp(-Psi |grad rho| / max |grad rho|), Psi = (psi1 rho_1 + psi2 rho_2) / rho
+ * (the paper uses psi1 = 30, psi2 = 150), grad the physical gradient
+ * (1/J) sum_k J xi_k/x d rho/d xi_k with second-order central differences in xi and
+ * the metrics of x; phi = 1 everywhere when max |grad rho| = 0.  JU, J, x: state
+ * (read).  phi (written, DEVICE): 1 field.  FP64 in both precisions; no host
+ * synchronisation.  Uses the context's scratch (not concurrently with other calls
+ * on the same context). */
+es_status es_schlieren(es_ctx* ctx, const double* JU, const double* J, const double* x, double psi1, double psi2,
+                       double* phi, void* stream);
 
 /* Entropy diagnostics (Sec. 1 definitions, Sec. 5 total entropy):
  * out2[0] = P = sum_i dxi^d (V_i . dJU_i - phi_i dJ_i)  (= d/dt of the total

@@ -109,6 +109,7 @@ std::string check_cfg(const es_config& g)
     for (int s = 0; s < g.n_sigma; ++s) {
         if (g.sigma[s] < 0 || g.sigma[s] > 5) return "bad monitor variable";
         if (!(g.alpha[s] >= 0)) return "alpha must be >= 0";
+        if (g.sigma_op[s] < ES_MON_GRAD2 || g.sigma_op[s] > ES_MON_LAP) return "bad monitor term operator";
     }
     if (g.mu < 0 || g.nf < 0) return "mu and nf must be >= 0";
     if (g.weno != ES_WENO_MR && g.weno != ES_WENO_JS) return "weno must be ES_WENO_MR or ES_WENO_JS";
@@ -151,7 +152,7 @@ Inst make_inst(const es_config& g)
     I.weno_eps = g.weno_eps;
     I.cfl = g.cfl;
     I.n_sigma = g.n_sigma;
-    for (int s = 0; s < 4; ++s) { I.sigma[s] = g.sigma[s]; I.alpha[s] = g.alpha[s]; }
+    for (int s = 0; s < 4; ++s) { I.sigma[s] = g.sigma[s]; I.alpha[s] = g.alpha[s]; I.sigma_op[s] = g.sigma_op[s]; }
     I.mu = g.mu;
     I.nf = g.nf;
     I.weno = g.weno;
@@ -632,6 +633,28 @@ es_status es_step(es_ctx* c, double* JU, double* J, double* x, double dt_fixed, 
     StagePtrs* const none[3] = { nullptr, nullptr, nullptr };
     launch_step(c, M, nullptr, P, none, (cudaStream_t)stream);
     return cuda_check(c, "es_step");
+}
+
+es_status es_schlieren(es_ctx* c, const double* JU, const double* J, const double* x, double psi1, double psi2,
+                       double* phi, void* stream)
+{
+    if (!c) return ES_ERR_ARG;
+    if (!JU || !J || !x || !phi) return fail(c, ES_ERR_ARG, "es_schlieren: null pointer");
+    if (c->n_inst != 1) return fail(c, ES_ERR_UNSUPPORTED, "es_schlieren: single-instance context required");
+    cudaStream_t st = (cudaStream_t)stream;
+    StagePtrs P;
+    memset(&P, 0, sizeof(P));
+    P.JU = JU;
+    P.J = J;
+    P.x = x;
+    P.M = c->hS[0].M;
+    P.out = phi;
+    launch_metrics(c, P, nullptr, st);     // metrics of x (no VCL part) into the scratch
+    red_init_kernel<<<(c->n_inst + 127) / 128, 128, 0, st>>>(c->dS, c->n_inst);
+    const int gc = node_grid(c, c->n_cell);
+    schlieren_grad_kernel<<<gc, NODE_TPB, 0, st>>>(c->dI, P, c->w_cell, c->n_cell, c->dS);
+    schlieren_phi_kernel<<<gc, NODE_TPB, 0, st>>>(c->dI, P, c->w_cell, c->n_cell, c->dS, psi1, psi2);
+    return cuda_check(c, "es_schlieren");
 }
 
 es_status entropy_production(es_ctx* c, const double* JU, const double* J, const double* dJU, const double* dJ,

@@ -18,6 +18,7 @@ constexpr int HALO = 3;    // stencil half width of the flux (w = 3) and WENO-MR
 enum { BC_PERIODIC = 0, BC_REFLECT = 1, BC_INFLOW = 2, BC_OUTFLOW = 3 };
 enum { SIG_RHO = 0, SIG_RHO1 = 1, SIG_RHO2 = 2, SIG_P = 3, SIG_Y2 = 4, SIG_V1 = 5 };
 enum { ST_NONPHYSICAL = 1, ST_TIMEOUT = 2 };
+enum { MON_GRAD2 = 0, MON_GRAD = 1, MON_LAP = 2 };   // monitor term operators
 
 // alpha_{3,m} of the sixth-order EC flux (Sec. 3.1) and the matching delta weights
 __host__ __device__ constexpr double alpha3(int m) { return m == 1 ? 1.5 : (m == 2 ? -0.3 : 1.0 / 30.0); }
@@ -34,7 +35,7 @@ struct Inst {
     double gamma[2], cv[2], pinf[2], Rs[2], cvG[2], pinf_tot;
     int es;
     double chi[3], weno_eps, cfl;
-    int n_sigma, sigma[4];
+    int n_sigma, sigma[4], sigma_op[4];
     double alpha[4];
     int mu, nf;
     int weno;                 // ES_WENO_MR (0) or ES_WENO_JS (1)

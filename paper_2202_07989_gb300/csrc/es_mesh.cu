@@ -19,6 +19,8 @@ __global__ void red_init_kernel(const Scratch* __restrict__ scr, int ninst)
     double* r = scr[i].red;
     for (int q = 0; q < 5; ++q) r[q] = 0.0;
     r[5] = 1.0;
+    r[6] = 0.0;
+    r[7] = 0.0;
 }
 
 template <typename T>
@@ -214,7 +216,9 @@ __global__ void cfl_grad_kernel(const Inst* __restrict__ insts, StagePtrs single
             }
             s = to_d(sr);
             if (!(s >= 0.0)) s = 0.0;
-            R gr[4] = { R(0), R(0), R(0), R(0) };
+            // per term |grad_xi sigma| (squared sums) or the Laplacian (second differences)
+            R gr[4] = { R(0), R(0), R(0), R(0) }, lp[4] = { R(0), R(0), R(0), R(0) }, sc[4];
+            for (int q = 0; q < I.n_sigma; ++q) sc[q] = sigma_t<R>(I, I.sigma[q], U);
             for (int k = 0; k < I.d; ++k) {
                 int ip[3] = { i[0], i[1], i[2] }, im[3] = { i[0], i[1], i[2] };
                 ip[k] += 1;
@@ -222,13 +226,16 @@ __global__ void cfl_grad_kernel(const Inst* __restrict__ insts, StagePtrs single
                 R Up[MAXC], Um[MAXC];
                 load_U_t<R>(I, P.JU, P.J, ip[0], ip[1], ip[2], Up);
                 load_U_t<R>(I, P.JU, P.J, im[0], im[1], im[2], Um);
+                const R h2 = std::is_same<R, float>::value ? R(I.f_h2[k]) : R(I.inv_dxi[k] * I.inv_dxi[k]);
                 for (int q = 0; q < I.n_sigma; ++q) {
-                    R gk = (sigma_t<R>(I, I.sigma[q], Up) - sigma_t<R>(I, I.sigma[q], Um)) * to_r<R>(0.5 * I.inv_dxi[k]);
+                    const R sp = sigma_t<R>(I, I.sigma[q], Up), sm = sigma_t<R>(I, I.sigma[q], Um);
+                    R gk = (sp - sm) * to_r<R>(0.5 * I.inv_dxi[k]);
                     gr[q] += gk * gk;
+                    lp[q] += (sp - R(2) * sc[q] + sm) * h2;
                 }
             }
             for (int q = 0; q < I.n_sigma; ++q) {
-                g[q] = to_d(R(sqrt(gr[q])));
+                g[q] = to_d(I.sigma_op[q] == MON_LAP ? R(fabs(lp[q])) : R(sqrt(gr[q])));
                 if (!(g[q] >= 0.0)) g[q] = 0.0;
                 scr[it.x].g[(long long)q * I.ncell + p] = g[q];
             }
@@ -253,7 +260,8 @@ __device__ __forceinline__ R theta_at(const Inst& I, const Scratch& S, const dou
             R r;
             if constexpr (std::is_same<R, double>::value) r = S.g[(long long)q * I.ncell + p] * inv[q];
             else r = to_r<R>(S.g[(long long)q * I.ncell + p]) * to_r<R>(inv[q]);
-            t += to_r<R>(I.alpha[q]) * r * r;
+            // Eq. (monitor) squares the ratio; the vortex monitor's terms are linear
+            t += I.sigma_op[q] == MON_GRAD2 ? to_r<R>(I.alpha[q]) * r * r : to_r<R>(I.alpha[q]) * r;
         }
     }
     return sqrt(t);
@@ -758,6 +766,66 @@ __global__ void entropy_final_kernel(const Inst* __restrict__ insts, StagePtrs s
         for (int k = 0; k < I.d; ++k) vol *= I.dxi[k];
         P.out[0] = vol * sa;
         P.out[1] = vol * sb;
+    }
+}
+
+// schlieren function (Example 5.8, Eq. (schlieren)), pass 1: |grad_x rho| = |(1/J) sum_k
+// J xi_k/x d rho/d xi_k| with central differences in xi and the metrics in M; per-instance
+// maximum into red[6]
+__global__ void schlieren_grad_kernel(const Inst* __restrict__ insts, StagePtrs single, const int2* __restrict__ work,
+                                      int nwork, const Scratch* __restrict__ scr)
+{
+    __shared__ double sh[32];
+    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+        const int2 it = work[wi];
+        const Inst& I = insts[it.x];
+        const StagePtrs& P = single;
+        int i[3];
+        const bool valid = tile_node(I, it.y, 0, i[0], i[1], i[2]);
+        double gmag = 0.0;
+        if (valid) {
+            const long long p = lin(I, i[0], i[1], i[2]), pid = plin(I, i[0], i[1], i[2]);
+            double drho[3] = { 0.0, 0.0, 0.0 };
+            for (int k = 0; k < I.d; ++k) {
+                int ip[3] = { i[0], i[1], i[2] }, im[3] = { i[0], i[1], i[2] };
+                ip[k] += 1;
+                im[k] -= 1;
+                double Up[MAXC], Um[MAXC];
+                load_U(I, P.JU, P.J, ip[0], ip[1], ip[2], Up);
+                load_U(I, P.JU, P.J, im[0], im[1], im[2], Um);
+                const double rp = Up[0] + (I.N == 2 ? Up[1] : 0.0), rm = Um[0] + (I.N == 2 ? Um[1] : 0.0);
+                drho[k] = (rp - rm) * (0.5 * I.inv_dxi[k]);
+            }
+            double acc = 0.0;
+            for (int j = 0; j < I.d; ++j) {
+                double gj = 0.0;
+                for (int k = 0; k < I.d; ++k) gj += scr[it.x].M[(long long)(k * (I.d + 1) + 1 + j) * I.npad + pid] * drho[k];
+                gj /= P.J[p];
+                acc += gj * gj;
+            }
+            gmag = sqrt(acc);
+            scr[it.x].g[p] = gmag;
+        }
+        const double m = block_max<double>(gmag, sh);
+        if (threadIdx.x == 0) atomic_max_pos(&scr[it.x].red[6], m);
+    }
+}
+
+// pass 2: phi = exp(-Psi |grad rho| / max), Psi = (psi1 rho_1 + psi2 rho_2) / rho; 1 for max 0
+__global__ void schlieren_phi_kernel(const Inst* __restrict__ insts, StagePtrs single, const int2* __restrict__ work,
+                                     int nwork, const Scratch* __restrict__ scr, double psi1, double psi2)
+{
+    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+        const int2 it = work[wi];
+        const Inst& I = insts[it.x];
+        const StagePtrs& P = single;
+        int i0, i1, i2;
+        if (!tile_node(I, it.y, 0, i0, i1, i2)) continue;
+        const long long p = lin(I, i0, i1, i2);
+        const double gmax = scr[it.x].red[6];
+        const double r1 = P.JU[p], r2 = I.N == 2 ? P.JU[I.ncell + p] : 0.0;   // J rho_l: J cancels in Psi
+        const double psi = (psi1 * r1 + psi2 * r2) / (r1 + r2);
+        P.out[p] = gmax > 0.0 ? exp(-psi * scr[it.x].g[p] / gmax) : 1.0;
     }
 }
 

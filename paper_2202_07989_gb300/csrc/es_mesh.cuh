@@ -20,6 +20,10 @@ void launch_jacobi(bool mixed, int d, bool last, int grid, cudaStream_t st, cons
                    const StagePtrs* table, const int2* work, int nwork, const Scratch* scr, int sweep, int theta_sel);
 __global__ void limiter_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work, int nwork,
                                const Scratch* scr);
+__global__ void schlieren_grad_kernel(const Inst* insts, StagePtrs single, const int2* work, int nwork,
+                                      const Scratch* scr);
+__global__ void schlieren_phi_kernel(const Inst* insts, StagePtrs single, const int2* work, int nwork,
+                                     const Scratch* scr, double psi1, double psi2);
 __global__ void entropy_partial_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work,
                                        int nwork, double* partial);
 __global__ void entropy_final_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int* first_work,

@@ -41,6 +41,7 @@ class EsConfig(C.Structure):
         ("chi", C.c_double * 3), ("weno_eps", C.c_double), ("cfl", C.c_double),
         ("n_sigma", C.c_int), ("sigma", C.c_int * 4), ("alpha", C.c_double * 4),
         ("mu", C.c_int), ("nf", C.c_int), ("weno", C.c_int), ("fixed_mesh", C.c_int),
+        ("sigma_op", C.c_int * 4),
     ]
 
 
@@ -65,6 +66,7 @@ def lib():
             "es_rk_step": (C.c_int, [vp, dp, dp, dp, dp, dp, vp]),
             "mesh_redistribute": (C.c_int, [vp, dp, dp, dp, C.c_double, dp, dp, vp]),
             "es_step": (C.c_int, [vp, dp, dp, dp, C.c_double, dp, dp, vp]),
+            "es_schlieren": (C.c_int, [vp, dp, dp, dp, C.c_double, C.c_double, dp, vp]),
             "es_autotune": (C.c_int, [vp, dp, dp, dp, dp, C.c_int, vp]),
             "es_get_tuning": (C.c_int, [vp, ip, ip, ip, ip, C.POINTER(C.c_float)]),
             "es_set_tuning": (C.c_int, [vp, C.c_int, C.c_int, C.c_int]),
@@ -110,6 +112,8 @@ def make_config(pb: Problem, precision: int = FP64) -> EsConfig:
         c.sigma[q], c.alpha[q] = s, a
     c.mu, c.nf = pb.mu, pb.nf
     c.weno, c.fixed_mesh = int(pb.weno), int(pb.fixed_mesh)
+    for q, op in enumerate(pb.sigma_op):
+        c.sigma_op[q] = int(op)
     return c
 
 
@@ -248,6 +252,15 @@ class Context:
 
     def es_set_tuning(self, k: int, shape: int, grid: int = 0):
         self._chk(self.L.es_set_tuning(self.h, int(k), int(shape), int(grid)), "es_set_tuning")
+
+    def es_schlieren(self, JU, J, x, psi1: float = 30.0, psi2: float = 150.0, phi=None):
+        """Schlieren function of Eq. (schlieren) at the nodes."""
+        pb = self.pb
+        if phi is None:
+            phi = torch.empty(pb.shape, dtype=torch.float64, device=JU.device)
+        self._chk(self.L.es_schlieren(self.h, _ptr(JU, pb.nc, pb, "JU"), _ptr(J, 1, pb, "J"), _ptr(x, pb.d, pb, "x"),
+                                      float(psi1), float(psi2), _ptr(phi, 1, pb, "phi"), _stream()), "es_schlieren")
+        return phi
 
     def entropy_production(self, JU, J, dJU=None, dJ=None, out=None):
         pb = self.pb

@@ -295,6 +295,37 @@ def test_rhs_weno_js(d, N, jump):
 
 
 @pytest.mark.parametrize("d,N", CASES)
+@pytest.mark.parametrize("form", [0, 1])
+def test_schlieren(d, N, form):
+    """Eq. (schlieren) on a moving curvilinear mesh with reflecting, inflow, outflow and
+    periodic sides vs the oracle, 1e-12 (FP64 in both forms)."""
+    torch = need_gpu()
+    pb, JU, J, x, xdot = case(d, N, GRIDS[d], "mixed", es=True, seed=41, jump=True)
+    want = Oracle(pb).schlieren(JU, J, x, 30.0, 150.0)
+    got = _ctx(pb, form).es_schlieren(to_dev(JU, torch), to_dev(J, torch), to_dev(x, torch), 30.0, 150.0)
+    err = float(np.abs(got.cpu().numpy() - want).max())
+    assert err <= 1e-12, err
+    assert want.min() < 0.5 < want.max() <= 1.0
+
+
+@pytest.mark.parametrize("bc", ["periodic", "mixed"])
+@pytest.mark.parametrize("form", [0, 1])
+def test_mesh_redistribute_vortex_monitor(bc, form):
+    """Example 5.1's monitor (linear gradient and Laplacian terms, alpha 20 and 10) in the mesh
+    step vs the oracle: FP64 mesh velocity at 1e-11, mixed at FP32 level."""
+    torch = need_gpu()
+    pb, JU, J, x, xdot = case(2, 1, GRIDS[2], bc, seed=43, jump=True)
+    pb = pb.with_(mu=5, nf=3, sigma=(W.SIG_RHO, W.SIG_RHO), alpha=(20.0, 10.0), sigma_op=(W.MON_GRAD, W.MON_LAP))
+    xd_o, dt_o, dtau_o = Oracle(pb).mesh_redistribute(JU, J, x)
+    xd, dd = _ctx(pb, form).mesh_redistribute(to_dev(JU, torch), to_dev(J, torch), to_dev(x, torch))
+    scale = np.abs(xd_o).max()
+    e = np.abs(xd.cpu().numpy() - xd_o).max() / scale
+    print("vortex monitor mesh velocity error", bc, form, e)
+    assert scale > 0
+    assert e <= (1e-11 if form == 0 else 1e-5), e
+
+
+@pytest.mark.parametrize("d,N", CASES)
 def test_entropy_production(d, N):
     torch = need_gpu()
     pb, JU, J, x, xdot = case(d, N, GRIDS[d], "periodic", es=False, seed=9)
