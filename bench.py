@@ -583,6 +583,10 @@ def main_kernel_case(args):
         pb, U, x = W.shock_bubble_2d(nx, ny, length=(2.0, 1.0))
     r = Single(pb, U, x, es.MIXED if args.kernel_form == "mixed" else es.FP64, torch)
     tiles = tune(r) if args.kernel_tune else None
+    if args.kernel_shapes:
+        for k, sh in enumerate(int(v) for v in args.kernel_shapes.split(",")):
+            r.ctx.es_set_tuning(k, sh, 0)
+        tiles = r.ctx.es_get_tuning()
     for _ in range(args.kernel_steps):
         r.step()
     torch.cuda.synchronize()
@@ -611,6 +615,7 @@ def main():
     ap.add_argument("--kernel-steps", type=int, default=2)
     ap.add_argument("--kernel-time", type=int, default=0, help="also time this many eager steps per kernel class")
     ap.add_argument("--kernel-tune", action="store_true", help="run the flux autotuner before the steps")
+    ap.add_argument("--kernel-shapes", default=None, help="fix the flux tile shape per direction, e.g. 2,1")
     args = ap.parse_args()
     if args.kernel_case:
         return main_kernel_case(args)

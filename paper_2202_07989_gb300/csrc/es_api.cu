@@ -291,10 +291,10 @@ void launch_metrics(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStr
 {
     ProfScope ps(c, PC_METRICS, st);
     if (c->d == 2) {
-        metrics2d_kernel<<<node_grid(c, c->n_pad), NODE_TPB, 0, st>>>(c->dI, P, tab, c->w_pad, c->n_pad);
+        pdl_launch(metrics2d_kernel, node_grid(c, c->n_pad), NODE_TPB, 0, st, c->dI, P, tab, c->w_pad, c->n_pad);
     } else {
-        dx3d_kernel<<<node_grid(c, c->n_ext), NODE_TPB, 0, st>>>(c->dI, P, tab, c->w_ext, c->n_ext, c->dS);
-        metrics3d_kernel<<<node_grid(c, c->n_pad), NODE_TPB, 0, st>>>(c->dI, P, tab, c->w_pad, c->n_pad, c->dS);
+        pdl_launch(dx3d_kernel, node_grid(c, c->n_ext), NODE_TPB, 0, st, c->dI, P, tab, c->w_ext, c->n_ext, c->dS);
+        pdl_launch(metrics3d_kernel, node_grid(c, c->n_pad), NODE_TPB, 0, st, c->dI, P, tab, c->w_pad, c->n_pad, c->dS);
     }
 }
 
@@ -381,7 +381,7 @@ void launch_mesh(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStream
     Q.M = c->hS[0].M;
     launch_metrics(c, Q, tab, st);
     ProfScope ps(c, PC_MESH, st);
-    red_init_kernel<<<(c->n_inst + 127) / 128, 128, 0, st>>>(c->dS, c->n_inst);
+    pdl_launch(red_init_kernel, (c->n_inst + 127) / 128, 128, 0, st, c->dS, c->n_inst);
     int gc = node_grid(c, c->n_cell);
     launch_cfl_grad(c->mixed, gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
     if (c->hI[0].fixed) {
@@ -395,7 +395,7 @@ void launch_mesh(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStream
     int th_sel = nf % 2;
     for (int s = 0; s < mu; ++s)
         launch_jacobi(c->mixed, c->d, s == mu - 1, gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS, s, th_sel);
-    if (mu == 0) limiter_kernel<<<gc, NODE_TPB, 0, st>>>(c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
+    if (mu == 0) pdl_launch(limiter_kernel, gc, NODE_TPB, 0, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
     if (step) launch_xdot_vcl(c->mixed, c->d, node_grid(c, c->n_pad), st, c->dI, P, tab, c->w_pad, c->n_pad, c->dS);
     else launch_xdot(c->mixed, gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
 }
@@ -543,7 +543,7 @@ es_status es_init_mesh(es_ctx* c, const double* x, double* J, void* stream)
     P.Jo = J;
     int n = c->hI[0].ntile_nodes;
     // instance 0 only: its cell tiles are the first n entries of the cell work list
-    init_J_kernel<<<node_grid(c, n), NODE_TPB, 0, (cudaStream_t)stream>>>(c->dI, P, nullptr, c->w_cell, n);
+    pdl_launch(init_J_kernel, node_grid(c, n), NODE_TPB, 0, (cudaStream_t)stream, c->dI, P, nullptr, c->w_cell, n);
     return cuda_check(c, "es_init_mesh");
 }
 
@@ -650,10 +650,10 @@ es_status es_schlieren(es_ctx* c, const double* JU, const double* J, const doubl
     P.M = c->hS[0].M;
     P.out = phi;
     launch_metrics(c, P, nullptr, st);     // metrics of x (no VCL part) into the scratch
-    red_init_kernel<<<(c->n_inst + 127) / 128, 128, 0, st>>>(c->dS, c->n_inst);
+    pdl_launch(red_init_kernel, (c->n_inst + 127) / 128, 128, 0, st, c->dS, c->n_inst);
     const int gc = node_grid(c, c->n_cell);
-    schlieren_grad_kernel<<<gc, NODE_TPB, 0, st>>>(c->dI, P, c->w_cell, c->n_cell, c->dS);
-    schlieren_phi_kernel<<<gc, NODE_TPB, 0, st>>>(c->dI, P, c->w_cell, c->n_cell, c->dS, psi1, psi2);
+    pdl_launch(schlieren_grad_kernel, gc, NODE_TPB, 0, st, c->dI, P, c->w_cell, c->n_cell, c->dS);
+    pdl_launch(schlieren_phi_kernel, gc, NODE_TPB, 0, st, c->dI, P, c->w_cell, c->n_cell, c->dS, psi1, psi2);
     return cuda_check(c, "es_schlieren");
 }
 
@@ -672,8 +672,8 @@ es_status entropy_production(es_ctx* c, const double* JU, const double* J, const
     P.out = out2;
     cudaStream_t st = (cudaStream_t)stream;
     ProfScope ps(c, PC_ENTROPY, st);
-    entropy_partial_kernel<<<node_grid(c, c->n_cell), NODE_TPB, 0, st>>>(c->dI, P, nullptr, c->w_cell, c->n_cell, c->partial);
-    entropy_final_kernel<<<1, 256, 0, st>>>(c->dI, P, nullptr, c->d_first_cell, c->partial);
+    pdl_launch(entropy_partial_kernel, node_grid(c, c->n_cell), NODE_TPB, 0, st, c->dI, P, nullptr, c->w_cell, c->n_cell, c->partial);
+    pdl_launch(entropy_final_kernel, 1, 256, 0, st, c->dI, P, nullptr, c->d_first_cell, c->partial);
     return cuda_check(c, "entropy_production");
 }
 

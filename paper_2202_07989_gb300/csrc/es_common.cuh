@@ -48,6 +48,16 @@ struct Inst {
     double mc[3][3];          // (1/2) alpha_m / dxi_k: delta_k of a coordinate divided by dxi_k
 };
 
+// Programmatic dependent launch: every kernel of a step waits until its predecessor has
+// completed and its memory is visible before it touches any data.  A CTA lets the next
+// kernel launch when it exits (no explicit trigger: CTAs of the next kernel would otherwise
+// sit on the SMs beside the running ones).  A no-op for a kernel that was not launched with
+// programmatic stream serialization.
+__device__ __forceinline__ void pdl_entry()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // the constants of an instance in the compute type R
 template <typename R>
 struct Cst;

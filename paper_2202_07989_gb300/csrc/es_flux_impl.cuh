@@ -223,6 +223,7 @@ __device__ __forceinline__ void load_U_r(const Inst& I, const double* __restrict
 template <int D, int NS, typename R, int S, int WT, int WK>
 __global__ void __launch_bounds__(FLUX_TPB, (sizeof(R) == 4 ? (D == 2 ? 3 : 2) : 1)) flux_kernel(FluxLaunch L)
 {
+    pdl_entry();
     using Y = Lay<D, NS>;
     using TL = Tile<S, WT>;
     constexpr int NC = Y::NC, NN = TL::NN, NI = TL::NI, NF = Y::NF, NPL = TL::NPL, NP = TL::NP;
@@ -645,8 +646,8 @@ void launch_flux(const FluxLaunch& L, int shape, int grid, cudaStream_t st)
 {
 #define ES_LAUNCH(SH)                                                                                        \
     if (shape == SH)                                                                                         \
-        flux_kernel<D, NS, R, SHAPE_S[SH], SHAPE_WT[SH], WK>                                                 \
-            <<<grid, FLUX_TPB, smem_of<D, NS, R, SHAPE_S[SH], SHAPE_WT[SH]>(), st>>>(L);
+        pdl_launch(flux_kernel<D, NS, R, SHAPE_S[SH], SHAPE_WT[SH], WK>, grid, FLUX_TPB,                       \
+                   smem_of<D, NS, R, SHAPE_S[SH], SHAPE_WT[SH]>(), st, L);
     ES_FLUX_SHAPES(ES_LAUNCH)
 #undef ES_LAUNCH
 }

@@ -32,6 +32,7 @@ __global__ void __launch_bounds__(NODE_TPB) metrics2d_kernel(const Inst* __restr
                                                               const StagePtrs* __restrict__ table,
                                                               const int2* __restrict__ work, int nwork)
 {
+    pdl_entry();
     constexpr int HX = NT_X + 6, HY = NT_Y + 6;
     __shared__ double sx[2][HY][HX];
     const int lx = (int)threadIdx.x % NT_X, ly = (int)threadIdx.x / NT_X;
@@ -99,6 +100,7 @@ __global__ void __launch_bounds__(NODE_TPB) metrics2d_kernel(const Inst* __restr
 __global__ void dx3d_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
                             const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr)
 {
+    pdl_entry();
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
         int2 it = work[wi];
         const Inst& I = insts[it.x];
@@ -153,6 +155,7 @@ __global__ void dx3d_kernel(const Inst* __restrict__ insts, StagePtrs single, co
 __global__ void metrics3d_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
                                  const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr)
 {
+    pdl_entry();
     // KOF[a][b]: metric row k of the ordered pair (a, b); SGN[a][b]: its sign
     const int KOF[3][3] = { { -1, 2, 1 }, { 2, -1, 0 }, { 1, 0, -1 } };
     const double SGN[3][3] = { { 0.0, -1.0, 1.0 }, { 1.0, 0.0, -1.0 }, { -1.0, 1.0, 0.0 } };
@@ -232,6 +235,7 @@ __global__ void metrics3d_kernel(const Inst* __restrict__ insts, StagePtrs singl
 __global__ void init_J_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
                               const int2* __restrict__ work, int nwork)
 {
+    pdl_entry();
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
         int2 it = work[wi];
         const Inst& I = insts[it.x];

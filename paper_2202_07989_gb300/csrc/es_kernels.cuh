@@ -16,6 +16,24 @@ constexpr int SHAPE_DEFAULT_K0 = 0;    // direction 1: 62 nodes along the line x
 constexpr int SHAPE_DEFAULT_KN = 3;    // directions 2, 3: 30 nodes x 8 neighbouring lines (coalesced)
 constexpr int NODE_TPB = 256;
 
+// launch with programmatic stream serialization (the kernel must begin with pdl_entry())
+template <typename... KArgs, typename... Args>
+inline cudaError_t pdl_launch(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t st,
+                              Args&&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 enum { MODE_WRITE = 0, MODE_ACC = 1, MODE_RK = 2 };
 
 struct FluxLaunch {

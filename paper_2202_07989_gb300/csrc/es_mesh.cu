@@ -14,6 +14,7 @@ namespace es {
 
 __global__ void red_init_kernel(const Scratch* __restrict__ scr, int ninst)
 {
+    pdl_entry();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ninst) return;
     double* r = scr[i].red;
@@ -180,6 +181,7 @@ template <typename R>
 __global__ void cfl_grad_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
                                 const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr)
 {
+    pdl_entry();
     __shared__ double sh[32];
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
         int2 it = work[wi];
@@ -271,6 +273,7 @@ template <typename R>
 __global__ void monitor_theta_kernel(const Inst* __restrict__ insts, const int2* __restrict__ work, int nwork,
                                      const Scratch* __restrict__ scr)
 {
+    pdl_entry();
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
         int2 it = work[wi];
         const Inst& I = insts[it.x];
@@ -290,6 +293,7 @@ template <typename R, bool FROM_G>
 __global__ void filter_kernel(const Inst* __restrict__ insts, const int2* __restrict__ work, int nwork,
                               const Scratch* __restrict__ scr, int parity)
 {
+    pdl_entry();
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
         int2 it = work[wi];
         const Inst& I = insts[it.x];
@@ -329,6 +333,7 @@ __global__ void jacobi_kernel(const Inst* __restrict__ insts, StagePtrs single, 
                               const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr, int sweep,
                               int theta_sel)
 {
+    pdl_entry();
     __shared__ double sh[32];
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
         int2 it = work[wi];
@@ -450,6 +455,7 @@ __global__ void __launch_bounds__(NODE_TPB) jacobi_y_kernel(const Inst* __restri
                                                              const int2* __restrict__ work, int nwork,
                                                              const Scratch* __restrict__ scr, int sweep, int theta_sel)
 {
+    pdl_entry();
     __shared__ double sh[32];
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
         const int2 it = work[wi];
@@ -546,6 +552,7 @@ __device__ inline const double* xmu_of(const StagePtrs& P, const Scratch& S, int
 __global__ void limiter_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
                                const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr)
 {
+    pdl_entry();
     __shared__ double sh[32];
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
         int2 it = work[wi];
@@ -585,6 +592,7 @@ template <bool FAST>
 __global__ void xdot_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
                             const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr)
 {
+    pdl_entry();
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
         int2 it = work[wi];
         const Inst& I = insts[it.x];
@@ -627,6 +635,7 @@ template <int D, bool MIXED>
 __global__ void xdot_vcl_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
                                 const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr)
 {
+    pdl_entry();
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
         const int2 it = work[wi];
         const Inst& I = insts[it.x];
@@ -696,6 +705,7 @@ __global__ void xdot_vcl_kernel(const Inst* __restrict__ insts, StagePtrs single
 __global__ void entropy_partial_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
                                        const int2* __restrict__ work, int nwork, double* __restrict__ partial)
 {
+    pdl_entry();
     __shared__ double sh[2][32];
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
         int2 it = work[wi];
@@ -748,6 +758,7 @@ __global__ void entropy_partial_kernel(const Inst* __restrict__ insts, StagePtrs
 __global__ void entropy_final_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
                                      const int* __restrict__ first_work, const double* __restrict__ partial)
 {
+    pdl_entry();
     __shared__ double sh[2][32];
     int inst = blockIdx.x;
     const Inst& I = insts[inst];
@@ -775,6 +786,7 @@ __global__ void entropy_final_kernel(const Inst* __restrict__ insts, StagePtrs s
 __global__ void schlieren_grad_kernel(const Inst* __restrict__ insts, StagePtrs single, const int2* __restrict__ work,
                                       int nwork, const Scratch* __restrict__ scr)
 {
+    pdl_entry();
     __shared__ double sh[32];
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
         const int2 it = work[wi];
@@ -815,6 +827,7 @@ __global__ void schlieren_grad_kernel(const Inst* __restrict__ insts, StagePtrs 
 __global__ void schlieren_phi_kernel(const Inst* __restrict__ insts, StagePtrs single, const int2* __restrict__ work,
                                      int nwork, const Scratch* __restrict__ scr, double psi1, double psi2)
 {
+    pdl_entry();
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
         const int2 it = work[wi];
         const Inst& I = insts[it.x];
@@ -832,33 +845,33 @@ __global__ void schlieren_phi_kernel(const Inst* __restrict__ insts, StagePtrs s
 void launch_monitor_theta(bool mixed, int grid, cudaStream_t st, const Inst* insts, const int2* work, int nwork,
                           const Scratch* scr)
 {
-    if (mixed) monitor_theta_kernel<float><<<grid, NODE_TPB, 0, st>>>(insts, work, nwork, scr);
-    else monitor_theta_kernel<double><<<grid, NODE_TPB, 0, st>>>(insts, work, nwork, scr);
+    if (mixed) pdl_launch(monitor_theta_kernel<float>, grid, NODE_TPB, 0, st, insts, work, nwork, scr);
+    else pdl_launch(monitor_theta_kernel<double>, grid, NODE_TPB, 0, st, insts, work, nwork, scr);
 }
 
 void launch_filter(bool mixed, bool from_g, int grid, cudaStream_t st, const Inst* insts, const int2* work, int nwork,
                    const Scratch* scr, int parity)
 {
     if (mixed) {
-        if (from_g) filter_kernel<float, true><<<grid, NODE_TPB, 0, st>>>(insts, work, nwork, scr, parity);
-        else filter_kernel<float, false><<<grid, NODE_TPB, 0, st>>>(insts, work, nwork, scr, parity);
+        if (from_g) pdl_launch(filter_kernel<float, true>, grid, NODE_TPB, 0, st, insts, work, nwork, scr, parity);
+        else pdl_launch(filter_kernel<float, false>, grid, NODE_TPB, 0, st, insts, work, nwork, scr, parity);
     } else {
-        if (from_g) filter_kernel<double, true><<<grid, NODE_TPB, 0, st>>>(insts, work, nwork, scr, parity);
-        else filter_kernel<double, false><<<grid, NODE_TPB, 0, st>>>(insts, work, nwork, scr, parity);
+        if (from_g) pdl_launch(filter_kernel<double, true>, grid, NODE_TPB, 0, st, insts, work, nwork, scr, parity);
+        else pdl_launch(filter_kernel<double, false>, grid, NODE_TPB, 0, st, insts, work, nwork, scr, parity);
     }
 }
 
 void launch_cfl_grad(bool mixed, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
                      const StagePtrs* table, const int2* work, int nwork, const Scratch* scr)
 {
-    if (mixed) cfl_grad_kernel<float><<<grid, NODE_TPB, 0, st>>>(insts, single, table, work, nwork, scr);
-    else cfl_grad_kernel<double><<<grid, NODE_TPB, 0, st>>>(insts, single, table, work, nwork, scr);
+    if (mixed) pdl_launch(cfl_grad_kernel<float>, grid, NODE_TPB, 0, st, insts, single, table, work, nwork, scr);
+    else pdl_launch(cfl_grad_kernel<double>, grid, NODE_TPB, 0, st, insts, single, table, work, nwork, scr);
 }
 
 void launch_xdot_vcl(bool mixed, int d, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
                      const StagePtrs* table, const int2* work, int nwork, const Scratch* scr)
 {
-#define XV(D, MX) xdot_vcl_kernel<D, MX><<<grid, NODE_TPB, 0, st>>>(insts, single, table, work, nwork, scr)
+#define XV(D, MX) pdl_launch(xdot_vcl_kernel<D, MX>, grid, NODE_TPB, 0, st, insts, single, table, work, nwork, scr)
     if (d == 2) { if (mixed) XV(2, true); else XV(2, false); }
     else { if (mixed) XV(3, true); else XV(3, false); }
 #undef XV
@@ -867,15 +880,15 @@ void launch_xdot_vcl(bool mixed, int d, int grid, cudaStream_t st, const Inst* i
 void launch_xdot(bool mixed, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
                  const StagePtrs* table, const int2* work, int nwork, const Scratch* scr)
 {
-    if (mixed) xdot_kernel<true><<<grid, NODE_TPB, 0, st>>>(insts, single, table, work, nwork, scr);
-    else xdot_kernel<false><<<grid, NODE_TPB, 0, st>>>(insts, single, table, work, nwork, scr);
+    if (mixed) pdl_launch(xdot_kernel<true>, grid, NODE_TPB, 0, st, insts, single, table, work, nwork, scr);
+    else pdl_launch(xdot_kernel<false>, grid, NODE_TPB, 0, st, insts, single, table, work, nwork, scr);
 }
 
 void launch_jacobi(bool mixed, int d, bool last, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
                    const StagePtrs* table, const int2* work, int nwork, const Scratch* scr, int sweep, int theta_sel)
 {
-#define JL(R, LS) jacobi_kernel<R, LS><<<grid, NODE_TPB, 0, st>>>(insts, single, table, work, nwork, scr, sweep, theta_sel)
-#define JY(D, F, LS) jacobi_y_kernel<D, F, LS><<<grid, NODE_TPB, 0, st>>>(insts, single, table, work, nwork, scr, sweep, theta_sel)
+#define JL(R, LS) pdl_launch(jacobi_kernel<R, LS>, grid, NODE_TPB, 0, st, insts, single, table, work, nwork, scr, sweep, theta_sel)
+#define JY(D, F, LS) pdl_launch(jacobi_y_kernel<D, F, LS>, grid, NODE_TPB, 0, st, insts, single, table, work, nwork, scr, sweep, theta_sel)
     if (mixed) {
         const bool first = sweep == 0;
         if (d == 2) {
