@@ -68,8 +68,9 @@ def flux_flops_per_interface(D, NS, es=True):
 def launches_per_step(pb):
     """Kernel launches of one es_step: the mesh step (metrics of x^n, reduction reset,
     CFL + gradients, nf filter passes or the monitor pass, mu sweeps or the limiter, the
-    velocity + VCL pass), then d flux launches per stage and metrics for stages 2 and 3."""
-    m = 1 if pb.d == 2 else 2
+    velocity + VCL pass), then d flux launches per stage and metrics for stages 2 and 3
+    (2D: one metrics launch; 3D: the position grid, delta_b[x_p] and the metrics)."""
+    m = 1 if pb.d == 2 else 3
     mesh = m + 3 + pb.nf + pb.mu + (pb.nf == 0) + (pb.mu == 0)
     return mesh + 3 * pb.d + 2 * m
 

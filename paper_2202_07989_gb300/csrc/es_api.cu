@@ -26,6 +26,7 @@ struct es_ctx {
     // work lists (inst, tile)
     int2* w_pad = nullptr;  int n_pad = 0;
     int2* w_ext = nullptr;  int n_ext = 0;
+    int2* w_xe = nullptr;   int n_xe = 0;
     int2* w_cell = nullptr; int n_cell = 0;
     int2* w_flux[3][NSHAPE] = {};          // flux work list per direction and tile shape
     int n_flux[3][NSHAPE] = {};
@@ -293,6 +294,7 @@ void launch_metrics(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStr
     if (c->d == 2) {
         pdl_launch(metrics2d_kernel, node_grid(c, c->n_pad), NODE_TPB, 0, st, c->dI, P, tab, c->w_pad, c->n_pad);
     } else {
+        pdl_launch(xe_fill_kernel, node_grid(c, c->n_xe), NODE_TPB, 0, st, c->dI, P, tab, c->w_xe, c->n_xe, c->dS);
         pdl_launch(dx3d_kernel, node_grid(c, c->n_ext), NODE_TPB, 0, st, c->dI, P, tab, c->w_ext, c->n_ext, c->dS);
         pdl_launch(metrics3d_kernel, node_grid(c, c->n_pad), NODE_TPB, 0, st, c->dI, P, tab, c->w_pad, c->n_pad, c->dS);
     }
@@ -459,6 +461,8 @@ es_status es_create_batch(const es_config* cfgs, int n_inst, es_ctx** out)
         if (I.d == 3) {
             long long ne = (long long)(I.n[0] + 12) * (I.n[1] + 12) * (I.n[2] + 12);
             ok = ok && dalloc(c, (void**)&S.D3, sizeof(double) * 9 * ne);
+            const long long nx = (long long)(I.n[0] + 18) * (I.n[1] + 18) * (I.n[2] + 18);
+            ok = ok && dalloc(c, (void**)&S.XE, sizeof(double) * 3 * nx);
         }
         ok = ok && dalloc(c, (void**)&S.accU, sizeof(double) * I.nc * n);
         ok = ok && dalloc(c, (void**)&S.accJ, sizeof(double) * n);
@@ -491,6 +495,7 @@ es_status es_create_batch(const es_config* cfgs, int n_inst, es_ctx** out)
     c->w_pad = build_work(c, [](const Inst& I) { return (long long)node_tiles(I, 3); }, c->n_pad);
     c->w_cell = build_work(c, [](const Inst& I) { return (long long)node_tiles(I, 0); }, c->n_cell);
     if (c->d == 3) c->w_ext = build_work(c, [](const Inst& I) { return (long long)node_tiles(I, 6); }, c->n_ext);
+    if (c->d == 3) c->w_xe = build_work(c, [](const Inst& I) { return (long long)node_tiles(I, 9); }, c->n_xe);
     for (int k = 0; k < c->d; ++k)
         for (int sh = 0; sh < NSHAPE; ++sh) {
             c->w_flux[k][sh] = build_work(c, [k, sh](const Inst& I) { return flux_tiles(I, k, sh); }, c->n_flux[k][sh]);
@@ -508,7 +513,7 @@ es_status es_create_batch(const es_config* cfgs, int n_inst, es_ctx** out)
     else prepare_all<3, 2>(c->weno);
     for (int k = 0; k < c->d; ++k) c->flux_grid[k] = c->sms * flux_occ(c, c->flux_shape[k]);
     cudaError_t e = cudaDeviceSynchronize();
-    if (!ok || e != cudaSuccess || !c->w_pad || !c->w_cell || (c->d == 3 && !c->w_ext)) {
+    if (!ok || e != cudaSuccess || !c->w_pad || !c->w_cell || (c->d == 3 && (!c->w_ext || !c->w_xe))) {
         fprintf(stderr, "es_create: setup failed: %s\n", cudaGetErrorString(e));
         es_destroy(c);
         return ES_ERR_CUDA;

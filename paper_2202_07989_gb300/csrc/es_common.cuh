@@ -109,6 +109,7 @@ struct StagePtrs {
 struct Scratch {
     double* M;                // padded metrics
     double* D3;               // 3D: delta_b[x_p] on the grid with 6 ghost layers
+    double* XE;               // 3D: x on the grid with 9 ghost layers (boundary maps applied once)
     double* accU;
     double* accJ;
     double* red;              // reductions: [0] CFL max, [1..4] monitor maxima, [5] Delta_tau

@@ -96,7 +96,36 @@ __global__ void __launch_bounds__(NODE_TPB) metrics2d_kernel(const Inst* __restr
     }
 }
 
-// 3D pass 1: D[b][p] = delta_b[x_p] at nodes with 6 ghost layers (extent n + 12)
+// 3D pass 0: x on the grid with 9 ghost layers (extent n + 18), every ghost node mapped once
+// (periodic shift, wall mirror), so the passes below read positions without branches
+__global__ void xe_fill_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
+                               const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr)
+{
+    pdl_entry();
+    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+        const int2 it = work[wi];
+        const Inst& I = insts[it.x];
+        ES_PTRS(S);
+        int i0, i1, i2;
+        if (!tile_node(I, it.y, 9, i0, i1, i2)) continue;
+        const long long X0 = I.n[0] + 18, X1 = I.n[1] + 18, nx = X0 * X1 * (I.n[2] + 18);
+        const long long e = ((long long)(i2 + 9) * X1 + (i1 + 9)) * X0 + (i0 + 9);
+        double v[3];
+        if (i0 >= 0 && i0 < I.n[0] && i1 >= 0 && i1 < I.n[1] && i2 >= 0 && i2 < I.n[2]) {
+            const long long c = lin(I, i0, i1, i2);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) v[q] = S.x[q * I.ncell + c];
+        } else {
+            x_at<false>(I, S.x, i0, i1, i2, v);
+        }
+        double* XE = scr[it.x].XE;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) XE[q * nx + e] = v[q];
+    }
+}
+
+// 3D pass 1: D[b][p] = delta_b[x_p] at nodes with 6 ghost layers (extent n + 12), from the
+// 9-layer position grid
 __global__ void dx3d_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
                             const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr)
 {
@@ -104,40 +133,27 @@ __global__ void dx3d_kernel(const Inst* __restrict__ insts, StagePtrs single, co
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
         int2 it = work[wi];
         const Inst& I = insts[it.x];
-        ES_PTRS(S);
         long long E0 = I.n[0] + 12, E1 = I.n[1] + 12, E2 = I.n[2] + 12, ne = E0 * E1 * E2;
         int i0, i1, i2;
         if (!tile_node(I, it.y, 6, i0, i1, i2)) continue;
         const long long p = ((long long)(i2 + 6) * E1 + (i1 + 6)) * E0 + (i0 + 6);
+        const long long X0 = I.n[0] + 18, X1 = I.n[1] + 18, nx = X0 * X1 * (I.n[2] + 18);
+        const long long xc = ((long long)(i2 + 9) * X1 + (i1 + 9)) * X0 + (i0 + 9);
+        const long long xst[3] = { 1, X0, X0 * X1 };
+        const double* XE = scr[it.x].XE;
         double* D = scr[it.x].D3;
         double acc[3][3];
 #pragma unroll
         for (int b = 0; b < 3; ++b)
 #pragma unroll
             for (int q = 0; q < 3; ++q) acc[b][q] = 0.0;
-        const bool inner = i0 >= 3 && i0 < I.n[0] - 3 && i1 >= 3 && i1 < I.n[1] - 3 && i2 >= 3 && i2 < I.n[2] - 3;
-        const long long ci = inner ? lin(I, i0, i1, i2) : 0;
-        const long long st[3] = { 1, I.n[0], (long long)I.n[0] * I.n[1] };
 #pragma unroll
         for (int m = 1; m <= 3; ++m) {
 #pragma unroll
             for (int b = 0; b < 3; ++b) {
-                double u[3], v[3];
-                if (inner) {
 #pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        u[q] = S.x[q * I.ncell + ci + m * st[b]];
-                        v[q] = S.x[q * I.ncell + ci - m * st[b]];
-                    }
-                } else {
-                    int ip[3] = { i0, i1, i2 }, im[3] = { i0, i1, i2 };
-                    ip[b] += m;
-                    im[b] -= m;
-                    x_at<false>(I, S.x, ip[0], ip[1], ip[2], u);
-                    x_at<false>(I, S.x, im[0], im[1], im[2], v);
-                }
-#pragma unroll
-                for (int q = 0; q < 3; ++q) acc[b][q] += alpha3(m) * (u[q] - v[q]);
+                for (int q = 0; q < 3; ++q)
+                    acc[b][q] += alpha3(m) * (XE[q * nx + xc + m * xst[b]] - XE[q * nx + xc - m * xst[b]]);
             }
         }
 #pragma unroll
@@ -172,9 +188,10 @@ __global__ void metrics3d_kernel(const Inst* __restrict__ insts, StagePtrs singl
         const long long E0 = I.n[0] + 12, E1 = I.n[1] + 12, ne = E0 * E1 * (I.n[2] + 12);
         const long long e_c = ((long long)(i2 + 6) * E1 + (i1 + 6)) * E0 + (i0 + 6);
         const long long est[3] = { 1, E0, E0 * E1 };
-        const bool inner = i0 >= 3 && i0 < I.n[0] - 3 && i1 >= 3 && i1 < I.n[1] - 3 && i2 >= 3 && i2 < I.n[2] - 3;
-        const long long ci = inner ? lin(I, i0, i1, i2) : 0;
-        const long long st[3] = { 1, I.n[0], (long long)I.n[0] * I.n[1] };
+        const long long X0 = I.n[0] + 18, X1 = I.n[1] + 18, nx = X0 * X1 * (I.n[2] + 18);
+        const long long xc = ((long long)(i2 + 9) * X1 + (i1 + 9)) * X0 + (i0 + 9);
+        const long long xst[3] = { 1, X0, X0 * X1 };
+        const double* XE = scr[it.x].XE;
         double t[3][3];
 #pragma unroll
         for (int k = 0; k < 3; ++k)
@@ -185,18 +202,10 @@ __global__ void metrics3d_kernel(const Inst* __restrict__ insts, StagePtrs singl
 #pragma unroll
             for (int mm = 1; mm <= 3; ++mm) {
                 double xp[3], xm[3];
-                if (inner) {
 #pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        xp[q] = S.x[q * I.ncell + ci + mm * st[a]];
-                        xm[q] = S.x[q * I.ncell + ci - mm * st[a]];
-                    }
-                } else {
-                    int ip[3] = { i0, i1, i2 }, im[3] = { i0, i1, i2 };
-                    ip[a] += mm;
-                    im[a] -= mm;
-                    x_at<false>(I, S.x, ip[0], ip[1], ip[2], xp);
-                    x_at<false>(I, S.x, im[0], im[1], im[2], xm);
+                for (int q = 0; q < 3; ++q) {
+                    xp[q] = XE[q * nx + xc + mm * xst[a]];
+                    xm[q] = XE[q * nx + xc - mm * xst[a]];
                 }
                 const long long ep = e_c + mm * est[a], em = e_c - mm * est[a];
 #pragma unroll
