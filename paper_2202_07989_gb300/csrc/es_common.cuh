@@ -108,7 +108,7 @@ struct StagePtrs {
 // context-owned scratch of one instance (fixed for the context's lifetime)
 struct Scratch {
     double* M;                // padded metrics
-    double* D3;               // 3D: delta_b[x_p] on the grid with 6 ghost layers
+    double* D3;               // 3D: products delta_b[x_p] x_q on the grid with 6 ghost layers
     double* XE;               // 3D: x on the grid with 9 ghost layers (boundary maps applied once)
     double* accU;
     double* accJ;

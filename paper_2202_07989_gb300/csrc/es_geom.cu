@@ -124,12 +124,14 @@ __global__ void xe_fill_kernel(const Inst* __restrict__ insts, StagePtrs single,
     }
 }
 
-// 3D pass 1: D[b][p] = delta_b[x_p] at nodes with 6 ghost layers (extent n + 12), from the
-// 9-layer position grid
+// 3D pass 1: at the nodes with 6 ghost layers (extent n + 12), from the 9-layer position
+// grid, the products P[b][j] = delta_b[x_p] x_q for (p, q) = (2,3), (3,1), (1,2) (j = 1, 2, 3):
+// every delta_b[x_p] enters Eq. (SCLCoeff) only multiplied by x_q at the same node
 __global__ void dx3d_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
                             const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr)
 {
     pdl_entry();
+    const int PQ[3][2] = { { 1, 2 }, { 2, 0 }, { 0, 1 } };
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
         int2 it = work[wi];
         const Inst& I = insts[it.x];
@@ -142,6 +144,7 @@ __global__ void dx3d_kernel(const Inst* __restrict__ insts, StagePtrs single, co
         const long long xst[3] = { 1, X0, X0 * X1 };
         const double* XE = scr[it.x].XE;
         double* D = scr[it.x].D3;
+        // delta_b[x_q] = (1/2) sum_m alpha_m (x_q(+m) - x_q(-m)): the 1/2 folded into the weights
         double acc[3][3];
 #pragma unroll
         for (int b = 0; b < 3; ++b)
@@ -153,17 +156,20 @@ __global__ void dx3d_kernel(const Inst* __restrict__ insts, StagePtrs single, co
             for (int b = 0; b < 3; ++b) {
 #pragma unroll
                 for (int q = 0; q < 3; ++q)
-                    acc[b][q] += alpha3(m) * (XE[q * nx + xc + m * xst[b]] - XE[q * nx + xc - m * xst[b]]);
+                    acc[b][q] += (0.5 * alpha3(m)) * (XE[q * nx + xc + m * xst[b]] - XE[q * nx + xc - m * xst[b]]);
             }
         }
+        double xq[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) xq[q] = XE[q * nx + xc];
 #pragma unroll
         for (int b = 0; b < 3; ++b)
 #pragma unroll
-            for (int q = 0; q < 3; ++q) D[(b * 3 + q) * ne + p] = 0.5 * acc[b][q];
+            for (int j = 0; j < 3; ++j) D[(b * 3 + j) * ne + p] = acc[b][PQ[j][0]] * xq[PQ[j][1]];
     }
 }
 
-// 3D pass 2: J xi_k/x_j = (delta_a[D_b[x_p] x_q] - delta_b[D_a[x_p] x_q]) / (dxi_a dxi_b)
+// 3D pass 2: J xi_k/x_j = (delta_a[P_b] - delta_b[P_a]) / (dxi_a dxi_b), P_b = delta_b[x_p] x_q
 // with (a, b) = (3,2), (1,3), (2,1) for k = 1, 2, 3 and (p, q) = (2,3), (3,1), (1,2)
 // for j = 1, 2, 3 (cyclic permutation of Eq. (SCLCoeff)).  Every ordered pair (a, b), a != b,
 // belongs to exactly one k, with sign +1 when (a, b) is k's pair and -1 when reversed; the
@@ -176,7 +182,6 @@ __global__ void metrics3d_kernel(const Inst* __restrict__ insts, StagePtrs singl
     const int KOF[3][3] = { { -1, 2, 1 }, { 2, -1, 0 }, { 1, 0, -1 } };
     const double SGN[3][3] = { { 0.0, -1.0, 1.0 }, { 1.0, 0.0, -1.0 }, { -1.0, 1.0, 0.0 } };
     const int AB[3][2] = { { 2, 1 }, { 0, 2 }, { 1, 0 } };
-    const int PQ[3][2] = { { 1, 2 }, { 2, 0 }, { 0, 1 } };
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
         int2 it = work[wi];
         const Inst& I = insts[it.x];
@@ -188,10 +193,6 @@ __global__ void metrics3d_kernel(const Inst* __restrict__ insts, StagePtrs singl
         const long long E0 = I.n[0] + 12, E1 = I.n[1] + 12, ne = E0 * E1 * (I.n[2] + 12);
         const long long e_c = ((long long)(i2 + 6) * E1 + (i1 + 6)) * E0 + (i0 + 6);
         const long long est[3] = { 1, E0, E0 * E1 };
-        const long long X0 = I.n[0] + 18, X1 = I.n[1] + 18, nx = X0 * X1 * (I.n[2] + 18);
-        const long long xc = ((long long)(i2 + 9) * X1 + (i1 + 9)) * X0 + (i0 + 9);
-        const long long xst[3] = { 1, X0, X0 * X1 };
-        const double* XE = scr[it.x].XE;
         double t[3][3];
 #pragma unroll
         for (int k = 0; k < 3; ++k)
@@ -201,12 +202,6 @@ __global__ void metrics3d_kernel(const Inst* __restrict__ insts, StagePtrs singl
         for (int a = 0; a < 3; ++a) {
 #pragma unroll
             for (int mm = 1; mm <= 3; ++mm) {
-                double xp[3], xm[3];
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    xp[q] = XE[q * nx + xc + mm * xst[a]];
-                    xm[q] = XE[q * nx + xc - mm * xst[a]];
-                }
                 const long long ep = e_c + mm * est[a], em = e_c - mm * est[a];
 #pragma unroll
                 for (int b = 0; b < 3; ++b) {
@@ -215,18 +210,19 @@ __global__ void metrics3d_kernel(const Inst* __restrict__ insts, StagePtrs singl
                     const double sg = SGN[a][b] * alpha3(mm);
 #pragma unroll
                     for (int j = 0; j < 3; ++j) {
-                        const int pp = PQ[j][0], q = PQ[j][1];
-                        const double* Dbp = D + (long long)(b * 3 + pp) * ne;
-                        t[k][j] += sg * (Dbp[ep] * xp[q] - Dbp[em] * xm[q]);
+                        const double* Pbj = D + (long long)(b * 3 + j) * ne;   // delta_b[x_p] x_q
+                        t[k][j] += sg * (Pbj[ep] - Pbj[em]);
                     }
                 }
             }
         }
         double m[3][3];
 #pragma unroll
-        for (int k = 0; k < 3; ++k)
+        for (int k = 0; k < 3; ++k) {
+            const double ck = 0.5 * I.inv_dxi[AB[k][0]] * I.inv_dxi[AB[k][1]];
 #pragma unroll
-            for (int j = 0; j < 3; ++j) m[k][j] = 0.5 * t[k][j] * I.inv_dxi[AB[k][0]] * I.inv_dxi[AB[k][1]];
+            for (int j = 0; j < 3; ++j) m[k][j] = t[k][j] * ck;
+        }
         double xd[3] = { 0, 0, 0 };
         if (S.xdot) x_at<true>(I, S.xdot, i0, i1, i2, xd);
         double* M = S.M;
