@@ -174,8 +174,10 @@ Inst make_inst(const es_config& g)
     I.f_pinf_tot = (float)I.pinf_tot;
     for (int q = 0; q < 3; ++q) I.f_chi[q] = (float)I.chi[q];
     I.f_eps = (float)I.weno_eps;
+    for (int q = 0; q < 4; ++q) I.f_alpha[q] = (float)I.alpha[q];
     for (int k = 0; k < 3; ++k) {
         I.f_h2[k] = (float)(I.inv_dxi[k] * I.inv_dxi[k]);
+        I.f_inv_dxi[k] = (float)I.inv_dxi[k];
         for (int m = 1; m <= 3; ++m) I.mc[k][m - 1] = 0.5 * alpha3(m) * I.inv_dxi[k];
     }
     return I;

@@ -45,6 +45,7 @@ struct Inst {
     // mixed form (converting the binary64 ones in the kernels would use the FP64 pipe)
     float f_gamma[2], f_cv[2], f_Rs[2], f_cvG[2], f_pinf_tot, f_chi[3], f_eps;
     float f_h2[3];            // 1 / dxi_k^2 (Jacobi weights of the mixed form)
+    float f_inv_dxi[3], f_alpha[4];
     double mc[3][3];          // (1/2) alpha_m / dxi_k: delta_k of a coordinate divided by dxi_k
 };
 

@@ -172,80 +172,122 @@ __device__ __forceinline__ R sigma_t(const Inst& I, int kind, const R* U)
     }
 }
 
-// one pass over the nodes: the CFL spectral-radius sum of Eq. (cfl) at x^n and the
-// monitor gradients |grad_xi sigma_s| (second-order central differences); per-instance
-// maxima by atomics on the non-negative bit patterns.  R = float in the mixed form (the
-// time step is a bound and the monitor is an FP32 quantity there); the metrics are read
-// from M.
+// the reciprocal of dxi_k, the weight alpha_q and the monitor gradient storage in the compute
+// type (the mixed form keeps binary32 copies, so its node kernels run no FP64 arithmetic)
 template <typename R>
-__global__ void cfl_grad_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
-                                const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr)
+__device__ __forceinline__ R inv_dxi_r(const Inst& I, int k)
+{
+    if constexpr (std::is_same<R, float>::value) return I.f_inv_dxi[k];
+    else return I.inv_dxi[k];
+}
+template <typename R>
+__device__ __forceinline__ R alpha_r(const Inst& I, int q)
+{
+    if constexpr (std::is_same<R, float>::value) return I.f_alpha[q];
+    else return I.alpha[q];
+}
+template <typename R>
+__device__ __forceinline__ R* grad_r(const Scratch& S) { return reinterpret_cast<R*>(S.g); }
+
+// one pass over the nodes: the CFL spectral-radius sum of Eq. (cfl) at x^n and the monitor
+// terms |grad_xi sigma_s| or |Laplacian_xi sigma_s| (second-order central differences);
+// per-instance maxima by atomics on the non-negative bit patterns.  R = float in the mixed
+// form (the time step is a bound and the monitor is an FP32 quantity there); the metrics
+// are read from M.  Each block evaluates sigma once per node of its 32 x 8 tile and of a
+// 1-node halo in the (i1, i2) plane into shared memory; the third direction reads globally.
+template <typename R>
+__global__ void __launch_bounds__(NODE_TPB) cfl_grad_kernel(const Inst* __restrict__ insts, StagePtrs single,
+                                                             const StagePtrs* __restrict__ table,
+                                                             const int2* __restrict__ work, int nwork,
+                                                             const Scratch* __restrict__ scr)
 {
     pdl_entry();
+    constexpr int TX = NT_X + 2, TY = NT_Y + 2;
+    __shared__ R ssig[4][TY][TX];
     __shared__ double sh[32];
+    const int lx = (int)threadIdx.x % NT_X, ly = (int)threadIdx.x / NT_X;
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
-        int2 it = work[wi];
+        const int2 it = work[wi];
         const Inst& I = insts[it.x];
         ES_PTRS(P);
-        int i[3];
-        const bool valid = tile_node(I, it.y, 0, i[0], i[1], i[2]);
-        const long long p = valid ? lin(I, i[0], i[1], i[2]) : 0;
+        const int n0 = I.n[0], n1 = I.n[1], ns = I.n_sigma;
+        const int ntx = (n0 + NT_X - 1) / NT_X, nty = (n1 + NT_Y - 1) / NT_Y;
+        const int tr = it.y / ntx;
+        const int b0 = (it.y % ntx) * NT_X - 1, b1 = (tr % nty) * NT_Y - 1, i2 = I.d == 3 ? tr / nty : 0;
+        __syncthreads();    // the previous tile's readers are done
+        for (int q = threadIdx.x; q < TX * TY; q += NODE_TPB) {
+            const int a = q % TX, b = q / TX;
+            const int g0 = b0 + a, g1 = b1 + b;
+            const bool corner = (a == 0 || a == TX - 1) && (b == 0 || b == TY - 1);
+            if (corner || g0 > n0 || g1 > n1 || ns == 0) continue;
+            R Ug[MAXC];
+            load_U_t<R>(I, P.JU, P.J, g0, g1, i2, Ug);
+            for (int s = 0; s < ns; ++s) ssig[s][b][a] = sigma_t<R>(I, I.sigma[s], Ug);
+        }
+        __syncthreads();
+        const int i[3] = { b0 + 1 + lx, b1 + 1 + ly, i2 };
+        const bool valid = i[0] < n0 && i[1] < n1;
         double s = 0.0, g[4] = { 0, 0, 0, 0 };
         if (valid) {
+            const long long p = lin(I, i[0], i[1], i[2]);
             R U[MAXC];
             load_U_t<R>(I, P.JU, P.J, i[0], i[1], i[2], U);
-            R rho = U[0] + (I.N == 2 ? U[1] : R(0));
+            const R rho = U[0] + (I.N == 2 ? U[1] : R(0));
             R v[3], v2 = R(0), cvr = R(0), a = R(0), gm = R(0);
             for (int m = 0; m < I.d; ++m) { v[m] = U[I.N + m] / rho; v2 += v[m] * v[m]; }
             for (int l = 0; l < I.N; ++l) {
-                a += to_r<R>((I.gamma[l] - 1.0) * I.cv[l]) * U[l];
-                gm += to_r<R>(I.gamma[l] * I.cv[l]) * U[l];
-                cvr += to_r<R>(I.cv[l]) * U[l];
+                a += Cst<R>::Rs(I, l) * U[l];          // (Gamma_l - 1) c_v,l rho_l
+                gm += Cst<R>::cvG(I, l) * U[l];        // Gamma_l c_v,l rho_l
+                cvr += Cst<R>::cv(I, l) * U[l];
             }
-            R T = (U[I.N + I.d] - R(0.5) * rho * v2 - to_r<R>(I.pinf_tot)) / cvr;
-            R c = sqrt((a / rho) * (gm / cvr) * T);
+            const R T = (U[I.N + I.d] - R(0.5) * rho * v2 - Cst<R>::pinf(I)) / cvr;
+            const R c = sqrt((a / rho) * (gm / cvr) * T);
             // spatial metrics of x^n, formed by the metrics pass that opens the mesh step
-            double m[3][3];
             const long long pid = plin(I, i[0], i[1], i[2]);
-            for (int k = 0; k < I.d; ++k)
-                for (int j = 0; j < I.d; ++j) m[k][j] = scr[it.x].M[(long long)(k * (I.d + 1) + 1 + j) * I.npad + pid];
             const R Jp = to_r<R>(P.J[p]);
             R sr = R(0);
             for (int k = 0; k < I.d; ++k) {
                 R L2 = R(0), vn = R(0);
-                for (int j = 0; j < I.d; ++j) { R mk = to_r<R>(m[k][j]); L2 += mk * mk; vn += mk * v[j]; }
-                sr += (fabs(vn) + c * sqrt(L2)) / Jp * to_r<R>(I.inv_dxi[k]);
+                for (int j = 0; j < I.d; ++j) {
+                    const R mk = to_r<R>(scr[it.x].M[(long long)(k * (I.d + 1) + 1 + j) * I.npad + pid]);
+                    L2 += mk * mk;
+                    vn += mk * v[j];
+                }
+                sr += (fabs(vn) + c * sqrt(L2)) / Jp * inv_dxi_r<R>(I, k);
             }
             s = to_d(sr);
             if (!(s >= 0.0)) s = 0.0;
             // per term |grad_xi sigma| (squared sums) or the Laplacian (second differences)
-            R gr[4] = { R(0), R(0), R(0), R(0) }, lp[4] = { R(0), R(0), R(0), R(0) }, sc[4];
-            for (int q = 0; q < I.n_sigma; ++q) sc[q] = sigma_t<R>(I, I.sigma[q], U);
+            R gr[4] = { R(0), R(0), R(0), R(0) }, lp[4] = { R(0), R(0), R(0), R(0) };
             for (int k = 0; k < I.d; ++k) {
-                int ip[3] = { i[0], i[1], i[2] }, im[3] = { i[0], i[1], i[2] };
-                ip[k] += 1;
-                im[k] -= 1;
                 R Up[MAXC], Um[MAXC];
-                load_U_t<R>(I, P.JU, P.J, ip[0], ip[1], ip[2], Up);
-                load_U_t<R>(I, P.JU, P.J, im[0], im[1], im[2], Um);
-                const R h2 = std::is_same<R, float>::value ? R(I.f_h2[k]) : R(I.inv_dxi[k] * I.inv_dxi[k]);
-                for (int q = 0; q < I.n_sigma; ++q) {
-                    const R sp = sigma_t<R>(I, I.sigma[q], Up), sm = sigma_t<R>(I, I.sigma[q], Um);
-                    R gk = (sp - sm) * to_r<R>(0.5 * I.inv_dxi[k]);
+                if (k == 2) {
+                    load_U_t<R>(I, P.JU, P.J, i[0], i[1], i[2] + 1, Up);
+                    load_U_t<R>(I, P.JU, P.J, i[0], i[1], i[2] - 1, Um);
+                }
+                const R hk = R(0.5) * inv_dxi_r<R>(I, k);
+                const R h2 = inv_dxi_r<R>(I, k) * inv_dxi_r<R>(I, k);
+                for (int q = 0; q < ns; ++q) {
+                    R sp, sm;
+                    if (k == 0) { sp = ssig[q][ly + 1][lx + 2]; sm = ssig[q][ly + 1][lx]; }
+                    else if (k == 1) { sp = ssig[q][ly + 2][lx + 1]; sm = ssig[q][ly][lx + 1]; }
+                    else { sp = sigma_t<R>(I, I.sigma[q], Up); sm = sigma_t<R>(I, I.sigma[q], Um); }
+                    const R gk = (sp - sm) * hk;
                     gr[q] += gk * gk;
-                    lp[q] += (sp - R(2) * sc[q] + sm) * h2;
+                    lp[q] += (sp - R(2) * ssig[q][ly + 1][lx + 1] + sm) * h2;
                 }
             }
-            for (int q = 0; q < I.n_sigma; ++q) {
-                g[q] = to_d(I.sigma_op[q] == MON_LAP ? R(fabs(lp[q])) : R(sqrt(gr[q])));
+            for (int q = 0; q < ns; ++q) {
+                const R gq = I.sigma_op[q] == MON_LAP ? R(fabs(lp[q])) : R(sqrt(gr[q]));
+                grad_r<R>(scr[it.x])[(long long)q * I.ncell + p] = gq;
+                g[q] = to_d(gq);
                 if (!(g[q] >= 0.0)) g[q] = 0.0;
-                scr[it.x].g[(long long)q * I.ncell + p] = g[q];
             }
         }
         double mx = block_max<double>(s, sh);
         if (threadIdx.x == 0) atomic_max_pos(&scr[it.x].red[0], mx);
         for (int q = 0; q < 4; ++q) {
-            if (q >= I.n_sigma) break;
+            if (q >= ns) break;
             double mq = block_max<double>(g[q], sh);
             if (threadIdx.x == 0) atomic_max_pos(&scr[it.x].red[1 + q], mq);
         }
@@ -254,19 +296,27 @@ __global__ void cfl_grad_kernel(const Inst* __restrict__ insts, StagePtrs single
 
 // Eq. (monitor) at node p from the gradients and the reciprocal instance maxima (0 for a zero maximum)
 template <typename R>
-__device__ __forceinline__ R theta_at(const Inst& I, const Scratch& S, const double* inv, long long p)
+__device__ __forceinline__ R theta_at(const Inst& I, const Scratch& S, const R* inv, long long p)
 {
     R t = R(1);
     for (int q = 0; q < I.n_sigma; ++q) {
-        if (inv[q] > 0.0) {
-            R r;
-            if constexpr (std::is_same<R, double>::value) r = S.g[(long long)q * I.ncell + p] * inv[q];
-            else r = to_r<R>(S.g[(long long)q * I.ncell + p]) * to_r<R>(inv[q]);
+        if (inv[q] > R(0)) {
+            const R r = grad_r<R>(S)[(long long)q * I.ncell + p] * inv[q];
             // Eq. (monitor) squares the ratio; the vortex monitor's terms are linear
-            t += I.sigma_op[q] == MON_GRAD2 ? to_r<R>(I.alpha[q]) * r * r : to_r<R>(I.alpha[q]) * r;
+            t += I.sigma_op[q] == MON_GRAD2 ? alpha_r<R>(I, q) * r * r : alpha_r<R>(I, q) * r;
         }
     }
     return sqrt(t);
+}
+
+// reciprocal of the instance maximum of monitor term q in the compute type (0 for a zero maximum)
+template <typename R>
+__device__ __forceinline__ R inv_max(const Scratch& S, int q)
+{
+    const double m = S.red[1 + q];
+    if (!(m > 0.0)) return R(0);
+    if constexpr (std::is_same<R, float>::value) return R(1) / f64_to_f32(m);
+    else return 1.0 / m;
 }
 
 template <typename R>
@@ -281,8 +331,8 @@ __global__ void monitor_theta_kernel(const Inst* __restrict__ insts, const int2*
         int i0, i1, i2;
         if (!tile_node(I, it.y, 0, i0, i1, i2)) continue;
         const long long p = lin(I, i0, i1, i2);
-        double inv[4] = { 0, 0, 0, 0 };
-        for (int q = 0; q < I.n_sigma; ++q) inv[q] = P.red[1 + q] > 0.0 ? 1.0 / P.red[1 + q] : 0.0;
+        R inv[4] = { R(0), R(0), R(0), R(0) };
+        for (int q = 0; q < I.n_sigma; ++q) inv[q] = inv_max<R>(P, q);
         reinterpret_cast<R*>(P.th0)[p] = theta_at<R>(I, P, inv, p);
     }
 }
@@ -303,9 +353,9 @@ __global__ void filter_kernel(const Inst* __restrict__ insts, const int2* __rest
         const long long p = lin(I, i0, i1, i2);
         const R* a = reinterpret_cast<const R*>(parity ? Sc.th1 : Sc.th0);
         R* dst = reinterpret_cast<R*>(parity ? Sc.th0 : Sc.th1);
-        double inv[4] = { 0, 0, 0, 0 };
+        R inv[4] = { R(0), R(0), R(0), R(0) };
         if (FROM_G)
-            for (int q = 0; q < I.n_sigma; ++q) inv[q] = Sc.red[1 + q] > 0.0 ? 1.0 / Sc.red[1 + q] : 0.0;
+            for (int q = 0; q < I.n_sigma; ++q) inv[q] = inv_max<R>(Sc, q);
         auto val = [&](long long q) -> R { return FROM_G ? theta_at<R>(I, Sc, inv, q) : a[q]; };
         R acc = R(0);
         int lo3 = I.d == 3 ? -1 : 0, hi3 = I.d == 3 ? 1 : 0;
