@@ -397,8 +397,12 @@ void launch_mesh(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStream
     if (nf == 0) launch_monitor_theta(c->mixed, gc, st, c->dI, c->w_cell, c->n_cell, c->dS);
     for (int f = 0; f < nf; ++f) launch_filter(c->mixed, f == 0, gc, st, c->dI, c->w_cell, c->n_cell, c->dS, f % 2);
     int th_sel = nf % 2;
-    for (int s = 0; s < mu; ++s)
-        launch_jacobi(c->mixed, c->d, s == mu - 1, gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS, s, th_sel);
+    if (c->mixed && c->d == 2 && mu >= 1 && mu <= JACOBI_FUSED_MAX) {
+        launch_jacobi_fused2d(gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS, mu, th_sel);
+    } else {
+        for (int s = 0; s < mu; ++s)
+            launch_jacobi(c->mixed, c->d, s == mu - 1, gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS, s, th_sel);
+    }
     if (mu == 0) pdl_launch(limiter_kernel, gc, NODE_TPB, 0, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
     if (step) launch_xdot_vcl(c->mixed, c->d, node_grid(c, c->n_pad), st, c->dI, P, tab, c->w_pad, c->n_pad, c->dS);
     else launch_xdot(c->mixed, gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
@@ -513,6 +517,7 @@ es_status es_create_batch(const es_config* cfgs, int n_inst, es_ctx** out)
     else if (c->d == 2 && c->N == 2) prepare_all<2, 2>(c->weno);
     else if (c->d == 3 && c->N == 1) prepare_all<3, 1>(c->weno);
     else prepare_all<3, 2>(c->weno);
+    prepare_mesh();
     for (int k = 0; k < c->d; ++k) c->flux_grid[k] = c->sms * flux_occ(c, c->flux_shape[k]);
     cudaError_t e = cudaDeviceSynchronize();
     if (!ok || e != cudaSuccess || !c->w_pad || !c->w_cell || (c->d == 3 && (!c->w_ext || !c->w_xe))) {

@@ -593,6 +593,175 @@ __global__ void __launch_bounds__(NODE_TPB) jacobi_y_kernel(const Inst* __restri
     }
 }
 
+// Mixed form, 2D: all mu <= 8 Jacobi sweeps of jacobi_y_kernel in one launch (temporal
+// blocking).  A block stages the region of its 32 x 8 node tile plus a halo of H = mu nodes
+// in shared memory: displacements (ping-pong), Theta and the spacings dl_{k+-} (formed in FP64
+// from x^n, rounded to binary32).  Each sweep updates every in-domain node of the region with
+// the arithmetic of jacobi_y_kernel (same operations in the same order), then re-mirrors the
+// wall ghost nodes from their source nodes; the valid zone shrinks by one node per sweep, so
+// after H sweeps the tile is exact.  Periodic directions need no care: the region runs over
+// unwrapped indices and reads the wrapped node's data.  The last sweep forms the limiter
+// bounds of Sec. 4 for the tile.  Dynamic shared memory: 13 RX RY floats.
+__global__ void __launch_bounds__(NODE_TPB) jacobi_fused2d_kernel(const Inst* __restrict__ insts, StagePtrs single,
+                                                                   const StagePtrs* __restrict__ table,
+                                                                   const int2* __restrict__ work, int nwork,
+                                                                   const Scratch* __restrict__ scr, int H, int theta_sel)
+{
+    pdl_entry();
+    extern __shared__ float jsm[];
+    __shared__ double sh[32];
+    const int RX = NT_X + 2 * H, RY = NT_Y + 2 * H, NR = RX * RY;
+    float* ya = jsm;              // [2][NR]
+    float* yb = ya + 2 * NR;      // [2][NR]
+    float* tq = yb + 2 * NR;      // [NR]
+    float* dq = tq + NR;          // [8][NR]: (k * 2 + s) * 2 + j
+    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+        const int2 it = work[wi];
+        const Inst& I = insts[it.x];
+        ES_PTRS(P);
+        const Scratch& Sc = scr[it.x];
+        const int n0 = I.n[0], n1 = I.n[1];
+        const bool per0 = I.bc[0][0] == BC_PERIODIC, per1 = I.bc[1][0] == BC_PERIODIC;
+        const int ntx = (n0 + NT_X - 1) / NT_X;
+        const int r0 = (it.y % ntx) * NT_X - H, r1 = (it.y / ntx) * NT_Y - H;    // region origin
+        const float* th = reinterpret_cast<const float*>(theta_sel ? Sc.th1 : Sc.th0);
+        const long long n = I.ncell;
+        __syncthreads();
+        // stage Theta, y = 0 and the + side spacings x^n_{i+e_k} - x^n_i of the in-domain nodes
+        // (a periodic copy takes its wrapped node's, unshifted); the - side of a node whose
+        // - neighbour is a wall ghost is formed here too, all others below
+        for (int q = threadIdx.x; q < NR; q += NODE_TPB) {
+            const int a = q % RX, b = q / RX;
+            const int g0 = r0 + a, g1 = r1 + b;
+            tq[q] = th[s_map(I, g0, g1, 0)];
+            ya[q] = ya[NR + q] = yb[q] = yb[NR + q] = 0.0f;
+            const bool ghost = (!per0 && (g0 < 0 || g0 >= n0)) || (!per1 && (g1 < 0 || g1 >= n1));
+            if (ghost) continue;
+            const int w0 = per0 ? g0 - floordiv_(g0, n0) * n0 : g0, w1 = per1 ? g1 - floordiv_(g1, n1) * n1 : g1;
+            const long long c = lin(I, w0, w1, 0);
+            const double xc[2] = { P.x[c], P.x[n + c] };
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+#pragma unroll
+                for (int sd = 0; sd < 2; ++sd) {
+                    const int nb0 = w0 + (k == 0 ? (sd ? 1 : -1) : 0), nb1 = w1 + (k == 1 ? (sd ? 1 : -1) : 0);
+                    const bool inside = nb0 >= 0 && nb0 < n0 && nb1 >= 0 && nb1 < n1;
+                    const bool wall = !(k == 0 ? per0 : per1) && !inside;
+                    if (sd == 0 && !wall) continue;          // from the neighbour's + side below
+                    double xn[3];
+                    if (inside) {
+                        const long long cn = lin(I, nb0, nb1, 0);
+                        xn[0] = P.x[cn];
+                        xn[1] = P.x[n + cn];
+                    } else {
+                        x_at<false>(I, P.x, nb0, nb1, 0, xn);
+                    }
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) dq[((k * 2 + sd) * 2 + j) * NR + q] = f64_to_f32(xn[j] - xc[j]);
+                }
+        }
+        __syncthreads();
+        // the remaining - sides: minus the + side of the - neighbour (the same pair of nodes)
+        for (int q = threadIdx.x; q < NR; q += NODE_TPB) {
+            const int a = q % RX, b = q / RX;
+            const int g0 = r0 + a, g1 = r1 + b;
+            const bool ghost = (!per0 && (g0 < 0 || g0 >= n0)) || (!per1 && (g1 < 0 || g1 >= n1));
+            if (ghost) continue;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const bool wall = k == 0 ? (!per0 && g0 == 0) : (!per1 && g1 == 0);
+                if (wall || (k == 0 ? a == 0 : b == 0)) continue;
+                const int qn = q - (k == 0 ? 1 : RX);
+#pragma unroll
+                for (int j = 0; j < 2; ++j) dq[((k * 2 + 0) * 2 + j) * NR + q] = -dq[((k * 2 + 1) * 2 + j) * NR + qn];
+            }
+        }
+        __syncthreads();
+        float* yc = ya;
+        float* yn = yb;
+        for (int sw = 0; sw < H; ++sw) {
+            // in-domain nodes: one sweep (neighbours outside the region leave a node invalid)
+            for (int q = threadIdx.x; q < NR; q += NODE_TPB) {
+                const int a = q % RX, b = q / RX;
+                const int g0 = r0 + a, g1 = r1 + b;
+                const bool ghost = (!per0 && (g0 < 0 || g0 >= n0)) || (!per1 && (g1 < 0 || g1 >= n1));
+                if (ghost || a == 0 || a == RX - 1 || b == 0 || b == RY - 1) continue;
+                const float tc = tq[q];
+                float num[2] = { 0.0f, 0.0f }, den = 0.0f;
+#pragma unroll
+                for (int k = 0; k < 2; ++k)
+#pragma unroll
+                    for (int sd = 0; sd < 2; ++sd) {
+                        const int qn = q + (k == 0 ? (sd ? 1 : -1) : (sd ? RX : -RX));
+                        const float w = 0.5f * (tc + tq[qn]) * I.f_h2[k];
+#pragma unroll
+                        for (int j = 0; j < 2; ++j) num[j] = fmaf(w, dq[((k * 2 + sd) * 2 + j) * NR + q] + yc[j * NR + qn], num[j]);
+                        den += w;
+                    }
+#pragma unroll
+                for (int j = 0; j < 2; ++j) yn[j * NR + q] = num[j] / den;
+            }
+            __syncthreads();
+            // wall ghosts: the mirror of their source node, the mirrored component negated
+            for (int q = threadIdx.x; q < NR; q += NODE_TPB) {
+                const int a = q % RX, b = q / RX;
+                const int g0 = r0 + a, g1 = r1 + b;
+                const bool o0 = !per0 && (g0 < 0 || g0 >= n0), o1 = !per1 && (g1 < 0 || g1 >= n1);
+                if (!o0 && !o1) continue;
+                const int m0 = o0 ? (g0 < 0 ? -1 - g0 : 2 * n0 - 1 - g0) : g0;
+                const int m1 = o1 ? (g1 < 0 ? -1 - g1 : 2 * n1 - 1 - g1) : g1;
+                const int sa = m0 - r0, sb = m1 - r1;
+                float v0 = 0.0f, v1 = 0.0f;
+                if (sa >= 0 && sa < RX && sb >= 0 && sb < RY) {    // else the ghost is outside the valid zone
+                    v0 = yn[sb * RX + sa];
+                    v1 = yn[NR + sb * RX + sa];
+                }
+                yn[q] = o0 ? -v0 : v0;
+                yn[NR + q] = o1 ? -v1 : v1;
+            }
+            __syncthreads();
+            float* t = yc;
+            yc = yn;
+            yn = t;
+        }
+        // the tile: store y^[mu] and form the limiter bounds
+        const int lx = (int)threadIdx.x % NT_X, ly = (int)threadIdx.x / NT_X;
+        const int i0 = r0 + H + lx, i1 = r1 + H + ly;
+        float bnd = 1.0f;
+        if (i0 < n0 && i1 < n1) {
+            const int q = (ly + H) * RX + lx + H;
+            const long long p = lin(I, i0, i1, 0);
+            float* yd = reinterpret_cast<float*>(I.mu % 2 == 1 ? Sc.xa : Sc.xb);
+            yd[p] = yc[q];
+            yd[n + p] = yc[NR + q];
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const float dx = yc[k * NR + q];
+                if (dx < 0.0f) bnd = fminf(bnd, dq[((k * 2 + 0) * 2 + k) * NR + q] / (2.0f * dx));
+                else if (dx > 0.0f) bnd = fminf(bnd, dq[((k * 2 + 1) * 2 + k) * NR + q] / (2.0f * dx));
+            }
+            if (!(bnd >= 0.0f)) bnd = 0.0f;
+        }
+        const double m = block_min_pos(f32_to_f64(bnd), sh);
+        if (threadIdx.x == 0) atomic_min_pos(&scr[it.x].red[5], m);
+    }
+}
+
+size_t jacobi_fused2d_smem(int H) { return sizeof(float) * 13 * (size_t)(NT_X + 2 * H) * (NT_Y + 2 * H); }
+
+void prepare_mesh()
+{
+    cudaFuncSetAttribute(jacobi_fused2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)jacobi_fused2d_smem(JACOBI_FUSED_MAX));
+}
+
+void launch_jacobi_fused2d(int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
+                           const StagePtrs* table, const int2* work, int nwork, const Scratch* scr, int H, int theta_sel)
+{
+    pdl_launch(jacobi_fused2d_kernel, grid, NODE_TPB, jacobi_fused2d_smem(H), st, insts, single, table, work, nwork, scr,
+               H, theta_sel);
+}
+
 // Delta_tau = min(1, bounds of Sec. 4) per instance
 __device__ inline const double* xmu_of(const StagePtrs& P, const Scratch& S, int mu)
 {
