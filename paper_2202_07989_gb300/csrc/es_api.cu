@@ -394,12 +394,13 @@ void launch_mesh(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStream
         return;
     }
     int nf = c->hI[0].nf, mu = c->hI[0].mu;
-    if (nf == 0) launch_monitor_theta(c->mixed, gc, st, c->dI, c->w_cell, c->n_cell, c->dS);
-    for (int f = 0; f < nf; ++f) launch_filter(c->mixed, f == 0, gc, st, c->dI, c->w_cell, c->n_cell, c->dS, f % 2);
     int th_sel = nf % 2;
-    if (c->mixed && c->d == 2 && mu >= 1 && mu <= JACOBI_FUSED_MAX) {
-        launch_jacobi_fused2d(gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS, mu, th_sel);
+    if (c->mixed && c->d == 2 && mu >= 1 && mu <= JACOBI_FUSED_MAX && nf <= FILTER_FUSED_MAX) {
+        // monitor, filter passes and sweeps in one launch
+        launch_jacobi_fused2d(gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS, mu, nf, th_sel);
     } else {
+        if (nf == 0) launch_monitor_theta(c->mixed, gc, st, c->dI, c->w_cell, c->n_cell, c->dS);
+        for (int f = 0; f < nf; ++f) launch_filter(c->mixed, f == 0, gc, st, c->dI, c->w_cell, c->n_cell, c->dS, f % 2);
         for (int s = 0; s < mu; ++s)
             launch_jacobi(c->mixed, c->d, s == mu - 1, gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS, s, th_sel);
     }

@@ -593,28 +593,35 @@ __global__ void __launch_bounds__(NODE_TPB) jacobi_y_kernel(const Inst* __restri
     }
 }
 
-// Mixed form, 2D: all mu <= 8 Jacobi sweeps of jacobi_y_kernel in one launch (temporal
-// blocking).  A block stages the region of its 32 x 8 node tile plus a halo of H = mu nodes
-// in shared memory: displacements (ping-pong), Theta and the spacings dl_{k+-} (formed in FP64
-// from x^n, rounded to binary32).  Each sweep updates every in-domain node of the region with
-// the arithmetic of jacobi_y_kernel (same operations in the same order), then re-mirrors the
-// wall ghost nodes from their source nodes; the valid zone shrinks by one node per sweep, so
-// after H sweeps the tile is exact.  Periodic directions need no care: the region runs over
+// Mixed form, 2D: the monitor, its F <= 4 filter passes and all H = mu <= 8 Jacobi sweeps
+// of jacobi_y_kernel in one launch (temporal blocking).  A block stages the region of its
+// 32 x 8 node tile plus a halo of H + F nodes in shared memory: Theta (formed from the
+// monitor gradients, then filtered F times; the halo shrinks by one node per pass), then on
+// the inner region (halo H) the displacements (ping-pong) and the spacings dl_{k+-} (formed in
+// FP64 from x^n, rounded to binary32).  Each Jacobi sweep updates every in-domain node of the
+// inner region with the arithmetic of jacobi_y_kernel, then re-mirrors the wall ghost nodes
+// from their source nodes; each filter pass likewise re-copies the boundary node into its
+// ghosts (the maps of s_map).  The valid zone shrinks by one node per pass or sweep, so after
+// all of them the tile is exact.  Periodic directions need no care: the region runs over
 // unwrapped indices and reads the wrapped node's data.  The last sweep forms the limiter
-// bounds of Sec. 4 for the tile.  Dynamic shared memory: 13 RX RY floats.
+// bounds of Sec. 4 for the tile.  F < 0: Theta is read from the buffer theta_sel instead.
 __global__ void __launch_bounds__(NODE_TPB) jacobi_fused2d_kernel(const Inst* __restrict__ insts, StagePtrs single,
                                                                    const StagePtrs* __restrict__ table,
                                                                    const int2* __restrict__ work, int nwork,
-                                                                   const Scratch* __restrict__ scr, int H, int theta_sel)
+                                                                   const Scratch* __restrict__ scr, int H, int F,
+                                                                   int theta_sel)
 {
     pdl_entry();
     extern __shared__ float jsm[];
     __shared__ double sh[32];
+    const int Fp = F > 0 ? F : 0;
     const int RX = NT_X + 2 * H, RY = NT_Y + 2 * H, NR = RX * RY;
+    const int RXo = RX + 2 * Fp, RYo = RY + 2 * Fp, NRo = RXo * RYo;
     float* ya = jsm;              // [2][NR]
     float* yb = ya + 2 * NR;      // [2][NR]
-    float* tq = yb + 2 * NR;      // [NR]
-    float* dq = tq + NR;          // [8][NR]: (k * 2 + s) * 2 + j
+    float* dq = yb + 2 * NR;      // [8][NR]: (k * 2 + s) * 2 + j
+    float* ta = dq + 8 * NR;      // [NRo] Theta ping-pong on the outer region
+    float* tb = ta + NRo;
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
         const int2 it = work[wi];
         const Inst& I = insts[it.x];
@@ -623,17 +630,60 @@ __global__ void __launch_bounds__(NODE_TPB) jacobi_fused2d_kernel(const Inst* __
         const int n0 = I.n[0], n1 = I.n[1];
         const bool per0 = I.bc[0][0] == BC_PERIODIC, per1 = I.bc[1][0] == BC_PERIODIC;
         const int ntx = (n0 + NT_X - 1) / NT_X;
-        const int r0 = (it.y % ntx) * NT_X - H, r1 = (it.y / ntx) * NT_Y - H;    // region origin
-        const float* th = reinterpret_cast<const float*>(theta_sel ? Sc.th1 : Sc.th0);
+        const int r0 = (it.y % ntx) * NT_X - H, r1 = (it.y / ntx) * NT_Y - H;    // inner region origin
+        const int o0 = r0 - Fp, o1 = r1 - Fp;                                     // outer region origin
         const long long n = I.ncell;
         __syncthreads();
+        // Theta on the outer region: Eq. (monitor) from the gradients at the mapped node (s_map)
+        float inv[4] = { 0.0f, 0.0f, 0.0f, 0.0f };
+        if (F >= 0)
+            for (int q = 0; q < I.n_sigma; ++q) inv[q] = inv_max<float>(Sc, q);
+        const float* th = reinterpret_cast<const float*>(theta_sel ? Sc.th1 : Sc.th0);
+        for (int q = threadIdx.x; q < NRo; q += NODE_TPB) {
+            const long long src = s_map(I, o0 + q % RXo, o1 + q / RXo, 0);
+            ta[q] = F >= 0 ? theta_at<float>(I, Sc, inv, src) : th[src];
+        }
+        __syncthreads();
+        // F filter passes (weights (1/2)^(|j|_1 + 2) over the 3 x 3 stencil)
+        float* tc_ = ta;
+        float* tn_ = tb;
+        for (int f = 0; f < F; ++f) {
+            for (int q = threadIdx.x; q < NRo; q += NODE_TPB) {
+                const int a = q % RXo, b = q / RXo;
+                const int g0 = o0 + a, g1 = o1 + b;
+                const bool ghost = (!per0 && (g0 < 0 || g0 >= n0)) || (!per1 && (g1 < 0 || g1 >= n1));
+                if (ghost || a == 0 || a == RXo - 1 || b == 0 || b == RYo - 1) continue;
+                float acc = 0.0f;
+#pragma unroll
+                for (int j2 = -1; j2 <= 1; ++j2) {
+                    const int qr = q + j2 * RXo;
+                    const float row = 0.25f * (tc_[qr - 1] + tc_[qr + 1]) + 0.5f * tc_[qr];
+                    acc += (j2 == 0 ? 0.5f : 0.25f) * row;
+                }
+                tn_[q] = acc;
+            }
+            __syncthreads();
+            // wall ghosts: copies of the boundary node
+            for (int q = threadIdx.x; q < NRo; q += NODE_TPB) {
+                const int a = q % RXo, b = q / RXo;
+                const int g0 = o0 + a, g1 = o1 + b;
+                const bool x0 = !per0 && (g0 < 0 || g0 >= n0), x1 = !per1 && (g1 < 0 || g1 >= n1);
+                if (!x0 && !x1) continue;
+                const int sa = (x0 ? (g0 < 0 ? 0 : n0 - 1) : g0) - o0, sb = (x1 ? (g1 < 0 ? 0 : n1 - 1) : g1) - o1;
+                tn_[q] = (sa >= 0 && sa < RXo && sb >= 0 && sb < RYo) ? tn_[sb * RXo + sa] : 1.0f;
+            }
+            __syncthreads();
+            float* t = tc_;
+            tc_ = tn_;
+            tn_ = t;
+        }
+        const float* tq = tc_ + Fp * RXo + Fp;     // Theta at inner node (a, b): tq[b * RXo + a]
         // stage Theta, y = 0 and the + side spacings x^n_{i+e_k} - x^n_i of the in-domain nodes
         // (a periodic copy takes its wrapped node's, unshifted); the - side of a node whose
         // - neighbour is a wall ghost is formed here too, all others below
         for (int q = threadIdx.x; q < NR; q += NODE_TPB) {
             const int a = q % RX, b = q / RX;
             const int g0 = r0 + a, g1 = r1 + b;
-            tq[q] = th[s_map(I, g0, g1, 0)];
             ya[q] = ya[NR + q] = yb[q] = yb[NR + q] = 0.0f;
             const bool ghost = (!per0 && (g0 < 0 || g0 >= n0)) || (!per1 && (g1 < 0 || g1 >= n1));
             if (ghost) continue;
@@ -686,14 +736,16 @@ __global__ void __launch_bounds__(NODE_TPB) jacobi_fused2d_kernel(const Inst* __
                 const int g0 = r0 + a, g1 = r1 + b;
                 const bool ghost = (!per0 && (g0 < 0 || g0 >= n0)) || (!per1 && (g1 < 0 || g1 >= n1));
                 if (ghost || a == 0 || a == RX - 1 || b == 0 || b == RY - 1) continue;
-                const float tc = tq[q];
+                const int qt = b * RXo + a;
+                const float tc = tq[qt];
                 float num[2] = { 0.0f, 0.0f }, den = 0.0f;
 #pragma unroll
                 for (int k = 0; k < 2; ++k)
 #pragma unroll
                     for (int sd = 0; sd < 2; ++sd) {
                         const int qn = q + (k == 0 ? (sd ? 1 : -1) : (sd ? RX : -RX));
-                        const float w = 0.5f * (tc + tq[qn]) * I.f_h2[k];
+                        const int qtn = qt + (k == 0 ? (sd ? 1 : -1) : (sd ? RXo : -RXo));
+                        const float w = 0.5f * (tc + tq[qtn]) * I.f_h2[k];
 #pragma unroll
                         for (int j = 0; j < 2; ++j) num[j] = fmaf(w, dq[((k * 2 + sd) * 2 + j) * NR + q] + yc[j * NR + qn], num[j]);
                         den += w;
@@ -747,19 +799,25 @@ __global__ void __launch_bounds__(NODE_TPB) jacobi_fused2d_kernel(const Inst* __
     }
 }
 
-size_t jacobi_fused2d_smem(int H) { return sizeof(float) * 13 * (size_t)(NT_X + 2 * H) * (NT_Y + 2 * H); }
+size_t jacobi_fused2d_smem(int H, int F)
+{
+    const size_t nr = (size_t)(NT_X + 2 * H) * (NT_Y + 2 * H);
+    const size_t Fp = F > 0 ? F : 0, nro = (NT_X + 2 * H + 2 * Fp) * (NT_Y + 2 * H + 2 * Fp);
+    return sizeof(float) * (12 * nr + 2 * nro);
+}
 
 void prepare_mesh()
 {
     cudaFuncSetAttribute(jacobi_fused2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)jacobi_fused2d_smem(JACOBI_FUSED_MAX));
+                         (int)jacobi_fused2d_smem(JACOBI_FUSED_MAX, FILTER_FUSED_MAX));
 }
 
 void launch_jacobi_fused2d(int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
-                           const StagePtrs* table, const int2* work, int nwork, const Scratch* scr, int H, int theta_sel)
+                           const StagePtrs* table, const int2* work, int nwork, const Scratch* scr, int H, int F,
+                           int theta_sel)
 {
-    pdl_launch(jacobi_fused2d_kernel, grid, NODE_TPB, jacobi_fused2d_smem(H), st, insts, single, table, work, nwork, scr,
-               H, theta_sel);
+    pdl_launch(jacobi_fused2d_kernel, grid, NODE_TPB, jacobi_fused2d_smem(H, F), st, insts, single, table, work, nwork,
+               scr, H, F, theta_sel);
 }
 
 // Delta_tau = min(1, bounds of Sec. 4) per instance

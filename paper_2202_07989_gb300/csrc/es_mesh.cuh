@@ -16,11 +16,13 @@ void launch_monitor_theta(bool mixed, int grid, cudaStream_t st, const Inst* ins
                           const Scratch* scr);
 void launch_filter(bool mixed, bool from_g, int grid, cudaStream_t st, const Inst* insts, const int2* work, int nwork,
                    const Scratch* scr, int parity);
-// mixed form, 2D: up to JACOBI_FUSED_MAX sweeps in one launch
-constexpr int JACOBI_FUSED_MAX = 8;
+// mixed form, 2D: the monitor, up to FILTER_FUSED_MAX filter passes and up to JACOBI_FUSED_MAX
+// sweeps in one launch (F < 0: Theta read from the buffer theta_sel)
+constexpr int JACOBI_FUSED_MAX = 8, FILTER_FUSED_MAX = 4;
 void prepare_mesh();    // kernel attributes, once per context
 void launch_jacobi_fused2d(int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
-                           const StagePtrs* table, const int2* work, int nwork, const Scratch* scr, int H, int theta_sel);
+                           const StagePtrs* table, const int2* work, int nwork, const Scratch* scr, int H, int F,
+                           int theta_sel);
 void launch_jacobi(bool mixed, int d, bool last, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
                    const StagePtrs* table, const int2* work, int nwork, const Scratch* scr, int sweep, int theta_sel);
 __global__ void limiter_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work, int nwork,
