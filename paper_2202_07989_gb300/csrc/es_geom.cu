@@ -178,9 +178,8 @@ __global__ void metrics3d_kernel(const Inst* __restrict__ insts, StagePtrs singl
                                  const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr)
 {
     pdl_entry();
-    // KOF[a][b]: metric row k of the ordered pair (a, b); SGN[a][b]: its sign
-    const int KOF[3][3] = { { -1, 2, 1 }, { 2, -1, 0 }, { 1, 0, -1 } };
-    const double SGN[3][3] = { { 0.0, -1.0, 1.0 }, { 1.0, 0.0, -1.0 }, { -1.0, 1.0, 0.0 } };
+    // the ordered pair (a, b) belongs to metric row k = 3 - a - b, with sign +1 when b follows a
+    // cyclically by two, -1 by one (compile-time constants once the loops unroll)
     const int AB[3][2] = { { 2, 1 }, { 0, 2 }, { 1, 0 } };
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
         int2 it = work[wi];
@@ -206,8 +205,8 @@ __global__ void metrics3d_kernel(const Inst* __restrict__ insts, StagePtrs singl
 #pragma unroll
                 for (int b = 0; b < 3; ++b) {
                     if (b == a) continue;
-                    const int k = KOF[a][b];
-                    const double sg = SGN[a][b] * alpha3(mm);
+                    const int k = 3 - a - b;
+                    const double sg = (b == (a + 2) % 3 ? 1.0 : -1.0) * alpha3(mm);
 #pragma unroll
                     for (int j = 0; j < 3; ++j) {
                         const double* Pbj = D + (long long)(b * 3 + j) * ne;   // delta_b[x_p] x_q

@@ -913,18 +913,27 @@ __global__ void xdot_vcl_kernel(const Inst* __restrict__ insts, StagePtrs single
                                 const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr)
 {
     pdl_entry();
+    __shared__ double sc3[3];
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
         const int2 it = work[wi];
         const Inst& I = insts[it.x];
         ES_PTRS(P);
-        const double* red = scr[it.x].red;
         const double* xmu = xmu_of(P, scr[it.x], I.mu);
-        const double dt = P.dt_fixed > 0.0 ? P.dt_fixed : I.cfl / red[0];
-        const double dtau = red[5];
-        if (it.y == 0 && threadIdx.x == 0) {
-            P.out[0] = dt;
-            P.out[1] = dtau;
+        // Delta t, Delta_tau and Delta_tau / Delta t: one thread per block divides
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const double* red = scr[it.x].red;
+            const double dt_ = P.dt_fixed > 0.0 ? P.dt_fixed : I.cfl / red[0];
+            sc3[0] = dt_;
+            sc3[1] = red[5];
+            sc3[2] = red[5] / dt_;
+            if (it.y == 0) {
+                P.out[0] = dt_;
+                P.out[1] = red[5];
+            }
         }
+        __syncthreads();
+        const double dt = sc3[0], dtau = sc3[1];
         int i[3];
         if (!tile_node(I, it.y, 3, i[0], i[1], i[2])) continue;
         bool interior = true;
@@ -935,7 +944,7 @@ __global__ void xdot_vcl_kernel(const Inst* __restrict__ insts, StagePtrs single
         double xd[3] = { 0.0, 0.0, 0.0 };
         if (MIXED) {
             if (I.mu > 0) {
-                const double sc = dtau / dt;
+                const double sc = sc3[2];
                 const float* y = reinterpret_cast<const float*>(xmu);
                 float yv[3];
                 if (interior) {
