@@ -196,23 +196,68 @@ struct Tile {
     static constexpr int NP = NPL * WT;
 };
 
-// conserved point state at a node reached along line direction k, in the compute type
-template <typename R>
-__device__ __forceinline__ void load_U_r(const Inst& I, const double* __restrict__ JU, const double* __restrict__ J,
-                                         int k, const int* idx_in, R* U)
+// byte offset of the staging buffer behind the compute-type arrays of a flux tile (16-byte aligned)
+template <int D, int NS, typename R, int S, int WT>
+__host__ __device__ constexpr size_t stage_offset()
 {
-    int idx[3] = { idx_in[0], idx_in[1], idx_in[2] };
-    int gi, side;
-    int t = map_line(I, k, idx[k], gi, side);
-    if (t == 2) {
-        for (int q = 0; q < I.nc; ++q) U[q] = to_r<R>(I.inflow[k][side][q]);
-        return;
+    using Y = Lay<D, NS>;
+    using TL = Tile<S, WT>;
+    return (sizeof(double) * (TL::NI + TL::NN) +
+            sizeof(R) * (Y::NF * TL::NN + Y::NC * TL::NP + (NS + 1) * TL::NI + Y::NC * TL::NI) + 15) / 16 * 16;
+}
+
+// asynchronous 8-byte global -> shared copies (cp.async), one group per tile
+__device__ __forceinline__ void cp_async8(double* smem, const double* gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Issue the raw FP64 node inputs of tile `wi` into the staging buffer stg[NC + D + 2][NN]:
+// JU and J of the node the boundary map of direction k reaches (nothing for an inflow
+// ghost, whose state is a constant) and the metric row of direction k at the node.
+template <int D, int NS, int S, int WT>
+__device__ __forceinline__ void flux_stage(const FluxLaunch& L, int k, int wi, double* stg)
+{
+    using TL = Tile<S, WT>;
+    constexpr int NC = NS + D + 1, NN = TL::NN;
+    const int adim = k == 0 ? 1 : 0, bdim = k == 2 ? 1 : 2;
+    const int2 it = L.work[wi];
+    const Inst& I = L.insts[it.x];
+    const double* JU = L.ptrs ? L.ptrs[it.x].JU : L.single.JU;
+    const double* J = L.ptrs ? L.ptrs[it.x].J : L.single.J;
+    const double* M = L.ptrs ? L.ptrs[it.x].M : L.single.M;
+    const int nk = I.n[k], na = I.n[adim];
+    const int ns = (nk + S - 1) / S, nat = (na + WT - 1) / WT;
+    const int s0 = (it.y % ns) * S, a0 = ((it.y / ns) % nat) * WT, tb = it.y / (ns * nat);
+    const long long ncell = I.ncell, np = I.npad;
+    for (int t = threadIdx.x; t < NN; t += blockDim.x) {
+        int s, w;
+        if (k == 0) { s = t % (S + 6); w = t / (S + 6); }
+        else { w = t % WT; s = t / WT; }
+        const int node = w * (S + 6) + s;
+        const int g = s0 - 3 + s, a = a0 + w;
+        if (a >= na || g > nk + 2) continue;
+        int idx[3] = { 0, 0, 0 };
+        idx[k] = g;
+        idx[adim] = a;
+        if (bdim < D) idx[bdim] = tb;
+        int gi, side;
+        if (map_line(I, k, g, gi, side) != 2) {
+            int src[3] = { idx[0], idx[1], idx[2] };
+            src[k] = gi;
+            const long long id = lin(I, src[0], src[1], src[2]);
+#pragma unroll
+            for (int q = 0; q < NC; ++q) cp_async8(stg + q * NN + node, JU + q * ncell + id);
+            cp_async8(stg + NC * NN + node, J + id);
+        }
+        const long long pid = plin(I, idx[0], idx[1], idx[2]);
+#pragma unroll
+        for (int c = 0; c <= D; ++c) cp_async8(stg + (NC + 1 + c) * NN + node, M + (long long)(k * (D + 1) + c) * np + pid);
     }
-    idx[k] = gi;
-    long long id = lin(I, idx[0], idx[1], I.d == 3 ? idx[2] : 0);
-    R inv = Ar<R>::rcp(to_r<R>(J[id]));
-    for (int q = 0; q < I.nc; ++q) U[q] = to_r<R>(JU[q * I.ncell + id]) * inv;
-    if (t == 1) U[I.N + k] = -U[I.N + k];
+    cp_async_commit();
 }
 
 // Phases of one tile: (1) node states, entropy variables and metrics into shared memory;
@@ -234,9 +279,16 @@ __global__ void __launch_bounds__(FLUX_TPB, (sizeof(R) == 4 ? (D == 2 ? 3 : 2) :
     R* pf = nr + NF * NN;                                        // [NC][NP] pair fluxes
     R* cm = pf + NC * NP;                                        // [NS + 1][NI] centre-pair means
     R* fl = cm + (NS + 1) * NI;                                  // [NC][NI] interface fluxes
+    double* stg = reinterpret_cast<double*>(smem_raw + stage_offset<D, NS, R, S, WT>());   // [NC + D + 2][NN]
     const int k = L.k;
     const int adim = k == 0 ? 1 : 0, bdim = k == 2 ? 1 : 2;
 
+    // When a CTA has several tiles, their node inputs go through the staging buffer: the
+    // first tile's now, each later tile's once the previous tile's phase 1 has consumed the
+    // buffer, so their loads overlap phases 2-4.  With one tile per CTA there is nothing to
+    // overlap, and phase 1 loads directly.
+    const bool staged = L.nwork > (int)gridDim.x;
+    if (staged && blockIdx.x < L.nwork) flux_stage<D, NS, S, WT>(L, k, blockIdx.x, stg);
     for (int wi = blockIdx.x; wi < L.nwork; wi += gridDim.x) {
         const int2 it = L.work[wi];
         const Inst& I = L.insts[it.x];
@@ -249,6 +301,10 @@ __global__ void __launch_bounds__(FLUX_TPB, (sizeof(R) == 4 ? (D == 2 ? 3 : 2) :
         const double inv_dx = I.inv_dxi[k];
 
         // ---------------- phase 1: node states, entropy variables, metrics ----------------
+        if (staged) {
+            cp_async_wait_all();
+            __syncthreads();
+        }
         for (int t = threadIdx.x; t < NN; t += blockDim.x) {
             int s, w;
             if (k == 0) { s = t % (S + 6); w = t / (S + 6); }
@@ -264,8 +320,25 @@ __global__ void __launch_bounds__(FLUX_TPB, (sizeof(R) == 4 ? (D == 2 ? 3 : 2) :
             idx[k] = g;
             idx[adim] = a;
             if (bdim < D) idx[bdim] = tb;
+            // the conserved point state from the staged JU, J; the boundary map of direction k
+            // negates the normal momentum (reflect) or gives the fixed state (inflow)
             R U[MAXC];
-            load_U_r<R>(I, P.JU, P.J, k, idx, U);
+            const long long pid = plin(I, idx[0], idx[1], idx[2]);
+            {
+                int gi, side;
+                const int tmap = map_line(I, k, g, gi, side);
+                if (tmap == 2) {
+                    for (int q = 0; q < NC; ++q) U[q] = to_r<R>(I.inflow[k][side][q]);
+                } else {
+                    int src[3] = { idx[0], idx[1], idx[2] };
+                    src[k] = gi;
+                    const long long id = staged ? 0 : lin(I, src[0], src[1], src[2]);
+                    const R inv = Ar<R>::rcp(to_r<R>(staged ? stg[NC * NN + node] : P.J[id]));
+#pragma unroll
+                    for (int q = 0; q < NC; ++q) U[q] = to_r<R>(staged ? stg[q * NN + node] : P.JU[q * ncell + id]) * inv;
+                    if (tmap == 1) U[NS + k] = -U[NS + k];
+                }
+            }
             R rho = U[0] + (NS == 2 ? U[1] : R(0));
             R irho = Ar<R>::rcp(rho);
             R v[D], v2 = R(0);
@@ -313,15 +386,17 @@ __global__ void __launch_bounds__(FLUX_TPB, (sizeof(R) == 4 ? (D == 2 ? 3 : 2) :
             // metrics of direction k at this node from the metrics kernel (padded buffer covering
             // g in [-3, n + 3))
             {
-                long long pid = plin(I, idx[0], idx[1], idx[2]);
-                double m0 = P.M[(long long)(k * (D + 1)) * I.npad + pid];
+                const long long mrow = (long long)(k * (D + 1)) * I.npad + pid;
+                const double m0 = staged ? stg[(NC + 1) * NN + node] : P.M[mrow];
                 mt64[node] = m0;
                 nr[Y::MR * NN + node] = to_r<R>(m0);
 #pragma unroll
-                for (int j = 0; j < D; ++j) nr[(Y::MR + 1 + j) * NN + node] = to_r<R>(P.M[(long long)(k * (D + 1) + 1 + j) * I.npad + pid]);
+                for (int j = 0; j < D; ++j)
+                    nr[(Y::MR + 1 + j) * NN + node] = to_r<R>(staged ? stg[(NC + 2 + j) * NN + node] : P.M[mrow + (1 + j) * I.npad]);
             }
         }
         __syncthreads();
+        if (staged && wi + (int)gridDim.x < L.nwork) flux_stage<D, NS, S, WT>(L, k, wi + (int)gridDim.x, stg);
 
         // ---------------- phase 2: distinct two-point EC fluxes ----------------
         for (int t = threadIdx.x; t < NP; t += blockDim.x) {
@@ -608,10 +683,7 @@ __global__ void __launch_bounds__(FLUX_TPB, (sizeof(R) == 4 ? (D == 2 ? 3 : 2) :
 template <int D, int NS, typename R, int S, int WT>
 static size_t smem_of()
 {
-    using Y = Lay<D, NS>;
-    using TL = Tile<S, WT>;
-    return sizeof(double) * (TL::NI + TL::NN) +
-           sizeof(R) * (Y::NF * TL::NN + Y::NC * TL::NP + (NS + 1) * TL::NI + Y::NC * TL::NI);
+    return stage_offset<D, NS, R, S, WT>() + sizeof(double) * (NS + 2 * D + 3) * Tile<S, WT>::NN;
 }
 
 // one case per tile shape of the table in es_kernels.cuh
