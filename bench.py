@@ -66,16 +66,16 @@ def flux_flops_per_interface(D, NS, es=True):
 
 
 def launches_per_step(pb, mixed=True):
-    """Kernel launches of one es_step: the mesh step (metrics of x^n, reduction reset,
+    """Kernel launches of one es_step: the mesh step (metrics of x^n with the reduction reset,
     CFL + gradients, nf filter passes or the monitor pass, mu sweeps or the limiter, the
     velocity + VCL pass), then d flux launches per stage and metrics for stages 2 and 3
     (2D: one metrics launch; 3D: the position grid, delta_b[x_p] and the metrics).  The
     mixed 2D form runs the monitor, filter passes and sweeps (mu 1..8, nf <= 4) as one launch."""
     m = 1 if pb.d == 2 else 3
     if mixed and pb.d == 2 and 1 <= pb.mu <= 8 and pb.nf <= 4:
-        mesh = m + 2 + 1 + 1
+        mesh = m + 1 + 1 + 1
     else:
-        mesh = m + 3 + pb.nf + pb.mu + (pb.nf == 0) + (pb.mu == 0)
+        mesh = m + 2 + pb.nf + pb.mu + (pb.nf == 0) + (pb.mu == 0)
     return mesh + 3 * pb.d + 2 * m
 
 

@@ -290,13 +290,16 @@ struct ProfScope {
 };
 
 // metrics of the stage mesh P.x / P.xdot into P.M
-void launch_metrics(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStream_t st)
+// metrics of a stage; reset = true also resets the reduction slots (the first kernel of a mesh step)
+void launch_metrics(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStream_t st, bool reset = false)
 {
     ProfScope ps(c, PC_METRICS, st);
     if (c->d == 2) {
-        pdl_launch(metrics2d_kernel, node_grid(c, c->n_pad), NODE_TPB, 0, st, c->dI, P, tab, c->w_pad, c->n_pad);
+        pdl_launch(metrics2d_kernel, node_grid(c, c->n_pad), NODE_TPB, 0, st, c->dI, P, tab, c->w_pad, c->n_pad,
+                   reset ? c->dS : nullptr, c->n_inst);
     } else {
-        pdl_launch(xe_fill_kernel, node_grid(c, c->n_xe), NODE_TPB, 0, st, c->dI, P, tab, c->w_xe, c->n_xe, c->dS);
+        pdl_launch(xe_fill_kernel, node_grid(c, c->n_xe), NODE_TPB, 0, st, c->dI, P, tab, c->w_xe, c->n_xe, c->dS,
+                   reset ? c->n_inst : 0);
         pdl_launch(dx3d_kernel, node_grid(c, c->n_ext), NODE_TPB, 0, st, c->dI, P, tab, c->w_ext, c->n_ext, c->dS);
         pdl_launch(metrics3d_kernel, node_grid(c, c->n_pad), NODE_TPB, 0, st, c->dI, P, tab, c->w_pad, c->n_pad, c->dS);
     }
@@ -383,9 +386,8 @@ void launch_mesh(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStream
     StagePtrs Q = P;
     Q.xdot = nullptr;
     Q.M = c->hS[0].M;
-    launch_metrics(c, Q, tab, st);
+    launch_metrics(c, Q, tab, st, true);     // also resets the reduction slots
     ProfScope ps(c, PC_MESH, st);
-    pdl_launch(red_init_kernel, (c->n_inst + 127) / 128, 128, 0, st, c->dS, c->n_inst);
     int gc = node_grid(c, c->n_cell);
     launch_cfl_grad(c->mixed, gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
     if (c->hI[0].fixed) {
@@ -662,8 +664,7 @@ es_status es_schlieren(es_ctx* c, const double* JU, const double* J, const doubl
     P.x = x;
     P.M = c->hS[0].M;
     P.out = phi;
-    launch_metrics(c, P, nullptr, st);     // metrics of x (no VCL part) into the scratch
-    pdl_launch(red_init_kernel, (c->n_inst + 127) / 128, 128, 0, st, c->dS, c->n_inst);
+    launch_metrics(c, P, nullptr, st, true);     // metrics of x (no VCL part); reduction slots reset
     const int gc = node_grid(c, c->n_cell);
     pdl_launch(schlieren_grad_kernel, gc, NODE_TPB, 0, st, c->dI, P, c->w_cell, c->n_cell, c->dS);
     pdl_launch(schlieren_phi_kernel, gc, NODE_TPB, 0, st, c->dI, P, c->w_cell, c->n_cell, c->dS, psi1, psi2);

@@ -123,6 +123,20 @@ struct Scratch {
     double* zeros;            // d zero fields (absent mesh velocity)
 };
 
+// the per-instance reduction slots at the start of a mesh step (CFL max, monitor maxima,
+// Delta_tau = 1, schlieren max), done by block 0 of the first kernel of the step
+__device__ __forceinline__ void reset_reductions(const Scratch* scr, int ninst)
+{
+    if (!scr || blockIdx.x != 0) return;
+    for (int i = threadIdx.x; i < ninst; i += blockDim.x) {
+        double* r = scr[i].red;
+        for (int q = 0; q < 5; ++q) r[q] = 0.0;
+        r[5] = 1.0;
+        r[6] = 0.0;
+        r[7] = 0.0;
+    }
+}
+
 #define ES_PTRS(P) const StagePtrs P = (table ? table[it.x] : single)
 
 // node-wise kernels run over tiles of NT_X x NT_Y nodes of one (i1, i0) plane

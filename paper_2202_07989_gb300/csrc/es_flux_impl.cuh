@@ -716,10 +716,13 @@ int flux_blocks_per_sm(int shape)
 template <int D, int NS, typename R, int WK>
 void launch_flux(const FluxLaunch& L, int shape, int grid, cudaStream_t st)
 {
+    // the staging buffer only when a CTA has several tiles (the kernel's own test)
+    const bool staged = L.nwork > grid;
 #define ES_LAUNCH(SH)                                                                                        \
     if (shape == SH)                                                                                         \
         pdl_launch(flux_kernel<D, NS, R, SHAPE_S[SH], SHAPE_WT[SH], WK>, grid, FLUX_TPB,                       \
-                   smem_of<D, NS, R, SHAPE_S[SH], SHAPE_WT[SH]>(), st, L);
+                   staged ? smem_of<D, NS, R, SHAPE_S[SH], SHAPE_WT[SH]>() : stage_offset<D, NS, R, SHAPE_S[SH], SHAPE_WT[SH]>(), \
+                   st, L);
     ES_FLUX_SHAPES(ES_LAUNCH)
 #undef ES_LAUNCH
 }

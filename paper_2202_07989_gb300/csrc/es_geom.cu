@@ -24,15 +24,18 @@ __device__ inline double delta_x(const Inst& I, const double* __restrict__ x, in
 }
 
 // 2D: J xi_1/x = (delta_2[x_2], -delta_2[x_1]) / dxi_2, J xi_2/x = (-delta_1[x_2], delta_1[x_1]) / dxi_1
-// over the padded node range (3 ghost layers).  Each block stages x on its tile and on a
+// over the padded node range (3 ghost layers); with `reset`, block 0 also resets the reduction
+// slots of the ninst instances (the first kernel of a mesh step).  Each block stages x on its tile and on a
 // halo of 3 nodes in shared memory (ghost nodes through the boundary maps, once per node),
 // then forms both derivatives from shared memory; the coefficients mc = alpha_m / (2 dxi_k)
 // fold the scaling into the stencil.
 __global__ void __launch_bounds__(NODE_TPB) metrics2d_kernel(const Inst* __restrict__ insts, StagePtrs single,
                                                               const StagePtrs* __restrict__ table,
-                                                              const int2* __restrict__ work, int nwork)
+                                                              const int2* __restrict__ work, int nwork,
+                                                              const Scratch* __restrict__ reset, int ninst)
 {
     pdl_entry();
+    reset_reductions(reset, ninst);
     constexpr int HX = NT_X + 6, HY = NT_Y + 6;
     __shared__ double sx[2][HY][HX];
     const int lx = (int)threadIdx.x % NT_X, ly = (int)threadIdx.x / NT_X;
@@ -99,9 +102,10 @@ __global__ void __launch_bounds__(NODE_TPB) metrics2d_kernel(const Inst* __restr
 // 3D pass 0: x on the grid with 9 ghost layers (extent n + 18), every ghost node mapped once
 // (periodic shift, wall mirror), so the passes below read positions without branches
 __global__ void xe_fill_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
-                               const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr)
+                               const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr, int reset_n)
 {
     pdl_entry();
+    reset_reductions(reset_n > 0 ? scr : nullptr, reset_n);
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
         const int2 it = work[wi];
         const Inst& I = insts[it.x];

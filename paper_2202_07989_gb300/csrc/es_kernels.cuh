@@ -48,9 +48,10 @@ struct FluxLaunch {
     int* status;
 };
 
-__global__ void metrics2d_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work, int nwork);
+__global__ void metrics2d_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work, int nwork,
+                                 const Scratch* reset, int ninst);
 __global__ void xe_fill_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work, int nwork,
-                               const Scratch* scr);
+                               const Scratch* scr, int reset_n);
 __global__ void dx3d_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work, int nwork,
                             const Scratch* scr);
 __global__ void metrics3d_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work, int nwork,

@@ -12,18 +12,6 @@ namespace es {
 // reduction slots per instance
 //   red[0] max_i sum_k rho_{i,k}/dxi_k,  red[1..4] max |grad sigma_s|,  red[5] Delta_tau
 
-__global__ void red_init_kernel(const Scratch* __restrict__ scr, int ninst)
-{
-    pdl_entry();
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ninst) return;
-    double* r = scr[i].red;
-    for (int q = 0; q < 5; ++q) r[q] = 0.0;
-    r[5] = 1.0;
-    r[6] = 0.0;
-    r[7] = 0.0;
-}
-
 template <typename T>
 __device__ inline T block_max(T v, T* sh)
 {

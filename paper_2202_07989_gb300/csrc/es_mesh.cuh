@@ -5,7 +5,6 @@
 
 namespace es {
 
-__global__ void red_init_kernel(const Scratch* scr, int ninst);
 void launch_cfl_grad(bool mixed, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
                      const StagePtrs* table, const int2* work, int nwork, const Scratch* scr);
 void launch_xdot(bool mixed, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
