@@ -175,6 +175,7 @@ Inst make_inst(const es_config& g)
     for (int q = 0; q < 3; ++q) I.f_chi[q] = (float)I.chi[q];
     I.f_eps = (float)I.weno_eps;
     for (int q = 0; q < 4; ++q) I.f_alpha[q] = (float)I.alpha[q];
+    I.f_ichi3 = (float)(1.0 / I.chi[2]);
     for (int k = 0; k < 3; ++k) {
         I.f_h2[k] = (float)(I.inv_dxi[k] * I.inv_dxi[k]);
         I.f_inv_dxi[k] = (float)I.inv_dxi[k];

@@ -46,6 +46,7 @@ struct Inst {
     float f_gamma[2], f_cv[2], f_Rs[2], f_cvG[2], f_pinf_tot, f_chi[3], f_eps;
     float f_h2[3];            // 1 / dxi_k^2 (Jacobi weights of the mixed form)
     float f_inv_dxi[3], f_alpha[4];
+    float f_ichi3;            // 1 / chi_3 of WENO-MR
     double mc[3][3];          // (1/2) alpha_m / dxi_k: delta_k of a coordinate divided by dxi_k
 };
 

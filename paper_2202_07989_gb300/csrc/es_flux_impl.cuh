@@ -142,6 +142,48 @@ __device__ __forceinline__ R weno_mr(R w0, R w1, R w2, R w3, R w4, R c1, R c2, R
     }
 }
 
+// binary32 pairs: two independent evaluations in the two lanes of Blackwell's paired FP32
+// instructions (FADD2 / FMUL2 / FFMA2, IEEE round-to-nearest in each lane)
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f), a); }   // a - b, one rounding
+
+// weno_mr<float> for W^- (lane x, from W_{j-2..j+2}) and W^+ (lane y, the mirrored stencil)
+// at once: the same closed forms, evaluated lane by lane; divisions and min/abs per lane
+__device__ __forceinline__ float2 weno_mr_pair(float2 w0, float2 w1, float2 w2, float2 w3, float2 w4, float c1, float c2,
+                                               float c3, float ic3, float eps)
+{
+    const float2 s13 = add2(w1, w3), d31 = sub2(w3, w1), s04 = add2(w0, w4), d04 = sub2(w0, w4);
+    const float2 a2 = mul2(f2(0.5f), d31);
+    const float2 a3 = sub2(mul2(f2(0.5f), s13), w2);
+    const float2 b2 = mul2(fma2(f2(11.0f), d04, mul2(f2(82.0f), d31)), f2(1.0f / 120.0f));
+    const float2 b3 = mul2(fma2(f2(-3.0f), s04, fma2(f2(40.0f), s13, mul2(f2(-74.0f), w2))), f2(1.0f / 56.0f));
+    const float2 b4 = mul2(fma2(f2(2.0f), d31, d04), f2(-1.0f / 12.0f));
+    const float2 b5 = mul2(fma2(f2(-4.0f), s13, fma2(f2(6.0f), w2, s04)), f2(1.0f / 24.0f));
+    const float2 d21 = sub2(w2, w1), d32 = sub2(w3, w2);
+    const float2 q0 = mul2(d21, d21), q1 = mul2(d32, d32);
+    const float2 be1 = make_float2(fminf(q0.x, q1.x), fminf(q0.y, q1.y));
+    const float2 be2 = fma2(f2(13.0f / 3.0f), mul2(a3, a3), mul2(a2, a2));
+    const float2 t1 = fma2(f2(0.1f), b4, b2), t2 = fma2(f2(123.0f / 455.0f), b5, b3);
+    const float2 be3 = fma2(t1, t1, fma2(f2(13.0f / 3.0f), mul2(t2, t2),
+                                         fma2(f2(781.0f / 20.0f), mul2(b4, b4), mul2(f2(1421461.0f / 2275.0f), mul2(b5, b5)))));
+    const float2 u1 = sub2(be3, be1), u2 = sub2(be3, be2);
+    const float tx = 0.5f * (fabsf(u1.x) + fabsf(u2.x)), ty = 0.5f * (fabsf(u1.y) + fabsf(u2.y));
+    const float2 tau = make_float2(tx * tx, ty * ty);
+    const float2 h2 = fma2(f2(1.0f / 6.0f), a3, fma2(f2(0.5f), a2, w2));
+    const float2 h3 = fma2(f2(1.0f / 70.0f), b5, fma2(f2(0.05f), b4, fma2(f2(1.0f / 6.0f), b3, fma2(f2(0.5f), b2, w2))));
+    const float2 h3c = mul2(fma2(f2(-c2), h2, fma2(f2(-c1), w2, h3)), f2(ic3));
+    const float2 e1 = add2(f2(eps), be1), e2 = add2(f2(eps), be2), e3 = add2(f2(eps), be3);
+    const float2 o1 = fma2(f2(c1), make_float2(__fdividef(tau.x, e1.x), __fdividef(tau.y, e1.y)), f2(c1));
+    const float2 o2 = fma2(f2(c2), make_float2(__fdividef(tau.x, e2.x), __fdividef(tau.y, e2.y)), f2(c2));
+    const float2 o3 = fma2(f2(c3), make_float2(__fdividef(tau.x, e3.x), __fdividef(tau.y, e3.y)), f2(c3));
+    const float2 num = fma2(o3, h3c, fma2(o2, h2, mul2(o1, w2)));
+    const float2 den = add2(o1, add2(o2, o3));
+    return make_float2(__fdividef(num.x, den.x), __fdividef(num.y, den.y));
+}
+
 // classical fifth-order WENO (Jiang and Shu; the MM-WENOJS comparison of Sec. 5) at
 // x_{j+1/2} from W_{j-2..j+2}: candidate values of the three quadratic reconstructions,
 // their smoothness indicators, linear weights 1/10, 6/10, 3/10 and weights d_k/(eps+beta_k)^2
@@ -596,18 +638,37 @@ __global__ void __launch_bounds__(FLUX_TPB, (sizeof(R) == 4 ? (D == 2 ? 3 : 2) :
                     }
 #pragma unroll
                     for (int j = 0; j < D; ++j) rc[NS + j] = ru[j];
-                    // scaled entropy variables W_j = r_col . V_j at the six nodes
-                    R wv[6];
+                    // scaled entropy variables W_j = r_col . V_j at the six nodes, then W^- and W^+
+                    R Wm, Wp, jp;
+                    if constexpr (std::is_same<R, float>::value && WK == 0) {
+                        // binary32 WENO-MR: the node pairs (0,5), (1,4), (2,3) of the two stencils in paired lanes
+                        float2 p05 = f2(0.0f), p14 = f2(0.0f), p23 = f2(0.0f);
 #pragma unroll
-                    for (int j = 0; j < 6; ++j) {
-                        R s_ = R(0);
+                        for (int q = 0; q < NC; ++q) {
+                            const float2 rq = f2(rc[q]);
+                            p05 = fma2(rq, make_float2(NR(Y::VV + q, 0), NR(Y::VV + q, 5)), p05);
+                            p14 = fma2(rq, make_float2(NR(Y::VV + q, 1), NR(Y::VV + q, 4)), p14);
+                            p23 = fma2(rq, make_float2(NR(Y::VV + q, 2), NR(Y::VV + q, 3)), p23);
+                        }
+                        const float2 r = weno_mr_pair(p05, p14, p23, make_float2(p23.y, p23.x), make_float2(p14.y, p14.x),
+                                                      ch1, ch2, ch3, I.f_ichi3, eps);
+                        Wm = r.x;
+                        Wp = r.y;
+                        jp = p23.y - p23.x;
+                    } else {
+                        R wv[6];
 #pragma unroll
-                        for (int q = 0; q < NC; ++q) s_ += rc[q] * NR(Y::VV + q, j);
-                        wv[j] = s_;
+                        for (int j = 0; j < 6; ++j) {
+                            R s_ = R(0);
+#pragma unroll
+                            for (int q = 0; q < NC; ++q) s_ += rc[q] * NR(Y::VV + q, j);
+                            wv[j] = s_;
+                        }
+                        Wm = weno_val<R, WK>(wv[0], wv[1], wv[2], wv[3], wv[4], ch1, ch2, ch3, eps);
+                        Wp = weno_val<R, WK>(wv[5], wv[4], wv[3], wv[2], wv[1], ch1, ch2, ch3, eps);
+                        jp = wv[3] - wv[2];
                     }
-                    R Wm = weno_val<R, WK>(wv[0], wv[1], wv[2], wv[3], wv[4], ch1, ch2, ch3, eps);
-                    R Wp = weno_val<R, WK>(wv[5], wv[4], wv[3], wv[2], wv[1], ch1, ch2, ch3, eps);
-                    R jw = Wp - Wm, jp = wv[3] - wv[2];
+                    R jw = Wp - Wm;
                     R rn = R(0);
 #pragma unroll
                     for (int q = 0; q < NC; ++q) rn += rc[q] * rc[q];
