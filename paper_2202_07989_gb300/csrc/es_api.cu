@@ -402,8 +402,10 @@ void launch_mesh(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStream
         // monitor, filter passes and sweeps in one launch
         launch_jacobi_fused2d(gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS, mu, nf, th_sel);
     } else {
-        if (nf == 0) launch_monitor_theta(c->mixed, gc, st, c->dI, c->w_cell, c->n_cell, c->dS);
-        for (int f = 0; f < nf; ++f) launch_filter(c->mixed, f == 0, gc, st, c->dI, c->w_cell, c->n_cell, c->dS, f % 2);
+        // Theta once per node, then plain filter passes (forming it inside the first pass costs
+        // 3^d evaluations per node)
+        launch_monitor_theta(c->mixed, gc, st, c->dI, c->w_cell, c->n_cell, c->dS);
+        for (int f = 0; f < nf; ++f) launch_filter(c->mixed, false, gc, st, c->dI, c->w_cell, c->n_cell, c->dS, f % 2);
         for (int s = 0; s < mu; ++s)
             launch_jacobi(c->mixed, c->d, s == mu - 1, gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS, s, th_sel);
     }

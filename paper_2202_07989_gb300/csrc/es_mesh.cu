@@ -517,6 +517,33 @@ __global__ void __launch_bounds__(NODE_TPB) jacobi_y_kernel(const Inst* __restri
             float num[D], den = 0.0f, dk[D][2];
 #pragma unroll
             for (int j = 0; j < D; ++j) num[j] = 0.0f;
+            if (inner && !FIRST) {
+                // interior, after the first sweep: every load up front, no boundary maps
+                const long long st[3] = { 1, I.n[0], (long long)I.n[0] * I.n[1] };
+                float tn[D][2], dv[D][2][D], yv[D][2][D];
+#pragma unroll
+                for (int k = 0; k < D; ++k)
+#pragma unroll
+                    for (int s = 0; s < 2; ++s) {
+                        const long long q = p + (s ? st[k] : -st[k]);
+                        tn[k][s] = th[q];
+#pragma unroll
+                        for (int j = 0; j < D; ++j) {
+                            dv[k][s][j] = dl[((k * 2 + s) * D + j) * n + p];
+                            yv[k][s][j] = ys[j * n + q];
+                        }
+                    }
+#pragma unroll
+                for (int k = 0; k < D; ++k)
+#pragma unroll
+                    for (int s = 0; s < 2; ++s) {
+                        const float w = 0.5f * (tc + tn[k][s]) * I.f_h2[k];
+                        dk[k][s] = dv[k][s][k];
+#pragma unroll
+                        for (int j = 0; j < D; ++j) num[j] = fmaf(w, dv[k][s][j] + yv[k][s][j], num[j]);
+                        den += w;
+                    }
+            } else {
             long long stride = 1;
 #pragma unroll
             for (int k = 0; k < D; ++k) {
@@ -557,6 +584,7 @@ __global__ void __launch_bounds__(NODE_TPB) jacobi_y_kernel(const Inst* __restri
                     den += w;
                 }
                 stride *= I.n[k];
+            }
             }
             float ynew[D];
 #pragma unroll
