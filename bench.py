@@ -66,17 +66,20 @@ def flux_flops_per_interface(D, NS, es=True):
 
 
 def launches_per_step(pb, mixed=True):
-    """Kernel launches of one es_step: the mesh step (metrics of x^n with the reduction reset,
-    CFL + gradients, nf filter passes or the monitor pass, mu sweeps or the limiter, the
-    velocity + VCL pass), then d flux launches per stage and metrics for stages 2 and 3
-    (2D: one metrics launch; 3D: the position grid, delta_b[x_p] and the metrics).  The
-    mixed 2D form runs the monitor, filter passes and sweeps (mu 1..8, nf <= 4) as one launch."""
+    """Kernel launches of one es_step.  The mesh step: the metrics of x^n (with the reduction
+    reset; 2D one launch, 3D three), CFL + gradients, then the monitor, nf filter passes and mu
+    sweeps (the mixed 2D form runs them as one launch for mu 1..8, nf <= 4; otherwise one
+    launch each plus the limiter when mu = 0), and the velocity pass; a fixed mesh stops after
+    CFL with the velocity pass.  Then d flux launches per stage; 3D stages 2 and 3 form their
+    metrics, 2D stages use M + s dt M(xdot) from the velocity pass."""
     m = 1 if pb.d == 2 else 3
+    if pb.fixed_mesh:
+        return m + 2 + 3 * pb.d
     if mixed and pb.d == 2 and 1 <= pb.mu <= 8 and pb.nf <= 4:
         mesh = m + 1 + 1 + 1
     else:
-        mesh = m + 2 + pb.nf + pb.mu + (pb.nf == 0) + (pb.mu == 0)
-    return mesh + 3 * pb.d + 2 * m
+        mesh = m + 1 + 1 + pb.nf + pb.mu + (pb.mu == 0) + 1
+    return mesh + 3 * pb.d + (0 if pb.d == 2 else 2 * m)
 
 
 class ClockSampler:

@@ -290,14 +290,16 @@ struct ProfScope {
     ~ProfScope() { prof_end(c, i, st); }
 };
 
-// metrics of the stage mesh P.x / P.xdot into P.M
-// metrics of a stage; reset = true also resets the reduction slots (the first kernel of a mesh step)
-void launch_metrics(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStream_t st, bool reset = false)
+// metrics of the stage mesh P.x / P.xdot into P.M; reset = true also resets the reduction
+// slots (the first kernel of a mesh step); dot = true (2D) also forms the metrics of the mesh
+// velocity into P.Md, so the later stages of an RK step need no metrics pass
+void launch_metrics(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStream_t st, bool reset = false,
+                    bool dot = false)
 {
     ProfScope ps(c, PC_METRICS, st);
     if (c->d == 2) {
-        pdl_launch(metrics2d_kernel, node_grid(c, c->n_pad), NODE_TPB, 0, st, c->dI, P, tab, c->w_pad, c->n_pad,
-                   reset ? c->dS : nullptr, c->n_inst);
+        launch_metrics2d(dot, node_grid(c, c->n_pad), st, c->dI, P, tab, c->w_pad, c->n_pad, reset ? c->dS : nullptr,
+                         c->n_inst);
     } else {
         pdl_launch(xe_fill_kernel, node_grid(c, c->n_xe), NODE_TPB, 0, st, c->dI, P, tab, c->w_xe, c->n_xe, c->dS,
                    reset ? c->n_inst : 0);
@@ -308,11 +310,12 @@ void launch_metrics(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStr
 
 // residual of one stage: metrics, then one flux launch per direction.  With
 // rk = true the last direction applies the Shu-Osher stage (a, b); metrics = false
-// when M already holds the metrics of the stage (the first stage of a full step).
+// when M already holds the metrics of the stage; mcoef != 0 (2D) makes the stage metrics
+// M + mcoef dt Md, the metrics of x^n + mcoef dt xdot; dot = true (2D) forms Md with M.
 void launch_residual(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, bool rk, double a, double b, cudaStream_t st,
-                     bool metrics = true)
+                     bool metrics = true, double mcoef = 0.0, bool dot = false)
 {
-    if (metrics) launch_metrics(c, P, tab, st);
+    if (metrics) launch_metrics(c, P, tab, st, false, dot);
     for (int k = 0; k < c->d; ++k) {
         FluxLaunch L;
         L.insts = c->dI;
@@ -326,6 +329,7 @@ void launch_residual(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, bool r
         if (rk && k == c->d - 1) L.mode = MODE_RK;
         L.a = a;
         L.b = b;
+        L.mcoef = mcoef;
         L.status = c->status;
         ProfScope ps(c, PC_FLUX + k, st);
         flux_launch(c, L, sh, c->flux_grid[k], st);
@@ -362,6 +366,7 @@ void stage_ptrs(es_ctx* c, int i, double* JU, double* J, double* x, const double
         P.x = in_x[s];
         P.xdot = (xdot && !fixed) ? xdot : S.zeros;
         P.M = S.M;
+        P.Md = S.Md;
         P.accU = S.accU;
         P.accJ = S.accJ;
         P.JU0 = JU;
@@ -377,6 +382,11 @@ void stage_ptrs(es_ctx* c, int i, double* JU, double* J, double* x, const double
 
 const double RK_A[3] = { 0.0, 0.75, 1.0 / 3.0 };
 const double RK_B[3] = { 1.0, 0.25, 2.0 / 3.0 };
+// the stage meshes of SSP-RK3 with xdot constant: x^n, x^n + dt xdot, x^n + dt xdot / 2
+const double MCOEF[3] = { 0.0, 1.0, 0.5 };
+
+// 2D moving meshes form the stage metrics as M(x^n) + s dt M(xdot) (the metrics are linear in x)
+bool linear_stage_metrics(const es_ctx* c) { return c->d == 2 && !c->hI[0].fixed; }
 
 // mesh redistribution (Sec. 4): the metrics of x^n (Eq. (cfl) and the monitor need them),
 // Delta t and the monitor gradients, the filter passes, the Jacobi sweeps with the limiter,
@@ -410,7 +420,8 @@ void launch_mesh(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStream
             launch_jacobi(c->mixed, c->d, s == mu - 1, gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS, s, th_sel);
     }
     if (mu == 0) pdl_launch(limiter_kernel, gc, NODE_TPB, 0, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
-    if (step) launch_xdot_vcl(c->mixed, c->d, node_grid(c, c->n_pad), st, c->dI, P, tab, c->w_pad, c->n_pad, c->dS);
+    if (step && c->d == 2) launch_xdot_vel2d(c->mixed, node_grid(c, c->n_pad), st, c->dI, P, tab, c->w_pad, c->n_pad, c->dS);
+    else if (step) launch_xdot_vcl(c->mixed, c->d, node_grid(c, c->n_pad), st, c->dI, P, tab, c->w_pad, c->n_pad, c->dS);
     else launch_xdot(c->mixed, gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
 }
 
@@ -420,10 +431,12 @@ void launch_step(es_ctx* c, const StagePtrs& mesh, const StagePtrs* tab_mesh, co
                  StagePtrs* const tab_stage[3], cudaStream_t st)
 {
     launch_mesh(c, mesh, tab_mesh, st, true);
-    // the first stage reuses the metrics of x^n; on a fixed mesh every stage does
-    const bool fixed = c->hI[0].fixed != 0;
+    // the first stage reuses the metrics of x^n; on a fixed mesh every stage does; in 2D the
+    // velocity pass also formed M(xdot), so no stage forms metrics
+    const bool fixed = c->hI[0].fixed != 0, lin = linear_stage_metrics(c);
     for (int s = 0; s < 3; ++s)
-        launch_residual(c, stage[s], tab_stage[s], true, RK_A[s], RK_B[s], st, s > 0 && !fixed);
+        launch_residual(c, stage[s], tab_stage[s], true, RK_A[s], RK_B[s], st, s > 0 && !fixed && !lin,
+                        lin ? MCOEF[s] : 0.0);
 }
 
 __global__ void time_acc_kernel(double* t, const double* dt_dtau) { *t += dt_dtau[0]; }
@@ -470,6 +483,7 @@ es_status es_create_batch(const es_config* cfgs, int n_inst, es_ctx** out)
         memset(&S, 0, sizeof(S));
         long long n = I.ncell;
         ok = ok && dalloc(c, (void**)&S.M, sizeof(double) * I.d * (I.d + 1) * I.npad);
+        if (I.d == 2) ok = ok && dalloc(c, (void**)&S.Md, sizeof(double) * 6 * I.npad);
         if (I.d == 3) {
             long long ne = (long long)(I.n[0] + 12) * (I.n[1] + 12) * (I.n[2] + 12);
             ok = ok && dalloc(c, (void**)&S.D3, sizeof(double) * 9 * ne);
@@ -605,10 +619,12 @@ es_status es_rk_step(es_ctx* c, double* JU, double* J, double* x, const double* 
     if (c->n_inst != 1) return fail(c, ES_ERR_UNSUPPORTED, "es_rk_step: single-instance context required");
     StagePtrs P[3];
     stage_ptrs(c, 0, JU, J, x, xdot, dt, P);
-    // on a fixed mesh the stage meshes equal x, so the metrics of the first stage serve all three
-    const bool fixed = c->hI[0].fixed != 0;
+    // on a fixed mesh the stage meshes equal x, so the metrics of the first stage serve all three;
+    // in 2D the first stage also forms M(xdot) and the others use M + s dt M(xdot)
+    const bool fixed = c->hI[0].fixed != 0, lin = linear_stage_metrics(c);
     for (int s = 0; s < 3; ++s)
-        launch_residual(c, P[s], nullptr, true, RK_A[s], RK_B[s], (cudaStream_t)stream, s == 0 || !fixed);
+        launch_residual(c, P[s], nullptr, true, RK_A[s], RK_B[s], (cudaStream_t)stream, s == 0 || (!fixed && !lin),
+                        lin ? MCOEF[s] : 0.0, lin && s == 0);
     return cuda_check(c, "es_rk_step");
 }
 
@@ -815,6 +831,7 @@ es_status es_autotune(es_ctx* c, const double* JU, const double* J, const double
                 L.mode = MODE_WRITE;
                 L.a = 0.0;
                 L.b = 1.0;
+                L.mcoef = 0.0;
                 L.status = c->status;
                 const int grid = c->sms * o;
                 flux_launch(c, L, sh, grid, st);

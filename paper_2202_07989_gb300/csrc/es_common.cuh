@@ -93,6 +93,7 @@ struct StagePtrs {
     const double* x;
     const double* xdot;
     double* M;                // padded metrics target
+    double* Md;               // 2D: padded metrics of the mesh velocity (stage k: M + s_k dt Md)
     double* accU;             // residual accumulators: n_c fields and J
     double* accJ;
     const double* JU0;        // RK base state q^n
@@ -110,6 +111,7 @@ struct StagePtrs {
 // context-owned scratch of one instance (fixed for the context's lifetime)
 struct Scratch {
     double* M;                // padded metrics
+    double* Md;               // 2D: padded metrics of the mesh velocity
     double* D3;               // 3D: products delta_b[x_p] x_q on the grid with 6 ghost layers
     double* XE;               // 3D: x on the grid with 9 ghost layers (boundary maps applied once)
     double* accU;
@@ -240,6 +242,40 @@ __device__ __forceinline__ double vcl_metric(const double* xd, const double* m)
 #pragma unroll
     for (int j = 1; j < D; ++j) s = fma(xd[j], m[j], s);
     return -s;
+}
+
+// 2D metrics of a staged two-component field v at tile position (cy, cx) (3-node halo):
+// m[0] = delta_2[v_2] / dxi_2, m[1] = -delta_2[v_1] / dxi_2, m[2] = -delta_1[v_2] / dxi_1,
+// m[3] = delta_1[v_1] / dxi_1, with mc = alpha_m / (2 dxi_k).  The operator is linear in v, so
+// the metrics of the mesh x + s xdot are M(x) + s M(xdot).
+template <int HY, int HX>
+__device__ __forceinline__ void metrics2d_at(const Inst& I, const double (*v)[HY][HX], int cy, int cx, double m[4])
+{
+    double m11 = 0.0, m12 = 0.0, m21 = 0.0, m22 = 0.0;
+#pragma unroll
+    for (int a = 1; a <= 3; ++a) {
+        const double c1 = I.mc[0][a - 1], c2 = I.mc[1][a - 1];
+        m11 = fma(c2, v[1][cy + a][cx] - v[1][cy - a][cx], m11);
+        m12 = fma(c2, v[0][cy - a][cx] - v[0][cy + a][cx], m12);
+        m21 = fma(c1, v[1][cy][cx - a] - v[1][cy][cx + a], m21);
+        m22 = fma(c1, v[0][cy][cx + a] - v[0][cy][cx - a], m22);
+    }
+    m[0] = m11;
+    m[1] = m12;
+    m[2] = m21;
+    m[3] = m22;
+}
+
+// the six padded 2D metric rows at p: VCL row, then the spatial rows, for k = 1, 2
+__device__ __forceinline__ void store_metrics2d(double* M, long long np, long long p, const double xd[2], const double m[4])
+{
+    const double r1[2] = { m[0], m[1] }, r2[2] = { m[2], m[3] };
+    M[0 * np + p] = vcl_metric<2>(xd, r1);
+    M[1 * np + p] = m[0];
+    M[2 * np + p] = m[1];
+    M[3 * np + p] = vcl_metric<2>(xd, r2);
+    M[4 * np + p] = m[2];
+    M[5 * np + p] = m[3];
 }
 
 // scalar node field with periodic wrap, else copy of the boundary node

@@ -238,6 +238,12 @@ struct Tile {
     static constexpr int NP = NPL * WT;
 };
 
+// rows of the staging buffer: JU (n_c), J and the metric row of direction k (d + 1); a 2D
+// stage's Md rows (metrics M + s dt Md) are read directly in phase 1 (staging them too cost
+// the RK launch of the batched form a quarter of its speed)
+template <int D, int NS>
+__host__ __device__ constexpr int stage_rows() { return NS + 2 * D + 3; }
+
 // byte offset of the staging buffer behind the compute-type arrays of a flux tile (16-byte aligned)
 template <int D, int NS, typename R, int S, int WT>
 __host__ __device__ constexpr size_t stage_offset()
@@ -257,7 +263,7 @@ __device__ __forceinline__ void cp_async8(double* smem, const double* gmem)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// Issue the raw FP64 node inputs of tile `wi` into the staging buffer stg[NC + D + 2][NN]:
+// Issue the raw FP64 node inputs of tile `wi` into the staging buffer stg[stage_rows][NN]:
 // JU and J of the node the boundary map of direction k reaches (nothing for an inflow
 // ghost, whose state is a constant) and the metric row of direction k at the node.
 template <int D, int NS, int S, int WT>
@@ -341,6 +347,8 @@ __global__ void __launch_bounds__(FLUX_TPB, (sizeof(R) == 4 ? (D == 2 ? 3 : 2) :
         const int s0 = ts * S, a0 = ta * WT;
         const long long ncell = I.ncell;
         const double inv_dx = I.inv_dxi[k];
+        // 2D stage metrics M + s Md with s = mcoef dt (the stage mesh is x^n + s xdot)
+        const double sM = (D == 2 && L.mcoef != 0.0) ? L.mcoef * *P.dt : 0.0;
 
         // ---------------- phase 1: node states, entropy variables, metrics ----------------
         if (staged) {
@@ -429,12 +437,18 @@ __global__ void __launch_bounds__(FLUX_TPB, (sizeof(R) == 4 ? (D == 2 ? 3 : 2) :
             // g in [-3, n + 3))
             {
                 const long long mrow = (long long)(k * (D + 1)) * I.npad + pid;
-                const double m0 = staged ? stg[(NC + 1) * NN + node] : P.M[mrow];
-                mt64[node] = m0;
-                nr[Y::MR * NN + node] = to_r<R>(m0);
+                double mv[D + 1];
 #pragma unroll
-                for (int j = 0; j < D; ++j)
-                    nr[(Y::MR + 1 + j) * NN + node] = to_r<R>(staged ? stg[(NC + 2 + j) * NN + node] : P.M[mrow + (1 + j) * I.npad]);
+                for (int c = 0; c <= D; ++c) mv[c] = staged ? stg[(NC + 1 + c) * NN + node] : P.M[mrow + c * I.npad];
+                if (D == 2 && sM != 0.0) {
+#pragma unroll
+                    for (int c = 0; c <= D; ++c)
+                        mv[c] = fma(sM, P.Md[mrow + c * I.npad], mv[c]);
+                }
+                mt64[node] = mv[0];
+                nr[Y::MR * NN + node] = to_r<R>(mv[0]);
+#pragma unroll
+                for (int j = 0; j < D; ++j) nr[(Y::MR + 1 + j) * NN + node] = to_r<R>(mv[1 + j]);
             }
         }
         __syncthreads();
@@ -744,7 +758,7 @@ __global__ void __launch_bounds__(FLUX_TPB, (sizeof(R) == 4 ? (D == 2 ? 3 : 2) :
 template <int D, int NS, typename R, int S, int WT>
 static size_t smem_of()
 {
-    return stage_offset<D, NS, R, S, WT>() + sizeof(double) * (NS + 2 * D + 3) * Tile<S, WT>::NN;
+    return stage_offset<D, NS, R, S, WT>() + sizeof(double) * stage_rows<D, NS>() * Tile<S, WT>::NN;
 }
 
 // one case per tile shape of the table in es_kernels.cuh

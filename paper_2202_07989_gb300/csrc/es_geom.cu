@@ -24,11 +24,13 @@ __device__ inline double delta_x(const Inst& I, const double* __restrict__ x, in
 }
 
 // 2D: J xi_1/x = (delta_2[x_2], -delta_2[x_1]) / dxi_2, J xi_2/x = (-delta_1[x_2], delta_1[x_1]) / dxi_1
-// over the padded node range (3 ghost layers); with `reset`, block 0 also resets the reduction
+// over the padded node range (3 ghost layers); with DOT also the metrics of the mesh velocity
+// xdot into Md (the 2D metrics are linear in x); with `reset`, block 0 also resets the reduction
 // slots of the ninst instances (the first kernel of a mesh step).  Each block stages x on its tile and on a
 // halo of 3 nodes in shared memory (ghost nodes through the boundary maps, once per node),
 // then forms both derivatives from shared memory; the coefficients mc = alpha_m / (2 dxi_k)
 // fold the scaling into the stencil.
+template <bool DOT>
 __global__ void __launch_bounds__(NODE_TPB) metrics2d_kernel(const Inst* __restrict__ insts, StagePtrs single,
                                                               const StagePtrs* __restrict__ table,
                                                               const int2* __restrict__ work, int nwork,
@@ -38,6 +40,7 @@ __global__ void __launch_bounds__(NODE_TPB) metrics2d_kernel(const Inst* __restr
     reset_reductions(reset, ninst);
     constexpr int HX = NT_X + 6, HY = NT_Y + 6;
     __shared__ double sx[2][HY][HX];
+    __shared__ double sv[DOT ? 2 : 1][DOT ? HY : 1][DOT ? HX : 1];
     const int lx = (int)threadIdx.x % NT_X, ly = (int)threadIdx.x / NT_X;
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
         const int2 it = work[wi];
@@ -52,34 +55,38 @@ __global__ void __launch_bounds__(NODE_TPB) metrics2d_kernel(const Inst* __restr
         for (int q = threadIdx.x; q < HX * HY; q += NODE_TPB) {
             const int a = q % HX, b = q / HX;
             const int g0 = b0 + a, g1 = b1 + b;
-            double v[2] = { 0.0, 0.0 };
+            double v[2] = { 0.0, 0.0 }, w[2] = { 0.0, 0.0 };
             if (inner) {
                 const int c = g1 * n0 + g0;
                 v[0] = S.x[c];
                 v[1] = S.x[I.ncell + c];
+                if (DOT) {
+                    w[0] = S.xdot[c];
+                    w[1] = S.xdot[I.ncell + c];
+                }
             } else if (g0 >= -6 && g0 < n0 + 6 && g1 >= -6 && g1 < n1 + 6) {
                 // entries beyond 6 ghost layers feed only nodes outside the padded range
                 x_at<false>(I, S.x, g0, g1, 0, v);
+                if (DOT) x_at<true>(I, S.xdot, g0, g1, 0, w);
             }
             sx[0][b][a] = v[0];
             sx[1][b][a] = v[1];
+            if (DOT) {
+                sv[0][b][a] = w[0];
+                sv[1][b][a] = w[1];
+            }
         }
         __syncthreads();
         const int i0 = b0 + 3 + lx, i1 = b1 + 3 + ly;
         if (i0 >= n0 + 3 || i1 >= n1 + 3) continue;
         const int cx = lx + 3, cy = ly + 3;
-        // m11 = delta_2[x_2] / dxi_2, m12 = -delta_2[x_1] / dxi_2, m21 = -delta_1[x_2] / dxi_1, m22 = delta_1[x_1] / dxi_1
-        double m11 = 0.0, m12 = 0.0, m21 = 0.0, m22 = 0.0;
-#pragma unroll
-        for (int m = 1; m <= 3; ++m) {
-            const double c1 = I.mc[0][m - 1], c2 = I.mc[1][m - 1];
-            m11 = fma(c2, sx[1][cy + m][cx] - sx[1][cy - m][cx], m11);
-            m12 = fma(c2, sx[0][cy - m][cx] - sx[0][cy + m][cx], m12);
-            m21 = fma(c1, sx[1][cy][cx - m] - sx[1][cy][cx + m], m21);
-            m22 = fma(c1, sx[0][cy][cx + m] - sx[0][cy][cx - m], m22);
-        }
+        double m[4];
+        metrics2d_at<HY, HX>(I, sx, cy, cx, m);
         double xd[2] = { 0.0, 0.0 };
-        if (!S.xdot) {
+        if (DOT) {
+            xd[0] = sv[0][cy][cx];
+            xd[1] = sv[1][cy][cx];
+        } else if (!S.xdot) {
         } else if (i0 >= 0 && i0 < n0 && i1 >= 0 && i1 < n1) {
             const int c = i1 * n0 + i0;
             xd[0] = S.xdot[c];
@@ -87,16 +94,22 @@ __global__ void __launch_bounds__(NODE_TPB) metrics2d_kernel(const Inst* __restr
         } else {
             x_at<true>(I, S.xdot, i0, i1, 0, xd);
         }
-        double* M = S.M;
         const long long np = I.npad, p = plin(I, i0, i1, 0);
-        const double r1[2] = { m11, m12 }, r2[2] = { m21, m22 };
-        M[0 * np + p] = vcl_metric<2>(xd, r1);
-        M[1 * np + p] = m11;
-        M[2 * np + p] = m12;
-        M[3 * np + p] = vcl_metric<2>(xd, r2);
-        M[4 * np + p] = m21;
-        M[5 * np + p] = m22;
+        store_metrics2d(S.M, np, p, xd, m);
+        if (DOT) {
+            // metrics of the mesh velocity: the stages of an RK step use M + s dt Md
+            double md[4];
+            metrics2d_at<DOT ? HY : 1, DOT ? HX : 1>(I, sv, cy, cx, md);
+            store_metrics2d(S.Md, np, p, xd, md);
+        }
     }
+}
+
+void launch_metrics2d(bool dot, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
+                      const StagePtrs* table, const int2* work, int nwork, const Scratch* reset, int ninst)
+{
+    if (dot) pdl_launch(metrics2d_kernel<true>, grid, NODE_TPB, 0, st, insts, single, table, work, nwork, reset, ninst);
+    else pdl_launch(metrics2d_kernel<false>, grid, NODE_TPB, 0, st, insts, single, table, work, nwork, reset, ninst);
 }
 
 // 3D pass 0: x on the grid with 9 ghost layers (extent n + 18), every ghost node mapped once

@@ -45,11 +45,13 @@ struct FluxLaunch {
     int k;             // direction
     int mode;          // MODE_*
     double a, b;       // Shu-Osher coefficients of the stage (MODE_RK)
+    double mcoef;      // 2D: the stage metrics are M + mcoef dt Md (0: M alone)
     int* status;
 };
 
-__global__ void metrics2d_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work, int nwork,
-                                 const Scratch* reset, int ninst);
+// 2D metrics; dot = true also forms the metrics of the mesh velocity into Md
+void launch_metrics2d(bool dot, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
+                      const StagePtrs* table, const int2* work, int nwork, const Scratch* reset, int ninst);
 __global__ void xe_fill_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work, int nwork,
                                const Scratch* scr, int reset_n);
 __global__ void dx3d_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work, int nwork,

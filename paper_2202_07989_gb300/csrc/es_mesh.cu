@@ -1003,6 +1003,102 @@ __global__ void xdot_vcl_kernel(const Inst* __restrict__ insts, StagePtrs single
     }
 }
 
+// 2D velocity pass of a full time step, over the padded node range: the mesh velocity on a tile
+// plus a 3-node halo in shared memory (ghost nodes through the velocity map, values exactly as
+// xdot_kernel forms them), then at every padded node the first stage's VCL metrics (from the
+// spatial metrics of x^n in M), the metrics of the velocity into Md (the later stages use
+// M + s dt Md: the 2D metrics are linear in x) and, at interior nodes, xdot itself.
+template <bool MIXED>
+__global__ void __launch_bounds__(NODE_TPB) xdot_vel2d_kernel(const Inst* __restrict__ insts, StagePtrs single,
+                                                               const StagePtrs* __restrict__ table,
+                                                               const int2* __restrict__ work, int nwork,
+                                                               const Scratch* __restrict__ scr)
+{
+    pdl_entry();
+    constexpr int HX = NT_X + 6, HY = NT_Y + 6;
+    __shared__ double sv[2][HY][HX];
+    __shared__ double sc3[3];
+    const int lx = (int)threadIdx.x % NT_X, ly = (int)threadIdx.x / NT_X;
+    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+        const int2 it = work[wi];
+        const Inst& I = insts[it.x];
+        ES_PTRS(P);
+        const Scratch& Sc = scr[it.x];
+        const double* xmu = xmu_of(P, Sc, I.mu);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const double dt_ = P.dt_fixed > 0.0 ? P.dt_fixed : I.cfl / Sc.red[0];
+            sc3[0] = dt_;
+            sc3[1] = Sc.red[5];
+            sc3[2] = Sc.red[5] / dt_;
+            if (it.y == 0) {
+                P.out[0] = dt_;
+                P.out[1] = Sc.red[5];
+            }
+        }
+        __syncthreads();
+        const double dt = sc3[0], dtau = sc3[1], sc = sc3[2];
+        const int n0 = I.n[0], n1 = I.n[1];
+        const long long n = I.ncell;
+        const int ntx = (n0 + 6 + NT_X - 1) / NT_X;
+        const int b0 = (it.y % ntx) * NT_X - 6, b1 = (it.y / ntx) * NT_Y - 6;
+        for (int q = threadIdx.x; q < HX * HY; q += NODE_TPB) {
+            const int a = q % HX, b = q / HX;
+            const int g0 = b0 + a, g1 = b1 + b;
+            double w[2] = { 0.0, 0.0 };
+            if (g0 >= -6 && g0 < n0 + 6 && g1 >= -6 && g1 < n1 + 6) {
+                const bool in = g0 >= 0 && g0 < n0 && g1 >= 0 && g1 < n1;
+                if (MIXED) {
+                    if (I.mu > 0) {
+                        const float* y = reinterpret_cast<const float*>(xmu);
+                        float yv[3];
+                        if (in) {
+                            yv[0] = y[(long long)g1 * n0 + g0];
+                            yv[1] = y[n + (long long)g1 * n0 + g0];
+                        } else {
+                            y_at(I, y, g0, g1, 0, yv);
+                        }
+                        w[0] = sc * f32_to_f64(yv[0]);
+                        w[1] = sc * f32_to_f64(yv[1]);
+                    }
+                } else {
+                    double ax[3], bx[3];
+                    if (in) {
+                        const long long c = (long long)g1 * n0 + g0;
+                        ax[0] = xmu[c];
+                        ax[1] = xmu[n + c];
+                        bx[0] = P.x[c];
+                        bx[1] = P.x[n + c];
+                    } else {
+                        x_at<true>(I, xmu, g0, g1, 0, ax);
+                        x_at<true>(I, P.x, g0, g1, 0, bx);
+                    }
+                    w[0] = dtau * (ax[0] - bx[0]) / dt;
+                    w[1] = dtau * (ax[1] - bx[1]) / dt;
+                }
+            }
+            sv[0][b][a] = w[0];
+            sv[1][b][a] = w[1];
+        }
+        __syncthreads();
+        const int i0 = b0 + 3 + lx, i1 = b1 + 3 + ly;
+        if (i0 >= n0 + 3 || i1 >= n1 + 3) continue;
+        const int cx = lx + 3, cy = ly + 3;
+        const double xd[2] = { sv[0][cy][cx], sv[1][cy][cx] };
+        if (i0 >= 0 && i0 < n0 && i1 >= 0 && i1 < n1) {
+            const long long c = (long long)i1 * n0 + i0;
+            P.xdot_out[c] = xd[0];
+            P.xdot_out[n + c] = xd[1];
+        }
+        const long long np = I.npad, p = plin(I, i0, i1, 0);
+        const double m[4] = { Sc.M[1 * np + p], Sc.M[2 * np + p], Sc.M[4 * np + p], Sc.M[5 * np + p] };
+        store_metrics2d(Sc.M, np, p, xd, m);
+        double md[4];
+        metrics2d_at<HY, HX>(I, sv, cy, cx, md);
+        store_metrics2d(Sc.Md, np, p, xd, md);
+    }
+}
+
 // entropy diagnostics: per-block partial sums of V.dJU - phi dJ and J eta
 __global__ void entropy_partial_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
                                        const int2* __restrict__ work, int nwork, double* __restrict__ partial)
@@ -1177,6 +1273,13 @@ void launch_xdot_vcl(bool mixed, int d, int grid, cudaStream_t st, const Inst* i
     if (d == 2) { if (mixed) XV(2, true); else XV(2, false); }
     else { if (mixed) XV(3, true); else XV(3, false); }
 #undef XV
+}
+
+void launch_xdot_vel2d(bool mixed, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
+                       const StagePtrs* table, const int2* work, int nwork, const Scratch* scr)
+{
+    if (mixed) pdl_launch(xdot_vel2d_kernel<true>, grid, NODE_TPB, 0, st, insts, single, table, work, nwork, scr);
+    else pdl_launch(xdot_vel2d_kernel<false>, grid, NODE_TPB, 0, st, insts, single, table, work, nwork, scr);
 }
 
 void launch_xdot(bool mixed, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,

@@ -11,6 +11,8 @@ void launch_xdot(bool mixed, int grid, cudaStream_t st, const Inst* insts, const
                  const StagePtrs* table, const int2* work, int nwork, const Scratch* scr);
 void launch_xdot_vcl(bool mixed, int d, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
                      const StagePtrs* table, const int2* work, int nwork, const Scratch* scr);
+void launch_xdot_vel2d(bool mixed, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
+                       const StagePtrs* table, const int2* work, int nwork, const Scratch* scr);
 void launch_monitor_theta(bool mixed, int grid, cudaStream_t st, const Inst* insts, const int2* work, int nwork,
                           const Scratch* scr);
 void launch_filter(bool mixed, bool from_g, int grid, cudaStream_t st, const Inst* insts, const int2* work, int nwork,
