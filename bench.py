@@ -44,6 +44,10 @@ WORKLOAD = ("2D two-component stiffened-gas shock-bubble, 400x200 cells on [0,2]
 # FP64 as stated for GB300 (1.25 TFLOP/s)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FP64_PEAK_TFLOPS = 1.25
+# DRAM bytes (read + write) per flux launch of the 400x200 mixed step: the mean of the two
+# launches of a stage in one ncu capture of the same tuned kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum, cold cache); the capture and its command are in profiles/
+FLUX_TRAFFIC_BYTES = 9.30e6
 
 
 def flux_flops_per_interface(D, NS, es=True):
@@ -498,7 +502,7 @@ def main_ours(args):
     avg_s = flux_ms / flux_n / 1e3 if flux_n else float("nan")
     ach = flops_launch / avg_s / 1e12
     roofline = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
-                "traffic": None, "kernel": "flux_kernel (mixed form)", "flops_per_launch": flops_launch,
+                "traffic": FLUX_TRAFFIC_BYTES, "traffic_unit": "bytes per launch", "kernel": "flux_kernel (mixed form)", "flops_per_launch": flops_launch,
                 "avg_launch_ms": avg_s * 1e3, "peak_source": "FP32: 152 SMs x 128 lanes x 2 x 2.07 GHz"}
     flux64_ms = sum(prof_d[k][0] for k in ("flux_k1", "flux_k2", "flux_k3"))
     flux64_n = sum(prof_d[k][1] for k in ("flux_k1", "flux_k2", "flux_k3"))
