@@ -48,6 +48,8 @@ FP64_PEAK_TFLOPS = 1.25
 # launches of a stage in one ncu capture of the same tuned kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum, cold cache); the capture and its command are in profiles/
 FLUX_TRAFFIC_BYTES = 9.30e6
+# the same for one fused 2D stage launch (both directions); None until captured
+FLUX2D_TRAFFIC_BYTES = None
 
 
 def flux_flops_per_interface(D, NS, es=True):
@@ -69,21 +71,23 @@ def flux_flops_per_interface(D, NS, es=True):
     return ec + gcl + setup + NC * column + NC
 
 
-def launches_per_step(pb, mixed=True):
+def launches_per_step(pb, mixed=True, fused=False):
     """Kernel launches of one es_step.  The mesh step: the metrics of x^n (with the reduction
     reset; 2D one launch, 3D three), CFL + gradients, then the monitor, nf filter passes and mu
     sweeps (the mixed 2D form runs them as one launch for mu 1..8, nf <= 4; otherwise one
     launch each plus the limiter when mu = 0), and the velocity pass; a fixed mesh stops after
-    CFL with the velocity pass.  Then d flux launches per stage; 3D stages 2 and 3 form their
-    metrics, 2D stages use M + s dt M(xdot) from the velocity pass."""
+    CFL with the velocity pass.  Then d flux launches per stage (one with the fused 2D stage
+    launch); 3D stages 2 and 3 form their metrics, 2D stages use M + s dt M(xdot) from the
+    velocity pass."""
     m = 1 if pb.d == 2 else 3
+    per_stage = 1 if (fused and pb.d == 2) else pb.d
     if pb.fixed_mesh:
-        return m + 2 + 3 * pb.d
+        return m + 2 + 3 * per_stage
     if mixed and pb.d == 2 and 1 <= pb.mu <= 8 and pb.nf <= 4:
         mesh = m + 1 + 1 + 1
     else:
         mesh = m + 1 + 1 + pb.nf + pb.mu + (pb.mu == 0) + 1
-    return mesh + 3 * pb.d + (0 if pb.d == 2 else 2 * m)
+    return mesh + 3 * per_stage + (0 if pb.d == 2 else 2 * m)
 
 
 class ClockSampler:
@@ -256,12 +260,21 @@ class Batch:
 
 def tune(runner, batched=False):
     """Run the library's flux autotuner on the runner's state; returns the choice per
-    direction as "S x WT tile, grid CTAs"."""
+    direction as "S x WT tile, grid CTAs, ms per launch" and, in 2D, the fused stage launch
+    ("fused TX x TY tile ..." when chosen, else "fused off" with its best time)."""
     if batched:
         t = runner.ctx.es_autotune()
     else:
         t = runner.ctx.es_autotune(runner.JU, runner.J, runner.x, runner.xdot)
-    return ["%dx%d tile, %d CTAs, %.3f ms" % (S, WT, grid, ms) for _, S, WT, grid, ms in t]
+    out = ["%dx%d tile, %d CTAs, %.3f ms" % (S, WT, grid, ms) for _, S, WT, grid, ms in t]
+    if len(t) == 2:
+        sh, TX, TY, grid, ms = runner.ctx.es_get_fusion()
+        out.append("fused %dx%d tile, %d CTAs, %.3f ms" % (TX, TY, grid, ms) if sh >= 0 else "fused off (best %.3f ms)" % ms)
+    return out
+
+
+def is_fused(runner):
+    return runner.ctx.pb.d == 2 and runner.ctx.es_get_fusion()[0] >= 0
 
 
 def time_steps(runner, steps, warmup, torch, flush):
@@ -316,6 +329,16 @@ def errors_vs(ref_JU, ref_J, pb, JU, J):
     return {"rho_l1": float(np.abs(r1 - r0).mean()), "rho_linf": float(np.abs(r1 - r0).max()),
             "p_l1": float(np.abs(p1 - p0).mean()), "p_linf": float(np.abs(p1 - p0).max()),
             "total_entropy_abs": float(abs(s1 - s0)), "total_entropy_rel": float(abs(s1 - s0) / abs(s0))}
+
+
+def oracle_one_step(pb, U, x):
+    """One full oracle step (mesh redistribution + SSP-RK3) of (U, x) from t = 0: (JU, J, x)."""
+    from oracle.oracle import Oracle
+    o = Oracle(pb)
+    J = o.init_J(x)
+    JU = U * J
+    xd, dt, dtau = o.mesh_redistribute(JU, J, x)
+    return o.rk_step(JU, J, x, xd, dt)
 
 
 def cpu_baseline_leg(pb, U, x, gpu_after_one, budget_s=20.0):
@@ -492,24 +515,31 @@ def main_ours(args):
         e2e = {"value": pb.ncell * 3 * ke / te, "unit": UNIT, "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb + 8,
                "steps": ke, "call": "es_run_host (host buffers, 1 step per call)"}
 
-    # roofline of the dominant kernel (flux + divergence + RK stage) in the headline form
-    flux_ms = sum(prof_m[k][0] for k in ("flux_k1", "flux_k2", "flux_k3"))
-    flux_n = sum(prof_m[k][1] for k in ("flux_k1", "flux_k2", "flux_k3"))
+    # roofline of the dominant kernel (flux + divergence + RK stage) in the headline form:
+    # the flops of every interface of a step over the time of the step's flux launches
+    FLUX = ("flux_k1", "flux_k2", "flux_k3", "flux_2d")
+    flux_ms = sum(prof_m[k][0] for k in FLUX)
+    flux_n = sum(prof_m[k][1] for k in FLUX)
     per_iface = flux_flops_per_interface(pb.d, pb.N, pb.es)
-    # interfaces per launch: (n_k + 1) per grid line, averaged over the directions
-    ifaces = sum((pb.n[k] + 1) * pb.ncell // pb.n[k] for k in range(pb.d)) / pb.d
-    flops_launch = per_iface * ifaces
+    # interfaces of one stage: (n_k + 1) per grid line of each direction
+    ifaces_stage = sum((pb.n[k] + 1) * pb.ncell // pb.n[k] for k in range(pb.d))
+    fused_m = is_fused(main)
+    flops_launch = per_iface * ifaces_stage / (1 if fused_m else pb.d)
     avg_s = flux_ms / flux_n / 1e3 if flux_n else float("nan")
     ach = flops_launch / avg_s / 1e12
     roofline = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
-                "traffic": FLUX_TRAFFIC_BYTES, "traffic_unit": "bytes per launch", "kernel": "flux_kernel (mixed form)", "flops_per_launch": flops_launch,
+                "traffic": FLUX_TRAFFIC_BYTES if not fused_m else FLUX2D_TRAFFIC_BYTES, "traffic_unit": "bytes per launch",
+                "kernel": "flux2d_kernel (fused stage, mixed form)" if fused_m else "flux_kernel (mixed form)", "flops_per_launch": flops_launch,
                 "avg_launch_ms": avg_s * 1e3, "peak_source": "FP32: 152 SMs x 128 lanes x 2 x 2.07 GHz"}
-    flux64_ms = sum(prof_d[k][0] for k in ("flux_k1", "flux_k2", "flux_k3"))
-    flux64_n = sum(prof_d[k][1] for k in ("flux_k1", "flux_k2", "flux_k3"))
+    flux64_ms = sum(prof_d[k][0] for k in FLUX)
+    flux64_n = sum(prof_d[k][1] for k in FLUX)
     avg64 = flux64_ms / flux64_n / 1e3 if flux64_n else float("nan")
-    ach64 = flops_launch / avg64 / 1e12
+    fused_d = is_fused(r64)
+    flops64 = per_iface * ifaces_stage / (1 if fused_d else pb.d)
+    ach64 = flops64 / avg64 / 1e12
     roofline_fp64 = {"bound": "alu", "achieved": ach64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": ach64 / FP64_PEAK_TFLOPS, "avg_launch_ms": avg64 * 1e3, "kernel": "flux_kernel (FP64 form)"}
+                     "frac": ach64 / FP64_PEAK_TFLOPS, "avg_launch_ms": avg64 * 1e3,
+                     "kernel": "flux2d_kernel (fused stage, FP64 form)" if fused_d else "flux_kernel (FP64 form)"}
 
     # CPU baseline (rank 0 only): the oracle on a bounded sample, and the errors after one step
     cpu = None
@@ -524,6 +554,36 @@ def main_ours(args):
             torch.cuda.synchronize()
             errs[name] = errors_vs(ref1[0], ref1[1], pb, r.JU.cpu().numpy(), r.J.cpu().numpy())
             errs[name]["vs"] = "FP64 oracle after one full step from t = 0"
+        # the batched launch: a fresh batch of the same 64 instances, one step, and the
+        # oracle on its three smallest instances and its largest
+        if not args.no_batched:
+            insts = W.batched_2d(64)
+            bt1 = Batch(insts, es.MIXED, torch)
+            bt1.step()
+            torch.cuda.synchronize()
+            order = sorted(range(len(insts)), key=lambda i: insts[i][0].ncell)
+            eb = {"vs": "FP64 oracle after one full step from t = 0, per sampled instance of the 64-instance batch"}
+            for i in order[:3] + order[-1:]:
+                p_, U_, x_ = insts[i]
+                o1 = oracle_one_step(p_, U_, x_)
+                eb["instance_%d_%dx%d" % (i, p_.n[0], p_.n[1])] = errors_vs(
+                    o1[0], o1[1], p_, bt1.JU[i].cpu().numpy(), bt1.J[i].cpu().numpy())
+            errs["batched_mixed"] = eb
+            del bt1
+        # the 3D path at sizes the oracle steps in seconds (the timed 3D forms are 128^3 and
+        # 128 x 64 x 64; the kernels and launch shapes are the same at every size)
+        if not args.no_3d:
+            for name, (p3, U3, x3) in (("3d_riemann_32^3", W.riemann_3d(32)),
+                                       ("3d_shock_bubble_48x24x24", W.shock_bubble_3d(24))):
+                o1 = oracle_one_step(p3, U3, x3)
+                for prec, tag in ((es.MIXED, "mixed"), (es.FP64, "fp64")):
+                    r3 = Single(p3, U3, x3, prec, torch)
+                    r3.step()
+                    torch.cuda.synchronize()
+                    e3 = errors_vs(o1[0], o1[1], p3, r3.JU.cpu().numpy(), r3.J.cpu().numpy())
+                    e3["vs"] = "FP64 oracle after one full step from t = 0"
+                    errs["%s_%s" % (tag, name)] = e3
+                    del r3
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -538,7 +598,7 @@ def main_ours(args):
                       "fp64": {k: v[0] / k64 for k, v in prof_d.items()},
                       "batched_mixed": ({k: v[0] / kb for k, v in prof_b.items()} if batched else None)},
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-        "gpu_launches": launches_per_step(pb) * args.steps,
+        "gpu_launches": launches_per_step(pb, True, fused_m) * args.steps,
     }
     if rank == 0:
         print(json.dumps(line))
@@ -599,6 +659,9 @@ def main_kernel_case(args):
         for k, sh in enumerate(int(v) for v in args.kernel_shapes.split(",")):
             r.ctx.es_set_tuning(k, sh, 0)
         tiles = r.ctx.es_get_tuning()
+    if args.kernel_fusion is not None:
+        r.ctx.es_set_fusion(args.kernel_fusion)
+        tiles = [tiles, r.ctx.es_get_fusion()]
     for _ in range(args.kernel_steps):
         r.step()
     torch.cuda.synchronize()
@@ -628,6 +691,7 @@ def main():
     ap.add_argument("--kernel-time", type=int, default=0, help="also time this many eager steps per kernel class")
     ap.add_argument("--kernel-tune", action="store_true", help="run the flux autotuner before the steps")
     ap.add_argument("--kernel-shapes", default=None, help="fix the flux tile shape per direction, e.g. 2,1")
+    ap.add_argument("--kernel-fusion", type=int, default=None, help="2D: fix the fused stage shape (0..4, -1 off)")
     args = ap.parse_args()
     if args.kernel_case:
         return main_kernel_case(args)

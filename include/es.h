@@ -180,6 +180,25 @@ es_status es_get_tuning(const es_ctx* ctx, int* shape, int* S, int* WT, int* gri
  * CTAs (0 = SM count x occupancy of that shape).  ES_ERR_ARG when out of range. */
 es_status es_set_tuning(es_ctx* ctx, int k, int shape, int grid);
 
+/* Fused 2D stage launch (the paper has no counterpart; a launch schedule): both
+ * directions of the residual of Eqs. (semi_U), (semi_J), and the stage update,
+ * in one launch over TX x TY node tiles (5 fused shapes).  Every interface flux
+ * and node divergence is formed by the arithmetic of the per-direction launches,
+ * and the two directions' divergences are summed in the same FP64 order, so
+ * results are bitwise those of the per-direction launches.  es_autotune on a 2D
+ * context also times each fused shape and keeps the fused launch when it beats
+ * the sum of the best per-direction launches; a new context starts without it.
+ * es_get_fusion: fused shape index (-1: per-direction launches), TX, TY, grid
+ * (CTAs) and the best fused time per launch the last es_autotune measured (0 if
+ * none; set even when the per-direction launches won).  All pointers HOST, one
+ * value each. */
+es_status es_get_fusion(const es_ctx* ctx, int* shape, int* TX, int* TY, int* grid, float* ms);
+
+/* Fix the fused 2D stage launch: shape -1 (per-direction launches) or 0..4, and
+ * `grid` CTAs (0 = SM count x occupancy of that shape).  ES_ERR_ARG when out of
+ * range or when shape >= 0 on a 3D context. */
+es_status es_set_fusion(es_ctx* ctx, int shape, int grid);
+
 /* Schlieren function of Example 5.8, Eq. (schlieren), on one instance:
  * phi = exp(-Psi |grad rho| / max |grad rho|), Psi = (psi1 rho_1 + psi2 rho_2) / rho
  * (the paper uses psi1 = 30, psi2 = 150), grad the physical gradient

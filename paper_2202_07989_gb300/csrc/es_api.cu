@@ -30,6 +30,8 @@ struct es_ctx {
     int2* w_cell = nullptr; int n_cell = 0;
     int2* w_flux[3][NSHAPE] = {};          // flux work list per direction and tile shape
     int n_flux[3][NSHAPE] = {};
+    int2* w_fused[NFSHAPE] = {};           // fused 2D stage work list per fused tile shape
+    int n_fused[NFSHAPE] = {};
     int* d_first_cell = nullptr;
     double* partial = nullptr;
     int* status = nullptr;
@@ -46,6 +48,10 @@ struct es_ctx {
     int flux_shape[3] = { SHAPE_DEFAULT_K0, SHAPE_DEFAULT_KN, SHAPE_DEFAULT_KN };
     int flux_grid[3] = { 0, 0, 0 };
     float flux_ms[3] = { 0.f, 0.f, 0.f };
+    // fused 2D stage launch (-1: one launch per direction)
+    int fused_shape = -1;
+    int fused_grid = 0;
+    float fused_ms = 0.f;
     std::string err;
     // kernel timing (es_profile)
     bool prof = false;
@@ -209,6 +215,15 @@ void prepare_all(int weno)
         prepare_flux<D, NS, double, 0>();
         prepare_flux<D, NS, float, 0>();
     }
+    if constexpr (D == 2) {
+        if (weno) {
+            prepare_flux2d<NS, double, 1>();
+            prepare_flux2d<NS, float, 1>();
+        } else {
+            prepare_flux2d<NS, double, 0>();
+            prepare_flux2d<NS, float, 0>();
+        }
+    }
 }
 
 // one flux launch in the given tile shape and grid
@@ -226,6 +241,39 @@ void flux_launch(es_ctx* c, const FluxLaunch& L, int shape, int grid, cudaStream
     else if (c->d == 3 && c->N == 1) FD(3, 1);
     else FD(3, 2);
 #undef FD
+}
+
+// one fused 2D stage launch in the given fused tile shape and grid
+void flux2d_launch(es_ctx* c, const FluxLaunch& L, int shape, int grid, cudaStream_t st)
+{
+    if (grid > L.nwork) grid = L.nwork;
+    if (grid <= 0) return;
+#define F2(n)                                                                                         \
+    do {                                                                                              \
+        if (c->weno) { if (c->mixed) launch_flux2d<n, float, 1>(L, shape, grid, st); else launch_flux2d<n, double, 1>(L, shape, grid, st); } \
+        else { if (c->mixed) launch_flux2d<n, float, 0>(L, shape, grid, st); else launch_flux2d<n, double, 0>(L, shape, grid, st); }        \
+    } while (0)
+    if (c->N == 1) F2(1);
+    else F2(2);
+#undef F2
+}
+
+int flux2d_occ(es_ctx* c, int shape)
+{
+#define FO2(n)                                                                                                \
+    do {                                                                                                      \
+        if (c->weno) return c->mixed ? flux2d_blocks_per_sm<n, float, 1>(shape) : flux2d_blocks_per_sm<n, double, 1>(shape); \
+        return c->mixed ? flux2d_blocks_per_sm<n, float, 0>(shape) : flux2d_blocks_per_sm<n, double, 0>(shape);            \
+    } while (0)
+    if (c->N == 1) FO2(1);
+    FO2(2);
+#undef FO2
+}
+
+// fused 2D stage tiles of instance I in fused tile shape `shape`
+long long fused_tiles(const Inst& I, int shape)
+{
+    return (long long)((I.n[0] + FSHAPE_TX[shape] - 1) / FSHAPE_TX[shape]) * ((I.n[1] + FSHAPE_TY[shape] - 1) / FSHAPE_TY[shape]);
 }
 
 // flux tiles of instance I along direction k in tile shape `shape`
@@ -257,7 +305,7 @@ int node_grid(es_ctx* c, int nwork)
     return nwork < cap ? nwork : cap;
 }
 
-constexpr int PC_FLUX = 0, PC_METRICS = 3, PC_MESH = 4, PC_ENTROPY = 5;
+constexpr int PC_FLUX = 0, PC_METRICS = 3, PC_MESH = 4, PC_ENTROPY = 5, PC_FLUX2D = 6;
 
 bool capturing(cudaStream_t st)
 {
@@ -308,14 +356,32 @@ void launch_metrics(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStr
     }
 }
 
-// residual of one stage: metrics, then one flux launch per direction.  With
-// rk = true the last direction applies the Shu-Osher stage (a, b); metrics = false
-// when M already holds the metrics of the stage; mcoef != 0 (2D) makes the stage metrics
-// M + mcoef dt Md, the metrics of x^n + mcoef dt xdot; dot = true (2D) forms Md with M.
+// residual of one stage: metrics, then one flux launch per direction (or, in 2D, the
+// fused stage launch when the context uses it).  With rk = true the last direction applies
+// the Shu-Osher stage (a, b); metrics = false when M already holds the metrics of the stage;
+// mcoef != 0 (2D) makes the stage metrics M + mcoef dt Md, the metrics of x^n + mcoef dt
+// xdot; dot = true (2D) forms Md with M.
 void launch_residual(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, bool rk, double a, double b, cudaStream_t st,
                      bool metrics = true, double mcoef = 0.0, bool dot = false)
 {
     if (metrics) launch_metrics(c, P, tab, st, false, dot);
+    if (c->d == 2 && c->fused_shape >= 0) {
+        FluxLaunch L;
+        L.insts = c->dI;
+        L.single = P;
+        L.ptrs = tab;
+        L.work = c->w_fused[c->fused_shape];
+        L.nwork = c->n_fused[c->fused_shape];
+        L.k = 0;
+        L.mode = rk ? MODE_RK : MODE_WRITE;
+        L.a = a;
+        L.b = b;
+        L.mcoef = mcoef;
+        L.status = c->status;
+        ProfScope ps(c, PC_FLUX2D, st);
+        flux2d_launch(c, L, c->fused_shape, c->fused_grid, st);
+        return;
+    }
     for (int k = 0; k < c->d; ++k) {
         FluxLaunch L;
         L.insts = c->dI;
@@ -526,6 +592,11 @@ es_status es_create_batch(const es_config* cfgs, int n_inst, es_ctx** out)
         for (int sh = 0; sh < NSHAPE; ++sh) {
             c->w_flux[k][sh] = build_work(c, [k, sh](const Inst& I) { return flux_tiles(I, k, sh); }, c->n_flux[k][sh]);
             ok = ok && c->w_flux[k][sh];
+        }
+    if (c->d == 2)
+        for (int sh = 0; sh < NFSHAPE; ++sh) {
+            c->w_fused[sh] = build_work(c, [sh](const Inst& I) { return fused_tiles(I, sh); }, c->n_fused[sh]);
+            ok = ok && c->w_fused[sh];
         }
     // per-instance ranges of the cell work list (entropy reduction)
     std::vector<int> first(n_inst + 1, 0);
@@ -851,6 +922,47 @@ es_status es_autotune(es_ctx* c, const double* JU, const double* J, const double
         }
         c->flux_ms[k] = best;
     }
+    // 2D: the fused stage launch in each fused shape against the sum of the best
+    // per-direction launches (both in MODE_WRITE); the faster form is kept
+    c->fused_shape = -1;
+    c->fused_ms = 0.f;
+    if (c->d == 2) {
+        float best = 3.0e38f;
+        for (int sh = 0; sh < NFSHAPE; ++sh) {
+            const int occ = flux2d_occ(c, sh);
+            for (int o = occ; o >= 1 && o >= occ - 1; --o) {
+                FluxLaunch L;
+                L.insts = c->dI;
+                L.single = P;
+                L.ptrs = tab;
+                L.work = c->w_fused[sh];
+                L.nwork = c->n_fused[sh];
+                L.k = 0;
+                L.mode = MODE_WRITE;
+                L.a = 0.0;
+                L.b = 1.0;
+                L.mcoef = 0.0;
+                L.status = c->status;
+                const int grid = c->sms * o;
+                flux2d_launch(c, L, sh, grid, st);
+                cudaEventRecord(e0, st);
+                for (int r = 0; r < reps; ++r) flux2d_launch(c, L, sh, grid, st);
+                cudaEventRecord(e1, st);
+                if (cudaEventSynchronize(e1) != cudaSuccess) break;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms /= (float)reps;
+                if (ms < best) {
+                    best = ms;
+                    c->fused_ms = ms;
+                    if (ms < c->flux_ms[0] + c->flux_ms[1]) {
+                        c->fused_shape = sh;
+                        c->fused_grid = grid;
+                    }
+                }
+            }
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return cuda_check(c, "es_autotune");
@@ -878,6 +990,29 @@ es_status es_set_tuning(es_ctx* c, int k, int shape, int grid)
     c->flux_shape[k] = shape;
     c->flux_grid[k] = grid > 0 ? grid : c->sms * flux_occ(c, shape);
     c->flux_ms[k] = 0.f;
+    return ES_OK;
+}
+
+es_status es_get_fusion(const es_ctx* c, int* shape, int* TX, int* TY, int* grid, float* ms)
+{
+    if (!c || !shape || !TX || !TY || !grid || !ms) return ES_ERR_ARG;
+    const int sh = c->fused_shape;
+    *shape = sh;
+    *TX = sh >= 0 ? FSHAPE_TX[sh] : 0;
+    *TY = sh >= 0 ? FSHAPE_TY[sh] : 0;
+    *grid = sh >= 0 ? c->fused_grid : 0;
+    *ms = c->fused_ms;
+    return ES_OK;
+}
+
+es_status es_set_fusion(es_ctx* c, int shape, int grid)
+{
+    if (!c) return ES_ERR_ARG;
+    if (shape < -1 || shape >= NFSHAPE || grid < 0 || (shape >= 0 && c->d != 2))
+        return fail(c, ES_ERR_ARG, "es_set_fusion: shape out of range, negative grid or not a 2D context");
+    c->fused_shape = shape;
+    c->fused_grid = shape >= 0 ? (grid > 0 ? grid : c->sms * flux2d_occ(c, shape)) : 0;
+    c->fused_ms = 0.f;
     return ES_OK;
 }
 

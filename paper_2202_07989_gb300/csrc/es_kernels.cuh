@@ -14,6 +14,11 @@ constexpr int SHAPE_S[NSHAPE] = { 62, 58, 122, 30, 26, 14 };
 constexpr int SHAPE_WT[NSHAPE] = { 4, 4, 2, 8, 8, 16 };
 constexpr int SHAPE_DEFAULT_K0 = 0;    // direction 1: 62 nodes along the line x 4 lines
 constexpr int SHAPE_DEFAULT_KN = 3;    // directions 2, 3: 30 nodes x 8 neighbouring lines (coalesced)
+// fused 2D stage tiles (both directions in one launch): TX x TY output nodes, at most 256
+// interfaces per direction; the autotuner picks one shape, or the per-direction launches
+constexpr int NFSHAPE = 5;
+constexpr int FSHAPE_TX[NFSHAPE] = { 16, 12, 14, 24, 20 };
+constexpr int FSHAPE_TY[NFSHAPE] = { 12, 16, 14, 8, 10 };
 constexpr int NODE_TPB = 256;
 
 // launch with programmatic stream serialization (the kernel must begin with pdl_entry())
@@ -42,7 +47,7 @@ struct FluxLaunch {
     const StagePtrs* ptrs;    // per-instance table of a batched call (or null)
     const int2* work;
     int nwork;
-    int k;             // direction
+    int k;             // direction (per-direction kernel)
     int mode;          // MODE_*
     double a, b;       // Shu-Osher coefficients of the stage (MODE_RK)
     double mcoef;      // 2D: the stage metrics are M + mcoef dt Md (0: M alone)
@@ -69,5 +74,13 @@ template <int D, int NS, typename R, int WK>
 void prepare_flux();
 template <int D, int NS, typename R, int WK>
 int flux_blocks_per_sm(int shape);
+
+// fused 2D stage (both directions, MODE_RK or MODE_WRITE), fused tile shape index `shape`
+template <int NS, typename R, int WK>
+void launch_flux2d(const FluxLaunch& L, int shape, int grid, cudaStream_t st);
+template <int NS, typename R, int WK>
+void prepare_flux2d();
+template <int NS, typename R, int WK>
+int flux2d_blocks_per_sm(int shape);
 
 }  // namespace es

@@ -70,6 +70,8 @@ def lib():
             "es_autotune": (C.c_int, [vp, dp, dp, dp, dp, C.c_int, vp]),
             "es_get_tuning": (C.c_int, [vp, ip, ip, ip, ip, C.POINTER(C.c_float)]),
             "es_set_tuning": (C.c_int, [vp, C.c_int, C.c_int, C.c_int]),
+            "es_get_fusion": (C.c_int, [vp, ip, ip, ip, ip, C.POINTER(C.c_float)]),
+            "es_set_fusion": (C.c_int, [vp, C.c_int, C.c_int]),
             "entropy_production": (C.c_int, [vp, dp, dp, dp, dp, dp, vp]),
             "es_bind_batch": (C.c_int, [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp)]),
             "es_step_batch": (C.c_int, [vp, vp]),
@@ -253,6 +255,17 @@ class Context:
     def es_set_tuning(self, k: int, shape: int, grid: int = 0):
         self._chk(self.L.es_set_tuning(self.h, int(k), int(shape), int(grid)), "es_set_tuning")
 
+    def es_get_fusion(self):
+        """(fused shape or -1, TX, TY, grid, best fused ms per launch) of the 2D stage launch."""
+        a = [C.c_int() for _ in range(4)]
+        ms = C.c_float()
+        self._chk(self.L.es_get_fusion(self.h, *[C.byref(v) for v in a], C.byref(ms)), "es_get_fusion")
+        return tuple(v.value for v in a) + (ms.value,)
+
+    def es_set_fusion(self, shape: int, grid: int = 0):
+        """Fused 2D stage launch in fused shape `shape` (0..4), or -1 for one launch per direction."""
+        self._chk(self.L.es_set_fusion(self.h, int(shape), int(grid)), "es_set_fusion")
+
     def es_schlieren(self, JU, J, x, psi1: float = 30.0, psi2: float = 150.0, phi=None):
         """Schlieren function of Eq. (schlieren) at the nodes."""
         pb = self.pb
@@ -305,7 +318,7 @@ class Context:
                   "es_run_host")
         return tt.value
 
-    PROFILE_CLASSES = ("flux_k1", "flux_k2", "flux_k3", "metrics", "mesh", "entropy")
+    PROFILE_CLASSES = ("flux_k1", "flux_k2", "flux_k3", "metrics", "mesh", "entropy", "flux_2d")
 
     def es_profile(self, enable: bool = True):
         self._chk(self.L.es_profile(self.h, int(enable)), "es_profile")

@@ -1,0 +1,145 @@
+"""The fused 2D stage launch (both directions of a stage's residual and the stage update in
+one launch over TX x TY node tiles) against the per-direction launches, bit for bit, and
+against the FP64 oracle.
+
+Grids: 70 x 37 leaves ragged tiles in both directions for every fused shape (16x12, 12x16,
+14x14, 24x8, 20x10); 10 x 11 is smaller than one tile in both directions.
+"""
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle
+from paper_2202_07989_gb300 import workloads as W
+
+from .helpers import TOL_FP64, case, fieldwise, need_gpu, rel_max_err, to_dev
+
+pytestmark = pytest.mark.gpu
+
+NFSHAPE = 5
+
+
+def _ctx(pb, precision=0):
+    from paper_2202_07989_gb300 import es
+    return es.Context(pb, precision)
+
+
+def _same(a, b):
+    return all(bool((u == v).all()) for u, v in zip(a, b))
+
+
+@pytest.mark.parametrize("N", [1, 2])
+@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("bc", ["periodic", "mixed", "reflect"])
+def test_fused_stage_bitwise(N, form, bc):
+    """Every fused shape, at one CTA per SM and at full occupancy, gives the residual and the
+    RK step (stage metrics M + s dt Md) of the per-direction launches bit for bit: with and
+    without the dissipation, WENO-MR and WENO-JS, ragged and sub-tile grids."""
+    torch = need_gpu()
+    variants = (((70, 37), True, 0, 11), ((10, 11), True, 0, 12), ((70, 37), False, 0, 13), ((41, 29), True, 1, 14))
+    for n, es_, weno, seed in variants:
+        pb, JU, J, x, xdot = case(2, N, n, bc, es=es_, seed=seed + N, jump=True, pinf=0.6 if N == 1 else 0.0)
+        pb = pb.with_(weno=weno)
+        ctx = _ctx(pb, form)
+        G = [to_dev(t, torch) for t in (JU, J, x, xdot)]
+        dt = torch.tensor([0.3 * Oracle(pb).cfl_dt(JU, J, x)], dtype=torch.float64, device="cuda")
+        assert ctx.es_get_fusion()[0] == -1
+        ref = ctx.es_rhs(*G)
+        A = [t.clone() for t in G[:3]]
+        ctx.es_rk_step(*A, G[3], dt)
+        for shape in range(NFSHAPE):
+            for grid in (0, 152):
+                ctx.es_set_fusion(shape, grid)
+                got = ctx.es_rhs(*G)
+                assert _same(got, ref), (n, es_, weno, shape, grid)
+                B = [t.clone() for t in G[:3]]
+                ctx.es_rk_step(*B, G[3], dt)
+                assert _same(A, B), (n, es_, weno, shape, grid)
+        ctx.es_set_fusion(-1)
+        assert ctx.es_poll_status() == 0
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_fused_step_and_batch_bitwise(form):
+    """Full steps (mesh redistribution + SSP-RK3) with the fused stage launch equal those with
+    the per-direction launches bit for bit, for a single shock-bubble instance and for a
+    batch of uneven instances."""
+    torch = need_gpu()
+    from paper_2202_07989_gb300 import es
+    pb, U, x = W.shock_bubble_2d(96, 64)
+    J = Oracle(pb).init_J(x)
+    st0 = [to_dev(t, torch) for t in (U * J, J, x)]
+    runs = []
+    for shape in (-1, 0, 3):
+        ctx = _ctx(pb, form)
+        ctx.es_set_fusion(shape)
+        S = [t.clone() for t in st0]
+        for _ in range(2):
+            xd, dd = ctx.es_step(*S)
+        runs.append(S + [xd, dd])
+    assert _same(runs[0], runs[1]) and _same(runs[0], runs[2])
+
+    insts = W.batched_2d(count=3, nmin=40, nmax=90, mu=3)
+    probs = [p for p, _, _ in insts]
+    st = []
+    for p, U, x in insts:
+        J = Oracle(p).init_J(x)
+        st.append((U * J, J, x))
+    outs = []
+    for shape in (-1, 1, 4):
+        b = es.Context(probs, form)
+        b.es_set_fusion(shape)
+        JU = [to_dev(s[0], torch) for s in st]
+        Jd = [to_dev(s[1], torch) for s in st]
+        X = [to_dev(s[2], torch) for s in st]
+        XD = [torch.zeros_like(t) for t in X]
+        DD = [torch.zeros(2, dtype=torch.float64, device="cuda") for _ in st]
+        b.es_bind_batch(JU, Jd, X, XD, DD)
+        for _ in range(2):
+            b.es_step_batch()
+        outs.append(JU + Jd + X)
+    assert _same(outs[0], outs[1]) and _same(outs[0], outs[2])
+
+
+@pytest.mark.parametrize("N", [1, 2])
+def test_fused_rk_step_vs_oracle(N):
+    """With the fused stage launch, one FP64 RK step from the oracle's state matches the
+    oracle's step to 1e-12 per field (ragged tiles, outflow/inflow and reflecting sides)."""
+    torch = need_gpu()
+    pb, JU, J, x, xdot = case(2, N, (70, 37), "mixed", es=True, seed=5 + N)
+    o = Oracle(pb)
+    dt = 0.3 * o.cfl_dt(JU, J, x)
+    ctx = _ctx(pb)
+    ctx.es_set_fusion(0)
+    JUg, Jg, xg = to_dev(JU, torch), to_dev(J, torch), to_dev(x, torch)
+    ctx.es_rk_step(JUg, Jg, xg, to_dev(xdot, torch), torch.tensor([dt], dtype=torch.float64, device="cuda"))
+    JUo, Jo, xo = o.rk_step(JU, J, x, xdot, dt)
+    e = fieldwise(JUg.cpu().numpy(), JUo, N=N, d=2) + [rel_max_err(Jg.cpu().numpy(), Jo), rel_max_err(xg.cpu().numpy(), xo)]
+    assert max(e) <= TOL_FP64, e
+
+
+def test_fused_autotune_and_errors():
+    """es_autotune on a 2D context also times the fused launch and reports a valid choice;
+    results after tuning are unchanged; a fused shape on a 3D context or out of range is
+    refused with ES_ERR_ARG."""
+    torch = need_gpu()
+    from paper_2202_07989_gb300 import es
+    pb, JU, J, x, xdot = case(2, 2, (70, 37), "mixed", es=True, seed=41, jump=True)
+    ctx = _ctx(pb, 1)
+    G = [to_dev(t, torch) for t in (JU, J, x, xdot)]
+    ref = ctx.es_rhs(*G)
+    ctx.es_autotune(*G, reps=2)
+    sh, TX, TY, grid, ms = ctx.es_get_fusion()
+    assert -1 <= sh < NFSHAPE and ms > 0
+    if sh >= 0:
+        assert (TX + 1) * TY <= 256 and (TY + 1) * TX <= 256 and grid > 0
+    assert _same(ctx.es_rhs(*G), ref)
+    for bad in (-2, NFSHAPE):
+        with pytest.raises(es.EsError):
+            ctx.es_set_fusion(bad)
+    pb3, *_ = case(3, 1, (12, 11, 10), "periodic", seed=1)
+    c3 = _ctx(pb3, 1)
+    with pytest.raises(es.EsError):
+        c3.es_set_fusion(0)
+    c3.es_set_fusion(-1)
+    assert c3.es_get_fusion()[0] == -1
+    assert np.isfinite(ref[0].cpu().numpy()).all()
