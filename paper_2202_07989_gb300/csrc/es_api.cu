@@ -466,7 +466,7 @@ void launch_mesh(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStream
     launch_metrics(c, Q, tab, st, true);     // also resets the reduction slots
     ProfScope ps(c, PC_MESH, st);
     int gc = node_grid(c, c->n_cell);
-    launch_cfl_grad(c->mixed, gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
+    launch_cfl_grad(c->mixed, c->d, c->N, gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
     if (c->hI[0].fixed) {
         // fixed mesh: Delta t only; xdot = 0 (the metrics above carry no VCL part)
         launch_xdot(c->mixed, gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS);

@@ -42,18 +42,18 @@ __host__ __device__ constexpr size_t smem_flux2d()
 // Phases 2 (distinct pairs) and 3 (interfaces) of direction K (0: along the rows, 1: along
 // the columns).  Row pairs and interfaces are numbered line by line; column pairs and
 // interfaces position by position across the TX columns, so that consecutive threads read
-// consecutive nodes in both directions.
-template <int K, int NS, typename R, int TX, int TY, int WK>
-__device__ __forceinline__ void flux2d_pairs(const Inst& I, int i0, int j0, const R* nr, R* pf, R* cm)
+// consecutive nodes in both directions.  The kernel inlines both directions (constant K);
+// a single copy looping over a run-time K measured no faster.
+template <int NS, typename R, int TX, int TY, int WK>
+__device__ __forceinline__ void flux2d_pairs(const int K, const Inst& I, int i0, int j0, const R* nr, R* pf, R* cm)
 {
     using Y = Lay<2, NS>;
     using T = Tile2<TX, TY>;
     constexpr int NN = T::NN, NP = T::NP, NI = T::NI, RW = T::RW;
-    constexpr int S = K ? TY : TX, NPL = 3 * S + 6, NPK = K ? T::NP1 : T::NP0;
-    constexpr int MR = K ? Y::NF : Y::MR;
+    const int S = K ? TY : TX, NPK = K ? T::NP1 : T::NP0, MR = K ? Y::NF : Y::MR;
     const int nk = I.n[K], na = I.n[1 - K], s0 = K ? j0 : i0, a0 = K ? i0 : j0;
     for (int t = threadIdx.x; t < NPK; t += blockDim.x) {
-        const int w = K ? t % TX : t / NPL, r_ = K ? t / TX : t % NPL;
+        const int w = K ? t % TX : t / T::NPL0, r_ = K ? t / TX : t % T::NPL0;
         int m, Ln;
         if (r_ < S + 1) { m = 1; Ln = r_ + 2; }
         else if (r_ < 2 * S + 3) { m = 2; Ln = r_ - (S + 1) + 1; }
@@ -65,31 +65,42 @@ __device__ __forceinline__ void flux2d_pairs(const Inst& I, int i0, int j0, cons
     }
 }
 
-template <int K, int NS, typename R, int TX, int TY, int WK>
-__device__ __forceinline__ void flux2d_ifaces(const Inst& I, int i0, int j0, const R* nr, const double* mtk, const R* pf,
-                                              const R* cm, R* fl, double* gt)
+template <int NS, typename R, int TX, int TY, int WK>
+__device__ __forceinline__ void flux2d_ifaces(const int K, const Inst& I, int i0, int j0, const R* nr, const double* mtk,
+                                              const R* pf, const R* cm, R* fl, double* gt)
 {
     using Y = Lay<2, NS>;
     using T = Tile2<TX, TY>;
     constexpr int NN = T::NN, NP = T::NP, NI = T::NI, RW = T::RW;
-    constexpr int S = K ? TY : TX, NPL = 3 * S + 6, NIK = K ? T::NI1 : T::NI0;
-    constexpr int MR = K ? Y::NF : Y::MR;
+    const int S = K ? TY : TX, NIK = K ? T::NI1 : T::NI0, MR = K ? Y::NF : Y::MR;
     const int nk = I.n[K], na = I.n[1 - K], s0 = K ? j0 : i0, a0 = K ? i0 : j0;
+    // strides: nodes along the line, J xi_k/t along the line, pairs of one kind along the line
+    const int ns = K ? RW : 1, ms = K ? TX : 1, ps = K ? TX : 1;
     for (int f = threadIdx.x; f < NIK; f += blockDim.x) {
-        const int w = K ? f % TX : f / (S + 1), s = K ? f / TX : f % (S + 1);
+        const int w = K ? f % TX : f / (TX + 1), s = K ? f / TX : f % (TX + 1);
         const int gi = s0 - 1 + s;     // interface gi + 1/2
         if (a0 + w >= na || gi > nk - 1) continue;
-        if constexpr (K == 0) {
-            const int base = (w + 3) * RW + s;    // node gi - 2 of row w
-            const int p = w * NPL + s;
-            iface_flux<2, NS, R, WK>(I, nr + base, NN, 1, MR, mtk + w * RW + s, 1, pf, NP, p, p + (S + 1), p + (2 * S + 3), 1,
-                                     cm, NI, f, fl, gt);
-        } else {
-            const int base = s * RW + (w + 3);    // node gi - 2 of column w
-            const int p = s * TX + w;
-            iface_flux<2, NS, R, WK>(I, nr + base, NN, RW, MR, mtk + s * TX + w, TX, pf, NP, p, p + (S + 1) * TX,
-                                     p + (2 * S + 3) * TX, TX, cm, NI, f, fl, gt);
-        }
+        const int base = K ? s * RW + (w + 3) : (w + 3) * RW + s;    // node gi - 2 of line w
+        const int mb = K ? s * TX + w : w * RW + s;
+        const int p = K ? s * TX + w : w * T::NPL0 + s;
+        iface_flux<2, NS, R, WK>(I, nr + base, NN, ns, MR, mtk + mb, ms, pf, NP, p, p + (S + 1) * ps, p + (2 * S + 3) * ps,
+                                 ps, cm, NI, f, fl, gt);
+    }
+}
+
+// divergence of direction 1 at the tile's output nodes into acc (FP64)
+template <int NS, typename R, int TX, int TY>
+__device__ __forceinline__ void flux2d_div1(const Inst& I, int i0, int j0, const R* fl, const double* gt, double* acc)
+{
+    constexpr int NC = NS + 3, NI = Tile2<TX, TY>::NI, NO = TX * TY;
+    for (int t = threadIdx.x; t < NO; t += blockDim.x) {
+        const int il = t % TX, jl = t / TX;
+        if (i0 + il >= I.n[0] || j0 + jl >= I.n[1]) continue;
+        const int fr = jl * (TX + 1) + il + 1;
+        double r[NC + 1];
+        node_div<NC, R>(I, fl, NI, gt, fr, fr - 1, I.inv_dxi[0], r);
+#pragma unroll
+        for (int q = 0; q <= NC; ++q) acc[q * NO + t] = r[q];
     }
 }
 
@@ -172,24 +183,16 @@ __global__ void __launch_bounds__(FLUX_TPB, (sizeof(R) == 4 ? 3 : 1)) flux2d_ker
         __syncthreads();
 
         // ---------------- direction 1: pairs, interfaces ----------------
-        flux2d_pairs<0, NS, R, TX, TY, WK>(I, i0, j0, nr, pf, cm);
+        flux2d_pairs<NS, R, TX, TY, WK>(0, I, i0, j0, nr, pf, cm);
         __syncthreads();
-        flux2d_ifaces<0, NS, R, TX, TY, WK>(I, i0, j0, nr, mt0, pf, cm, fl, gt);
+        flux2d_ifaces<NS, R, TX, TY, WK>(0, I, i0, j0, nr, mt0, pf, cm, fl, gt);
         __syncthreads();
 
-        // ---------------- divergence of direction 1; pairs of direction 2 ----------------
-        for (int t = threadIdx.x; t < NO; t += blockDim.x) {
-            const int il = t % TX, jl = t / TX;
-            if (i0 + il >= n0 || j0 + jl >= n1) continue;
-            const int fr = jl * (TX + 1) + il + 1;
-            double r[NC + 1];
-            node_div<NC, R>(I, fl, NI, gt, fr, fr - 1, I.inv_dxi[0], r);
-#pragma unroll
-            for (int q = 0; q <= NC; ++q) acc[q * NO + t] = r[q];
-        }
-        flux2d_pairs<1, NS, R, TX, TY, WK>(I, i0, j0, nr, pf, cm);
+        // ---------------- divergence of direction 1; direction 2: pairs, interfaces ----------------
+        flux2d_div1<NS, R, TX, TY>(I, i0, j0, fl, gt, acc);
+        flux2d_pairs<NS, R, TX, TY, WK>(1, I, i0, j0, nr, pf, cm);
         __syncthreads();
-        flux2d_ifaces<1, NS, R, TX, TY, WK>(I, i0, j0, nr, mt1, pf, cm, fl, gt);
+        flux2d_ifaces<NS, R, TX, TY, WK>(1, I, i0, j0, nr, mt1, pf, cm, fl, gt);
         __syncthreads();
 
         // ---------------- divergence of direction 2 and output ----------------

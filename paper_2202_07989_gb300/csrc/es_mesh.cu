@@ -282,6 +282,171 @@ __global__ void __launch_bounds__(NODE_TPB) cfl_grad_kernel(const Inst* __restri
     }
 }
 
+// ordered integer key of a non-negative value (the IEEE order of non-negative floats and
+// doubles is the order of their bit patterns), for exact max reductions on the integer ALU
+__device__ __forceinline__ unsigned int max_key(float v) { return __float_as_uint(v); }
+__device__ __forceinline__ unsigned long long max_key(double v) { return (unsigned long long)__double_as_longlong(v); }
+__device__ __forceinline__ unsigned int shfl_max(unsigned int k, int o) { return max(k, __shfl_xor_sync(0xffffffffu, k, o)); }
+__device__ __forceinline__ unsigned long long shfl_max(unsigned long long k, int o)
+{
+    return max(k, (unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)k, o));
+}
+__device__ __forceinline__ double key_value(unsigned int k) { return to_d(__uint_as_float(k)); }
+__device__ __forceinline__ double key_value(unsigned long long k) { return __longlong_as_double((long long)k); }
+
+// sigma_t of a 2D instance with NS species (the same arithmetic, with the field indices known)
+template <typename R, int NS>
+__device__ __forceinline__ R sigma2d(const Inst& I, int kind, const R* U)
+{
+    const R rho = NS == 2 ? U[0] + U[1] : U[0];
+    switch (kind) {
+    case SIG_RHO1: return U[0];
+    case SIG_RHO2: return NS == 2 ? U[1] : R(0);
+    case SIG_Y2: return NS == 2 ? U[1] / rho : R(0);
+    case SIG_V1: return U[NS] / rho;
+    case SIG_P: {
+        R cvr = R(0), rr = R(0), v2 = R(0);
+#pragma unroll
+        for (int l = 0; l < NS; ++l) { cvr += to_r<R>(I.cv[l]) * U[l]; rr += to_r<R>(I.Rs[l]) * U[l]; }
+#pragma unroll
+        for (int m = 0; m < 2; ++m) { R v = U[NS + m] / rho; v2 += v * v; }
+        R T = (U[NS + 2] - R(0.5) * rho * v2 - to_r<R>(I.pinf_tot)) / cvr;
+        return rr * T - to_r<R>(I.pinf_tot);
+    }
+    default: return rho;
+    }
+}
+
+// cfl_grad_kernel for 2D instances with NS species: the same terms in the same arithmetic.
+// The halo pass loads each node's state once: it stores sigma_s and, at the tile's own
+// nodes, forms the CFL spectral-radius sum there.  The gradient pass then reads only shared
+// memory, and one block reduction (integer keys of the non-negative maxima) ends the tile.
+template <typename R, int NS>
+__global__ void __launch_bounds__(NODE_TPB) cfl_grad2d_kernel(const Inst* __restrict__ insts, StagePtrs single,
+                                                               const StagePtrs* __restrict__ table,
+                                                               const int2* __restrict__ work, int nwork,
+                                                               const Scratch* __restrict__ scr)
+{
+    pdl_entry();
+    using K = decltype(max_key(R(0)));
+    constexpr int NC = NS + 3, TX = NT_X + 2, TY = NT_Y + 2, NW = NODE_TPB / 32;
+    __shared__ R ssig[4][TY][TX];
+    __shared__ K sred[5][NW];
+    const int lane = (int)threadIdx.x & 31, wid = (int)threadIdx.x >> 5;
+    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+        const int2 it = work[wi];
+        const Inst& I = insts[it.x];
+        ES_PTRS(P);
+        const Scratch& Sc = scr[it.x];
+        const int n0 = I.n[0], n1 = I.n[1], ns = I.n_sigma;
+        const int ntx = (n0 + NT_X - 1) / NT_X;
+        const int b0 = (it.y % ntx) * NT_X - 1, b1 = (it.y / ntx) * NT_Y - 1;
+        K kmax[5] = { 0, 0, 0, 0, 0 };    // CFL sum, then the monitor terms
+        __syncthreads();    // the previous tile's readers are done
+        for (int q = threadIdx.x; q < TX * TY; q += NODE_TPB) {
+            const int a = q % TX, b = q / TX;
+            const int g0 = b0 + a, g1 = b1 + b;
+            // a node outside the domain in both directions (a tile corner, or on a ragged tile
+            // an edge node beyond the last row or column) is no neighbour of any tile node
+            const bool out0 = g0 < 0 || g0 >= n0, out1 = g1 < 0 || g1 >= n1;
+            if ((out0 && out1) || g0 > n0 || g1 > n1) continue;
+            const bool own = a >= 1 && a <= NT_X && b >= 1 && b <= NT_Y && !out0 && !out1;
+            if (ns == 0 && !own) continue;
+            // the point state with the ghost map of the one direction the node lies outside:
+            // the arithmetic of load_U_t, with the field count known
+            R U[MAXC];
+            {
+                int gi0 = g0, gi1 = g1, kk = 0, side = 0, tmap = 0;
+                if (out0) tmap = map_line(I, 0, g0, gi0, side);
+                else if (out1) { kk = 1; tmap = map_line(I, 1, g1, gi1, side); }
+                if (tmap == 2) {
+#pragma unroll
+                    for (int f = 0; f < NC; ++f) U[f] = to_r<R>(I.inflow[kk][side][f]);
+                } else {
+                    const long long id = lin(I, gi0, gi1, 0);
+                    const R inv = R(1) / to_r<R>(P.J[id]);
+#pragma unroll
+                    for (int f = 0; f < NC; ++f) U[f] = to_r<R>(P.JU[f * I.ncell + id]) * inv;
+                    if (tmap == 1) U[NS + kk] = -U[NS + kk];
+                }
+            }
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+                if (s < ns) ssig[s][b][a] = sigma2d<R, NS>(I, I.sigma[s], U);
+            if (!own) continue;
+            // Eq. (cfl) at node (g0, g1) with the metrics of x^n
+            const R rho = U[0] + (NS == 2 ? U[1] : R(0));
+            R v[2], v2 = R(0), cvr = R(0), ar = R(0), gm = R(0);
+#pragma unroll
+            for (int m = 0; m < 2; ++m) { v[m] = U[NS + m] / rho; v2 += v[m] * v[m]; }
+#pragma unroll
+            for (int l = 0; l < NS; ++l) {
+                ar += Cst<R>::Rs(I, l) * U[l];          // (Gamma_l - 1) c_v,l rho_l
+                gm += Cst<R>::cvG(I, l) * U[l];         // Gamma_l c_v,l rho_l
+                cvr += Cst<R>::cv(I, l) * U[l];
+            }
+            const R T = (U[NC - 1] - R(0.5) * rho * v2 - Cst<R>::pinf(I)) / cvr;
+            const R c = sqrt((ar / rho) * (gm / cvr) * T);
+            const long long p = lin(I, g0, g1, 0), pid = plin(I, g0, g1, 0);
+            const R Jp = to_r<R>(P.J[p]);
+            R sr = R(0);
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                R L2 = R(0), vn = R(0);
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const R mk = to_r<R>(Sc.M[(long long)(k * 3 + 1 + j) * I.npad + pid]);
+                    L2 += mk * mk;
+                    vn += mk * v[j];
+                }
+                sr += (fabs(vn) + c * sqrt(L2)) / Jp * inv_dxi_r<R>(I, k);
+            }
+            if (!(sr >= R(0))) sr = R(0);
+            kmax[0] = max(kmax[0], max_key(sr));
+        }
+        __syncthreads();
+        // per term |grad_xi sigma| (squared sums) or the Laplacian (second differences)
+        {
+            const int lx = (int)threadIdx.x % NT_X, ly = (int)threadIdx.x / NT_X;
+            const int i0 = b0 + 1 + lx, i1 = b1 + 1 + ly;
+            if (i0 < n0 && i1 < n1) {
+                const long long p = lin(I, i0, i1, 0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (q >= ns) break;
+                    R gr = R(0), lp = R(0);
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        const R hk = R(0.5) * inv_dxi_r<R>(I, k);
+                        const R h2 = inv_dxi_r<R>(I, k) * inv_dxi_r<R>(I, k);
+                        const R sp = k == 0 ? ssig[q][ly + 1][lx + 2] : ssig[q][ly + 2][lx + 1];
+                        const R sm = k == 0 ? ssig[q][ly + 1][lx] : ssig[q][ly][lx + 1];
+                        const R gk = (sp - sm) * hk;
+                        gr += gk * gk;
+                        lp += (sp - R(2) * ssig[q][ly + 1][lx + 1] + sm) * h2;
+                    }
+                    R gq = I.sigma_op[q] == MON_LAP ? R(fabs(lp)) : R(sqrt(gr));
+                    grad_r<R>(Sc)[(long long)q * I.ncell + p] = gq;
+                    if (!(gq >= R(0))) gq = R(0);
+                    kmax[1 + q] = max(kmax[1 + q], max_key(gq));
+                }
+            }
+        }
+        // block maxima of the CFL sum and of each monitor term, then the instance maxima
+#pragma unroll
+        for (int r = 0; r < 5; ++r)
+            for (int o = 16; o > 0; o >>= 1) kmax[r] = shfl_max(kmax[r], o);
+        if (lane == 0)
+            for (int r = 0; r < 5; ++r) sred[r][wid] = kmax[r];
+        __syncthreads();
+        if ((int)threadIdx.x <= ns) {
+            K m = sred[threadIdx.x][0];
+            for (int w = 1; w < NW; ++w) m = max(m, sred[threadIdx.x][w]);
+            atomic_max_pos(&Sc.red[threadIdx.x], key_value(m));
+        }
+    }
+}
+
 // Eq. (monitor) at node p from the gradients and the reciprocal instance maxima (0 for a zero maximum)
 template <typename R>
 __device__ __forceinline__ R theta_at(const Inst& I, const Scratch& S, const R* inv, long long p)
@@ -1259,9 +1424,19 @@ void launch_filter(bool mixed, bool from_g, int grid, cudaStream_t st, const Ins
     }
 }
 
-void launch_cfl_grad(bool mixed, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
+void launch_cfl_grad(bool mixed, int d, int N, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
                      const StagePtrs* table, const int2* work, int nwork, const Scratch* scr)
 {
+    if (d == 2) {
+        if (mixed) {
+            if (N == 1) pdl_launch(cfl_grad2d_kernel<float, 1>, grid, NODE_TPB, 0, st, insts, single, table, work, nwork, scr);
+            else pdl_launch(cfl_grad2d_kernel<float, 2>, grid, NODE_TPB, 0, st, insts, single, table, work, nwork, scr);
+        } else {
+            if (N == 1) pdl_launch(cfl_grad2d_kernel<double, 1>, grid, NODE_TPB, 0, st, insts, single, table, work, nwork, scr);
+            else pdl_launch(cfl_grad2d_kernel<double, 2>, grid, NODE_TPB, 0, st, insts, single, table, work, nwork, scr);
+        }
+        return;
+    }
     if (mixed) pdl_launch(cfl_grad_kernel<float>, grid, NODE_TPB, 0, st, insts, single, table, work, nwork, scr);
     else pdl_launch(cfl_grad_kernel<double>, grid, NODE_TPB, 0, st, insts, single, table, work, nwork, scr);
 }

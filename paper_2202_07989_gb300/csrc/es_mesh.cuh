@@ -5,7 +5,7 @@
 
 namespace es {
 
-void launch_cfl_grad(bool mixed, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
+void launch_cfl_grad(bool mixed, int d, int N, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
                      const StagePtrs* table, const int2* work, int nwork, const Scratch* scr);
 void launch_xdot(bool mixed, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
                  const StagePtrs* table, const int2* work, int nwork, const Scratch* scr);
