@@ -48,8 +48,10 @@ FP64_PEAK_TFLOPS = 1.25
 # launches of a stage in one ncu capture of the same tuned kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum, cold cache); the capture and its command are in profiles/
 FLUX_TRAFFIC_BYTES = 9.30e6
-# the same for one fused 2D stage launch (both directions); None until captured
-FLUX2D_TRAFFIC_BYTES = None
+# the same for one fused 2D stage launch (both directions): the mean of the three stage
+# launches of a step in one ncu capture (stage 1 10.51 MB; stages 2 and 3, which also read
+# M(xdot) and the step-start state, 19.58 MB each)
+FLUX2D_TRAFFIC_BYTES = 16.56e6
 
 
 def flux_flops_per_interface(D, NS, es=True):
@@ -91,7 +93,7 @@ def launches_per_step(pb, mixed=True, fused=False):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms during the timed region."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -659,8 +661,9 @@ def main_kernel_case(args):
         for k, sh in enumerate(int(v) for v in args.kernel_shapes.split(",")):
             r.ctx.es_set_tuning(k, sh, 0)
         tiles = r.ctx.es_get_tuning()
-    if args.kernel_fusion is not None:
-        r.ctx.es_set_fusion(args.kernel_fusion)
+    if args.kernel_fusion is not None or (args.kernel_shapes and pb.d == 2):
+        # fixed per-direction shapes in 2D mean the per-direction launches unless a fused shape is given
+        r.ctx.es_set_fusion(args.kernel_fusion if args.kernel_fusion is not None else -1)
         tiles = [tiles, r.ctx.es_get_fusion()]
     for _ in range(args.kernel_steps):
         r.step()

@@ -187,7 +187,8 @@ es_status es_set_tuning(es_ctx* ctx, int k, int shape, int grid);
  * and the two directions' divergences are summed in the same FP64 order, so
  * results are bitwise those of the per-direction launches.  es_autotune on a 2D
  * context also times each fused shape and keeps the fused launch when it beats
- * the sum of the best per-direction launches; a new context starts without it.
+ * the sum of the best per-direction launches.  A new 2D context starts with the
+ * fused launch in shape 0 (16 x 12 tiles, full occupancy).
  * es_get_fusion: fused shape index (-1: per-direction launches), TX, TY, grid
  * (CTAs) and the best fused time per launch the last es_autotune measured (0 if
  * none; set even when the per-direction launches won).  All pointers HOST, one

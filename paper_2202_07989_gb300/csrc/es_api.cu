@@ -610,6 +610,11 @@ es_status es_create_batch(const es_config* cfgs, int n_inst, es_ctx** out)
     else prepare_all<3, 2>(c->weno);
     prepare_mesh();
     for (int k = 0; k < c->d; ++k) c->flux_grid[k] = c->sms * flux_occ(c, c->flux_shape[k]);
+    // 2D contexts start with the fused stage launch in fused shape 0 (es_autotune may change it)
+    if (c->d == 2) {
+        c->fused_shape = 0;
+        c->fused_grid = c->sms * flux2d_occ(c, 0);
+    }
     cudaError_t e = cudaDeviceSynchronize();
     if (!ok || e != cudaSuccess || !c->w_pad || !c->w_cell || (c->d == 3 && (!c->w_ext || !c->w_xe))) {
         fprintf(stderr, "es_create: setup failed: %s\n", cudaGetErrorString(e));

@@ -332,7 +332,8 @@ __device__ __forceinline__ void pair_flux(const Inst& I, const R* nr, int NN, in
 // (stride ms).  The distinct pair fluxes (field stride NP) of (i, i+1) sit at p1, of
 // (i-1, i+1) and (i, i+2) at p2 and p2 + ps, of (i-2, i+1), (i-1, i+2) and (i, i+3) at
 // p3, p3 + ps and p3 + 2 ps; the centre-pair means cm (field stride NI) and the outputs,
-// the interface flux fl (field stride NI) and the FP64 GCL flux gt, at f.
+// the interface flux fl (field stride NI) and the FP64 GCL flux gt, at f.  Each output is
+// stored as soon as it is formed, which keeps registers free through the dissipation.
 template <int D, int NS, typename R, int WK>
 __device__ __forceinline__ void iface_flux(const Inst& I, const R* nb, int NN, int ns, int mr, const double* m64, int ms,
                                            const R* pf, int NP, int p1, int p2, int p3, int ps, const R* cm, int NI, int f,
@@ -342,15 +343,16 @@ __device__ __forceinline__ void iface_flux(const Inst& I, const R* nb, int NN, i
     constexpr int NC = Y::NC;
 #define NR(fld, j) nb[(fld) * NN + (j) * ns]
     const R a1 = R(alpha3(1)), a2 = R(alpha3(2)), a3 = R(alpha3(3));
-    R Fe[NC];
+    // the EC flux goes to its output slot at once; the dissipation is subtracted there at the end
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
         const R* pq = pf + q * NP;
-        Fe[q] = a1 * pq[p1] + a2 * (pq[p2] + pq[p2 + ps]) + a3 * (pq[p3] + pq[p3 + ps] + pq[p3 + 2 * ps]);
+        fl[q * NI + f] = a1 * pq[p1] + a2 * (pq[p2] + pq[p2 + ps]) + a3 * (pq[p3] + pq[p3 + ps] + pq[p3 + 2 * ps]);
     }
     // GCL flux of (J xi_k/t, J xi_k/x_j): stencil (1, -8, 37, 37, -8, 1)/60
     const double c0 = 0.5 * (alpha3(1) + alpha3(2) + alpha3(3)), c1 = 0.5 * (alpha3(2) + alpha3(3)), c2 = 0.5 * alpha3(3);
     const double Gt = c0 * (m64[2 * ms] + m64[3 * ms]) + c1 * (m64[ms] + m64[4 * ms]) + c2 * (m64[0] + m64[5 * ms]);
+    gt[f] = Gt;
     if (I.es) {
         R Gx[D], L2 = R(0);
 #pragma unroll
@@ -434,8 +436,10 @@ __device__ __forceinline__ void iface_flux(const Inst& I, const R* nb, int NN, i
         R Fd[NC];
 #pragma unroll
         for (int q = 0; q < NC; ++q) Fd[q] = R(0);
+        // the two acoustic columns first, so that their averages are dead for the others
 #pragma unroll
-        for (int col = 0; col < NC; ++col) {
+        for (int ci = 0; ci < NC; ++ci) {
+            const int col = ci == 0 ? 0 : (ci == 1 ? NC - 1 : ci - 1);
             // column col of R in the rotated frame
             R rc[NC];
 #pragma unroll
@@ -522,12 +526,9 @@ __device__ __forceinline__ void iface_flux(const Inst& I, const R* nb, int NN, i
             }
         }
 #pragma unroll
-        for (int q = 0; q < NC; ++q) Fe[q] -= R(0.5) * Fd[q];
+        for (int q = 0; q < NC; ++q) fl[q * NI + f] = fl[q * NI + f] - R(0.5) * Fd[q];
     }
 #undef NR
-#pragma unroll
-    for (int q = 0; q < NC; ++q) fl[q * NI + f] = Fe[q];
-    gt[f] = Gt;
 }
 
 // Phase 4 of one node along direction k: r[0..NC) = -(F_{i+1/2} - F_{i-1/2}) / dxi_k from

@@ -1,9 +1,10 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
 
-Sizes span several flux tiles with ragged tails (tiles are 63 x 4 nodes along
-direction 1 and 31 x 8 along directions 2 and 3).  FP64 path: relative max-norm
-error per field <= 1e-12.  Mixed path: FP32-level bounds, with the measured
-errors printed.
+Sizes span several flux tiles with ragged tails: 2D contexts run the fused stage
+launch (16 x 12 node tiles) unless a test turns it off; 3D contexts run the
+per-direction launches (62 x 4 nodes along direction 1, 30 x 8 along directions 2
+and 3).  FP64 path: relative max-norm error per field <= 1e-12.  Mixed path:
+FP32-level bounds, with the measured errors printed.
 """
 import numpy as np
 import pytest
@@ -215,6 +216,8 @@ def test_flux_tile_shapes_and_autotune_bitwise(d, N, form):
     torch = need_gpu()
     pb, JU, J, x, xdot = case(d, N, GRIDS[d], "mixed", es=True, seed=23, jump=True)
     ctx = _ctx(pb, form)
+    if d == 2:
+        ctx.es_set_fusion(-1)     # the per-direction launches (2D contexts start fused)
     G = [to_dev(t, torch) for t in (JU, J, x, xdot)]
     ref = ctx.es_rhs(*G)
     for shape in range(6):
