@@ -774,6 +774,26 @@ __global__ void __launch_bounds__(NODE_TPB) jacobi_y_kernel(const Inst* __restri
     }
 }
 
+// Slot q = threadIdx.x, threadIdx.x + NODE_TPB, ... of a W-wide region and its column and row
+// (a, b) = (q % W, q / W), stepped without a division per slot (W is a run-time width)
+struct SlotIter {
+    int q, a, b, da, db, W;
+    __device__ explicit SlotIter(int W_) : q((int)threadIdx.x), W(W_)
+    {
+        b = q / W;
+        a = q - b * W;
+        db = NODE_TPB / W;
+        da = NODE_TPB - db * W;
+    }
+    __device__ void next()
+    {
+        q += NODE_TPB;
+        a += da;
+        b += db;
+        if (a >= W) { a -= W; ++b; }
+    }
+};
+
 // Mixed form, 2D: the monitor, its F <= 4 filter passes and all H = mu <= 8 Jacobi sweeps
 // of jacobi_y_kernel in one launch (temporal blocking).  A block stages the region of its
 // 32 x 8 node tile plus a halo of H + F nodes in shared memory: Theta (formed from the
@@ -814,14 +834,19 @@ __global__ void __launch_bounds__(NODE_TPB) jacobi_fused2d_kernel(const Inst* __
         const int r0 = (it.y % ntx) * NT_X - H, r1 = (it.y / ntx) * NT_Y - H;    // inner region origin
         const int o0 = r0 - Fp, o1 = r1 - Fp;                                     // outer region origin
         const long long n = I.ncell;
+        // whether the outer / inner region holds wall ghost nodes (tile-uniform: a region
+        // without them skips the ghost passes and their barriers)
+        const bool gh_out = (!per0 && (o0 < 0 || o0 + RXo > n0)) || (!per1 && (o1 < 0 || o1 + RYo > n1));
+        const bool gh_in = (!per0 && (r0 < 0 || r0 + RX > n0)) || (!per1 && (r1 < 0 || r1 + RY > n1));
         __syncthreads();
         // Theta on the outer region: Eq. (monitor) from the gradients at the mapped node (s_map)
         float inv[4] = { 0.0f, 0.0f, 0.0f, 0.0f };
         if (F >= 0)
             for (int q = 0; q < I.n_sigma; ++q) inv[q] = inv_max<float>(Sc, q);
         const float* th = reinterpret_cast<const float*>(theta_sel ? Sc.th1 : Sc.th0);
-        for (int q = threadIdx.x; q < NRo; q += NODE_TPB) {
-            const long long src = s_map(I, o0 + q % RXo, o1 + q / RXo, 0);
+        for (SlotIter sl(RXo); sl.q < NRo; sl.next()) {
+            const int q = sl.q;
+            const long long src = s_map(I, o0 + sl.a, o1 + sl.b, 0);
             ta[q] = F >= 0 ? theta_at<float>(I, Sc, inv, src) : th[src];
         }
         __syncthreads();
@@ -829,8 +854,8 @@ __global__ void __launch_bounds__(NODE_TPB) jacobi_fused2d_kernel(const Inst* __
         float* tc_ = ta;
         float* tn_ = tb;
         for (int f = 0; f < F; ++f) {
-            for (int q = threadIdx.x; q < NRo; q += NODE_TPB) {
-                const int a = q % RXo, b = q / RXo;
+            for (SlotIter sl(RXo); sl.q < NRo; sl.next()) {
+                const int q = sl.q, a = sl.a, b = sl.b;
                 const int g0 = o0 + a, g1 = o1 + b;
                 const bool ghost = (!per0 && (g0 < 0 || g0 >= n0)) || (!per1 && (g1 < 0 || g1 >= n1));
                 if (ghost || a == 0 || a == RXo - 1 || b == 0 || b == RYo - 1) continue;
@@ -845,8 +870,9 @@ __global__ void __launch_bounds__(NODE_TPB) jacobi_fused2d_kernel(const Inst* __
             }
             __syncthreads();
             // wall ghosts: copies of the boundary node
-            for (int q = threadIdx.x; q < NRo; q += NODE_TPB) {
-                const int a = q % RXo, b = q / RXo;
+            if (gh_out) {
+            for (SlotIter sl(RXo); sl.q < NRo; sl.next()) {
+                const int q = sl.q, a = sl.a, b = sl.b;
                 const int g0 = o0 + a, g1 = o1 + b;
                 const bool x0 = !per0 && (g0 < 0 || g0 >= n0), x1 = !per1 && (g1 < 0 || g1 >= n1);
                 if (!x0 && !x1) continue;
@@ -854,6 +880,7 @@ __global__ void __launch_bounds__(NODE_TPB) jacobi_fused2d_kernel(const Inst* __
                 tn_[q] = (sa >= 0 && sa < RXo && sb >= 0 && sb < RYo) ? tn_[sb * RXo + sa] : 1.0f;
             }
             __syncthreads();
+            }
             float* t = tc_;
             tc_ = tn_;
             tn_ = t;
@@ -862,8 +889,8 @@ __global__ void __launch_bounds__(NODE_TPB) jacobi_fused2d_kernel(const Inst* __
         // stage Theta, y = 0 and the + side spacings x^n_{i+e_k} - x^n_i of the in-domain nodes
         // (a periodic copy takes its wrapped node's, unshifted); the - side of a node whose
         // - neighbour is a wall ghost is formed here too, all others below
-        for (int q = threadIdx.x; q < NR; q += NODE_TPB) {
-            const int a = q % RX, b = q / RX;
+        for (SlotIter sl(RX); sl.q < NR; sl.next()) {
+            const int q = sl.q, a = sl.a, b = sl.b;
             const int g0 = r0 + a, g1 = r1 + b;
             ya[q] = ya[NR + q] = yb[q] = yb[NR + q] = 0.0f;
             const bool ghost = (!per0 && (g0 < 0 || g0 >= n0)) || (!per1 && (g1 < 0 || g1 >= n1));
@@ -893,8 +920,8 @@ __global__ void __launch_bounds__(NODE_TPB) jacobi_fused2d_kernel(const Inst* __
         }
         __syncthreads();
         // the remaining - sides: minus the + side of the - neighbour (the same pair of nodes)
-        for (int q = threadIdx.x; q < NR; q += NODE_TPB) {
-            const int a = q % RX, b = q / RX;
+        for (SlotIter sl(RX); sl.q < NR; sl.next()) {
+            const int q = sl.q, a = sl.a, b = sl.b;
             const int g0 = r0 + a, g1 = r1 + b;
             const bool ghost = (!per0 && (g0 < 0 || g0 >= n0)) || (!per1 && (g1 < 0 || g1 >= n1));
             if (ghost) continue;
@@ -912,8 +939,8 @@ __global__ void __launch_bounds__(NODE_TPB) jacobi_fused2d_kernel(const Inst* __
         float* yn = yb;
         for (int sw = 0; sw < H; ++sw) {
             // in-domain nodes: one sweep (neighbours outside the region leave a node invalid)
-            for (int q = threadIdx.x; q < NR; q += NODE_TPB) {
-                const int a = q % RX, b = q / RX;
+            for (SlotIter sl(RX); sl.q < NR; sl.next()) {
+                const int q = sl.q, a = sl.a, b = sl.b;
                 const int g0 = r0 + a, g1 = r1 + b;
                 const bool ghost = (!per0 && (g0 < 0 || g0 >= n0)) || (!per1 && (g1 < 0 || g1 >= n1));
                 if (ghost || a == 0 || a == RX - 1 || b == 0 || b == RY - 1) continue;
@@ -936,8 +963,9 @@ __global__ void __launch_bounds__(NODE_TPB) jacobi_fused2d_kernel(const Inst* __
             }
             __syncthreads();
             // wall ghosts: the mirror of their source node, the mirrored component negated
-            for (int q = threadIdx.x; q < NR; q += NODE_TPB) {
-                const int a = q % RX, b = q / RX;
+            if (gh_in) {
+            for (SlotIter sl(RX); sl.q < NR; sl.next()) {
+                const int q = sl.q, a = sl.a, b = sl.b;
                 const int g0 = r0 + a, g1 = r1 + b;
                 const bool o0 = !per0 && (g0 < 0 || g0 >= n0), o1 = !per1 && (g1 < 0 || g1 >= n1);
                 if (!o0 && !o1) continue;
@@ -953,6 +981,7 @@ __global__ void __launch_bounds__(NODE_TPB) jacobi_fused2d_kernel(const Inst* __
                 yn[NR + q] = o1 ? -v1 : v1;
             }
             __syncthreads();
+            }
             float* t = yc;
             yc = yn;
             yn = t;
