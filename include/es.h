@@ -275,6 +275,14 @@ es_status es_profile_read(es_ctx* ctx, double* ms, long long* launches, int n_cl
  * exactly.  in, out32, out64: DEVICE arrays of n elements. */
 es_status es_check_conversions(const double* in, int n, float* out32, double* out64, void* stream);
 
+/* Self-check of the exact mean {a} = a/2 + b/2 that the mixed form's log-mean
+ * small-jump branch (Sec. 3.3, the Ismail-Roe series) assembles with integer
+ * instructions: out[i] = a[i]/2 + b[i]/2 as a binary64 value.  Exact for
+ * positive normal a, b whose binary32 exponents differ by at most 7 (the branch
+ * has |b - a| < (a + b)/10); otherwise the binary64 sum of the binary32 halves.
+ * a, b: DEVICE arrays of n binary32 values; out: DEVICE array of n doubles. */
+es_status es_check_half_sums(const float* a, const float* b, int n, double* out, void* stream);
+
 /* Reads and clears the sticky device status (synchronises the stream):
  * *flags = bit 0 non-physical state, bit 1 timeout. */
 es_status es_poll_status(es_ctx* ctx, int* flags, void* stream);

@@ -1029,6 +1029,14 @@ es_status es_check_conversions(const double* in, int n, float* out32, double* ou
     return cudaGetLastError() == cudaSuccess ? ES_OK : ES_ERR_CUDA;
 }
 
+es_status es_check_half_sums(const float* a, const float* b, int n, double* out, void* stream)
+{
+    if (!a || !b || !out || n < 0) return ES_ERR_ARG;
+    if (n == 0) return ES_OK;
+    half_sum_check_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(a, b, n, out);
+    return cudaGetLastError() == cudaSuccess ? ES_OK : ES_ERR_CUDA;
+}
+
 es_status es_profile(es_ctx* c, int enable)
 {
     if (!c) return ES_ERR_ARG;

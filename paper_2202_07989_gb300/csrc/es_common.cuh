@@ -377,6 +377,25 @@ __device__ __forceinline__ float to_r<float>(double x) { return f64_to_f32(x); }
 __device__ __forceinline__ double to_d(double x) { return x; }
 __device__ __forceinline__ double to_d(float x) { return f32_to_f64(x); }
 
+// {a} = a/2 + b/2 of two positive binary32 values as the exact binary64 value, built with
+// integer instructions.  For normal a, b (biased exponents >= 2) whose exponents differ by
+// at most 7, the sum of the significands aligned to the smaller exponent has at most 32
+// bits, so a/2 + b/2 = M 2^(e - 151) exactly; M is placed in the binary64 fields directly.
+// Otherwise the value is the binary64 sum of the halves, as the FP64 pipe forms it.
+__device__ __forceinline__ double half_sum_exact(float a, float b)
+{
+    const unsigned int ua = __float_as_uint(a), ub = __float_as_uint(b);
+    const int ea = (int)(ua >> 23), eb = (int)(ub >> 23);
+    const int e = min(ea, eb), dl = max(ea, eb) - e;
+    if (e < 2 || dl > 7 || max(ea, eb) > 254) return f32_to_f64(0.5f * a) + f32_to_f64(0.5f * b);
+    const unsigned int ma = (ua & 0x7fffffu) | 0x800000u, mb = (ub & 0x7fffffu) | 0x800000u;
+    const unsigned int M = (ma << (ea - e)) + (mb << (eb - e));
+    const int k = 31 - __clz((int)M);     // the leading one of M; its bit carries into the exponent
+    const unsigned long long bits =
+        ((unsigned long long)(k + e + 871) << 52) + ((unsigned long long)M << (52 - k));
+    return __longlong_as_double((long long)bits);
+}
+
 // bounded reductions of non-negative doubles: the IEEE order of non-negative
 // doubles is the order of their bit patterns
 __device__ inline void atomic_max_pos(double* a, double v)

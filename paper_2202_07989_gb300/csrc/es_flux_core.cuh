@@ -65,11 +65,13 @@ struct Ar<float> {
     static __device__ __forceinline__ float sq(float x) { return sqrtf(x); }
     static __device__ __forceinline__ float ab(float x) { return fabsf(x); }
     // small jumps ((b-a)/(b+a))^2 < 1e-2: {a}^ln = {a} (1 - delta(u)), the mean {a}
-    // and the correction formed in FP64; delta is the series of 1 - f/artanh(f)
+    // and the correction formed in FP64; delta is the series of 1 - f/artanh(f).  {a} is
+    // exact in binary64 and is assembled with integer instructions, so the FP64 pipe runs
+    // only the fused multiply-add (a, b > 0 here: |b - a| < (a + b)/10)
     static __device__ __forceinline__ double small_branch(float a, float b, float u)
     {
         float del = u * (1.f / 3.f + u * (4.f / 45.f + u * (44.f / 945.f + u * (428.f / 14175.f))));
-        double hs = f32_to_f64(0.5f * a) + f32_to_f64(0.5f * b);   // {a}, exact
+        const double hs = half_sum_exact(a, b);
         return fma(-hs, f32_to_f64(del), hs);
     }
     static __device__ __forceinline__ float lmean(float a, float b, float la, float lb)

@@ -286,4 +286,12 @@ __global__ void conversion_check_kernel(const double* __restrict__ in, int n, fl
     o64[i] = f32_to_f64(f);
 }
 
+__global__ void half_sum_check_kernel(const float* __restrict__ a, const float* __restrict__ b, int n,
+                                      double* __restrict__ out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] = half_sum_exact(a[i], b[i]);
+}
+
 }  // namespace es

@@ -79,6 +79,7 @@ def lib():
             "es_poll_status": (C.c_int, [vp, ip, vp]),
             "es_profile": (C.c_int, [vp, C.c_int]),
             "es_check_conversions": (C.c_int, [dp, C.c_int, dp, dp, vp]),
+            "es_check_half_sums": (C.c_int, [dp, dp, C.c_int, dp, vp]),
             "es_entropy_production_noalloc": (C.c_int, [C.POINTER(EsConfig), dp, dp, dp, dp, dp, vp]),
             "es_profile_read": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.c_int]),
         }
@@ -351,6 +352,22 @@ def es_check_conversions(x: torch.Tensor):
     if st != 0:
         raise EsError("es_check_conversions: %s" % ES_STATUS.get(st, st))
     return o32, o64
+
+
+def es_check_half_sums(a: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
+    """a/2 + b/2 in binary64 of two float32 CUDA tensors through the library's integer-built
+    exact mean (the log-mean small-jump branch of the mixed form)."""
+    for t, nm in ((a, "a"), (b, "b")):
+        if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+            raise EsError("%s must be a contiguous float32 CUDA tensor" % nm)
+    if a.shape != b.shape:
+        raise EsError("a and b must have the same shape")
+    out = torch.empty(a.shape, dtype=torch.float64, device=a.device)
+    st = lib().es_check_half_sums(C.c_void_p(a.data_ptr()), C.c_void_p(b.data_ptr()), a.numel(),
+                                  C.c_void_p(out.data_ptr()), _stream())
+    if st != 0:
+        raise EsError("es_check_half_sums: %s" % ES_STATUS.get(st, st))
+    return out
 
 
 # module-level aliases with the C names

@@ -468,6 +468,40 @@ def test_nonphysical_state_is_reported():
     assert ctx.es_poll_status() == 0
 
 
+def test_integer_built_half_sum_is_exact():
+    """The exact mean {a} = a/2 + b/2 that the mixed log-mean small branch assembles with
+    integer instructions equals the binary64 value bit for bit: random pairs within 10% of
+    each other across the whole exponent range, pairs straddling every power of two, equal
+    pairs, and pairs outside the precondition (exponents 7+ apart, the smallest normal binade,
+    subnormals), which take the binary64 sum of the binary32 halves."""
+    torch = need_gpu()
+    from paper_2202_07989_gb300 import es
+    rng = np.random.default_rng(43)
+    n = 400000
+    a = rng.uniform(1.0, 2.0, n) * np.exp2(rng.integers(-124, 126, n))
+    b = a * rng.uniform(0.82, 1.22, n)
+    p2 = np.exp2(np.arange(-124, 126)).repeat(8)
+    edge_a = p2 * (1.0 - rng.uniform(0, 0.05, p2.size))
+    edge_b = p2 * (1.0 + rng.uniform(0, 0.05, p2.size))
+    far_a = rng.uniform(1.0, 2.0, 2000)
+    far_b = far_a * np.exp2(rng.integers(8, 40, 2000))
+    tiny = np.concatenate([rng.uniform(1.0, 2.0, 2000) * 2.0 ** -126, rng.uniform(0.0, 1.0, 2000) * 2.0 ** -126])
+    A = np.concatenate([a, edge_a, edge_b, a, far_a, tiny, tiny[::-1]]).astype(np.float32)
+    B = np.concatenate([b, edge_b, edge_a, a, far_b, tiny[::-1], tiny * 1.01]).astype(np.float32)
+    ok = np.isfinite(B) & (B < 3.0e38)
+    A, B = A[ok], B[ok]
+    at, bt = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    got = es.es_check_half_sums(at, bt)
+    exact = (at.double() + bt.double()) * 0.5                      # exact: at most 53 bits
+    halves = (at * 0.5).double() + (bt * 0.5).double()
+    ea = np.frexp(A)[1] + 126
+    eb = np.frexp(B)[1] + 126
+    pre = torch.from_numpy((np.minimum(ea, eb) >= 2) & (np.abs(ea - eb) <= 7) & (A > 0) & (B > 0)).cuda()
+    assert int(pre.sum()) > 400000 and int((~pre).sum()) > 4000
+    assert torch.equal(got[pre].view(torch.int64), exact[pre].view(torch.int64))
+    assert torch.equal(got[~pre].view(torch.int64), halves[~pre].view(torch.int64))
+
+
 def test_integer_pipe_conversions_match_hardware():
     """The mixed form's integer-instruction binary64 -> binary32 rounding equals the hardware
     conversion bit for bit (outside the flushed range below 2^-126), and widening is exact."""
