@@ -515,7 +515,7 @@ def main_ours(args):
         te = time.perf_counter() - t0
         nb = (pb.nc + 1 + pb.d) * pb.ncell * 8
         e2e = {"value": pb.ncell * 3 * ke / te, "unit": UNIT, "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb + 8,
-               "steps": ke, "call": "es_run_host (host buffers, 1 step per call)"}
+               "steps": ke, "call": "es_run_host (host buffers, 1 step per call; the library replays its CUDA graph of a step)"}
 
     # roofline of the dominant kernel (flux + divergence + RK stage) in the headline form:
     # the flops of every interface of a step over the time of the step's flux launches

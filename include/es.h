@@ -19,7 +19,8 @@
  * Ownership: the caller owns every state, input and output buffer; pointers
  * are DEVICE pointers unless a call says HOST.  A context owns only scratch it
  * allocates in es_create / es_create_batch and frees in es_destroy; no call
- * after creation allocates device memory, except the first es_run_host and
+ * after creation allocates device memory, except es_run_host (its buffers on
+ * the first call; its step graph on the first call after a tuning change) and
  * es_profile(ctx, 1) on a context.
  *
  * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
@@ -253,7 +254,12 @@ es_status es_step_batch(es_ctx* ctx, void* stream);
  * runs `steps` times mesh_redistribute (CFL Delta t, or dt_fixed > 0) + an
  * SSP-RK3 step, copies (JU, J, x) back and adds the elapsed time to *t.
  * Synchronous.  Uses device buffers owned by the context, allocated by the
- * first call. */
+ * first call (with one pinned host word for the elapsed time); one
+ * cudaMemcpyAsync per buffer and direction (asynchronous when the host buffers
+ * are pinned).  Each step replays a CUDA graph of es_step on those buffers,
+ * captured on a private stream by the first call and again after es_autotune,
+ * es_set_tuning, es_set_fusion or a new dt_fixed; with es_profile on, the steps
+ * are launched one kernel at a time instead.  ES_ERR_ARG during stream capture. */
 es_status es_run_host(es_ctx* ctx, double* JU, double* J, double* x, int steps, double dt_fixed, double* t,
                       void* stream);
 

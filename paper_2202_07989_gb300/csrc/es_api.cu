@@ -41,8 +41,13 @@ struct es_ctx {
     StagePtrs* tab_mesh = nullptr;
     StagePtrs* tab_stage[3] = { nullptr, nullptr, nullptr };
     bool bound = false;
-    // device buffers of es_run_host
+    // device buffers of es_run_host, and its CUDA graph of one step on them (captured on a
+    // private stream; rebuilt after a change of tuning or of dt_fixed)
     double *hJU = nullptr, *hJ = nullptr, *hx = nullptr, *hxd = nullptr, *hdt = nullptr, *htacc = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t run_exec = nullptr;
+    double run_dtf = 0.0;
+    double* tacc_pinned = nullptr;     // pinned host word for the elapsed time
     int sms = 152;
     // flux launch configuration per direction (defaults, or the autotuner's choice)
     int flux_shape[3] = { SHAPE_DEFAULT_K0, SHAPE_DEFAULT_KN, SHAPE_DEFAULT_KN };
@@ -84,6 +89,13 @@ es_status cuda_check(es_ctx* c, const char* where)
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(c, ES_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
     return ES_OK;
+}
+
+// the step graph of es_run_host bakes in the launch configuration: drop it when that changes
+void drop_run_graph(es_ctx* c)
+{
+    if (c->run_exec) cudaGraphExecDestroy(c->run_exec);
+    c->run_exec = nullptr;
 }
 
 std::string check_cfg(const es_config& g)
@@ -507,6 +519,20 @@ void launch_step(es_ctx* c, const StagePtrs& mesh, const StagePtrs* tab_mesh, co
 
 __global__ void time_acc_kernel(double* t, const double* dt_dtau) { *t += dt_dtau[0]; }
 
+// copies of (JU, J, x) between the caller's host buffers and the context's device buffers
+// (one SM-driven copy kernel over mapped pinned memory measured no faster than these)
+void copy_state(es_ctx* c, double* JU, double* J, double* x, bool to_device, cudaStream_t st)
+{
+    const Inst& I = c->hI[0];
+    const long long n = I.ncell;
+    double* host[3] = { JU, J, x };
+    double* dev[3] = { c->hJU, c->hJ, c->hx };
+    const long long cnt[3] = { I.nc * n, n, I.d * n };
+    for (int k = 0; k < 3; ++k)
+        cudaMemcpyAsync(to_device ? dev[k] : host[k], to_device ? host[k] : dev[k], sizeof(double) * cnt[k],
+                        to_device ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost, st);
+}
+
 }  // namespace
 
 extern "C" {
@@ -630,6 +656,9 @@ es_status es_create(const es_config* cfg, es_ctx** out) { return es_create_batch
 void es_destroy(es_ctx* c)
 {
     if (!c) return;
+    drop_run_graph(c);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->tacc_pinned) cudaFreeHost(c->tacc_pinned);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     for (void* p : c->allocs) cudaFree(p);
     delete c;
@@ -842,27 +871,53 @@ es_status es_run_host(es_ctx* c, double* JU, double* J, double* x, int steps, do
     if (!c->hJU) {
         bool ok = dalloc(c, (void**)&c->hJU, sizeof(double) * I.nc * n) && dalloc(c, (void**)&c->hJ, sizeof(double) * n) &&
                   dalloc(c, (void**)&c->hx, sizeof(double) * I.d * n) && dalloc(c, (void**)&c->hxd, sizeof(double) * I.d * n) &&
-                  dalloc(c, (void**)&c->hdt, sizeof(double) * 2) && dalloc(c, (void**)&c->htacc, sizeof(double));
+                  dalloc(c, (void**)&c->hdt, sizeof(double) * 2) && dalloc(c, (void**)&c->htacc, sizeof(double)) &&
+                  cudaMallocHost((void**)&c->tacc_pinned, sizeof(double)) == cudaSuccess;
         if (!ok) return fail(c, ES_ERR_CUDA, "es_run_host: allocation failed");
     }
     cudaStream_t st = (cudaStream_t)stream;
-    cudaMemcpyAsync(c->hJU, JU, sizeof(double) * I.nc * n, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(c->hJ, J, sizeof(double) * n, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(c->hx, x, sizeof(double) * I.d * n, cudaMemcpyHostToDevice, st);
+    if (capturing(st)) return fail(c, ES_ERR_ARG, "es_run_host: not allowed during stream capture");
+    // one step (es_step + the time accumulation) as a CUDA graph, replayed per step; with
+    // es_profile on, the launches stay eager so that each is timed
+    const bool graph = !c->prof;
+    if (graph && (!c->run_exec || c->run_dtf != dt_fixed)) {
+        drop_run_graph(c);
+        if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+            return fail(c, ES_ERR_CUDA, "es_run_host: stream creation failed");
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return fail(c, ES_ERR_CUDA, "es_run_host: graph capture failed");
+        es_status r = es_step(c, c->hJU, c->hJ, c->hx, dt_fixed, c->hxd, c->hdt, c->cap_stream);
+        if (r == ES_OK) time_acc_kernel<<<1, 1, 0, c->cap_stream>>>(c->htacc, c->hdt);
+        cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+        if (r != ES_OK) {
+            if (g) cudaGraphDestroy(g);
+            return r;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&c->run_exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            c->run_exec = nullptr;
+            return fail(c, ES_ERR_CUDA, std::string("es_run_host: step graph: ") + cudaGetErrorString(e));
+        }
+        c->run_dtf = dt_fixed;
+    }
+    copy_state(c, JU, J, x, true, st);
     cudaMemsetAsync(c->htacc, 0, sizeof(double), st);
     for (int s = 0; s < steps; ++s) {
+        if (graph) {
+            if (cudaGraphLaunch(c->run_exec, st) != cudaSuccess) return fail(c, ES_ERR_CUDA, "es_run_host: graph launch failed");
+            continue;
+        }
         es_status r = es_step(c, c->hJU, c->hJ, c->hx, dt_fixed, c->hxd, c->hdt, stream);
         if (r != ES_OK) return r;
         time_acc_kernel<<<1, 1, 0, st>>>(c->htacc, c->hdt);
     }
-    double tacc = 0.0;
-    cudaMemcpyAsync(JU, c->hJU, sizeof(double) * I.nc * n, cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(J, c->hJ, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(x, c->hx, sizeof(double) * I.d * n, cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(&tacc, c->htacc, sizeof(double), cudaMemcpyDeviceToHost, st);
+    copy_state(c, JU, J, x, false, st);
+    cudaMemcpyAsync(c->tacc_pinned, c->htacc, sizeof(double), cudaMemcpyDeviceToHost, st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(c, ES_ERR_CUDA, std::string("es_run_host: ") + cudaGetErrorString(e));
-    if (t) *t += tacc;
+    if (t) *t += *c->tacc_pinned;
     return cuda_check(c, "es_run_host");
 }
 
@@ -931,6 +986,7 @@ es_status es_autotune(es_ctx* c, const double* JU, const double* J, const double
     // per-direction launches (both in MODE_WRITE); the faster form is kept
     c->fused_shape = -1;
     c->fused_ms = 0.f;
+    drop_run_graph(c);
     if (c->d == 2) {
         float best = 3.0e38f;
         for (int sh = 0; sh < NFSHAPE; ++sh) {
@@ -995,6 +1051,7 @@ es_status es_set_tuning(es_ctx* c, int k, int shape, int grid)
     c->flux_shape[k] = shape;
     c->flux_grid[k] = grid > 0 ? grid : c->sms * flux_occ(c, shape);
     c->flux_ms[k] = 0.f;
+    drop_run_graph(c);
     return ES_OK;
 }
 
@@ -1018,6 +1075,7 @@ es_status es_set_fusion(es_ctx* c, int shape, int grid)
     c->fused_shape = shape;
     c->fused_grid = shape >= 0 ? (grid > 0 ? grid : c->sms * flux2d_occ(c, shape)) : 0;
     c->fused_ms = 0.f;
+    drop_run_graph(c);
     return ES_OK;
 }
 

@@ -161,6 +161,17 @@ __global__ void __launch_bounds__(FLUX_TPB, (sizeof(R) == 4 ? 3 : 1)) flux2d_ker
                 }
             }
             node_fields<2, NS, R>(I, U, nr, NN, t, L.status);
+            // the stage update of x at an output node needs no residual: it runs here, where
+            // the FP64 pipe is idle, instead of in the FP64-bound epilogue
+            if (L.mode == MODE_RK && P.xo && use0 && use1) {
+                const long long id = lin(I, i, j, 0);
+                const double A = L.a, B = L.b, dt = *P.dt;
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    double bx = A != 0.0 ? A * P.x0[c * ncell + id] : 0.0;
+                    P.xo[c * ncell + id] = bx + B * (P.x[c * ncell + id] + dt * P.xdot[c * ncell + id]);
+                }
+            }
             const long long pid = plin(I, i, j, 0);
 #pragma unroll
             for (int kk = 0; kk < 2; ++kk) {
@@ -214,13 +225,6 @@ __global__ void __launch_bounds__(FLUX_TPB, (sizeof(R) == 4 ? 3 : 1)) flux2d_ker
                 double rj = acc[NC * NO + t] + r[NC];
                 double bj = A != 0.0 ? A * P.J0[id] : 0.0;
                 P.Jo[id] = bj + B * (P.J[id] + dt * rj);
-                if (P.xo) {    // null on a fixed mesh
-#pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        double bx = A != 0.0 ? A * P.x0[j * ncell + id] : 0.0;
-                        P.xo[j * ncell + id] = bx + B * (P.x[j * ncell + id] + dt * P.xdot[j * ncell + id]);
-                    }
-                }
             } else {
 #pragma unroll
                 for (int q = 0; q < NC; ++q) P.accU[q * ncell + id] = acc[q * NO + t] + r[q];

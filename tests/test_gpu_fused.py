@@ -144,3 +144,47 @@ def test_fused_autotune_and_errors():
     c3.es_set_fusion(-1)
     assert c3.es_get_fusion()[0] == -1
     assert np.isfinite(ref[0].cpu().numpy()).all()
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_run_host_equals_device_steps(form):
+    """es_run_host (host buffers; one captured CUDA graph of a step replayed per step) leaves
+    the same state, bit for bit, as es_step on device buffers and reports the summed Delta t:
+    with the default launch configuration, after a tuning change (the graph is rebuilt), with
+    a fixed Delta t, and with es_profile on (launches one at a time, each timed)."""
+    torch = need_gpu()
+    pb, U, x = W.shock_bubble_2d(96, 64)
+    J = Oracle(pb).init_J(x)
+    host0 = [np.ascontiguousarray(t) for t in (U * J, J, x)]
+
+    def device_run(ctx, steps, dt_fixed=0.0):
+        D = [to_dev(t, torch) for t in host0]
+        total = 0.0
+        for _ in range(steps):
+            xd, dd = ctx.es_step(*D, dt_fixed)
+            total += float(dd[0])
+        return [t.cpu() for t in D], total
+
+    def host_run(ctx, steps, dt_fixed=0.0):
+        H = [torch.from_numpy(t.copy()).pin_memory() for t in host0]
+        total = ctx.es_run_host(*H, steps, dt_fixed)
+        return H, total
+
+    ctx = _ctx(pb, form)
+    ref, tref = device_run(ctx, 3)
+    got, tgot = host_run(ctx, 3)
+    assert _same(got, ref) and tgot == tref
+    got, tgot = host_run(ctx, 3)                     # the graph replayed again
+    assert _same(got, ref) and tgot == tref
+    ctx.es_set_fusion(-1)                            # per-direction launches: graph rebuilt
+    got, _ = host_run(ctx, 3)
+    assert _same(got, ref)
+    dtf = 0.5 * tref / 3
+    ref_f, tf = device_run(ctx, 2, dtf)
+    got_f, tgf = host_run(ctx, 2, dtf)
+    assert _same(got_f, ref_f) and tgf == tf == 2 * dtf
+    ctx.es_profile(True)
+    got, _ = host_run(ctx, 3)
+    prof = ctx.es_profile_read()
+    ctx.es_profile(False)
+    assert _same(got, ref) and prof["flux_k1"][1] == 9 and prof["mesh"][1] == 3
