@@ -94,6 +94,9 @@ typedef struct es_config {
                                 (monitor); 0 = default), ES_MON_GRAD (alpha |grad_xi sigma|/max) or
                                 ES_MON_LAP (alpha |Laplacian_xi sigma|/max), the linear terms of
                                 Example 5.1's vortex monitor; second-order central differences */
+    int w;                   /* EC flux order 2w (Sec. 3.1): 1, 2 or 3; 0 means 3, the order of the
+                                paper's examples.  The metric operator delta_k and the GCL flux
+                                take the same order; the dissipation (5th-order WENO) does not */
 } es_config;
 
 typedef struct es_ctx es_ctx;

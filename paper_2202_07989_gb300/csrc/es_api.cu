@@ -133,6 +133,7 @@ std::string check_cfg(const es_config& g)
     if (g.mu < 0 || g.nf < 0) return "mu and nf must be >= 0";
     if (g.weno != ES_WENO_MR && g.weno != ES_WENO_JS) return "weno must be ES_WENO_MR or ES_WENO_JS";
     if (g.fixed_mesh != 0 && g.fixed_mesh != 1) return "fixed_mesh must be 0 or 1";
+    if (g.w < 0 || g.w > 3) return "w must be 1, 2 or 3 (0: 3)";
     return "";
 }
 
@@ -176,6 +177,7 @@ Inst make_inst(const es_config& g)
     I.nf = g.nf;
     I.weno = g.weno;
     I.fixed = g.fixed_mesh;
+    I.w = g.w == 0 ? 3 : g.w;
     if (I.fixed) {
         // no monitor, no sweeps: the mesh step reduces to the CFL time step
         I.n_sigma = 0;
@@ -197,8 +199,17 @@ Inst make_inst(const es_config& g)
     for (int k = 0; k < 3; ++k) {
         I.f_h2[k] = (float)(I.inv_dxi[k] * I.inv_dxi[k]);
         I.f_inv_dxi[k] = (float)I.inv_dxi[k];
-        for (int m = 1; m <= 3; ++m) I.mc[k][m - 1] = 0.5 * alpha3(m) * I.inv_dxi[k];
+        for (int m = 1; m <= 3; ++m) I.mc[k][m - 1] = 0.5 * alpha_w(I.w, m) * I.inv_dxi[k];
     }
+    for (int m = 0; m < 3; ++m) {
+        I.ecw[m] = alpha_w(I.w, m + 1);
+        I.f_ecw[m] = (float)I.ecw[m];
+    }
+    // GCL stencil weights of node pairs (i-j, i+1+j): (1/2) sum over the pair distances m >= j + 1
+    I.gcw[0] = 0.5 * (I.ecw[0] + I.ecw[1] + I.ecw[2]);
+    I.gcw[1] = 0.5 * (I.ecw[1] + I.ecw[2]);
+    I.gcw[2] = 0.5 * I.ecw[2];
+    for (int j = 0; j < 3; ++j) I.f_gcw[j] = (float)I.gcw[j];
     return I;
 }
 

@@ -21,7 +21,14 @@ enum { ST_NONPHYSICAL = 1, ST_TIMEOUT = 2 };
 enum { MON_GRAD2 = 0, MON_GRAD = 1, MON_LAP = 2 };   // monitor term operators
 
 // alpha_{3,m} of the sixth-order EC flux (Sec. 3.1) and the matching delta weights
-__host__ __device__ constexpr double alpha3(int m) { return m == 1 ? 1.5 : (m == 2 ? -0.3 : 1.0 / 30.0); }
+// alpha_m of the 2w-order central difference and EC flux (Sec. 3.1: sum_m alpha_m = 1 and
+// sum_m alpha_m m^(2s-1) = 0 for s = 2..w), w = 1, 2, 3; zero for m > w
+__host__ __device__ constexpr double alpha_w(int w, int m)
+{
+    return w == 1 ? (m == 1 ? 1.0 : 0.0)
+         : w == 2 ? (m == 1 ? 4.0 / 3.0 : (m == 2 ? -1.0 / 6.0 : 0.0))
+                  : (m == 1 ? 1.5 : (m == 2 ? -0.3 : 1.0 / 30.0));
+}
 
 // one instance of the problem: grid, boundary, physics and scheme parameters
 struct Inst {
@@ -48,6 +55,10 @@ struct Inst {
     float f_inv_dxi[3], f_alpha[4];
     float f_ichi3;            // 1 / chi_3 of WENO-MR
     double mc[3][3];          // (1/2) alpha_m / dxi_k: delta_k of a coordinate divided by dxi_k
+    int w;                    // EC flux order 2w
+    double ecw[3];            // alpha_m of order 2w (zero for m > w): the EC pair sum and delta_k
+    double gcw[3];            // the GCL stencil: (1/2) sum_{m >= j+1} alpha_m for node pairs j = 0..2
+    float f_ecw[3], f_gcw[3]; // binary32 copies
 };
 
 // Programmatic dependent launch: every kernel of a step waits until its predecessor has
@@ -72,6 +83,8 @@ struct Cst<double> {
     static __device__ __forceinline__ double pinf(const Inst& I) { return I.pinf_tot; }
     static __device__ __forceinline__ double chi(const Inst& I, int q) { return I.chi[q]; }
     static __device__ __forceinline__ double eps(const Inst& I) { return I.weno_eps; }
+    static __device__ __forceinline__ double ecw(const Inst& I, int m) { return I.ecw[m]; }
+    static __device__ __forceinline__ double gcw(const Inst& I, int j) { return I.gcw[j]; }
 };
 template <>
 struct Cst<float> {
@@ -82,6 +95,8 @@ struct Cst<float> {
     static __device__ __forceinline__ float pinf(const Inst& I) { return I.f_pinf_tot; }
     static __device__ __forceinline__ float chi(const Inst& I, int q) { return I.f_chi[q]; }
     static __device__ __forceinline__ float eps(const Inst& I) { return I.f_eps; }
+    static __device__ __forceinline__ float ecw(const Inst& I, int m) { return I.f_ecw[m]; }
+    static __device__ __forceinline__ float gcw(const Inst& I, int j) { return I.f_gcw[j]; }
 };
 
 // per-call device pointers of one instance: the stage input, the metric target,

@@ -344,15 +344,15 @@ __device__ __forceinline__ void iface_flux(const Inst& I, const R* nb, int NN, i
     using Y = Lay<D, NS>;
     constexpr int NC = Y::NC;
 #define NR(fld, j) nb[(fld) * NN + (j) * ns]
-    const R a1 = R(alpha3(1)), a2 = R(alpha3(2)), a3 = R(alpha3(3));
+    const R a1 = Cst<R>::ecw(I, 0), a2 = Cst<R>::ecw(I, 1), a3 = Cst<R>::ecw(I, 2);
     // the EC flux goes to its output slot at once; the dissipation is subtracted there at the end
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
         const R* pq = pf + q * NP;
         fl[q * NI + f] = a1 * pq[p1] + a2 * (pq[p2] + pq[p2 + ps]) + a3 * (pq[p3] + pq[p3 + ps] + pq[p3 + 2 * ps]);
     }
-    // GCL flux of (J xi_k/t, J xi_k/x_j): stencil (1, -8, 37, 37, -8, 1)/60
-    const double c0 = 0.5 * (alpha3(1) + alpha3(2) + alpha3(3)), c1 = 0.5 * (alpha3(2) + alpha3(3)), c2 = 0.5 * alpha3(3);
+    // GCL flux of (J xi_k/t, J xi_k/x_j): stencil (1, -8, 37, 37, -8, 1)/60 for w = 3
+    const double c0 = I.gcw[0], c1 = I.gcw[1], c2 = I.gcw[2];
     const double Gt = c0 * (m64[2 * ms] + m64[3 * ms]) + c1 * (m64[ms] + m64[4 * ms]) + c2 * (m64[0] + m64[5 * ms]);
     gt[f] = Gt;
     if (I.es) {
@@ -360,7 +360,8 @@ __device__ __forceinline__ void iface_flux(const Inst& I, const R* nb, int NN, i
 #pragma unroll
         for (int j = 0; j < D; ++j) {
             const int fj = mr + 1 + j;
-            Gx[j] = R(c0) * (NR(fj, 2) + NR(fj, 3)) + R(c1) * (NR(fj, 1) + NR(fj, 4)) + R(c2) * (NR(fj, 0) + NR(fj, 5));
+            Gx[j] = Cst<R>::gcw(I, 0) * (NR(fj, 2) + NR(fj, 3)) + Cst<R>::gcw(I, 1) * (NR(fj, 1) + NR(fj, 4)) +
+                    Cst<R>::gcw(I, 2) * (NR(fj, 0) + NR(fj, 5));
             L2 += Gx[j] * Gx[j];
         }
         R Ln = Ar<R>::sq(L2), iL = Ar<R>::rcp(Ln);

@@ -18,7 +18,7 @@ __device__ inline double delta_x(const Inst& I, const double* __restrict__ x, in
         im[k] -= m;
         x_at<false>(I, x, ip[0], ip[1], ip[2], a);
         x_at<false>(I, x, im[0], im[1], im[2], b);
-        acc += alpha3(m) * (a[p] - b[p]);
+        acc += I.ecw[m - 1] * (a[p] - b[p]);
     }
     return 0.5 * acc;
 }
@@ -173,7 +173,7 @@ __global__ void dx3d_kernel(const Inst* __restrict__ insts, StagePtrs single, co
             for (int b = 0; b < 3; ++b) {
 #pragma unroll
                 for (int q = 0; q < 3; ++q)
-                    acc[b][q] += (0.5 * alpha3(m)) * (XE[q * nx + xc + m * xst[b]] - XE[q * nx + xc - m * xst[b]]);
+                    acc[b][q] += (0.5 * I.ecw[m - 1]) * (XE[q * nx + xc + m * xst[b]] - XE[q * nx + xc - m * xst[b]]);
             }
         }
         double xq[3];
@@ -223,7 +223,7 @@ __global__ void metrics3d_kernel(const Inst* __restrict__ insts, StagePtrs singl
                 for (int b = 0; b < 3; ++b) {
                     if (b == a) continue;
                     const int k = 3 - a - b;
-                    const double sg = (b == (a + 2) % 3 ? 1.0 : -1.0) * alpha3(mm);
+                    const double sg = (b == (a + 2) % 3 ? 1.0 : -1.0) * I.ecw[mm - 1];
 #pragma unroll
                     for (int j = 0; j < 3; ++j) {
                         const double* Pbj = D + (long long)(b * 3 + j) * ne;   // delta_b[x_p] x_q

@@ -76,42 +76,6 @@ __device__ inline double sigma_of(const Inst& I, int kind, const double* U)
     }
 }
 
-// 2D node metrics J xi_k/x_j at interior node (i0, i1) (Sec. 3.2, degenerate case)
-__device__ inline void node_metrics2d(const Inst& I, const double* __restrict__ x, int i0, int i1, double m[3][3])
-{
-    double d1[2] = { 0, 0 }, d2[2] = { 0, 0 };
-    const int n0 = I.n[0], n1 = I.n[1];
-    if (i0 >= 3 && i0 < n0 - 3 && i1 >= 3 && i1 < n1 - 3) {
-        const double* X0 = x;
-        const double* X1 = x + I.ncell;
-        const int c = i1 * n0 + i0;
-#pragma unroll
-        for (int q = 1; q <= 3; ++q) {
-            d1[0] += alpha3(q) * (X0[c + q] - X0[c - q]);
-            d1[1] += alpha3(q) * (X1[c + q] - X1[c - q]);
-            d2[0] += alpha3(q) * (X0[c + q * n0] - X0[c - q * n0]);
-            d2[1] += alpha3(q) * (X1[c + q * n0] - X1[c - q * n0]);
-        }
-    } else {
-        double a[2], b[2], cc[2], e[2];
-#pragma unroll
-        for (int q = 1; q <= 3; ++q) {
-            x_at<false>(I, x, i0 + q, i1, 0, a);
-            x_at<false>(I, x, i0 - q, i1, 0, b);
-            x_at<false>(I, x, i0, i1 + q, 0, cc);
-            x_at<false>(I, x, i0, i1 - q, 0, e);
-            d1[0] += alpha3(q) * (a[0] - b[0]);
-            d1[1] += alpha3(q) * (a[1] - b[1]);
-            d2[0] += alpha3(q) * (cc[0] - e[0]);
-            d2[1] += alpha3(q) * (cc[1] - e[1]);
-        }
-    }
-    m[0][0] = 0.5 * d2[1] * I.inv_dxi[1];
-    m[0][1] = -0.5 * d2[0] * I.inv_dxi[1];
-    m[1][0] = -0.5 * d1[1] * I.inv_dxi[0];
-    m[1][1] = 0.5 * d1[0] * I.inv_dxi[0];
-}
-
 // conserved point state at a node in the compute type (ghost maps of load_U)
 template <typename R>
 __device__ __forceinline__ void load_U_t(const Inst& I, const double* __restrict__ JU, const double* __restrict__ J,

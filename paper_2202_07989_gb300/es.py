@@ -41,7 +41,7 @@ class EsConfig(C.Structure):
         ("chi", C.c_double * 3), ("weno_eps", C.c_double), ("cfl", C.c_double),
         ("n_sigma", C.c_int), ("sigma", C.c_int * 4), ("alpha", C.c_double * 4),
         ("mu", C.c_int), ("nf", C.c_int), ("weno", C.c_int), ("fixed_mesh", C.c_int),
-        ("sigma_op", C.c_int * 4),
+        ("sigma_op", C.c_int * 4), ("w", C.c_int),
     ]
 
 
@@ -117,6 +117,7 @@ def make_config(pb: Problem, precision: int = FP64) -> EsConfig:
     c.weno, c.fixed_mesh = int(pb.weno), int(pb.fixed_mesh)
     for q, op in enumerate(pb.sigma_op):
         c.sigma_op[q] = int(op)
+    c.w = int(pb.w)
     return c
 
 

@@ -412,16 +412,17 @@ def _interior(pb, M, depth):
     return M[tuple(sl)]
 
 
-@pytest.mark.parametrize("d", [2, 3])
-def test_metrics_exact_for_polynomial_maps(d):
+@pytest.mark.parametrize("d,w", [(2, 1), (2, 2), (2, 3), (3, 3)])
+def test_metrics_exact_for_polynomial_maps(d, w):
     """J xi_k/x_j of Eq. (SCLCoeff) (and the 2D degenerate case) equal the cofactors of
-    dx/dxi for polynomial maps the 2w-order central differences integrate exactly."""
+    dx/dxi for polynomial maps the 2w-order central differences differentiate exactly
+    (degree 2w in 2D)."""
     n = 20 if d == 2 else 16
-    pb = W.random_problem(d, 1, (n,) * d, bc="reflect")
+    pb = W.random_problem(d, 1, (n,) * d, bc="reflect").with_(w=w)
     o = Oracle(pb)
     rng = np.random.default_rng(21)
     xi = W.xi_nodes(pb)
-    deg = 6 if d == 2 else 2
+    deg = 2 * w if d == 2 else 2
     coef = rng.uniform(-0.05, 0.05, size=(d, d, deg + 1))
 
     def comp(j, xs):
@@ -451,18 +452,18 @@ def test_metrics_exact_for_polynomial_maps(d):
             np.testing.assert_allclose(got, cof[..., k, j][sl], rtol=0, atol=1e-12)
 
 
-@pytest.mark.parametrize("d", [2, 3])
+@pytest.mark.parametrize("d,w", [(2, 1), (2, 2), (2, 3), (3, 1), (3, 2), (3, 3)])
 @pytest.mark.parametrize("bc", ["periodic", "mixed"])
-def test_discrete_scl(d, bc):
+def test_discrete_scl(d, w, bc):
     """Discrete SCL Eq. (SCL_dis): sum_k delta_k[J xi_k/x_j]/dxi_k = 0 at every node
-    (the GCL-flux difference telescopes to delta_k), random smooth moving meshes."""
+    (the GCL-flux difference telescopes to delta_k), random smooth moving meshes, each order 2w."""
     n = 12 if d == 2 else 10
-    pb = W.random_problem(d, 1, (n,) * d, bc=bc)
+    pb = W.random_problem(d, 1, (n,) * d, bc=bc).with_(w=w)
     o = Oracle(pb)
     rng = np.random.default_rng(22)
     x = W.smooth_mesh(pb, rng)
     M = o.metrics(x)
-    al = o.alpha()
+    al = list(o.alpha(w)) + [0.0] * (3 - w)
     for j in range(d):
         tot = 0.0
         for k in range(d):
@@ -480,11 +481,13 @@ def test_discrete_scl(d, bc):
 
 @pytest.mark.parametrize("d,N", CASES)
 @pytest.mark.parametrize("es", [False, True])
-def test_free_stream_preservation(d, N, es):
+@pytest.mark.parametrize("w", [1, 2, 3])
+def test_free_stream_preservation(d, N, es, w):
     """A constant state on a randomly perturbed moving mesh stays constant: d(JU)/dt = U dJ/dt
-    for the residual and U is unchanged to round-off after SSP-RK3 steps (remark in Sec. 3.2)."""
+    for the residual and U is unchanged to round-off after SSP-RK3 steps (remark in Sec. 3.2),
+    for each order 2w."""
     n = 12 if d == 2 else 10
-    pb = W.random_problem(d, N, (n,) * d, pinf=1.0 if N == 1 else 0.0, es=es)
+    pb = W.random_problem(d, N, (n,) * d, pinf=1.0 if N == 1 else 0.0, es=es).with_(w=w)
     o = Oracle(pb)
     rng = np.random.default_rng(23)
     x = W.smooth_mesh(pb, rng)
