@@ -376,11 +376,28 @@ def cpu_baseline_leg(pb, U, x, gpu_after_one, budget_s=20.0):
             "sample": "%d full steps (mesh redistribution + SSP-RK3) of the 400x200 workload from t = 0, %.1f s" % (steps, el)}, first
 
 
+def rank_env():
+    """(rank, world size, local rank) of this process from the launcher's environment."""
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(value, device):
+    """The maximum of a host scalar over all ranks (the value itself without a process group),
+    followed by a barrier, so that every rank leaves the timed bracket together."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
 def main_ours(args):
     import torch
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local = rank_env()
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
@@ -413,11 +430,7 @@ def main_ours(args):
     clocks.start()
     t_main = time_steps(main, args.steps, args.warmup, torch, flush)
     clk = clocks.stop()
-    if world > 1:
-        tt = torch.tensor([t_main], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.barrier()
-        t_main = float(tt.item())
+    t_main = max_over_ranks(t_main, "cuda")
     value = pb.ncell * 3 * args.steps * world / t_main
     forms["mixed"] = {"value": pb.ncell * 3 * args.steps / t_main, "ms_per_step": 1e3 * t_main / args.steps}
 
@@ -631,8 +644,7 @@ def main_ours(args):
 # ---------------------------------------------------------------------------
 
 def main_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank, world, _ = rank_env()
     if rank != 0:
         return
     from oracle.oracle import Oracle
