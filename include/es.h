@@ -292,6 +292,15 @@ es_status es_check_conversions(const double* in, int n, float* out32, double* ou
  * a, b: DEVICE arrays of n binary32 values; out: DEVICE array of n doubles. */
 es_status es_check_half_sums(const float* a, const float* b, int n, double* out, void* stream);
 
+/* Self-check of the mixed form's log-mean small-jump value {a}(1 - del) rounded to
+ * binary32 (Sec. 3.3): fast[i] as the flux kernels form it (integer-built {a},
+ * conversions without special cases where their preconditions hold) and
+ * general[i] by the general conversions with an FP64 add for {a}; both through
+ * one FP64 fused multiply-add.  a, b > 0, 0 <= del <= 1/2.  a, b, del, fast,
+ * general: DEVICE arrays of n binary32 values. */
+es_status es_check_logmean_small(const float* a, const float* b, const float* del, int n, float* fast, float* general,
+                                 void* stream);
+
 /* Reads and clears the sticky device status (synchronises the stream):
  * *flags = bit 0 non-physical state, bit 1 timeout. */
 es_status es_poll_status(es_ctx* ctx, int* flags, void* stream);

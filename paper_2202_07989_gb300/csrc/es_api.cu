@@ -1106,6 +1106,15 @@ es_status es_check_half_sums(const float* a, const float* b, int n, double* out,
     return cudaGetLastError() == cudaSuccess ? ES_OK : ES_ERR_CUDA;
 }
 
+es_status es_check_logmean_small(const float* a, const float* b, const float* del, int n, float* fast, float* general,
+                                 void* stream)
+{
+    if (!a || !b || !del || !fast || !general || n < 0) return ES_ERR_ARG;
+    if (n == 0) return ES_OK;
+    logmean_small_check_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(a, b, del, n, fast, general);
+    return cudaGetLastError() == cudaSuccess ? ES_OK : ES_ERR_CUDA;
+}
+
 es_status es_profile(es_ctx* c, int enable)
 {
     if (!c) return ES_ERR_ARG;

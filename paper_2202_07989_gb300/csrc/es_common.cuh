@@ -411,6 +411,49 @@ __device__ __forceinline__ double half_sum_exact(float a, float b)
     return __longlong_as_double((long long)bits);
 }
 
+// binary32 -> binary64 (exact) of a positive normal value: the significand shifted into place
+// and the exponent rebiased from 127 to 1023 by one 64-bit add
+__device__ __forceinline__ double f32_to_f64_posnormal(float f)
+{
+    return __longlong_as_double((long long)(((unsigned long long)__float_as_uint(f) << 29) + (896ull << 52)));
+}
+
+// binary64 -> binary32, round to nearest even, of a positive value whose binary32 result is a
+// normal number or infinity: the exponent rebiased from 1023 to 127 in the shifted bit pattern
+__device__ __forceinline__ float f64_to_f32_posnormal(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    unsigned int f = (unsigned int)((b >> 29) - (896ull << 23));
+    const unsigned int rem = (unsigned int)b & 0x1fffffffu;
+    f += (rem > 0x10000000u || (rem == 0x10000000u && (f & 1u))) ? 1u : 0u;
+    return __uint_as_float(f);
+}
+
+// {a}(1 - del) rounded to binary32, the value of the log-mean small-jump branch (the
+// Ismail-Roe series, Sec. 3.3): {a} = a/2 + b/2 exact in binary64, times (1 - del) by one FP64
+// fused multiply-add, then rounded.  a, b > 0 and 0 <= del <= 1/2.  When a and b are normal
+// (biased exponents >= 2) and at most 7 binades apart and del is zero or normal, {a} is built
+// with integer instructions (as in half_sum_exact) and the conversions skip their special
+// cases; otherwise the general conversions run.  Both give the same value.
+__device__ __forceinline__ float logmean_small(float a, float b, float del)
+{
+    const unsigned int ua = __float_as_uint(a), ub = __float_as_uint(b);
+    const int ea = (int)(ua >> 23), eb = (int)(ub >> 23);
+    const int e = min(ea, eb), dl = max(ea, eb) - e;
+    const bool del_ok = del == 0.0f || (__float_as_uint(del) >> 23) != 0u;
+    if (e >= 2 && dl <= 7 && max(ea, eb) <= 254 && del_ok) {
+        const unsigned int ma = (ua & 0x7fffffu) | 0x800000u, mb = (ub & 0x7fffffu) | 0x800000u;
+        const unsigned int M = (ma << (ea - e)) + (mb << (eb - e));
+        const int k = 31 - __clz((int)M);
+        const double hs = __longlong_as_double(
+            (long long)(((unsigned long long)(k + e + 871) << 52) + ((unsigned long long)M << (52 - k))));
+        const double d = del == 0.0f ? 0.0 : f32_to_f64_posnormal(del);
+        return f64_to_f32_posnormal(fma(-hs, d, hs));
+    }
+    const double hs = f32_to_f64(0.5f * a) + f32_to_f64(0.5f * b);
+    return f64_to_f32(fma(-hs, f32_to_f64(del), hs));
+}
+
 // bounded reductions of non-negative doubles: the IEEE order of non-negative
 // doubles is the order of their bit patterns
 __device__ inline void atomic_max_pos(double* a, double v)

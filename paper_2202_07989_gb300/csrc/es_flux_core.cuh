@@ -65,21 +65,20 @@ struct Ar<float> {
     static __device__ __forceinline__ float sq(float x) { return sqrtf(x); }
     static __device__ __forceinline__ float ab(float x) { return fabsf(x); }
     // small jumps ((b-a)/(b+a))^2 < 1e-2: {a}^ln = {a} (1 - delta(u)), the mean {a}
-    // and the correction formed in FP64; delta is the series of 1 - f/artanh(f).  {a} is
-    // exact in binary64 and is assembled with integer instructions, so the FP64 pipe runs
-    // only the fused multiply-add (a, b > 0 here: |b - a| < (a + b)/10)
-    static __device__ __forceinline__ double small_branch(float a, float b, float u)
+    // and the correction formed in FP64 (logmean_small: {a} exact in binary64, built with
+    // integer instructions, and one FP64 fused multiply-add); delta is the series of
+    // 1 - f/artanh(f).  Here a, b > 0: |b - a| < (a + b)/10
+    static __device__ __forceinline__ float small_branch(float a, float b, float u)
     {
         float del = u * (1.f / 3.f + u * (4.f / 45.f + u * (44.f / 945.f + u * (428.f / 14175.f))));
-        const double hs = half_sum_exact(a, b);
-        return fma(-hs, f32_to_f64(del), hs);
+        return logmean_small(a, b, del);
     }
     static __device__ __forceinline__ float lmean(float a, float b, float la, float lb)
     {
         float s = a + b, dd = b - a;
         if (fabsf(dd) < 0.1f * s) {
             float f = __fdividef(dd, s);
-            return f64_to_f32(small_branch(a, b, f * f));
+            return small_branch(a, b, f * f);
         }
         return __fdividef(dd, lb - la);
     }
@@ -88,7 +87,7 @@ struct Ar<float> {
         float dd = b - a;
         if (fabsf(dd) < 0.1f * (a + b)) {
             float f = dd * is;
-            return __frcp_rn(f64_to_f32(small_branch(a, b, f * f)));
+            return __frcp_rn(small_branch(a, b, f * f));
         }
         return __fdividef(lb - la, dd);
     }

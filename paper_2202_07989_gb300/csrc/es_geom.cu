@@ -294,4 +294,16 @@ __global__ void half_sum_check_kernel(const float* __restrict__ a, const float* 
     out[i] = half_sum_exact(a[i], b[i]);
 }
 
+// logmean_small beside the same value by the general conversions and an FP64 add for {a}
+__global__ void logmean_small_check_kernel(const float* __restrict__ a, const float* __restrict__ b,
+                                           const float* __restrict__ del, int n, float* __restrict__ fast,
+                                           float* __restrict__ general)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    fast[i] = logmean_small(a[i], b[i], del[i]);
+    const double hs = f32_to_f64(0.5f * a[i]) + f32_to_f64(0.5f * b[i]);
+    general[i] = f64_to_f32(fma(-hs, f32_to_f64(del[i]), hs));
+}
+
 }  // namespace es

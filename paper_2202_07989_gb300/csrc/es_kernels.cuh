@@ -65,6 +65,8 @@ __global__ void metrics3d_kernel(const Inst* insts, StagePtrs single, const Stag
                                  const Scratch* scr);
 __global__ void conversion_check_kernel(const double* in, int n, float* o32, double* o64);
 __global__ void half_sum_check_kernel(const float* a, const float* b, int n, double* out);
+__global__ void logmean_small_check_kernel(const float* a, const float* b, const float* del, int n, float* fast,
+                                           float* general);
 __global__ void init_J_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work, int nwork);
 
 // flux + divergence (+ RK stage) for one direction; D dims, NS species, R compute type,

@@ -80,6 +80,7 @@ def lib():
             "es_profile": (C.c_int, [vp, C.c_int]),
             "es_check_conversions": (C.c_int, [dp, C.c_int, dp, dp, vp]),
             "es_check_half_sums": (C.c_int, [dp, dp, C.c_int, dp, vp]),
+            "es_check_logmean_small": (C.c_int, [dp, dp, dp, C.c_int, dp, dp, vp]),
             "es_entropy_production_noalloc": (C.c_int, [C.POINTER(EsConfig), dp, dp, dp, dp, dp, vp]),
             "es_profile_read": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.c_int]),
         }
@@ -369,6 +370,23 @@ def es_check_half_sums(a: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
     if st != 0:
         raise EsError("es_check_half_sums: %s" % ES_STATUS.get(st, st))
     return out
+
+
+def es_check_logmean_small(a: torch.Tensor, b: torch.Tensor, d: torch.Tensor):
+    """(fast, general) binary32 values of the log-mean small-jump branch {a}(1 - d) for float32
+    CUDA tensors a, b > 0 and 0 <= d <= 1/2."""
+    for t, nm in ((a, "a"), (b, "b"), (d, "d")):
+        if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+            raise EsError("%s must be a contiguous float32 CUDA tensor" % nm)
+    if not (a.shape == b.shape == d.shape):
+        raise EsError("a, b and d must have the same shape")
+    fast = torch.empty_like(a)
+    general = torch.empty_like(a)
+    st = lib().es_check_logmean_small(C.c_void_p(a.data_ptr()), C.c_void_p(b.data_ptr()), C.c_void_p(d.data_ptr()),
+                                      a.numel(), C.c_void_p(fast.data_ptr()), C.c_void_p(general.data_ptr()), _stream())
+    if st != 0:
+        raise EsError("es_check_logmean_small: %s" % ES_STATUS.get(st, st))
+    return fast, general
 
 
 # module-level aliases with the C names

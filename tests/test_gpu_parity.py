@@ -502,6 +502,36 @@ def test_integer_built_half_sum_is_exact():
     assert torch.equal(got[~pre].view(torch.int64), halves[~pre].view(torch.int64))
 
 
+def test_logmean_small_branch_fast_path_equals_general():
+    """The mixed log-mean small-jump value {a}(1 - del) as the flux kernels form it (integer-built
+    {a}, conversions without special cases) equals the value by the general conversions and an
+    FP64 add for {a}, bit for bit: pairs within 10% across every binade with del from the
+    series (including del = 0 for equal pairs), and inputs outside the fast path's
+    preconditions (the smallest binades, subnormal del, far-apart pairs)."""
+    torch = need_gpu()
+    from paper_2202_07989_gb300 import es
+    rng = np.random.default_rng(47)
+    n = 400000
+    a = rng.uniform(1.0, 2.0, n) * np.exp2(rng.integers(-124, 126, n))
+    b = a * rng.uniform(0.82, 1.22, n)
+    f = (b - a) / (a + b)
+    u = f * f
+    d = u * (1 / 3 + u * (4 / 45 + u * (44 / 945 + u * (428 / 14175))))
+    eq = rng.uniform(1.0, 2.0, 20000) * np.exp2(rng.integers(-120, 120, 20000))
+    far = rng.uniform(1.0, 2.0, 2000)
+    tiny = rng.uniform(0.5, 2.0, 2000) * 2.0 ** -126
+    A = np.concatenate([a, eq, far, tiny, a[:2000]]).astype(np.float32)
+    B = np.concatenate([b, eq, far * 512.0, tiny * 1.05, b[:2000]]).astype(np.float32)
+    D = np.concatenate([d, np.zeros(20000), np.full(2000, 1e-3), np.full(2000, 2e-3), np.full(2000, 1e-40)]).astype(np.float32)
+    ok = np.isfinite(A) & np.isfinite(B)
+    at, bt, dt_ = (torch.from_numpy(v[ok]).cuda() for v in (A, B, D))
+    fast, general = es.es_check_logmean_small(at, bt, dt_)
+    assert torch.equal(fast.view(torch.int32), general.view(torch.int32))
+    # the equal pairs give {a} itself
+    m = (at == bt) & (dt_ == 0)
+    assert int(m.sum()) >= 20000 and torch.equal(fast[m], at[m])
+
+
 def test_integer_pipe_conversions_match_hardware():
     """The mixed form's integer-instruction binary64 -> binary32 rounding equals the hardware
     conversion bit for bit (outside the flushed range below 2^-126), and widening is exact."""
