@@ -52,7 +52,13 @@ __global__ void __launch_bounds__(NODE_TPB) metrics2d_kernel(const Inst* __restr
         const int b0 = (it.y % ntx) * NT_X - 6, b1 = (it.y / ntx) * NT_Y - 6;
         const bool inner = b0 >= 0 && b0 + HX <= n0 && b1 >= 0 && b1 + HY <= n1;
         __syncthreads();
-        for (int q = threadIdx.x; q < HX * HY; q += NODE_TPB) {
+        // at most three halo slots per thread, in one unrolled body so that their loads are
+        // issued together
+        static_assert(HX * HY <= 3 * NODE_TPB, "three halo slots per thread");
+#pragma unroll
+        for (int h = 0; h < 3; ++h) {
+            const int q = (int)threadIdx.x + h * NODE_TPB;
+            if (q >= HX * HY) continue;
             const int a = q % HX, b = q / HX;
             const int g0 = b0 + a, g1 = b1 + b;
             double v[2] = { 0.0, 0.0 }, w[2] = { 0.0, 0.0 };

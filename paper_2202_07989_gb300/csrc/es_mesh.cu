@@ -307,7 +307,13 @@ __global__ void __launch_bounds__(NODE_TPB) cfl_grad2d_kernel(const Inst* __rest
         const int b0 = (it.y % ntx) * NT_X - 1, b1 = (it.y / ntx) * NT_Y - 1;
         K kmax[5] = { 0, 0, 0, 0, 0 };    // CFL sum, then the monitor terms
         __syncthreads();    // the previous tile's readers are done
-        for (int q = threadIdx.x; q < TX * TY; q += NODE_TPB) {
+        // at most two halo slots per thread, in one unrolled body so that the loads of both
+        // are issued together
+        static_assert(TX * TY <= 2 * NODE_TPB, "two halo slots per thread");
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int q = (int)threadIdx.x + h * NODE_TPB;
+            if (q >= TX * TY) continue;
             const int a = q % TX, b = q / TX;
             const int g0 = b0 + a, g1 = b1 + b;
             // a node outside the domain in both directions (a tile corner, or on a ragged tile
@@ -316,6 +322,15 @@ __global__ void __launch_bounds__(NODE_TPB) cfl_grad2d_kernel(const Inst* __rest
             if ((out0 && out1) || g0 > n0 || g1 > n1) continue;
             const bool own = a >= 1 && a <= NT_X && b >= 1 && b <= NT_Y && !out0 && !out1;
             if (ns == 0 && !own) continue;
+            // the spatial metrics of x^n at a tile node, loaded ahead of the state arithmetic
+            const long long p = lin(I, g0, g1, 0), pid = plin(I, g0, g1, 0);
+            double mraw[4] = { 0.0, 0.0, 0.0, 0.0 };
+            if (own) {
+#pragma unroll
+                for (int k = 0; k < 2; ++k)
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) mraw[2 * k + j] = Sc.M[(long long)(k * 3 + 1 + j) * I.npad + pid];
+            }
             // the point state with the ghost map of the one direction the node lies outside:
             // the arithmetic of load_U_t, with the field count known
             R U[MAXC];
@@ -351,7 +366,6 @@ __global__ void __launch_bounds__(NODE_TPB) cfl_grad2d_kernel(const Inst* __rest
             }
             const R T = (U[NC - 1] - R(0.5) * rho * v2 - Cst<R>::pinf(I)) / cvr;
             const R c = sqrt((ar / rho) * (gm / cvr) * T);
-            const long long p = lin(I, g0, g1, 0), pid = plin(I, g0, g1, 0);
             const R Jp = to_r<R>(P.J[p]);
             R sr = R(0);
 #pragma unroll
@@ -359,7 +373,7 @@ __global__ void __launch_bounds__(NODE_TPB) cfl_grad2d_kernel(const Inst* __rest
                 R L2 = R(0), vn = R(0);
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
-                    const R mk = to_r<R>(Sc.M[(long long)(k * 3 + 1 + j) * I.npad + pid]);
+                    const R mk = to_r<R>(mraw[2 * k + j]);
                     L2 += mk * mk;
                     vn += mk * v[j];
                 }
