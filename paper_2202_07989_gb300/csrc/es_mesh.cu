@@ -801,6 +801,8 @@ __global__ void __launch_bounds__(NODE_TPB) jacobi_fused2d_kernel(const Inst* __
     float* dq = yb + 2 * NR;      // [8][NR]: (k * 2 + s) * 2 + j
     float* ta = dq + 8 * NR;      // [NRo] Theta ping-pong on the outer region
     float* tb = ta + NRo;
+    float* wq = tb + NRo;         // [4][NR] sweep weights (k * 2 + s), fixed while Theta is
+    float* dn = wq + 4 * NR;      // [NR] their sum; 0 marks a slot no sweep updates
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
         const int2 it = work[wi];
         const Inst& I = insts[it.x];
@@ -897,11 +899,28 @@ __global__ void __launch_bounds__(NODE_TPB) jacobi_fused2d_kernel(const Inst* __
                 }
         }
         __syncthreads();
-        // the remaining - sides: minus the + side of the - neighbour (the same pair of nodes)
+        // the remaining - sides: minus the + side of the - neighbour (the same pair of nodes);
+        // and the sweep weights Theta_{k+-1/2} / dxi_k^2 of every slot a sweep updates, with
+        // their sum, formed once since Theta stays fixed through the sweeps
         for (SlotIter sl(RX); sl.q < NR; sl.next()) {
             const int q = sl.q, a = sl.a, b = sl.b;
             const int g0 = r0 + a, g1 = r1 + b;
             const bool ghost = (!per0 && (g0 < 0 || g0 >= n0)) || (!per1 && (g1 < 0 || g1 >= n1));
+            float den = 0.0f;
+            if (!ghost && a != 0 && a != RX - 1 && b != 0 && b != RY - 1) {
+                const int qt = b * RXo + a;
+                const float tc = tq[qt];
+#pragma unroll
+                for (int k = 0; k < 2; ++k)
+#pragma unroll
+                    for (int sd = 0; sd < 2; ++sd) {
+                        const int qtn = qt + (k == 0 ? (sd ? 1 : -1) : (sd ? RXo : -RXo));
+                        const float w = 0.5f * (tc + tq[qtn]) * I.f_h2[k];
+                        wq[(k * 2 + sd) * NR + q] = w;
+                        den += w;
+                    }
+            }
+            dn[q] = den;
             if (ghost) continue;
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
@@ -916,25 +935,20 @@ __global__ void __launch_bounds__(NODE_TPB) jacobi_fused2d_kernel(const Inst* __
         float* yc = ya;
         float* yn = yb;
         for (int sw = 0; sw < H; ++sw) {
-            // in-domain nodes: one sweep (neighbours outside the region leave a node invalid)
-            for (SlotIter sl(RX); sl.q < NR; sl.next()) {
-                const int q = sl.q, a = sl.a, b = sl.b;
-                const int g0 = r0 + a, g1 = r1 + b;
-                const bool ghost = (!per0 && (g0 < 0 || g0 >= n0)) || (!per1 && (g1 < 0 || g1 >= n1));
-                if (ghost || a == 0 || a == RX - 1 || b == 0 || b == RY - 1) continue;
-                const int qt = b * RXo + a;
-                const float tc = tq[qt];
-                float num[2] = { 0.0f, 0.0f }, den = 0.0f;
+            // in-domain nodes: one sweep (neighbours outside the region leave a node invalid);
+            // the slots with a zero weight sum (wall ghosts, the region's edge) keep their values
+            for (int q = threadIdx.x; q < NR; q += NODE_TPB) {
+                const float den = dn[q];
+                if (den == 0.0f) continue;
+                float num[2] = { 0.0f, 0.0f };
 #pragma unroll
                 for (int k = 0; k < 2; ++k)
 #pragma unroll
                     for (int sd = 0; sd < 2; ++sd) {
                         const int qn = q + (k == 0 ? (sd ? 1 : -1) : (sd ? RX : -RX));
-                        const int qtn = qt + (k == 0 ? (sd ? 1 : -1) : (sd ? RXo : -RXo));
-                        const float w = 0.5f * (tc + tq[qtn]) * I.f_h2[k];
+                        const float w = wq[(k * 2 + sd) * NR + q];
 #pragma unroll
                         for (int j = 0; j < 2; ++j) num[j] = fmaf(w, dq[((k * 2 + sd) * 2 + j) * NR + q] + yc[j * NR + qn], num[j]);
-                        den += w;
                     }
 #pragma unroll
                 for (int j = 0; j < 2; ++j) yn[j * NR + q] = num[j] / den;
@@ -991,7 +1005,7 @@ size_t jacobi_fused2d_smem(int H, int F)
 {
     const size_t nr = (size_t)(NT_X + 2 * H) * (NT_Y + 2 * H);
     const size_t Fp = F > 0 ? F : 0, nro = (NT_X + 2 * H + 2 * Fp) * (NT_Y + 2 * H + 2 * Fp);
-    return sizeof(float) * (12 * nr + 2 * nro);
+    return sizeof(float) * (17 * nr + 2 * nro);
 }
 
 void prepare_mesh()
