@@ -365,12 +365,12 @@ struct ProfScope {
 // slots (the first kernel of a mesh step); dot = true (2D) also forms the metrics of the mesh
 // velocity into P.Md, so the later stages of an RK step need no metrics pass
 void launch_metrics(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStream_t st, bool reset = false,
-                    bool dot = false)
+                    bool dot = false, bool vcl = true)
 {
     ProfScope ps(c, PC_METRICS, st);
     if (c->d == 2) {
         launch_metrics2d(dot, node_grid(c, c->n_pad), st, c->dI, P, tab, c->w_pad, c->n_pad, reset ? c->dS : nullptr,
-                         c->n_inst);
+                         c->n_inst, vcl);
     } else {
         pdl_launch(xe_fill_kernel, node_grid(c, c->n_xe), NODE_TPB, 0, st, c->dI, P, tab, c->w_xe, c->n_xe, c->dS,
                    reset ? c->n_inst : 0);
@@ -486,7 +486,9 @@ void launch_mesh(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStream
     StagePtrs Q = P;
     Q.xdot = nullptr;
     Q.M = c->hS[0].M;
-    launch_metrics(c, Q, tab, st, true);     // also resets the reduction slots
+    // also resets the reduction slots; the VCL rows (xdot = 0 here) matter only on a fixed mesh,
+    // whose stages use these metrics: a moving-mesh step's velocity pass writes them
+    launch_metrics(c, Q, tab, st, true, false, c->hI[0].fixed != 0);
     ProfScope ps(c, PC_MESH, st);
     int gc = node_grid(c, c->n_cell);
     launch_cfl_grad(c->mixed, c->d, c->N, gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS);

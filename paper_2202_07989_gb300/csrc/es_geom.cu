@@ -26,7 +26,8 @@ __device__ inline double delta_x(const Inst& I, const double* __restrict__ x, in
 // 2D: J xi_1/x = (delta_2[x_2], -delta_2[x_1]) / dxi_2, J xi_2/x = (-delta_1[x_2], delta_1[x_1]) / dxi_1
 // over the padded node range (3 ghost layers); with DOT also the metrics of the mesh velocity
 // xdot into Md (the 2D metrics are linear in x); with `reset`, block 0 also resets the reduction
-// slots of the ninst instances (the first kernel of a mesh step).  Each block stages x on its tile and on a
+// slots of the ninst instances (the first kernel of a mesh step); vcl = false leaves the VCL
+// rows of M alone (a moving-mesh step, whose velocity pass writes them).  Each block stages x on its tile and on a
 // halo of 3 nodes in shared memory (ghost nodes through the boundary maps, once per node),
 // then forms both derivatives from shared memory; the coefficients mc = alpha_m / (2 dxi_k)
 // fold the scaling into the stencil.
@@ -34,7 +35,7 @@ template <bool DOT>
 __global__ void __launch_bounds__(NODE_TPB) metrics2d_kernel(const Inst* __restrict__ insts, StagePtrs single,
                                                               const StagePtrs* __restrict__ table,
                                                               const int2* __restrict__ work, int nwork,
-                                                              const Scratch* __restrict__ reset, int ninst)
+                                                              const Scratch* __restrict__ reset, int ninst, bool vcl)
 {
     pdl_entry();
     reset_reductions(reset, ninst);
@@ -101,7 +102,14 @@ __global__ void __launch_bounds__(NODE_TPB) metrics2d_kernel(const Inst* __restr
             x_at<true>(I, S.xdot, i0, i1, 0, xd);
         }
         const long long np = I.npad, p = plin(I, i0, i1, 0);
-        store_metrics2d(S.M, np, p, xd, m);
+        if (vcl) {
+            store_metrics2d(S.M, np, p, xd, m);
+        } else {
+            S.M[1 * np + p] = m[0];
+            S.M[2 * np + p] = m[1];
+            S.M[4 * np + p] = m[2];
+            S.M[5 * np + p] = m[3];
+        }
         if (DOT) {
             // metrics of the mesh velocity: the stages of an RK step use M + s dt Md
             double md[4];
@@ -112,10 +120,10 @@ __global__ void __launch_bounds__(NODE_TPB) metrics2d_kernel(const Inst* __restr
 }
 
 void launch_metrics2d(bool dot, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
-                      const StagePtrs* table, const int2* work, int nwork, const Scratch* reset, int ninst)
+                      const StagePtrs* table, const int2* work, int nwork, const Scratch* reset, int ninst, bool vcl)
 {
-    if (dot) pdl_launch(metrics2d_kernel<true>, grid, NODE_TPB, 0, st, insts, single, table, work, nwork, reset, ninst);
-    else pdl_launch(metrics2d_kernel<false>, grid, NODE_TPB, 0, st, insts, single, table, work, nwork, reset, ninst);
+    if (dot) pdl_launch(metrics2d_kernel<true>, grid, NODE_TPB, 0, st, insts, single, table, work, nwork, reset, ninst, true);
+    else pdl_launch(metrics2d_kernel<false>, grid, NODE_TPB, 0, st, insts, single, table, work, nwork, reset, ninst, vcl);
 }
 
 // 3D pass 0: x on the grid with 9 ghost layers (extent n + 18), every ghost node mapped once

@@ -54,9 +54,11 @@ struct FluxLaunch {
     int* status;
 };
 
-// 2D metrics; dot = true also forms the metrics of the mesh velocity into Md
+// 2D metrics; dot = true also forms the metrics of the mesh velocity into Md; vcl = false
+// stores the spatial rows only
 void launch_metrics2d(bool dot, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
-                      const StagePtrs* table, const int2* work, int nwork, const Scratch* reset, int ninst);
+                      const StagePtrs* table, const int2* work, int nwork, const Scratch* reset, int ninst,
+                      bool vcl = true);
 __global__ void xe_fill_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work, int nwork,
                                const Scratch* scr, int reset_n);
 __global__ void dx3d_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work, int nwork,

@@ -1278,7 +1278,10 @@ __global__ void __launch_bounds__(NODE_TPB) xdot_vel2d_kernel(const Inst* __rest
         }
         const long long np = I.npad, p = plin(I, i0, i1, 0);
         const double m[4] = { Sc.M[1 * np + p], Sc.M[2 * np + p], Sc.M[4 * np + p], Sc.M[5 * np + p] };
-        store_metrics2d(Sc.M, np, p, xd, m);
+        // the spatial rows of M hold m already (the metrics pass of x^n): only the VCL rows change
+        const double r1[2] = { m[0], m[1] }, r2[2] = { m[2], m[3] };
+        Sc.M[0 * np + p] = vcl_metric<2>(xd, r1);
+        Sc.M[3 * np + p] = vcl_metric<2>(xd, r2);
         double md[4];
         metrics2d_at<HY, HX>(I, sv, cy, cx, md);
         store_metrics2d(Sc.Md, np, p, xd, md);
