@@ -4,8 +4,9 @@
 A step is one full time step of the method: mesh redistribution (CFL time step,
 monitor + filter, Jacobi sweeps, limiter, mesh velocity) followed by one SSP-RK3
 step (three residual evaluations with metrics, sixth-order EC flux, WENO-MR
-dissipation, divergence and the fused stage update).  The metric is cell-stage
-updates per second: cells x 3 stages x steps / time, summed over all ranks.
+dissipation, divergence and the stage update; in 2D one fused launch per stage
+covers both directions).  The metric is cell-stage updates per second:
+cells x 3 stages x steps / time, summed over all ranks.
 
 Default workload: the 2D two-component stiffened-gas shock-bubble instance,
 400 x 200 cells on [0, 2] x [0, 1], adaptive moving mesh with 5 Jacobi sweeps

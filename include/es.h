@@ -271,9 +271,10 @@ es_status es_run_host(es_ctx* ctx, double* JU, double* J, double* x, int steps, 
  * around every kernel launch on the call's stream.  es_profile_read
  * synchronises, returns per class the summed milliseconds and the launch
  * count since the last read, then resets them.  Classes (n_classes <= 8):
- * 0..2 flux + divergence (+ RK stage) for directions 1..3, 3 metrics,
- * 4 mesh redistribution (CFL, monitor, filter, Jacobi, limiter, xdot),
- * 5 entropy diagnostics.  es_profile(ctx, 0) frees the events. */
+ * 0..2 flux + divergence (+ RK stage) for directions 1..3 (per-direction
+ * launches), 3 metrics, 4 mesh redistribution (CFL, monitor, filter, Jacobi,
+ * limiter, xdot), 5 entropy diagnostics, 6 the fused 2D stage launch (both
+ * directions, + RK stage).  es_profile(ctx, 0) frees the events. */
 es_status es_profile(es_ctx* ctx, int enable);
 es_status es_profile_read(es_ctx* ctx, double* ms, long long* launches, int n_classes);
 
