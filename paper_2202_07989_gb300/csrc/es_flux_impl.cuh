@@ -93,9 +93,11 @@ __device__ __forceinline__ void flux_stage(const FluxLaunch& L, int k, int wi, d
 // (2) every distinct two-point flux F(U_j, U_{j+m}) (m = 1, 2, 3) of the tile, once; (3)
 // per interface the 2w-order EC flux as sum_m alpha_m sum_s of the stored pairs, the GCL
 // flux of J xi_k/t and the ES dissipation; (4) divergence and output / RK stage.
-// FP32 tiles: 3 CTAs per SM in 2D (<= 85 registers), 2 in 3D; FP64 tiles: 1 (FP64-pipe bound)
+// FP32 tiles: 3 CTAs per SM (<= 85 registers) in 2D and for one species in 3D, 2 for two
+// species in 3D (whose tiles need more shared memory than 3 CTAs allow); FP64 tiles: 1
+// (FP64-pipe bound)
 template <int D, int NS, typename R, int S, int WT, int WK>
-__global__ void __launch_bounds__(FLUX_TPB, (sizeof(R) == 4 ? (D == 2 ? 3 : 2) : 1)) flux_kernel(FluxLaunch L)
+__global__ void __launch_bounds__(FLUX_TPB, (sizeof(R) == 4 ? ((D == 2 || NS == 1) ? 3 : 2) : 1)) flux_kernel(FluxLaunch L)
 {
     pdl_entry();
     using Y = Lay<D, NS>;
