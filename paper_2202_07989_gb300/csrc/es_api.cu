@@ -28,6 +28,7 @@ struct es_ctx {
     int2* w_ext = nullptr;  int n_ext = 0;
     int2* w_xe = nullptr;   int n_xe = 0;
     int2* w_cell = nullptr; int n_cell = 0;
+    int2* w_col = nullptr;  int n_col = 0;     // 3D: column chunks of the kernels marching along i3
     int2* w_flux[3][NSHAPE] = {};          // flux work list per direction and tile shape
     int n_flux[3][NSHAPE] = {};
     int2* w_fused[NFSHAPE] = {};           // fused 2D stage work list per fused tile shape
@@ -322,6 +323,17 @@ int flux_occ(es_ctx* c, int shape)
 #undef FO
 }
 
+// planes per chunk of the 3D kernels that march along i3: chunks enough for about four
+// waves of 3 CTAs per SM over the instance's columns, at least 4 planes a chunk
+int march_zc(const Inst& I, int sms)
+{
+    const long long cols = (long long)((I.n[0] + NT_X - 1) / NT_X) * ((I.n[1] + NT_Y - 1) / NT_Y);
+    long long chunks = (12LL * sms + cols - 1) / cols;
+    if (chunks > I.n[2]) chunks = I.n[2];
+    const int zc = (int)((I.n[2] + chunks - 1) / chunks);
+    return zc >= 4 ? zc : (I.n[2] < 4 ? I.n[2] : 4);
+}
+
 int node_grid(es_ctx* c, int nwork)
 {
     int cap = c->sms * 8;
@@ -507,8 +519,13 @@ void launch_mesh(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStream
         // 3^d evaluations per node)
         launch_monitor_theta(c->mixed, gc, st, c->dI, c->w_cell, c->n_cell, c->dS);
         for (int f = 0; f < nf; ++f) launch_filter(c->mixed, false, gc, st, c->dI, c->w_cell, c->n_cell, c->dS, f % 2);
-        for (int s = 0; s < mu; ++s)
-            launch_jacobi(c->mixed, c->d, s == mu - 1, gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS, s, th_sel);
+        for (int s = 0; s < mu; ++s) {
+            if (c->mixed && c->d == 3)
+                launch_jacobi3d(s == 0, s == mu - 1, node_grid(c, c->n_col), st, c->dI, c->w_col, c->n_col, c->dS, s,
+                                th_sel);
+            else
+                launch_jacobi(c->mixed, c->d, s == mu - 1, gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS, s, th_sel);
+        }
     }
     if (mu == 0) pdl_launch(limiter_kernel, gc, NODE_TPB, 0, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
     if (step && c->d == 2) launch_xdot_vel2d(c->mixed, node_grid(c, c->n_pad), st, c->dI, P, tab, c->w_pad, c->n_pad, c->dS);
@@ -579,6 +596,7 @@ es_status es_create_batch(const es_config* cfgs, int n_inst, es_ctx** out)
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
     for (int i = 0; i < n_inst; ++i) c->hI.push_back(make_inst(cfgs[i]));
+    for (Inst& I : c->hI) I.zc = I.d == 3 ? march_zc(I, c->sms) : 1;
     bool ok = true;
     ok = ok && dalloc(c, (void**)&c->dI, sizeof(Inst) * n_inst);
     size_t rsz = c->mixed ? sizeof(float) : sizeof(double);
@@ -603,7 +621,12 @@ es_status es_create_batch(const es_config* cfgs, int n_inst, es_ctx** out)
         ok = ok && dalloc(c, &S.th1, rsz * n);
         ok = ok && dalloc(c, (void**)&S.xa, sizeof(double) * I.d * n);
         ok = ok && dalloc(c, (void**)&S.xb, sizeof(double) * I.d * n);
-        if (c->mixed) ok = ok && dalloc(c, (void**)&S.dl, sizeof(float) * 2 * I.d * I.d * n);
+        if (c->mixed) {
+            // 2D: dl_{k+-} per node; 3D: the edge spacings E_k on the grid extended by one node below
+            long long nd = 2LL * I.d * I.d * n;
+            if (I.d == 3) nd = 9LL * (I.n[0] + 1) * (I.n[1] + 1) * (I.n[2] + 1);
+            ok = ok && dalloc(c, (void**)&S.dl, sizeof(float) * nd);
+        }
         ok = ok && dalloc(c, (void**)&S.zeros, sizeof(double) * I.d * n);
         if (ok) cudaMemset(S.zeros, 0, sizeof(double) * I.d * n);
         double *A = nullptr, *B = nullptr;
@@ -627,6 +650,7 @@ es_status es_create_batch(const es_config* cfgs, int n_inst, es_ctx** out)
     c->w_cell = build_work(c, [](const Inst& I) { return (long long)node_tiles(I, 0); }, c->n_cell);
     if (c->d == 3) c->w_ext = build_work(c, [](const Inst& I) { return (long long)node_tiles(I, 6); }, c->n_ext);
     if (c->d == 3) c->w_xe = build_work(c, [](const Inst& I) { return (long long)node_tiles(I, 9); }, c->n_xe);
+    if (c->d == 3) c->w_col = build_work(c, [](const Inst& I) { return (long long)col3_items(I); }, c->n_col);
     for (int k = 0; k < c->d; ++k)
         for (int sh = 0; sh < NSHAPE; ++sh) {
             c->w_flux[k][sh] = build_work(c, [k, sh](const Inst& I) { return flux_tiles(I, k, sh); }, c->n_flux[k][sh]);
@@ -655,7 +679,7 @@ es_status es_create_batch(const es_config* cfgs, int n_inst, es_ctx** out)
         c->fused_grid = c->sms * flux2d_occ(c, 0);
     }
     cudaError_t e = cudaDeviceSynchronize();
-    if (!ok || e != cudaSuccess || !c->w_pad || !c->w_cell || (c->d == 3 && (!c->w_ext || !c->w_xe))) {
+    if (!ok || e != cudaSuccess || !c->w_pad || !c->w_cell || (c->d == 3 && (!c->w_ext || !c->w_xe || !c->w_col))) {
         fprintf(stderr, "es_create: setup failed: %s\n", cudaGetErrorString(e));
         es_destroy(c);
         return ES_ERR_CUDA;

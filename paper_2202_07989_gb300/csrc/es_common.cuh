@@ -48,6 +48,7 @@ struct Inst {
     int weno;                 // ES_WENO_MR (0) or ES_WENO_JS (1)
     int fixed;                // 1: the mesh never moves
     int ntile_nodes;          // 1D node tiles for node-wise kernels
+    int zc;                   // 3D: planes per chunk of the kernels that march along i3
     // binary32 copies of the physical and scheme constants for the FP32 arithmetic of the
     // mixed form (converting the binary64 ones in the kernels would use the FP64 pipe)
     float f_gamma[2], f_cv[2], f_Rs[2], f_cvG[2], f_pinf_tot, f_chi[3], f_eps;
@@ -165,6 +166,27 @@ __host__ __device__ inline int node_tiles(const Inst& I, int pad)
 {
     int e0 = I.n[0] + 2 * pad, e1 = I.n[1] + 2 * pad, e2 = I.d == 3 ? I.n[2] + 2 * pad : 1;
     return ((e0 + NT_X - 1) / NT_X) * ((e1 + NT_Y - 1) / NT_Y) * e2;
+}
+
+// 3D kernels that march along i3: an item is a 32 x 8 column of the (i1, i2) plane and a
+// chunk of zc planes of it
+struct Col3 {
+    int b0, b1, z0, z1;
+};
+__host__ __device__ inline int col3_items(const Inst& I)
+{
+    return ((I.n[0] + NT_X - 1) / NT_X) * ((I.n[1] + NT_Y - 1) / NT_Y) * ((I.n[2] + I.zc - 1) / I.zc);
+}
+__device__ inline Col3 col3(const Inst& I, int item)
+{
+    const int ntx = (I.n[0] + NT_X - 1) / NT_X, nc = ntx * ((I.n[1] + NT_Y - 1) / NT_Y);
+    const int t = item % nc, ch = item / nc;
+    Col3 c;
+    c.b0 = (t % ntx) * NT_X;
+    c.b1 = (t / ntx) * NT_Y;
+    c.z0 = ch * I.zc;
+    c.z1 = min(I.n[2], c.z0 + I.zc);
+    return c;
 }
 
 // the node of this thread in node tile `tile` (ghost layers included); false outside the grid

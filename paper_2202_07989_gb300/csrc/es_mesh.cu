@@ -12,35 +12,6 @@ namespace es {
 // reduction slots per instance
 //   red[0] max_i sum_k rho_{i,k}/dxi_k,  red[1..4] max |grad sigma_s|,  red[5] Delta_tau
 
-template <typename T>
-__device__ inline T block_max(T v, T* sh)
-{
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    if (wid == 0) {
-        v = lane < (int)(blockDim.x >> 5) ? sh[lane] : T(0);
-        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    }
-    return v;
-}
-
-__device__ inline double block_min_pos(double v, double* sh)
-{
-    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    if (wid == 0) {
-        v = lane < (int)(blockDim.x >> 5) ? sh[lane] : 1.0;
-        for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-    }
-    return v;
-}
-
 __device__ inline void node_coords(const Inst& I, long long p, int& i0, int& i1, int& i2)
 {
     i0 = (int)(p % I.n[0]);
@@ -593,34 +564,6 @@ __global__ void jacobi_kernel(const Inst* __restrict__ insts, StagePtrs single, 
             double m = block_min_pos(bnd, sh);
             if (threadIdx.x == 0) atomic_min_pos(&scr[it.x].red[5], m);
         }
-    }
-}
-
-// binary32 displacement y = x - x^n at a node reached along grid lines: periodic wrap
-// (the shift cancels), wall mirror negates the mirrored component
-__device__ inline void y_at(const Inst& I, const float* __restrict__ y, int i0, int i1, int i2, float* out)
-{
-    int i[3] = { i0, i1, i2 };
-    bool flip[3] = { false, false, false };
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        if (k >= I.d) break;
-        const int n = I.n[k];
-        if (i[k] >= 0 && i[k] < n) continue;
-        const int side = i[k] < 0 ? 0 : 1;
-        if (I.bc[k][side] == BC_PERIODIC) {
-            i[k] -= floordiv_(i[k], n) * n;
-        } else {
-            i[k] = side == 0 ? -1 - i[k] : 2 * n - 1 - i[k];
-            flip[k] = true;
-        }
-    }
-    const long long id = lin(I, i[0], i[1], I.d == 3 ? i[2] : 0);
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        if (j >= I.d) break;
-        const float v = y[j * I.ncell + id];
-        out[j] = flip[j] ? -v : v;
     }
 }
 

@@ -5,6 +5,63 @@
 
 namespace es {
 
+template <typename T>
+__device__ inline T block_max(T v, T* sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? sh[lane] : T(0);
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    }
+    return v;
+}
+
+__device__ inline double block_min_pos(double v, double* sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? sh[lane] : 1.0;
+        for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    }
+    return v;
+}
+
+// binary32 displacement y = x - x^n at a node reached along grid lines: periodic wrap
+// (the shift cancels), wall mirror negates the mirrored component
+__device__ inline void y_at(const Inst& I, const float* __restrict__ y, int i0, int i1, int i2, float* out)
+{
+    int i[3] = { i0, i1, i2 };
+    bool flip[3] = { false, false, false };
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (k >= I.d) break;
+        const int n = I.n[k];
+        if (i[k] >= 0 && i[k] < n) continue;
+        const int side = i[k] < 0 ? 0 : 1;
+        if (I.bc[k][side] == BC_PERIODIC) {
+            i[k] -= floordiv_(i[k], n) * n;
+        } else {
+            i[k] = side == 0 ? -1 - i[k] : 2 * n - 1 - i[k];
+            flip[k] = true;
+        }
+    }
+    const long long id = lin(I, i[0], i[1], I.d == 3 ? i[2] : 0);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        if (j >= I.d) break;
+        const float v = y[j * I.ncell + id];
+        out[j] = flip[j] ? -v : v;
+    }
+}
+
 void launch_cfl_grad(bool mixed, int d, int N, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
                      const StagePtrs* table, const int2* work, int nwork, const Scratch* scr);
 void launch_xdot(bool mixed, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
@@ -24,6 +81,9 @@ void prepare_mesh();    // kernel attributes, once per context
 void launch_jacobi_fused2d(int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
                            const StagePtrs* table, const int2* work, int nwork, const Scratch* scr, int H, int F,
                            int theta_sel);
+// mixed form, 3D: one Jacobi sweep marching along i3 over the column items of col3 (es_mesh3d.cu)
+void launch_jacobi3d(bool first, bool last, int grid, cudaStream_t st, const Inst* insts, const int2* work, int nwork,
+                     const Scratch* scr, int sweep, int theta_sel);
 void launch_jacobi(bool mixed, int d, bool last, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
                    const StagePtrs* table, const int2* work, int nwork, const Scratch* scr, int sweep, int theta_sel);
 __global__ void limiter_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work, int nwork,

@@ -1,0 +1,328 @@
+// Mixed form, 3D: the node kernels of the mesh step that march along i3 (2.5D blocking).
+// A block owns a 32 x 8 column of the (i1, i2) plane and a chunk of zc planes of it.  The
+// planes it reads (its nodes plus a one-node halo in i1 and i2) sit in a ring of shared-memory
+// planes: the ghost maps of the boundary conditions are applied once, when a plane is staged,
+// and every node value is loaded once per pass plus the halo, so the stencil arithmetic runs
+// without boundary branches.  The arithmetic per node is that of the per-node kernels
+// (jacobi_y_kernel, filter_kernel), term for term.
+#include "es_mesh.cuh"
+
+namespace es {
+
+constexpr int M3_TX = NT_X, M3_TY = NT_Y;               // 32 x 8 node columns
+constexpr int M3_PX = M3_TX + 2, M3_PY = M3_TY + 2;     // a staged plane: the column and its halo
+constexpr int M3_NH = 2 * M3_TX + 2 * M3_TY;            // halo slots of a plane (no corners)
+static_assert(M3_TX == 32 && M3_TX * M3_TY == NODE_TPB, "one warp per row of a column");
+static_assert(M3_NH <= NODE_TPB, "one halo slot per thread at most");
+
+// the halo slot h of a staged plane (slot coordinates a in [0, M3_PX), b in [0, M3_PY))
+__device__ __forceinline__ void m3_halo_slot(int h, int& a, int& b)
+{
+    if (h < M3_TX) { a = h + 1; b = 0; }
+    else if (h < 2 * M3_TX) { a = h - M3_TX + 1; b = M3_PY - 1; }
+    else if (h < 2 * M3_TX + M3_TY) { a = 0; b = h - 2 * M3_TX + 1; }
+    else { a = M3_PX - 1; b = h - 2 * M3_TX - M3_TY + 1; }
+}
+
+// Theta (and with WITH_Y the binary32 displacement) at node (g0, g1, g2), which lies at most
+// one node outside the grid in one direction: the maps of s_map and y_at at a ghost node.
+// Other positions (outside in two directions, or further out) are no face neighbour of any
+// node of the grid and read as zero.
+template <bool WITH_Y>
+__device__ __forceinline__ void m3_node(const Inst& I, const float* __restrict__ ys, const float* __restrict__ th,
+                                        int g0, int g1, int g2, float y[3], float& t)
+{
+    const int n0 = I.n[0], n1 = I.n[1], n2 = I.n[2];
+    const bool o0 = g0 < 0 || g0 >= n0, o1 = g1 < 0 || g1 >= n1, o2 = g2 < 0 || g2 >= n2;
+    y[0] = y[1] = y[2] = 0.0f;
+    t = 0.0f;
+    if (g0 < -1 || g0 > n0 || g1 < -1 || g1 > n1 || g2 < -1 || g2 > n2 || (int)o0 + (int)o1 + (int)o2 > 1) return;
+    if (!(o0 || o1 || o2)) {
+        const long long p = ((long long)g2 * n1 + g1) * n0 + g0;
+        t = th[p];
+        if (WITH_Y) {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) y[j] = ys[j * I.ncell + p];
+        }
+    } else {
+        t = th[s_map(I, g0, g1, g2)];
+        if (WITH_Y) y_at(I, ys, g0, g1, g2, y);
+    }
+}
+
+// Mesh spacings of the mixed Jacobi sweeps, stored once per edge: E_k[j] at node i is
+// x^n_j(i + e_k) - x^n_j(i) formed in FP64 and rounded to binary32, on the grid extended by
+// one node below in every direction (entry i_k = -1 is the edge from the ghost node to the
+// first node).  The sweep reads dl_{k+}(i) = E_k(i) and dl_{k-}(i) = -E_k(i - e_k): rounding
+// to nearest is symmetric, so the negated entry is the rounded difference taken the other way.
+struct Edges3 {
+    long long ne;                 // (n0 + 1)(n1 + 1)(n2 + 1)
+    int x0, x1;                   // n0 + 1, n1 + 1
+    __device__ explicit Edges3(const Inst& I) : x0(I.n[0] + 1), x1(I.n[1] + 1)
+    {
+        ne = (long long)x0 * x1 * (I.n[2] + 1);
+    }
+    __device__ long long at(int g0, int g1, int g2) const
+    {
+        return ((long long)(g2 + 1) * x1 + (g1 + 1)) * x0 + (g0 + 1);
+    }
+};
+
+// the three components of E_k at node g from the 9-layer ghost-extended positions XE
+__device__ __forceinline__ void m3_edge_xe(const Inst& I, const double* __restrict__ XE, int k, int g0, int g1,
+                                           int g2, float e[3])
+{
+    const long long X0 = I.n[0] + 18, X1 = I.n[1] + 18, nx = X0 * X1 * (I.n[2] + 18);
+    const long long c = ((long long)(g2 + 9) * X1 + (g1 + 9)) * X0 + (g0 + 9);
+    const long long s = k == 0 ? 1 : (k == 1 ? X0 : X0 * X1);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) e[j] = f64_to_f32(XE[j * nx + c + s] - XE[j * nx + c]);
+}
+
+// E_k of plane q at this thread's node (k = 0, 1, 2), E_0 left of its row (lane 0) and E_1
+// below its column's first row (warp 0); zero where no node is, and all zero unless act.  FIRST forms them from XE
+// and stores each entry once: a node's own edges, and the edges from the ghost nodes below
+// the grid where the column touches the low boundary.
+template <bool FIRST>
+__device__ __forceinline__ void m3_edges(const Inst& I, const Scratch& Sc, const Edges3& EG, const Col3& C, int g0,
+                                         int g1, int q, bool act, float ep[3][3], float e0h[3], float e1h[3])
+{
+    float* E = Sc.dl;
+    const bool valid = act && g0 < I.n[0] && g1 < I.n[1];
+    const bool left = act && g0 == C.b0 && g1 < I.n[1], below = act && g1 == C.b1 && g0 < I.n[0];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        e0h[j] = 0.0f;
+        e1h[j] = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) ep[k][j] = 0.0f;
+    }
+    if (FIRST) {
+        if (valid) {
+            const long long e = EG.at(g0, g1, q);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                m3_edge_xe(I, Sc.XE, k, g0, g1, q, ep[k]);
+#pragma unroll
+                for (int j = 0; j < 3; ++j) E[(k * 3 + j) * EG.ne + e] = ep[k][j];
+            }
+        }
+        if (left) {
+            m3_edge_xe(I, Sc.XE, 0, C.b0 - 1, g1, q, e0h);
+            if (C.b0 == 0) {
+#pragma unroll
+                for (int j = 0; j < 3; ++j) E[j * EG.ne + EG.at(-1, g1, q)] = e0h[j];
+            }
+        }
+        if (below) {
+            m3_edge_xe(I, Sc.XE, 1, g0, C.b1 - 1, q, e1h);
+            if (C.b1 == 0) {
+#pragma unroll
+                for (int j = 0; j < 3; ++j) E[(3 + j) * EG.ne + EG.at(g0, -1, q)] = e1h[j];
+            }
+        }
+    } else {
+        if (valid) {
+            const long long e = EG.at(g0, g1, q);
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) ep[k][j] = E[(k * 3 + j) * EG.ne + e];
+        }
+        if (left) {
+            const long long e = EG.at(C.b0 - 1, g1, q);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) e0h[j] = E[j * EG.ne + e];
+        }
+        if (below) {
+            const long long e = EG.at(g0, C.b1 - 1, q);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) e1h[j] = E[(3 + j) * EG.ne + e];
+        }
+    }
+}
+
+// E_2 of the plane below the chunk (the minus-i3 spacing of the chunk's first plane)
+template <bool FIRST>
+__device__ __forceinline__ void m3_edge_below(const Inst& I, const Scratch& Sc, const Edges3& EG, int g0, int g1,
+                                              int z0, float e[3])
+{
+    e[0] = e[1] = e[2] = 0.0f;
+    if (g0 >= I.n[0] || g1 >= I.n[1]) return;
+    const long long a = EG.at(g0, g1, z0 - 1);
+    if (FIRST) {
+        m3_edge_xe(I, Sc.XE, 2, g0, g1, z0 - 1, e);
+        if (z0 == 0) {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) Sc.dl[(6 + j) * EG.ne + a] = e[j];
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) e[j] = Sc.dl[(6 + j) * EG.ne + a];
+    }
+}
+
+// One mixed Jacobi sweep of a 3D instance, with the arithmetic of jacobi_y_kernel:
+// y_i <- sum_{k,s} w_{k,s} (dl_{k,s} + y_{i+-e_k}) / sum_{k,s} w_{k,s}, w_{k,s} = (Theta_i +
+// Theta_{i+-e_k}) / 2 / dxi_k^2, in the order k = 1, 2, 3 with the minus side first.  FIRST:
+// y = 0, and the spacings are formed from XE (x^n with its ghost maps, staged by the metrics
+// pass that opens the mesh step) and stored; LAST: the limiter bounds of Sec. 4,
+// dl_{k,s}[k] / (2 y_k) with s the sign of y_k, reduced to the instance minimum.
+template <bool FIRST, bool LAST>
+__global__ void __launch_bounds__(NODE_TPB, 3) jacobi3d_kernel(const Inst* __restrict__ insts,
+                                                                const int2* __restrict__ work, int nwork,
+                                                                const Scratch* __restrict__ scr, int sweep,
+                                                                int theta_sel)
+{
+    pdl_entry();
+    __shared__ float sy[FIRST ? 1 : 4][3][M3_PY][M3_PX];
+    __shared__ float sth[4][M3_PY][M3_PX];
+    __shared__ float se1[2][3][M3_TY][M3_TX];
+    __shared__ double sh[32];
+    const int lx = (int)threadIdx.x % M3_TX, ly = (int)threadIdx.x / M3_TX;
+    int ha = -1, hb = -1;
+    if ((int)threadIdx.x < M3_NH) m3_halo_slot((int)threadIdx.x, ha, hb);
+    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+        const int2 it = work[wi];
+        const Inst& I = insts[it.x];
+        const Scratch& Sc = scr[it.x];
+        const Col3 C = col3(I, it.y);
+        const Edges3 EG(I);
+        const long long n = I.ncell;
+        const float* th = reinterpret_cast<const float*>(theta_sel ? Sc.th1 : Sc.th0);
+        const float* ys = reinterpret_cast<const float*>(sweep % 2 == 1 ? Sc.xa : Sc.xb);
+        float* yd = reinterpret_cast<float*>(sweep % 2 == 0 ? Sc.xa : Sc.xb);
+        const int g0 = C.b0 + lx, g1 = C.b1 + ly, h0 = C.b0 - 1 + ha, h1 = C.b1 - 1 + hb;
+        const bool valid = g0 < I.n[0] && g1 < I.n[1];
+        __syncthreads();    // the previous item's readers of the ring are done
+        // planes z0 - 1, z0 and z0 + 1 into the ring (z0 + 1 <= z1: the plane above the chunk
+        // is a grid plane or the ghost plane i3 = n3)
+        for (int q = C.z0 - 1; q <= C.z0 + 1; ++q) {
+            float yo[3], to, yh[3], tv;
+            m3_node<!FIRST>(I, ys, th, g0, g1, q, yo, to);
+            if (ha >= 0) m3_node<!FIRST>(I, ys, th, h0, h1, q, yh, tv);
+            const int s = q & 3;
+            sth[s][ly + 1][lx + 1] = to;
+            if (ha >= 0) sth[s][hb][ha] = tv;
+            if (!FIRST) {
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    sy[FIRST ? 0 : s][j][ly + 1][lx + 1] = yo[j];
+                    if (ha >= 0) sy[FIRST ? 0 : s][j][hb][ha] = yh[j];
+                }
+            }
+        }
+        float ep[3][3], e0h[3], e1h[3], em2[3];
+        m3_edges<FIRST>(I, Sc, EG, C, g0, g1, C.z0, true, ep, e0h, e1h);
+        m3_edge_below<FIRST>(I, Sc, EG, g0, g1, C.z0, em2);
+        float bnd = 1.0f;
+        for (int z = C.z0; z < C.z1; ++z) {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) se1[z & 1][j][ly][lx] = ep[1][j];
+            __syncthreads();
+            // loads of the next planes: Theta and y of plane z + 2, the edges of plane z + 1
+            const bool more = z + 2 <= C.z1;
+            float yo[3], to, yh[3], tv;
+            if (more) {
+                m3_node<!FIRST>(I, ys, th, g0, g1, z + 2, yo, to);
+                if (ha >= 0) m3_node<!FIRST>(I, ys, th, h0, h1, z + 2, yh, tv);
+            }
+            float epn[3][3], e0n[3], e1n[3];
+            m3_edges<FIRST>(I, Sc, EG, C, g0, g1, z + 1, z + 1 < C.z1, epn, e0n, e1n);
+            // the minus-side spacings of this node: E_0 of the left neighbour (the lane
+            // before), E_1 of the node below (the row before), E_2 of the plane below
+            float em[3][3];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const float l = __shfl_up_sync(0xffffffffu, ep[0][j], 1);
+                em[0][j] = lx == 0 ? e0h[j] : l;
+                em[1][j] = ly == 0 ? e1h[j] : se1[z & 1][j][ly - 1][lx];
+                em[2][j] = em2[j];
+            }
+            if (valid) {
+                const int c = z & 3, m = (z - 1) & 3, pp = (z + 1) & 3;
+                const float tc = sth[c][ly + 1][lx + 1];
+                const float tn[3][2] = { { sth[c][ly + 1][lx], sth[c][ly + 1][lx + 2] },
+                                         { sth[c][ly][lx + 1], sth[c][ly + 2][lx + 1] },
+                                         { sth[m][ly + 1][lx + 1], sth[pp][ly + 1][lx + 1] } };
+                float num[3] = { 0.0f, 0.0f, 0.0f }, den = 0.0f, dk[3][2];
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+#pragma unroll
+                    for (int s = 0; s < 2; ++s) {
+                        const float w = 0.5f * (tc + tn[k][s]) * I.f_h2[k];
+                        float dv[3], yv[3];
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) {
+                            dv[j] = s ? ep[k][j] : -em[k][j];
+                            if (FIRST) {
+                                yv[j] = 0.0f;
+                            } else {
+                                const int b = FIRST ? 0 : c;
+                                yv[j] = k == 0 ? sy[b][j][ly + 1][lx + 2 * s]
+                                      : (k == 1 ? sy[b][j][ly + 2 * s][lx + 1] : sy[FIRST ? 0 : (s ? pp : m)][j][ly + 1][lx + 1]);
+                            }
+                        }
+                        dk[k][s] = dv[k];
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) num[j] = fmaf(w, dv[j] + yv[j], num[j]);
+                        den += w;
+                    }
+                float ynew[3];
+                const long long p = ((long long)z * I.n[1] + g1) * I.n[0] + g0;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    ynew[j] = num[j] / den;
+                    yd[j * n + p] = ynew[j];
+                }
+                if (LAST) {
+                    float b = 1.0f;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        const float dx = ynew[k];
+                        if (dx < 0.0f) b = fminf(b, dk[k][0] / (2.0f * dx));
+                        else if (dx > 0.0f) b = fminf(b, dk[k][1] / (2.0f * dx));
+                    }
+                    if (!(b >= 0.0f)) b = 0.0f;
+                    bnd = fminf(bnd, b);
+                }
+            }
+            // plane z + 2 into the ring: its slot last held plane z - 2, read at plane z - 1
+            if (more) {
+                const int s = (z + 2) & 3;
+                sth[s][ly + 1][lx + 1] = to;
+                if (ha >= 0) sth[s][hb][ha] = tv;
+                if (!FIRST) {
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        sy[FIRST ? 0 : s][j][ly + 1][lx + 1] = yo[j];
+                        if (ha >= 0) sy[FIRST ? 0 : s][j][hb][ha] = yh[j];
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                em2[j] = ep[2][j];
+                e0h[j] = e0n[j];
+                e1h[j] = e1n[j];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) ep[k][j] = epn[k][j];
+            }
+        }
+        if (LAST) {
+            const double mb = block_min_pos(f32_to_f64(bnd), sh);
+            if (threadIdx.x == 0) atomic_min_pos(&Sc.red[5], mb);
+        }
+    }
+}
+
+void launch_jacobi3d(bool first, bool last, int grid, cudaStream_t st, const Inst* insts, const int2* work, int nwork,
+                     const Scratch* scr, int sweep, int theta_sel)
+{
+#define J3(F, L) pdl_launch(jacobi3d_kernel<F, L>, grid, NODE_TPB, 0, st, insts, work, nwork, scr, sweep, theta_sel)
+    if (first) { if (last) J3(true, true); else J3(true, false); }
+    else { if (last) J3(false, true); else J3(false, false); }
+#undef J3
+}
+
+}  // namespace es
