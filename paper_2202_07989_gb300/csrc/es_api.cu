@@ -503,7 +503,10 @@ void launch_mesh(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStream
     launch_metrics(c, Q, tab, st, true, false, c->hI[0].fixed != 0);
     ProfScope ps(c, PC_MESH, st);
     int gc = node_grid(c, c->n_cell);
-    launch_cfl_grad(c->mixed, c->d, c->N, gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
+    if (c->mixed && c->d == 3)
+        launch_cfl_grad3d(c->N, gc, node_grid(c, c->n_col), st, c->dI, P, tab, c->w_cell, c->n_cell, c->w_col, c->n_col,
+                          c->dS, c->hI[0].n_sigma > 0 || c->n_inst > 1);
+    else launch_cfl_grad(c->mixed, c->d, c->N, gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
     if (c->hI[0].fixed) {
         // fixed mesh: Delta t only; xdot = 0 (the metrics above carry no VCL part)
         launch_xdot(c->mixed, gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
@@ -518,7 +521,10 @@ void launch_mesh(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStream
         // Theta once per node, then plain filter passes (forming it inside the first pass costs
         // 3^d evaluations per node)
         launch_monitor_theta(c->mixed, gc, st, c->dI, c->w_cell, c->n_cell, c->dS);
-        for (int f = 0; f < nf; ++f) launch_filter(c->mixed, false, gc, st, c->dI, c->w_cell, c->n_cell, c->dS, f % 2);
+        for (int f = 0; f < nf; ++f) {
+            if (c->mixed && c->d == 3) launch_filter3d(node_grid(c, c->n_col), st, c->dI, c->w_col, c->n_col, c->dS, f % 2);
+            else launch_filter(c->mixed, false, gc, st, c->dI, c->w_cell, c->n_cell, c->dS, f % 2);
+        }
         for (int s = 0; s < mu; ++s) {
             if (c->mixed && c->d == 3)
                 launch_jacobi3d(s == 0, s == mu - 1, node_grid(c, c->n_col), st, c->dI, c->w_col, c->n_col, c->dS, s,

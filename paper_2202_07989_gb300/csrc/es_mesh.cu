@@ -229,8 +229,9 @@ __device__ __forceinline__ unsigned long long shfl_max(unsigned long long k, int
 __device__ __forceinline__ double key_value(unsigned int k) { return to_d(__uint_as_float(k)); }
 __device__ __forceinline__ double key_value(unsigned long long k) { return __longlong_as_double((long long)k); }
 
-// sigma_t of a 2D instance with NS species (the same arithmetic, with the field indices known)
-template <typename R, int NS>
+// sigma_t of a D-dimensional instance with NS species (the same arithmetic, with the field
+// indices known)
+template <typename R, int NS, int D = 2>
 __device__ __forceinline__ R sigma2d(const Inst& I, int kind, const R* U)
 {
     const R rho = NS == 2 ? U[0] + U[1] : U[0];
@@ -244,8 +245,8 @@ __device__ __forceinline__ R sigma2d(const Inst& I, int kind, const R* U)
 #pragma unroll
         for (int l = 0; l < NS; ++l) { cvr += to_r<R>(I.cv[l]) * U[l]; rr += to_r<R>(I.Rs[l]) * U[l]; }
 #pragma unroll
-        for (int m = 0; m < 2; ++m) { R v = U[NS + m] / rho; v2 += v * v; }
-        R T = (U[NS + 2] - R(0.5) * rho * v2 - to_r<R>(I.pinf_tot)) / cvr;
+        for (int m = 0; m < D; ++m) { R v = U[NS + m] / rho; v2 += v * v; }
+        R T = (U[NS + D] - R(0.5) * rho * v2 - to_r<R>(I.pinf_tot)) / cvr;
         return rr * T - to_r<R>(I.pinf_tot);
     }
     default: return rho;
@@ -392,6 +393,219 @@ __global__ void __launch_bounds__(NODE_TPB) cfl_grad2d_kernel(const Inst* __rest
             K m = sred[threadIdx.x][0];
             for (int w = 1; w < NW; ++w) m = max(m, sred[threadIdx.x][w]);
             atomic_max_pos(&Sc.red[threadIdx.x], key_value(m));
+        }
+    }
+}
+
+// cfl_grad_kernel for 3D instances in the mixed form, in two passes with the same terms.
+// Pass 1, one node per thread: the CFL spectral-radius sum of Eq. (cfl) with the metrics of
+// x^n, and sigma_s of the node state, stored behind the gradients in the gradient buffer.
+template <int NS>
+__global__ void __launch_bounds__(NODE_TPB) cfl_sigma3d_kernel(const Inst* __restrict__ insts, StagePtrs single,
+                                                                const StagePtrs* __restrict__ table,
+                                                                const int2* __restrict__ work, int nwork,
+                                                                const Scratch* __restrict__ scr)
+{
+    pdl_entry();
+    using R = float;
+    using K = unsigned int;
+    constexpr int NC = NS + 4, NW = NODE_TPB / 32;
+    __shared__ K sred[NW];
+    const int lane = (int)threadIdx.x & 31, wid = (int)threadIdx.x >> 5;
+    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+        const int2 it = work[wi];
+        const Inst& I = insts[it.x];
+        ES_PTRS(P);
+        const Scratch& Sc = scr[it.x];
+        int i0, i1, i2;
+        K kc = 0;
+        if (tile_node(I, it.y, 0, i0, i1, i2)) {
+            const long long p = lin(I, i0, i1, i2), pid = plin(I, i0, i1, i2);
+            double mraw[9];
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) mraw[3 * k + j] = Sc.M[(long long)(k * 4 + 1 + j) * I.npad + pid];
+            R U[NC];
+            const R Jp = to_r<R>(P.J[p]);
+            const R inv = R(1) / Jp;
+#pragma unroll
+            for (int f = 0; f < NC; ++f) U[f] = to_r<R>(P.JU[f * I.ncell + p]) * inv;
+            float* sg = grad_r<R>(Sc) + (long long)I.n_sigma * I.ncell;
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+                if (s < I.n_sigma) sg[(long long)s * I.ncell + p] = sigma2d<R, NS, 3>(I, I.sigma[s], U);
+            const R rho = U[0] + (NS == 2 ? U[1] : R(0));
+            R v[3], v2 = R(0), cvr = R(0), ar = R(0), gm = R(0);
+#pragma unroll
+            for (int m = 0; m < 3; ++m) { v[m] = U[NS + m] / rho; v2 += v[m] * v[m]; }
+#pragma unroll
+            for (int l = 0; l < NS; ++l) {
+                ar += Cst<R>::Rs(I, l) * U[l];          // (Gamma_l - 1) c_v,l rho_l
+                gm += Cst<R>::cvG(I, l) * U[l];         // Gamma_l c_v,l rho_l
+                cvr += Cst<R>::cv(I, l) * U[l];
+            }
+            const R T = (U[NC - 1] - R(0.5) * rho * v2 - Cst<R>::pinf(I)) / cvr;
+            const R c = sqrt((ar / rho) * (gm / cvr) * T);
+            R sr = R(0);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                R L2 = R(0), vn = R(0);
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const R mk = to_r<R>(mraw[3 * k + j]);
+                    L2 += mk * mk;
+                    vn += mk * v[j];
+                }
+                sr += (fabs(vn) + c * sqrt(L2)) / Jp * inv_dxi_r<R>(I, k);
+            }
+            if (!(sr >= R(0))) sr = R(0);
+            kc = max_key(sr);
+        }
+        for (int o = 16; o > 0; o >>= 1) kc = shfl_max(kc, o);
+        __syncthreads();    // the previous item's readers of sred are done
+        if (lane == 0) sred[wid] = kc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            K mx = sred[0];
+            for (int w = 1; w < NW; ++w) mx = max(mx, sred[w]);
+            atomic_max_pos(&Sc.red[0], key_value(mx));
+        }
+    }
+}
+
+// sigma_s (s < n_sigma) at position g of a staged plane, at most one node outside the grid in
+// one direction: at a ghost node, the value of the mapped node (load_U's maps), with v_1
+// negated across a wall normal to i1 (the only monitor variable the reflection changes) and
+// the inflow state's values on an inflow side
+template <int NS>
+__device__ __forceinline__ void grad3d_sigma(const Inst& I, const float* __restrict__ sg, int g0, int g1, int g2,
+                                             float v[4])
+{
+    v[0] = v[1] = v[2] = v[3] = 0.0f;
+    const int ns = I.n_sigma;
+    int i[3] = { g0, g1, g2 }, kk = -1, out = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (i[k] < -1 || i[k] > I.n[k]) return;
+        if (i[k] < 0 || i[k] >= I.n[k]) { kk = k; ++out; }
+    }
+    if (out > 1) return;
+    int tmap = 0, side = 0;
+    if (kk >= 0) {
+        int gi;
+        tmap = map_line(I, kk, kk == 0 ? i[0] : (kk == 1 ? i[1] : i[2]), gi, side);
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            if (k == kk) i[k] = gi;     // (unrolled: i stays in registers)
+    }
+    if (tmap == 2) {
+        float U[MAXC];
+#pragma unroll
+        for (int f = 0; f < NS + 4; ++f) U[f] = to_r<float>(I.inflow[kk][side][f]);
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+            if (s < ns) v[s] = sigma2d<float, NS, 3>(I, I.sigma[s], U);
+        return;
+    }
+    const long long p = lin(I, i[0], i[1], i[2]);
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        if (s >= ns) break;
+        v[s] = sg[(long long)s * I.ncell + p];
+        if (tmap == 1 && kk == 0 && I.sigma[s] == SIG_V1) v[s] = -v[s];
+    }
+}
+
+// Pass 2, marching along i3 over the column items of col3: per monitor term |grad_xi sigma|
+// or |Laplacian_xi sigma| (second-order central differences) from sigma_s staged plane by
+// plane (the column and its one-node halo, in a ring of four planes), the instance maxima by
+// one block reduction per item (integer keys of the non-negative maxima).
+template <int NS>
+__global__ void __launch_bounds__(NODE_TPB) grad3d_kernel(const Inst* __restrict__ insts,
+                                                          const int2* __restrict__ work, int nwork,
+                                                          const Scratch* __restrict__ scr)
+{
+    pdl_entry();
+    using R = float;
+    using K = unsigned int;
+    constexpr int NW = NODE_TPB / 32;
+    __shared__ R ssig[4][4][M3_PY][M3_PX];
+    __shared__ K sred[4][NW];
+    const int lx = (int)threadIdx.x % M3_TX, ly = (int)threadIdx.x / M3_TX;
+    const int lane = (int)threadIdx.x & 31, wid = (int)threadIdx.x >> 5;
+    int ha = -1, hb = -1;
+    if ((int)threadIdx.x < M3_NH) m3_halo_slot((int)threadIdx.x, ha, hb);
+    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+        const int2 it = work[wi];
+        const Inst& I = insts[it.x];
+        const Scratch& Sc = scr[it.x];
+        const Col3 C = col3(I, it.y);
+        const int ns = I.n_sigma;
+        const float* sg = grad_r<R>(Sc) + (long long)ns * I.ncell;
+        const int g0 = C.b0 + lx, g1 = C.b1 + ly, h0 = C.b0 - 1 + ha, h1 = C.b1 - 1 + hb;
+        const bool valid = g0 < I.n[0] && g1 < I.n[1];
+        K kmax[4] = { 0, 0, 0, 0 };
+        float vo[4], vh[4] = { 0.0f, 0.0f, 0.0f, 0.0f };
+        auto put = [&](int q) {
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                ssig[q & 3][s][ly + 1][lx + 1] = vo[s];
+                if (ha >= 0) ssig[q & 3][s][hb][ha] = vh[s];
+            }
+        };
+        __syncthreads();    // the previous item's readers are done
+        for (int q = C.z0 - 1; q <= C.z0 + 1; ++q) {
+            grad3d_sigma<NS>(I, sg, g0, g1, q, vo);
+            if (ha >= 0) grad3d_sigma<NS>(I, sg, h0, h1, q, vh);
+            put(q);
+        }
+        for (int z = C.z0; z < C.z1; ++z) {
+            __syncthreads();
+            // plane z + 2 into registers, into the ring after this plane's terms (its slot last
+            // held plane z - 2, read at plane z - 1)
+            const bool more = z + 2 <= C.z1;
+            if (more) {
+                grad3d_sigma<NS>(I, sg, g0, g1, z + 2, vo);
+                if (ha >= 0) grad3d_sigma<NS>(I, sg, h0, h1, z + 2, vh);
+            }
+            if (valid) {
+                const long long p = lin(I, g0, g1, z);
+                const int c = z & 3, m = (z - 1) & 3, pp = (z + 1) & 3;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (q >= ns) break;
+                    const R sc = ssig[c][q][ly + 1][lx + 1];
+                    R gr = R(0), lp = R(0);
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        const R hk = R(0.5) * inv_dxi_r<R>(I, k);
+                        const R h2 = inv_dxi_r<R>(I, k) * inv_dxi_r<R>(I, k);
+                        const R sp = k == 0 ? ssig[c][q][ly + 1][lx + 2] : (k == 1 ? ssig[c][q][ly + 2][lx + 1] : ssig[pp][q][ly + 1][lx + 1]);
+                        const R sm = k == 0 ? ssig[c][q][ly + 1][lx] : (k == 1 ? ssig[c][q][ly][lx + 1] : ssig[m][q][ly + 1][lx + 1]);
+                        const R gk = (sp - sm) * hk;
+                        gr += gk * gk;
+                        lp += (sp - R(2) * sc + sm) * h2;
+                    }
+                    R gq = I.sigma_op[q] == MON_LAP ? R(fabs(lp)) : R(sqrt(gr));
+                    grad_r<R>(Sc)[(long long)q * I.ncell + p] = gq;
+                    if (!(gq >= R(0))) gq = R(0);
+                    kmax[q] = max(kmax[q], max_key(gq));
+                }
+            }
+            if (more) put(z + 2);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            for (int o = 16; o > 0; o >>= 1) kmax[r] = shfl_max(kmax[r], o);
+        __syncthreads();    // the previous item's readers of sred are done
+        if (lane == 0)
+            for (int r = 0; r < 4; ++r) sred[r][wid] = kmax[r];
+        __syncthreads();
+        if ((int)threadIdx.x < ns) {
+            K mx = sred[threadIdx.x][0];
+            for (int w = 1; w < NW; ++w) mx = max(mx, sred[threadIdx.x][w]);
+            atomic_max_pos(&Sc.red[1 + threadIdx.x], key_value(mx));
         }
     }
 }
@@ -953,6 +1167,7 @@ size_t jacobi_fused2d_smem(int H, int F)
 
 void prepare_mesh()
 {
+    prepare_mesh3d();
     cudaFuncSetAttribute(jacobi_fused2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)jacobi_fused2d_smem(JACOBI_FUSED_MAX, FILTER_FUSED_MAX));
 }
@@ -1406,6 +1621,17 @@ void launch_cfl_grad(bool mixed, int d, int N, int grid, cudaStream_t st, const 
     }
     if (mixed) pdl_launch(cfl_grad_kernel<float>, grid, NODE_TPB, 0, st, insts, single, table, work, nwork, scr);
     else pdl_launch(cfl_grad_kernel<double>, grid, NODE_TPB, 0, st, insts, single, table, work, nwork, scr);
+}
+
+void launch_cfl_grad3d(int N, int grid_cell, int grid_col, cudaStream_t st, const Inst* insts, const StagePtrs& single,
+                       const StagePtrs* table, const int2* w_cell, int n_cell, const int2* w_col, int n_col,
+                       const Scratch* scr, bool monitor)
+{
+    if (N == 1) pdl_launch(cfl_sigma3d_kernel<1>, grid_cell, NODE_TPB, 0, st, insts, single, table, w_cell, n_cell, scr);
+    else pdl_launch(cfl_sigma3d_kernel<2>, grid_cell, NODE_TPB, 0, st, insts, single, table, w_cell, n_cell, scr);
+    if (!monitor) return;
+    if (N == 1) pdl_launch(grad3d_kernel<1>, grid_col, NODE_TPB, 0, st, insts, w_col, n_col, scr);
+    else pdl_launch(grad3d_kernel<2>, grid_col, NODE_TPB, 0, st, insts, w_col, n_col, scr);
 }
 
 void launch_xdot_vcl(bool mixed, int d, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,

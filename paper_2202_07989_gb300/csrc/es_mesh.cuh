@@ -5,6 +5,23 @@
 
 namespace es {
 
+// kernels marching along i3 (3D): a block owns a 32 x 8 column of the (i1, i2) plane and stages
+// planes of it with a one-node halo
+constexpr int M3_TX = NT_X, M3_TY = NT_Y;               // 32 x 8 node columns
+constexpr int M3_PX = M3_TX + 2, M3_PY = M3_TY + 2;     // a staged plane: the column and its halo
+constexpr int M3_NH = 2 * M3_TX + 2 * M3_TY;            // halo slots of a plane (no corners)
+static_assert(M3_TX == 32 && M3_TX * M3_TY == NODE_TPB, "one warp per row of a column");
+static_assert(M3_NH <= NODE_TPB, "one halo slot per thread at most");
+
+// the halo slot h of a staged plane (slot coordinates a in [0, M3_PX), b in [0, M3_PY))
+__device__ __forceinline__ void m3_halo_slot(int h, int& a, int& b)
+{
+    if (h < M3_TX) { a = h + 1; b = 0; }
+    else if (h < 2 * M3_TX) { a = h - M3_TX + 1; b = M3_PY - 1; }
+    else if (h < 2 * M3_TX + M3_TY) { a = 0; b = h - 2 * M3_TX + 1; }
+    else { a = M3_PX - 1; b = h - 2 * M3_TX - M3_TY + 1; }
+}
+
 template <typename T>
 __device__ inline T block_max(T v, T* sh)
 {
@@ -64,6 +81,11 @@ __device__ inline void y_at(const Inst& I, const float* __restrict__ y, int i0, 
 
 void launch_cfl_grad(bool mixed, int d, int N, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
                      const StagePtrs* table, const int2* work, int nwork, const Scratch* scr);
+// mixed form, 3D: Eq. (cfl) and sigma_s one node per thread (work list w_cell), then with monitor
+// terms (n_sigma > 0) the monitor gradients marching along i3 (the column items w_col of col3)
+void launch_cfl_grad3d(int N, int grid_cell, int grid_col, cudaStream_t st, const Inst* insts, const StagePtrs& single,
+                       const StagePtrs* table, const int2* w_cell, int n_cell, const int2* w_col, int n_col,
+                       const Scratch* scr, bool monitor);
 void launch_xdot(bool mixed, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
                  const StagePtrs* table, const int2* work, int nwork, const Scratch* scr);
 void launch_xdot_vcl(bool mixed, int d, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
@@ -78,9 +100,13 @@ void launch_filter(bool mixed, bool from_g, int grid, cudaStream_t st, const Ins
 // sweeps in one launch (F < 0: Theta read from the buffer theta_sel)
 constexpr int JACOBI_FUSED_MAX = 8, FILTER_FUSED_MAX = 4;
 void prepare_mesh();    // kernel attributes, once per context
+void prepare_mesh3d();  // those of es_mesh3d.cu
 void launch_jacobi_fused2d(int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
                            const StagePtrs* table, const int2* work, int nwork, const Scratch* scr, int H, int F,
                            int theta_sel);
+// mixed form, 3D: one filter pass marching along i3 over the column items of col3 (es_mesh3d.cu)
+void launch_filter3d(int grid, cudaStream_t st, const Inst* insts, const int2* work, int nwork, const Scratch* scr,
+                     int parity);
 // mixed form, 3D: one Jacobi sweep marching along i3 over the column items of col3 (es_mesh3d.cu)
 void launch_jacobi3d(bool first, bool last, int grid, cudaStream_t st, const Inst* insts, const int2* work, int nwork,
                      const Scratch* scr, int sweep, int theta_sel);

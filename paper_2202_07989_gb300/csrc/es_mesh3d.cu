@@ -9,21 +9,6 @@
 
 namespace es {
 
-constexpr int M3_TX = NT_X, M3_TY = NT_Y;               // 32 x 8 node columns
-constexpr int M3_PX = M3_TX + 2, M3_PY = M3_TY + 2;     // a staged plane: the column and its halo
-constexpr int M3_NH = 2 * M3_TX + 2 * M3_TY;            // halo slots of a plane (no corners)
-static_assert(M3_TX == 32 && M3_TX * M3_TY == NODE_TPB, "one warp per row of a column");
-static_assert(M3_NH <= NODE_TPB, "one halo slot per thread at most");
-
-// the halo slot h of a staged plane (slot coordinates a in [0, M3_PX), b in [0, M3_PY))
-__device__ __forceinline__ void m3_halo_slot(int h, int& a, int& b)
-{
-    if (h < M3_TX) { a = h + 1; b = 0; }
-    else if (h < 2 * M3_TX) { a = h - M3_TX + 1; b = M3_PY - 1; }
-    else if (h < 2 * M3_TX + M3_TY) { a = 0; b = h - 2 * M3_TX + 1; }
-    else { a = M3_PX - 1; b = h - 2 * M3_TX - M3_TY + 1; }
-}
-
 // Theta (and with WITH_Y the binary32 displacement) at node (g0, g1, g2), which lies at most
 // one node outside the grid in one direction: the maps of s_map and y_at at a ghost node.
 // Other positions (outside in two directions, or further out) are no face neighbour of any
@@ -316,13 +301,305 @@ __global__ void __launch_bounds__(NODE_TPB, 3) jacobi3d_kernel(const Inst* __res
     }
 }
 
+// asynchronous 4-byte global -> shared copies (cp.async) and their groups
+__device__ __forceinline__ void m3_cp4(void* smem, const void* gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void m3_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void m3_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// the grid node whose Theta and y a staged position g stands for (g at most one node outside
+// the grid, in one direction) and the component of y that a wall mirror negates there (-1:
+// none).  At one node outside, the mirror of y_at and the copy of s_map pick the same node
+// (the boundary node), and a periodic side wraps for both.  False: g is no face neighbour
+// of a grid node.
+__device__ __forceinline__ bool m3_source(const Inst& I, int g0, int g1, int g2, long long& src, int& flip)
+{
+    int i[3] = { g0, g1, g2 }, out = 0;
+    flip = -1;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int n = I.n[k];
+        if (i[k] < -1 || i[k] > n) return false;
+        if (i[k] >= 0 && i[k] < n) continue;
+        ++out;
+        const int side = i[k] < 0 ? 0 : 1;
+        if (I.bc[k][side] == BC_PERIODIC) {
+            i[k] = side == 0 ? n - 1 : 0;
+        } else {
+            i[k] = side == 0 ? 0 : n - 1;
+            flip = k;
+        }
+    }
+    if (out > 1) return false;
+    src = ((long long)i[2] * I.n[1] + i[1]) * I.n[0] + i[0];
+    return true;
+}
+
+// shared memory of the later sweeps: Theta and y planes in a ring of six (three read by a
+// plane's update, three in flight), the spacings E_k of a plane (this column's nodes, the
+// E_0 left of each row, the E_1 below the first row) in a ring of four
+constexpr int J3_YR = 6, J3_ER = 4;
+struct J3Smem {
+    float y[J3_YR][3][M3_PY][M3_PX];
+    float th[J3_YR][M3_PY][M3_PX];
+    float e[J3_ER][9][M3_TY][M3_TX];
+    float e0h[J3_ER][3][M3_TY];
+    float e1h[J3_ER][3][M3_TX];
+};
+
+// A later Jacobi sweep of a 3D instance (the arithmetic of jacobi3d_kernel, bit for bit).  The
+// planes are staged with cp.async two planes ahead of the update: at plane i3 the block issues
+// Theta and y of plane i3 + 3 and the spacings of plane i3 + 2, then waits for those issued two
+// planes before.  A thread that copied a ghost position across a wall negates the mirrored
+// component of y after its copy lands, before the block barrier.
+template <bool LAST>
+__global__ void __launch_bounds__(NODE_TPB, 3) jacobi3d_async_kernel(const Inst* __restrict__ insts,
+                                                                      const int2* __restrict__ work, int nwork,
+                                                                      const Scratch* __restrict__ scr, int sweep,
+                                                                      int theta_sel)
+{
+    pdl_entry();
+    extern __shared__ __align__(16) unsigned char m3_dyn[];
+    J3Smem& S = *reinterpret_cast<J3Smem*>(m3_dyn);
+    __shared__ double sh[32];
+    const int lx = (int)threadIdx.x % M3_TX, ly = (int)threadIdx.x / M3_TX;
+    int ha = -1, hb = -1;
+    if ((int)threadIdx.x < M3_NH) m3_halo_slot((int)threadIdx.x, ha, hb);
+    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+        const int2 it = work[wi];
+        const Inst& I = insts[it.x];
+        const Scratch& Sc = scr[it.x];
+        const Col3 C = col3(I, it.y);
+        const Edges3 EG(I);
+        const long long n = I.ncell;
+        const float* th = reinterpret_cast<const float*>(theta_sel ? Sc.th1 : Sc.th0);
+        const float* ys = reinterpret_cast<const float*>(sweep % 2 == 1 ? Sc.xa : Sc.xb);
+        float* yd = reinterpret_cast<float*>(sweep % 2 == 0 ? Sc.xa : Sc.xb);
+        const float* E = Sc.dl;
+        const int g0 = C.b0 + lx, g1 = C.b1 + ly;
+        const bool valid = g0 < I.n[0] && g1 < I.n[1];
+        // Theta and y of plane q at this thread's position and halo position
+        auto stage_y = [&](int q) {
+            const int r = (q + J3_YR) % J3_YR;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (h == 1 && ha < 0) break;
+                const int a = h ? ha : lx + 1, b = h ? hb : ly + 1;
+                long long src;
+                int fl;
+                if (!m3_source(I, C.b0 - 1 + a, C.b1 - 1 + b, q, src, fl)) continue;
+                m3_cp4(&S.th[r][b][a], th + src);
+#pragma unroll
+                for (int j = 0; j < 3; ++j) m3_cp4(&S.y[r][j][b][a], ys + j * n + src);
+            }
+        };
+        // after the copies of plane q landed: the wall mirror's sign
+        auto fix_y = [&](int q) {
+            const int r = (q + J3_YR) % J3_YR;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (h == 1 && ha < 0) break;
+                const int a = h ? ha : lx + 1, b = h ? hb : ly + 1;
+                long long src;
+                int fl;
+                if (!m3_source(I, C.b0 - 1 + a, C.b1 - 1 + b, q, src, fl) || fl < 0) continue;
+                S.y[r][fl][b][a] = -S.y[r][fl][b][a];
+            }
+        };
+        // the spacings of plane q (k0 = 2: only E_2, for the plane below the chunk)
+        auto stage_e = [&](int q, int k0) {
+            const int r = q & (J3_ER - 1);
+            if (valid) {
+                const long long e = EG.at(g0, g1, q);
+                for (int kj = 3 * k0; kj < 9; ++kj) m3_cp4(&S.e[r][kj][ly][lx], E + kj * EG.ne + e);
+            }
+            if (k0 > 0) return;
+            const int t = (int)threadIdx.x;
+            if (t < M3_TY && C.b1 + t < I.n[1]) {
+                const long long e = EG.at(C.b0 - 1, C.b1 + t, q);
+#pragma unroll
+                for (int j = 0; j < 3; ++j) m3_cp4(&S.e0h[r][j][t], E + j * EG.ne + e);
+            } else if (t >= 32 && t < 32 + M3_TX && C.b0 + t - 32 < I.n[0]) {
+                const long long e = EG.at(C.b0 + t - 32, C.b1 - 1, q);
+#pragma unroll
+                for (int j = 0; j < 3; ++j) m3_cp4(&S.e1h[r][j][t - 32], E + (3 + j) * EG.ne + e);
+            }
+        };
+        __syncthreads();    // the previous item's readers of the rings are done
+        for (int q = C.z0 - 1; q <= C.z0 + 1; ++q) stage_y(q);
+        stage_e(C.z0 - 1, 2);
+        stage_e(C.z0, 0);
+        m3_commit();
+        if (C.z0 + 2 <= C.z1) stage_y(C.z0 + 2);
+        if (C.z0 + 1 < C.z1) stage_e(C.z0 + 1, 0);
+        m3_commit();
+        float bnd = 1.0f;
+        for (int z = C.z0; z < C.z1; ++z) {
+            m3_wait<1>();    // this thread's copies for plane z (y: up to z + 1) have landed
+            if (z == C.z0) {
+                fix_y(z - 1);
+                fix_y(z);
+            }
+            fix_y(z + 1);
+            __syncthreads();
+            if (z + 3 <= C.z1) stage_y(z + 3);
+            if (z + 2 < C.z1) stage_e(z + 2, 0);
+            m3_commit();
+            if (valid) {
+                const int c = (z + J3_YR) % J3_YR, m = (z - 1 + J3_YR) % J3_YR, pp = (z + 1) % J3_YR;
+                const int ec = z & (J3_ER - 1), em_ = (z - 1) & (J3_ER - 1);
+                float ep[3][3], em[3][3];
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) ep[k][j] = S.e[ec][k * 3 + j][ly][lx];
+                    em[0][j] = lx == 0 ? S.e0h[ec][j][ly] : S.e[ec][j][ly][lx - 1];
+                    em[1][j] = ly == 0 ? S.e1h[ec][j][lx] : S.e[ec][3 + j][ly - 1][lx];
+                    em[2][j] = S.e[em_][6 + j][ly][lx];
+                }
+                const float tc = S.th[c][ly + 1][lx + 1];
+                const float tn[3][2] = { { S.th[c][ly + 1][lx], S.th[c][ly + 1][lx + 2] },
+                                         { S.th[c][ly][lx + 1], S.th[c][ly + 2][lx + 1] },
+                                         { S.th[m][ly + 1][lx + 1], S.th[pp][ly + 1][lx + 1] } };
+                float num[3] = { 0.0f, 0.0f, 0.0f }, den = 0.0f, dk[3][2];
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+#pragma unroll
+                    for (int s2 = 0; s2 < 2; ++s2) {
+                        const float w = 0.5f * (tc + tn[k][s2]) * I.f_h2[k];
+                        float dv[3], yv[3];
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) {
+                            dv[j] = s2 ? ep[k][j] : -em[k][j];
+                            yv[j] = k == 0 ? S.y[c][j][ly + 1][lx + 2 * s2]
+                                  : (k == 1 ? S.y[c][j][ly + 2 * s2][lx + 1] : S.y[s2 ? pp : m][j][ly + 1][lx + 1]);
+                        }
+                        dk[k][s2] = dv[k];
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) num[j] = fmaf(w, dv[j] + yv[j], num[j]);
+                        den += w;
+                    }
+                float ynew[3];
+                const long long p = ((long long)z * I.n[1] + g1) * I.n[0] + g0;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    ynew[j] = num[j] / den;
+                    yd[j * n + p] = ynew[j];
+                }
+                if (LAST) {
+                    float b = 1.0f;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        const float dx = ynew[k];
+                        if (dx < 0.0f) b = fminf(b, dk[k][0] / (2.0f * dx));
+                        else if (dx > 0.0f) b = fminf(b, dk[k][1] / (2.0f * dx));
+                    }
+                    if (!(b >= 0.0f)) b = 0.0f;
+                    bnd = fminf(bnd, b);
+                }
+            }
+        }
+        m3_wait<0>();
+        if (LAST) {
+            const double mb = block_min_pos(f32_to_f64(bnd), sh);
+            if (threadIdx.x == 0) atomic_min_pos(&Sc.red[5], mb);
+        }
+    }
+}
+
+void prepare_mesh3d()
+{
+    cudaFuncSetAttribute(jacobi3d_async_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(J3Smem));
+    cudaFuncSetAttribute(jacobi3d_async_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(J3Smem));
+}
+
 void launch_jacobi3d(bool first, bool last, int grid, cudaStream_t st, const Inst* insts, const int2* work, int nwork,
                      const Scratch* scr, int sweep, int theta_sel)
 {
-#define J3(F, L) pdl_launch(jacobi3d_kernel<F, L>, grid, NODE_TPB, 0, st, insts, work, nwork, scr, sweep, theta_sel)
-    if (first) { if (last) J3(true, true); else J3(true, false); }
-    else { if (last) J3(false, true); else J3(false, false); }
-#undef J3
+    const size_t sm = sizeof(J3Smem);
+    if (first) {
+        if (last) pdl_launch(jacobi3d_kernel<true, true>, grid, NODE_TPB, 0, st, insts, work, nwork, scr, sweep, theta_sel);
+        else pdl_launch(jacobi3d_kernel<true, false>, grid, NODE_TPB, 0, st, insts, work, nwork, scr, sweep, theta_sel);
+    } else {
+        if (last) pdl_launch(jacobi3d_async_kernel<true>, grid, NODE_TPB, sm, st, insts, work, nwork, scr, sweep, theta_sel);
+        else pdl_launch(jacobi3d_async_kernel<false>, grid, NODE_TPB, sm, st, insts, work, nwork, scr, sweep, theta_sel);
+    }
+}
+
+// the halo slots with the four corners (h in [0, M3_NH + 4)): the 3 x 3 stencils need them
+__device__ __forceinline__ void m3_halo_slot_c(int h, int& a, int& b)
+{
+    if (h < M3_NH) { m3_halo_slot(h, a, b); return; }
+    a = (h - M3_NH) % 2 == 0 ? 0 : M3_PX - 1;
+    b = h - M3_NH < 2 ? 0 : M3_PY - 1;
+}
+
+// a scalar node field at (g0, g1, g2) within one node of the grid in every direction, through
+// the map of s_map (periodic wrap, else the boundary node); zero further out
+__device__ __forceinline__ float m3_scalar(const Inst& I, const float* __restrict__ f, int g0, int g1, int g2)
+{
+    const int n0 = I.n[0], n1 = I.n[1], n2 = I.n[2];
+    if (g0 < -1 || g0 > n0 || g1 < -1 || g1 > n1 || g2 < -1 || g2 > n2) return 0.0f;
+    if (g0 >= 0 && g0 < n0 && g1 >= 0 && g1 < n1 && g2 >= 0 && g2 < n2) return f[((long long)g2 * n1 + g1) * n0 + g0];
+    return f[s_map(I, g0, g1, g2)];
+}
+
+// One pass of the low-pass filter on a 3D instance (mixed form): the 3^3 stencil with weights
+// (1/2)^(|j|_1 + 3), the tensor product of (1/4, 1/2, 1/4) in each direction, taken one
+// direction at a time: rows r(j2) = (a(i1-1) + a(i1+1)) / 4 + a(i1) / 2 of a staged plane,
+// the plane sums P = (r(-1) + r(1)) / 4 + r(0) / 2, then (P(i3-1) + P(i3+1)) / 4 + P(i3) / 2.
+// Each plane sum serves three output planes.  Ghost nodes of the stencil: the maps of s_map.
+__global__ void __launch_bounds__(NODE_TPB) filter3d_kernel(const Inst* __restrict__ insts,
+                                                             const int2* __restrict__ work, int nwork,
+                                                             const Scratch* __restrict__ scr, int parity)
+{
+    pdl_entry();
+    __shared__ float sa[2][M3_PY][M3_PX];
+    const int lx = (int)threadIdx.x % M3_TX, ly = (int)threadIdx.x / M3_TX;
+    int ha = -1, hb = -1;
+    if ((int)threadIdx.x < M3_NH + 4) m3_halo_slot_c((int)threadIdx.x, ha, hb);
+    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+        const int2 it = work[wi];
+        const Inst& I = insts[it.x];
+        const Scratch& Sc = scr[it.x];
+        const Col3 C = col3(I, it.y);
+        const float* a = reinterpret_cast<const float*>(parity ? Sc.th1 : Sc.th0);
+        float* dst = reinterpret_cast<float*>(parity ? Sc.th0 : Sc.th1);
+        const int g0 = C.b0 + lx, g1 = C.b1 + ly, h0 = C.b0 - 1 + ha, h1 = C.b1 - 1 + hb;
+        const bool valid = g0 < I.n[0] && g1 < I.n[1];
+        __syncthreads();    // the previous item's readers are done
+        float vo = m3_scalar(I, a, g0, g1, C.z0 - 1), vh = ha >= 0 ? m3_scalar(I, a, h0, h1, C.z0 - 1) : 0.0f;
+        float pm2 = 0.0f, pm1 = 0.0f;
+        for (int q = C.z0 - 1; q <= C.z1; ++q) {
+            const int b = q & 1;
+            sa[b][ly + 1][lx + 1] = vo;
+            if (ha >= 0) sa[b][hb][ha] = vh;
+            __syncthreads();
+            if (q < C.z1) {
+                vo = m3_scalar(I, a, g0, g1, q + 1);
+                if (ha >= 0) vh = m3_scalar(I, a, h0, h1, q + 1);
+            }
+            float r[3];
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                r[j] = 0.25f * (sa[b][ly + j][lx] + sa[b][ly + j][lx + 2]) + 0.5f * sa[b][ly + j][lx + 1];
+            const float pq = 0.25f * (r[0] + r[2]) + 0.5f * r[1];
+            if (valid && q >= C.z0 + 1)
+                dst[((long long)(q - 1) * I.n[1] + g1) * I.n[0] + g0] = 0.25f * (pm2 + pq) + 0.5f * pm1;
+            pm2 = pm1;
+            pm1 = pq;
+        }
+    }
+}
+
+void launch_filter3d(int grid, cudaStream_t st, const Inst* insts, const int2* work, int nwork, const Scratch* scr,
+                     int parity)
+{
+    pdl_launch(filter3d_kernel, grid, NODE_TPB, 0, st, insts, work, nwork, scr, parity);
 }
 
 }  // namespace es
