@@ -412,6 +412,37 @@ def test_batched_equals_single():
             assert torch.equal(ju, JU[i]) and torch.equal(jj, J[i]) and torch.equal(xx, X[i])
 
 
+def test_batched_3d_equals_single():
+    """es_step_batch over uneven 3D instances equals es_step on each instance alone, bit for
+    bit, in both forms: the mixed form's mesh-step kernels march along i3 in plane chunks sized
+    per instance, over one work list of all instances' columns."""
+    torch = need_gpu()
+    from paper_2202_07989_gb300 import es
+    insts = []
+    for n, bc, seed in (((22, 12, 11), "periodic", 1), ((13, 25, 17), "reflect", 2), ((40, 10, 12), "mixed", 3)):
+        pb, JU, J, x, _ = case(3, 1, n, bc, es=True, seed=seed)
+        pb = pb.with_(mu=4, nf=2, sigma=(W.SIG_RHO, W.SIG_P), alpha=(50.0, 20.0))
+        insts.append((pb, JU, J, x))
+    probs = [i[0] for i in insts]
+    for prec in (0, 1):
+        b = es.Context(probs, prec)
+        JU = [to_dev(i[1], torch) for i in insts]
+        J = [to_dev(i[2], torch) for i in insts]
+        X = [to_dev(i[3], torch) for i in insts]
+        XD = [torch.zeros_like(t) for t in X]
+        DD = [torch.zeros(2, dtype=torch.float64, device="cuda") for _ in insts]
+        b.es_bind_batch(JU, J, X, XD, DD)
+        for _ in range(2):
+            b.es_step_batch()
+        assert b.es_poll_status() == 0
+        for k, (pb, ju0, j0, x0) in enumerate(insts):
+            c = es.Context(pb, prec)
+            ju, jj, xx = to_dev(ju0, torch), to_dev(j0, torch), to_dev(x0, torch)
+            for _ in range(2):
+                xd, dd = c.es_step(ju, jj, xx)
+            assert torch.equal(ju, JU[k]) and torch.equal(jj, J[k]) and torch.equal(xx, X[k]), (prec, k)
+
+
 @pytest.mark.parametrize("form", [0, 1])
 def test_full_step_shock_bubble_config(form):
     """The 400 x 200 two-component shock-bubble instance (adaptive mesh, 5 sweeps): one full
