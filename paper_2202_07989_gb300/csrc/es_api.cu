@@ -629,8 +629,9 @@ es_status es_create_batch(const es_config* cfgs, int n_inst, es_ctx** out)
         ok = ok && dalloc(c, (void**)&S.xb, sizeof(double) * I.d * n);
         if (c->mixed) {
             // 2D: dl_{k+-} per node; 3D: the edge spacings E_k on the grid extended by one node below
+            // (es_mesh3d.cu)
             long long nd = 2LL * I.d * I.d * n;
-            if (I.d == 3) nd = 9LL * (I.n[0] + 1) * (I.n[1] + 1) * (I.n[2] + 1);
+            if (I.d == 3) nd = e3_size(I.n[0], I.n[1], I.n[2]);
             ok = ok && dalloc(c, (void**)&S.dl, sizeof(float) * nd);
         }
         ok = ok && dalloc(c, (void**)&S.zeros, sizeof(double) * I.d * n);

@@ -13,6 +13,18 @@ constexpr int M3_NH = 2 * M3_TX + 2 * M3_TY;            // halo slots of a plane
 static_assert(M3_TX == 32 && M3_TX * M3_TY == NODE_TPB, "one warp per row of a column");
 static_assert(M3_NH <= NODE_TPB, "one halo slot per thread at most");
 
+// The binary32 edge spacings E_k of the mixed 3D Jacobi sweeps (9 components) live on the grid
+// extended by one node below in every direction. Rows have a pitch of a multiple of 4 floats
+// and node i1 = 0 sits at column 4, so the row segment of a 32 x 8 column starts on a 16-byte
+// boundary (16-byte cp.async copies); the buffer carries E3_PAD floats of slack for the
+// copies of a ragged column's last row.
+constexpr int E3_PAD = 32;
+__host__ __device__ inline int e3_pitch(int n0) { return (n0 + 4 + 3) & ~3; }
+__host__ __device__ inline long long e3_size(int n0, int n1, int n2)
+{
+    return 9LL * e3_pitch(n0) * (n1 + 1) * (n2 + 1) + E3_PAD;
+}
+
 // the halo slot h of a staged plane (slot coordinates a in [0, M3_PX), b in [0, M3_PY))
 __device__ __forceinline__ void m3_halo_slot(int h, int& a, int& b)
 {

@@ -40,16 +40,17 @@ __device__ __forceinline__ void m3_node(const Inst& I, const float* __restrict__
 // one node below in every direction (entry i_k = -1 is the edge from the ghost node to the
 // first node).  The sweep reads dl_{k+}(i) = E_k(i) and dl_{k-}(i) = -E_k(i - e_k): rounding
 // to nearest is symmetric, so the negated entry is the rounded difference taken the other way.
+// Rows have the pitch e3_pitch and node i1 = 0 sits at column 4 (es_mesh.cuh).
 struct Edges3 {
-    long long ne;                 // (n0 + 1)(n1 + 1)(n2 + 1)
-    int x0, x1;                   // n0 + 1, n1 + 1
-    __device__ explicit Edges3(const Inst& I) : x0(I.n[0] + 1), x1(I.n[1] + 1)
+    long long ne;                 // entries per component: pitch (n1 + 1)(n2 + 1)
+    int x0, x1;                   // row pitch, rows per plane (n1 + 1)
+    __device__ explicit Edges3(const Inst& I) : x0(e3_pitch(I.n[0])), x1(I.n[1] + 1)
     {
         ne = (long long)x0 * x1 * (I.n[2] + 1);
     }
     __device__ long long at(int g0, int g1, int g2) const
     {
-        return ((long long)(g2 + 1) * x1 + (g1 + 1)) * x0 + (g0 + 1);
+        return ((long long)(g2 + 1) * x1 + (g1 + 1)) * x0 + (g0 + 4);
     }
 };
 
@@ -307,6 +308,11 @@ __device__ __forceinline__ void m3_cp4(void* smem, const void* gmem)
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void m3_cp16(void* smem, const void* gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void m3_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void m3_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
@@ -346,9 +352,9 @@ constexpr int J3_YR = 6, J3_ER = 4;
 struct J3Smem {
     float y[J3_YR][3][M3_PY][M3_PX];
     float th[J3_YR][M3_PY][M3_PX];
-    float e[J3_ER][9][M3_TY][M3_TX];
+    alignas(16) float e[J3_ER][9][M3_TY][M3_TX];
     float e0h[J3_ER][3][M3_TY];
-    float e1h[J3_ER][3][M3_TX];
+    alignas(16) float e1h[J3_ER][3][M3_TX];
 };
 
 // A later Jacobi sweep of a 3D instance (the arithmetic of jacobi3d_kernel, bit for bit).  The
@@ -382,16 +388,22 @@ __global__ void __launch_bounds__(NODE_TPB, 3) jacobi3d_async_kernel(const Inst*
         const float* E = Sc.dl;
         const int g0 = C.b0 + lx, g1 = C.b1 + ly;
         const bool valid = g0 < I.n[0] && g1 < I.n[1];
+        // a staged plane holds ghost positions only in a column at a side of the grid, or
+        // below and above the grid
+        const bool side = C.b0 == 0 || C.b0 + M3_TX >= I.n[0] || C.b1 == 0 || C.b1 + M3_TY >= I.n[1];
+        auto inner = [&](int q) { return !side && q >= 0 && q < I.n[2]; };
         // Theta and y of plane q at this thread's position and halo position
         auto stage_y = [&](int q) {
             const int r = (q + J3_YR) % J3_YR;
+            const bool in = inner(q);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 if (h == 1 && ha < 0) break;
                 const int a = h ? ha : lx + 1, b = h ? hb : ly + 1;
                 long long src;
                 int fl;
-                if (!m3_source(I, C.b0 - 1 + a, C.b1 - 1 + b, q, src, fl)) continue;
+                if (in) src = ((long long)q * I.n[1] + (C.b1 - 1 + b)) * I.n[0] + (C.b0 - 1 + a);
+                else if (!m3_source(I, C.b0 - 1 + a, C.b1 - 1 + b, q, src, fl)) continue;
                 m3_cp4(&S.th[r][b][a], th + src);
 #pragma unroll
                 for (int j = 0; j < 3; ++j) m3_cp4(&S.y[r][j][b][a], ys + j * n + src);
@@ -399,6 +411,7 @@ __global__ void __launch_bounds__(NODE_TPB, 3) jacobi3d_async_kernel(const Inst*
         };
         // after the copies of plane q landed: the wall mirror's sign
         auto fix_y = [&](int q) {
+            if (inner(q)) return;
             const int r = (q + J3_YR) % J3_YR;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -410,23 +423,25 @@ __global__ void __launch_bounds__(NODE_TPB, 3) jacobi3d_async_kernel(const Inst*
                 S.y[r][fl][b][a] = -S.y[r][fl][b][a];
             }
         };
-        // the spacings of plane q (k0 = 2: only E_2, for the plane below the chunk)
+        // the spacings of plane q (k0 = 2: only E_2, for the plane below the chunk): each row of
+        // the column in 16-byte copies, the E_0 left of each row in 4-byte copies
         auto stage_e = [&](int q, int k0) {
             const int r = q & (J3_ER - 1);
-            if (valid) {
-                const long long e = EG.at(g0, g1, q);
-                for (int kj = 3 * k0; kj < 9; ++kj) m3_cp4(&S.e[r][kj][ly][lx], E + kj * EG.ne + e);
+            const int t = (int)threadIdx.x;
+            const long long e0 = EG.at(C.b0, C.b1, q);
+            for (int c = t; c < (9 - 3 * k0) * M3_TY * 8; c += NODE_TPB) {
+                const int kj = 3 * k0 + c / (M3_TY * 8), row = (c / 8) % M3_TY, seg = c % 8;
+                if (C.b1 + row >= I.n[1]) continue;
+                m3_cp16(&S.e[r][kj][row][4 * seg], E + kj * EG.ne + e0 + (long long)row * EG.x0 + 4 * seg);
             }
             if (k0 > 0) return;
-            const int t = (int)threadIdx.x;
             if (t < M3_TY && C.b1 + t < I.n[1]) {
                 const long long e = EG.at(C.b0 - 1, C.b1 + t, q);
 #pragma unroll
                 for (int j = 0; j < 3; ++j) m3_cp4(&S.e0h[r][j][t], E + j * EG.ne + e);
-            } else if (t >= 32 && t < 32 + M3_TX && C.b0 + t - 32 < I.n[0]) {
-                const long long e = EG.at(C.b0 + t - 32, C.b1 - 1, q);
-#pragma unroll
-                for (int j = 0; j < 3; ++j) m3_cp4(&S.e1h[r][j][t - 32], E + (3 + j) * EG.ne + e);
+            } else if (t >= 32 && t < 32 + 3 * 8) {
+                const int j = (t - 32) / 8, seg = (t - 32) % 8;
+                m3_cp16(&S.e1h[r][j][4 * seg], E + (3 + j) * EG.ne + EG.at(C.b0, C.b1 - 1, q) + 4 * seg);
             }
         };
         __syncthreads();    // the previous item's readers of the rings are done
