@@ -412,13 +412,31 @@ __global__ void __launch_bounds__(NODE_TPB) cfl_sigma3d_kernel(const Inst* __res
     constexpr int NC = NS + 4, NW = NODE_TPB / 32;
     __shared__ K sred[NW];
     const int lane = (int)threadIdx.x & 31, wid = (int)threadIdx.x >> 5;
+    // the CFL maximum of a run of items of one instance: one block reduction per run
+    K kc = 0;
+    int cur = -1;
+    auto flush = [&]() {
+        for (int o = 16; o > 0; o >>= 1) kc = shfl_max(kc, o);
+        __syncthreads();    // the previous run's readers of sred are done
+        if (lane == 0) sred[wid] = kc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            K mx = sred[0];
+            for (int w = 1; w < NW; ++w) mx = max(mx, sred[w]);
+            atomic_max_pos(&scr[cur].red[0], key_value(mx));
+        }
+        kc = 0;
+    };
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
         const int2 it = work[wi];
+        if (it.x != cur) {
+            if (cur >= 0) flush();
+            cur = it.x;
+        }
         const Inst& I = insts[it.x];
         ES_PTRS(P);
         const Scratch& Sc = scr[it.x];
         int i0, i1, i2;
-        K kc = 0;
         if (tile_node(I, it.y, 0, i0, i1, i2)) {
             const long long p = lin(I, i0, i1, i2), pid = plin(I, i0, i1, i2);
             double mraw[9];
@@ -460,18 +478,10 @@ __global__ void __launch_bounds__(NODE_TPB) cfl_sigma3d_kernel(const Inst* __res
                 sr += (fabs(vn) + c * sqrt(L2)) / Jp * inv_dxi_r<R>(I, k);
             }
             if (!(sr >= R(0))) sr = R(0);
-            kc = max_key(sr);
-        }
-        for (int o = 16; o > 0; o >>= 1) kc = shfl_max(kc, o);
-        __syncthreads();    // the previous item's readers of sred are done
-        if (lane == 0) sred[wid] = kc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            K mx = sred[0];
-            for (int w = 1; w < NW; ++w) mx = max(mx, sred[w]);
-            atomic_max_pos(&Sc.red[0], key_value(mx));
+            kc = max(kc, max_key(sr));
         }
     }
+    if (cur >= 0) flush();
 }
 
 // sigma_s (s < n_sigma) at position g of a staged plane, at most one node outside the grid in
@@ -1274,25 +1284,30 @@ __global__ void xdot_vcl_kernel(const Inst* __restrict__ insts, StagePtrs single
 {
     pdl_entry();
     __shared__ double sc3[3];
+    int cur = -1;
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
         const int2 it = work[wi];
         const Inst& I = insts[it.x];
         ES_PTRS(P);
         const double* xmu = xmu_of(P, scr[it.x], I.mu);
-        // Delta t, Delta_tau and Delta_tau / Delta t: one thread per block divides
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const double* red = scr[it.x].red;
-            const double dt_ = P.dt_fixed > 0.0 ? P.dt_fixed : I.cfl / red[0];
-            sc3[0] = dt_;
-            sc3[1] = red[5];
-            sc3[2] = red[5] / dt_;
-            if (it.y == 0) {
-                P.out[0] = dt_;
-                P.out[1] = red[5];
+        // Delta t, Delta_tau and Delta_tau / Delta t: one thread of the block divides, once per
+        // run of items of one instance
+        if (it.x != cur) {
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const double* red = scr[it.x].red;
+                const double dt_ = P.dt_fixed > 0.0 ? P.dt_fixed : I.cfl / red[0];
+                sc3[0] = dt_;
+                sc3[1] = red[5];
+                sc3[2] = red[5] / dt_;
             }
+            __syncthreads();
+            cur = it.x;
         }
-        __syncthreads();
+        if (threadIdx.x == 0 && it.y == 0) {
+            P.out[0] = sc3[0];
+            P.out[1] = sc3[1];
+        }
         const double dt = sc3[0], dtau = sc3[1];
         int i[3];
         if (!tile_node(I, it.y, 3, i[0], i[1], i[2])) continue;

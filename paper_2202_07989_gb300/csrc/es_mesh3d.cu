@@ -388,22 +388,23 @@ __global__ void __launch_bounds__(NODE_TPB, 3) jacobi3d_async_kernel(const Inst*
         const float* E = Sc.dl;
         const int g0 = C.b0 + lx, g1 = C.b1 + ly;
         const bool valid = g0 < I.n[0] && g1 < I.n[1];
-        // a staged plane holds ghost positions only in a column at a side of the grid, or
-        // below and above the grid
-        const bool side = C.b0 == 0 || C.b0 + M3_TX >= I.n[0] || C.b1 == 0 || C.b1 + M3_TY >= I.n[1];
-        auto inner = [&](int q) { return !side && q >= 0 && q < I.n[2]; };
+        // a staged position inside the grid reads its own node; only ghost positions need the
+        // boundary maps
+        auto inside = [&](int s0, int s1, int q) {
+            return (unsigned)s0 < (unsigned)I.n[0] && (unsigned)s1 < (unsigned)I.n[1] && (unsigned)q < (unsigned)I.n[2];
+        };
         // Theta and y of plane q at this thread's position and halo position
         auto stage_y = [&](int q) {
             const int r = (q + J3_YR) % J3_YR;
-            const bool in = inner(q);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 if (h == 1 && ha < 0) break;
                 const int a = h ? ha : lx + 1, b = h ? hb : ly + 1;
+                const int s0 = C.b0 - 1 + a, s1 = C.b1 - 1 + b;
                 long long src;
                 int fl;
-                if (in) src = ((long long)q * I.n[1] + (C.b1 - 1 + b)) * I.n[0] + (C.b0 - 1 + a);
-                else if (!m3_source(I, C.b0 - 1 + a, C.b1 - 1 + b, q, src, fl)) continue;
+                if (inside(s0, s1, q)) src = ((long long)q * I.n[1] + s1) * I.n[0] + s0;
+                else if (!m3_source(I, s0, s1, q, src, fl)) continue;
                 m3_cp4(&S.th[r][b][a], th + src);
 #pragma unroll
                 for (int j = 0; j < 3; ++j) m3_cp4(&S.y[r][j][b][a], ys + j * n + src);
@@ -411,15 +412,15 @@ __global__ void __launch_bounds__(NODE_TPB, 3) jacobi3d_async_kernel(const Inst*
         };
         // after the copies of plane q landed: the wall mirror's sign
         auto fix_y = [&](int q) {
-            if (inner(q)) return;
             const int r = (q + J3_YR) % J3_YR;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 if (h == 1 && ha < 0) break;
                 const int a = h ? ha : lx + 1, b = h ? hb : ly + 1;
+                const int s0 = C.b0 - 1 + a, s1 = C.b1 - 1 + b;
                 long long src;
                 int fl;
-                if (!m3_source(I, C.b0 - 1 + a, C.b1 - 1 + b, q, src, fl) || fl < 0) continue;
+                if (inside(s0, s1, q) || !m3_source(I, s0, s1, q, src, fl) || fl < 0) continue;
                 S.y[r][fl][b][a] = -S.y[r][fl][b][a];
             }
         };
