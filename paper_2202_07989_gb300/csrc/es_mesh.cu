@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(NODE_TPB) cfl_grad2d_kernel(const Inst* __rest
 // Pass 1, one node per thread: the CFL spectral-radius sum of Eq. (cfl) with the metrics of
 // x^n, and sigma_s of the node state, stored behind the gradients in the gradient buffer.
 template <int NS>
-__global__ void __launch_bounds__(NODE_TPB) cfl_sigma3d_kernel(const Inst* __restrict__ insts, StagePtrs single,
+__global__ void __launch_bounds__(NODE_TPB, 4) cfl_sigma3d_kernel(const Inst* __restrict__ insts, StagePtrs single,
                                                                 const StagePtrs* __restrict__ table,
                                                                 const int2* __restrict__ work, int nwork,
                                                                 const Scratch* __restrict__ scr)
