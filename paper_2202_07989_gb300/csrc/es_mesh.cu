@@ -114,10 +114,11 @@ __device__ __forceinline__ R* grad_r(const Scratch& S) { return reinterpret_cast
 
 // one pass over the nodes: the CFL spectral-radius sum of Eq. (cfl) at x^n and the monitor
 // terms |grad_xi sigma_s| or |Laplacian_xi sigma_s| (second-order central differences);
-// per-instance maxima by atomics on the non-negative bit patterns.  R = float in the mixed
-// form (the time step is a bound and the monitor is an FP32 quantity there); the metrics
-// are read from M.  Each block evaluates sigma once per node of its 32 x 8 tile and of a
-// 1-node halo in the (i1, i2) plane into shared memory; the third direction reads globally.
+// per-instance maxima by atomics on the non-negative bit patterns; the metrics are read from
+// M.  Each block evaluates sigma once per node of its 32 x 8 tile and of a 1-node halo in the
+// (i1, i2) plane into shared memory; the third direction reads globally.  It serves the FP64
+// form of 3D instances (R = double); 2D instances run cfl_grad2d_kernel, and the mixed form of
+// 3D instances cfl_sigma3d_kernel and grad3d_kernel, with the same terms.
 template <typename R>
 __global__ void __launch_bounds__(NODE_TPB) cfl_grad_kernel(const Inst* __restrict__ insts, StagePtrs single,
                                                              const StagePtrs* __restrict__ table,
@@ -1634,8 +1635,9 @@ void launch_cfl_grad(bool mixed, int d, int N, int grid, cudaStream_t st, const 
         }
         return;
     }
-    if (mixed) pdl_launch(cfl_grad_kernel<float>, grid, NODE_TPB, 0, st, insts, single, table, work, nwork, scr);
-    else pdl_launch(cfl_grad_kernel<double>, grid, NODE_TPB, 0, st, insts, single, table, work, nwork, scr);
+    // 3D: the FP64 form here; the mixed form runs launch_cfl_grad3d
+    (void)mixed;
+    pdl_launch(cfl_grad_kernel<double>, grid, NODE_TPB, 0, st, insts, single, table, work, nwork, scr);
 }
 
 void launch_cfl_grad3d(int N, int grid_cell, int grid_col, cudaStream_t st, const Inst* insts, const StagePtrs& single,
@@ -1678,14 +1680,11 @@ void launch_jacobi(bool mixed, int d, bool last, int grid, cudaStream_t st, cons
 #define JL(R, LS) pdl_launch(jacobi_kernel<R, LS>, grid, NODE_TPB, 0, st, insts, single, table, work, nwork, scr, sweep, theta_sel)
 #define JY(D, F, LS) pdl_launch(jacobi_y_kernel<D, F, LS>, grid, NODE_TPB, 0, st, insts, single, table, work, nwork, scr, sweep, theta_sel)
     if (mixed) {
+        // 2D (beyond the fused kernel's limits); the mixed 3D sweeps run launch_jacobi3d
+        (void)d;
         const bool first = sweep == 0;
-        if (d == 2) {
-            if (first) { if (last) JY(2, true, true); else JY(2, true, false); }
-            else { if (last) JY(2, false, true); else JY(2, false, false); }
-        } else {
-            if (first) { if (last) JY(3, true, true); else JY(3, true, false); }
-            else { if (last) JY(3, false, true); else JY(3, false, false); }
-        }
+        if (first) { if (last) JY(2, true, true); else JY(2, true, false); }
+        else { if (last) JY(2, false, true); else JY(2, false, false); }
     } else {
         if (last) JL(double, true);
         else JL(double, false);
