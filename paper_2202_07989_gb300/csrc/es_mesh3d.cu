@@ -9,30 +9,16 @@
 
 namespace es {
 
-// Theta (and with WITH_Y the binary32 displacement) at node (g0, g1, g2), which lies at most
-// one node outside the grid in one direction: the maps of s_map and y_at at a ghost node.
-// Other positions (outside in two directions, or further out) are no face neighbour of any
-// node of the grid and read as zero.
-template <bool WITH_Y>
-__device__ __forceinline__ void m3_node(const Inst& I, const float* __restrict__ ys, const float* __restrict__ th,
-                                        int g0, int g1, int g2, float y[3], float& t)
+// Theta at node (g0, g1, g2), which lies at most one node outside the grid in one direction:
+// the map of s_map at a ghost node.  Other positions (outside in two directions, or further
+// out) are no face neighbour of any node of the grid and read as zero.
+__device__ __forceinline__ float m3_theta(const Inst& I, const float* __restrict__ th, int g0, int g1, int g2)
 {
     const int n0 = I.n[0], n1 = I.n[1], n2 = I.n[2];
     const bool o0 = g0 < 0 || g0 >= n0, o1 = g1 < 0 || g1 >= n1, o2 = g2 < 0 || g2 >= n2;
-    y[0] = y[1] = y[2] = 0.0f;
-    t = 0.0f;
-    if (g0 < -1 || g0 > n0 || g1 < -1 || g1 > n1 || g2 < -1 || g2 > n2 || (int)o0 + (int)o1 + (int)o2 > 1) return;
-    if (!(o0 || o1 || o2)) {
-        const long long p = ((long long)g2 * n1 + g1) * n0 + g0;
-        t = th[p];
-        if (WITH_Y) {
-#pragma unroll
-            for (int j = 0; j < 3; ++j) y[j] = ys[j * I.ncell + p];
-        }
-    } else {
-        t = th[s_map(I, g0, g1, g2)];
-        if (WITH_Y) y_at(I, ys, g0, g1, g2, y);
-    }
+    if (g0 < -1 || g0 > n0 || g1 < -1 || g1 > n1 || g2 < -1 || g2 > n2 || (int)o0 + (int)o1 + (int)o2 > 1) return 0.0f;
+    if (!(o0 || o1 || o2)) return th[((long long)g2 * n1 + g1) * n0 + g0];
+    return th[s_map(I, g0, g1, g2)];
 }
 
 // Mesh spacings of the mixed Jacobi sweeps, stored once per edge: E_k[j] at node i is
@@ -66,10 +52,9 @@ __device__ __forceinline__ void m3_edge_xe(const Inst& I, const double* __restri
 }
 
 // E_k of plane q at this thread's node (k = 0, 1, 2), E_0 left of its row (lane 0) and E_1
-// below its column's first row (warp 0); zero where no node is, and all zero unless act.  FIRST forms them from XE
-// and stores each entry once: a node's own edges, and the edges from the ghost nodes below
-// the grid where the column touches the low boundary.
-template <bool FIRST>
+// below its column's first row (warp 0), formed from XE; zero where no node is, and all zero
+// unless act.  Each entry is stored once: a node's own edges, and the edges from the ghost
+// nodes below the grid where the column touches the low boundary.
 __device__ __forceinline__ void m3_edges(const Inst& I, const Scratch& Sc, const Edges3& EG, const Col3& C, int g0,
                                          int g1, int q, bool act, float ep[3][3], float e0h[3], float e1h[3])
 {
@@ -83,85 +68,59 @@ __device__ __forceinline__ void m3_edges(const Inst& I, const Scratch& Sc, const
 #pragma unroll
         for (int k = 0; k < 3; ++k) ep[k][j] = 0.0f;
     }
-    if (FIRST) {
-        if (valid) {
-            const long long e = EG.at(g0, g1, q);
+    if (valid) {
+        const long long e = EG.at(g0, g1, q);
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                m3_edge_xe(I, Sc.XE, k, g0, g1, q, ep[k]);
+        for (int k = 0; k < 3; ++k) {
+            m3_edge_xe(I, Sc.XE, k, g0, g1, q, ep[k]);
 #pragma unroll
-                for (int j = 0; j < 3; ++j) E[(k * 3 + j) * EG.ne + e] = ep[k][j];
-            }
+            for (int j = 0; j < 3; ++j) E[(k * 3 + j) * EG.ne + e] = ep[k][j];
         }
-        if (left) {
-            m3_edge_xe(I, Sc.XE, 0, C.b0 - 1, g1, q, e0h);
-            if (C.b0 == 0) {
+    }
+    if (left) {
+        m3_edge_xe(I, Sc.XE, 0, C.b0 - 1, g1, q, e0h);
+        if (C.b0 == 0) {
 #pragma unroll
-                for (int j = 0; j < 3; ++j) E[j * EG.ne + EG.at(-1, g1, q)] = e0h[j];
-            }
+            for (int j = 0; j < 3; ++j) E[j * EG.ne + EG.at(-1, g1, q)] = e0h[j];
         }
-        if (below) {
-            m3_edge_xe(I, Sc.XE, 1, g0, C.b1 - 1, q, e1h);
-            if (C.b1 == 0) {
+    }
+    if (below) {
+        m3_edge_xe(I, Sc.XE, 1, g0, C.b1 - 1, q, e1h);
+        if (C.b1 == 0) {
 #pragma unroll
-                for (int j = 0; j < 3; ++j) E[(3 + j) * EG.ne + EG.at(g0, -1, q)] = e1h[j];
-            }
-        }
-    } else {
-        if (valid) {
-            const long long e = EG.at(g0, g1, q);
-#pragma unroll
-            for (int k = 0; k < 3; ++k)
-#pragma unroll
-                for (int j = 0; j < 3; ++j) ep[k][j] = E[(k * 3 + j) * EG.ne + e];
-        }
-        if (left) {
-            const long long e = EG.at(C.b0 - 1, g1, q);
-#pragma unroll
-            for (int j = 0; j < 3; ++j) e0h[j] = E[j * EG.ne + e];
-        }
-        if (below) {
-            const long long e = EG.at(g0, C.b1 - 1, q);
-#pragma unroll
-            for (int j = 0; j < 3; ++j) e1h[j] = E[(3 + j) * EG.ne + e];
+            for (int j = 0; j < 3; ++j) E[(3 + j) * EG.ne + EG.at(g0, -1, q)] = e1h[j];
         }
     }
 }
 
-// E_2 of the plane below the chunk (the minus-i3 spacing of the chunk's first plane)
-template <bool FIRST>
+// E_2 of the plane below the chunk (the minus-i3 spacing of the chunk's first plane), formed
+// from XE and stored where it is the edge from the ghost plane below the grid
 __device__ __forceinline__ void m3_edge_below(const Inst& I, const Scratch& Sc, const Edges3& EG, int g0, int g1,
                                               int z0, float e[3])
 {
     e[0] = e[1] = e[2] = 0.0f;
     if (g0 >= I.n[0] || g1 >= I.n[1]) return;
-    const long long a = EG.at(g0, g1, z0 - 1);
-    if (FIRST) {
-        m3_edge_xe(I, Sc.XE, 2, g0, g1, z0 - 1, e);
-        if (z0 == 0) {
+    m3_edge_xe(I, Sc.XE, 2, g0, g1, z0 - 1, e);
+    if (z0 == 0) {
+        const long long a = EG.at(g0, g1, -1);
 #pragma unroll
-            for (int j = 0; j < 3; ++j) Sc.dl[(6 + j) * EG.ne + a] = e[j];
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j < 3; ++j) e[j] = Sc.dl[(6 + j) * EG.ne + a];
+        for (int j = 0; j < 3; ++j) Sc.dl[(6 + j) * EG.ne + a] = e[j];
     }
 }
 
-// One mixed Jacobi sweep of a 3D instance, with the arithmetic of jacobi_y_kernel:
+// The first mixed Jacobi sweep of a 3D instance, with the arithmetic of jacobi_y_kernel:
 // y_i <- sum_{k,s} w_{k,s} (dl_{k,s} + y_{i+-e_k}) / sum_{k,s} w_{k,s}, w_{k,s} = (Theta_i +
-// Theta_{i+-e_k}) / 2 / dxi_k^2, in the order k = 1, 2, 3 with the minus side first.  FIRST:
-// y = 0, and the spacings are formed from XE (x^n with its ghost maps, staged by the metrics
-// pass that opens the mesh step) and stored; LAST: the limiter bounds of Sec. 4,
-// dl_{k,s}[k] / (2 y_k) with s the sign of y_k, reduced to the instance minimum.
-template <bool FIRST, bool LAST>
-__global__ void __launch_bounds__(NODE_TPB, 3) jacobi3d_kernel(const Inst* __restrict__ insts,
-                                                                const int2* __restrict__ work, int nwork,
-                                                                const Scratch* __restrict__ scr, int sweep,
-                                                                int theta_sel)
+// Theta_{i+-e_k}) / 2 / dxi_k^2, in the order k = 1, 2, 3 with the minus side first, from
+// y = 0.  It forms the spacings from XE (x^n with its ghost maps, staged by the metrics pass
+// that opens the mesh step) and stores them for the later sweeps.  Theta sits in a ring of
+// four staged planes, loaded one plane ahead.  LAST (a single sweep): the limiter bounds of
+// Sec. 4, dl_{k,s}[k] / (2 y_k) with s the sign of y_k, reduced to the instance minimum.
+template <bool LAST>
+__global__ void __launch_bounds__(NODE_TPB, 3) jacobi3d_first_kernel(const Inst* __restrict__ insts,
+                                                                      const int2* __restrict__ work, int nwork,
+                                                                      const Scratch* __restrict__ scr, int theta_sel)
 {
     pdl_entry();
-    __shared__ float sy[FIRST ? 1 : 4][3][M3_PY][M3_PX];
     __shared__ float sth[4][M3_PY][M3_PX];
     __shared__ float se1[2][3][M3_TY][M3_TX];
     __shared__ double sh[32];
@@ -176,45 +135,34 @@ __global__ void __launch_bounds__(NODE_TPB, 3) jacobi3d_kernel(const Inst* __res
         const Edges3 EG(I);
         const long long n = I.ncell;
         const float* th = reinterpret_cast<const float*>(theta_sel ? Sc.th1 : Sc.th0);
-        const float* ys = reinterpret_cast<const float*>(sweep % 2 == 1 ? Sc.xa : Sc.xb);
-        float* yd = reinterpret_cast<float*>(sweep % 2 == 0 ? Sc.xa : Sc.xb);
+        float* yd = reinterpret_cast<float*>(Sc.xa);     // the sweep count starts at 0
         const int g0 = C.b0 + lx, g1 = C.b1 + ly, h0 = C.b0 - 1 + ha, h1 = C.b1 - 1 + hb;
         const bool valid = g0 < I.n[0] && g1 < I.n[1];
         __syncthreads();    // the previous item's readers of the ring are done
         // planes z0 - 1, z0 and z0 + 1 into the ring (z0 + 1 <= z1: the plane above the chunk
         // is a grid plane or the ghost plane i3 = n3)
         for (int q = C.z0 - 1; q <= C.z0 + 1; ++q) {
-            float yo[3], to, yh[3], tv;
-            m3_node<!FIRST>(I, ys, th, g0, g1, q, yo, to);
-            if (ha >= 0) m3_node<!FIRST>(I, ys, th, h0, h1, q, yh, tv);
             const int s = q & 3;
-            sth[s][ly + 1][lx + 1] = to;
-            if (ha >= 0) sth[s][hb][ha] = tv;
-            if (!FIRST) {
-#pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    sy[FIRST ? 0 : s][j][ly + 1][lx + 1] = yo[j];
-                    if (ha >= 0) sy[FIRST ? 0 : s][j][hb][ha] = yh[j];
-                }
-            }
+            sth[s][ly + 1][lx + 1] = m3_theta(I, th, g0, g1, q);
+            if (ha >= 0) sth[s][hb][ha] = m3_theta(I, th, h0, h1, q);
         }
         float ep[3][3], e0h[3], e1h[3], em2[3];
-        m3_edges<FIRST>(I, Sc, EG, C, g0, g1, C.z0, true, ep, e0h, e1h);
-        m3_edge_below<FIRST>(I, Sc, EG, g0, g1, C.z0, em2);
+        m3_edges(I, Sc, EG, C, g0, g1, C.z0, true, ep, e0h, e1h);
+        m3_edge_below(I, Sc, EG, g0, g1, C.z0, em2);
         float bnd = 1.0f;
         for (int z = C.z0; z < C.z1; ++z) {
 #pragma unroll
             for (int j = 0; j < 3; ++j) se1[z & 1][j][ly][lx] = ep[1][j];
             __syncthreads();
-            // loads of the next planes: Theta and y of plane z + 2, the edges of plane z + 1
+            // loads of the next planes: Theta of plane z + 2, the edges of plane z + 1
             const bool more = z + 2 <= C.z1;
-            float yo[3], to, yh[3], tv;
+            float to = 0.0f, tv = 0.0f;
             if (more) {
-                m3_node<!FIRST>(I, ys, th, g0, g1, z + 2, yo, to);
-                if (ha >= 0) m3_node<!FIRST>(I, ys, th, h0, h1, z + 2, yh, tv);
+                to = m3_theta(I, th, g0, g1, z + 2);
+                if (ha >= 0) tv = m3_theta(I, th, h0, h1, z + 2);
             }
             float epn[3][3], e0n[3], e1n[3];
-            m3_edges<FIRST>(I, Sc, EG, C, g0, g1, z + 1, z + 1 < C.z1, epn, e0n, e1n);
+            m3_edges(I, Sc, EG, C, g0, g1, z + 1, z + 1 < C.z1, epn, e0n, e1n);
             // the minus-side spacings of this node: E_0 of the left neighbour (the lane
             // before), E_1 of the node below (the row before), E_2 of the plane below
             float em[3][3];
@@ -241,13 +189,7 @@ __global__ void __launch_bounds__(NODE_TPB, 3) jacobi3d_kernel(const Inst* __res
 #pragma unroll
                         for (int j = 0; j < 3; ++j) {
                             dv[j] = s ? ep[k][j] : -em[k][j];
-                            if (FIRST) {
-                                yv[j] = 0.0f;
-                            } else {
-                                const int b = FIRST ? 0 : c;
-                                yv[j] = k == 0 ? sy[b][j][ly + 1][lx + 2 * s]
-                                      : (k == 1 ? sy[b][j][ly + 2 * s][lx + 1] : sy[FIRST ? 0 : (s ? pp : m)][j][ly + 1][lx + 1]);
-                            }
+                            yv[j] = 0.0f;
                         }
                         dk[k][s] = dv[k];
 #pragma unroll
@@ -278,13 +220,6 @@ __global__ void __launch_bounds__(NODE_TPB, 3) jacobi3d_kernel(const Inst* __res
                 const int s = (z + 2) & 3;
                 sth[s][ly + 1][lx + 1] = to;
                 if (ha >= 0) sth[s][hb][ha] = tv;
-                if (!FIRST) {
-#pragma unroll
-                    for (int j = 0; j < 3; ++j) {
-                        sy[FIRST ? 0 : s][j][ly + 1][lx + 1] = yo[j];
-                        if (ha >= 0) sy[FIRST ? 0 : s][j][hb][ha] = yh[j];
-                    }
-                }
             }
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
@@ -357,7 +292,8 @@ struct J3Smem {
     alignas(16) float e1h[J3_ER][3][M3_TX];
 };
 
-// A later Jacobi sweep of a 3D instance (the arithmetic of jacobi3d_kernel, bit for bit).  The
+// A later Jacobi sweep of a 3D instance (the arithmetic of jacobi3d_first_kernel with y read
+// from the previous sweep, bit for bit that of jacobi_y_kernel).  The
 // planes are staged with cp.async two planes ahead of the update: at plane i3 the block issues
 // Theta and y of plane i3 + 3 and the spacings of plane i3 + 2, then waits for those issued two
 // planes before.  A thread that copied a ghost position across a wall negates the mirrored
@@ -538,8 +474,8 @@ void launch_jacobi3d(bool first, bool last, int grid, cudaStream_t st, const Ins
 {
     const size_t sm = sizeof(J3Smem);
     if (first) {
-        if (last) pdl_launch(jacobi3d_kernel<true, true>, grid, NODE_TPB, 0, st, insts, work, nwork, scr, sweep, theta_sel);
-        else pdl_launch(jacobi3d_kernel<true, false>, grid, NODE_TPB, 0, st, insts, work, nwork, scr, sweep, theta_sel);
+        if (last) pdl_launch(jacobi3d_first_kernel<true>, grid, NODE_TPB, 0, st, insts, work, nwork, scr, theta_sel);
+        else pdl_launch(jacobi3d_first_kernel<false>, grid, NODE_TPB, 0, st, insts, work, nwork, scr, theta_sel);
     } else {
         if (last) pdl_launch(jacobi3d_async_kernel<true>, grid, NODE_TPB, sm, st, insts, work, nwork, scr, sweep, theta_sel);
         else pdl_launch(jacobi3d_async_kernel<false>, grid, NODE_TPB, sm, st, insts, work, nwork, scr, sweep, theta_sel);
