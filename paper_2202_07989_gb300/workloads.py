@@ -237,11 +237,13 @@ def shock_bubble_2d(nx: int = 400, ny: int = 200, Ms: float = 1.22, radius: floa
     """Two-component shock-bubble interaction shaped like Example 5.8.
 
     Gas 1 (Gamma 1.4, p_inf 0, c_v 1) at rest with rho = p = 1; a Mach Ms shock at
-    x_1 = shock_x moves left into it; a circular bubble of gas 2 (density ratio
-    rho_ratio at the same p and T).  Pure regions carry a trace eps = 0.03 of the other
-    species, the value of Example 5.8 (the scheme is not positivity preserving, and a
-    trace of 1e-5 goes negative at the material interface in the first stage).  Reflecting top and bottom, inflow on the right, outflow on the left.
-    Returns (problem, U point values, x)."""
+    x_1 = shock_x moves left into it; a circular bubble of gas 2 at the same pressure, with
+    R_2 = R_1 / rho_ratio and density rho_ratio (the pure gases are then at equal p and T).
+    Pure regions carry a trace eps = 0.03 of the other species, the value of Example 5.8
+    (the scheme is not positivity preserving, and a trace of 1e-5 goes negative at the
+    material interface in the first stage); the traces shift the mixture temperatures of
+    the bubble and its surroundings apart.  Reflecting top and bottom, inflow on the right,
+    outflow on the left.  Returns (problem, U point values, x)."""
     cv1 = 1.0
     R1 = cv1 * 0.4
     R2 = R1 / rho_ratio
