@@ -296,8 +296,9 @@ def shock_bubble_3d(n: int = 128, Ms: float = 1.22, radius: float = 0.2, gamma2:
                     rho_ratio: float = 0.138, eps: float = 0.03, mu: int = 10) -> Tuple[Problem, np.ndarray, np.ndarray]:
     """3D two-component shock-bubble shaped like Example 5.10: (2n, n, n) cells on [0, 2] x [0, 1]^2,
     gas 1 (Gamma 1.4) at rest with rho = p = 1, a Mach Ms shock at x_1 = 1.4 moving left, a
-    spherical bubble of radius 0.2 at (1, 0.5, 0.5) of gas 2 (density ratio rho_ratio at equal p, T),
-    trace eps of the absent species; reflecting side walls, inflow right, outflow left."""
+    spherical bubble of radius 0.2 at (1, 0.5, 0.5) of gas 2 (density ratio rho_ratio, the pure
+    gases' ratio at equal p and T), trace eps of the absent species (which shifts the mixture
+    temperatures apart at equal pressure); reflecting side walls, inflow right, outflow left."""
     cv1 = 1.0
     R1 = cv1 * 0.4
     R2 = R1 / rho_ratio
