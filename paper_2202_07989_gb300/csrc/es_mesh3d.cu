@@ -3,8 +3,8 @@
 // planes it reads (its nodes plus a one-node halo in i1 and i2) sit in a ring of shared-memory
 // planes: the ghost maps of the boundary conditions are applied once, when a plane is staged,
 // and every node value is loaded once per pass plus the halo, so the stencil arithmetic runs
-// without boundary branches.  The arithmetic per node is that of the per-node kernels
-// (jacobi_y_kernel, filter_kernel), term for term.
+// without boundary branches.  A sweep's arithmetic per node is that of jacobi_y_kernel, term
+// for term; the filter sums filter_kernel's weights one direction at a time.
 #include "es_mesh.cuh"
 
 namespace es {
@@ -281,8 +281,8 @@ __device__ __forceinline__ bool m3_source(const Inst& I, int g0, int g1, int g2,
 }
 
 // shared memory of the later sweeps: Theta and y planes in a ring of six (three read by a
-// plane's update, three in flight), the spacings E_k of a plane (this column's nodes, the
-// E_0 left of each row, the E_1 below the first row) in a ring of four
+// plane's update, two in flight, one spare), the spacings E_k of a plane (this column's nodes,
+// the E_0 left of each row, the E_1 below the first row) in a ring of four
 constexpr int J3_YR = 6, J3_ER = 4;
 struct J3Smem {
     float y[J3_YR][3][M3_PY][M3_PX];
@@ -293,11 +293,12 @@ struct J3Smem {
 };
 
 // A later Jacobi sweep of a 3D instance (the arithmetic of jacobi3d_first_kernel with y read
-// from the previous sweep, bit for bit that of jacobi_y_kernel).  The
-// planes are staged with cp.async two planes ahead of the update: at plane i3 the block issues
-// Theta and y of plane i3 + 3 and the spacings of plane i3 + 2, then waits for those issued two
-// planes before.  A thread that copied a ghost position across a wall negates the mirrored
-// component of y after its copy lands, before the block barrier.
+// from the previous sweep, bit for bit that of jacobi_y_kernel).  The planes are staged with
+// cp.async two planes ahead of the update: at plane i3 each thread waits for the copies it
+// issued two planes before (Theta and y up to plane i3 + 1, the spacings of plane i3), and
+// after the block barrier the block issues Theta and y of plane i3 + 3 and the spacings of
+// plane i3 + 2.  A thread that copied a ghost position across a wall negates the mirrored
+// component of y after its copy lands, before the barrier.
 template <bool LAST>
 __global__ void __launch_bounds__(NODE_TPB, 3) jacobi3d_async_kernel(const Inst* __restrict__ insts,
                                                                       const int2* __restrict__ work, int nwork,
