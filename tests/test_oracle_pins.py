@@ -781,3 +781,146 @@ def test_limiter_keeps_node_order_and_mesh_velocity():
     xmu = o.jacobi(x, th)
     np.testing.assert_allclose(xdot, dtau * (xmu - x) / dt, rtol=1e-13, atol=1e-15)
     assert abs(o.limiter(x, xmu) - dtau) == 0.0
+
+
+# ---------------------------------------------------------------------------
+# Jacobi sweeps: the converged discrete mesh equation with a varying monitor
+# ---------------------------------------------------------------------------
+
+def _jacobi_equilibrium(theta_line, a, b, periodic):
+    """Node positions along one line at the fixed point of the discrete mesh equation of
+    Sec. 4 when Theta varies along that line only: Theta_{i+1/2} (x_{i+1} - x_i) = C with
+    Theta_{i+1/2} = (Theta_i + Theta_{i+1}) / 2.  Wall sides: the ghost node is the mirror
+    image 2a - x_0 and carries Theta_0, so the half cell at the wall gives Theta_0 2 (x_0 - a)
+    = C (likewise at b); the spacings fill [a, b].  Periodic sides: the line closes with
+    x_n = x_0 + (b - a) and Theta_n = Theta_0; only the spacings are fixed."""
+    th = np.asarray(theta_line, dtype=np.float64)
+    n = th.size
+    if periodic:
+        half = 0.5 * (th + np.roll(th, -1))                 # Theta_{i+1/2}, i = 0..n-1
+        C = (b - a) / np.sum(1.0 / half)
+        return C / half                                     # the n spacings x_{i+1} - x_i
+    half = 0.5 * (th[:-1] + th[1:])
+    C = (b - a) / (1.0 / (2.0 * th[0]) + np.sum(1.0 / half) + 1.0 / (2.0 * th[-1]))
+    x = np.empty(n)
+    x[0] = a + C / (2.0 * th[0])
+    x[1:] = x[0] + np.cumsum(C / half)
+    return x
+
+
+@pytest.mark.parametrize("bc", ["reflect", "periodic"])
+@pytest.mark.parametrize("d", [2, 3])
+def test_jacobi_converges_to_the_discrete_equilibrium(bc, d):
+    """Theta varying along xi_1 only (by a factor of about 3): after enough Jacobi sweeps the
+    x_1 positions on every xi_1 line reach the equilibrium of the discrete mesh equation
+    with the half-sum weights (Theta_i + Theta_{i+1})/2, wall half cells included; the other
+    coordinates stay uniform.  Weights Theta_i or Theta_{i+1} alone, swapped half weights, or
+    a ghost Theta other than the boundary node's give a different equilibrium."""
+    n = (13, 10, 10)[:d]
+    pb = W.random_problem(d, 1, n, bc=bc).with_(mu=12000)
+    o = Oracle(pb)
+    xi = np.stack(W.xi_nodes(pb))
+    rng = np.random.default_rng(5)
+    th1 = 1.0 + 2.0 * rng.uniform(0.0, 1.0, size=n[0])
+    theta = np.broadcast_to(th1.reshape((1,) * (3 - 1) + (n[0],)), pb.shape).copy()
+    xmu = o.jacobi(xi, theta)
+    a, b = pb.xi_lo[0], pb.xi_lo[0] + pb.length[0]
+    want = _jacobi_equilibrium(th1, a, b, bc == "periodic")
+    for line in xmu[0].reshape(-1, n[0]):
+        if bc == "periodic":
+            got = np.diff(np.concatenate([line, [line[0] + (b - a)]]))
+            np.testing.assert_allclose(got, want, rtol=1e-12)
+        else:
+            np.testing.assert_allclose(line, want, rtol=0, atol=1e-12 * (b - a))
+    for j in range(1, d):
+        np.testing.assert_allclose(xmu[j], xi[j], rtol=0, atol=1e-13)
+    # the equilibrium is not the uniform mesh: the monitor moves nodes by a sizable fraction
+    assert np.abs(xmu[0] - xi[0]).max() > 0.05 * pb.dxi[0]
+
+
+# ---------------------------------------------------------------------------
+# the size of the ES dissipation at a small step
+# ---------------------------------------------------------------------------
+
+def _step_state(pb, rng, eps):
+    """U_L and U_R = U_L + O(eps) (species densities, velocity and pressure moved along a
+    random direction), so every characteristic field jumps."""
+    rl = rng.uniform(0.5, 1.5, size=pb.N)
+    v = rng.uniform(-0.6, 0.6, size=pb.d)
+    p = rng.uniform(0.8, 1.5)
+    dr, dv, dp = rng.uniform(0.5, 1.0, size=pb.N), rng.uniform(-1.0, 1.0, size=pb.d), rng.uniform(0.5, 1.0)
+    UL = W.cons_state(pb, rl, v, p)[: pb.nc]
+    UR = W.cons_state(pb, rl * (1.0 + eps * dr), v + eps * dv, p * (1.0 + eps * dp))[: pb.nc]
+    return UL, UR
+
+
+def _sound_speed(pb, U):
+    """c^2 = Gamma_mix (p + p_inf) / rho of the stiffened mixture (Sec. 1)."""
+    N, d = pb.N, pb.d
+    rho = U[:N].sum()
+    v2 = sum((U[N + m] / rho) ** 2 for m in range(d))
+    cvr = sum(pb.cv[l] * U[l] for l in range(N))
+    pinf = sum(pb.pinf[:N])
+    T = (U[N + d] - 0.5 * rho * v2 - pinf) / cvr
+    rr = sum(pb.R(l) * U[l] for l in range(N))
+    gam = sum(pb.gamma[l] * pb.cv[l] * U[l] for l in range(N)) / cvr
+    p = rr * T - pinf
+    return math.sqrt(gam * (p + pinf) / rho)
+
+
+@pytest.mark.parametrize("d,N,pinf", [(2, 1, 0.0), (2, 2, 1.5), (3, 1, 0.8), (3, 2, 1.5)])
+def test_dissipation_magnitude_at_a_small_step(d, N, pinf):
+    """Eq. (HOstable) between two constant states U_L, U_R = U_L + O(eps) on an affine,
+    translating mesh whose xi_1 normal is rotated off the x axes: only the interface at the
+    step has [[W]] != 0, there [[W]]^WENO = [[W]] up to the WENO epsilon, so Y = I and, by
+    dU/dV = R R^T, the dissipation is D = -1/2 |Lambda| T^T R R^T T [[V]] = -1/2 |Lambda| [[U]]
+    + O(eps^2), with |Lambda| = |J xi_t + L n.v| + L c (a scalar, Sec. 3.4).  (dJU_ES - dJU_EC)
+    at the node left of the step is -D / dxi_1.  The test forms |Lambda| itself from the affine
+    metrics, the mesh velocity and the arithmetic mean state, and checks the error against
+    -1/2 |Lambda| [[U]] falls like eps^2.  A dropped 1/2, a dropped J xi_t, a mixed-up T / T^T
+    or a wrong eigenvector scaling fail it."""
+    n = (24, 14, 14)[:d]
+    pb = W.random_problem(d, N, n, bc="reflect", pinf=pinf)
+    if N == 2 and pinf:
+        pb = pb.with_(pinf=(pinf, 0.5 * pinf))
+    # the WENO epsilon is set far below jump^4 so that the WENO-MR weights pick the one-sided
+    # constant candidate at the step exactly (with the paper's 1e-10 they would blend in the
+    # higher-order candidates for jumps below about 1e-2)
+    pb = pb.with_(bc=((W.OUTFLOW, W.OUTFLOW),) * 3, inflow=None, weno_eps=1e-40)
+    A = np.eye(d) + np.array([[0.0, 0.35, -0.2], [-0.25, 0.1, 0.3], [0.15, -0.3, 0.05]])[:d, :d]
+    Jdet = np.linalg.det(A)
+    xi = np.stack(W.xi_nodes(pb))
+    x = np.einsum("jk,k...->j...", A, xi)
+    bvel = np.array([0.3, -0.2, 0.25])[:d]
+    xdot = np.broadcast_to(bvel.reshape((d,) + (1,) * 3), (d,) + pb.shape).copy()
+    # J xi_1 / x_j: the first row of the cofactor matrix of A (J = det A); J xi_1 / t
+    Mx = np.linalg.inv(A)[0] * Jdet
+    Mt = -float(bvel @ Mx)
+    L = float(np.linalg.norm(Mx))
+    nrm = Mx / L
+    i_step = n[0] // 2
+    mid = tuple(k // 2 for k in n[1:][::-1])          # a node far from the xi_2, xi_3 sides
+    errs = []
+    for eps in (0.04, 0.02, 0.01):
+        rng = np.random.default_rng(100 + 10 * d + N)
+        UL, UR = _step_state(pb, rng, eps)
+        right = (np.arange(n[0]) >= i_step).reshape((1,) * 2 + (n[0],))
+        U = np.where(right[None], UR.reshape(-1, 1, 1, 1), UL.reshape(-1, 1, 1, 1))
+        J = np.full(pb.shape, Jdet)
+        JU = U * J
+        dES, _ = Oracle(pb).rhs(JU, J, x, xdot)
+        dEC, _ = Oracle(pb.with_(es=False)).rhs(JU, J, x, xdot)
+        idx = (slice(None),) + ((mid[0],) if d == 3 else (0,)) + (mid[-1], i_step - 1)
+        D = -(dES - dEC)[idx] * pb.dxi[0]
+        Ubar = 0.5 * (UL + UR)
+        rho = Ubar[:N].sum()
+        vbar = Ubar[N:N + d] / rho
+        lam = abs(Mt + L * float(nrm @ vbar)) + L * _sound_speed(pb, Ubar)
+        want = -0.5 * lam * (UR - UL)
+        errs.append(np.abs(D - want).max() / np.abs(want).max())
+        # the node right of the step sees the same flux with the other sign
+        idx_r = idx[:-1] + (i_step,)
+        np.testing.assert_allclose(-(dES - dEC)[idx_r] * pb.dxi[0], -D, rtol=1e-9, atol=1e-12 * np.abs(D).max())
+    # relative error O(eps): halving eps halves it (absolute error O(eps^2))
+    assert errs[-1] < 0.02, errs
+    assert errs[1] / errs[2] > 1.6 and errs[0] / errs[1] > 1.6, errs
