@@ -23,5 +23,22 @@ def build(force: bool = False) -> str:
     return LIB
 
 
+OPC_SRC = os.path.join(HERE, "opcount.cpp")
+OPC_LIB = os.path.join(HERE, "libopcount.so")
+
+
+def build_opcount(force: bool = False) -> str:
+    """The operation-counting build of the same oracle source (opcount.cpp includes
+    es_oracle.c with double replaced by a counting binary64 type), oracle/libopcount.so."""
+    deps = [SRC, OPC_SRC, os.path.join(HERE, "es_oracle.h")]
+    if not force and os.path.exists(OPC_LIB) and os.path.getmtime(OPC_LIB) >= max(os.path.getmtime(d) for d in deps):
+        return OPC_LIB
+    tmp = OPC_LIB + ".tmp%d" % os.getpid()
+    cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-o", tmp, OPC_SRC]
+    subprocess.check_call(cmd)
+    os.replace(tmp, OPC_LIB)
+    return OPC_LIB
+
+
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv))

@@ -31,45 +31,51 @@ class OrConfig(C.Structure):
     ]
 
 
+def bind(L):
+    """Set the C signatures of the oracle's entry points on a loaded library (the plain build
+    or the operation-counting build, which export the same functions)."""
+    dp = C.POINTER(C.c_double)
+    cp = C.POINTER(OrConfig)
+    sig = {
+        "or_alpha": (None, [C.c_int, dp]),
+        "or_primitives": (None, [cp, dp, dp, dp, dp, dp]),
+        "or_entropy_vars": (None, [cp, dp, dp]),
+        "or_eta": (C.c_double, [cp, dp]),
+        "or_phi": (C.c_double, [cp, dp]),
+        "or_phys_flux": (None, [cp, C.c_int, dp, dp]),
+        "or_logmean": (C.c_double, [C.c_double, C.c_double]),
+        "or_Utilde": (None, [cp, dp, dp, dp]),
+        "or_Ftilde": (None, [cp, C.c_int, dp, dp, dp]),
+        "or_ec_pair": (None, [cp, dp, dp, dp, dp, dp]),
+        "or_eigvec_point": (None, [cp, dp, dp]),
+        "or_eigvec_avg": (None, [cp, dp, dp, dp, dp]),
+        "or_weno_mr": (C.c_double, [dp, dp, C.c_double]),
+        "or_weno_js": (C.c_double, [dp, C.c_double]),
+        "or_metrics": (None, [cp, dp, dp, dp]),
+        "or_init_J": (None, [cp, dp, dp]),
+        "or_rhs": (None, [cp, dp, dp, dp, dp, dp, dp]),
+        "or_rk_step": (None, [cp, dp, dp, dp, dp, C.c_double]),
+        "or_rhs_margins": (None, [cp, dp, dp, dp, dp, dp, dp, dp]),
+        "or_cfl_dt": (C.c_double, [cp, dp, dp, dp]),
+        "or_monitor": (None, [cp, dp, dp, dp]),
+        "or_schlieren": (None, [cp, dp, dp, dp, C.c_double, C.c_double, dp]),
+        "or_filter": (None, [cp, dp]),
+        "or_jacobi": (None, [cp, dp, dp, dp]),
+        "or_limiter": (C.c_double, [cp, dp, dp]),
+        "or_mesh_redistribute": (None, [cp, dp, dp, dp, C.c_double, dp, dp]),
+        "or_entropy": (None, [cp, dp, dp, dp, dp, dp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
 def lib():
     global _lib
     if _lib is None:
-        _lib = C.CDLL(_build.build())
-        dp = C.POINTER(C.c_double)
-        cp = C.POINTER(OrConfig)
-        sig = {
-            "or_alpha": (None, [C.c_int, dp]),
-            "or_primitives": (None, [cp, dp, dp, dp, dp, dp]),
-            "or_entropy_vars": (None, [cp, dp, dp]),
-            "or_eta": (C.c_double, [cp, dp]),
-            "or_phi": (C.c_double, [cp, dp]),
-            "or_phys_flux": (None, [cp, C.c_int, dp, dp]),
-            "or_logmean": (C.c_double, [C.c_double, C.c_double]),
-            "or_Utilde": (None, [cp, dp, dp, dp]),
-            "or_Ftilde": (None, [cp, C.c_int, dp, dp, dp]),
-            "or_ec_pair": (None, [cp, dp, dp, dp, dp, dp]),
-            "or_eigvec_point": (None, [cp, dp, dp]),
-            "or_eigvec_avg": (None, [cp, dp, dp, dp, dp]),
-            "or_weno_mr": (C.c_double, [dp, dp, C.c_double]),
-            "or_weno_js": (C.c_double, [dp, C.c_double]),
-            "or_metrics": (None, [cp, dp, dp, dp]),
-            "or_init_J": (None, [cp, dp, dp]),
-            "or_rhs": (None, [cp, dp, dp, dp, dp, dp, dp]),
-            "or_rk_step": (None, [cp, dp, dp, dp, dp, C.c_double]),
-            "or_rhs_margins": (None, [cp, dp, dp, dp, dp, dp, dp, dp]),
-            "or_cfl_dt": (C.c_double, [cp, dp, dp, dp]),
-            "or_monitor": (None, [cp, dp, dp, dp]),
-            "or_schlieren": (None, [cp, dp, dp, dp, C.c_double, C.c_double, dp]),
-            "or_filter": (None, [cp, dp]),
-            "or_jacobi": (None, [cp, dp, dp, dp]),
-            "or_limiter": (C.c_double, [cp, dp, dp]),
-            "or_mesh_redistribute": (None, [cp, dp, dp, dp, C.c_double, dp, dp]),
-            "or_entropy": (None, [cp, dp, dp, dp, dp, dp]),
-        }
-        for name, (res, args) in sig.items():
-            f = getattr(_lib, name)
-            f.restype = res
-            f.argtypes = args
+        _lib = bind(C.CDLL(_build.build()))
     return _lib
 
 
