@@ -97,6 +97,9 @@ typedef struct es_config {
     int w;                   /* EC flux order 2w (Sec. 3.1): 1, 2 or 3; 0 means 3, the order of the
                                 paper's examples.  The metric operator delta_k and the GCL flux
                                 take the same order; the dissipation (5th-order WENO) does not */
+    int march_planes;        /* 3D mixed form: planes per chunk of the mesh-step kernels that march
+                                along i3 (a schedule, not part of the method; it changes no result).
+                                0 = automatic (about four waves of CTAs); otherwise 4 <= value <= n[2] */
 } es_config;
 
 typedef struct es_ctx es_ctx;
@@ -301,6 +304,19 @@ es_status es_check_half_sums(const float* a, const float* b, int n, double* out,
  * general: DEVICE arrays of n binary32 values. */
 es_status es_check_logmean_small(const float* a, const float* b, const float* del, int n, float* fast, float* general,
                                  void* stream);
+
+/* ALU throughput microbenchmark: the measured denominators of the flux kernels'
+ * roofline (the paper has no counterpart; its method is bound by the plain FP32 and
+ * FP64 pipes, not by HBM or tensor cores).  Launches `grid` CTAs of 256 threads; every
+ * thread runs `iters` rounds of 16 independent fused multiply-add chains of kind
+ * 0 = binary32 (FFMA), 1 = paired binary32 (FFMA2: two lanes per instruction) or
+ * 2 = binary64 (DFMA).  The caller times the launch on `stream` (CUDA events).
+ * sink (written, DEVICE): grid * 256 doubles, each thread's chain sum, which keeps
+ * every operation live.  es_alu_peak_flops returns the flops of such a launch
+ * (2 per multiply-add lane), 0 for bad arguments.  ES_ERR_ARG for a bad kind, a
+ * non-positive grid or iters, or a null sink. */
+es_status es_alu_peak(int kind, int grid, int iters, double* sink, void* stream);
+long long es_alu_peak_flops(int kind, int grid, int iters);
 
 /* Reads and clears the sticky device status (synchronises the stream):
  * *flags = bit 0 non-physical state, bit 1 timeout. */

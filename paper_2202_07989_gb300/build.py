@@ -10,7 +10,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libes.so")
 SOURCES = ["es_flux_%s_%s.cu" % (case, kind) for case in ("2d1", "2d2", "3d1", "3d2") for kind in ("mr", "js")] + \
     ["es_flux2d_%d_%s.cu" % (ns, kind) for ns in (1, 2) for kind in ("mr", "js")] + \
-    ["es_geom.cu", "es_mesh.cu", "es_mesh3d.cu", "es_api.cu"]
+    ["es_geom.cu", "es_mesh.cu", "es_mesh3d.cu", "es_api.cu", "es_peak.cu"]
 HEADERS = ["es_common.cuh", "es_kernels.cuh", "es_mesh.cuh", "es_flux_core.cuh", "es_flux_impl.cuh", "es_flux2d_impl.cuh"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-gencode", "arch=compute_103a,code=sm_103a",

@@ -135,6 +135,8 @@ std::string check_cfg(const es_config& g)
     if (g.weno != ES_WENO_MR && g.weno != ES_WENO_JS) return "weno must be ES_WENO_MR or ES_WENO_JS";
     if (g.fixed_mesh != 0 && g.fixed_mesh != 1) return "fixed_mesh must be 0 or 1";
     if (g.w < 0 || g.w > 3) return "w must be 1, 2 or 3 (0: 3)";
+    if (g.march_planes != 0 && (g.d != 3 || g.march_planes < 4 || g.march_planes > g.n[2]))
+        return "march_planes must be 0, or 4..n[2] on a 3D instance";
     return "";
 }
 
@@ -602,7 +604,10 @@ es_status es_create_batch(const es_config* cfgs, int n_inst, es_ctx** out)
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
     for (int i = 0; i < n_inst; ++i) c->hI.push_back(make_inst(cfgs[i]));
-    for (Inst& I : c->hI) I.zc = I.d == 3 ? march_zc(I, c->sms) : 1;
+    for (int i = 0; i < n_inst; ++i) {
+        Inst& I = c->hI[i];
+        I.zc = I.d == 3 ? (cfgs[i].march_planes > 0 ? cfgs[i].march_planes : march_zc(I, c->sms)) : 1;
+    }
     bool ok = true;
     ok = ok && dalloc(c, (void**)&c->dI, sizeof(Inst) * n_inst);
     size_t rsz = c->mixed ? sizeof(float) : sizeof(double);
@@ -1251,8 +1256,10 @@ es_status noalloc_scratch(double** out)
     return ES_OK;
 }
 
-// one tile of 256 nodes per block: V.dJU - phi dJ and J eta summed in the same fixed order
-// as the context's entropy reduction
+// one tile of 256 consecutive nodes per block: V.dJU - phi dJ and J eta summed in a
+// deterministic, fixed order (warp shuffles, then the warps in order).  The order differs
+// from the context's entropy reduction, which sums over 2D node tiles, so the two calls
+// agree to round-off, not bit for bit
 __global__ void noalloc_entropy_partial_kernel(Inst I, const double* __restrict__ JU, const double* __restrict__ J,
                                                const double* __restrict__ dJU, const double* __restrict__ dJ,
                                                double* __restrict__ partial)

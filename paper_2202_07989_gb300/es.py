@@ -41,7 +41,7 @@ class EsConfig(C.Structure):
         ("chi", C.c_double * 3), ("weno_eps", C.c_double), ("cfl", C.c_double),
         ("n_sigma", C.c_int), ("sigma", C.c_int * 4), ("alpha", C.c_double * 4),
         ("mu", C.c_int), ("nf", C.c_int), ("weno", C.c_int), ("fixed_mesh", C.c_int),
-        ("sigma_op", C.c_int * 4), ("w", C.c_int),
+        ("sigma_op", C.c_int * 4), ("w", C.c_int), ("march_planes", C.c_int),
     ]
 
 
@@ -83,6 +83,8 @@ def lib():
             "es_check_logmean_small": (C.c_int, [dp, dp, dp, C.c_int, dp, dp, vp]),
             "es_entropy_production_noalloc": (C.c_int, [C.POINTER(EsConfig), dp, dp, dp, dp, dp, vp]),
             "es_profile_read": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.c_int]),
+            "es_alu_peak": (C.c_int, [C.c_int, C.c_int, C.c_int, dp, vp]),
+            "es_alu_peak_flops": (C.c_longlong, [C.c_int, C.c_int, C.c_int]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -92,8 +94,11 @@ def lib():
     return _lib
 
 
-def make_config(pb: Problem, precision: int = FP64) -> EsConfig:
+def make_config(pb: Problem, precision: int = FP64, march_planes: int = 0) -> EsConfig:
+    """The C es_config of a problem; march_planes fixes the plane chunk of the 3D mixed
+    mesh-step kernels (0 = automatic), a schedule choice that changes no result."""
     c = EsConfig()
+    c.march_planes = int(march_planes)
     c.d, c.N = pb.d, pb.N
     for k in range(3):
         c.n[k] = pb.n[k] if k < pb.d else 1
@@ -143,14 +148,14 @@ def _ptr(t: Optional[torch.Tensor], fields: int, pb: Problem, name: str) -> Opti
 class Context:
     """An es_ctx for one instance (or a batch of instances sharing d, N, precision, mu, nf)."""
 
-    def __init__(self, problems, precision: int = FP64):
+    def __init__(self, problems, precision: int = FP64, march_planes: int = 0):
         if isinstance(problems, Problem):
             problems = [problems]
         self.problems = list(problems)
         self.pb = self.problems[0]
         self.precision = precision
         self.L = lib()
-        cfgs = (EsConfig * len(self.problems))(*[make_config(p, precision) for p in self.problems])
+        cfgs = (EsConfig * len(self.problems))(*[make_config(p, precision, march_planes) for p in self.problems])
         h = C.c_void_p()
         if len(self.problems) == 1:
             st = self.L.es_create(cfgs, C.byref(h))
@@ -410,3 +415,18 @@ def es_entropy_production_noalloc(pb: Problem, JU, J, dJU, dJ, out2, precision: 
     return lib().es_entropy_production_noalloc(C.byref(cfg), _ptr(JU, pb.nc, pb, "JU"), _ptr(J, 1, pb, "J"),
                                                 _ptr(dJU, pb.nc, pb, "dJU"), _ptr(dJ, 1, pb, "dJ"),
                                                 C.c_void_p(out2.data_ptr()), _stream())
+
+
+ALU_KINDS = ("fp32_ffma", "fp32_ffma2", "fp64_dfma")
+
+
+def es_alu_peak(kind: int, grid: int, iters: int, sink: torch.Tensor) -> int:
+    """Launch the ALU throughput microbenchmark (kind 0 FFMA, 1 FFMA2, 2 DFMA) on the current
+    stream; sink is a float64 CUDA tensor of at least grid * 256 entries.  Returns the flops of
+    the launch; the caller times it."""
+    if not (sink.is_cuda and sink.dtype == torch.float64 and sink.is_contiguous() and sink.numel() >= grid * 256):
+        raise EsError("sink must be a contiguous float64 CUDA tensor of grid * 256 entries")
+    st = lib().es_alu_peak(int(kind), int(grid), int(iters), C.c_void_p(sink.data_ptr()), _stream())
+    if st != 0:
+        raise EsError("es_alu_peak: %s" % ES_STATUS.get(st, st))
+    return int(lib().es_alu_peak_flops(int(kind), int(grid), int(iters)))

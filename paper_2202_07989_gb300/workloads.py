@@ -343,11 +343,10 @@ def water_air_3d(n: int = 256, mu: int = 10, eps: float = 1e-5) -> Tuple[Problem
     return pb, U, x
 
 
-def batched_2d(count: int = 64, nmin: int = 96, nmax: int = 512, seed: int = SEED,
-               mu: int = 5) -> List[Tuple[Problem, np.ndarray, np.ndarray]]:
-    """Independent two-component stiffened-gas shock-bubble instances on [0, 1]^2 with
-    n ~ U{nmin..nmax} (square grids), shock Mach ~ U(1.1, 3), bubble radius ~ U(0.1, 0.3),
-    gas-2 Gamma ~ U(1.1, 4.4) and p_inf,2 ~ U(0, 10); shock at x_1 = 0.8 moving left."""
+def batched_params(count: int = 64, nmin: int = 96, nmax: int = 512, seed: int = SEED) -> List[dict]:
+    """The seeded draws of the batched workload, one dict per instance: grid n ~ U{nmin..nmax}
+    (square), shock Mach Ms ~ U(1.1, 3), bubble radius r ~ U(0.1, 0.3), gas-2 Gamma g2 ~
+    U(1.1, 4.4) and p_inf,2 pi2 ~ U(0, 10)."""
     rng = np.random.default_rng(seed)
     out = []
     for _ in range(count):
@@ -356,6 +355,77 @@ def batched_2d(count: int = 64, nmin: int = 96, nmax: int = 512, seed: int = SEE
         r = float(rng.uniform(0.1, 0.3))
         g2 = float(rng.uniform(1.1, 4.4))
         pi2 = float(rng.uniform(0.0, 10.0))
-        out.append(shock_bubble_2d(n, n, Ms=Ms, radius=r, gamma2=g2, pinf2=pi2, length=(1.0, 1.0),
-                                   shock_x=0.8, centre=(0.5, 0.5), mu=mu))
+        out.append(dict(n=n, Ms=Ms, r=r, g2=g2, pi2=pi2))
     return out
+
+
+def batched_instance(prm: dict, n: Optional[int] = None, mu: int = 5) -> Tuple[Problem, np.ndarray, np.ndarray]:
+    """One instance of the batched workload from its draws (batched_params), on its own grid or
+    on an n x n grid: a two-component stiffened-gas shock-bubble on [0, 1]^2, shock at x_1 = 0.8
+    moving left, bubble at the centre."""
+    n = prm["n"] if n is None else n
+    return shock_bubble_2d(n, n, Ms=prm["Ms"], radius=prm["r"], gamma2=prm["g2"], pinf2=prm["pi2"],
+                           length=(1.0, 1.0), shock_x=0.8, centre=(0.5, 0.5), mu=mu)
+
+
+def batched_2d(count: int = 64, nmin: int = 96, nmax: int = 512, seed: int = SEED,
+               mu: int = 5) -> List[Tuple[Problem, np.ndarray, np.ndarray]]:
+    """Independent two-component stiffened-gas shock-bubble instances on [0, 1]^2 with
+    n ~ U{nmin..nmax} (square grids), shock Mach ~ U(1.1, 3), bubble radius ~ U(0.1, 0.3),
+    gas-2 Gamma ~ U(1.1, 4.4) and p_inf,2 ~ U(0, 10); shock at x_1 = 0.8 moving left."""
+    return [batched_instance(prm, mu=mu) for prm in batched_params(count, nmin, nmax, seed)]
+
+
+def shard(sizes: Sequence[int], world: int, rank: int) -> List[int]:
+    """The instances rank `rank` of `world` advances when independent instances of the given
+    sizes (cells) are split across ranks: largest first, each to the rank with the fewest
+    cells so far (ties to the lower rank).  Every instance goes to exactly one rank."""
+    load = [0] * world
+    owner = [0] * len(sizes)
+    for i in sorted(range(len(sizes)), key=lambda j: (-sizes[j], j)):
+        r = min(range(world), key=lambda q: (load[q], q))
+        owner[i] = r
+        load[r] += sizes[i]
+    return [i for i in range(len(sizes)) if owner[i] == rank]
+
+
+def shock_bubble_3d_stiffened(n: int = 80, eps: float = 0.05, Ms: float = 10.0, mu: int = 10, nf: int = 3,
+                              shock_cells: float = 1.0,
+                              fixed_mesh: bool = True) -> Tuple[Problem, np.ndarray, np.ndarray]:
+    """3D shock-bubble interaction II of Example 5.11: on [0, 445] x [-44.5, 44.5]^2 with
+    (5n, n, n) cells, a bubble of ideal gas (species 2: Gamma 1.4, p_inf 0) of radius 25 at
+    (225, 0, 0) in a stiffened gas (species 1: Gamma 3, p_inf 100), c_v = 1 for both; a Mach Ms
+    shock at x_1 = 275 moving left.  States (rho_1, rho_2, v, p): surroundings ahead of the
+    shock (1 - eps, eps, 0, 100), behind it the Rankine-Hugoniot state of the stiffened gas
+    (at Mach 10: 1.980198 - eps, eps, (-121.2497, 0, 0), 29800), bubble (eps, 5 - eps, 0, 100),
+    eps = 0.05.  Monitor on (rho_1, p) with alpha (500, 500), WENO-MR linear weights
+    (0.95, 0.045, 0.005) as in Example 5.10, CFL 0.3.  Sides as in the 2D shock-bubble
+    (Example 5.8) extended to 3D: reflecting walls in x_2 and x_3, outflow on the left, inflow
+    of the post-shock state on the right.
+
+    The shock is spread over about `shock_cells` cells (a tanh profile in x_1 between the two
+    states; 0 = the sharp step): a sharp Mach 10 step drives the trace rho_2 negative behind it
+    in the first stage.  fixed_mesh = True is the paper's uniform-mesh form of the example
+    (UM-WENOMR); from a uniform start mesh the moving-mesh form's first mesh step moves the
+    nodes at the bubble half a cell per step and drives the traces negative there."""
+    pb = Problem(d=3, N=2, n=(5 * n, n, n), xi_lo=(0.0, -44.5, -44.5), length=(445.0, 89.0, 89.0),
+                 bc=((OUTFLOW, INFLOW), (REFLECT, REFLECT), (REFLECT, REFLECT)),
+                 gamma=(3.0, 1.4), cv=(1.0, 1.0), pinf=(100.0, 0.0), es=True, cfl=0.3,
+                 chi=(0.95, 0.045, 0.005), sigma=(SIG_RHO1, SIG_P), alpha=(500.0, 500.0), mu=mu, nf=nf,
+                 fixed_mesh=fixed_mesh)
+    x = np.stack(xi_nodes(pb))
+    inside = (x[0] - 225.0) ** 2 + x[1] ** 2 + x[2] ** 2 < 25.0 ** 2
+    rho_s, u_s, p_s = _post_shock(pb, Ms, 1.0, 100.0)     # (1.980198, 121.2497, 29800) at Mach 10
+    if shock_cells > 0:
+        s = 0.5 * (1.0 + np.tanh((x[0] - 275.0) / (shock_cells * pb.dxi[0])))
+    else:
+        s = (x[0] > 275.0).astype(np.float64)
+    r1 = np.where(inside, eps, (1.0 - eps) * (1.0 - s) + (rho_s - eps) * s)
+    r2 = np.where(inside, 5.0 - eps, eps)
+    v1 = -u_s * s
+    z = np.zeros_like(v1)
+    p = 100.0 * (1.0 - s) + p_s * s
+    U = prim_to_cons(pb, [r1, r2], [v1, z, z], p)
+    inflow = np.zeros((3, 2, 8))
+    inflow[0, 1] = cons_state(pb, [rho_s - eps, eps], [-u_s, 0.0, 0.0], p_s)
+    return pb.with_(inflow=inflow), U, x

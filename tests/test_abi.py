@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     src = open(os.path.join(ROOT, "include", "es.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:es_status|void|const char\*|int|unsigned long long)\s+\**(\w+)\s*\(", src, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:es_status|void|const char\*|int|unsigned long long|long long)\s+\**(\w+)\s*\(", src, flags=re.M)))
 
 
 @pytest.fixture(scope="module")

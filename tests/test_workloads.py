@@ -82,3 +82,61 @@ def test_shock_bubble_fields():
     np.testing.assert_allclose(rho_l[1][bubble] + eps, ratio * (1.0 + 0.0), rtol=1e-12)
     np.testing.assert_allclose(rho_l[1][ambient], eps, rtol=1e-14)
     np.testing.assert_allclose(rho_l[0][bubble], eps, rtol=1e-14)
+
+
+def test_stiffened_3d_shock_bubble_fields():
+    """Example 5.11's input: at Mach 10 the post-shock state of the stiffened gas (Gamma 3,
+    p_inf 100) ahead of which rho = 1, p = 100 is the one the paper prints (1.980198,
+    -121.2497, 29800); the bubble of ideal gas (rho_2 = 5 - eps) and the surroundings sit at
+    p = 100; the inflow side carries the post-shock state.  The sharp form has the pure states
+    on both sides of x_1 = 275; the default spreads the shock over about one cell, every node
+    a state between the two (monotone in x_1), the bubble untouched."""
+    pb, U, x = W.shock_bubble_3d_stiffened(8, shock_cells=0.0)
+    assert pb.n == (40, 8, 8) and pb.N == 2 and pb.d == 3 and pb.pinf == (100.0, 0.0)
+    rs, us, ps = W._post_shock(pb, 10.0, 1.0, 100.0)
+    assert abs(rs - 1.980198) < 1e-6 and abs(us - 121.2497) < 1e-4 and abs(ps - 29800.0) < 1e-9
+    o = Oracle(pb)
+
+    def prims(U_):
+        prim = [o.primitives(u) for u in U_.reshape(pb.nc, -1).T]
+        shape = U_.shape[1:]
+        rho_l = [np.array([q[0][l] for q in prim]).reshape(shape) for l in range(2)]
+        v1 = np.array([q[1][0] for q in prim]).reshape(shape)
+        p = np.array([q[3] for q in prim]).reshape(shape)
+        return rho_l, v1, p
+
+    rho_l, v1, p = prims(U)
+    eps = 0.05
+    behind = x[0] > 275.0
+    bubble = (x[0] - 225.0) ** 2 + x[1] ** 2 + x[2] ** 2 < 25.0 ** 2
+    assert bubble.any() and behind.any() and not (bubble & behind).any()
+    np.testing.assert_allclose(p[~behind], 100.0, rtol=1e-12)
+    np.testing.assert_allclose(rho_l[1][bubble], 5.0 - eps, rtol=1e-14)
+    np.testing.assert_allclose(rho_l[0][~behind & ~bubble], 1.0 - eps, rtol=1e-14)
+    np.testing.assert_allclose(p[behind], ps, rtol=1e-12)
+    np.testing.assert_allclose(v1[behind], -us, rtol=1e-12)
+    np.testing.assert_allclose(rho_l[0][behind], rs - eps, rtol=1e-14)
+    infl = o.primitives(pb.inflow[0, 1][: pb.nc])
+    assert abs(infl[3] - ps) <= 1e-9 * ps and abs(infl[1][0] + us) <= 1e-12 * us
+    # the spread shock: pressure and velocity between the two states, monotone along x_1
+    pb1, U1, x1 = W.shock_bubble_3d_stiffened(8)
+    rho_l1, v11, p1 = prims(U1)
+    assert (p1 >= 100.0 - 1e-9).all() and (p1 <= ps * (1 + 1e-12)).all()
+    assert (np.diff(p1, axis=2) >= -1e-9).all() and (np.diff(v11, axis=2) <= 1e-12).all()
+    np.testing.assert_allclose(rho_l1[1][bubble], 5.0 - eps, rtol=1e-14)
+    mid = np.abs(x1[0] - 275.0) < 0.5 * pb1.dxi[0] + 1e-9
+    assert mid.any() and (p1[mid] > 100.0 + 0.1 * (ps - 100.0)).all() and (p1[mid] < ps - 0.1 * (ps - 100.0)).all()
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 4, 8])
+def test_batch_shard_partitions_the_instances(world):
+    """The per-rank shares of the batched workload are disjoint, cover every instance, and no
+    rank carries more than the mean share plus the largest instance (largest first to the
+    least loaded rank)."""
+    sizes = [p["n"] ** 2 for p in W.batched_params(64)]
+    shares = [W.shard(sizes, world, r) for r in range(world)]
+    flat = sorted(i for s in shares for i in s)
+    assert flat == list(range(64))
+    loads = [sum(sizes[i] for i in s) for s in shares]
+    assert max(loads) <= sum(sizes) / world + max(sizes)
+    assert W.shard(sizes, world, 0) == shares[0]          # deterministic
