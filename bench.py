@@ -41,10 +41,42 @@ WORKLOAD = ("2D two-component stiffened-gas shock-bubble, 400x200 cells on [0,2]
             "(Gamma2 1.648, density ratio 0.138), adaptive moving mesh (monitor sqrt(1+alpha|grad rho|^2/max), "
             "alpha 100, 3 filter passes, 5 Jacobi sweeps per step), sixth-order EC + WENO-MR ES flux, SSP-RK3, CFL 0.4")
 
-# peaks: FP32 from the SM count and maximum clock (152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz);
-# FP64 as stated for GB300 (1.25 TFLOP/s)
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-FP64_PEAK_TFLOPS = 1.25
+# nominal peaks, for context beside the measured ones: FP32 from the SM count and maximum clock
+# (152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz); FP64 as stated for GB300 (1.25 TFLOP/s)
+FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def measure_alu_peaks(torch, seconds=0.6):
+    """Fused multiply-add throughput of the FP32 (FFMA, paired FFMA2) and FP64 (DFMA) pipes from
+    the library's microbenchmark (es_alu_peak), timed with CUDA events on the launch stream:
+    launches of about 10 ms repeated for `seconds` per kind; the best launch counts.  The SM
+    clock is sampled meanwhile (median under load reported; no clock is set)."""
+    from paper_2202_07989_gb300 import es
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    grid = sms * 8
+    sink = torch.empty(grid * 256, dtype=torch.float64, device="cuda")
+    iters = {0: 40000, 1: 20000, 2: 600}
+    out = {"grid_ctas": grid, "threads_per_cta": 256, "chains_per_thread": 16}
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    for kind, name in enumerate(es.ALU_KINDS):
+        es.es_alu_peak(kind, grid, iters[kind], sink)
+        torch.cuda.synchronize()
+        best, t_end = float("inf"), time.perf_counter() + seconds
+        while time.perf_counter() < t_end:
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            flops = es.es_alu_peak(kind, grid, iters[kind], sink)
+            b.record()
+            b.synchronize()
+            best = min(best, a.elapsed_time(b) / 1e3)
+        out[name + "_tflops"] = flops / best / 1e12
+    out["clocks"] = clocks.stop()
+    out["fp32_tflops"] = max(out["fp32_ffma_tflops"], out["fp32_ffma2_tflops"])
+    out["fp64_tflops"] = out["fp64_dfma_tflops"]
+    return out
 
 
 def hbm_peak_gbs():
@@ -81,6 +113,20 @@ def flux_flops_per_interface(D, NS, es=True):
     weno = 96
     column = 8 + NC + 2 * D * D + 12 * NC + 2 * weno + 2 * NC
     return ec + gcl + setup + NC * column + NC
+
+
+def oracle_flops_per_interface(D, NS):
+    """Flops per interface of the residual without its metrics pass, counted on the FP64 oracle
+    by its operation-counting build (tests/golden/op_counts.json, written by python -m
+    oracle.opcount): the method as the paper writes it, every pair of every interface formed
+    from scratch.  Returns (flops, {class: count}) or (None, None) when the file is missing."""
+    path = os.path.join(ROOT, "tests", "golden", "op_counts.json")
+    try:
+        with open(path) as f:
+            c = json.load(f)["cases"]["%dd%d" % (D, NS)]["per_interface_flux"]
+        return float(c["flops"]), c
+    except (OSError, KeyError, ValueError):
+        return None, None
 
 
 def launches_per_step(pb, mixed=True, fused=False):
@@ -225,6 +271,22 @@ class RkOnly(Single):
         self.ctx.es_rk_step(self.JU, self.J, self.x, self.xdot, self.dd)
 
 
+class EntropyLogged(Single):
+    """A full step followed by the entropy diagnostics of the new state (total entropy; the
+    production needs a residual and is not formed), captured together."""
+
+    def __init__(self, pb, U, x, precision, torch):
+        super().__init__(pb, U, x, precision, torch)
+        self.ent = torch.zeros(2, dtype=torch.float64, device="cuda")
+
+    def step(self):
+        super().step()
+        self.ctx.entropy_production(self.JU, self.J, None, None, self.ent)
+
+
+FORM5 = "mixed_3d_stiffened_shock_bubble_800x160x160_um"
+
+
 class Batch:
     """Independent instances advanced by one launch per kernel per stage."""
 
@@ -289,12 +351,15 @@ def is_fused(runner):
     return runner.ctx.pb.d == 2 and runner.ctx.es_get_fusion()[0] >= 0
 
 
-def time_steps(runner, steps, warmup, torch, flush):
+def time_steps(runner, steps, warmup, torch, flush, after=None):
+    """Device time (s) of exactly `steps` steps after `warmup` untimed ones, each step bracketed
+    by CUDA events on the launch stream, L2 rewritten before each; `after(i)` runs after step i,
+    outside the events."""
     for _ in range(warmup):
         runner.run()
     torch.cuda.synchronize()
     total = 0.0
-    for _ in range(steps):
+    for i in range(steps):
         flush.zero_()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
@@ -303,8 +368,19 @@ def time_steps(runner, steps, warmup, torch, flush):
         b.record()
         b.synchronize()
         total += a.elapsed_time(b)
+        if after is not None:
+            after(i)
     torch.cuda.synchronize()
     return total / 1000.0
+
+
+def time_span(runner, min_seconds, torch, flush):
+    """Steps timed as time_steps does until their device time reaches min_seconds: (steps, s)."""
+    total, n = 0.0, 0
+    while total < min_seconds:
+        total += time_steps(runner, 1, 0, torch, flush)
+        n += 1
+    return n, total
 
 
 def kernel_profile(runner, steps, torch):
@@ -344,13 +420,35 @@ def errors_vs(ref_JU, ref_J, pb, JU, J):
 
 
 def oracle_one_step(pb, U, x):
-    """One full oracle step (mesh redistribution + SSP-RK3) of (U, x) from t = 0: (JU, J, x)."""
+    """One full oracle step (mesh redistribution + SSP-RK3; on a fixed mesh the CFL step and
+    SSP-RK3) of (U, x) from t = 0: (JU, J, x)."""
     from oracle.oracle import Oracle
     o = Oracle(pb)
     J = o.init_J(x)
     JU = U * J
+    if pb.fixed_mesh:
+        return o.rk_step(JU, J, x, np.zeros_like(x), o.cfl_dt(JU, J, x))
     xd, dt, dtau = o.mesh_redistribute(JU, J, x)
     return o.rk_step(JU, J, x, xd, dt)
+
+
+def oracle_steps(pb, U, x, marks):
+    """Full oracle steps (mesh redistribution + SSP-RK3; on a fixed mesh the CFL step and SSP-RK3)
+    of (U, x) from t = 0: {k: (JU, J)} after each step count k in marks."""
+    from oracle.oracle import Oracle
+    o = Oracle(pb)
+    J = o.init_J(x)
+    JU = U * J
+    out = {}
+    for k in range(1, max(marks) + 1):
+        if pb.fixed_mesh:
+            JU, J, x = o.rk_step(JU, J, x, np.zeros_like(x), o.cfl_dt(JU, J, x))
+        else:
+            xd, dt, dtau = o.mesh_redistribute(JU, J, x)
+            JU, J, x = o.rk_step(JU, J, x, xd, dt)
+        if k in marks:
+            out[k] = (JU.copy(), J.copy())
+    return out
 
 
 def cpu_baseline_leg(pb, U, x, gpu_after_one, budget_s=20.0):
@@ -430,10 +528,17 @@ def main_ours(args):
     clocks = ClockSampler(local)
     clocks.start()
     t_main = time_steps(main, args.steps, args.warmup, torch, flush)
+    # a sustained span of at least args.min_seconds of the same steps right after the timed
+    # ones, so that the clock record covers a stretch longer than the sampling period
+    n_sus, t_sus = time_span(main, args.min_seconds, torch, flush)
     clk = clocks.stop()
     t_main = max_over_ranks(t_main, "cuda")
     value = pb.ncell * 3 * args.steps * world / t_main
     forms["mixed"] = {"value": pb.ncell * 3 * args.steps / t_main, "ms_per_step": 1e3 * t_main / args.steps}
+    forms["mixed_sustained"] = {"value": pb.ncell * 3 * n_sus / t_sus, "ms_per_step": 1e3 * t_sus / n_sus,
+                                "steps": n_sus, "seconds": t_sus,
+                                "what": "the headline step repeated for at least %.1f s of device time right after "
+                                        "the timed steps (clocks sampled over both)" % args.min_seconds}
 
     # FP64 form
     r64 = runners["fp64"]
@@ -493,16 +598,25 @@ def main_ours(args):
     prof_b = None
     kb = 1
     if not args.no_batched:
+        # the 64 instances are split across the ranks (no data-path communication: instances
+        # share nothing); each rank advances its share in one batched launch per kernel
         insts = W.batched_2d(64)
-        bt = Batch(insts, es.MIXED, torch)
+        total_cells = sum(p.ncell for p, _, _ in insts)
+        mine = W.shard([p.ncell for p, _, _ in insts], world, rank)
+        bt = Batch([insts[i] for i in mine], es.MIXED, torch)
         bt.step()
         torch.cuda.synchronize()
         tiles["batched_mixed"] = tune(bt, batched=True)
         bt.capture()
         kb = max(3, min(args.steps, 10))
-        tb = time_steps(bt, kb, 2, torch, flush)
-        batched = {"value": bt.cells * 3 * kb / tb, "ms_per_step": 1e3 * tb / kb, "instances": len(insts),
-                   "cells": bt.cells}
+        if world > 1:
+            torch.distributed.barrier()
+        tb = max_over_ranks(time_steps(bt, kb, 2, torch, flush), "cuda")
+        batched = {"value": total_cells * 3 * kb / tb, "ms_per_step": 1e3 * tb / kb, "instances": len(insts),
+                   "cells": total_cells, "instances_this_rank": len(mine), "cells_this_rank": bt.cells,
+                   "scaling": "strong",
+                   "split": "the 64 instances split across %d rank(s) by cells (largest first to the least "
+                            "loaded rank); time = slowest rank" % world}
         forms["batched_mixed"] = batched
         prof_b = kernel_profile(bt, kb, torch)
 
@@ -520,6 +634,26 @@ def main_ours(args):
             t3 = time_steps(r3, k3, 2, torch, flush)
             forms[name] = {"value": p3.ncell * 3 * k3 / t3, "ms_per_step": 1e3 * t3 / k3, "cells": p3.ncell}
             del r3
+        # the two-component stiffened 3D case (Example 5.11, p_inf = 100 around an ideal-gas
+        # bubble, Mach 10), uniform-mesh form at the paper's finest grid, 800 x 160 x 160, with the
+        # total entropy formed after every step (inside the timed step)
+        p5, U5, x5 = W.shock_bubble_3d_stiffened(160)
+        r5 = EntropyLogged(p5, U5, x5, es.MIXED, torch)
+        del U5, x5
+        r5.step()
+        r5.reset()
+        tiles[FORM5] = tune(r5)
+        r5.capture()
+        r5.reset()
+        k5 = max(3, min(args.steps, 6))
+        log = []
+        t5 = time_steps(r5, k5, 1, torch, flush, after=lambda i: log.append(float(r5.ent[1])))
+        forms[FORM5] = {"value": p5.ncell * 3 * k5 / t5, "ms_per_step": 1e3 * t5 / k5, "cells": p5.ncell,
+                        "total_entropy_per_step": log, "status": r5.ctx.es_poll_status(),
+                        "what": "Example 5.11 (stiffened gas Gamma 3, p_inf 100; ideal-gas bubble; Mach 10), "
+                                "uniform-mesh form (the paper's UM-WENOMR), 800x160x160 cells, mixed; "
+                                "total entropy formed after every step inside the timed step"}
+        del r5
 
     # end to end: C-ABI call on pinned host buffers, copies inside the timed region
     e2e = None
@@ -545,17 +679,35 @@ def main_ours(args):
     FLUX = ("flux_k1", "flux_k2", "flux_k3", "flux_2d")
     flux_ms = sum(prof_m[k][0] for k in FLUX)
     flux_n = sum(prof_m[k][1] for k in FLUX)
-    per_iface = flux_flops_per_interface(pb.d, pb.N, pb.es)
+    hand_iface = flux_flops_per_interface(pb.d, pb.N, pb.es)
+    oracle_iface, oracle_classes = oracle_flops_per_interface(pb.d, pb.N)
+    # the algorithmic flops per interface: the oracle's counted work; the hand count
+    # of the kernel's contracted arithmetic is reported beside it
+    per_iface = oracle_iface if oracle_iface else hand_iface
     # interfaces of one stage: (n_k + 1) per grid line of each direction
     ifaces_stage = sum((pb.n[k] + 1) * pb.ncell // pb.n[k] for k in range(pb.d))
     fused_m = is_fused(main)
     flops_launch = per_iface * ifaces_stage / (1 if fused_m else pb.d)
     avg_s = flux_ms / flux_n / 1e3 if flux_n else float("nan")
     ach = flops_launch / avg_s / 1e12
-    roofline = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
+    ach_hand = hand_iface * ifaces_stage / (1 if fused_m else pb.d) / avg_s / 1e12
+    peaks = measure_alu_peaks(torch)
+    fp32_peak, fp64_peak = peaks["fp32_tflops"], peaks["fp64_tflops"]
+    roofline = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
                 "traffic": FLUX_TRAFFIC_BYTES if not fused_m else FLUX2D_TRAFFIC_BYTES, "traffic_unit": "bytes per launch",
                 "kernel": "flux2d_kernel (fused stage, mixed form)" if fused_m else "flux_kernel (mixed form)", "flops_per_launch": flops_launch,
-                "avg_launch_ms": avg_s * 1e3, "peak_source": "FP32: 152 SMs x 128 lanes x 2 x 2.07 GHz"}
+                "avg_launch_ms": avg_s * 1e3,
+                "flops_per_interface": per_iface,
+                "flops_source": ("FP64 oracle, operation-counting build (tests/golden/op_counts.json), per interface "
+                                 "of the residual without metrics" if oracle_iface else "hand count"),
+                "oracle_op_classes_per_interface": oracle_classes,
+                "mufu_share": ((oracle_classes["div"] + oracle_classes["sqrt"] + oracle_classes["log"] + oracle_classes["exp"])
+                               / oracle_classes["flops"]) if oracle_classes else None,
+                "hand_count_flops_per_interface": hand_iface,
+                "achieved_hand_count": ach_hand, "frac_hand_count": None,
+                "peak_source": "measured FP32 fused multiply-add throughput (es_alu_peak, best of FFMA and paired "
+                               "FFMA2) in this run, of measured; nominal %.1f TFLOP/s" % FP32_NOMINAL_TFLOPS}
+    roofline["frac_hand_count"] = ach_hand / fp32_peak
     # DRAM side of the same kernel: the captured bytes per launch over the live launch time,
     # against the measured copy bandwidth (the kernel is not HBM-bound)
     traffic = roofline["traffic"]
@@ -571,9 +723,26 @@ def main_ours(args):
     fused_d = is_fused(r64)
     flops64 = per_iface * ifaces_stage / (1 if fused_d else pb.d)
     ach64 = flops64 / avg64 / 1e12
-    roofline_fp64 = {"bound": "alu", "achieved": ach64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": ach64 / FP64_PEAK_TFLOPS, "avg_launch_ms": avg64 * 1e3,
+    roofline_fp64 = {"bound": "alu", "achieved": ach64, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": ach64 / fp64_peak, "avg_launch_ms": avg64 * 1e3,
+                     "peak_source": "measured FP64 fused multiply-add throughput (es_alu_peak, DFMA) in this run, "
+                                    "of measured; nominal %.2f TFLOP/s" % FP64_NOMINAL_TFLOPS,
                      "kernel": "flux2d_kernel (fused stage, FP64 form)" if fused_d else "flux_kernel (FP64 form)"}
+
+    # the same kernel at the batched size (the 64-instance batch, or this rank's share of it)
+    if prof_b is not None:
+        fb_ms = sum(prof_b[k][0] for k in FLUX)
+        fb_n = sum(prof_b[k][1] for k in FLUX)
+        if fb_n:
+            fused_b = is_fused(bt)
+            bprobs = bt.probs
+            iface_b = sum(sum((p.n[k] + 1) * p.ncell // p.n[k] for k in range(p.d)) for p in bprobs)
+            flops_b = per_iface * iface_b / (1 if fused_b else 2)
+            avg_b = fb_ms / fb_n / 1e3
+            hand_b = hand_iface * iface_b / (1 if fused_b else 2) / avg_b / 1e12
+            roofline["batched"] = {"achieved": flops_b / avg_b / 1e12, "frac": flops_b / avg_b / 1e12 / fp32_peak,
+                                   "avg_launch_ms": avg_b * 1e3, "flops_per_launch": flops_b, "cells": bt.cells,
+                                   "achieved_hand_count": hand_b, "frac_hand_count": hand_b / fp32_peak}
 
     # CPU baseline (rank 0 only): the oracle on a bounded sample, and the errors after one step
     cpu = None
@@ -607,8 +776,8 @@ def main_ours(args):
         # the 3D path at sizes the oracle steps in seconds (the timed 3D forms are 128^3 and
         # 128 x 64 x 64; the kernels and launch shapes are the same at every size)
         if not args.no_3d:
-            for name, (p3, U3, x3) in (("3d_riemann_32^3", W.riemann_3d(32)),
-                                       ("3d_shock_bubble_48x24x24", W.shock_bubble_3d(24))):
+            for name, (p3, U3, x3) in (("3d_shock_bubble_48x24x24", W.shock_bubble_3d(24)),
+                                       ("3d_stiffened_shock_bubble_80x16x16_um", W.shock_bubble_3d_stiffened(16))):
                 o1 = oracle_one_step(p3, U3, x3)
                 for prec, tag in ((es.MIXED, "mixed"), (es.FP64, "fp64")):
                     r3 = Single(p3, U3, x3, prec, torch)
@@ -618,6 +787,22 @@ def main_ours(args):
                     e3["vs"] = "FP64 oracle after one full step from t = 0"
                     errs["%s_%s" % (tag, name)] = e3
                     del r3
+            # the octant Riemann problem (the 128^3 form's workload) at 32^3: errors after 1 and
+            # after 10 full steps
+            p3, U3, x3 = W.riemann_3d(32)
+            states = oracle_steps(p3, U3, x3, (1, 10))
+            for prec, tag in ((es.MIXED, "mixed"), (es.FP64, "fp64")):
+                r3 = Single(p3, U3, x3, prec, torch)
+                done = 0
+                for k, (JUo, Jo) in states.items():
+                    while done < k:
+                        r3.step()
+                        done += 1
+                    torch.cuda.synchronize()
+                    e3 = errors_vs(JUo, Jo, p3, r3.JU.cpu().numpy(), r3.J.cpu().numpy())
+                    e3["vs"] = "FP64 oracle after %d full steps from t = 0" % k
+                    errs["%s_3d_riemann_32^3_%d_steps" % (tag, k)] = e3
+                del r3
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -631,7 +816,7 @@ def main_ours(args):
         "kernel_ms": {"mixed": {k: v[0] / args.steps for k, v in prof_m.items()},
                       "fp64": {k: v[0] / k64 for k, v in prof_d.items()},
                       "batched_mixed": ({k: v[0] / kb for k, v in prof_b.items()} if batched else None)},
-        "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+        "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "alu_peaks": peaks,
         "gpu_launches": launches_per_step(pb, True, fused_m) * args.steps,
     }
     if rank == 0:
@@ -719,6 +904,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-3d", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--min-seconds", type=float, default=1.0,
+                    help="device time of the sustained span of headline steps after the timed ones")
     ap.add_argument("--kernel-case", default=None, help="NXxNY | 3d:riemann:N | 3d:sb:N: only run a few steps of that grid (profiling)")
     ap.add_argument("--kernel-form", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--kernel-steps", type=int, default=2)
