@@ -399,7 +399,7 @@ void launch_metrics(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStr
 // mcoef != 0 (2D) makes the stage metrics M + mcoef dt Md, the metrics of x^n + mcoef dt
 // xdot; dot = true (2D) forms Md with M.
 void launch_residual(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, bool rk, double a, double b, cudaStream_t st,
-                     bool metrics = true, double mcoef = 0.0, bool dot = false)
+                     bool metrics = true, double mcoef = 0.0, bool dot = false, double xc = 0.0)
 {
     if (metrics) launch_metrics(c, P, tab, st, false, dot);
     if (c->d == 2 && c->fused_shape >= 0) {
@@ -414,6 +414,7 @@ void launch_residual(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, bool r
         L.a = a;
         L.b = b;
         L.mcoef = mcoef;
+        L.xc = xc;
         L.status = c->status;
         ProfScope ps(c, PC_FLUX2D, st);
         flux2d_launch(c, L, c->fused_shape, c->fused_grid, st);
@@ -433,6 +434,7 @@ void launch_residual(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, bool r
         L.a = a;
         L.b = b;
         L.mcoef = mcoef;
+        L.xc = xc;
         L.status = c->status;
         ProfScope ps(c, PC_FLUX + k, st);
         flux_launch(c, L, sh, c->flux_grid[k], st);
@@ -485,8 +487,10 @@ void stage_ptrs(es_ctx* c, int i, double* JU, double* J, double* x, const double
 
 const double RK_A[3] = { 0.0, 0.75, 1.0 / 3.0 };
 const double RK_B[3] = { 1.0, 0.25, 2.0 / 3.0 };
-// the stage meshes of SSP-RK3 with xdot constant: x^n, x^n + dt xdot, x^n + dt xdot / 2
+// the stage meshes of SSP-RK3 with xdot constant: x^n, x^n + dt xdot, x^n + dt xdot / 2 (the
+// input of stage s), and the stage outputs x^n + dt xdot, x^n + dt xdot / 2, x^n + dt xdot
 const double MCOEF[3] = { 0.0, 1.0, 0.5 };
+const double XCOEF[3] = { 1.0, 0.5, 1.0 };
 
 // 2D moving meshes form the stage metrics as M(x^n) + s dt M(xdot) (the metrics are linear in x)
 bool linear_stage_metrics(const es_ctx* c) { return c->d == 2 && !c->hI[0].fixed; }
@@ -552,7 +556,7 @@ void launch_step(es_ctx* c, const StagePtrs& mesh, const StagePtrs* tab_mesh, co
     const bool fixed = c->hI[0].fixed != 0, lin = linear_stage_metrics(c);
     for (int s = 0; s < 3; ++s)
         launch_residual(c, stage[s], tab_stage[s], true, RK_A[s], RK_B[s], st, s > 0 && !fixed && !lin,
-                        lin ? MCOEF[s] : 0.0);
+                        lin ? MCOEF[s] : 0.0, false, XCOEF[s]);
 }
 
 __global__ void time_acc_kernel(double* t, const double* dt_dtau) { *t += dt_dtau[0]; }
@@ -778,7 +782,7 @@ es_status es_rk_step(es_ctx* c, double* JU, double* J, double* x, const double* 
     const bool fixed = c->hI[0].fixed != 0, lin = linear_stage_metrics(c);
     for (int s = 0; s < 3; ++s)
         launch_residual(c, P[s], nullptr, true, RK_A[s], RK_B[s], (cudaStream_t)stream, s == 0 || (!fixed && !lin),
-                        lin ? MCOEF[s] : 0.0, lin && s == 0);
+                        lin ? MCOEF[s] : 0.0, lin && s == 0, XCOEF[s]);
     return cuda_check(c, "es_rk_step");
 }
 
@@ -1012,6 +1016,7 @@ es_status es_autotune(es_ctx* c, const double* JU, const double* J, const double
                 L.a = 0.0;
                 L.b = 1.0;
                 L.mcoef = 0.0;
+                L.xc = 0.0;
                 L.status = c->status;
                 const int grid = c->sms * o;
                 flux_launch(c, L, sh, grid, st);
@@ -1052,6 +1057,7 @@ es_status es_autotune(es_ctx* c, const double* JU, const double* J, const double
                 L.a = 0.0;
                 L.b = 1.0;
                 L.mcoef = 0.0;
+                L.xc = 0.0;
                 L.status = c->status;
                 const int grid = c->sms * o;
                 flux2d_launch(c, L, sh, grid, st);

@@ -533,6 +533,15 @@ __device__ __forceinline__ void iface_flux(const Inst& I, const R* nb, int NN, i
 #undef NR
 }
 
+// Shu-Osher stage of one FP64 field (SSP-RK3, Sec. 5): a q^n + b (q + dt r).  The first stage
+// (a = 0, b = 1) is q + dt r, one fused multiply-add; the others b (q + dt r) + a q^n with the
+// outer product fused.  q0 points at q^n (read only when a != 0).
+__device__ __forceinline__ double rk_stage(const FluxLaunch& L, double q, const double* q0, double dt, double r)
+{
+    const double s = fma(dt, r, q);
+    return (L.a == 0.0 && L.b == 1.0) ? s : fma(L.b, s, L.a * *q0);
+}
+
 // Phase 4 of one node along direction k: r[0..NC) = -(F_{i+1/2} - F_{i-1/2}) / dxi_k from
 // the interface fluxes at fr and fL (field stride NI), r[NC] the same of the FP64 GCL flux
 // (the J equation), and the p_inf J xi_k/t part of the energy flux added in FP64

@@ -25,6 +25,10 @@ struct Tile {
 template <int D, int NS>
 __host__ __device__ constexpr int stage_rows() { return NS + 2 * D + 3; }
 
+// whether tiles of this case stage the next tile's inputs (not for two species in 3D)
+template <int D, int NS>
+__host__ __device__ constexpr bool stages_inputs() { return !(D == 3 && NS == 2); }
+
 // byte offset of the staging buffer behind the compute-type arrays of a flux tile (16-byte aligned)
 template <int D, int NS, typename R, int S, int WT>
 __host__ __device__ constexpr size_t stage_offset()
@@ -93,11 +97,11 @@ __device__ __forceinline__ void flux_stage(const FluxLaunch& L, int k, int wi, d
 // (2) every distinct two-point flux F(U_j, U_{j+m}) (m = 1, 2, 3) of the tile, once; (3)
 // per interface the 2w-order EC flux as sum_m alpha_m sum_s of the stored pairs, the GCL
 // flux of J xi_k/t and the ES dissipation; (4) divergence and output / RK stage.
-// FP32 tiles: 3 CTAs per SM (<= 85 registers) in 2D and for one species in 3D, 2 for two
-// species in 3D (whose tiles need more shared memory than 3 CTAs allow); FP64 tiles: 1
-// (FP64-pipe bound)
+// FP32 tiles: 3 CTAs per SM (<= 85 registers); FP64 tiles: 1 (FP64-pipe bound).  Two-species
+// 3D tiles have no staging buffer (with it they fit only 2 CTAs per SM, which measured 1-4%
+// slower than 3 CTAs without it, spills included)
 template <int D, int NS, typename R, int S, int WT, int WK>
-__global__ void __launch_bounds__(FLUX_TPB, (sizeof(R) == 4 ? ((D == 2 || NS == 1) ? 3 : 2) : 1)) flux_kernel(FluxLaunch L)
+__global__ void __launch_bounds__(FLUX_TPB, (sizeof(R) == 4 ? 3 : 1)) flux_kernel(FluxLaunch L)
 {
     pdl_entry();
     using Y = Lay<D, NS>;
@@ -118,7 +122,7 @@ __global__ void __launch_bounds__(FLUX_TPB, (sizeof(R) == 4 ? ((D == 2 || NS == 
     // first tile's now, each later tile's once the previous tile's phase 1 has consumed the
     // buffer, so their loads overlap phases 2-4.  With one tile per CTA there is nothing to
     // overlap, and phase 1 loads directly.
-    const bool staged = L.nwork > (int)gridDim.x;
+    const bool staged = stages_inputs<D, NS>() && L.nwork > (int)gridDim.x;
     if (staged && blockIdx.x < L.nwork) flux_stage<D, NS, S, WT>(L, k, blockIdx.x, stg);
     for (int wi = blockIdx.x; wi < L.nwork; wi += gridDim.x) {
         const int2 it = L.work[wi];
@@ -243,22 +247,14 @@ __global__ void __launch_bounds__(FLUX_TPB, (sizeof(R) == 4 ? ((D == 2 || NS == 
                 for (int q = 0; q < NC; ++q) P.accU[q * ncell + id] += r[q];
                 P.accJ[id] += r[NC];
             } else {
-                const double A = L.a, B = L.b;
 #pragma unroll
-                for (int q = 0; q < NC; ++q) {
-                    double rq = P.accU[q * ncell + id] + r[q];
-                    double base = A != 0.0 ? A * P.JU0[q * ncell + id] : 0.0;
-                    P.JUo[q * ncell + id] = base + B * (P.JU[q * ncell + id] + dt * rq);
-                }
-                double rj = P.accJ[id] + r[NC];
-                double bj = A != 0.0 ? A * P.J0[id] : 0.0;
-                P.Jo[id] = bj + B * (P.J[id] + dt * rj);
-                if (P.xo) {    // null on a fixed mesh
+                for (int q = 0; q < NC; ++q)
+                    P.JUo[q * ncell + id] = rk_stage(L, P.JU[q * ncell + id], P.JU0 + q * ncell + id, dt, P.accU[q * ncell + id] + r[q]);
+                P.Jo[id] = rk_stage(L, P.J[id], P.J0 + id, dt, P.accJ[id] + r[NC]);
+                if (P.xo) {    // null on a fixed mesh; xdot is constant over the step: x^n + xc dt xdot
+                    const double cdt = L.xc * dt;
 #pragma unroll
-                    for (int j = 0; j < D; ++j) {
-                        double bx = A != 0.0 ? A * P.x0[j * ncell + id] : 0.0;
-                        P.xo[j * ncell + id] = bx + B * (P.x[j * ncell + id] + dt * P.xdot[j * ncell + id]);
-                    }
+                    for (int j = 0; j < D; ++j) P.xo[j * ncell + id] = fma(cdt, P.xdot[j * ncell + id], P.x0[j * ncell + id]);
                 }
             }
         }
@@ -269,7 +265,7 @@ __global__ void __launch_bounds__(FLUX_TPB, (sizeof(R) == 4 ? ((D == 2 || NS == 
 template <int D, int NS, typename R, int S, int WT>
 static size_t smem_of()
 {
-    return stage_offset<D, NS, R, S, WT>() + sizeof(double) * stage_rows<D, NS>() * Tile<S, WT>::NN;
+    return stage_offset<D, NS, R, S, WT>() + (stages_inputs<D, NS>() ? sizeof(double) * stage_rows<D, NS>() * Tile<S, WT>::NN : 0);
 }
 
 // one case per tile shape of the table in es_kernels.cuh
@@ -303,7 +299,7 @@ template <int D, int NS, typename R, int WK>
 void launch_flux(const FluxLaunch& L, int shape, int grid, cudaStream_t st)
 {
     // the staging buffer only when a CTA has several tiles (the kernel's own test)
-    const bool staged = L.nwork > grid;
+    const bool staged = stages_inputs<D, NS>() && L.nwork > grid;
 #define ES_LAUNCH(SH)                                                                                        \
     if (shape == SH)                                                                                         \
         pdl_launch(flux_kernel<D, NS, R, SHAPE_S[SH], SHAPE_WT[SH], WK>, grid, FLUX_TPB,                       \

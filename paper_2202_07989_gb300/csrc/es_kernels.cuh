@@ -51,6 +51,7 @@ struct FluxLaunch {
     int mode;          // MODE_*
     double a, b;       // Shu-Osher coefficients of the stage (MODE_RK)
     double mcoef;      // 2D: the stage metrics are M + mcoef dt Md (0: M alone)
+    double xc;         // MODE_RK: the stage's output mesh is x^n + xc dt xdot (xdot constant over the step)
     int* status;
 };
 
