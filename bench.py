@@ -475,6 +475,62 @@ def cpu_baseline_leg(pb, U, x, gpu_after_one, budget_s=20.0):
             "sample": "%d full steps (mesh redistribution + SSP-RK3) of the 400x200 workload from t = 0, %.1f s" % (steps, el)}, first
 
 
+def cpu_model():
+    """The host CPU's model as /proc/cpuinfo states it (x86: model name; Arm: the implementer and
+    part codes), and the number of logical cores."""
+    fields = {}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ":" in ln:
+                    k, v = [t.strip() for t in ln.split(":", 1)]
+                    fields.setdefault(k, v)
+    except OSError:
+        pass
+    name = fields.get("model name") or fields.get("Model") or (
+        "CPU implementer %s part %s" % (fields.get("CPU implementer", "?"), fields.get("CPU part", "?")))
+    return {"model": name, "logical_cores": os.cpu_count()}
+
+
+def _oracle_batch_step(i):
+    """One full oracle step from t = 0 of instance i of the 64-instance batch (a worker process)."""
+    sys.path.insert(0, ROOT)
+    from oracle.oracle import Oracle
+    from paper_2202_07989_gb300 import workloads as W
+    pb, U, x = W.batched_instance(W.batched_params(64)[i])
+    o = Oracle(pb)
+    J = o.init_J(x)
+    JU = U * J
+    t0 = time.perf_counter()
+    xd, dt, dtau = o.mesh_redistribute(JU, J, x)
+    o.rk_step(JU, J, x, xd, dt)
+    return pb.ncell, time.perf_counter() - t0
+
+
+def cpu_baseline_all_cores():
+    """The oracle as it stands on every host core at once: one full step of each of the 64
+    instances of the batched workload, the instances spread over a process pool (spawn) of one
+    worker per logical core.  Value = the batch's cells x 3 stages / wall time of the pool."""
+    import multiprocessing as mp
+    n = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(n) as pool:
+        pool.map(_oracle_batch_step, [0] * n)          # start-up and imports, outside the timing
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_batch_step, sorted(range(64), key=lambda i: -W_batched_cells(i)), chunksize=1)
+        wall = time.perf_counter() - t0
+    cells = sum(c for c, _ in res)
+    return {"value": cells * 3 / wall, "unit": UNIT, "cores": n, "kind": "oracle",
+            "sample": "one full step (mesh redistribution + SSP-RK3) from t = 0 of each of the 64 instances of "
+                      "the batched workload (%d cells), one worker process per core, %.1f s wall, %.1f s CPU"
+                      % (cells, wall, sum(t for _, t in res))}
+
+
+def W_batched_cells(i):
+    from paper_2202_07989_gb300 import workloads as W
+    return W.batched_params(64)[i]["n"] ** 2
+
+
 def rank_env():
     """(rank, world size, local rank) of this process from the launcher's environment."""
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
@@ -749,6 +805,9 @@ def main_ours(args):
     errs = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu, ref1 = cpu_baseline_leg(pb, U, x, None, budget_s=args.cpu_seconds)
+        cpu["cpu"] = cpu_model()
+        if not args.no_batched:
+            cpu["all_cores_batched"] = cpu_baseline_all_cores()
         errs = {}
         for name in ("fp64", "mixed"):
             r = runners[name]
