@@ -924,3 +924,34 @@ def test_dissipation_magnitude_at_a_small_step(d, N, pinf):
     # relative error O(eps): halving eps halves it (absolute error O(eps^2))
     assert errs[-1] < 0.02, errs
     assert errs[1] / errs[2] > 1.6 and errs[0] / errs[1] > 1.6, errs
+
+
+@pytest.mark.parametrize("d,N", CASES)
+@pytest.mark.parametrize("band,below,above", [(1e-12, 4e-16, 1e-9), (3e-7, 2e-9, 1e-5)])
+def test_y_band_separates_round_off_from_jumps(d, N, band, below, above):
+    """The sign band of Y (Sec. 3.4; a jump [[W_m]] within band x ||r_m|| (||V_i|| + ||V_i+1||)
+    counts as zero) sits between round-off and real jumps: for a step whose relative size is a
+    few units of the arithmetic's last place (binary64 band 1e-12: 4e-16; binary32 band 3e-7:
+    2e-9) every jump falls inside the band and the ES flux equals the EC flux exactly; for a
+    step well above the band (1e-9, 1e-5) the dissipation acts at the step."""
+    n = (16, 12, 12)[:d]
+    pb = W.random_problem(d, N, n, bc="periodic")
+    rng = np.random.default_rng(7 + d + N)
+    UL = _random_state(pb, rng)
+    x = np.stack(W.xi_nodes(pb))
+    xdot = np.zeros_like(x)
+    J = np.ones(pb.shape)
+    right = (np.arange(n[0]) >= n[0] // 2).reshape((1,) * 2 + (n[0],))
+    for size, zero in ((below, True), (above, False)):
+        UR = UL * (1.0 + size * rng.uniform(0.5, 1.0, size=pb.nc))
+        U = np.where(right[None], UR.reshape(-1, 1, 1, 1), UL.reshape(-1, 1, 1, 1))
+        es_o = Oracle(pb)
+        es_o.cfg.y_band = band
+        ec_o = Oracle(pb.with_(es=False))
+        dES, _ = es_o.rhs(U * J, J, x, xdot)
+        dEC, _ = ec_o.rhs(U * J, J, x, xdot)
+        diss = np.abs(dES - dEC).max()
+        if zero:
+            assert diss == 0.0, (size, diss)
+        else:
+            assert diss > 0.0, size
