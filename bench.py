@@ -924,9 +924,10 @@ def main_kernel_case(args):
     B.build()
     from paper_2202_07989_gb300 import es, workloads as W
     if args.kernel_case.startswith("3d:"):
-        # 3D octant Riemann problem (single component) or shock-bubble (two components, 2n x n x n)
+        # 3D octant Riemann problem (single component), shock-bubble (two components, 2n x n x n) or
+        # the stiffened shock-bubble of Example 5.11 (uniform-mesh form, 5n x n x n)
         kind, n = args.kernel_case[3:].split(":")
-        pb, U, x = W.riemann_3d(int(n)) if kind == "riemann" else W.shock_bubble_3d(int(n))
+        pb, U, x = {"riemann": W.riemann_3d, "sb": W.shock_bubble_3d, "sb2": W.shock_bubble_3d_stiffened}[kind](int(n))
     else:
         nx, ny = [int(v) for v in args.kernel_case.split("x")]
         pb, U, x = W.shock_bubble_2d(nx, ny, length=(2.0, 1.0))
@@ -965,7 +966,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--min-seconds", type=float, default=1.0,
                     help="device time of the sustained span of headline steps after the timed ones")
-    ap.add_argument("--kernel-case", default=None, help="NXxNY | 3d:riemann:N | 3d:sb:N: only run a few steps of that grid (profiling)")
+    ap.add_argument("--kernel-case", default=None, help="NXxNY | 3d:riemann:N | 3d:sb:N | 3d:sb2:N: only run a few steps of that grid (profiling)")
     ap.add_argument("--kernel-form", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--kernel-steps", type=int, default=2)
     ap.add_argument("--kernel-time", type=int, default=0, help="also time this many eager steps per kernel class")
