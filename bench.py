@@ -86,14 +86,12 @@ def hbm_peak_gbs():
             return float(json.load(f)["hbm_gbs"]), "measured"
     except (OSError, KeyError, ValueError):
         return 6800.0, "fallback"
-# DRAM bytes (read + write) per flux launch of the 400x200 mixed step: the mean of the two
-# launches of a stage in one ncu capture of the same tuned kernel (dram__bytes_read.sum +
-# dram__bytes_write.sum, cold cache); the capture and its command are in profiles/
-FLUX_TRAFFIC_BYTES = 9.30e6
-# the same for one fused 2D stage launch (both directions): the mean of the three stage
-# launches of a step in one ncu capture (stage 1 10.51 MB; stages 2 and 3, which also read
-# M(xdot) and the step-start state, 19.58 MB each)
-FLUX2D_TRAFFIC_BYTES = 16.56e6
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, cold cache) per fused 2D stage launch
+# of the 400x200 mixed step: the mean of the three stage launches of a step in one ncu capture of
+# the current kernel (stage 1 10.51 MB; stages 2 and 3, which also read M(xdot) and the step-start
+# state, 18.30 MB each); the capture and its command are in profiles/.  The per-direction launches
+# have no current capture (traffic null when the tuner picks them).
+FLUX2D_TRAFFIC_BYTES = 15.71e6
 
 
 def flux_flops_per_interface(D, NS, es=True):
@@ -750,7 +748,7 @@ def main_ours(args):
     peaks = measure_alu_peaks(torch)
     fp32_peak, fp64_peak = peaks["fp32_tflops"], peaks["fp64_tflops"]
     roofline = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
-                "traffic": FLUX_TRAFFIC_BYTES if not fused_m else FLUX2D_TRAFFIC_BYTES, "traffic_unit": "bytes per launch",
+                "traffic": FLUX2D_TRAFFIC_BYTES if fused_m else None, "traffic_unit": "bytes per launch",
                 "kernel": "flux2d_kernel (fused stage, mixed form)" if fused_m else "flux_kernel (mixed form)", "flops_per_launch": flops_launch,
                 "avg_launch_ms": avg_s * 1e3,
                 "flops_per_interface": per_iface,

@@ -1,0 +1,121 @@
+"""Parity at the benchmark's full sizes, on sampled nodes.
+
+The residual at a node depends only on the state within 3 nodes and the mesh within 6 nodes of
+it (fluxes at the node's interfaces use nodes i-3..i+3 and their metrics, and each metric uses
+positions within 3 nodes in up to two directions).  So the oracle's residual on a 13-node block
+around a sampled node, with any boundary treatment on block sides that are not sides of the grid,
+is the exact residual at that node.  The GPU residual of the whole grid, in the launch
+configuration the benchmark times (tuned flux tiles), is compared there: the 128^3 octant Riemann
+problem and Example 5.11 at 800 x 160 x 160, after one full GPU step (moved mesh, evolved state),
+FP64 at 1e-12 of each field's max-norm, mixed at FP32 level.
+"""
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle
+from paper_2202_07989_gb300 import workloads as W
+
+from .helpers import MARGIN_DECADES, TOL_FP64, need_gpu, to_dev
+
+pytestmark = pytest.mark.gpu
+
+HALF = 6
+
+
+def _block(pb, c):
+    """Node ranges [lo, hi) of the 13-node block around node c and its sides' boundary codes."""
+    rng, bc = [], []
+    for k in range(pb.d):
+        n = pb.n[k]
+        assert pb.bc[k][0] != W.PERIODIC, "blocks of periodic grids are not supported here"
+        lo, hi = c[k] - HALF, c[k] + HALF + 1
+        sides = [W.OUTFLOW, W.OUTFLOW]
+        if lo <= 0:
+            lo, hi = 0, 2 * HALF + 1
+            sides[0] = pb.bc[k][0]
+        if hi >= n:
+            lo, hi = n - 2 * HALF - 1, n
+            sides[1] = pb.bc[k][1]
+        rng.append((lo, hi))
+        bc.append(tuple(sides))
+    return rng, bc
+
+
+def _oracle_at(pb, JU, J, x, xdot, c, band):
+    """Oracle residual (dJU, dJ) and Y-decision margin at node c from its block."""
+    rng, bc = _block(pb, c)
+    # arrays are (n3, n2, n1), n3 = 1 in 2D
+    sl = tuple(slice(*rng[k]) if k < pb.d else slice(None) for k in (2, 1, 0))
+    n = tuple(hi - lo for lo, hi in rng)
+    xi_lo = tuple(pb.xi_lo[k] + rng[k][0] * pb.dxi[k] for k in range(pb.d))
+    sub = pb.with_(n=n + (1,) * (3 - pb.d), xi_lo=xi_lo + (0.0,) * (3 - pb.d),
+                   length=tuple(n[k] * pb.dxi[k] for k in range(pb.d)) + (1.0,) * (3 - pb.d),
+                   bc=tuple(bc) + ((W.PERIODIC, W.PERIODIC),) * (3 - pb.d), fixed_mesh=False)
+    o = Oracle(sub)
+    o.cfg.y_band = band
+    cut = lambda a: np.ascontiguousarray(a[(slice(None),) + sl])
+    dJU, dJ, mg = o.rhs_margins(cut(JU), np.ascontiguousarray(J[sl]), cut(x), cut(xdot))
+    loc = tuple(c[k] - rng[k][0] if k < pb.d else 0 for k in (2, 1, 0))
+    return dJU[(slice(None),) + loc], dJ[loc], mg[loc]
+
+
+def _samples(pb, rng, count):
+    """Corner, edge and face nodes of the grid and random interior nodes."""
+    n = pb.n[: pb.d]
+    pts = [tuple(0 if (m >> k) & 1 == 0 else n[k] - 1 for k in range(pb.d)) for m in range(2 ** pb.d)]
+    pts += [tuple(int(rng.integers(0, n[k])) if k != j else (0 if rng.uniform() < 0.5 else n[k] - 1)
+                  for k in range(pb.d)) for j in range(pb.d) for _ in range(2)]
+    pts += [tuple(int(rng.integers(0, n[k])) for k in range(pb.d)) for _ in range(count)]
+    return pts
+
+
+def _full_size_case(torch, pb, U, x, form, count, seed):
+    from paper_2202_07989_gb300 import es
+    ctx = es.Context(pb, form)
+    xg = to_dev(x, torch)
+    J = ctx.es_init_mesh(xg)
+    JU = (to_dev(U, torch) * J).contiguous()
+    ctx.es_step(JU, J, xg)                                  # the timed path, one step (tiles untuned)
+    ctx.es_autotune(JU, J, xg, None, reps=2)                # the benchmark's launch configuration
+    xd, dd = ctx.mesh_redistribute(JU, J, xg)
+    dJU, dJ = ctx.es_rhs(JU, J, xg, xd)
+    assert ctx.es_poll_status() == 0
+    host = [t.cpu().numpy() for t in (JU, J, xg, xd, dJU, dJ)]
+    del ctx, JU, J, xg, xd, dJU, dJ
+    torch.cuda.empty_cache()
+    JUh, Jh, xh, xdh, dJUh, dJh = host
+    scale = [float(np.abs(dJUh[q]).max()) for q in range(pb.nc)]
+    m = max(scale[pb.N: pb.N + pb.d])
+    scale = [m if pb.N <= q < pb.N + pb.d else s for q, s in enumerate(scale)]
+    sJ = float(np.abs(dJh).max())
+    errs, skipped = [], 0
+    for c in _samples(pb, np.random.default_rng(seed), count):
+        o_dJU, o_dJ, mg = _oracle_at(pb, JUh, Jh, xh, xdh, c, 1e-12 if form == 0 else 3e-7)
+        if form == 0 and mg < MARGIN_DECADES:
+            skipped += 1
+            continue
+        idx = tuple(c[k] if k < pb.d else 0 for k in (2, 1, 0))
+        e = max(abs(dJUh[(q,) + idx] - o_dJU[q]) / scale[q] for q in range(pb.nc))
+        errs.append(max(e, abs(dJh[idx] - o_dJ) / sJ))
+    return errs, skipped
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_riemann_128_residual_at_sampled_nodes(form):
+    torch = need_gpu()
+    pb, U, x = W.riemann_3d(128)
+    errs, skipped = _full_size_case(torch, pb, U, x, form, 24, 128)
+    print("128^3 Riemann, form", form, "sampled nodes", len(errs), "max rel err %.2e" % max(errs), "skipped", skipped)
+    assert len(errs) >= 30 and skipped <= 2
+    assert max(errs) <= (TOL_FP64 if form == 0 else 2e-4), errs
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_stiffened_800x160x160_residual_at_sampled_nodes(form):
+    torch = need_gpu()
+    pb, U, x = W.shock_bubble_3d_stiffened(160)
+    errs, skipped = _full_size_case(torch, pb, U, x, form, 24, 160)
+    print("Example 5.11 800x160x160, form", form, "sampled nodes", len(errs), "max rel err %.2e" % max(errs),
+          "skipped", skipped)
+    assert len(errs) >= 30 and skipped <= 2
+    assert max(errs) <= (TOL_FP64 if form == 0 else 2e-4), errs
