@@ -25,9 +25,9 @@ struct Tile {
 template <int D, int NS>
 __host__ __device__ constexpr int stage_rows() { return NS + 2 * D + 3; }
 
-// whether tiles of this case stage the next tile's inputs (not for two species in 3D)
+// whether tiles of this case stage the next tile's inputs (not in 3D, whose tiles run 4 CTAs per SM)
 template <int D, int NS>
-__host__ __device__ constexpr bool stages_inputs() { return !(D == 3 && NS == 2); }
+__host__ __device__ constexpr bool stages_inputs() { return D != 3; }
 
 // byte offset of the staging buffer behind the compute-type arrays of a flux tile (16-byte aligned)
 template <int D, int NS, typename R, int S, int WT>
@@ -97,11 +97,11 @@ __device__ __forceinline__ void flux_stage(const FluxLaunch& L, int k, int wi, d
 // (2) every distinct two-point flux F(U_j, U_{j+m}) (m = 1, 2, 3) of the tile, once; (3)
 // per interface the 2w-order EC flux as sum_m alpha_m sum_s of the stored pairs, the GCL
 // flux of J xi_k/t and the ES dissipation; (4) divergence and output / RK stage.
-// FP32 tiles: 3 CTAs per SM (<= 85 registers); FP64 tiles: 1 (FP64-pipe bound).  Two-species
-// 3D tiles have no staging buffer (with it they fit only 2 CTAs per SM, which measured 1-4%
-// slower than 3 CTAs without it, spills included)
+// FP32 tiles: 3 CTAs per SM in 2D (<= 85 registers), 4 in 3D (<= 64 registers: the compact 3D
+// node layout and no staging buffer leave room for 4, measured 3-10% faster than 3 with the
+// staging buffer, spills included); FP64 tiles: 1 (FP64-pipe bound)
 template <int D, int NS, typename R, int S, int WT, int WK>
-__global__ void __launch_bounds__(FLUX_TPB, (sizeof(R) == 4 ? 3 : 1)) flux_kernel(FluxLaunch L)
+__global__ void __launch_bounds__(FLUX_TPB, (sizeof(R) == 4 ? (D == 3 ? 4 : 3) : 1)) flux_kernel(FluxLaunch L)
 {
     pdl_entry();
     using Y = Lay<D, NS>;

@@ -96,7 +96,8 @@ def _full_size_case(torch, pb, U, x, form, count, seed):
             continue
         idx = tuple(c[k] if k < pb.d else 0 for k in (2, 1, 0))
         e = max(abs(dJUh[(q,) + idx] - o_dJU[q]) / scale[q] for q in range(pb.nc))
-        errs.append(max(e, abs(dJh[idx] - o_dJ) / sJ))
+        # dJ is identically zero on a fixed mesh: its error is then absolute
+        errs.append(max(e, abs(dJh[idx] - o_dJ) / sJ if sJ > 0 else abs(dJh[idx] - o_dJ)))
     return errs, skipped
 
 
