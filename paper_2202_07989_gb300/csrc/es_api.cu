@@ -26,7 +26,6 @@ struct es_ctx {
     // work lists (inst, tile)
     int2* w_pad = nullptr;  int n_pad = 0;
     int2* w_ext = nullptr;  int n_ext = 0;
-    int2* w_xe = nullptr;   int n_xe = 0;
     int2* w_cell = nullptr; int n_cell = 0;
     int2* w_col = nullptr;  int n_col = 0;     // 3D: column chunks of the kernels marching along i3
     int2* w_flux[3][NSHAPE] = {};          // flux work list per direction and tile shape
@@ -386,10 +385,13 @@ void launch_metrics(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStr
         launch_metrics2d(dot, node_grid(c, c->n_pad), st, c->dI, P, tab, c->w_pad, c->n_pad, reset ? c->dS : nullptr,
                          c->n_inst, vcl);
     } else {
-        pdl_launch(xe_fill_kernel, node_grid(c, c->n_xe), NODE_TPB, 0, st, c->dI, P, tab, c->w_xe, c->n_xe, c->dS,
+        // positions within 6 ghost layers, products within 3, metrics at the interior nodes, then
+        // the metrics of the 3 ghost layers from those of the nodes they map to
+        pdl_launch(xe_fill_kernel, node_grid(c, c->n_ext), NODE_TPB, 0, st, c->dI, P, tab, c->w_ext, c->n_ext, c->dS,
                    reset ? c->n_inst : 0);
-        pdl_launch(dx3d_kernel, node_grid(c, c->n_ext), NODE_TPB, 0, st, c->dI, P, tab, c->w_ext, c->n_ext, c->dS);
-        pdl_launch(metrics3d_kernel, node_grid(c, c->n_pad), NODE_TPB, 0, st, c->dI, P, tab, c->w_pad, c->n_pad, c->dS);
+        pdl_launch(dx3d_kernel, node_grid(c, c->n_pad), NODE_TPB, 0, st, c->dI, P, tab, c->w_pad, c->n_pad, c->dS);
+        pdl_launch(metrics3d_kernel, node_grid(c, c->n_cell), NODE_TPB, 0, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
+        pdl_launch(metrics3d_ghost_kernel, node_grid(c, c->n_pad), NODE_TPB, 0, st, c->dI, P, tab, c->w_pad, c->n_pad);
     }
 }
 
@@ -665,7 +667,6 @@ es_status es_create_batch(const es_config* cfgs, int n_inst, es_ctx** out)
     c->w_pad = build_work(c, [](const Inst& I) { return (long long)node_tiles(I, 3); }, c->n_pad);
     c->w_cell = build_work(c, [](const Inst& I) { return (long long)node_tiles(I, 0); }, c->n_cell);
     if (c->d == 3) c->w_ext = build_work(c, [](const Inst& I) { return (long long)node_tiles(I, 6); }, c->n_ext);
-    if (c->d == 3) c->w_xe = build_work(c, [](const Inst& I) { return (long long)node_tiles(I, 9); }, c->n_xe);
     if (c->d == 3) c->w_col = build_work(c, [](const Inst& I) { return (long long)col3_items(I); }, c->n_col);
     for (int k = 0; k < c->d; ++k)
         for (int sh = 0; sh < NSHAPE; ++sh) {
@@ -695,7 +696,7 @@ es_status es_create_batch(const es_config* cfgs, int n_inst, es_ctx** out)
         c->fused_grid = c->sms * flux2d_occ(c, 0);
     }
     cudaError_t e = cudaDeviceSynchronize();
-    if (!ok || e != cudaSuccess || !c->w_pad || !c->w_cell || (c->d == 3 && (!c->w_ext || !c->w_xe || !c->w_col))) {
+    if (!ok || e != cudaSuccess || !c->w_pad || !c->w_cell || (c->d == 3 && (!c->w_ext || !c->w_col))) {
         fprintf(stderr, "es_create: setup failed: %s\n", cudaGetErrorString(e));
         es_destroy(c);
         return ES_ERR_CUDA;

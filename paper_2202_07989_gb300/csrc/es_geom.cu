@@ -126,8 +126,9 @@ void launch_metrics2d(bool dot, int grid, cudaStream_t st, const Inst* insts, co
     else pdl_launch(metrics2d_kernel<false>, grid, NODE_TPB, 0, st, insts, single, table, work, nwork, reset, ninst, vcl);
 }
 
-// 3D pass 0: x on the grid with 9 ghost layers (extent n + 18), every ghost node mapped once
-// (periodic shift, wall mirror), so the passes below read positions without branches
+// 3D pass 0: x on the grid with 9 ghost layers (extent n + 18), of which the 6 the passes below
+// read are filled, every ghost node mapped once (periodic shift, wall mirror), so those passes
+// read positions without branches
 __global__ void xe_fill_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
                                const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr, int reset_n)
 {
@@ -138,7 +139,7 @@ __global__ void xe_fill_kernel(const Inst* __restrict__ insts, StagePtrs single,
         const Inst& I = insts[it.x];
         ES_PTRS(S);
         int i0, i1, i2;
-        if (!tile_node(I, it.y, 9, i0, i1, i2)) continue;
+        if (!tile_node(I, it.y, 6, i0, i1, i2)) continue;
         const long long X0 = I.n[0] + 18, X1 = I.n[1] + 18, nx = X0 * X1 * (I.n[2] + 18);
         const long long e = ((long long)(i2 + 9) * X1 + (i1 + 9)) * X0 + (i0 + 9);
         double v[3];
@@ -155,9 +156,10 @@ __global__ void xe_fill_kernel(const Inst* __restrict__ insts, StagePtrs single,
     }
 }
 
-// 3D pass 1: at the nodes with 6 ghost layers (extent n + 12), from the 9-layer position
-// grid, the products P[b][j] = delta_b[x_p] x_q for (p, q) = (2,3), (3,1), (1,2) (j = 1, 2, 3):
-// every delta_b[x_p] enters Eq. (SCLCoeff) only multiplied by x_q at the same node
+// 3D pass 1: at the nodes within 3 ghost layers (stored on the grid with 6 ghost layers, extent
+// n + 12), from the ghost-extended positions, the products P[b][j] = delta_b[x_p] x_q for
+// (p, q) = (2,3), (3,1), (1,2) (j = 1, 2, 3): every delta_b[x_p] enters Eq. (SCLCoeff) only
+// multiplied by x_q at the same node
 __global__ void dx3d_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
                             const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr)
 {
@@ -168,7 +170,7 @@ __global__ void dx3d_kernel(const Inst* __restrict__ insts, StagePtrs single, co
         const Inst& I = insts[it.x];
         long long E0 = I.n[0] + 12, E1 = I.n[1] + 12, E2 = I.n[2] + 12, ne = E0 * E1 * E2;
         int i0, i1, i2;
-        if (!tile_node(I, it.y, 6, i0, i1, i2)) continue;
+        if (!tile_node(I, it.y, 3, i0, i1, i2)) continue;
         const long long p = ((long long)(i2 + 6) * E1 + (i1 + 6)) * E0 + (i0 + 6);
         const long long X0 = I.n[0] + 18, X1 = I.n[1] + 18, nx = X0 * X1 * (I.n[2] + 18);
         const long long xc = ((long long)(i2 + 9) * X1 + (i1 + 9)) * X0 + (i0 + 9);
@@ -202,9 +204,10 @@ __global__ void dx3d_kernel(const Inst* __restrict__ insts, StagePtrs single, co
 
 // 3D pass 2: J xi_k/x_j = (delta_a[P_b] - delta_b[P_a]) / (dxi_a dxi_b), P_b = delta_b[x_p] x_q
 // with (a, b) = (3,2), (1,3), (2,1) for k = 1, 2, 3 and (p, q) = (2,3), (3,1), (1,2)
-// for j = 1, 2, 3 (cyclic permutation of Eq. (SCLCoeff)).  Every ordered pair (a, b), a != b,
-// belongs to exactly one k, with sign +1 when (a, b) is k's pair and -1 when reversed; the
-// kernel walks the outer direction a and offset m once and adds each product term to its k.
+// for j = 1, 2, 3 (cyclic permutation of Eq. (SCLCoeff)), at the interior nodes (the ghost
+// layers follow by metrics3d_ghost_kernel).  Every ordered pair (a, b), a != b, belongs to
+// exactly one k, with sign +1 when (a, b) is k's pair and -1 when reversed; the kernel walks
+// the outer direction a and offset m once and adds each product term to its k.
 __global__ void metrics3d_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
                                  const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr)
 {
@@ -217,7 +220,7 @@ __global__ void metrics3d_kernel(const Inst* __restrict__ insts, StagePtrs singl
         const Inst& I = insts[it.x];
         ES_PTRS(S);
         int i0, i1, i2;
-        if (!tile_node(I, it.y, 3, i0, i1, i2)) continue;
+        if (!tile_node(I, it.y, 0, i0, i1, i2)) continue;
         const long long p = plin(I, i0, i1, i2);
         const double* D = scr[it.x].D3;
         const long long E0 = I.n[0] + 12, E1 = I.n[1] + 12, ne = E0 * E1 * (I.n[2] + 12);
@@ -262,6 +265,57 @@ __global__ void metrics3d_kernel(const Inst* __restrict__ insts, StagePtrs singl
             M[(k * 4 + 0) * np + p] = vcl_metric<3>(xd, m[k]);
 #pragma unroll
             for (int j = 0; j < 3; ++j) M[(k * 4 + 1 + j) * np + p] = m[k][j];
+        }
+    }
+}
+
+// 3D pass 3: the metrics at the 3 ghost layers of the padded buffer from those of the interior
+// node the ghost maps to.  A periodic ghost is the wrapped node shifted by the box length, so
+// its metrics are the wrapped node's.  A wall ghost (every non-periodic side) is the half-cell
+// mirror of an interior node with the normal coordinate mirrored, x_d -> 2a - x_d: the
+// reflections of xi_d and x_d flip the sign of J xi_k/x_j when exactly one of k, j is d, and of
+// J xi_k/t (with xdot_d negated) when k is d; a node outside in several directions takes the
+// product of the flips.  The values equal the nested operators evaluated at the ghost node from
+// the mapped positions, up to the rounding of the shifted or mirrored coordinates.
+__global__ void metrics3d_ghost_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
+                                       const int2* __restrict__ work, int nwork)
+{
+    pdl_entry();
+    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+        int2 it = work[wi];
+        const Inst& I = insts[it.x];
+        ES_PTRS(S);
+        int i[3];
+        if (!tile_node(I, it.y, 3, i[0], i[1], i[2])) continue;
+        int src[3] = { i[0], i[1], i[2] };
+        bool mir[3] = { false, false, false }, ghost = false;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int n = I.n[d];
+            if (i[d] >= 0 && i[d] < n) continue;
+            ghost = true;
+            const int side = i[d] < 0 ? 0 : 1;
+            if (I.bc[d][side] == BC_PERIODIC) {
+                src[d] = i[d] - floordiv_(i[d], n) * n;
+            } else {
+                src[d] = side == 0 ? -1 - i[d] : 2 * n - 1 - i[d];
+                mir[d] = true;
+            }
+        }
+        if (!ghost) continue;
+        double* M = S.M;
+        const long long np = I.npad, p = plin(I, i[0], i[1], i[2]), q = plin(I, src[0], src[1], src[2]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                bool neg = false;
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+                    if (mir[d] && ((k == d) != (c > 0 && c - 1 == d))) neg = !neg;
+                const double v = M[(k * 4 + c) * np + q];
+                M[(k * 4 + c) * np + p] = neg ? -v : v;
+            }
         }
     }
 }
