@@ -35,6 +35,7 @@ struct es_ctx {
     int* d_first_cell = nullptr;
     double* partial = nullptr;
     int* status = nullptr;
+    int* mflag = nullptr;     // 3D: reuse test of the spatial metrics ([2] = reuse, see metrics_reuse_kernel)
     // stage buffers (per instance): (JU | J | x) for the two intermediate stages
     std::vector<double*> stA, stB;
     // batched tables
@@ -376,9 +377,11 @@ struct ProfScope {
 
 // metrics of the stage mesh P.x / P.xdot into P.M; reset = true also resets the reduction
 // slots (the first kernel of a mesh step); dot = true (2D) also forms the metrics of the mesh
-// velocity into P.Md, so the later stages of an RK step need no metrics pass
+// velocity into P.Md, so the later stages of an RK step need no metrics pass; reuse = true (3D)
+// keeps the spatial rows of M when they were formed from this very mesh (the VCL rows are
+// formed again)
 void launch_metrics(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStream_t st, bool reset = false,
-                    bool dot = false, bool vcl = true)
+                    bool dot = false, bool vcl = true, bool reuse = false)
 {
     ProfScope ps(c, PC_METRICS, st);
     if (c->d == 2) {
@@ -387,10 +390,15 @@ void launch_metrics(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStr
     } else {
         // positions within 6 ghost layers, products within 3, metrics at the interior nodes, then
         // the metrics of the 3 ghost layers from those of the nodes they map to
+        const int* ru = reuse ? c->mflag + 2 : nullptr;
+        if (reuse)
+            pdl_launch(metrics_reuse_kernel, node_grid(c, c->n_cell), NODE_TPB, 0, st, c->dI, P, tab, c->w_cell, c->n_cell,
+                       c->dS, c->mflag);
         pdl_launch(xe_fill_kernel, node_grid(c, c->n_ext), NODE_TPB, 0, st, c->dI, P, tab, c->w_ext, c->n_ext, c->dS,
                    reset ? c->n_inst : 0);
-        pdl_launch(dx3d_kernel, node_grid(c, c->n_pad), NODE_TPB, 0, st, c->dI, P, tab, c->w_pad, c->n_pad, c->dS);
-        pdl_launch(metrics3d_kernel, node_grid(c, c->n_cell), NODE_TPB, 0, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
+        pdl_launch(dx3d_kernel, node_grid(c, c->n_pad), NODE_TPB, 0, st, c->dI, P, tab, c->w_pad, c->n_pad, c->dS, ru);
+        pdl_launch(metrics3d_kernel, node_grid(c, c->n_cell), NODE_TPB, 0, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS,
+                   ru);
         pdl_launch(metrics3d_ghost_kernel, node_grid(c, c->n_pad), NODE_TPB, 0, st, c->dI, P, tab, c->w_pad, c->n_pad);
     }
 }
@@ -472,7 +480,9 @@ void stage_ptrs(es_ctx* c, int i, double* JU, double* J, double* x, const double
         P.J = in_j[s];
         P.x = in_x[s];
         P.xdot = (xdot && !fixed) ? xdot : S.zeros;
-        P.M = S.M;
+        // a 3D moving mesh keeps the second stage's metrics (those of x^n + dt xdot, the next
+        // step's mesh) in M and forms the third stage's in M3
+        P.M = (s == 2 && S.M3) ? S.M3 : S.M;
         P.Md = S.Md;
         P.accU = S.accU;
         P.accJ = S.accJ;
@@ -508,7 +518,7 @@ void launch_mesh(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStream
     Q.M = c->hS[0].M;
     // also resets the reduction slots; the VCL rows (xdot = 0 here) matter only on a fixed mesh,
     // whose stages use these metrics: a moving-mesh step's velocity pass writes them
-    launch_metrics(c, Q, tab, st, true, false, c->hI[0].fixed != 0);
+    launch_metrics(c, Q, tab, st, true, false, c->hI[0].fixed != 0, true);
     ProfScope ps(c, PC_MESH, st);
     int gc = node_grid(c, c->n_cell);
     if (c->mixed && c->d == 3)
@@ -629,6 +639,9 @@ es_status es_create_batch(const es_config* cfgs, int n_inst, es_ctx** out)
             ok = ok && dalloc(c, (void**)&S.D3, sizeof(double) * 9 * ne);
             const long long nx = (long long)(I.n[0] + 18) * (I.n[1] + 18) * (I.n[2] + 18);
             ok = ok && dalloc(c, (void**)&S.XE, sizeof(double) * 3 * nx);
+            if (!I.fixed) ok = ok && dalloc(c, (void**)&S.M3, sizeof(double) * 12 * I.npad);
+            ok = ok && dalloc(c, (void**)&S.Xm, sizeof(double) * 3 * n);
+            if (ok) cudaMemset(S.Xm, 0xff, sizeof(double) * 3 * n);     // NaN: equal to no position
         }
         ok = ok && dalloc(c, (void**)&S.accU, sizeof(double) * I.nc * n);
         ok = ok && dalloc(c, (void**)&S.accJ, sizeof(double) * n);
@@ -656,6 +669,7 @@ es_status es_create_batch(const es_config* cfgs, int n_inst, es_ctx** out)
     }
     ok = ok && dalloc(c, (void**)&c->dS, sizeof(Scratch) * n_inst);
     ok = ok && dalloc(c, (void**)&c->status, sizeof(int));
+    ok = ok && dalloc(c, (void**)&c->mflag, sizeof(int) * 3);
     if (!ok) {
         es_destroy(c);
         fprintf(stderr, "es_create: device allocation failed\n");
@@ -664,6 +678,7 @@ es_status es_create_batch(const es_config* cfgs, int n_inst, es_ctx** out)
     cudaMemcpy(c->dI, c->hI.data(), sizeof(Inst) * n_inst, cudaMemcpyHostToDevice);
     cudaMemcpy(c->dS, c->hS.data(), sizeof(Scratch) * n_inst, cudaMemcpyHostToDevice);
     cudaMemset(c->status, 0, sizeof(int));
+    cudaMemset(c->mflag, 0, sizeof(int) * 3);
     c->w_pad = build_work(c, [](const Inst& I) { return (long long)node_tiles(I, 3); }, c->n_pad);
     c->w_cell = build_work(c, [](const Inst& I) { return (long long)node_tiles(I, 0); }, c->n_cell);
     if (c->d == 3) c->w_ext = build_work(c, [](const Inst& I) { return (long long)node_tiles(I, 6); }, c->n_ext);

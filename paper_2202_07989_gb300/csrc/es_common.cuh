@@ -130,6 +130,8 @@ struct Scratch {
     double* Md;               // 2D: padded metrics of the mesh velocity
     double* D3;               // 3D: products delta_b[x_p] x_q on the grid with 6 ghost layers
     double* XE;               // 3D: x on the grid with 9 ghost layers (boundary maps applied once)
+    double* M3;               // 3D moving mesh: padded metrics of the third RK stage's mesh
+    double* Xm;               // 3D: the positions the spatial rows of M were formed from (NaN before)
     double* accU;
     double* accJ;
     double* red;              // reductions: [0] CFL max, [1..4] monitor maxima, [5] Delta_tau

@@ -126,9 +126,47 @@ void launch_metrics2d(bool dot, int grid, cudaStream_t st, const Inst* insts, co
     else pdl_launch(metrics2d_kernel<false>, grid, NODE_TPB, 0, st, insts, single, table, work, nwork, reset, ninst, vcl);
 }
 
+// Reuse test of the spatial metrics, before the pass that opens a mesh step: they are reused
+// when every instance's mesh equals, bit for bit, the positions its metrics buffer M was formed
+// from (Xm) and the pass writes M.  After an SSP-RK3 step the new mesh x^n + dt xdot is exactly
+// the second stage's mesh, whose metrics the second stage left in M; a fixed mesh never changes.
+// flag[0] collects mismatches, flag[1] counts finished blocks; the last block stores the
+// verdict in flag[2] and clears the other two for the next test.
+__global__ void metrics_reuse_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
+                                     const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr, int* flag)
+{
+    pdl_entry();
+    int bad = 0;
+    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+        const int2 it = work[wi];
+        const Inst& I = insts[it.x];
+        ES_PTRS(S);
+        const Scratch& Sc = scr[it.x];
+        if (S.M != Sc.M || !Sc.Xm) bad = 1;
+        int i0, i1, i2;
+        if (bad || !tile_node(I, it.y, 0, i0, i1, i2)) continue;
+        const long long c = lin(I, i0, i1, i2);
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            if (!(S.x[q * I.ncell + c] == Sc.Xm[q * I.ncell + c])) bad = 1;
+    }
+    bad = __syncthreads_or(bad);
+    if (threadIdx.x == 0) {
+        if (bad) atomicOr(&flag[0], 1);
+        __threadfence();
+        if (atomicAdd(&flag[1], 1) == (int)gridDim.x - 1) {
+            flag[2] = atomicOr(&flag[0], 0) == 0 ? 1 : 0;
+            flag[0] = 0;
+            flag[1] = 0;
+            __threadfence();
+        }
+    }
+}
+
 // 3D pass 0: x on the grid with 9 ghost layers (extent n + 18), of which the 6 the passes below
 // read are filled, every ghost node mapped once (periodic shift, wall mirror), so those passes
-// read positions without branches
+// read positions without branches.  When the pass writes the context's metrics buffer M, the
+// interior positions also go to Xm (the positions M's spatial rows are formed from).
 __global__ void xe_fill_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
                                const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr, int reset_n)
 {
@@ -147,6 +185,11 @@ __global__ void xe_fill_kernel(const Inst* __restrict__ insts, StagePtrs single,
             const long long c = lin(I, i0, i1, i2);
 #pragma unroll
             for (int q = 0; q < 3; ++q) v[q] = S.x[q * I.ncell + c];
+            double* Xm = scr[it.x].Xm;
+            if (Xm && S.M == scr[it.x].M) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) Xm[q * I.ncell + c] = v[q];
+            }
         } else {
             x_at<false>(I, S.x, i0, i1, i2, v);
         }
@@ -161,9 +204,10 @@ __global__ void xe_fill_kernel(const Inst* __restrict__ insts, StagePtrs single,
 // (p, q) = (2,3), (3,1), (1,2) (j = 1, 2, 3): every delta_b[x_p] enters Eq. (SCLCoeff) only
 // multiplied by x_q at the same node
 __global__ void dx3d_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
-                            const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr)
+                            const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr, const int* reuse)
 {
     pdl_entry();
+    if (reuse && *reuse) return;      // the spatial metrics in M are those of this mesh
     const int PQ[3][2] = { { 1, 2 }, { 2, 0 }, { 0, 1 } };
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
         int2 it = work[wi];
@@ -209,9 +253,11 @@ __global__ void dx3d_kernel(const Inst* __restrict__ insts, StagePtrs single, co
 // exactly one k, with sign +1 when (a, b) is k's pair and -1 when reversed; the kernel walks
 // the outer direction a and offset m once and adds each product term to its k.
 __global__ void metrics3d_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
-                                 const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr)
+                                 const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr,
+                                 const int* reuse)
 {
     pdl_entry();
+    const bool keep = reuse && *reuse;    // spatial rows of M already formed: the VCL rows only
     // the ordered pair (a, b) belongs to metric row k = 3 - a - b, with sign +1 when b follows a
     // cyclically by two, -1 by one (compile-time constants once the loops unroll)
     const int AB[3][2] = { { 2, 1 }, { 0, 2 }, { 1, 0 } };
@@ -222,6 +268,20 @@ __global__ void metrics3d_kernel(const Inst* __restrict__ insts, StagePtrs singl
         int i0, i1, i2;
         if (!tile_node(I, it.y, 0, i0, i1, i2)) continue;
         const long long p = plin(I, i0, i1, i2);
+        double* M = S.M;
+        const long long np = I.npad;
+        double xd[3] = { 0, 0, 0 };
+        if (S.xdot) x_at<true>(I, S.xdot, i0, i1, i2, xd);
+        if (keep) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                double m[3];
+#pragma unroll
+                for (int j = 0; j < 3; ++j) m[j] = M[(k * 4 + 1 + j) * np + p];
+                M[(k * 4 + 0) * np + p] = vcl_metric<3>(xd, m);
+            }
+            continue;
+        }
         const double* D = scr[it.x].D3;
         const long long E0 = I.n[0] + 12, E1 = I.n[1] + 12, ne = E0 * E1 * (I.n[2] + 12);
         const long long e_c = ((long long)(i2 + 6) * E1 + (i1 + 6)) * E0 + (i0 + 6);
@@ -256,10 +316,6 @@ __global__ void metrics3d_kernel(const Inst* __restrict__ insts, StagePtrs singl
 #pragma unroll
             for (int j = 0; j < 3; ++j) m[k][j] = t[k][j] * ck;
         }
-        double xd[3] = { 0, 0, 0 };
-        if (S.xdot) x_at<true>(I, S.xdot, i0, i1, i2, xd);
-        double* M = S.M;
-        long long np = I.npad;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             M[(k * 4 + 0) * np + p] = vcl_metric<3>(xd, m[k]);

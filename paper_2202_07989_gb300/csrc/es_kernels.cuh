@@ -60,12 +60,14 @@ struct FluxLaunch {
 void launch_metrics2d(bool dot, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
                       const StagePtrs* table, const int2* work, int nwork, const Scratch* reset, int ninst,
                       bool vcl = true);
+__global__ void metrics_reuse_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work,
+                                     int nwork, const Scratch* scr, int* flag);
 __global__ void xe_fill_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work, int nwork,
                                const Scratch* scr, int reset_n);
 __global__ void dx3d_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work, int nwork,
-                            const Scratch* scr);
+                            const Scratch* scr, const int* reuse);
 __global__ void metrics3d_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work, int nwork,
-                                 const Scratch* scr);
+                                 const Scratch* scr, const int* reuse);
 __global__ void metrics3d_ghost_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work,
                                        int nwork);
 __global__ void conversion_check_kernel(const double* in, int n, float* o32, double* o64);

@@ -1,0 +1,71 @@
+"""Reuse of the 3D spatial metrics across time steps.
+
+The pass that opens a 3D mesh step keeps the spatial metrics in the context's metrics buffer
+when they were formed from the very same positions: the second SSP-RK3 stage's mesh
+x^n + dt xdot is, bit for bit, the next step's mesh, and a fixed mesh never changes.  Otherwise
+it forms them again.  Kept and re-formed metrics agree bit for bit, so a run that reuses must
+equal a run whose reuse is defeated between steps, and a mesh changed between steps must give
+what a fresh context gives on the changed state.
+"""
+import pytest
+
+from paper_2202_07989_gb300 import workloads as W
+
+from .helpers import case, need_gpu, to_dev
+
+pytestmark = pytest.mark.gpu
+
+CASES = [((20, 14, 12), "periodic", 1, 1), ((13, 22, 15), "reflect", 2, 2), ((24, 12, 11), "mixed", 3, 2)]
+
+
+def _problem(n, bc, seed, N, fixed):
+    pb, JU, J, x, _ = case(3, N, n, bc, es=True, seed=seed, pinf=0.7)
+    sigma = (W.SIG_RHO, W.SIG_P) if N == 1 else (W.SIG_RHO1, W.SIG_P)
+    pb = pb.with_(mu=4, nf=2, sigma=sigma, alpha=(50.0, 20.0), fixed_mesh=fixed)
+    return pb, JU, J, x
+
+
+@pytest.mark.parametrize("fixed", [False, True])
+@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("n,bc,seed,N", CASES)
+def test_reused_metrics_equal_reformed(n, bc, seed, N, form, fixed):
+    torch = need_gpu()
+    from paper_2202_07989_gb300 import es
+    pb, JU0, J0, x0 = _problem(n, bc, seed, N, fixed)
+    out = []
+    for spoil in (False, True):
+        c = es.Context(pb, form)
+        ju, jj, xx = (to_dev(a, torch) for a in (JU0, J0, x0))
+        for s in range(3):
+            if spoil and s > 0:
+                # metrics of another mesh into the context's buffer: the mesh step must form
+                # those of xx again
+                c.es_rhs(ju, jj, (xx * 1.01).contiguous())
+            c.es_step(ju, jj, xx)
+        assert c.es_poll_status() == 0
+        out.append((ju, jj, xx))
+    for a, b in zip(*out):
+        assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("n,bc,seed,N", CASES)
+def test_changed_mesh_is_not_reused(n, bc, seed, N, form):
+    torch = need_gpu()
+    from paper_2202_07989_gb300 import es
+    pb, JU0, J0, x0 = _problem(n, bc, seed, N, False)
+    c = es.Context(pb, form)
+    ju, jj, xx = (to_dev(a, torch) for a in (JU0, J0, x0))
+    c.es_step(ju, jj, xx)
+    # move one interior node by a small fraction of the spacing between the steps
+    k = (n[2] // 2, n[1] // 2, n[0] // 2)
+    for j in range(3):
+        xx[(j,) + k] += 1e-4 * pb.dxi[j]
+    ref = [t.clone() for t in (ju, jj, xx)]
+    c.es_step(ju, jj, xx)
+    assert c.es_poll_status() == 0
+    f = es.Context(pb, form)
+    f.es_step(*ref)
+    assert f.es_poll_status() == 0
+    for a, b in zip((ju, jj, xx), ref):
+        assert torch.equal(a, b)
