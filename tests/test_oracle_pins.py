@@ -955,3 +955,60 @@ def test_y_band_separates_round_off_from_jumps(d, N, band, below, above):
             assert diss == 0.0, (size, diss)
         else:
             assert diss > 0.0, size
+
+
+# ---------------------------------------------------------------------------
+# metrics at ghost nodes: the symmetry of the boundary maps
+
+
+@pytest.mark.parametrize("d", [2, 3])
+@pytest.mark.parametrize("bc", ["periodic", "mixed", "reflect"])
+def test_metric_ghosts_follow_the_boundary_maps(d, bc):
+    """The positions of a ghost node are those of the interior node it maps to, shifted by the
+    box length (periodic side) or mirrored about the wall, x_d -> 2a - x_d, with xdot_d negated
+    (every other side; the ghost of node i is node -1-i, a half-cell mirror).  The metrics of
+    Eq. (SCLCoeff) and Eq. (VCLCoeff) evaluated there are then the mapped node's: unchanged
+    across a periodic side; across a wall the reflections of xi_d and x_d flip the sign of
+    J xi_k/x_j when exactly one of k, j is d, and of J xi_k/t when k is d, and flips compose at
+    edges and corners.  A mirror about the wrong node or a dropped sign fails this."""
+    n = (12, 11, 10)[:d]
+    pb = W.random_problem(d, 1, n, bc=bc)
+    rng = np.random.default_rng(7 + d)
+    x = W.smooth_mesh(pb, rng, amp=0.05)
+    xdot = 0.3 * (W.smooth_mesh(pb, rng, amp=0.05) - np.stack(W.xi_nodes(pb)))
+    M = Oracle(pb).metrics(x, xdot)
+    nf = d * (d + 1)
+    P = M.shape[1:][::-1]                       # padded extents (P0, P1[, P2])
+    scale = [np.abs(M[f]).max() for f in range(nf)]
+    checked = 0
+    worst = 0.0
+    for idx in np.ndindex(*[P[k] for k in range(d)][::-1]):
+        g = [idx[::-1][k] - 3 for k in range(d)]
+        if all(0 <= g[k] < n[k] for k in range(d)):
+            continue
+        src, mir = list(g), [False] * d
+        for k in range(d):
+            if 0 <= g[k] < n[k]:
+                continue
+            side = 0 if g[k] < 0 else 1
+            if pb.bc[k][side] == W.PERIODIC:
+                src[k] = g[k] % n[k]
+            else:
+                src[k] = -1 - g[k] if side == 0 else 2 * n[k] - 1 - g[k]
+                mir[k] = True
+        gi = tuple(v + 3 for v in g[::-1])
+        si = tuple(v + 3 for v in src[::-1])
+        if d == 2:
+            gi, si = (0,) + gi, (0,) + si
+        for k in range(d):
+            for c in range(d + 1):
+                neg = False
+                for m in range(d):
+                    if mir[m] and ((k == m) != (c > 0 and c - 1 == m)):
+                        neg = not neg
+                f = k * (d + 1) + c
+                want = -M[(f,) + si] if neg else M[(f,) + si]
+                worst = max(worst, abs(M[(f,) + gi] - want) / scale[f])
+        checked += 1
+    assert checked > 0
+    assert worst <= 1e-12, worst
