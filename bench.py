@@ -331,9 +331,10 @@ class Batch:
 
 
 def tune(runner, batched=False):
-    """Run the library's flux autotuner on the runner's state; returns the choice per
-    direction as "S x WT tile, grid CTAs, ms per launch" and, in 2D, the fused stage launch
-    ("fused TX x TY tile ..." when chosen, else "fused off" with its best time)."""
+    """Run the library's autotuner on the runner's state; returns the choice per direction as
+    "S x WT tile, grid CTAs, ms per launch" and, in 2D, the fused stage launch ("fused TX x TY
+    tile ..." when chosen, else "fused off" with its best time) and, on a mixed 2D moving mesh,
+    the tile of the fused mesh-step launch."""
     if batched:
         t = runner.ctx.es_autotune()
     else:
@@ -342,6 +343,9 @@ def tune(runner, batched=False):
     if len(t) == 2:
         sh, TX, TY, grid, ms = runner.ctx.es_get_fusion()
         out.append("fused %dx%d tile, %d CTAs, %.3f ms" % (TX, TY, grid, ms) if sh >= 0 else "fused off (best %.3f ms)" % ms)
+        sh, TX, TY, thr, ms = runner.ctx.es_get_mesh_tiles()
+        if sh >= 0:
+            out.append("mesh step %dx%d tile, %d threads, %.3f ms" % (TX, TY, thr, ms))
     return out
 
 

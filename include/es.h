@@ -207,6 +207,23 @@ es_status es_get_fusion(const es_ctx* ctx, int* shape, int* TX, int* TY, int* gr
  * range or when shape >= 0 on a 3D context. */
 es_status es_set_fusion(es_ctx* ctx, int shape, int grid);
 
+/* Tiles of the mixed-form 2D mesh step (the paper has no counterpart; a launch
+ * schedule).  The monitor, the filter passes and the Jacobi sweeps of Sec. 4 run
+ * in one launch over TX x TY node tiles, each staged in shared memory with a halo
+ * of mu + n_f nodes (temporal blocking), in one of 4 shapes: 0: 32 x 8 tiles with
+ * 256 threads per block; 1: 32 x 16, 2: 24 x 16, 3: 24 x 12, each with 512.
+ * Every node's displacement is formed by the same arithmetic in any tile, so the
+ * shape changes no result.  es_autotune on such a context also times every shape
+ * on one mesh step of the given state and keeps the fastest.  A new context
+ * starts in shape 0.
+ * es_get_mesh_tiles: shape index, TX, TY, threads per block and the best time per
+ * launch the last es_autotune measured (0 if none).  All pointers HOST, one value
+ * each; on contexts without the fused mesh step, shape -1 and zeros.
+ * es_set_mesh_tiles: shape 0..3; ES_ERR_ARG when out of range or when the context
+ * is not a mixed-form 2D context. */
+es_status es_get_mesh_tiles(const es_ctx* ctx, int* shape, int* TX, int* TY, int* threads, float* ms);
+es_status es_set_mesh_tiles(es_ctx* ctx, int shape);
+
 /* Schlieren function of Example 5.8, Eq. (schlieren), on one instance:
  * phi = exp(-Psi |grad rho| / max |grad rho|), Psi = (psi1 rho_1 + psi2 rho_2) / rho
  * (the paper uses psi1 = 30, psi2 = 150), grad the physical gradient
@@ -264,7 +281,7 @@ es_status es_step_batch(es_ctx* ctx, void* stream);
  * cudaMemcpyAsync per buffer and direction (asynchronous when the host buffers
  * are pinned).  Each step replays a CUDA graph of es_step on those buffers,
  * captured on a private stream by the first call and again after es_autotune,
- * es_set_tuning, es_set_fusion or a new dt_fixed; with es_profile on, the steps
+ * es_set_tuning, es_set_fusion, es_set_mesh_tiles or a new dt_fixed; with es_profile on, the steps
  * are launched one kernel at a time instead.  ES_ERR_ARG during stream capture. */
 es_status es_run_host(es_ctx* ctx, double* JU, double* J, double* x, int steps, double dt_fixed, double* t,
                       void* stream);

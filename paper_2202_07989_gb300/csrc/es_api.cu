@@ -32,6 +32,10 @@ struct es_ctx {
     int n_flux[3][NSHAPE] = {};
     int2* w_fused[NFSHAPE] = {};           // fused 2D stage work list per fused tile shape
     int n_fused[NFSHAPE] = {};
+    int2* w_jf[NJF_SHAPE] = {};            // mixed 2D: fused mesh-step tiles per shape (JF_SHAPES)
+    int n_jf[NJF_SHAPE] = {};
+    int jf_shape = JF_SHAPE_DEFAULT;
+    float jf_ms = 0.f;
     int* d_first_cell = nullptr;
     double* partial = nullptr;
     int* status = nullptr;
@@ -379,7 +383,7 @@ struct ProfScope {
 // slots (the first kernel of a mesh step); dot = true (2D) also forms the metrics of the mesh
 // velocity into P.Md, so the later stages of an RK step need no metrics pass; reuse = true (3D)
 // keeps the spatial rows of M when they were formed from this very mesh (the VCL rows are
-// formed again)
+// formed again when vcl = true, and left to the velocity pass otherwise)
 void launch_metrics(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStream_t st, bool reset = false,
                     bool dot = false, bool vcl = true, bool reuse = false)
 {
@@ -398,8 +402,10 @@ void launch_metrics(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStr
                    reset ? c->n_inst : 0);
         pdl_launch(dx3d_kernel, node_grid(c, c->n_pad), NODE_TPB, 0, st, c->dI, P, tab, c->w_pad, c->n_pad, c->dS, ru);
         pdl_launch(metrics3d_kernel, node_grid(c, c->n_cell), NODE_TPB, 0, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS,
-                   ru);
-        pdl_launch(metrics3d_ghost_kernel, node_grid(c, c->n_pad), NODE_TPB, 0, st, c->dI, P, tab, c->w_pad, c->n_pad);
+                   ru, vcl ? 1 : 0);
+        // kept metrics without VCL rows (the velocity pass writes them) keep their ghost layers too
+        pdl_launch(metrics3d_ghost_kernel, node_grid(c, c->n_pad), NODE_TPB, 0, st, c->dI, P, tab, c->w_pad, c->n_pad,
+                   vcl ? nullptr : ru);
     }
 }
 
@@ -507,6 +513,13 @@ const double XCOEF[3] = { 1.0, 0.5, 1.0 };
 // 2D moving meshes form the stage metrics as M(x^n) + s dt M(xdot) (the metrics are linear in x)
 bool linear_stage_metrics(const es_ctx* c) { return c->d == 2 && !c->hI[0].fixed; }
 
+// whether the mesh step runs the fused 2D launch (monitor, filter passes and sweeps)
+bool fused_mesh2d(const es_ctx* c)
+{
+    const Inst& I = c->hI[0];
+    return c->mixed && c->d == 2 && !I.fixed && I.mu >= 1 && I.mu <= JACOBI_FUSED_MAX && I.nf <= FILTER_FUSED_MAX;
+}
+
 // mesh redistribution (Sec. 4): the metrics of x^n (Eq. (cfl) and the monitor need them),
 // Delta t and the monitor gradients, the filter passes, the Jacobi sweeps with the limiter,
 // and the mesh velocity.  With step = true (a full time step follows) the velocity pass
@@ -532,9 +545,11 @@ void launch_mesh(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStream
     }
     int nf = c->hI[0].nf, mu = c->hI[0].mu;
     int th_sel = nf % 2;
-    if (c->mixed && c->d == 2 && mu >= 1 && mu <= JACOBI_FUSED_MAX && nf <= FILTER_FUSED_MAX) {
+    if (fused_mesh2d(c)) {
         // monitor, filter passes and sweeps in one launch
-        launch_jacobi_fused2d(gc, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS, mu, nf, th_sel);
+        const int js = c->jf_shape;
+        launch_jacobi_fused2d(js, node_grid(c, c->n_jf[js]), st, c->dI, P, tab, c->w_jf[js], c->n_jf[js], c->dS, mu, nf,
+                              th_sel);
     } else {
         // Theta once per node, then plain filter passes (forming it inside the first pass costs
         // 3^d evaluations per node)
@@ -692,6 +707,14 @@ es_status es_create_batch(const es_config* cfgs, int n_inst, es_ctx** out)
         for (int sh = 0; sh < NFSHAPE; ++sh) {
             c->w_fused[sh] = build_work(c, [sh](const Inst& I) { return fused_tiles(I, sh); }, c->n_fused[sh]);
             ok = ok && c->w_fused[sh];
+        }
+    if (c->d == 2 && c->mixed)
+        for (int sh = 0; sh < NJF_SHAPE; ++sh) {
+            c->w_jf[sh] = build_work(c, [sh](const Inst& I) {
+                return (long long)((I.n[0] + JF_SHAPES[sh][0] - 1) / JF_SHAPES[sh][0]) *
+                       ((I.n[1] + JF_SHAPES[sh][1] - 1) / JF_SHAPES[sh][1]);
+            }, c->n_jf[sh]);
+            ok = ok && c->w_jf[sh];
         }
     // per-instance ranges of the cell work list (entropy reduction)
     std::vector<int> first(n_inst + 1, 0);
@@ -1095,9 +1118,60 @@ es_status es_autotune(es_ctx* c, const double* JU, const double* J, const double
             }
         }
     }
+    // mixed 2D: the fused mesh-step launch in each tile shape, after the passes it reads
+    // (metrics, CFL and monitor gradients) on the same state; it writes only scratch
+    c->jf_ms = 0.f;
+    if (fused_mesh2d(c)) {
+        StagePtrs Q = P;
+        Q.xdot = nullptr;
+        const int mu = c->hI[0].mu, nf = c->hI[0].nf;
+        launch_metrics(c, Q, tab, st, true, false, false);
+        launch_cfl_grad(c->mixed, c->d, c->N, node_grid(c, c->n_cell), st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS);
+        float best = 3.0e38f;
+        for (int sh = 0; sh < NJF_SHAPE; ++sh) {
+            const int grid = node_grid(c, c->n_jf[sh]);
+            launch_jacobi_fused2d(sh, grid, st, c->dI, P, tab, c->w_jf[sh], c->n_jf[sh], c->dS, mu, nf, nf % 2);
+            cudaEventRecord(e0, st);
+            for (int r = 0; r < reps; ++r)
+                launch_jacobi_fused2d(sh, grid, st, c->dI, P, tab, c->w_jf[sh], c->n_jf[sh], c->dS, mu, nf, nf % 2);
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= (float)reps;
+            if (ms < best) {
+                best = ms;
+                c->jf_ms = ms;
+                c->jf_shape = sh;
+            }
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return cuda_check(c, "es_autotune");
+}
+
+es_status es_get_mesh_tiles(const es_ctx* c, int* shape, int* TX, int* TY, int* threads, float* ms)
+{
+    if (!c || !shape || !TX || !TY || !threads || !ms) return ES_ERR_ARG;
+    const bool on = fused_mesh2d(c);
+    *shape = on ? c->jf_shape : -1;
+    *TX = on ? JF_SHAPES[c->jf_shape][0] : 0;
+    *TY = on ? JF_SHAPES[c->jf_shape][1] : 0;
+    *threads = on ? JF_SHAPES[c->jf_shape][2] : 0;
+    *ms = on ? c->jf_ms : 0.f;
+    return ES_OK;
+}
+
+es_status es_set_mesh_tiles(es_ctx* c, int shape)
+{
+    if (!c) return ES_ERR_ARG;
+    if (!c->mixed || c->d != 2 || shape < 0 || shape >= NJF_SHAPE)
+        return fail(c, ES_ERR_ARG, "es_set_mesh_tiles: shape out of range or not a mixed-form 2D context");
+    c->jf_shape = shape;
+    c->jf_ms = 0.f;
+    drop_run_graph(c);
+    return ES_OK;
 }
 
 es_status es_get_tuning(const es_ctx* c, int* shape, int* S, int* WT, int* grid, float* ms)

@@ -254,10 +254,11 @@ __global__ void dx3d_kernel(const Inst* __restrict__ insts, StagePtrs single, co
 // the outer direction a and offset m once and adds each product term to its k.
 __global__ void metrics3d_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
                                  const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr,
-                                 const int* reuse)
+                                 const int* reuse, int vcl)
 {
     pdl_entry();
     const bool keep = reuse && *reuse;    // spatial rows of M already formed: the VCL rows only
+    if (keep && !vcl) return;             // ... and those are written by the velocity pass
     // the ordered pair (a, b) belongs to metric row k = 3 - a - b, with sign +1 when b follows a
     // cyclically by two, -1 by one (compile-time constants once the loops unroll)
     const int AB[3][2] = { { 2, 1 }, { 0, 2 }, { 1, 0 } };
@@ -334,9 +335,10 @@ __global__ void metrics3d_kernel(const Inst* __restrict__ insts, StagePtrs singl
 // product of the flips.  The values equal the nested operators evaluated at the ghost node from
 // the mapped positions, up to the rounding of the shifted or mirrored coordinates.
 __global__ void metrics3d_ghost_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
-                                       const int2* __restrict__ work, int nwork)
+                                       const int2* __restrict__ work, int nwork, const int* skip)
 {
     pdl_entry();
+    if (skip && *skip) return;            // ghost metrics kept with the interior ones
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
         int2 it = work[wi];
         const Inst& I = insts[it.x];

@@ -67,9 +67,9 @@ __global__ void xe_fill_kernel(const Inst* insts, StagePtrs single, const StageP
 __global__ void dx3d_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work, int nwork,
                             const Scratch* scr, const int* reuse);
 __global__ void metrics3d_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work, int nwork,
-                                 const Scratch* scr, const int* reuse);
+                                 const Scratch* scr, const int* reuse, int vcl);
 __global__ void metrics3d_ghost_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work,
-                                       int nwork);
+                                       int nwork, const int* skip);
 __global__ void conversion_check_kernel(const double* in, int n, float* o32, double* o64);
 __global__ void half_sum_check_kernel(const float* a, const float* b, int n, double* out);
 __global__ void logmean_small_check_kernel(const float* a, const float* b, const float* del, int n, float* fast,

@@ -920,29 +920,32 @@ __global__ void __launch_bounds__(NODE_TPB) jacobi_y_kernel(const Inst* __restri
     }
 }
 
-// Slot q = threadIdx.x, threadIdx.x + NODE_TPB, ... of a W-wide region and its column and row
+// Slot q = threadIdx.x, threadIdx.x + TPB, ... of a W-wide region (TPB threads per block) and its column and row
 // (a, b) = (q % W, q / W), stepped without a division per slot (W is a run-time width)
-struct SlotIter {
+template <int TPB>
+struct SlotIterN {
     int q, a, b, da, db, W;
-    __device__ explicit SlotIter(int W_) : q((int)threadIdx.x), W(W_)
+    __device__ explicit SlotIterN(int W_) : q((int)threadIdx.x), W(W_)
     {
         b = q / W;
         a = q - b * W;
-        db = NODE_TPB / W;
-        da = NODE_TPB - db * W;
+        db = TPB / W;
+        da = TPB - db * W;
     }
     __device__ void next()
     {
-        q += NODE_TPB;
+        q += TPB;
         a += da;
         b += db;
         if (a >= W) { a -= W; ++b; }
     }
 };
+using SlotIter = SlotIterN<NODE_TPB>;
+
 
 // Mixed form, 2D: the monitor, its F <= 4 filter passes and all H = mu <= 8 Jacobi sweeps
-// of jacobi_y_kernel in one launch (temporal blocking).  A block stages the region of its
-// 32 x 8 node tile plus a halo of H + F nodes in shared memory: Theta (formed from the
+// of jacobi_y_kernel in one launch (temporal blocking).  A block of TPB threads stages the region
+// of its TX x TY node tile plus a halo of H + F nodes in shared memory: Theta (formed from the
 // monitor gradients, then filtered F times; the halo shrinks by one node per pass), then on
 // the inner region (halo H) the displacements (ping-pong) and the spacings dl_{k+-} (formed in
 // FP64 from x^n, rounded to binary32).  Each Jacobi sweep updates every in-domain node of the
@@ -952,17 +955,19 @@ struct SlotIter {
 // all of them the tile is exact.  Periodic directions need no care: the region runs over
 // unwrapped indices and reads the wrapped node's data.  The last sweep forms the limiter
 // bounds of Sec. 4 for the tile.  F < 0: Theta is read from the buffer theta_sel instead.
-__global__ void __launch_bounds__(NODE_TPB) jacobi_fused2d_kernel(const Inst* __restrict__ insts, StagePtrs single,
-                                                                   const StagePtrs* __restrict__ table,
-                                                                   const int2* __restrict__ work, int nwork,
-                                                                   const Scratch* __restrict__ scr, int H, int F,
-                                                                   int theta_sel)
+template <int TX, int TY, int TPB>
+__global__ void __launch_bounds__(TPB, 1024 / TPB) jacobi_fused2d_kernel(const Inst* __restrict__ insts, StagePtrs single,
+                                                                          const StagePtrs* __restrict__ table,
+                                                                          const int2* __restrict__ work, int nwork,
+                                                                          const Scratch* __restrict__ scr, int H, int F,
+                                                                          int theta_sel)
 {
+    using SI = SlotIterN<TPB>;
     pdl_entry();
     extern __shared__ float jsm[];
     __shared__ double sh[32];
     const int Fp = F > 0 ? F : 0;
-    const int RX = NT_X + 2 * H, RY = NT_Y + 2 * H, NR = RX * RY;
+    const int RX = TX + 2 * H, RY = TY + 2 * H, NR = RX * RY;
     const int RXo = RX + 2 * Fp, RYo = RY + 2 * Fp, NRo = RXo * RYo;
     float* ya = jsm;              // [2][NR]
     float* yb = ya + 2 * NR;      // [2][NR]
@@ -978,8 +983,8 @@ __global__ void __launch_bounds__(NODE_TPB) jacobi_fused2d_kernel(const Inst* __
         const Scratch& Sc = scr[it.x];
         const int n0 = I.n[0], n1 = I.n[1];
         const bool per0 = I.bc[0][0] == BC_PERIODIC, per1 = I.bc[1][0] == BC_PERIODIC;
-        const int ntx = (n0 + NT_X - 1) / NT_X;
-        const int r0 = (it.y % ntx) * NT_X - H, r1 = (it.y / ntx) * NT_Y - H;    // inner region origin
+        const int ntx = (n0 + TX - 1) / TX;
+        const int r0 = (it.y % ntx) * TX - H, r1 = (it.y / ntx) * TY - H;    // inner region origin
         const int o0 = r0 - Fp, o1 = r1 - Fp;                                     // outer region origin
         const long long n = I.ncell;
         // whether the outer / inner region holds wall ghost nodes (tile-uniform: a region
@@ -992,7 +997,7 @@ __global__ void __launch_bounds__(NODE_TPB) jacobi_fused2d_kernel(const Inst* __
         if (F >= 0)
             for (int q = 0; q < I.n_sigma; ++q) inv[q] = inv_max<float>(Sc, q);
         const float* th = reinterpret_cast<const float*>(theta_sel ? Sc.th1 : Sc.th0);
-        for (SlotIter sl(RXo); sl.q < NRo; sl.next()) {
+        for (SI sl(RXo); sl.q < NRo; sl.next()) {
             const int q = sl.q;
             const long long src = s_map(I, o0 + sl.a, o1 + sl.b, 0);
             ta[q] = F >= 0 ? theta_at<float>(I, Sc, inv, src) : th[src];
@@ -1002,7 +1007,7 @@ __global__ void __launch_bounds__(NODE_TPB) jacobi_fused2d_kernel(const Inst* __
         float* tc_ = ta;
         float* tn_ = tb;
         for (int f = 0; f < F; ++f) {
-            for (SlotIter sl(RXo); sl.q < NRo; sl.next()) {
+            for (SI sl(RXo); sl.q < NRo; sl.next()) {
                 const int q = sl.q, a = sl.a, b = sl.b;
                 const int g0 = o0 + a, g1 = o1 + b;
                 const bool ghost = (!per0 && (g0 < 0 || g0 >= n0)) || (!per1 && (g1 < 0 || g1 >= n1));
@@ -1019,7 +1024,7 @@ __global__ void __launch_bounds__(NODE_TPB) jacobi_fused2d_kernel(const Inst* __
             __syncthreads();
             // wall ghosts: copies of the boundary node
             if (gh_out) {
-            for (SlotIter sl(RXo); sl.q < NRo; sl.next()) {
+            for (SI sl(RXo); sl.q < NRo; sl.next()) {
                 const int q = sl.q, a = sl.a, b = sl.b;
                 const int g0 = o0 + a, g1 = o1 + b;
                 const bool x0 = !per0 && (g0 < 0 || g0 >= n0), x1 = !per1 && (g1 < 0 || g1 >= n1);
@@ -1037,7 +1042,7 @@ __global__ void __launch_bounds__(NODE_TPB) jacobi_fused2d_kernel(const Inst* __
         // stage Theta, y = 0 and the + side spacings x^n_{i+e_k} - x^n_i of the in-domain nodes
         // (a periodic copy takes its wrapped node's, unshifted); the - side of a node whose
         // - neighbour is a wall ghost is formed here too, all others below
-        for (SlotIter sl(RX); sl.q < NR; sl.next()) {
+        for (SI sl(RX); sl.q < NR; sl.next()) {
             const int q = sl.q, a = sl.a, b = sl.b;
             const int g0 = r0 + a, g1 = r1 + b;
             ya[q] = ya[NR + q] = yb[q] = yb[NR + q] = 0.0f;
@@ -1070,7 +1075,7 @@ __global__ void __launch_bounds__(NODE_TPB) jacobi_fused2d_kernel(const Inst* __
         // the remaining - sides: minus the + side of the - neighbour (the same pair of nodes);
         // and the sweep weights Theta_{k+-1/2} / dxi_k^2 of every slot a sweep updates, with
         // their sum, formed once since Theta stays fixed through the sweeps
-        for (SlotIter sl(RX); sl.q < NR; sl.next()) {
+        for (SI sl(RX); sl.q < NR; sl.next()) {
             const int q = sl.q, a = sl.a, b = sl.b;
             const int g0 = r0 + a, g1 = r1 + b;
             const bool ghost = (!per0 && (g0 < 0 || g0 >= n0)) || (!per1 && (g1 < 0 || g1 >= n1));
@@ -1105,7 +1110,7 @@ __global__ void __launch_bounds__(NODE_TPB) jacobi_fused2d_kernel(const Inst* __
         for (int sw = 0; sw < H; ++sw) {
             // in-domain nodes: one sweep (neighbours outside the region leave a node invalid);
             // the slots with a zero weight sum (wall ghosts, the region's edge) keep their values
-            for (int q = threadIdx.x; q < NR; q += NODE_TPB) {
+            for (int q = threadIdx.x; q < NR; q += TPB) {
                 const float den = dn[q];
                 if (den == 0.0f) continue;
                 float num[2] = { 0.0f, 0.0f };
@@ -1124,7 +1129,7 @@ __global__ void __launch_bounds__(NODE_TPB) jacobi_fused2d_kernel(const Inst* __
             __syncthreads();
             // wall ghosts: the mirror of their source node, the mirrored component negated
             if (gh_in) {
-            for (SlotIter sl(RX); sl.q < NR; sl.next()) {
+            for (SI sl(RX); sl.q < NR; sl.next()) {
                 const int q = sl.q, a = sl.a, b = sl.b;
                 const int g0 = r0 + a, g1 = r1 + b;
                 const bool o0 = !per0 && (g0 < 0 || g0 >= n0), o1 = !per1 && (g1 < 0 || g1 >= n1);
@@ -1147,10 +1152,10 @@ __global__ void __launch_bounds__(NODE_TPB) jacobi_fused2d_kernel(const Inst* __
             yn = t;
         }
         // the tile: store y^[mu] and form the limiter bounds
-        const int lx = (int)threadIdx.x % NT_X, ly = (int)threadIdx.x / NT_X;
+        const int lx = (int)threadIdx.x % TX, ly = (int)threadIdx.x / TX;
         const int i0 = r0 + H + lx, i1 = r1 + H + ly;
         float bnd = 1.0f;
-        if (i0 < n0 && i1 < n1) {
+        if ((int)threadIdx.x < TX * TY && i0 < n0 && i1 < n1) {
             const int q = (ly + H) * RX + lx + H;
             const long long p = lin(I, i0, i1, 0);
             float* yd = reinterpret_cast<float*>(I.mu % 2 == 1 ? Sc.xa : Sc.xb);
@@ -1169,26 +1174,37 @@ __global__ void __launch_bounds__(NODE_TPB) jacobi_fused2d_kernel(const Inst* __
     }
 }
 
-size_t jacobi_fused2d_smem(int H, int F)
+size_t jacobi_fused2d_smem(int H, int F, int shape)
 {
-    const size_t nr = (size_t)(NT_X + 2 * H) * (NT_Y + 2 * H);
-    const size_t Fp = F > 0 ? F : 0, nro = (NT_X + 2 * H + 2 * Fp) * (NT_Y + 2 * H + 2 * Fp);
+    const int TX = JF_SHAPES[shape][0], TY = JF_SHAPES[shape][1];
+    const size_t nr = (size_t)(TX + 2 * H) * (TY + 2 * H);
+    const size_t Fp = F > 0 ? F : 0, nro = (TX + 2 * H + 2 * Fp) * (TY + 2 * H + 2 * Fp);
     return sizeof(float) * (17 * nr + 2 * nro);
 }
+
+#define JF_KERNELS(X) X(0, 32, 8, 256) X(1, 32, 16, 512) X(2, 24, 16, 512) X(3, 24, 12, 512)
 
 void prepare_mesh()
 {
     prepare_mesh3d();
-    cudaFuncSetAttribute(jacobi_fused2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)jacobi_fused2d_smem(JACOBI_FUSED_MAX, FILTER_FUSED_MAX));
+#define JF_ATTR(S, TX, TY, TPB)                                                                         \
+    cudaFuncSetAttribute(jacobi_fused2d_kernel<TX, TY, TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                         (int)jacobi_fused2d_smem(JACOBI_FUSED_MAX, FILTER_FUSED_MAX, S));
+    JF_KERNELS(JF_ATTR)
+#undef JF_ATTR
 }
 
-void launch_jacobi_fused2d(int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
+void launch_jacobi_fused2d(int shape, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
                            const StagePtrs* table, const int2* work, int nwork, const Scratch* scr, int H, int F,
                            int theta_sel)
 {
-    pdl_launch(jacobi_fused2d_kernel, grid, NODE_TPB, jacobi_fused2d_smem(H, F), st, insts, single, table, work, nwork,
-               scr, H, F, theta_sel);
+    const size_t sm = jacobi_fused2d_smem(H, F, shape);
+#define JF_LAUNCH(S, TX, TY, TPB)                                                                                  \
+    if (shape == S)                                                                                                \
+        pdl_launch(jacobi_fused2d_kernel<TX, TY, TPB>, grid, TPB, sm, st, insts, single, table, work, nwork, scr, H, F, \
+                   theta_sel);
+    JF_KERNELS(JF_LAUNCH)
+#undef JF_LAUNCH
 }
 
 // Delta_tau = min(1, bounds of Sec. 4) per instance

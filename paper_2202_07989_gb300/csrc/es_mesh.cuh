@@ -109,11 +109,16 @@ void launch_monitor_theta(bool mixed, int grid, cudaStream_t st, const Inst* ins
 void launch_filter(bool mixed, bool from_g, int grid, cudaStream_t st, const Inst* insts, const int2* work, int nwork,
                    const Scratch* scr, int parity);
 // mixed form, 2D: the monitor, up to FILTER_FUSED_MAX filter passes and up to JACOBI_FUSED_MAX
-// sweeps in one launch (F < 0: Theta read from the buffer theta_sel)
+// sweeps in one launch (F < 0: Theta read from the buffer theta_sel), over node tiles of one of
+// the shapes JF_SHAPES (TX, TY, threads per block) and a work list of those tiles
 constexpr int JACOBI_FUSED_MAX = 8, FILTER_FUSED_MAX = 4;
+constexpr int NJF_SHAPE = 4;
+constexpr int JF_SHAPES[NJF_SHAPE][3] = { { 32, 8, 256 }, { 32, 16, 512 }, { 24, 16, 512 }, { 24, 12, 512 } };
+constexpr int JF_SHAPE_DEFAULT = 0;
 void prepare_mesh();    // kernel attributes, once per context
 void prepare_mesh3d();  // those of es_mesh3d.cu
-void launch_jacobi_fused2d(int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
+size_t jacobi_fused2d_smem(int H, int F, int shape);
+void launch_jacobi_fused2d(int shape, int grid, cudaStream_t st, const Inst* insts, const StagePtrs& single,
                            const StagePtrs* table, const int2* work, int nwork, const Scratch* scr, int H, int F,
                            int theta_sel);
 // mixed form, 3D: one filter pass marching along i3 over the column items of col3 (es_mesh3d.cu)

@@ -72,6 +72,8 @@ def lib():
             "es_set_tuning": (C.c_int, [vp, C.c_int, C.c_int, C.c_int]),
             "es_get_fusion": (C.c_int, [vp, ip, ip, ip, ip, C.POINTER(C.c_float)]),
             "es_set_fusion": (C.c_int, [vp, C.c_int, C.c_int]),
+            "es_get_mesh_tiles": (C.c_int, [vp, ip, ip, ip, ip, C.POINTER(C.c_float)]),
+            "es_set_mesh_tiles": (C.c_int, [vp, C.c_int]),
             "entropy_production": (C.c_int, [vp, dp, dp, dp, dp, dp, vp]),
             "es_bind_batch": (C.c_int, [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp)]),
             "es_step_batch": (C.c_int, [vp, vp]),
@@ -273,6 +275,17 @@ class Context:
     def es_set_fusion(self, shape: int, grid: int = 0):
         """Fused 2D stage launch in fused shape `shape` (0..4), or -1 for one launch per direction."""
         self._chk(self.L.es_set_fusion(self.h, int(shape), int(grid)), "es_set_fusion")
+
+    def es_get_mesh_tiles(self):
+        """(shape or -1, TX, TY, threads, best ms per launch) of the fused mixed 2D mesh-step launch."""
+        a = [C.c_int() for _ in range(4)]
+        ms = C.c_float()
+        self._chk(self.L.es_get_mesh_tiles(self.h, *[C.byref(v) for v in a], C.byref(ms)), "es_get_mesh_tiles")
+        return tuple(v.value for v in a) + (ms.value,)
+
+    def es_set_mesh_tiles(self, shape: int):
+        """Fused mixed 2D mesh-step launch in tile shape `shape` (0..3)."""
+        self._chk(self.L.es_set_mesh_tiles(self.h, int(shape)), "es_set_mesh_tiles")
 
     def es_schlieren(self, JU, J, x, psi1: float = 30.0, psi2: float = 150.0, phi=None):
         """Schlieren function of Eq. (schlieren) at the nodes."""

@@ -16,6 +16,7 @@ from .helpers import TOL_FP64, case, fieldwise, need_gpu, rel_max_err, to_dev
 pytestmark = pytest.mark.gpu
 
 NFSHAPE = 5
+NJF_SHAPE = 4
 
 
 def _ctx(pb, precision=0):
@@ -188,3 +189,66 @@ def test_run_host_equals_device_steps(form):
     prof = ctx.es_profile_read()
     ctx.es_profile(False)
     assert _same(got, ref) and prof["flux_k1"][1] == 9 and prof["mesh"][1] == 3
+
+
+@pytest.mark.parametrize("bc", ["periodic", "mixed", "reflect"])
+def test_mesh_tiles_bitwise(bc):
+    """The fused mixed 2D mesh step (monitor, filter passes and Jacobi sweeps in one launch) in
+    every tile shape gives the mesh velocity and Delta t / Delta tau of shape 0 bit for bit:
+    ragged and sub-tile grids, the largest fused halo (mu = 8, n_f = 4), and a batch of uneven
+    instances; es_autotune keeps one of the shapes and changes no result."""
+    torch = need_gpu()
+    from paper_2202_07989_gb300 import es
+    for n, mu, nf, seed in (((70, 37), 5, 3, 21), ((10, 11), 4, 2, 22), ((53, 41), 8, 4, 23)):
+        pb, JU, J, x, _ = case(2, 2, n, bc, es=True, seed=seed, jump=True)
+        pb = pb.with_(mu=mu, nf=nf, sigma=(W.SIG_RHO1, W.SIG_P), alpha=(60.0, 25.0))
+        ctx = _ctx(pb, 1)
+        ju, jj, xx = to_dev(JU, torch), to_dev(J, torch), to_dev(x, torch)
+        out = []
+        for sh in range(NJF_SHAPE):
+            ctx.es_set_mesh_tiles(sh)
+            assert ctx.es_get_mesh_tiles()[0] == sh
+            out.append(ctx.mesh_redistribute(ju, jj, xx))
+        assert ctx.es_poll_status() == 0
+        for o in out[1:]:
+            assert _same(o, out[0]), (n, bc)
+        ctx.es_autotune(ju, jj, xx, None, reps=2)
+        assert 0 <= ctx.es_get_mesh_tiles()[0] < NJF_SHAPE and ctx.es_get_mesh_tiles()[4] > 0
+        assert _same(ctx.mesh_redistribute(ju, jj, xx), out[0])
+    # a batch of uneven instances, every shape against shape 0
+    insts = []
+    for n, seed in (((40, 23), 31), ((17, 52), 32), ((64, 12), 33)):
+        pb, JU, J, x, _ = case(2, 2, n, bc, es=True, seed=seed, jump=True)
+        insts.append((pb.with_(mu=5, nf=3, sigma=(W.SIG_RHO1, W.SIG_P), alpha=(60.0, 25.0)), JU, J, x))
+    res = []
+    for sh in range(NJF_SHAPE):
+        b = es.Context([i[0] for i in insts], 1)
+        b.es_set_mesh_tiles(sh)
+        JUs = [to_dev(i[1], torch) for i in insts]
+        Js = [to_dev(i[2], torch) for i in insts]
+        Xs = [to_dev(i[3], torch) for i in insts]
+        XD = [torch.zeros_like(t) for t in Xs]
+        DD = [torch.zeros(2, dtype=torch.float64, device="cuda") for _ in insts]
+        b.es_bind_batch(JUs, Js, Xs, XD, DD)
+        b.es_step_batch()
+        assert b.es_poll_status() == 0
+        res.append(JUs + Js + Xs + XD + DD)
+    for r in res[1:]:
+        assert _same(r, res[0]), bc
+
+
+def test_mesh_tiles_refused():
+    """es_set_mesh_tiles refuses shapes out of range and contexts without the fused mixed 2D
+    mesh step; es_get_mesh_tiles reports -1 there."""
+    need_gpu()
+    from paper_2202_07989_gb300 import es
+    pb, *_ = case(2, 1, (20, 20), "periodic")
+    pb = pb.with_(mu=5, nf=3)
+    ctx = _ctx(pb, 1)
+    for sh in (-1, NJF_SHAPE):
+        with pytest.raises(RuntimeError):
+            ctx.es_set_mesh_tiles(sh)
+    f = _ctx(pb, 0)
+    assert f.es_get_mesh_tiles()[0] == -1
+    with pytest.raises(RuntimeError):
+        f.es_set_mesh_tiles(0)
