@@ -39,7 +39,7 @@ struct es_ctx {
     int* d_first_cell = nullptr;
     double* partial = nullptr;
     int* status = nullptr;
-    int* mflag = nullptr;     // 3D: reuse test of the spatial metrics ([2] = reuse, see metrics_reuse_kernel)
+    int* mflag = nullptr;     // 3D: reuse test of the metrics (5 words, see metrics_reuse_kernel)
     // stage buffers (per instance): (JU | J | x) for the two intermediate stages
     std::vector<double*> stA, stB;
     // batched tables
@@ -399,13 +399,13 @@ void launch_metrics(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStr
             pdl_launch(metrics_reuse_kernel, node_grid(c, c->n_cell), NODE_TPB, 0, st, c->dI, P, tab, c->w_cell, c->n_cell,
                        c->dS, c->mflag);
         pdl_launch(xe_fill_kernel, node_grid(c, c->n_ext), NODE_TPB, 0, st, c->dI, P, tab, c->w_ext, c->n_ext, c->dS,
-                   reset ? c->n_inst : 0);
+                   reset ? c->n_inst : 0, ru);
         pdl_launch(dx3d_kernel, node_grid(c, c->n_pad), NODE_TPB, 0, st, c->dI, P, tab, c->w_pad, c->n_pad, c->dS, ru);
         pdl_launch(metrics3d_kernel, node_grid(c, c->n_cell), NODE_TPB, 0, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS,
-                   ru, vcl ? 1 : 0);
-        // kept metrics without VCL rows (the velocity pass writes them) keep their ghost layers too
+                   c->mflag, reuse ? 1 : 0, vcl ? 1 : 0);
+        // kept metrics keep their ghost layers unless the VCL rows are formed again
         pdl_launch(metrics3d_ghost_kernel, node_grid(c, c->n_pad), NODE_TPB, 0, st, c->dI, P, tab, c->w_pad, c->n_pad,
-                   vcl ? nullptr : ru);
+                   c->mflag, reuse ? 1 : 0, vcl ? 1 : 0);
     }
 }
 
@@ -684,7 +684,7 @@ es_status es_create_batch(const es_config* cfgs, int n_inst, es_ctx** out)
     }
     ok = ok && dalloc(c, (void**)&c->dS, sizeof(Scratch) * n_inst);
     ok = ok && dalloc(c, (void**)&c->status, sizeof(int));
-    ok = ok && dalloc(c, (void**)&c->mflag, sizeof(int) * 3);
+    ok = ok && dalloc(c, (void**)&c->mflag, sizeof(int) * 5);
     if (!ok) {
         es_destroy(c);
         fprintf(stderr, "es_create: device allocation failed\n");
@@ -693,7 +693,7 @@ es_status es_create_batch(const es_config* cfgs, int n_inst, es_ctx** out)
     cudaMemcpy(c->dI, c->hI.data(), sizeof(Inst) * n_inst, cudaMemcpyHostToDevice);
     cudaMemcpy(c->dS, c->hS.data(), sizeof(Scratch) * n_inst, cudaMemcpyHostToDevice);
     cudaMemset(c->status, 0, sizeof(int));
-    cudaMemset(c->mflag, 0, sizeof(int) * 3);
+    cudaMemset(c->mflag, 0, sizeof(int) * 5);
     c->w_pad = build_work(c, [](const Inst& I) { return (long long)node_tiles(I, 3); }, c->n_pad);
     c->w_cell = build_work(c, [](const Inst& I) { return (long long)node_tiles(I, 0); }, c->n_cell);
     if (c->d == 3) c->w_ext = build_work(c, [](const Inst& I) { return (long long)node_tiles(I, 6); }, c->n_ext);

@@ -130,19 +130,23 @@ void launch_metrics2d(bool dot, int grid, cudaStream_t st, const Inst* insts, co
 // when every instance's mesh equals, bit for bit, the positions its metrics buffer M was formed
 // from (Xm) and the pass writes M.  After an SSP-RK3 step the new mesh x^n + dt xdot is exactly
 // the second stage's mesh, whose metrics the second stage left in M; a fixed mesh never changes.
-// flag[0] collects mismatches, flag[1] counts finished blocks; the last block stores the
-// verdict in flag[2] and clears the other two for the next test.
+// The context's flag words: [0] collects mismatches (bit 0) and passes with a nonzero mesh
+// velocity (bit 1), [1] counts finished blocks, [2] the verdict (spatial rows kept), [3] set by
+// metrics3d_kernel: the VCL rows in M were formed with a zero mesh velocity, [4] the verdict that
+// the VCL rows are kept too (kept spatial rows, a zero velocity now and then).  The last block
+// stores [2] and [4] and clears [0] and [1] for the next test.
 __global__ void metrics_reuse_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
                                      const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr, int* flag)
 {
     pdl_entry();
-    int bad = 0;
+    int bad = 0, moving = 0;
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
         const int2 it = work[wi];
         const Inst& I = insts[it.x];
         ES_PTRS(S);
         const Scratch& Sc = scr[it.x];
         if (S.M != Sc.M || !Sc.Xm) bad = 1;
+        if (S.xdot && S.xdot != Sc.zeros) moving = 1;
         int i0, i1, i2;
         if (bad || !tile_node(I, it.y, 0, i0, i1, i2)) continue;
         const long long c = lin(I, i0, i1, i2);
@@ -151,11 +155,14 @@ __global__ void metrics_reuse_kernel(const Inst* __restrict__ insts, StagePtrs s
             if (!(S.x[q * I.ncell + c] == Sc.Xm[q * I.ncell + c])) bad = 1;
     }
     bad = __syncthreads_or(bad);
+    moving = __syncthreads_or(moving);
     if (threadIdx.x == 0) {
-        if (bad) atomicOr(&flag[0], 1);
+        if (bad || moving) atomicOr(&flag[0], (bad ? 1 : 0) | (moving ? 2 : 0));
         __threadfence();
         if (atomicAdd(&flag[1], 1) == (int)gridDim.x - 1) {
-            flag[2] = atomicOr(&flag[0], 0) == 0 ? 1 : 0;
+            const int v = atomicOr(&flag[0], 0);
+            flag[2] = (v & 1) == 0 ? 1 : 0;
+            flag[4] = (v == 0 && flag[3] == 1) ? 1 : 0;
             flag[0] = 0;
             flag[1] = 0;
             __threadfence();
@@ -168,13 +175,17 @@ __global__ void metrics_reuse_kernel(const Inst* __restrict__ insts, StagePtrs s
 // read positions without branches.  When the pass writes the context's metrics buffer M, the
 // interior positions also go to Xm (the positions M's spatial rows are formed from).
 __global__ void xe_fill_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
-                               const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr, int reset_n)
+                               const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr, int reset_n,
+                               const int* reuse)
 {
     pdl_entry();
     reset_reductions(reset_n > 0 ? scr : nullptr, reset_n);
+    // kept metrics of a fixed mesh: nothing reads these positions (no sweeps, no new metrics)
+    const bool keep = reuse && *reuse;
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
         const int2 it = work[wi];
         const Inst& I = insts[it.x];
+        if (keep && I.fixed) continue;
         ES_PTRS(S);
         int i0, i1, i2;
         if (!tile_node(I, it.y, 6, i0, i1, i2)) continue;
@@ -253,12 +264,18 @@ __global__ void dx3d_kernel(const Inst* __restrict__ insts, StagePtrs single, co
 // exactly one k, with sign +1 when (a, b) is k's pair and -1 when reversed; the kernel walks
 // the outer direction a and offset m once and adds each product term to its k.
 __global__ void metrics3d_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
-                                 const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr,
-                                 const int* reuse, int vcl)
+                                 const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr, int* flag,
+                                 int consult, int vcl)
 {
     pdl_entry();
-    const bool keep = reuse && *reuse;    // spatial rows of M already formed: the VCL rows only
-    if (keep && !vcl) return;             // ... and those are written by the velocity pass
+    const bool keep = consult && flag[2];   // spatial rows of M already formed: the VCL rows only,
+    if (keep && (!vcl || flag[4])) return;  // unless the velocity pass writes them or they are kept
+    if (blockIdx.x == 0 && threadIdx.x == 0 && nwork > 0) {
+        // whether the VCL rows this pass forms in the context's M come from a zero mesh velocity
+        const int2 it = work[0];
+        ES_PTRS(S);
+        if (S.M == scr[it.x].M) flag[3] = (!S.xdot || S.xdot == scr[it.x].zeros) ? 1 : 0;
+    }
     // the ordered pair (a, b) belongs to metric row k = 3 - a - b, with sign +1 when b follows a
     // cyclically by two, -1 by one (compile-time constants once the loops unroll)
     const int AB[3][2] = { { 2, 1 }, { 0, 2 }, { 1, 0 } };
@@ -335,10 +352,10 @@ __global__ void metrics3d_kernel(const Inst* __restrict__ insts, StagePtrs singl
 // product of the flips.  The values equal the nested operators evaluated at the ghost node from
 // the mapped positions, up to the rounding of the shifted or mirrored coordinates.
 __global__ void metrics3d_ghost_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
-                                       const int2* __restrict__ work, int nwork, const int* skip)
+                                       const int2* __restrict__ work, int nwork, const int* flag, int consult, int vcl)
 {
     pdl_entry();
-    if (skip && *skip) return;            // ghost metrics kept with the interior ones
+    if (consult && flag[2] && (!vcl || flag[4])) return;    // ghost metrics kept with the interior ones
     for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
         int2 it = work[wi];
         const Inst& I = insts[it.x];
