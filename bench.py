@@ -739,7 +739,7 @@ def main_ours(args):
     flux_n = sum(prof_m[k][1] for k in FLUX)
     hand_iface = flux_flops_per_interface(pb.d, pb.N, pb.es)
     oracle_iface, oracle_classes = oracle_flops_per_interface(pb.d, pb.N)
-    # the algorithmic flops per interface: the oracle's counted work; the hand count
+    # the algorithmic flops per interface: the oracle's counted work (operation-counting build); the hand count
     # of the kernel's contracted arithmetic is reported beside it
     per_iface = oracle_iface if oracle_iface else hand_iface
     # interfaces of one stage: (n_k + 1) per grid line of each direction
@@ -939,6 +939,9 @@ def main_kernel_case(args):
         for k, sh in enumerate(int(v) for v in args.kernel_shapes.split(",")):
             r.ctx.es_set_tuning(k, sh, 0)
         tiles = r.ctx.es_get_tuning()
+    if args.kernel_mesh_tiles is not None:
+        r.ctx.es_set_mesh_tiles(args.kernel_mesh_tiles)
+        tiles = [tiles, r.ctx.es_get_mesh_tiles()]
     if args.kernel_fusion is not None or (args.kernel_shapes and pb.d == 2):
         # fixed per-direction shapes in 2D mean the per-direction launches unless a fused shape is given
         r.ctx.es_set_fusion(args.kernel_fusion if args.kernel_fusion is not None else -1)
@@ -973,6 +976,8 @@ def main():
     ap.add_argument("--kernel-steps", type=int, default=2)
     ap.add_argument("--kernel-time", type=int, default=0, help="also time this many eager steps per kernel class")
     ap.add_argument("--kernel-tune", action="store_true", help="run the flux autotuner before the steps")
+    ap.add_argument("--kernel-mesh-tiles", type=int, default=None,
+                    help="tile shape 0..3 of the fused mixed 2D mesh-step launch (es_set_mesh_tiles)")
     ap.add_argument("--kernel-shapes", default=None, help="fix the flux tile shape per direction, e.g. 2,1")
     ap.add_argument("--kernel-fusion", type=int, default=None, help="2D: fix the fused stage shape (0..4, -1 off)")
     args = ap.parse_args()

@@ -131,8 +131,8 @@ void launch_metrics2d(bool dot, int grid, cudaStream_t st, const Inst* insts, co
 // from (Xm) and the pass writes M.  After an SSP-RK3 step the new mesh x^n + dt xdot is exactly
 // the second stage's mesh, whose metrics the second stage left in M; a fixed mesh never changes.
 // The context's flag words: [0] collects mismatches (bit 0) and passes with a nonzero mesh
-// velocity (bit 1), [1] counts finished blocks, [2] the verdict (spatial rows kept), [3] set by
-// metrics3d_kernel: the VCL rows in M were formed with a zero mesh velocity, [4] the verdict that
+// velocity (bit 1), [1] counts finished blocks, [2] the outcome (spatial rows kept), [3] set by
+// metrics3d_kernel: the VCL rows in M were formed with a zero mesh velocity, [4] the outcome that
 // the VCL rows are kept too (kept spatial rows, a zero velocity now and then).  The last block
 // stores [2] and [4] and clears [0] and [1] for the next test.
 __global__ void metrics_reuse_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
