@@ -74,3 +74,29 @@ def test_changed_mesh_is_not_reused(n, bc, seed, N, form):
     assert f.es_poll_status() == 0
     for a, b in zip((ju, jj, xx), ref):
         assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("fixed", [False, True])
+def test_run_host_reuses_across_calls(fixed):
+    """es_run_host replays one CUDA graph of a step; the reuse test runs on the device inside it.
+    Five steps as 3 + 2 steps of es_run_host on host buffers (the second call copies in the state
+    the first left, whose metrics the context still holds) equal five es_step calls on device
+    buffers in a fresh context, bit for bit."""
+    torch = need_gpu()
+    from paper_2202_07989_gb300 import es
+    pb, JU0, J0, x0 = _problem((20, 14, 12), "mixed", 5, 2, fixed)
+    c = es.Context(pb, 1)
+    H = [torch.from_numpy(a.copy()).pin_memory() for a in (JU0, J0, x0)]
+    t = c.es_run_host(*H, 3)
+    t += c.es_run_host(*H, 2)
+    assert c.es_poll_status() == 0
+    d = es.Context(pb, 1)
+    D = [to_dev(a, torch) for a in (JU0, J0, x0)]
+    td = 0.0
+    for _ in range(5):
+        _, dd = d.es_step(*D)
+        td += float(dd[0])
+    assert d.es_poll_status() == 0
+    for a, b in zip(H, D):
+        assert torch.equal(a, b.cpu())
+    assert t == pytest.approx(td, rel=1e-14)
