@@ -246,8 +246,7 @@ es_status entropy_production(es_ctx* ctx, const double* JU, const double* J, con
 /* Allocation-free entropy diagnostics: the same two sums as entropy_production
  * for one instance described by cfg, without a context.  The paper has no
  * counterpart; this call exists for callers that may not allocate device
- * memory -- code running while a CUDA graph is captured (cudaMalloc cannot be
- * captured), runtimes that hand out all device memory from their own pool, and
+ * memory -- runtimes that hand out all device memory from their own pool, and
  * real-time loops where an allocation may synchronise the device.  It calls no
  * cudaMalloc, cudaFree or allocating library routine; the caller passes the
  * inputs and the output (out2: DEVICE, 2 doubles).
@@ -255,10 +254,10 @@ es_status entropy_production(es_ctx* ctx, const double* JU, const double* J, con
  * (4096 tiles of 256 nodes), which every GPU that loads the library holds
  * until the process exits; grids over 4096 * 256 = 1,048,576 nodes are
  * rejected with ES_ERR_ARG and a message on stderr.  The first call on a
- * device looks up the array's device address for that device (make that
- * first call outside any stream capture).  All calls share the array: every
- * slot a call reads is written by the same call first, but calls that overlap
- * on the GPU (concurrent streams, several host threads) race on it. */
+ * device looks up the array's device address for that device.  All calls
+ * share the array: every slot a call reads is written by the same call first,
+ * but calls that overlap on the GPU (concurrent streams, several host threads)
+ * race on it. */
 es_status es_entropy_production_noalloc(const es_config* cfg, const double* JU, const double* J,
                                         const double* dJU, const double* dJ, double* out2, void* stream);
 

@@ -1311,9 +1311,8 @@ es_status es_poll_status(es_ctx* c, int* flags, void* stream)
 // ---------------------------------------------------------------------------
 // Allocation-free entropy diagnostics (es_entropy_production_noalloc).
 //
-// For callers that may not allocate device memory: code that runs while a CUDA
-// graph is being captured (cudaMalloc is not capturable), runtimes that hand out
-// every byte of device memory from their own pool, and real-time loops where an
+// For callers that may not allocate device memory: runtimes that hand out every
+// byte of device memory from their own pool, and real-time loops where an
 // allocation may synchronise the device.  The per-tile partial sums that
 // entropy_production keeps in context scratch live here in one file-scope device
 // array of fixed size instead; no context is created.

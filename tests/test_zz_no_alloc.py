@@ -1,11 +1,11 @@
 """The allocation-free entropy diagnostics call, es_entropy_production_noalloc.
 
-Some callers may not allocate device memory (a CUDA graph being captured, a runtime
-that owns every byte of device memory, a real-time loop).  For them the library offers
-one call that keeps its scratch in a fixed library-wide device array instead of a
-context.  This test calls it through the C ABI twice in a row, on different inputs,
+Some callers may not allocate device memory (a runtime that owns every byte of device
+memory, a real-time loop).  For them the library offers one call that keeps its scratch
+in a fixed library-wide device array instead of a context.  This test calls it through the C ABI twice in a row, on different inputs,
 and checks each result against entropy_production of a context, within the tolerance
-of the other parity tests; it also checks that grids over the limit are refused.
+of the other parity tests; it also checks that grids over the limit are refused and that a
+call leaves the device's free memory unchanged.
 It lives in a file that pytest collects last.
 """
 import ctypes as C
@@ -46,6 +46,22 @@ def test_noalloc_matches_context_call_twice():
         got = out.cpu().numpy()
         assert abs(got[0] - ref[0]) <= TOL * scale, (got, ref)
         assert abs(got[1] - ref[1]) <= TOL * abs(ref[1]), (got, ref)
+
+
+def test_noalloc_leaves_free_device_memory_unchanged():
+    torch = need_gpu()
+    from paper_2202_07989_gb300 import es
+    pb, JU, J, dJU, dJ, ref, scale = _ref_and_inputs(torch, 2, 2, (70, 37), 33)
+    out = torch.empty(2, dtype=torch.float64, device="cuda")
+    assert es.es_entropy_production_noalloc(pb, JU, J, dJU, dJ, out) == 0   # loads the kernels
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        assert es.es_entropy_production_noalloc(pb, JU, J, dJU, dJ, out) == 0
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    got = out.cpu().numpy()
+    assert abs(got[0] - ref[0]) <= TOL * scale and abs(got[1] - ref[1]) <= TOL * abs(ref[1])
 
 
 def test_noalloc_rejects_grids_over_the_limit():
