@@ -276,12 +276,15 @@ es_status es_step_batch(es_ctx* ctx, void* stream);
  * runs `steps` times mesh_redistribute (CFL Delta t, or dt_fixed > 0) + an
  * SSP-RK3 step, copies (JU, J, x) back and adds the elapsed time to *t.
  * Synchronous.  Uses device buffers owned by the context, allocated by the
- * first call (with one pinned host word for the elapsed time); one
- * cudaMemcpyAsync per buffer and direction (asynchronous when the host buffers
- * are pinned).  Each step replays a CUDA graph of es_step on those buffers,
- * captured on a private stream by the first call and again after es_autotune,
- * es_set_tuning, es_set_fusion, es_set_mesh_tiles or a new dt_fixed; with es_profile on, the steps
- * are launched one kernel at a time instead.  ES_ERR_ARG during stream capture. */
+ * first call (JU, J and x consecutive in one block, with one pinned host word
+ * for the elapsed time).  Copies: one cudaMemcpyAsync each way when the host
+ * buffers are consecutive in one allocation (J = JU + n_c * cells,
+ * x = J + cells), else one per buffer and direction (asynchronous when the host
+ * memory is pinned).  Each step replays a CUDA graph of es_step on the device
+ * buffers, captured on a private stream by the first call and again after
+ * es_autotune, es_set_tuning, es_set_fusion, es_set_mesh_tiles or a new
+ * dt_fixed; with es_profile on, the steps are launched one kernel at a time
+ * instead.  ES_ERR_ARG during stream capture. */
 es_status es_run_host(es_ctx* ctx, double* JU, double* J, double* x, int steps, double dt_fixed, double* t,
                       void* stream);
 

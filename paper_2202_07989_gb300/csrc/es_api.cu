@@ -588,12 +588,20 @@ void launch_step(es_ctx* c, const StagePtrs& mesh, const StagePtrs* tab_mesh, co
 
 __global__ void time_acc_kernel(double* t, const double* dt_dtau) { *t += dt_dtau[0]; }
 
-// copies of (JU, J, x) between the caller's host buffers and the context's device buffers
-// (one SM-driven copy kernel over mapped pinned memory measured no faster than these)
+// copies of (JU, J, x) between the caller's host buffers and the context's device buffers,
+// which are consecutive in one allocation: one transfer each way when the host buffers are
+// consecutive too, else one per buffer (one SM-driven copy kernel over mapped pinned memory
+// measured no faster than these)
 void copy_state(es_ctx* c, double* JU, double* J, double* x, bool to_device, cudaStream_t st)
 {
     const Inst& I = c->hI[0];
     const long long n = I.ncell;
+    if (J == JU + I.nc * n && x == J + n) {
+        const size_t bytes = sizeof(double) * (I.nc + 1 + I.d) * n;
+        cudaMemcpyAsync(to_device ? c->hJU : JU, to_device ? JU : c->hJU, bytes,
+                        to_device ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost, st);
+        return;
+    }
     double* host[3] = { JU, J, x };
     double* dev[3] = { c->hJU, c->hJ, c->hx };
     const long long cnt[3] = { I.nc * n, n, I.d * n };
@@ -961,11 +969,14 @@ es_status es_run_host(es_ctx* c, double* JU, double* J, double* x, int steps, do
     const Inst& I = c->hI[0];
     long long n = I.ncell;
     if (!c->hJU) {
-        bool ok = dalloc(c, (void**)&c->hJU, sizeof(double) * I.nc * n) && dalloc(c, (void**)&c->hJ, sizeof(double) * n) &&
-                  dalloc(c, (void**)&c->hx, sizeof(double) * I.d * n) && dalloc(c, (void**)&c->hxd, sizeof(double) * I.d * n) &&
+        // JU, J and x consecutive in one block (see copy_state)
+        bool ok = dalloc(c, (void**)&c->hJU, sizeof(double) * (I.nc + 1 + I.d) * n) &&
+                  dalloc(c, (void**)&c->hxd, sizeof(double) * I.d * n) &&
                   dalloc(c, (void**)&c->hdt, sizeof(double) * 2) && dalloc(c, (void**)&c->htacc, sizeof(double)) &&
                   cudaMallocHost((void**)&c->tacc_pinned, sizeof(double)) == cudaSuccess;
         if (!ok) return fail(c, ES_ERR_CUDA, "es_run_host: allocation failed");
+        c->hJ = c->hJU + I.nc * n;
+        c->hx = c->hJ + n;
     }
     cudaStream_t st = (cudaStream_t)stream;
     if (capturing(st)) return fail(c, ES_ERR_ARG, "es_run_host: not allowed during stream capture");

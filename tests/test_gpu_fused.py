@@ -151,8 +151,9 @@ def test_fused_autotune_and_errors():
 def test_run_host_equals_device_steps(form):
     """es_run_host (host buffers; one captured CUDA graph of a step replayed per step) leaves
     the same state, bit for bit, as es_step on device buffers and reports the summed Delta t:
-    with the default launch configuration, after a tuning change (the graph is rebuilt), with
-    a fixed Delta t, and with es_profile on (launches one at a time, each timed)."""
+    with the default launch configuration, with the state in one host block (one transfer each
+    way), after a tuning change (the graph is rebuilt), with a fixed Delta t, and with
+    es_profile on (launches one at a time, each timed)."""
     torch = need_gpu()
     pb, U, x = W.shock_bubble_2d(96, 64)
     J = Oracle(pb).init_J(x)
@@ -177,6 +178,12 @@ def test_run_host_equals_device_steps(form):
     assert _same(got, ref) and tgot == tref
     got, tgot = host_run(ctx, 3)                     # the graph replayed again
     assert _same(got, ref) and tgot == tref
+    # the state in one pinned block (JU, J, x consecutive): one transfer each way
+    sizes = [t.size for t in host0]
+    blk = torch.from_numpy(np.concatenate([t.reshape(-1) for t in host0])).pin_memory()
+    H = list(torch.split(blk, sizes))
+    tblk = ctx.es_run_host(*H, 3)
+    assert _same([h.reshape(t.shape) for h, t in zip(H, ref)], ref) and tblk == tref
     ctx.es_set_fusion(-1)                            # per-direction launches: graph rebuilt
     got, _ = host_run(ctx, 3)
     assert _same(got, ref)
