@@ -592,7 +592,9 @@ def main_ours(args):
     clk = clocks.stop()
     t_main = max_over_ranks(t_main, "cuda")
     value = pb.ncell * 3 * args.steps * world / t_main
-    forms["mixed"] = {"value": pb.ncell * 3 * args.steps / t_main, "ms_per_step": 1e3 * t_main / args.steps}
+    # the status word after every timed run: 0 = no non-physical state met by any kernel
+    forms["mixed"] = {"value": pb.ncell * 3 * args.steps / t_main, "ms_per_step": 1e3 * t_main / args.steps,
+                      "status": main.ctx.es_poll_status(), "steps_run": args.warmup + args.steps + n_sus}
     forms["mixed_sustained"] = {"value": pb.ncell * 3 * n_sus / t_sus, "ms_per_step": 1e3 * t_sus / n_sus,
                                 "steps": n_sus, "seconds": t_sus,
                                 "what": "the headline step repeated for at least %.1f s of device time right after "
@@ -602,7 +604,7 @@ def main_ours(args):
     r64 = runners["fp64"]
     k64 = max(3, min(args.steps, 10))
     t64 = time_steps(r64, k64, 2, torch, flush)
-    forms["fp64"] = {"value": pb.ncell * 3 * k64 / t64, "ms_per_step": 1e3 * t64 / k64}
+    forms["fp64"] = {"value": pb.ncell * 3 * k64 / t64, "ms_per_step": 1e3 * t64 / k64, "status": r64.ctx.es_poll_status()}
 
     # residual + stage updates only (the first way the metric is quoted), mixed form
     rk = RkOnly(pb, U, x, es.MIXED, torch)
@@ -614,6 +616,7 @@ def main_ours(args):
     krk = max(3, min(args.steps, 200))
     trk = time_steps(rk, krk, 3, torch, flush)
     forms["mixed_rk_only"] = {"value": pb.ncell * 3 * krk / trk, "ms_per_step": 1e3 * trk / krk,
+                              "status": rk.ctx.es_poll_status(),
                               "what": "residual + SSP-RK3 stage updates only, no mesh redistribution"}
     del rk
 
@@ -628,7 +631,7 @@ def main_ours(args):
     kum = max(3, min(args.steps, 200))
     tum = time_steps(um, kum, 3, torch, flush)
     forms["uniform_mesh_mixed"] = {"value": pb.ncell * 3 * kum / tum, "ms_per_step": 1e3 * tum / kum,
-                                   "mm_over_um_cost": (t_main / args.steps) / (tum / kum),
+                                   "mm_over_um_cost": (t_main / args.steps) / (tum / kum), "status": um.ctx.es_poll_status(),
                                    "what": "fixed uniform mesh: CFL step + SSP-RK3, metrics once per step"}
     del um
 
@@ -644,6 +647,7 @@ def main_ours(args):
     tjs = time_steps(js, kjs, 3, torch, flush)
     forms["mm_wenojs_mixed"] = {"value": pb.ncell * 3 * kjs / tjs, "ms_per_step": 1e3 * tjs / kjs,
                                 "wenomr_over_wenojs_cost": (t_main / args.steps) / (tjs / kjs),
+                                "status": js.ctx.es_poll_status(),
                                 "what": "moving-mesh step with the WENO-JS dissipation"}
     del js
 
@@ -672,6 +676,7 @@ def main_ours(args):
         tb = max_over_ranks(time_steps(bt, kb, 2, torch, flush), "cuda")
         batched = {"value": total_cells * 3 * kb / tb, "ms_per_step": 1e3 * tb / kb, "instances": len(insts),
                    "cells": total_cells, "instances_this_rank": len(mine), "cells_this_rank": bt.cells,
+                   "status": bt.ctx.es_poll_status(),
                    "scaling": "strong",
                    "split": "the 64 instances split across %d rank(s) by cells (largest first to the least "
                             "loaded rank); time = slowest rank" % world}
@@ -690,7 +695,8 @@ def main_ours(args):
             r3.reset()
             k3 = max(3, min(args.steps, 8))
             t3 = time_steps(r3, k3, 2, torch, flush)
-            forms[name] = {"value": p3.ncell * 3 * k3 / t3, "ms_per_step": 1e3 * t3 / k3, "cells": p3.ncell}
+            forms[name] = {"value": p3.ncell * 3 * k3 / t3, "ms_per_step": 1e3 * t3 / k3, "cells": p3.ncell,
+                           "status": r3.ctx.es_poll_status()}
             del r3
         # the two-component stiffened 3D case (Example 5.11, p_inf = 100 around an ideal-gas
         # bubble, Mach 10), uniform-mesh form at the paper's finest grid, 800 x 160 x 160, with the
