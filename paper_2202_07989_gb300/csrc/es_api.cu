@@ -26,6 +26,7 @@ struct es_ctx {
     // work lists (inst, tile)
     int2* w_pad = nullptr;  int n_pad = 0;
     int2* w_ext = nullptr;  int n_ext = 0;
+    int2* w_xe = nullptr;   int n_xe = 0;      // 3D FP64 form: nodes within 9 ghost layers
     int2* w_cell = nullptr; int n_cell = 0;
     int2* w_col = nullptr;  int n_col = 0;     // 3D: column chunks of the kernels marching along i3
     int2* w_flux[3][NSHAPE] = {};          // flux work list per direction and tile shape
@@ -392,20 +393,32 @@ void launch_metrics(es_ctx* c, const StagePtrs& P, const StagePtrs* tab, cudaStr
         launch_metrics2d(dot, node_grid(c, c->n_pad), st, c->dI, P, tab, c->w_pad, c->n_pad, reset ? c->dS : nullptr,
                          c->n_inst, vcl);
     } else {
-        // positions within 6 ghost layers, products within 3, metrics at the interior nodes, then
-        // the metrics of the 3 ghost layers from those of the nodes they map to
+        // mixed form: positions within 6 ghost layers, products within 3, the nested operators at
+        // the interior nodes, then the metrics of the 3 ghost layers from those of the nodes they
+        // map to.  FP64 form: the nested operators at every node of the padded buffer as well
+        // (positions within 9 ghost layers, products within 6), the oracle's evaluation order
+        // at the ghost nodes too.
         const int* ru = reuse ? c->mflag + 2 : nullptr;
+        const bool sym = c->mixed;
         if (reuse)
             pdl_launch(metrics_reuse_kernel, node_grid(c, c->n_cell), NODE_TPB, 0, st, c->dI, P, tab, c->w_cell, c->n_cell,
                        c->dS, c->mflag);
-        pdl_launch(xe_fill_kernel, node_grid(c, c->n_ext), NODE_TPB, 0, st, c->dI, P, tab, c->w_ext, c->n_ext, c->dS,
-                   reset ? c->n_inst : 0, ru);
-        pdl_launch(dx3d_kernel, node_grid(c, c->n_pad), NODE_TPB, 0, st, c->dI, P, tab, c->w_pad, c->n_pad, c->dS, ru);
-        pdl_launch(metrics3d_kernel, node_grid(c, c->n_cell), NODE_TPB, 0, st, c->dI, P, tab, c->w_cell, c->n_cell, c->dS,
-                   c->mflag, reuse ? 1 : 0, vcl ? 1 : 0);
-        // kept metrics keep their ghost layers unless the VCL rows are formed again
-        pdl_launch(metrics3d_ghost_kernel, node_grid(c, c->n_pad), NODE_TPB, 0, st, c->dI, P, tab, c->w_pad, c->n_pad,
-                   c->mflag, reuse ? 1 : 0, vcl ? 1 : 0);
+        if (sym) {
+            pdl_launch(xe_fill_kernel, node_grid(c, c->n_ext), NODE_TPB, 0, st, c->dI, P, tab, c->w_ext, c->n_ext, c->dS,
+                       reset ? c->n_inst : 0, ru, 6);
+            pdl_launch(dx3d_kernel, node_grid(c, c->n_pad), NODE_TPB, 0, st, c->dI, P, tab, c->w_pad, c->n_pad, c->dS, ru, 3);
+            pdl_launch(metrics3d_kernel, node_grid(c, c->n_cell), NODE_TPB, 0, st, c->dI, P, tab, c->w_cell, c->n_cell,
+                       c->dS, c->mflag, reuse ? 1 : 0, vcl ? 1 : 0, 0);
+            // kept metrics keep their ghost layers unless the VCL rows are formed again
+            pdl_launch(metrics3d_ghost_kernel, node_grid(c, c->n_pad), NODE_TPB, 0, st, c->dI, P, tab, c->w_pad, c->n_pad,
+                       c->mflag, reuse ? 1 : 0, vcl ? 1 : 0);
+        } else {
+            pdl_launch(xe_fill_kernel, node_grid(c, c->n_xe), NODE_TPB, 0, st, c->dI, P, tab, c->w_xe, c->n_xe, c->dS,
+                       reset ? c->n_inst : 0, ru, 9);
+            pdl_launch(dx3d_kernel, node_grid(c, c->n_ext), NODE_TPB, 0, st, c->dI, P, tab, c->w_ext, c->n_ext, c->dS, ru, 6);
+            pdl_launch(metrics3d_kernel, node_grid(c, c->n_pad), NODE_TPB, 0, st, c->dI, P, tab, c->w_pad, c->n_pad,
+                       c->dS, c->mflag, reuse ? 1 : 0, vcl ? 1 : 0, 3);
+        }
     }
 }
 
@@ -706,6 +719,7 @@ es_status es_create_batch(const es_config* cfgs, int n_inst, es_ctx** out)
     c->w_cell = build_work(c, [](const Inst& I) { return (long long)node_tiles(I, 0); }, c->n_cell);
     if (c->d == 3) c->w_ext = build_work(c, [](const Inst& I) { return (long long)node_tiles(I, 6); }, c->n_ext);
     if (c->d == 3) c->w_col = build_work(c, [](const Inst& I) { return (long long)col3_items(I); }, c->n_col);
+    if (c->d == 3 && !c->mixed) c->w_xe = build_work(c, [](const Inst& I) { return (long long)node_tiles(I, 9); }, c->n_xe);
     for (int k = 0; k < c->d; ++k)
         for (int sh = 0; sh < NSHAPE; ++sh) {
             c->w_flux[k][sh] = build_work(c, [k, sh](const Inst& I) { return flux_tiles(I, k, sh); }, c->n_flux[k][sh]);
@@ -742,7 +756,7 @@ es_status es_create_batch(const es_config* cfgs, int n_inst, es_ctx** out)
         c->fused_grid = c->sms * flux2d_occ(c, 0);
     }
     cudaError_t e = cudaDeviceSynchronize();
-    if (!ok || e != cudaSuccess || !c->w_pad || !c->w_cell || (c->d == 3 && (!c->w_ext || !c->w_col))) {
+    if (!ok || e != cudaSuccess || !c->w_pad || !c->w_cell || (c->d == 3 && (!c->w_ext || !c->w_col || (!c->mixed && !c->w_xe)))) {
         fprintf(stderr, "es_create: setup failed: %s\n", cudaGetErrorString(e));
         es_destroy(c);
         return ES_ERR_CUDA;

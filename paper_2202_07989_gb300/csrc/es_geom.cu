@@ -170,13 +170,14 @@ __global__ void metrics_reuse_kernel(const Inst* __restrict__ insts, StagePtrs s
     }
 }
 
-// 3D pass 0: x on the grid with 9 ghost layers (extent n + 18), of which the 6 the passes below
-// read are filled, every ghost node mapped once (periodic shift, wall mirror), so those passes
-// read positions without branches.  When the pass writes the context's metrics buffer M, the
+// 3D pass 0: x on the grid with 9 ghost layers (extent n + 18), filled within `pad` of them (6
+// when the nested operators run at the interior nodes only, 9 when they also run on the 3 ghost
+// layers of the metrics buffer), every ghost node mapped once (periodic shift, wall mirror), so
+// the passes below read positions without branches.  When the pass writes the context's metrics buffer M, the
 // interior positions also go to Xm (the positions M's spatial rows are formed from).
 __global__ void xe_fill_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
                                const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr, int reset_n,
-                               const int* reuse)
+                               const int* reuse, int pad)
 {
     pdl_entry();
     reset_reductions(reset_n > 0 ? scr : nullptr, reset_n);
@@ -188,7 +189,7 @@ __global__ void xe_fill_kernel(const Inst* __restrict__ insts, StagePtrs single,
         if (keep && I.fixed) continue;
         ES_PTRS(S);
         int i0, i1, i2;
-        if (!tile_node(I, it.y, 6, i0, i1, i2)) continue;
+        if (!tile_node(I, it.y, pad, i0, i1, i2)) continue;
         const long long X0 = I.n[0] + 18, X1 = I.n[1] + 18, nx = X0 * X1 * (I.n[2] + 18);
         const long long e = ((long long)(i2 + 9) * X1 + (i1 + 9)) * X0 + (i0 + 9);
         double v[3];
@@ -210,12 +211,13 @@ __global__ void xe_fill_kernel(const Inst* __restrict__ insts, StagePtrs single,
     }
 }
 
-// 3D pass 1: at the nodes within 3 ghost layers (stored on the grid with 6 ghost layers, extent
-// n + 12), from the ghost-extended positions, the products P[b][j] = delta_b[x_p] x_q for
+// 3D pass 1: at the nodes within `pad` ghost layers (3 or 6; stored on the grid with 6 ghost
+// layers, extent n + 12), from the ghost-extended positions, the products P[b][j] = delta_b[x_p] x_q for
 // (p, q) = (2,3), (3,1), (1,2) (j = 1, 2, 3): every delta_b[x_p] enters Eq. (SCLCoeff) only
 // multiplied by x_q at the same node
 __global__ void dx3d_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
-                            const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr, const int* reuse)
+                            const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr, const int* reuse,
+                            int pad)
 {
     pdl_entry();
     if (reuse && *reuse) return;      // the spatial metrics in M are those of this mesh
@@ -225,7 +227,7 @@ __global__ void dx3d_kernel(const Inst* __restrict__ insts, StagePtrs single, co
         const Inst& I = insts[it.x];
         long long E0 = I.n[0] + 12, E1 = I.n[1] + 12, E2 = I.n[2] + 12, ne = E0 * E1 * E2;
         int i0, i1, i2;
-        if (!tile_node(I, it.y, 3, i0, i1, i2)) continue;
+        if (!tile_node(I, it.y, pad, i0, i1, i2)) continue;
         const long long p = ((long long)(i2 + 6) * E1 + (i1 + 6)) * E0 + (i0 + 6);
         const long long X0 = I.n[0] + 18, X1 = I.n[1] + 18, nx = X0 * X1 * (I.n[2] + 18);
         const long long xc = ((long long)(i2 + 9) * X1 + (i1 + 9)) * X0 + (i0 + 9);
@@ -259,13 +261,14 @@ __global__ void dx3d_kernel(const Inst* __restrict__ insts, StagePtrs single, co
 
 // 3D pass 2: J xi_k/x_j = (delta_a[P_b] - delta_b[P_a]) / (dxi_a dxi_b), P_b = delta_b[x_p] x_q
 // with (a, b) = (3,2), (1,3), (2,1) for k = 1, 2, 3 and (p, q) = (2,3), (3,1), (1,2)
-// for j = 1, 2, 3 (cyclic permutation of Eq. (SCLCoeff)), at the interior nodes (the ghost
-// layers follow by metrics3d_ghost_kernel).  Every ordered pair (a, b), a != b, belongs to
+// for j = 1, 2, 3 (cyclic permutation of Eq. (SCLCoeff)), at the nodes within `pad` ghost layers
+// (0: the ghost layers follow by metrics3d_ghost_kernel; 3: the whole padded buffer).  Every
+// ordered pair (a, b), a != b, belongs to
 // exactly one k, with sign +1 when (a, b) is k's pair and -1 when reversed; the kernel walks
 // the outer direction a and offset m once and adds each product term to its k.
 __global__ void metrics3d_kernel(const Inst* __restrict__ insts, StagePtrs single, const StagePtrs* __restrict__ table,
                                  const int2* __restrict__ work, int nwork, const Scratch* __restrict__ scr, int* flag,
-                                 int consult, int vcl)
+                                 int consult, int vcl, int pad)
 {
     pdl_entry();
     const bool keep = consult && flag[2];   // spatial rows of M already formed: the VCL rows only,
@@ -284,7 +287,7 @@ __global__ void metrics3d_kernel(const Inst* __restrict__ insts, StagePtrs singl
         const Inst& I = insts[it.x];
         ES_PTRS(S);
         int i0, i1, i2;
-        if (!tile_node(I, it.y, 0, i0, i1, i2)) continue;
+        if (!tile_node(I, it.y, pad, i0, i1, i2)) continue;
         const long long p = plin(I, i0, i1, i2);
         double* M = S.M;
         const long long np = I.npad;

@@ -63,11 +63,11 @@ void launch_metrics2d(bool dot, int grid, cudaStream_t st, const Inst* insts, co
 __global__ void metrics_reuse_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work,
                                      int nwork, const Scratch* scr, int* flag);
 __global__ void xe_fill_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work, int nwork,
-                               const Scratch* scr, int reset_n, const int* reuse);
+                               const Scratch* scr, int reset_n, const int* reuse, int pad);
 __global__ void dx3d_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work, int nwork,
-                            const Scratch* scr, const int* reuse);
+                            const Scratch* scr, const int* reuse, int pad);
 __global__ void metrics3d_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work, int nwork,
-                                 const Scratch* scr, int* flag, int consult, int vcl);
+                                 const Scratch* scr, int* flag, int consult, int vcl, int pad);
 __global__ void metrics3d_ghost_kernel(const Inst* insts, StagePtrs single, const StagePtrs* table, const int2* work,
                                        int nwork, const int* flag, int consult, int vcl);
 __global__ void conversion_check_kernel(const double* in, int n, float* o32, double* o64);
