@@ -25,13 +25,17 @@ def _ctx(pb, precision=0):
     return es.Context(pb, precision)
 
 
+@pytest.mark.parametrize("form", [0, 1])
 @pytest.mark.parametrize("d", [2, 3])
-@pytest.mark.parametrize("bc", ["periodic", "mixed"])
-def test_init_mesh_and_metrics(d, bc):
+@pytest.mark.parametrize("bc", ["periodic", "mixed", "reflect"])
+def test_init_mesh_and_metrics(d, bc, form):
+    """J^0 and the padded metrics buffer (ghost layers included) against the oracle at 1e-12 in
+    both forms: the metrics are FP64 in both; the mixed form forms the 3D ghost layers by the
+    symmetry of the boundary maps, the FP64 form by the nested operators."""
     torch = need_gpu()
     pb, JU, J, x, xdot = case(d, 1, GRIDS[d], bc)
     o = Oracle(pb)
-    ctx = _ctx(pb)
+    ctx = _ctx(pb, form)
     Jg = ctx.es_init_mesh(to_dev(x, torch)).cpu().numpy()
     assert rel_max_err(Jg, o.init_J(x)) <= TOL_FP64
     Mg = ctx.es_metrics(to_dev(x, torch), to_dev(xdot, torch)).cpu().numpy()
