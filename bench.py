@@ -826,6 +826,28 @@ def main_ours(args):
             torch.cuda.synchronize()
             errs[name] = errors_vs(ref1[0], ref1[1], pb, r.JU.cpu().numpy(), r.J.cpu().numpy())
             errs[name]["vs"] = "FP64 oracle after one full step from t = 0"
+        # the mixed form against the FP64 GPU form over a longer run (the FP64 form matches the
+        # oracle at 1e-12 per step; the oracle itself takes about a second a step), both with one
+        # fixed Delta t so that they stay at the same time levels; the meshes move with each
+        # form's own monitor, so x is compared too
+        rm, rd = runners["mixed"], runners["fp64"]
+        rm.reset()
+        rd.reset()
+        _, dd0 = rd.ctx.mesh_redistribute(rd.JU, rd.J, rd.x)
+        dtf = 0.8 * float(dd0[0])
+        done = 0
+        for k_long in (100, 500):
+            while done < k_long:
+                rm.ctx.es_step(rm.JU, rm.J, rm.x, dtf, rm.xdot, rm.dd)
+                rd.ctx.es_step(rd.JU, rd.J, rd.x, dtf, rd.xdot, rd.dd)
+                done += 1
+            torch.cuda.synchronize()
+            e = errors_vs(rd.JU.cpu().numpy(), rd.J.cpu().numpy(), pb, rm.JU.cpu().numpy(), rm.J.cpu().numpy())
+            e["x_linf"] = float((rm.x - rd.x).abs().max())
+            e["t"] = k_long * dtf
+            e["status"] = [rm.ctx.es_poll_status(), rd.ctx.es_poll_status()]
+            e["vs"] = "FP64 GPU form after %d full steps of one fixed Delta t from t = 0" % k_long
+            errs["mixed_vs_fp64_gpu_%d_steps" % k_long] = e
         # the batched launch: a fresh batch of the same 64 instances, one step, and the
         # oracle on its three smallest instances and its largest
         if not args.no_batched:
