@@ -202,11 +202,12 @@ def test_run_host_equals_device_steps(form):
 def test_mesh_tiles_bitwise(bc):
     """The fused mixed 2D mesh step (monitor, filter passes and Jacobi sweeps in one launch) in
     every tile shape gives the mesh velocity and Delta t / Delta tau of shape 0 bit for bit:
-    ragged and sub-tile grids, the largest fused halo (mu = 8, n_f = 4), and a batch of uneven
-    instances; es_autotune keeps one of the shapes and changes no result."""
+    ragged and sub-tile grids, the largest fused halo (mu = 8, n_f = 4) and the smallest (one
+    sweep, no filter pass), and a batch of uneven instances; es_autotune keeps one of the shapes
+    and changes no result."""
     torch = need_gpu()
     from paper_2202_07989_gb300 import es
-    for n, mu, nf, seed in (((70, 37), 5, 3, 21), ((10, 11), 4, 2, 22), ((53, 41), 8, 4, 23)):
+    for n, mu, nf, seed in (((70, 37), 5, 3, 21), ((10, 11), 4, 2, 22), ((53, 41), 8, 4, 23), ((33, 17), 1, 0, 24)):
         pb, JU, J, x, _ = case(2, 2, n, bc, es=True, seed=seed, jump=True)
         pb = pb.with_(mu=mu, nf=nf, sigma=(W.SIG_RHO1, W.SIG_P), alpha=(60.0, 25.0))
         ctx = _ctx(pb, 1)
