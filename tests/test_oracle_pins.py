@@ -252,6 +252,40 @@ def test_interface_eigenvectors_reduce_to_point(d, N):
     np.testing.assert_allclose(R, o.eigvec_point(U), rtol=1e-12, atol=1e-12)
 
 
+@pytest.mark.parametrize("d,N", CASES)
+def test_interface_averages_are_symmetric_and_between(d, N):
+    """The interface averages of Sec. 3.4 are means of the two states: swapping the states
+    leaves the averaged R and c-bar unchanged, and c-bar^2 = R-bar Gamma-bar T-bar lies between
+    the smallest and largest products of the two states' R_mix, Gamma_mix and T (T-bar is a
+    mean of T, R-bar and Gamma-bar are means of the mixture values).  A one-sided value (the
+    left state's in place of a mean) or a wrong average (a sum, rho-bar in place of T-bar)
+    fails one of them."""
+    pb = _pb(d, N, 1.0)
+    o = Oracle(pb)
+    rng = np.random.default_rng(19 + 10 * d + N)
+
+    def mix(U):
+        rho_l = U[:N]
+        rho = rho_l.sum()
+        v2 = sum((U[N + m] / rho) ** 2 for m in range(d))
+        cvr = sum(pb.cv[l] * rho_l[l] for l in range(N))
+        rr = sum(pb.R(l) * rho_l[l] for l in range(N))
+        T = (U[N + d] - 0.5 * rho * v2 - sum(pb.pinf[:N])) / cvr
+        gmix = sum(pb.gamma[l] * pb.cv[l] * rho_l[l] for l in range(N)) / cvr
+        return rr / rho, gmix, T
+
+    for _ in range(20):
+        Ul, Ur = _random_state(pb, rng), _random_state(pb, rng)
+        R1, c1 = o.eigvec_avg(Ul, Ur)
+        R2, c2 = o.eigvec_avg(Ur, Ul)
+        np.testing.assert_allclose(R1, R2, rtol=1e-13, atol=1e-13 * np.abs(R1).max())
+        assert abs(c1 - c2) <= 1e-13 * c1
+        (Rl, Gl, Tl), (Rr, Gr, Tr) = mix(Ul), mix(Ur)
+        lo = min(Rl, Rr) * min(Gl, Gr) * min(Tl, Tr)
+        hi = max(Rl, Rr) * max(Gl, Gr) * max(Tl, Tr)
+        assert lo * (1 - 1e-12) <= c1 * c1 <= hi * (1 + 1e-12), (lo, c1 * c1, hi)
+
+
 # ---------------------------------------------------------------------------
 # WENO-MR (Appendix A)
 # ---------------------------------------------------------------------------
