@@ -53,7 +53,7 @@ struct es_ctx {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t run_exec = nullptr;
     double run_dtf = 0.0;
-    double* tacc_pinned = nullptr;     // pinned host word for the elapsed time
+    double* tacc_pinned = nullptr;     // mapped pinned host word for the elapsed time (htacc: its device address)
     int sms = 152;
     // flux launch configuration per direction (defaults, or the autotuner's choice)
     int flux_shape[3] = { SHAPE_DEFAULT_K0, SHAPE_DEFAULT_KN, SHAPE_DEFAULT_KN };
@@ -986,8 +986,11 @@ es_status es_run_host(es_ctx* c, double* JU, double* J, double* x, int steps, do
         // JU, J and x consecutive in one block (see copy_state)
         bool ok = dalloc(c, (void**)&c->hJU, sizeof(double) * (I.nc + 1 + I.d) * n) &&
                   dalloc(c, (void**)&c->hxd, sizeof(double) * I.d * n) &&
-                  dalloc(c, (void**)&c->hdt, sizeof(double) * 2) && dalloc(c, (void**)&c->htacc, sizeof(double)) &&
-                  cudaMallocHost((void**)&c->tacc_pinned, sizeof(double)) == cudaSuccess;
+                  dalloc(c, (void**)&c->hdt, sizeof(double) * 2) &&
+                  cudaHostAlloc((void**)&c->tacc_pinned, sizeof(double), cudaHostAllocMapped) == cudaSuccess;
+        // the elapsed time accumulates in a mapped pinned host word: the host zeroes it and
+        // reads it, no copy or memset on the stream
+        ok = ok && cudaHostGetDevicePointer((void**)&c->htacc, c->tacc_pinned, 0) == cudaSuccess;
         if (!ok) return fail(c, ES_ERR_CUDA, "es_run_host: allocation failed");
         c->hJ = c->hJU + I.nc * n;
         c->hx = c->hJ + n;
@@ -1019,8 +1022,8 @@ es_status es_run_host(es_ctx* c, double* JU, double* J, double* x, int steps, do
         }
         c->run_dtf = dt_fixed;
     }
+    *c->tacc_pinned = 0.0;    // the previous call synchronised: no kernel writes it now
     copy_state(c, JU, J, x, true, st);
-    cudaMemsetAsync(c->htacc, 0, sizeof(double), st);
     for (int s = 0; s < steps; ++s) {
         if (graph) {
             if (cudaGraphLaunch(c->run_exec, st) != cudaSuccess) return fail(c, ES_ERR_CUDA, "es_run_host: graph launch failed");
@@ -1031,7 +1034,6 @@ es_status es_run_host(es_ctx* c, double* JU, double* J, double* x, int steps, do
         time_acc_kernel<<<1, 1, 0, st>>>(c->htacc, c->hdt);
     }
     copy_state(c, JU, J, x, false, st);
-    cudaMemcpyAsync(c->tacc_pinned, c->htacc, sizeof(double), cudaMemcpyDeviceToHost, st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(c, ES_ERR_CUDA, std::string("es_run_host: ") + cudaGetErrorString(e));
     if (t) *t += *c->tacc_pinned;
