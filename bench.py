@@ -91,7 +91,7 @@ def hbm_peak_gbs():
 # the current kernel (stage 1 10.51 MB; stages 2 and 3, which also read M(xdot) and the step-start
 # state, 18.30 MB each); the capture and its command are in profiles/.  The per-direction launches
 # have no current capture (traffic null when the tuner picks them).
-FLUX2D_TRAFFIC_BYTES = 15.71e6
+FLUX2D_TRAFFIC_BYTES = 15.72e6
 
 
 def flux_flops_per_interface(D, NS, es=True):
