@@ -88,8 +88,8 @@ def hbm_peak_gbs():
         return 6800.0, "fallback"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, cold cache) per fused 2D stage launch
 # of the 400x200 mixed step: the mean of the three stage launches of a step in one ncu capture of
-# the current kernel (stage 1 10.51 MB; stages 2 and 3, which also read M(xdot) and the step-start
-# state, 18.30 MB each); the capture and its command are in profiles/.  The per-direction launches
+# the current kernel (stage 1 10.53 MB; stages 2 and 3, which also read M(xdot) and the step-start
+# state, 18.31 MB each); the capture and its command are in profiles/.  The per-direction launches
 # have no current capture (traffic null when the tuner picks them).
 FLUX2D_TRAFFIC_BYTES = 15.72e6
 
